@@ -1,0 +1,771 @@
+/*
+ * FP64 CPU oracle of the monolithic block AMG V-cycle and its FGMRES wrapper.
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).
+ * Sequential, unblocked, unfused: every loop follows the definition it cites,
+ * so that a reader can check it against the paper by eye.  See
+ * bamg_oracle.h for the interface and the list of paper passages.
+ *
+ * Compiled with -ffp-contract=off so that no multiply-add is fused and the
+ * result is the same on every host.
+ */
+#include "bamg_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* sparse block helpers                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* y = A x with block CSR A (b x b blocks, row-major). */
+int oracle_spmv(int n, int b, const int* row_ptr, const int* col_idx, const double* vals,
+                const double* x, double* y) {
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < b; ++r) {
+            double acc = 0.0;
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const double* blk = vals + (size_t)k * b * b;
+                int j = col_idx[k];
+                for (int c = 0; c < b; ++c) acc += blk[r * b + c] * x[(size_t)j * b + c];
+            }
+            y[(size_t)i * b + r] = acc;
+        }
+    }
+    return ORACLE_OK;
+}
+
+static double dot(size_t m, const double* a, const double* b) {
+    double s = 0.0;
+    for (size_t i = 0; i < m; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double nrm2(size_t m, const double* a) { return sqrt(dot(m, a, a)); }
+
+/* ------------------------------------------------------------------------ */
+/* Aggregation (Sec. 4.3.1): the aggregates are a disjoint cover of the     */
+/* nodes, each gives one coarse node, and they are formed greedily on the   */
+/* node graph of the matrix.  The greedy rule (the paper names none):       */
+/*  1. visit nodes in ascending index; a node whose neighbours and itself   */
+/*     are all still free becomes a root, and it and its neighbours form    */
+/*     one aggregate;                                                       */
+/*  2. every node still free joins the aggregate of step 1 that holds most  */
+/*     of its neighbours (ties: the smallest aggregate id), judged on the   */
+/*     membership of step 1 only;                                           */
+/*  3. aggregate ids are the ranks of the roots in ascending index.         */
+/* After step 1 every free node has a neighbour in some aggregate (a node   */
+/* with all neighbours free would have become a root), so step 2 places     */
+/* every node.                                                              */
+/* ------------------------------------------------------------------------ */
+int oracle_aggregate(int n, const int* row_ptr, const int* col_idx, int* agg, int* is_root) {
+    if (n < 0) return ORACLE_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        agg[i] = -1;
+        is_root[i] = 0;
+    }
+    int n_agg = 0;
+    /* step 1: roots in ascending index; ids are assigned in the same order */
+    for (int i = 0; i < n; ++i) {
+        if (agg[i] != -1) continue;
+        int all_free = 1;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int j = col_idx[k];
+            if (j != i && agg[j] != -1) all_free = 0;
+        }
+        if (!all_free) continue;
+        is_root[i] = 1;
+        agg[i] = n_agg;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) agg[col_idx[k]] = n_agg;
+        n_agg++;
+    }
+    /* step 2: attach the remaining nodes by step-1 membership */
+    int* phase1 = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!phase1) return ORACLE_ENOMEM;
+    memcpy(phase1, agg, sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (phase1[i] != -1) continue;
+        int best = -1, best_count = 0;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int j = col_idx[k];
+            if (j == i || phase1[j] == -1) continue;
+            int a = phase1[j];
+            int count = 0;
+            for (int k2 = row_ptr[i]; k2 < row_ptr[i + 1]; ++k2) {
+                int j2 = col_idx[k2];
+                if (j2 != i && phase1[j2] == a) count++;
+            }
+            if (count > best_count || (count == best_count && a < best)) {
+                best = a;
+                best_count = count;
+            }
+        }
+        agg[i] = best;
+    }
+    free(phase1);
+    for (int i = 0; i < n; ++i)
+        if (agg[i] < 0) return ORACLE_EINVAL; /* unreachable for a structurally symmetric graph */
+    return n_agg;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Colouring for the multicolour node-block Gauss-Seidel sub-solve:         */
+/* first fit in ascending index, colour(i) = smallest colour not used by a  */
+/* neighbour j < i.                                                         */
+/* ------------------------------------------------------------------------ */
+int oracle_colour(int n, const int* row_ptr, const int* col_idx, int* colour) {
+    int max_deg = 0;
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > max_deg) max_deg = row_ptr[i + 1] - row_ptr[i];
+    int* used = (int*)calloc((size_t)max_deg + 2, sizeof(int));
+    if (!used) return ORACLE_ENOMEM;
+    int n_colours = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int c = 0; c < max_deg + 2; ++c) used[c] = 0;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int j = col_idx[k];
+            if (j < i && colour[j] <= max_deg) used[colour[j]] = 1;
+        }
+        int c = 0;
+        while (used[c]) c++;
+        colour[i] = c;
+        if (c + 1 > n_colours) n_colours = c + 1;
+    }
+    free(used);
+    return n_colours;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Galerkin coarse operator A_c = R A P (Sec. 3) with R = P^T and the       */
+/* piecewise-constant P of Sec. 4.3.1: P[(i,d),(agg(i),d)] = 1 for every    */
+/* dof d, the same aggregates for every field (cloned), so P is block       */
+/* diagonal across fields (eq. blocktransfers).  Then                       */
+/*   A_c[I,J] = sum_{i in I} sum_{j in J} A[i,j]      (b x b block sums),   */
+/* pattern = every (agg(i), agg(j)) with (i,j) stored, columns ascending,   */
+/* values accumulated with i ascending, then j in stored order.             */
+/* ------------------------------------------------------------------------ */
+static int cmp_int(const void* a, const void* b) {
+    int x = *(const int*)a, y = *(const int*)b;
+    return (x > y) - (x < y);
+}
+
+/* members of every aggregate in ascending node order (counting sort) */
+static int aggregate_members(int n, const int* agg, int nc, int** mptr_out, int** mem_out) {
+    int* mptr = (int*)calloc((size_t)nc + 1, sizeof(int));
+    int* mem = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int* fill = (int*)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    if (!mptr || !mem || !fill) return ORACLE_ENOMEM;
+    for (int i = 0; i < n; ++i) {
+        if (agg[i] < 0 || agg[i] >= nc) return ORACLE_EINVAL;
+        mptr[agg[i] + 1]++;
+    }
+    for (int I = 0; I < nc; ++I) mptr[I + 1] += mptr[I];
+    for (int I = 0; I < nc; ++I) fill[I] = mptr[I];
+    for (int i = 0; i < n; ++i) mem[fill[agg[i]]++] = i;
+    free(fill);
+    *mptr_out = mptr;
+    *mem_out = mem;
+    return ORACLE_OK;
+}
+
+int oracle_rap_tentative(int n, int b, const int* row_ptr, const int* col_idx, const double* vals,
+                         const int* agg, int nc, int* rp_c, int* ci_c, double* vals_c) {
+    if (!rp_c) return ORACLE_EINVAL;
+    int *mptr, *mem;
+    int st = aggregate_members(n, agg, nc, &mptr, &mem);
+    if (st) return st;
+    int* mark = (int*)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    if (!mark) return ORACLE_ENOMEM;
+    for (int J = 0; J < nc; ++J) mark[J] = -1;
+    if (!ci_c) {
+        /* pattern sizes: for every coarse row I the number of distinct agg(j) */
+        rp_c[0] = 0;
+        for (int I = 0; I < nc; ++I) {
+            int count = 0;
+            for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+                int i = mem[q];
+                for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                    int J = agg[col_idx[k]];
+                    if (mark[J] != I) {
+                        mark[J] = I;
+                        count++;
+                    }
+                }
+            }
+            rp_c[I + 1] = rp_c[I] + count;
+        }
+        free(mark);
+        free(mptr);
+        free(mem);
+        return rp_c[nc];
+    }
+    /* column indices: the distinct agg(j) of each coarse row, sorted */
+    for (int I = 0; I < nc; ++I) {
+        int fill = rp_c[I];
+        for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+            int i = mem[q];
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int J = agg[col_idx[k]];
+                if (mark[J] != I) {
+                    mark[J] = I;
+                    ci_c[fill++] = J;
+                }
+            }
+        }
+        if (fill != rp_c[I + 1]) return ORACLE_EINVAL;
+        qsort(ci_c + rp_c[I], (size_t)(rp_c[I + 1] - rp_c[I]), sizeof(int), cmp_int);
+    }
+    free(mark);
+    free(mptr);
+    free(mem);
+    /* values: i ascending, then stored order of row i */
+    const size_t bb = (size_t)b * b;
+    memset(vals_c, 0, sizeof(double) * bb * (size_t)rp_c[nc]);
+    for (int i = 0; i < n; ++i) {
+        int I = agg[i];
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int J = agg[col_idx[k]];
+            int p = -1;
+            for (int q = rp_c[I]; q < rp_c[I + 1]; ++q)
+                if (ci_c[q] == J) p = q;
+            if (p < 0) return ORACLE_EINVAL;
+            for (size_t e = 0; e < bb; ++e) vals_c[(size_t)p * bb + e] += vals[(size_t)k * bb + e];
+        }
+    }
+    return rp_c[nc];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small dense inverses (node-block diagonal of one field): Gauss-Jordan    */
+/* elimination with partial pivoting on [a | I].                            */
+/* ------------------------------------------------------------------------ */
+int oracle_block_inverse(int m, const double* a, double* ainv) {
+    double w[ORACLE_MAX_B * ORACLE_MAX_B], v[ORACLE_MAX_B * ORACLE_MAX_B];
+    if (m < 1 || m > ORACLE_MAX_B) return ORACLE_EINVAL;
+    double norm = 0.0;
+    for (int r = 0; r < m; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < m; ++c) s += fabs(a[r * m + c]);
+        if (s > norm) norm = s;
+    }
+    for (int e = 0; e < m * m; ++e) w[e] = a[e];
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) v[r * m + c] = (r == c) ? 1.0 : 0.0;
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        for (int r = k + 1; r < m; ++r)
+            if (fabs(w[r * m + k]) > fabs(w[p * m + k])) p = r;
+        if (!(fabs(w[p * m + k]) >= 1e-14 * norm) || norm == 0.0) return ORACLE_ESINGULAR_BLOCK;
+        if (p != k) {
+            for (int c = 0; c < m; ++c) {
+                double t = w[k * m + c];
+                w[k * m + c] = w[p * m + c];
+                w[p * m + c] = t;
+                t = v[k * m + c];
+                v[k * m + c] = v[p * m + c];
+                v[p * m + c] = t;
+            }
+        }
+        double piv = w[k * m + k];
+        for (int c = 0; c < m; ++c) {
+            w[k * m + c] /= piv;
+            v[k * m + c] /= piv;
+        }
+        for (int r = 0; r < m; ++r) {
+            if (r == k) continue;
+            double f = w[r * m + k];
+            for (int c = 0; c < m; ++c) {
+                w[r * m + c] -= f * w[k * m + c];
+                v[r * m + c] -= f * v[k * m + c];
+            }
+        }
+    }
+    for (int e = 0; e < m * m; ++e) ainv[e] = v[e];
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense LU with partial pivoting for the direct solve on the coarsest      */
+/* level (Fig. 1, "u <- A^{-1} b" at l_max).                                */
+/* ------------------------------------------------------------------------ */
+int oracle_lu_factor(int n, double* a, int* piv) {
+    double norm = 0.0;
+    for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) s += fabs(a[(size_t)r * n + c]);
+        if (s > norm) norm = s;
+    }
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(a[(size_t)r * n + k]) > fabs(a[(size_t)p * n + k])) p = r;
+        if (!(fabs(a[(size_t)p * n + k]) >= 1e-14 * norm) || norm == 0.0)
+            return ORACLE_ESINGULAR_COARSE;
+        piv[k] = p;
+        if (p != k)
+            for (int c = 0; c < n; ++c) {
+                double t = a[(size_t)k * n + c];
+                a[(size_t)k * n + c] = a[(size_t)p * n + c];
+                a[(size_t)p * n + c] = t;
+            }
+        for (int r = k + 1; r < n; ++r) {
+            double l = a[(size_t)r * n + k] / a[(size_t)k * n + k];
+            a[(size_t)r * n + k] = l;
+            for (int c = k + 1; c < n; ++c) a[(size_t)r * n + c] -= l * a[(size_t)k * n + c];
+        }
+    }
+    return ORACLE_OK;
+}
+
+int oracle_lu_solve(int n, const double* lu, const int* piv, const double* rhs, double* x) {
+    for (int i = 0; i < n; ++i) x[i] = rhs[i];
+    for (int k = 0; k < n; ++k) {
+        double t = x[k];
+        x[k] = x[piv[k]];
+        x[piv[k]] = t;
+    }
+    for (int i = 0; i < n; ++i) { /* L y = P rhs, unit lower */
+        double s = x[i];
+        for (int c = 0; c < i; ++c) s -= lu[(size_t)i * n + c] * x[c];
+        x[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) { /* U x = y */
+        double s = x[i];
+        for (int c = i + 1; c < n; ++c) s -= lu[(size_t)i * n + c] * x[c];
+        x[i] = s / lu[(size_t)i * n + i];
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchy                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n, nnzb, n_colours, n_agg;
+    int *row_ptr, *col_idx;
+    double* vals;
+    int* agg;       /* [n] aggregate of each node (levels above the coarsest) */
+    int* colour;    /* [n] */
+    double* dinv;   /* [n][F][fb*fb] */
+    double *u, *rhs, *res; /* work vectors of n*b */
+} olevel;
+
+struct oracle_hier {
+    int nlev, b, F, fb;
+    int field_of_dof[ORACLE_MAX_B];
+    int fstart[ORACLE_MAX_B]; /* first dof of each field inside a node */
+    oracle_params p;
+    olevel lev[ORACLE_MAX_LEVELS];
+    double* lu; /* coarsest level, dense LU */
+    int* piv;
+    int nc_dense;
+    double* xt; /* smoother scratch: x~ and r_f of one field, n*fb each */
+    double* rf;
+};
+
+static void level_free(olevel* L) {
+    free(L->row_ptr);
+    free(L->col_idx);
+    free(L->vals);
+    free(L->agg);
+    free(L->colour);
+    free(L->dinv);
+    free(L->u);
+    free(L->rhs);
+    free(L->res);
+}
+
+void oracle_free(oracle_hier* h) {
+    if (!h) return;
+    for (int l = 0; l < h->nlev; ++l) level_free(&h->lev[l]);
+    free(h->lu);
+    free(h->piv);
+    free(h->xt);
+    free(h->rf);
+    free(h);
+}
+
+int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
+                 const double* vals, const int* field_of_dof, const oracle_params* p,
+                 oracle_hier** out) {
+    *out = NULL;
+    if (n <= 0 || b < 1 || b > ORACLE_MAX_B || p->max_levels < 1 || p->max_levels > ORACLE_MAX_LEVELS)
+        return ORACLE_EINVAL;
+    oracle_hier* h = (oracle_hier*)calloc(1, sizeof(oracle_hier));
+    if (!h) return ORACLE_ENOMEM;
+    h->b = b;
+    h->p = *p;
+    /* fields: contiguous, non-decreasing 0..F-1, equal sizes */
+    int F = 0;
+    for (int d = 0; d < b; ++d) {
+        h->field_of_dof[d] = field_of_dof[d];
+        if (d > 0 && field_of_dof[d] != field_of_dof[d - 1] && field_of_dof[d] != field_of_dof[d - 1] + 1) {
+            free(h);
+            return ORACLE_EINVAL;
+        }
+        if (field_of_dof[d] + 1 > F) F = field_of_dof[d] + 1;
+    }
+    if (field_of_dof[0] != 0 || b % F != 0) {
+        free(h);
+        return ORACLE_EINVAL;
+    }
+    h->F = F;
+    h->fb = b / F;
+    for (int f = 0; f < F; ++f) {
+        int cnt = 0, first = -1;
+        for (int d = 0; d < b; ++d)
+            if (field_of_dof[d] == f) {
+                if (first < 0) first = d;
+                cnt++;
+            }
+        if (cnt != h->fb) {
+            free(h);
+            return ORACLE_EINVAL;
+        }
+        h->fstart[f] = first;
+    }
+    const size_t bb = (size_t)b * b;
+    /* level 0 = a copy of A */
+    olevel* L0 = &h->lev[0];
+    L0->n = n;
+    L0->nnzb = nnzb;
+    L0->row_ptr = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+    L0->col_idx = (int*)malloc(sizeof(int) * (size_t)nnzb);
+    L0->vals = (double*)malloc(sizeof(double) * bb * (size_t)nnzb);
+    memcpy(L0->row_ptr, row_ptr, sizeof(int) * (size_t)(n + 1));
+    memcpy(L0->col_idx, col_idx, sizeof(int) * (size_t)nnzb);
+    memcpy(L0->vals, vals, sizeof(double) * bb * (size_t)nnzb);
+    h->nlev = 1;
+    int st = ORACLE_OK;
+    /* coarsen while n*b > max_coarse and fewer than max_levels levels */
+    while (h->nlev < p->max_levels && (long)h->lev[h->nlev - 1].n * b > p->max_coarse) {
+        olevel* F_ = &h->lev[h->nlev - 1];
+        F_->agg = (int*)malloc(sizeof(int) * (size_t)F_->n);
+        int* is_root = (int*)malloc(sizeof(int) * (size_t)F_->n);
+        int nc = oracle_aggregate(F_->n, F_->row_ptr, F_->col_idx, F_->agg, is_root);
+        free(is_root);
+        if (nc < 0) {
+            st = nc;
+            break;
+        }
+        if (nc == 0 || nc == F_->n) { /* no coarsening possible */
+            free(F_->agg);
+            F_->agg = NULL;
+            break;
+        }
+        F_->n_agg = nc;
+        olevel* C = &h->lev[h->nlev];
+        C->n = nc;
+        C->row_ptr = (int*)malloc(sizeof(int) * (size_t)(nc + 1));
+        int nnzc = oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc,
+                                        C->row_ptr, NULL, NULL);
+        C->nnzb = nnzc;
+        C->col_idx = (int*)malloc(sizeof(int) * (size_t)nnzc);
+        C->vals = (double*)malloc(sizeof(double) * bb * (size_t)nnzc);
+        oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc, C->row_ptr,
+                             C->col_idx, C->vals);
+        h->nlev++;
+    }
+    if (st != ORACLE_OK) {
+        oracle_free(h);
+        return st;
+    }
+    /* smoother data on every level except the coarsest */
+    size_t max_n = 0;
+    for (int l = 0; l < h->nlev; ++l) {
+        olevel* L = &h->lev[l];
+        if ((size_t)L->n > max_n) max_n = (size_t)L->n;
+        L->u = (double*)calloc((size_t)L->n * b, sizeof(double));
+        L->rhs = (double*)calloc((size_t)L->n * b, sizeof(double));
+        L->res = (double*)calloc((size_t)L->n * b, sizeof(double));
+        if (l == h->nlev - 1) break;
+        L->colour = (int*)malloc(sizeof(int) * (size_t)L->n);
+        L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
+        L->dinv = (double*)malloc(sizeof(double) * (size_t)L->n * F * h->fb * h->fb);
+        for (int i = 0; i < L->n && st == ORACLE_OK; ++i) {
+            int kd = -1;
+            for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k)
+                if (L->col_idx[k] == i) kd = k;
+            if (kd < 0) {
+                st = ORACLE_EINVAL;
+                break;
+            }
+            for (int f = 0; f < F; ++f) {
+                double blk[ORACLE_MAX_B * ORACLE_MAX_B];
+                int s = h->fstart[f], fb = h->fb;
+                for (int r = 0; r < fb; ++r)
+                    for (int c = 0; c < fb; ++c) blk[r * fb + c] = L->vals[(size_t)kd * bb + (s + r) * b + (s + c)];
+                st = oracle_block_inverse(fb, blk, L->dinv + ((size_t)i * F + f) * fb * fb);
+                if (st != ORACLE_OK) break;
+            }
+        }
+    }
+    if (st == ORACLE_OK) {
+        h->xt = (double*)calloc(max_n * h->fb, sizeof(double));
+        h->rf = (double*)calloc(max_n * h->fb, sizeof(double));
+        /* coarsest level: dense copy and LU */
+        olevel* L = &h->lev[h->nlev - 1];
+        int nd = L->n * b;
+        h->nc_dense = nd;
+        h->lu = (double*)calloc((size_t)nd * nd, sizeof(double));
+        h->piv = (int*)malloc(sizeof(int) * (size_t)nd);
+        if (!h->lu || !h->piv) st = ORACLE_ENOMEM;
+        for (int i = 0; i < L->n && st == ORACLE_OK; ++i)
+            for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                int j = L->col_idx[k];
+                for (int r = 0; r < b; ++r)
+                    for (int c = 0; c < b; ++c)
+                        h->lu[(size_t)(i * b + r) * nd + (j * b + c)] = L->vals[(size_t)k * bb + r * b + c];
+            }
+        if (st == ORACLE_OK) st = oracle_lu_factor(nd, h->lu, h->piv);
+    }
+    if (st != ORACLE_OK) {
+        oracle_free(h);
+        return st;
+    }
+    *out = h;
+    return ORACLE_OK;
+}
+
+int oracle_num_levels(const oracle_hier* h) { return h->nlev; }
+
+int oracle_level_sizes(const oracle_hier* h, int l, int* n, int* nnzb, int* n_colours, int* n_agg) {
+    if (l < 0 || l >= h->nlev) return ORACLE_EINVAL;
+    const olevel* L = &h->lev[l];
+    if (n) *n = L->n;
+    if (nnzb) *nnzb = L->nnzb;
+    if (n_colours) *n_colours = L->n_colours;
+    if (n_agg) *n_agg = (l < h->nlev - 1) ? L->n_agg : 0;
+    return ORACLE_OK;
+}
+
+int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, double* vals, int* agg,
+                     int* colour, double* dinv) {
+    if (l < 0 || l >= h->nlev) return ORACLE_EINVAL;
+    const olevel* L = &h->lev[l];
+    size_t bb = (size_t)h->b * h->b;
+    if (row_ptr) memcpy(row_ptr, L->row_ptr, sizeof(int) * (size_t)(L->n + 1));
+    if (col_idx) memcpy(col_idx, L->col_idx, sizeof(int) * (size_t)L->nnzb);
+    if (vals) memcpy(vals, L->vals, sizeof(double) * bb * (size_t)L->nnzb);
+    int has_smoother = l < h->nlev - 1;
+    if (agg && has_smoother) memcpy(agg, L->agg, sizeof(int) * (size_t)L->n);
+    if (colour && has_smoother) memcpy(colour, L->colour, sizeof(int) * (size_t)L->n);
+    if (dinv && has_smoother)
+        memcpy(dinv, L->dinv, sizeof(double) * (size_t)L->n * h->F * h->fb * h->fb);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Damped block Gauss-Seidel smoother, Algorithm 1 (Sec. 4.3.2), for F      */
+/* field blocks.  One sweep visits the fields in order; for field f:        */
+/*   r_f := b_f - sum_g A_fg x_g        with the current x (which includes  */
+/*                                       the update of field f-1);          */
+/*   solve A_ff x~_f = r_f approximately: one multicolour node-block        */
+/*     Gauss-Seidel sweep from x~ = 0 (colours ascending; node i of colour  */
+/*     c: x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j));        */
+/*   x_f := x_f + omega x~_f.                                               */
+/* ------------------------------------------------------------------------ */
+int oracle_bgs(oracle_hier* h, int l, double* x, const double* rhs, int sweeps) {
+    if (l < 0 || l >= h->nlev - 1) return ORACLE_EINVAL;
+    olevel* L = &h->lev[l];
+    const int b = h->b, F = h->F, fb = h->fb;
+    const size_t bb = (size_t)b * b;
+    double* rf = h->rf;
+    double* xt = h->xt;
+    for (int s = 0; s < sweeps; ++s) {
+        for (int f = 0; f < F; ++f) {
+            const int f0 = h->fstart[f];
+            /* residual of the rows of field f, all columns */
+            for (int i = 0; i < L->n; ++i)
+                for (int r = 0; r < fb; ++r) {
+                    double acc = rhs[(size_t)i * b + f0 + r];
+                    for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                        const double* blk = L->vals + (size_t)k * bb;
+                        int j = L->col_idx[k];
+                        for (int c = 0; c < b; ++c) acc -= blk[(f0 + r) * b + c] * x[(size_t)j * b + c];
+                    }
+                    rf[(size_t)i * fb + r] = acc;
+                }
+            /* approximate A_ff^{-1} r_f: one multicolour node-block GS sweep from zero */
+            for (size_t e = 0; e < (size_t)L->n * fb; ++e) xt[e] = 0.0;
+            for (int col = 0; col < L->n_colours; ++col) {
+                for (int i = 0; i < L->n; ++i) {
+                    if (L->colour[i] != col) continue;
+                    double t[ORACLE_MAX_B];
+                    for (int r = 0; r < fb; ++r) {
+                        double acc = rf[(size_t)i * fb + r];
+                        for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                            int j = L->col_idx[k];
+                            if (j == i) continue;
+                            const double* blk = L->vals + (size_t)k * bb;
+                            for (int c = 0; c < fb; ++c) acc -= blk[(f0 + r) * b + (f0 + c)] * xt[(size_t)j * fb + c];
+                        }
+                        t[r] = acc;
+                    }
+                    const double* Di = L->dinv + ((size_t)i * F + f) * fb * fb;
+                    for (int r = 0; r < fb; ++r) {
+                        double acc = 0.0;
+                        for (int c = 0; c < fb; ++c) acc += Di[r * fb + c] * t[c];
+                        xt[(size_t)i * fb + r] = acc;
+                    }
+                }
+            }
+            /* damped update of field f */
+            for (int i = 0; i < L->n; ++i)
+                for (int r = 0; r < fb; ++r) x[(size_t)i * b + f0 + r] += h->p.omega * xt[(size_t)i * fb + r];
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* V-cycle MGV(u, b, l) of Fig. 1, u = 0 on entry:                          */
+/*   l < l_max: u <- S_pre(A, u, b); r <- b - A u; u_c <- 0;                */
+/*              u_c <- MGV(u_c, R r, l+1); u <- u + P u_c; u <- S_post(...) */
+/*   l = l_max: u <- A^{-1} b                                               */
+/* R r sums r over the members of each aggregate (ascending node order),    */
+/* P u_c copies u_c[agg(i)] to node i, dof by dof.                          */
+/* ------------------------------------------------------------------------ */
+static int mgv(oracle_hier* h, int l, double* u, const double* rhs) {
+    olevel* L = &h->lev[l];
+    const int b = h->b;
+    const size_t nb = (size_t)L->n * b;
+    if (l == h->nlev - 1) return oracle_lu_solve((int)nb, h->lu, h->piv, rhs, u);
+    int st = oracle_bgs(h, l, u, rhs, h->p.n_pre);
+    if (st) return st;
+    oracle_spmv(L->n, b, L->row_ptr, L->col_idx, L->vals, u, L->res);
+    for (size_t e = 0; e < nb; ++e) L->res[e] = rhs[e] - L->res[e];
+    olevel* C = &h->lev[l + 1];
+    const size_t ncb = (size_t)C->n * b;
+    for (size_t e = 0; e < ncb; ++e) {
+        C->rhs[e] = 0.0;
+        C->u[e] = 0.0;
+    }
+    for (int i = 0; i < L->n; ++i)
+        for (int d = 0; d < b; ++d) C->rhs[(size_t)L->agg[i] * b + d] += L->res[(size_t)i * b + d];
+    st = mgv(h, l + 1, C->u, C->rhs);
+    if (st) return st;
+    for (int i = 0; i < L->n; ++i)
+        for (int d = 0; d < b; ++d) u[(size_t)i * b + d] += C->u[(size_t)L->agg[i] * b + d];
+    return oracle_bgs(h, l, u, rhs, h->p.n_post);
+}
+
+int oracle_vcycle(oracle_hier* h, const double* r, double* z) {
+    size_t nb = (size_t)h->lev[0].n * h->b;
+    for (size_t e = 0; e < nb; ++e) z[e] = 0.0;
+    return mgv(h, 0, z, r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restarted flexible GMRES (Saad 1993) with right preconditioning:         */
+/*   r0 = b - A x0, beta = ||r0||, v1 = r0 / beta; for j = 1..m:            */
+/*   z_j = M v_j; w = A z_j; modified Gram-Schmidt against v_1..v_j;        */
+/*   h_{j+1,j} = ||w||; Givens rotations on the Hessenberg column; stop     */
+/*   when |g_{j+1}| / ||b|| <= tol; x = x0 + Z y at the end of the cycle.   */
+/* Happy breakdown when h_{j+1,j} <= 1e-14 ||w|| (w before orthogonalising).*/
+/* ------------------------------------------------------------------------ */
+int oracle_fgmres(oracle_hier* h, const double* b, double* x, double tol, int m, int max_iter,
+                  int prec, int* iters, double* relres) {
+    olevel* L = &h->lev[0];
+    const size_t N = (size_t)L->n * h->b;
+    if (m < 1) return ORACLE_EINVAL;
+    double* V = (double*)malloc(sizeof(double) * N * (size_t)(m + 1));
+    double* Z = (double*)malloc(sizeof(double) * N * (size_t)m);
+    double* w = (double*)malloc(sizeof(double) * N);
+    double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
+    double* cs = (double*)calloc((size_t)m, sizeof(double));
+    double* sn = (double*)calloc((size_t)m, sizeof(double));
+    double* g = (double*)calloc((size_t)m + 1, sizeof(double));
+    double* y = (double*)calloc((size_t)m, sizeof(double));
+    if (!V || !Z || !w || !H || !cs || !sn || !g || !y) return ORACLE_ENOMEM;
+#define HH(i, j) H[(size_t)(i) * m + (j)]
+    int total = 0, converged = 0, st = ORACLE_OK;
+    double bnorm = nrm2(N, b), rel = 0.0;
+    if (bnorm == 0.0) {
+        for (size_t e = 0; e < N; ++e) x[e] = 0.0;
+        converged = 1;
+    }
+    while (!converged) {
+        oracle_spmv(L->n, h->b, L->row_ptr, L->col_idx, L->vals, x, w);
+        for (size_t e = 0; e < N; ++e) w[e] = b[e] - w[e];
+        double beta = nrm2(N, w);
+        rel = beta / bnorm;
+        if (rel <= tol) {
+            converged = 1;
+            break;
+        }
+        if (total >= max_iter) break;
+        for (size_t e = 0; e < N; ++e) V[e] = w[e] / beta;
+        for (int i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = V + (size_t)j * N;
+            double* zj = Z + (size_t)j * N;
+            if (prec == 0) {
+                st = oracle_vcycle(h, vj, zj);
+                if (st) break;
+            } else {
+                for (size_t e = 0; e < N; ++e) zj[e] = vj[e];
+            }
+            oracle_spmv(L->n, h->b, L->row_ptr, L->col_idx, L->vals, zj, w);
+            double wnorm0 = nrm2(N, w);
+            for (int i = 0; i <= j; ++i) {
+                const double* vi = V + (size_t)i * N;
+                HH(i, j) = dot(N, w, vi);
+                for (size_t e = 0; e < N; ++e) w[e] -= HH(i, j) * vi[e];
+            }
+            double hn = nrm2(N, w);
+            HH(j + 1, j) = hn;
+            total++;
+            k = j + 1;
+            int breakdown = !(hn > 1e-14 * wnorm0);
+            if (!breakdown) {
+                double* vn = V + (size_t)(j + 1) * N;
+                for (size_t e = 0; e < N; ++e) vn[e] = w[e] / hn;
+            }
+            for (int i = 0; i < j; ++i) {
+                double t = cs[i] * HH(i, j) + sn[i] * HH(i + 1, j);
+                HH(i + 1, j) = -sn[i] * HH(i, j) + cs[i] * HH(i + 1, j);
+                HH(i, j) = t;
+            }
+            double d = sqrt(HH(j, j) * HH(j, j) + HH(j + 1, j) * HH(j + 1, j));
+            if (d == 0.0) {
+                cs[j] = 1.0;
+                sn[j] = 0.0;
+            } else {
+                cs[j] = HH(j, j) / d;
+                sn[j] = HH(j + 1, j) / d;
+            }
+            HH(j, j) = d;
+            HH(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (fabs(g[j + 1]) / bnorm <= tol || breakdown || total >= max_iter) break;
+        }
+        if (st) break;
+        /* y = H(0:k,0:k)^{-1} g(0:k), upper triangular */
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int c = i + 1; c < k; ++c) s -= HH(i, c) * y[c];
+            y[i] = s / HH(i, i);
+        }
+        for (int i = 0; i < k; ++i) {
+            const double* zi = Z + (size_t)i * N;
+            for (size_t e = 0; e < N; ++e) x[e] += y[i] * zi[e];
+        }
+    }
+#undef HH
+    free(V);
+    free(Z);
+    free(w);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    *iters = total;
+    *relres = rel;
+    if (st) return st;
+    return converged ? ORACLE_OK : ORACLE_NOT_CONVERGED;
+}
