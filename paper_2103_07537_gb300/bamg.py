@@ -1,0 +1,258 @@
+"""Python binding of the bamg C ABI (include/bamg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+arguments are torch CUDA tensors (their storage is passed as a raw pointer),
+host arguments numpy arrays.  Every step of the solve runs in the CUDA
+library; if that library cannot be loaded these functions raise, there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+BAMG_OK, BAMG_NOT_CONVERGED = 0, 1
+BAMG_EINVAL, BAMG_ECUDA, BAMG_ESINGULAR_BLOCK, BAMG_ESINGULAR_COARSE = -1, -2, -3, -4
+BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
+
+#: every symbol the C header declares
+EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
+           "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AmgParams(C.Structure):
+    _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
+                ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int)]
+
+
+class BamgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {amg_strerror(status)} (status {status})")
+        self.status = status
+
+
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libbamg.so (building it in-tree if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"bamg CUDA library not built: {path}")
+            _build.build()
+        lib = C.CDLL(path)
+        lib.amg_default_params.argtypes = [C.POINTER(AmgParams)]
+        lib.amg_default_params.restype = None
+        lib.amg_setup.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip, C.POINTER(AmgParams), _vp,
+                                  C.POINTER(_vp)]
+        lib.amg_apply.argtypes = [_vp, _vp, _vp, _vp]
+        lib.fgmres_solve.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
+        lib.amg_solve_host.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip, C.POINTER(AmgParams), _vp,
+                                       _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
+        lib.bsr_spmv.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
+        lib.amg_num_levels.argtypes = [_vp]
+        lib.amg_level_info.argtypes = [_vp, C.c_int, _ip, _ip, _ip, _ip]
+        lib.amg_level_copy.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.amg_stats.argtypes = [_vp, C.c_char_p, C.c_int]
+        lib.amg_destroy.argtypes = [_vp]
+        lib.amg_strerror.argtypes = [C.c_int]
+        lib.amg_strerror.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _ptr(t) -> int:
+    """Raw device pointer of a contiguous torch CUDA tensor."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _hp(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def amg_strerror(status: int) -> str:
+    return load().amg_strerror(int(status)).decode()
+
+
+def amg_default_params(**overrides) -> AmgParams:
+    p = AmgParams()
+    load().amg_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def amg_setup(row_ptr, col_idx, vals, n_nodes: int, nnzb: int, b: int, field_of_dof, params=None,
+              stream=None) -> int:
+    """Returns the handle (an int); device tensors row_ptr/col_idx (int32), vals (float64)."""
+    fm = np.ascontiguousarray(field_of_dof, dtype=np.int32)
+    h = _vp()
+    st = load().amg_setup(_ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(n_nodes), int(nnzb), int(b),
+                          fm.ctypes.data_as(_ip), C.byref(params) if params is not None else None,
+                          _stream(stream), C.byref(h))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_setup")
+    return h.value
+
+
+def amg_apply(handle: int, r, z, stream=None) -> None:
+    st = load().amg_apply(handle, _ptr(r), _ptr(z), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_apply")
+
+
+def fgmres_solve(handle: int, b, x, tol=1e-8, restart=30, max_iter=10000, stream=None):
+    """Returns (status, iterations, true relative residual); x updated in place."""
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = load().fgmres_solve(handle, _ptr(b), _ptr(x), float(tol), int(restart), int(max_iter), C.byref(it),
+                             C.byref(rr), _stream(stream))
+    if st < 0:
+        raise BamgError(st, "fgmres_solve")
+    return st, it.value, rr.value
+
+
+def amg_solve_host(row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, n_nodes: int, nnzb: int, b: int,
+                   field_of_dof, rhs: np.ndarray, x: np.ndarray, tol=1e-8, restart=30, max_iter=10000,
+                   params=None, stream=None):
+    """Host arrays in, solution written to x (float64, in place)."""
+    fm = np.ascontiguousarray(field_of_dof, dtype=np.int32)
+    for a, dt in ((row_ptr, np.int32), (col_idx, np.int32), (vals, np.float64), (rhs, np.float64),
+                  (x, np.float64)):
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous int32 / float64")
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = load().amg_solve_host(_hp(row_ptr), _hp(col_idx), _hp(vals), int(n_nodes), int(nnzb), int(b),
+                               fm.ctypes.data_as(_ip), C.byref(params) if params is not None else None,
+                               _hp(rhs), _hp(x), float(tol), int(restart), int(max_iter), C.byref(it),
+                               C.byref(rr), _stream(stream))
+    if st < 0:
+        raise BamgError(st, "amg_solve_host")
+    return st, it.value, rr.value
+
+
+def bsr_spmv(row_ptr, col_idx, vals, n_nodes: int, b: int, x, y, stream=None) -> None:
+    st = load().bsr_spmv(_ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(n_nodes), int(b), _ptr(x), _ptr(y),
+                         _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "bsr_spmv")
+
+
+def amg_num_levels(handle: int) -> int:
+    n = load().amg_num_levels(handle)
+    if n < 0:
+        raise BamgError(n, "amg_num_levels")
+    return n
+
+
+def amg_level_info(handle: int, level: int):
+    n, nnz, nc, na = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    st = load().amg_level_info(handle, level, C.byref(n), C.byref(nnz), C.byref(nc), C.byref(na))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_info")
+    return n.value, nnz.value, nc.value, na.value
+
+
+def amg_level_copy(handle: int, level: int, b: int, F: int):
+    """dict of host copies of one level (see include/bamg.h)."""
+    n, nnz, ncol, nagg = amg_level_info(handle, level)
+    coarsest = level == amg_num_levels(handle) - 1
+    fb = b // F
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(nnz, np.int32)
+    v = np.zeros((nnz, b, b))
+    agg = None if coarsest else np.zeros(n, np.int32)
+    col = None if coarsest else np.zeros(n, np.int32)
+    dinv = None if coarsest else np.zeros((n, F, fb, fb))
+    st = load().amg_level_copy(handle, level, _hp(rp), _hp(ci), _hp(v), _hp(agg) if agg is not None else None,
+                               _hp(col) if col is not None else None, _hp(dinv) if dinv is not None else None)
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_copy")
+    return dict(n=n, nnzb=nnz, n_colours=ncol, n_agg=nagg, row_ptr=rp, col_idx=ci, vals=v, agg=agg,
+                colour=col, dinv=dinv)
+
+
+def amg_stats(handle: int) -> dict:
+    buf = C.create_string_buffer(1 << 16)
+    n = load().amg_stats(handle, buf, len(buf))
+    if n < 0:
+        raise BamgError(n, "amg_stats")
+    return json.loads(buf.value.decode())
+
+
+def amg_destroy(handle: int) -> None:
+    load().amg_destroy(handle)
+
+
+class Solver:
+    """Owns one hierarchy built from a block system held in device tensors."""
+
+    def __init__(self, row_ptr, col_idx, vals, b: int, field_of_dof, stream=None, **params):
+        self.b = int(b)
+        self.F = int(max(field_of_dof)) + 1
+        self.n = int(row_ptr.shape[0]) - 1
+        self.row_ptr, self.col_idx, self.vals = row_ptr, col_idx, vals
+        self.params = amg_default_params(**params)
+        self.handle = amg_setup(row_ptr, col_idx, vals, self.n, int(col_idx.shape[0]), self.b, field_of_dof,
+                                self.params, stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                amg_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def num_levels(self) -> int:
+        return amg_num_levels(self.handle)
+
+    def level(self, l: int) -> dict:
+        return amg_level_copy(self.handle, l, self.b, self.F)
+
+    def apply(self, r, z, stream=None):
+        amg_apply(self.handle, r, z, stream)
+        return z
+
+    def solve(self, b, x, tol=1e-8, restart=30, max_iter=10000, stream=None):
+        return fgmres_solve(self.handle, b, x, tol, restart, max_iter, stream)
+
+    def stats(self) -> dict:
+        return amg_stats(self.handle)

@@ -1,0 +1,697 @@
+// C ABI of the bamg library: hierarchy setup, one V-cycle, FGMRES, host
+// end-to-end solve, introspection.  Declarations and argument contracts are
+// in include/bamg.h.  Every compute step runs in the kernels of k_*.cu; this
+// file only allocates, sequences launches and reads back sizes and flags.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace bamg;
+
+namespace {
+
+constexpr int kRapCap = 256;        // maximum stored blocks per coarse row
+constexpr int kMaxCoarseDense = 1536;  // coarsest unknowns handled by the dense solve
+
+struct Level {
+    int n = 0, nnzb = 0, n_colours = 0, n_agg = 0;
+    int *rp = nullptr, *ci = nullptr, *diag = nullptr;
+    double* vals64 = nullptr;
+    float* vals32 = nullptr;
+    int *colour = nullptr, *colour_nodes = nullptr, *colour_ptr_d = nullptr;
+    std::vector<int> colour_ptr;
+    double* dinv64 = nullptr;
+    float* dinv32 = nullptr;
+    int *agg = nullptr, *agg_ptr = nullptr, *members = nullptr;
+    void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
+    int agg_rounds = 0, colour_rounds = 0;
+};
+
+int map_dev_error(int code) {
+    switch (code) {
+        case kDevOk: return BAMG_OK;
+        case kDevSingularBlock: return BAMG_ESINGULAR_BLOCK;
+        case kDevSingularCoarse: return BAMG_ESINGULAR_COARSE;
+        case kDevBadPattern: return BAMG_EINVAL;
+        case kDevRowTooLong: return BAMG_EUNSUPPORTED;
+        case kDevNonFinite: return BAMG_ENAN;
+        default: return BAMG_ECUDA;
+    }
+}
+
+bool supported_block(int b, int fb) {
+    switch (b * 16 + fb) {
+        case 1 * 16 + 1: case 2 * 16 + 2: case 3 * 16 + 3: case 4 * 16 + 4:
+        case 4 * 16 + 2: case 6 * 16 + 6: case 6 * 16 + 3: return true;
+        default: return false;
+    }
+}
+
+}  // namespace
+
+struct bamg_ctx {
+    int b = 0, F = 1, fb = 0, nlev = 0;
+    amg_params p{};
+    Level lev[kMaxLevels];
+    int nd = 0;
+    double *coarse_a = nullptr, *coarse_inv = nullptr;
+    int* coarse_piv = nullptr;
+    std::vector<void*> allocs;
+    long bytes = 0;
+    int* d_err = nullptr;   // device error flags [4]
+    int* h_pin = nullptr;   // pinned host ints [8]
+    cudaStream_t cap_stream = nullptr;
+    // cycle staging (graph input/output) and FP32 boundary buffers
+    double *cyc_in = nullptr, *cyc_out = nullptr;
+    float *r32 = nullptr, *z32 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    // FGMRES workspace
+    int m_alloc = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *h1 = nullptr, *h2 = nullptr,
+           *wsq = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr,
+           *scal = nullptr;
+    double* h_scal = nullptr;  // pinned [4]
+
+    template <typename T>
+    int alloc(T** ptr, size_t count) {
+        *ptr = nullptr;
+        if (count == 0) count = 1;
+        void* q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return BAMG_ECUDA;
+        allocs.push_back(q);
+        bytes += (long)(count * sizeof(T));
+        *ptr = static_cast<T*>(q);
+        return BAMG_OK;
+    }
+    void release(void* q) {
+        for (auto& a : allocs)
+            if (a == q) {
+                cudaFree(a);
+                a = nullptr;
+            }
+    }
+    ~bamg_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* a : allocs)
+            if (a) cudaFree(a);
+        if (h_pin) cudaFreeHost(h_pin);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+#define TRY(expr)                   \
+    do {                            \
+        int _st = (expr);           \
+        if (_st != BAMG_OK) return _st; \
+    } while (0)
+
+// read the device error flags (synchronises s)
+static int check_dev(bamg_ctx* h, cudaStream_t s) {
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return map_dev_error(h->h_pin[0]);
+}
+
+extern "C" void amg_default_params(amg_params* p) {
+    if (!p) return;
+    p->max_levels = 10;
+    p->max_coarse = 2500;
+    p->n_pre = 1;
+    p->n_post = 1;
+    p->omega = 0.5;
+    p->cycle_prec = 64;
+    p->use_graph = 1;
+}
+
+extern "C" const char* amg_strerror(int status) {
+    switch (status) {
+        case BAMG_OK: return "ok";
+        case BAMG_NOT_CONVERGED: return "not converged within max_iter";
+        case BAMG_EINVAL: return "invalid argument or matrix pattern";
+        case BAMG_ECUDA: return "CUDA runtime error";
+        case BAMG_ESINGULAR_BLOCK: return "singular node diagonal block";
+        case BAMG_ESINGULAR_COARSE: return "singular coarsest operator";
+        case BAMG_ENAN: return "non-finite value";
+        case BAMG_ETIMEOUT: return "setup iteration bound exceeded";
+        case BAMG_EUNSUPPORTED: return "size or block shape not supported";
+        default: return "unknown status";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const double* vals, int n,
+                      int nnzb, cudaStream_t s) {
+    const int b = h->b;
+    const size_t bb = (size_t)b * b;
+    TRY(h->alloc(&h->d_err, 4));
+    BAMG_CUDA_TRY(cudaMallocHost(&h->h_pin, 8 * sizeof(int)));
+    BAMG_CUDA_TRY(cudaMallocHost(&h->h_scal, 4 * sizeof(double)));
+    BAMG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s));
+    Level& L0 = h->lev[0];
+    L0.n = n;
+    L0.nnzb = nnzb;
+    TRY(h->alloc(&L0.rp, (size_t)n + 1));
+    TRY(h->alloc(&L0.ci, (size_t)nnzb));
+    TRY(h->alloc(&L0.vals64, (size_t)nnzb * bb));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L0.rp, row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L0.ci, col_idx, sizeof(int) * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L0.vals64, vals, sizeof(double) * bb * nnzb, cudaMemcpyDeviceToDevice, s));
+    // row_ptr consistency is checked on the host side of the device copy
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, L0.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 1, L0.rp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->h_pin[0] != nnzb || h->h_pin[1] != 0) return BAMG_EINVAL;
+
+    h->nlev = 1;
+    for (int l = 0;; ++l) {
+        Level& L = h->lev[l];
+        TRY(h->alloc(&L.diag, (size_t)L.n));
+        TRY(launch_check_pattern(L.n, L.rp, L.ci, L.diag, h->d_err, s));
+        TRY(check_dev(h, s));
+        const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
+        if (!coarsen) break;
+        // aggregation (clone for every field: one aggregate map per level)
+        AggWork w{};
+        int *d_count = nullptr, *scan_tmp = nullptr;
+        const long stb = scan_tmp_bytes(L.n) + 64;
+        TRY(h->alloc(&w.state, (size_t)L.n));
+        TRY(h->alloc(&w.rootid, (size_t)L.n + 1));
+        TRY(h->alloc(&w.agg1, (size_t)L.n));
+        TRY(h->alloc(&w.flag, 4));
+        TRY(h->alloc(&d_count, 4));
+        TRY(h->alloc(&scan_tmp, (size_t)stb / sizeof(int) + 1));
+        TRY(h->alloc(&L.agg, (size_t)L.n));
+        w.host_flag = h->h_pin;
+        BAMG_CUDA_TRY(cudaMemsetAsync(d_count, 0, 4 * sizeof(int), s));
+        int rounds = 0;
+        const int nc = aggregate_nodes(L.n, L.rp, L.ci, L.agg, w, d_count, scan_tmp, stb, s, &rounds);
+        if (nc < 0) return nc;
+        L.agg_rounds = rounds;
+        h->release(w.state);
+        h->release(w.rootid);
+        h->release(w.agg1);
+        if (nc == 0 || nc == L.n) break;  // no coarsening possible
+        L.n_agg = nc;
+        TRY(h->alloc(&L.agg_ptr, (size_t)nc + 1));
+        TRY(h->alloc(&L.members, (size_t)L.n));
+        int* tmp = nullptr;
+        TRY(h->alloc(&tmp, (size_t)nc + 1 + scan_tmp_bytes(nc) / sizeof(int) + 16));
+        TRY(build_members(L.n, nc, L.agg, L.agg_ptr, L.members, tmp, s));
+        // Galerkin product
+        Level& C = h->lev[l + 1];
+        C.n = nc;
+        int *count = nullptr, *tmp_cols = nullptr;
+        TRY(h->alloc(&count, (size_t)nc + 1));
+        TRY(h->alloc(&tmp_cols, (size_t)nc * kRapCap));
+        TRY(h->alloc(&C.rp, (size_t)nc + 1));
+        TRY(rap_symbolic(nc, L.agg_ptr, L.members, L.rp, L.ci, L.agg, count, tmp_cols, kRapCap, h->d_err, s));
+        TRY(check_dev(h, s));
+        int* scan2 = nullptr;
+        TRY(h->alloc(&scan2, (size_t)scan_tmp_bytes(nc) / sizeof(int) + 16));
+        TRY(exclusive_scan(nc, count, C.rp, scan2, scan_tmp_bytes(nc) + 64, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, C.rp + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        C.nnzb = h->h_pin[0];
+        TRY(h->alloc(&C.ci, (size_t)C.nnzb));
+        TRY(h->alloc(&C.vals64, (size_t)C.nnzb * bb));
+        TRY(rap_fill_cols(nc, C.rp, tmp_cols, kRapCap, C.ci, s));
+        TRY(rap_numeric(b, nc, L.agg_ptr, L.members, L.rp, L.ci, L.vals64, L.agg, C.rp, C.ci, C.vals64, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        h->release(w.flag);
+        h->release(d_count);
+        h->release(scan_tmp);
+        h->release(tmp);
+        h->release(count);
+        h->release(tmp_cols);
+        h->release(scan2);
+        h->nlev++;
+    }
+    // smoother data on every level but the coarsest
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+        Level& L = h->lev[l];
+        TRY(h->alloc(&L.colour, (size_t)L.n));
+        int* cflag = nullptr;
+        TRY(h->alloc(&cflag, 4));
+        int rounds = 0;
+        TRY(colour_nodes(L.n, L.rp, L.ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds));
+        L.colour_rounds = rounds;
+        h->release(cflag);
+        TRY(h->alloc(&L.colour_ptr_d, (size_t)L.n_colours + 1));
+        TRY(h->alloc(&L.colour_nodes, (size_t)L.n));
+        int* tmp = nullptr;
+        TRY(h->alloc(&tmp, (size_t)L.n + 1 + scan_tmp_bytes(L.n) / sizeof(int) + 16));
+        TRY(colour_order(L.n, L.n_colours, L.colour, L.colour_ptr_d, L.colour_nodes, tmp, s));
+        L.colour_ptr.assign(L.n_colours + 1, 0);
+        BAMG_CUDA_TRY(cudaMemcpyAsync(L.colour_ptr.data(), L.colour_ptr_d, sizeof(int) * (L.n_colours + 1),
+                                      cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        h->release(tmp);
+        if (L.colour_ptr[L.n_colours] != L.n) return BAMG_ECUDA;
+        TRY(h->alloc(&L.dinv64, (size_t)L.n * h->F * h->fb * h->fb));
+        TRY(block_inverses(b, h->fb, L.n, L.diag, L.vals64, L.dinv64, h->d_err, s));
+        TRY(check_dev(h, s));
+        if (h->p.cycle_prec == 32) {
+            TRY(h->alloc(&L.vals32, (size_t)L.nnzb * bb));
+            TRY(h->alloc(&L.dinv32, (size_t)L.n * h->F * h->fb * h->fb));
+            TRY(launch_convert_d2f((long)L.nnzb * bb, L.vals64, L.vals32, s));
+            TRY(launch_convert_d2f((long)L.n * h->F * h->fb * h->fb, L.dinv64, L.dinv32, s));
+        }
+    }
+    // coarsest level: dense FP64 LU and inverse
+    {
+        Level& L = h->lev[h->nlev - 1];
+        const long nd = (long)L.n * b;
+        if (nd > kMaxCoarseDense) return BAMG_EUNSUPPORTED;
+        h->nd = (int)nd;
+        TRY(h->alloc(&h->coarse_a, (size_t)(nd * nd)));
+        TRY(h->alloc(&h->coarse_inv, (size_t)(nd * nd)));
+        TRY(h->alloc(&h->coarse_piv, (size_t)nd));
+        TRY(coarse_dense(b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, s));
+        TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, h->d_err, s));
+        TRY(check_dev(h, s));
+    }
+    // work vectors in the cycle precision
+    const size_t es = h->p.cycle_prec == 32 ? sizeof(float) : sizeof(double);
+    for (int l = 0; l < h->nlev; ++l) {
+        Level& L = h->lev[l];
+        const size_t nb = (size_t)L.n * b;
+        char* q = nullptr;
+        if (l + 1 < h->nlev) {
+            TRY(h->alloc(&q, nb * es)); L.xa = q;
+            TRY(h->alloc(&q, nb * es)); L.xb = q;
+            TRY(h->alloc(&q, (size_t)L.n * h->fb * es)); L.xt = q;
+            TRY(h->alloc(&q, nb * es)); L.res = q;
+        }
+        if (l > 0) {
+            TRY(h->alloc(&q, nb * es)); L.rhs = q;
+            TRY(h->alloc(&q, nb * es)); L.uc = q;
+        }
+    }
+    const size_t N = (size_t)n * b;
+    TRY(h->alloc(&h->cyc_in, N));
+    TRY(h->alloc(&h->cyc_out, N));
+    if (h->p.cycle_prec == 32) {
+        TRY(h->alloc(&h->r32, N));
+        TRY(h->alloc(&h->z32, N));
+    }
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return BAMG_OK;
+}
+
+extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
+                         int b, const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out) {
+    if (!out) return BAMG_EINVAL;
+    *out = nullptr;
+    if (!row_ptr || !col_idx || !vals || !field_of_dof || n_nodes < 1 || nnzb < n_nodes || b < 1 || b > kMaxB)
+        return BAMG_EINVAL;
+    amg_params prm;
+    if (p) prm = *p;
+    else amg_default_params(&prm);
+    if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
+        !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64))
+        return BAMG_EINVAL;
+    // fields: non-decreasing 0..F-1 in unit steps, equal sizes
+    if (field_of_dof[0] != 0) return BAMG_EINVAL;
+    int F = 1;
+    for (int d = 1; d < b; ++d) {
+        const int step = field_of_dof[d] - field_of_dof[d - 1];
+        if (step != 0 && step != 1) return BAMG_EINVAL;
+        F = field_of_dof[d] + 1;
+    }
+    if (b % F) return BAMG_EINVAL;
+    const int fb = b / F;
+    for (int d = 0; d < b; ++d)
+        if (field_of_dof[d] != d / fb) return BAMG_EINVAL;
+    if (!supported_block(b, fb)) return BAMG_EUNSUPPORTED;
+    bamg_ctx* h = new (std::nothrow) bamg_ctx();
+    if (!h) return BAMG_ECUDA;
+    h->b = b;
+    h->F = F;
+    h->fb = fb;
+    h->p = prm;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return BAMG_ECUDA;
+    }
+    int st = setup_impl(h, row_ptr, col_idx, vals, n_nodes, nnzb, s);
+    if (st != BAMG_OK) {
+        cudaStreamSynchronize(s);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return BAMG_OK;
+}
+
+extern "C" int amg_destroy(bamg_t h) {
+    if (!h) return BAMG_OK;
+    cudaDeviceSynchronize();
+    delete h;
+    return BAMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle
+// ---------------------------------------------------------------------------
+template <typename T>
+static const T* level_vals(const Level& L);
+template <>
+const double* level_vals<double>(const Level& L) { return L.vals64; }
+template <>
+const float* level_vals<float>(const Level& L) { return L.vals32; }
+template <typename T>
+static const T* level_dinv(const Level& L);
+template <>
+const double* level_dinv<double>(const Level& L) { return L.dinv64; }
+template <>
+const float* level_dinv<float>(const Level& L) { return L.dinv32; }
+
+// one field step of Algorithm 1 on level l: x_out = x_in updated in field f
+template <typename T>
+static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x_out, cudaStream_t s) {
+    const Level& L = h->lev[l];
+    for (int c = 0; c < L.n_colours; ++c) {
+        BgsArgs a;
+        a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
+        a.nodes = L.colour_nodes + L.colour_ptr[c];
+        a.colour = c;
+        a.colours = L.colour;
+        a.rp = L.rp;
+        a.ci = L.ci;
+        a.vals = level_vals<T>(L);
+        a.dinv = level_dinv<T>(L);
+        a.rhs = rhs;
+        a.x_in = x_in;
+        a.x_out = x_out;
+        a.xt = L.xt;
+        a.field = f;
+        a.F = h->F;
+        a.omega = h->p.omega;
+        TRY(launch_bgs_colour<T>(h->b, h->fb, a, s));
+    }
+    return BAMG_OK;
+}
+
+// MGV(0, rhs, l) of Fig. 1 written to out
+template <typename T>
+static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
+    const Level& L = h->lev[l];
+    const int b = h->b;
+    if (l == h->nlev - 1) return launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s);
+    T* xa = static_cast<T*>(L.xa);
+    T* xb = static_cast<T*>(L.xb);
+    T* cur = nullptr;  // nullptr = the zero initial guess
+    const int S_pre = h->p.n_pre * h->F;
+    for (int t = 0; t < S_pre; ++t) {
+        T* dst = (cur == xa) ? xb : xa;
+        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, s));
+        cur = dst;
+    }
+    if (!cur) {
+        BAMG_CUDA_TRY(cudaMemsetAsync(xa, 0, sizeof(T) * (size_t)L.n * b, s));
+        cur = xa;
+    }
+    const Level& C = h->lev[l + 1];
+    T* res = static_cast<T*>(L.res);
+    TRY(launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+    TRY(launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
+    TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
+    TRY(launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
+    const int S_post = h->p.n_post * h->F;
+    if (S_post == 0)
+        BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
+    for (int t = 0; t < S_post; ++t) {
+        T* dst = (t == S_post - 1) ? out : ((cur == xa) ? xb : xa);
+        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, s));
+        cur = dst;
+    }
+    return BAMG_OK;
+}
+
+// z = M r on the finest level (r, z FP64, distinct)
+static int cycle_direct(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
+    const long N = (long)h->lev[0].n * h->b;
+    if (h->p.cycle_prec == 64) return mgv<double>(h, 0, r, z, s);
+    TRY(launch_cast_d2f(N, r, h->r32, s));
+    TRY(mgv<float>(h, 0, h->r32, h->z32, s));
+    return launch_cast_f2d(N, h->z32, z, s);
+}
+
+static int ensure_graph(bamg_ctx* h) {
+    if (h->graph_exec) return BAMG_OK;
+    cudaStream_t cs = h->cap_stream;
+    BAMG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = cycle_direct(h, h->cyc_in, h->cyc_out, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (st != BAMG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return BAMG_ECUDA;
+    h->graph = g;
+    BAMG_CUDA_TRY(cudaGraphInstantiate(&h->graph_exec, g, 0));
+    return BAMG_OK;
+}
+
+static int apply_impl(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
+    if (!h->p.use_graph) return cycle_direct(h, r, z, s);
+    TRY(ensure_graph(h));
+    const size_t nbytes = sizeof(double) * (size_t)h->lev[0].n * h->b;
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->cyc_in, r, nbytes, cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(z, h->cyc_out, nbytes, cudaMemcpyDeviceToDevice, s));
+    return BAMG_OK;
+}
+
+extern "C" int amg_apply(bamg_t h, const double* r, double* z, void* stream) {
+    if (!h || !r || !z || r == z) return BAMG_EINVAL;
+    return apply_impl(h, r, z, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES
+// ---------------------------------------------------------------------------
+static int ensure_krylov(bamg_ctx* h, int m) {
+    if (h->m_alloc >= m) return BAMG_OK;
+    for (void* q : {(void*)h->V, (void*)h->Z, (void*)h->w, (void*)h->partial, (void*)h->h1, (void*)h->h2,
+                    (void*)h->wsq, (void*)h->H, (void*)h->cs, (void*)h->sn, (void*)h->g, (void*)h->y,
+                    (void*)h->scal})
+        if (q) h->release(q);
+    const size_t N = (size_t)h->lev[0].n * h->b;
+    const int nchunk = krylov_chunks((long)N);
+    TRY(h->alloc(&h->V, N * (m + 1)));
+    TRY(h->alloc(&h->Z, N * m));
+    TRY(h->alloc(&h->w, N));
+    TRY(h->alloc(&h->partial, (size_t)(m + 2) * nchunk));
+    TRY(h->alloc(&h->h1, (size_t)m + 2));
+    TRY(h->alloc(&h->h2, (size_t)m + 2));
+    TRY(h->alloc(&h->wsq, 2));
+    TRY(h->alloc(&h->H, (size_t)(m + 1) * m));
+    TRY(h->alloc(&h->cs, (size_t)m));
+    TRY(h->alloc(&h->sn, (size_t)m));
+    TRY(h->alloc(&h->g, (size_t)m + 1));
+    TRY(h->alloc(&h->y, (size_t)m));
+    TRY(h->alloc(&h->scal, 4));
+    h->m_alloc = m;
+    return BAMG_OK;
+}
+
+// ||x||^2 into dst (device), via the deterministic chunked reduction
+static int norm_sq(bamg_ctx* h, long N, const double* x, double* dst, cudaStream_t s) {
+    TRY(launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, s));
+    return launch_finish(1, N, h->partial, dst, s);
+}
+
+extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
+                            int* iters, double* relres, void* stream) {
+    if (!h || !b || !x || restart < 1 || restart > kMaxRestart || max_iter < 0 || !(tol >= 0.0))
+        return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = restart;
+    TRY(ensure_krylov(h, m));
+    const Level& L0 = h->lev[0];
+    const long N = (long)L0.n * h->b;
+    const int bsz = h->b;
+    double* hs = h->h_scal;
+    TRY(norm_sq(h, N, b, h->wsq, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->wsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    const double bnorm = sqrt(hs[0]);
+    if (!isfinite(bnorm)) return BAMG_ENAN;
+    int total = 0, converged = 0;
+    double rel = 0.0;
+    if (bnorm == 0.0) {
+        BAMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        converged = 1;
+    }
+    while (!converged) {
+        TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
+        TRY(norm_sq(h, N, h->w, h->wsq, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->wsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        const double beta = sqrt(hs[0]);
+        rel = beta / bnorm;
+        if (!isfinite(rel)) return BAMG_ENAN;
+        if (rel <= tol) {
+            converged = 1;
+            break;
+        }
+        if (total >= max_iter) break;
+        TRY(launch_init_g(m, h->wsq, h->g, h->scal, s));
+        TRY(launch_scale(N, h->w, h->scal, h->V, 0, s));  // v_0 = r / beta
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            const double* vj = h->V + (size_t)j * N;
+            double* zj = h->Z + (size_t)j * N;
+            TRY(apply_impl(h, vj, zj, s));
+            TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
+            // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
+            TRY(launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, s));
+            TRY(launch_finish(j + 2, N, h->partial, h->h1, s));
+            TRY(launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, s));
+            TRY(launch_finish(j + 1, N, h->partial, h->h2, s));
+            TRY(launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, s));
+            TRY(launch_finish(1, N, h->partial, h->wsq, s));
+            TRY(launch_givens(j, m, h->h1, h->h2, h->wsq, h->H, h->cs, h->sn, h->g, h->scal, s));
+            TRY(launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
+            total++;
+            k = j + 1;
+            BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (!isfinite(hs[1])) return BAMG_ENAN;
+            if (hs[1] / bnorm <= tol || hs[2] != 0.0 || total >= max_iter) break;
+        }
+        TRY(launch_solve_upper(k, m, h->H, h->g, h->y, s));
+        TRY(launch_axpy_dot(N, x, h->Z, N, k, h->y, -1.0, 0, nullptr, s));  // x += Z y
+    }
+    if (iters) *iters = total;
+    if (relres) *relres = rel;
+    return converged ? BAMG_OK : BAMG_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// end-to-end with host buffers
+// ---------------------------------------------------------------------------
+extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes,
+                              int nnzb, int b, const int* field_of_dof, const amg_params* p,
+                              const double* rhs_host, double* x_host, double tol, int restart, int max_iter,
+                              int* iters, double* relres, void* stream) {
+    if (!row_ptr || !col_idx || !vals || !rhs_host || !x_host || n_nodes < 1 || nnzb < 1 || b < 1 || b > kMaxB)
+        return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t N = (size_t)n_nodes * b;
+    int *d_rp = nullptr, *d_ci = nullptr;
+    double *d_v = nullptr, *d_b = nullptr, *d_x = nullptr;
+    int st = BAMG_OK;
+    bamg_t h = nullptr;
+    if (cudaMalloc(&d_rp, sizeof(int) * (n_nodes + 1)) != cudaSuccess ||
+        cudaMalloc(&d_ci, sizeof(int) * (size_t)nnzb) != cudaSuccess ||
+        cudaMalloc(&d_v, sizeof(double) * (size_t)nnzb * b * b) != cudaSuccess ||
+        cudaMalloc(&d_b, sizeof(double) * N) != cudaSuccess || cudaMalloc(&d_x, sizeof(double) * N) != cudaSuccess)
+        st = BAMG_ECUDA;
+    if (st == BAMG_OK &&
+        (cudaMemcpyAsync(d_rp, row_ptr, sizeof(int) * (n_nodes + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(d_ci, col_idx, sizeof(int) * (size_t)nnzb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(d_v, vals, sizeof(double) * (size_t)nnzb * b * b, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(d_b, rhs_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(d_x, x_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess))
+        st = BAMG_ECUDA;
+    if (st == BAMG_OK) st = amg_setup(d_rp, d_ci, d_v, n_nodes, nnzb, b, field_of_dof, p, stream, &h);
+    int solve_st = BAMG_OK;
+    if (st == BAMG_OK) {
+        solve_st = fgmres_solve(h, d_b, d_x, tol, restart, max_iter, iters, relres, stream);
+        if (solve_st >= 0 &&
+            (cudaMemcpyAsync(x_host, d_x, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+             cudaStreamSynchronize(s) != cudaSuccess))
+            solve_st = BAMG_ECUDA;
+    }
+    cudaStreamSynchronize(s);
+    amg_destroy(h);
+    cudaFree(d_rp);
+    cudaFree(d_ci);
+    cudaFree(d_v);
+    cudaFree(d_b);
+    cudaFree(d_x);
+    return st != BAMG_OK ? st : solve_st;
+}
+
+// ---------------------------------------------------------------------------
+// plain SpMV entry point
+// ---------------------------------------------------------------------------
+extern "C" int bsr_spmv(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int b,
+                        const double* x, double* y, void* stream) {
+    if (!row_ptr || !col_idx || !vals || !x || !y || n_nodes < 0 || b < 1 || b > kMaxB || x == y)
+        return BAMG_EINVAL;
+    return launch_spmv<double>(b, n_nodes, row_ptr, col_idx, vals, x, nullptr, y,
+                               static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// introspection
+// ---------------------------------------------------------------------------
+extern "C" int amg_num_levels(bamg_t h) { return h ? h->nlev : BAMG_EINVAL; }
+
+extern "C" int amg_level_info(bamg_t h, int level, int* n_nodes, int* nnzb, int* n_colours, int* n_agg) {
+    if (!h || level < 0 || level >= h->nlev) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    const bool coarsest = level == h->nlev - 1;
+    if (n_nodes) *n_nodes = L.n;
+    if (nnzb) *nnzb = L.nnzb;
+    if (n_colours) *n_colours = coarsest ? 0 : L.n_colours;
+    if (n_agg) *n_agg = coarsest ? 0 : L.n_agg;
+    return BAMG_OK;
+}
+
+extern "C" int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, double* vals, int* agg,
+                              int* colour, double* dinv) {
+    if (!h || level < 0 || level >= h->nlev) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    const bool coarsest = level == h->nlev - 1;
+    const size_t bb = (size_t)h->b * h->b;
+    if (row_ptr) BAMG_CUDA_TRY(cudaMemcpy(row_ptr, L.rp, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
+    if (col_idx) BAMG_CUDA_TRY(cudaMemcpy(col_idx, L.ci, sizeof(int) * (size_t)L.nnzb, cudaMemcpyDeviceToHost));
+    if (vals) BAMG_CUDA_TRY(cudaMemcpy(vals, L.vals64, sizeof(double) * bb * L.nnzb, cudaMemcpyDeviceToHost));
+    if (!coarsest) {
+        if (agg) BAMG_CUDA_TRY(cudaMemcpy(agg, L.agg, sizeof(int) * (size_t)L.n, cudaMemcpyDeviceToHost));
+        if (colour) BAMG_CUDA_TRY(cudaMemcpy(colour, L.colour, sizeof(int) * (size_t)L.n, cudaMemcpyDeviceToHost));
+        if (dinv)
+            BAMG_CUDA_TRY(cudaMemcpy(dinv, L.dinv64, sizeof(double) * (size_t)L.n * h->F * h->fb * h->fb,
+                                     cudaMemcpyDeviceToHost));
+    }
+    return BAMG_OK;
+}
+
+extern "C" int amg_stats(bamg_t h, char* json, int cap) {
+    if (!h || !json || cap < 1) return BAMG_EINVAL;
+    std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
+                    ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) + ",\"coarse_unknowns\":" +
+                    std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"levels\":[";
+    for (int l = 0; l < h->nlev; ++l) {
+        const Level& L = h->lev[l];
+        if (l) o += ",";
+        o += "{\"n\":" + std::to_string(L.n) + ",\"nnzb\":" + std::to_string(L.nnzb) +
+             ",\"colours\":" + std::to_string(L.n_colours) + ",\"aggregates\":" + std::to_string(L.n_agg) +
+             ",\"aggregation_rounds\":" + std::to_string(L.agg_rounds) +
+             ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) + "}";
+    }
+    o += "]}";
+    const int len = (int)o.size();
+    const int w = len < cap - 1 ? len : cap - 1;
+    memcpy(json, o.data(), (size_t)w);
+    json[w] = 0;
+    return len;
+}

@@ -1,0 +1,188 @@
+// Shared device helpers and internal declarations of the bamg CUDA library.
+// Target: sm_103a (GB300).  No code here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bamg.h"
+
+namespace bamg {
+
+constexpr int kWarp = 32;
+constexpr int kMaxLevels = 16;
+constexpr int kMaxRestart = 64;
+constexpr int kMaxB = 8;
+
+// device error flag values (first error wins, atomicCAS from 0)
+enum DevErr : int {
+    kDevOk = 0,
+    kDevSingularBlock = 1,
+    kDevSingularCoarse = 2,
+    kDevBadPattern = 3,   // unsorted columns / missing diagonal / out-of-range index
+    kDevRowTooLong = 4,   // a coarse row exceeded the RAP row capacity
+    kDevNonFinite = 5,
+};
+
+__device__ __forceinline__ void set_error(int* flag, int code) { atomicCAS(flag, 0, code); }
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<double> {
+    using v2 = double2;
+};
+template <>
+struct VecOf<float> {
+    using v2 = float2;
+};
+
+// Load the B contiguous values starting at p (p aligned to the block-row
+// start; rows of B values start at multiples of B elements inside blocks of
+// B*B elements, blocks start at multiples of B*B elements, base 256-aligned).
+// Uses the widest vector load that keeps every row start aligned.
+template <typename T, int B>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&out)[B]) {
+    constexpr int bytes_row = B * (int)sizeof(T);
+    if constexpr (sizeof(T) == 4 && bytes_row % 16 == 0) {
+#pragma unroll
+        for (int c = 0; c < B; c += 4) {
+            float4 v = *reinterpret_cast<const float4*>(p + c);
+            out[c] = v.x;
+            out[c + 1] = v.y;
+            out[c + 2] = v.z;
+            out[c + 3] = v.w;
+        }
+    } else if constexpr (bytes_row % 16 == 0 || (sizeof(T) == 4 && bytes_row % 8 == 0)) {
+        using V2 = typename VecOf<T>::v2;
+#pragma unroll
+        for (int c = 0; c < B; c += 2) {
+            V2 v = *reinterpret_cast<const V2*>(p + c);
+            out[c] = v.x;
+            out[c + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < B; ++c) out[c] = p[c];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace bamg
+
+// ---------------------------------------------------------------------------
+// internal launchers (host functions, defined in the k_*.cu files)
+// ---------------------------------------------------------------------------
+namespace bamg {
+
+// ---- solve-phase kernels (k_solve.cu) ----
+// y = A x (+ optional: y = rhs - A x when rhs != nullptr).  T = matrix/vector type.
+template <typename T>
+int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs,
+                T* y, cudaStream_t s);
+// rc[I*b+d] = sum over members m of aggregate I (ascending) of res[m*b+d]
+template <typename T>
+int launch_restrict(int b, int nc, const int* agg_ptr, const int* members, const T* res, T* rc,
+                    cudaStream_t s);
+// u[i*b+d] += uc[agg[i]*b+d]
+template <typename T>
+int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s);
+// One colour of one field step of the block Gauss-Seidel smoother.
+struct BgsArgs {
+    int n_in_colour;
+    const int* nodes;    // node ids of this colour
+    int colour;          // colour index (neighbours of lower colour carry x~)
+    const int* colours;  // colour of every node
+    const int* rp;
+    const int* ci;
+    const void* vals;
+    const void* dinv;    // [n][F][fb*fb]
+    const void* rhs;
+    const void* x_in;    // nullptr = zero vector
+    void* x_out;
+    void* xt;            // [n][fb]
+    int field;
+    int F;
+    double omega;
+};
+template <typename T>
+int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// y = Ainv x for the dense FP64 nd x nd inverse (x, y of type T)
+template <typename T>
+int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s);
+int launch_cast_d2f(long m, const double* x, float* y, cudaStream_t s);
+int launch_cast_f2d(long m, const float* x, double* y, cudaStream_t s);
+
+// ---- setup kernels (k_setup.cu) ----
+// diag[i] = position of the diagonal block; flag kDevBadPattern on unsorted /
+// missing diagonal / out-of-range columns
+int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* err, cudaStream_t s);
+// aggregation; returns number of aggregates (>= 0) or a negative status.
+// agg[n] out; agg_ptr[nc+1] and members[n] allocated by the caller after the
+// count is known (second call).
+struct AggWork {
+    int* state;   // [n]
+    int* rootid;  // [n + 1]
+    int* agg1;    // [n]
+    int* flag;    // [1] device
+    int* host_flag;  // pinned host [1]
+};
+// d_count: 2 device ints (aggregate count, error flag); w.host_flag: 2 pinned ints
+int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, int* d_count,
+                    int* d_scan_tmp, long scan_tmp_bytes, cudaStream_t s, int* rounds_out);
+int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int* d_tmp,
+                  cudaStream_t s);
+int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
+                 cudaStream_t s, int* n_colours, int* rounds_out);
+// colour_ptr[C+1] and nodes sorted by (colour, index)
+int colour_order(int n, int C, const int* colour, int* colour_ptr, int* nodes, int* d_tmp,
+                 cudaStream_t s);
+// RAP with the tentative prolongator: symbolic (row sizes), then numeric
+int rap_symbolic(int nc, const int* agg_ptr, const int* members, const int* rp, const int* ci,
+                 const int* agg, int* count, int* tmp_cols, int cap, int* err, cudaStream_t s);
+int rap_fill_cols(int nc, const int* rp_c, const int* tmp_cols, int cap, int* ci_c, cudaStream_t s);
+int rap_numeric(int b, int nc, const int* agg_ptr, const int* members, const int* rp, const int* ci,
+                const double* vals, const int* agg, const int* rp_c, const int* ci_c, double* vals_c,
+                cudaStream_t s);
+// per-node, per-field inverses of the diagonal blocks (FP64 in, T out)
+int block_inverses(int b, int fb, int n, const int* diag, const double* vals, double* dinv64, int* err,
+                   cudaStream_t s);
+// dense FP64 coarsest matrix, LU with partial pivoting, inverse
+int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals, double* dense,
+                 cudaStream_t s);
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, int* err, cudaStream_t s);
+int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s);
+long scan_tmp_bytes(int n);
+int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);
+
+// ---- Krylov kernels (k_krylov.cu) ----
+int krylov_chunks(long N);
+// partial[v*nchunk + c] = chunk c of x . Y_v (v < nv); if want_xx also x . x at v = nv
+int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx,
+                     double* partial, cudaStream_t s);
+// x -= sign * sum_v h[v] Y_v; then mode 1: dots with Y_v, mode 2: x . x, mode 0: none
+int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign,
+                    int mode, double* partial, cudaStream_t s);
+// out[v] = sum of the chunk partials of v (v < nv)
+int launch_finish(int nv, long N, const double* partial, double* out, cudaStream_t s);
+int launch_givens(int j, int m, const double* h1, const double* h2, const double* wsq, double* H, double* cs,
+                  double* sn, double* g, double* scal, cudaStream_t s);
+int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s);
+int launch_scale(long N, const double* x, const double* scal, double* y, int check_breakdown, cudaStream_t s);
+int launch_init_g(int m, const double* bsq, double* g, double* scal, cudaStream_t s);
+
+}  // namespace bamg
+
+#define BAMG_CUDA_TRY(expr)                      \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return BAMG_ECUDA; \
+    } while (0)

@@ -1,0 +1,224 @@
+// FP64 kernels of the outer flexible GMRES: Arnoldi orthogonalisation by
+// classical Gram-Schmidt applied twice (CGS2), Givens rotations of the
+// Hessenberg column, the triangular solve for y and the update x += Z y.
+// (The paper applies its V-cycle inside GMRES: Sec. 3 and Sec. 5.1.)
+//
+// Reductions are deterministic: every vector is cut into the same fixed
+// chunks (one CTA each), every chunk reduces in a fixed tree, and a single
+// CTA adds the chunk partials in chunk order.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace bamg {
+
+constexpr int kKThreads = 256;
+constexpr int kDotGroup = 8;  // dot products accumulated together per pass
+
+int krylov_chunks(long N) {
+    long c = (N + 4095) / 4096;
+    if (c > 2 * 152) c = 2 * 152;
+    return (int)(c < 1 ? 1 : c);
+}
+
+__device__ __forceinline__ void chunk_range(long N, long* e0, long* e1) {
+    const long per = (N + gridDim.x - 1) / gridDim.x;
+    *e0 = (long)blockIdx.x * per;
+    *e1 = min(N, *e0 + per);
+}
+
+// block-wide sum of G values per thread; result valid in thread 0
+template <int G>
+__device__ __forceinline__ void block_sum(double (&v)[G], double (*sh)[kKThreads / 32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
+        if (lane == 0) sh[g][wid] = v[g];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            double s = 0.0;
+            for (int w = 0; w < kKThreads / 32; ++w) s += sh[g][w];
+            v[g] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// partial[v * nchunk + chunk] = sum_{e in chunk} x[e] * Y_v[e], v < nv, and
+// if want_xx, partial[nv * nchunk + chunk] = sum x[e]^2
+__device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const double* __restrict__ Y,
+                           long ld, int nv, int want_xx, double* __restrict__ partial) {
+    __shared__ double sh[kDotGroup][kKThreads / 32];
+    const int nchunk = gridDim.x;
+    for (int v0 = 0; v0 < nv + want_xx; v0 += kDotGroup) {
+        double acc[kDotGroup];
+#pragma unroll
+        for (int g = 0; g < kDotGroup; ++g) acc[g] = 0.0;
+        for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const double xe = x[e];
+#pragma unroll
+            for (int g = 0; g < kDotGroup; ++g) {
+                const int v = v0 + g;
+                if (v < nv) acc[g] = fma(xe, Y[(size_t)v * ld + e], acc[g]);
+                else if (v == nv && want_xx) acc[g] = fma(xe, xe, acc[g]);
+            }
+        }
+        block_sum<kDotGroup>(acc, sh);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int g = 0; g < kDotGroup; ++g)
+                if (v0 + g < nv + want_xx) partial[(size_t)(v0 + g) * nchunk + blockIdx.x] = acc[g];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kKThreads) multi_dot_kernel(long N, const double* __restrict__ x,
+                                                              const double* __restrict__ Y, long ld, int nv,
+                                                              int want_xx, double* __restrict__ partial) {
+    long e0, e1;
+    chunk_range(N, &e0, &e1);
+    chunk_dots(e0, e1, x, Y, ld, nv, want_xx, partial);
+}
+
+// x -= sign * sum_v h[v] Y_v over the chunk, then (mode 1) the dots of the new
+// x with Y_0..Y_{nv-1}, (mode 2) its squared norm, (mode 0) nothing
+__global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __restrict__ x,
+                                                             const double* __restrict__ Y, long ld, int nv,
+                                                             const double* __restrict__ h, double sign,
+                                                             int mode, double* __restrict__ partial) {
+    __shared__ double sh_h[kMaxRestart + 1];
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) sh_h[v] = sign * h[v];
+    __syncthreads();
+    long e0, e1;
+    chunk_range(N, &e0, &e1);
+    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double t = x[e];
+        for (int v = 0; v < nv; ++v) t = fma(-sh_h[v], Y[(size_t)v * ld + e], t);
+        x[e] = t;
+    }
+    if (mode == 0) return;
+    __syncthreads();
+    if (mode == 1) chunk_dots(e0, e1, x, Y, ld, nv, 0, partial);
+    else chunk_dots(e0, e1, x, Y, ld, 0, 1, partial);
+}
+
+// out[v] = sum over chunks of partial[v * nchunk + c], one warp per v
+__global__ void finish_kernel(int nv, int nchunk, const double* __restrict__ partial, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int v = threadIdx.x >> 5; v < nv; v += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int c = lane; c < nchunk; c += 32) s += partial[(size_t)v * nchunk + c];
+        s = warp_sum(s);
+        if (lane == 0) out[v] = s;
+    }
+}
+
+int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx,
+                     double* partial, cudaStream_t s) {
+    multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign,
+                    int mode, double* partial, cudaStream_t s) {
+    axpy_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, h, sign, mode, partial);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+int launch_finish(int nv, long N, const double* partial, double* out, cudaStream_t s) {
+    finish_kernel<<<1, 512, 0, s>>>(nv, krylov_chunks(N), partial, out);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi bookkeeping on the device (one thread): column j of the Hessenberg
+// matrix from h1 + h2 and ||w||, breakdown test, previous rotations, the new
+// rotation, and the residual estimate |g_{j+1}|.
+// st layout: see GmresDev in capi.cu (passed as raw pointers here).
+// ---------------------------------------------------------------------------
+__global__ void givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
+                              const double* __restrict__ wsq, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // scal[0] = h_{j+1,j}, scal[1] = |g_{j+1}|, scal[2] = breakdown, scal[3] = ||w|| before
+    const double wn0 = sqrt(h1[j + 1]);  // h1[j+1] holds ||w||^2 before orthogonalising
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+    const double hn = sqrt(wsq[0]);
+    H[(size_t)(j + 1) * m + j] = hn;
+    const int breakdown = !(hn > 1e-14 * wn0);
+    for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+    }
+    const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+    const double d = sqrt(a * a + bb * bb);
+    if (d == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+    } else {
+        cs[j] = a / d;
+        sn[j] = bb / d;
+    }
+    H[(size_t)j * m + j] = d;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    scal[0] = hn;
+    scal[1] = fabs(g[j + 1]);
+    scal[2] = breakdown ? 1.0 : 0.0;
+    scal[3] = wn0;
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k), upper triangular
+__global__ void solve_upper_kernel(int k, int m, const double* __restrict__ H, const double* __restrict__ g,
+                                   double* __restrict__ y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[(size_t)i * m + c] * y[c];
+        y[i] = s / H[(size_t)i * m + i];
+    }
+}
+
+// y = x / scal[0] unless the breakdown flag scal[2] is set
+__global__ void scale_kernel(long N, const double* __restrict__ x, const double* __restrict__ scal,
+                             double* __restrict__ y, int check_breakdown) {
+    if (check_breakdown && scal[2] != 0.0) return;
+    const double inv_den = scal[0];
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long)gridDim.x * blockDim.x)
+        y[e] = x[e] / inv_den;
+}
+
+// g = (beta, 0, ..., 0) with beta = sqrt(*bsq); scal[0] = beta
+__global__ void init_g_kernel(int m, const double* __restrict__ bsq, double* __restrict__ g,
+                              double* __restrict__ scal) {
+    const int t = threadIdx.x;
+    const double beta = sqrt(bsq[0]);
+    for (int i = t; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta : 0.0;
+    if (t == 0) scal[0] = beta;
+}
+
+int launch_givens(int j, int m, const double* h1, const double* h2, const double* wsq, double* H, double* cs,
+                  double* sn, double* g, double* scal, cudaStream_t s) {
+    givens_kernel<<<1, 32, 0, s>>>(j, m, h1, h2, wsq, H, cs, sn, g, scal);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s) {
+    solve_upper_kernel<<<1, 32, 0, s>>>(k, m, H, g, y);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+int launch_scale(long N, const double* x, const double* scal, double* y, int check_breakdown, cudaStream_t s) {
+    long g = (N + 255) / 256;
+    scale_kernel<<<(int)(g < 1216 ? (g > 0 ? g : 1) : 1216), 256, 0, s>>>(N, x, scal, y, check_breakdown);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+int launch_init_g(int m, const double* bsq, double* g, double* scal, cudaStream_t s) {
+    init_g_kernel<<<1, 64, 0, s>>>(m, bsq, g, scal);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+}  // namespace bamg

@@ -1,0 +1,811 @@
+// Setup-phase kernels of the monolithic block AMG (Sec. 4.4 setup layouts):
+// node graph checks, aggregation (Sec. 4.3.1), colouring for the multicolour
+// node-block Gauss-Seidel sub-solve, the Galerkin product with the
+// piecewise-constant prolongator (Sec. 3 and 4.3.1), per-field inverses of
+// the node diagonal blocks, and the FP64 LU / inverse of the coarsest level.
+//
+// Order independence.  The aggregation and the colouring are defined by
+// sequential greedy rules in ascending node order; the kernels reach the
+// same result with priority rounds (a node decides once every lower-index
+// node that could influence it has decided), so the result does not depend
+// on thread scheduling.  A state only ever moves from "undecided" to a final
+// value, so a stale read inside a round can only delay a decision.
+#include "common.cuh"
+
+namespace bamg {
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (3 passes: tiles, tile sums, add)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_tot[kScanThreads / kWarp];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < kScanThreads / kWarp ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / kWarp) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int base = wid > 0 ? warp_tot[wid - 1] : 0;
+    *total = warp_tot[kScanThreads / kWarp - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void scan_tiles_kernel(int n, const int* __restrict__ in, int* __restrict__ out,
+                                  int* __restrict__ tile_sums) {
+    const long base = (long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        v[t] = (base + t < n) ? in[base + t] : 0;
+        s += v[t];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        if (base + t < n) out[base + t] = ex;
+        ex += v[t];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// one CTA scans the tile sums in chunks; tile_sums[ntiles] receives the total
+__global__ void scan_sums_kernel(int ntiles, int* __restrict__ tile_sums) {
+    int carry = 0;
+    for (int c0 = 0; c0 < ntiles; c0 += kScanThreads) {
+        int idx = c0 + threadIdx.x;
+        int v = idx < ntiles ? tile_sums[idx] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, &tot);
+        if (idx < ntiles) tile_sums[idx] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) tile_sums[ntiles] = carry;
+}
+
+__global__ void scan_add_kernel(int n, int* __restrict__ out, const int* __restrict__ tile_sums) {
+    const long base = (long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const int add = tile_sums[blockIdx.x];
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t)
+        if (base + t < n) out[base + t] += add;
+}
+
+long scan_tmp_bytes(int n) { return (long)sizeof(int) * (ceil_div(n, kScanTile) + 1); }
+
+// out[0..n-1] = exclusive scan of in; out[n] = total (out must hold n+1 ints).
+// in and out may alias.
+int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s) {
+    const int ntiles = ceil_div(n, kScanTile);
+    if (tmp_bytes < (long)sizeof(int) * (ntiles + 1)) return BAMG_EINVAL;
+    if (n > 0) scan_tiles_kernel<<<ntiles, kScanThreads, 0, s>>>(n, in, out, d_tmp);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(ntiles, d_tmp);
+    if (n > 0) scan_add_kernel<<<ntiles, kScanThreads, 0, s>>>(n, out, d_tmp);
+    BAMG_CUDA_TRY(cudaMemcpyAsync(out + n, d_tmp + ntiles, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// pattern checks: ascending in-range columns, diagonal present, structural
+// symmetry; diag[i] = position of block (i, i)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_col(const int* __restrict__ ci, int k0, int k1, int col) {
+    while (k0 < k1) {
+        int m = (k0 + k1) >> 1;
+        int v = ci[m];
+        if (v == col) return m;
+        if (v < col) k0 = m + 1;
+        else k1 = m;
+    }
+    return -1;
+}
+
+__global__ void check_pattern_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                     int* __restrict__ diag, int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k0 = rp[i], k1 = rp[i + 1];
+    int d = -1;
+    if (k1 < k0) {
+        set_error(err, kDevBadPattern);
+        return;
+    }
+    for (int k = k0; k < k1; ++k) {
+        int j = ci[k];
+        if (j < 0 || j >= n || (k > k0 && ci[k - 1] >= j)) {
+            set_error(err, kDevBadPattern);
+            return;
+        }
+        if (j == i) d = k;
+        else if (find_col(ci, rp[j], rp[j + 1], i) < 0) {
+            set_error(err, kDevBadPattern);
+            return;
+        }
+    }
+    if (d < 0) set_error(err, kDevBadPattern);
+    diag[i] = d;
+}
+
+int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* err, cudaStream_t s) {
+    if (n <= 0) return BAMG_OK;
+    check_pattern_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, ci, diag, err);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Aggregation.  Sequential rule (ascending node order): a node whose
+// neighbours and itself are all free becomes a root; it and its neighbours
+// form an aggregate.  Equivalently, the roots are the lexicographically-first
+// maximal set of nodes with pairwise hop distance >= 3.  Priority rounds:
+// an undecided node with a root within distance 2 is out; an undecided node
+// with no undecided lower-index node and no root within distance 2 is a root.
+// ---------------------------------------------------------------------------
+enum : int { kUndecided = 0, kRoot = 1, kOut = 2 };
+
+__global__ void mis2_round_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  int* state, int* any_undecided) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    volatile int* st = state;
+    if (st[i] != kUndecided) return;
+    bool blocked = false;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j == i) continue;
+        const int sj = st[j];
+        if (sj == kRoot) {
+            st[i] = kOut;
+            return;
+        }
+        if (sj == kUndecided && j < i) blocked = true;
+        for (int k2 = rp[j]; k2 < rp[j + 1]; ++k2) {
+            const int m = ci[k2];
+            if (m == i || m == j) continue;
+            const int sm = st[m];
+            if (sm == kRoot) {
+                st[i] = kOut;
+                return;
+            }
+            if (sm == kUndecided && m < i) blocked = true;
+        }
+    }
+    if (!blocked) st[i] = kRoot;
+    else *any_undecided = 1;
+}
+
+__global__ void is_root_kernel(int n, const int* __restrict__ state, int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = state[i] == kRoot ? 1 : 0;
+}
+
+// phase-1 membership: a root's id, or the id of the (unique) adjacent root
+__global__ void assign_phase1_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                     const int* __restrict__ state, const int* __restrict__ rootid,
+                                     int* __restrict__ agg1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = -1;
+    if (state[i] == kRoot) a = rootid[i];
+    else
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (state[j] == kRoot) a = rootid[j];
+        }
+    agg1[i] = a;
+}
+
+// every node left joins the phase-1 aggregate holding most of its neighbours
+// (ties: smallest aggregate id)
+__global__ void attach_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const int* __restrict__ agg1, int* __restrict__ agg, int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (agg1[i] >= 0) {
+        agg[i] = agg1[i];
+        return;
+    }
+    int best = -1, best_count = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j == i) continue;
+        const int a = agg1[j];
+        if (a < 0) continue;
+        int count = 0;
+        for (int k2 = rp[i]; k2 < rp[i + 1]; ++k2) {
+            const int j2 = ci[k2];
+            if (j2 != i && agg1[j2] == a) count++;
+        }
+        if (count > best_count || (count == best_count && a < best)) {
+            best = a;
+            best_count = count;
+        }
+    }
+    if (best < 0) set_error(err, kDevBadPattern);
+    agg[i] = best;
+}
+
+int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, int* d_count,
+                    int* d_scan_tmp, long scan_tmp_b, cudaStream_t s, int* rounds_out) {
+    const int threads = 256, blocks = ceil_div(n, threads);
+    BAMG_CUDA_TRY(cudaMemsetAsync(w.state, 0, sizeof(int) * (size_t)n, s));
+    const int batch = 8;
+    const long max_rounds = 4L * n + 64;
+    long rounds = 0;
+    for (;;) {
+        for (int r = 0; r < batch; ++r) {
+            if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
+            mis2_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.flag);
+        }
+        rounds += batch;
+        BAMG_CUDA_TRY(cudaMemcpyAsync(w.host_flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (*w.host_flag == 0) break;
+        if (rounds > max_rounds) return BAMG_ETIMEOUT;
+    }
+    if (rounds_out) *rounds_out = (int)rounds;
+    // ids = ranks of the roots in ascending index
+    is_root_kernel<<<blocks, threads, 0, s>>>(n, w.state, w.rootid);
+    int st = exclusive_scan(n, w.rootid, w.rootid, d_scan_tmp, scan_tmp_b, s);
+    if (st) return st;
+    assign_phase1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.rootid, w.agg1);
+    attach_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.agg1, agg, d_count + 1);
+    BAMG_CUDA_TRY(cudaMemcpyAsync(d_count, w.rootid + n, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(w.host_flag, d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (w.host_flag[1] != 0) return BAMG_EINVAL;
+    return w.host_flag[0];
+}
+
+// ---------------------------------------------------------------------------
+// members of every aggregate, ascending: count, scan, scatter, sort segments
+// ---------------------------------------------------------------------------
+__global__ void histogram_kernel(int n, const int* __restrict__ key, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(count + key[i], 1);
+}
+
+__global__ void scatter_by_key_kernel(int n, const int* __restrict__ key, const int* __restrict__ ptr,
+                                      int* __restrict__ fill, int* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = key[i];
+    out[ptr[a] + atomicAdd(fill + a, 1)] = i;
+}
+
+__global__ void sort_segments_kernel(int nseg, const int* __restrict__ ptr, int* __restrict__ v) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nseg) return;
+    const int a = ptr[I], b = ptr[I + 1];
+    for (int p = a + 1; p < b; ++p) {
+        int x = v[p], q = p - 1;
+        while (q >= a && v[q] > x) {
+            v[q + 1] = v[q];
+            --q;
+        }
+        v[q + 1] = x;
+    }
+}
+
+// d_tmp: >= nc + 1 + scan tmp ints
+int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int* d_tmp,
+                  cudaStream_t s) {
+    int* count = d_tmp;                 // nc + 1
+    int* scan_tmp = d_tmp + nc + 1;     // scan tmp
+    BAMG_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(nc + 1), s));
+    histogram_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, agg, count);
+    int st = exclusive_scan(nc, count, agg_ptr, scan_tmp, scan_tmp_bytes(nc), s);
+    if (st) return st;
+    BAMG_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(nc + 1), s));
+    scatter_by_key_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, agg, agg_ptr, count, members);
+    sort_segments_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(nc, agg_ptr, members);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Colouring: sequential first fit in ascending order = Jones-Plassmann with
+// index priority: a node takes the smallest colour unused by its lower-index
+// neighbours once all of them are coloured.
+// ---------------------------------------------------------------------------
+constexpr int kMaxColours = 128;
+
+__global__ void colour_round_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    int* colour, int* flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    volatile int* col = colour;
+    if (col[i] >= 0) return;
+    unsigned long long used[kMaxColours / 64] = {0ull, 0ull};
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j >= i) break;  // columns ascending
+        const int cj = col[j];
+        if (cj < 0) {
+            *flag = 1;
+            return;
+        }
+        if (cj < kMaxColours) used[cj >> 6] |= 1ull << (cj & 63);
+    }
+    int c = 0;
+    while (c < kMaxColours && (used[c >> 6] >> (c & 63) & 1ull)) ++c;
+    if (c >= kMaxColours) {
+        flag[1] = 1;  // too many colours
+        c = kMaxColours - 1;
+    }
+    col[i] = c;
+}
+
+__global__ void max_kernel(int n, const int* __restrict__ v, int* out) {
+    int m = -1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, v[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// d_flag: 3 device ints, h_flag: 3 pinned host ints
+int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
+                 cudaStream_t s, int* n_colours, int* rounds_out) {
+    const int threads = 256, blocks = ceil_div(n, threads);
+    BAMG_CUDA_TRY(cudaMemsetAsync(colour, 0xff, sizeof(int) * (size_t)n, s));
+    BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, 3 * sizeof(int), s));
+    const int batch = 16;
+    const long max_rounds = 2L * n + 64;
+    long rounds = 0;
+    for (;;) {
+        for (int r = 0; r < batch; ++r) {
+            if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+            colour_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, colour, d_flag);
+        }
+        rounds += batch;
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_flag[1]) return BAMG_EUNSUPPORTED;
+        if (h_flag[0] == 0) break;
+        if (rounds > max_rounds) return BAMG_ETIMEOUT;
+    }
+    if (rounds_out) *rounds_out = (int)rounds;
+    BAMG_CUDA_TRY(cudaMemsetAsync(d_flag + 2, 0xff, sizeof(int), s));
+    max_kernel<<<min(ceil_div(n, 256), 1024), 256, 0, s>>>(n, colour, d_flag + 2);
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag + 2, d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_colours = h_flag[2] + 1;
+    return BAMG_OK;
+}
+
+// nodes ordered by (colour, index): one stable compaction per colour
+__global__ void eq_flag_kernel(int n, const int* __restrict__ v, int c, int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = v[i] == c ? 1 : 0;
+}
+__global__ void compact_kernel(int n, const int* __restrict__ v, int c, const int* __restrict__ pos,
+                               const int* __restrict__ base, int* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && v[i] == c) out[*base + pos[i]] = i;
+}
+__global__ void advance_kernel(int* __restrict__ colour_ptr, int c, const int* __restrict__ pos, int n) {
+    colour_ptr[c + 1] = colour_ptr[c] + pos[n];
+}
+
+// d_tmp: n + 1 + scan tmp ints
+int colour_order(int n, int C, const int* colour, int* colour_ptr, int* nodes, int* d_tmp,
+                 cudaStream_t s) {
+    int* pos = d_tmp;
+    int* scan_tmp = d_tmp + n + 1;
+    BAMG_CUDA_TRY(cudaMemsetAsync(colour_ptr, 0, sizeof(int), s));
+    for (int c = 0; c < C; ++c) {
+        eq_flag_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, colour, c, pos);
+        int st = exclusive_scan(n, pos, pos, scan_tmp, scan_tmp_bytes(n), s);
+        if (st) return st;
+        compact_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, colour, c, pos, colour_ptr + c, nodes);
+        advance_kernel<<<1, 1, 0, s>>>(colour_ptr, c, pos, n);
+    }
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product with the tentative prolongator, one warp per coarse row I:
+//   pattern: the distinct agg(j) over all stored (i, j) with agg(i) = I,
+//   values:  A_c[I, J] = sum over members i of I (ascending), then over the
+//            stored blocks of row i (stored order), of A[i, j] with agg(j)=J.
+// The numeric pass adds the blocks one at a time in exactly that order, so
+// each coarse entry is the same sequence of FP64 additions as its definition.
+// ---------------------------------------------------------------------------
+constexpr int kRapWarps = 4;
+
+__global__ void __launch_bounds__(kRapWarps * 32)
+    rap_symbolic_kernel(int nc, const int* __restrict__ agg_ptr, const int* __restrict__ members,
+                        const int* __restrict__ rp, const int* __restrict__ ci,
+                        const int* __restrict__ agg, int* __restrict__ count,
+                        int* __restrict__ tmp_cols, int cap, int* err) {
+    extern __shared__ int sh[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * kRapWarps + wid;
+    if (I >= nc) return;
+    int* set = sh + wid * cap;
+    int size = 0;  // identical in every lane of the warp
+    bool overflow = false;
+    for (int q = agg_ptr[I]; q < agg_ptr[I + 1] && !overflow; ++q) {
+        const int i = members[q];
+        const int k0 = rp[i], k1 = rp[i + 1];
+        for (int kb = k0; kb < k1 && !overflow; kb += 32) {
+            const int k = kb + lane;
+            const bool valid = k < k1;
+            const int J = valid ? agg[ci[k]] : -1;
+            bool present = !valid;
+            for (int p = 0; p < size && !present; ++p) present = set[p] == J;
+            const unsigned same = __match_any_sync(0xffffffffu, J);
+            const bool leader = (__ffs(same) - 1) == lane;
+            const unsigned fresh = __ballot_sync(0xffffffffu, leader && !present);
+            const int rank = __popc(fresh & ((1u << lane) - 1u));
+            const int grown = size + __popc(fresh);
+            if (grown > cap) {
+                overflow = true;  // uniform: every lane sees the same ballot
+            } else {
+                if (leader && !present) set[size + rank] = J;
+                size = grown;
+            }
+            __syncwarp();
+        }
+    }
+    if (overflow) {
+        if (lane == 0) set_error(err, kDevRowTooLong);
+        if (lane == 0) count[I] = 0;
+        return;
+    }
+    if (lane == 0) {
+        for (int p = 1; p < size; ++p) {  // insertion sort of the (short) row
+            int x = set[p], r = p - 1;
+            while (r >= 0 && set[r] > x) {
+                set[r + 1] = set[r];
+                --r;
+            }
+            set[r + 1] = x;
+        }
+        count[I] = size;
+    }
+    __syncwarp();
+    for (int p = lane; p < size; p += 32) tmp_cols[(size_t)I * cap + p] = set[p];
+}
+
+int rap_symbolic(int nc, const int* agg_ptr, const int* members, const int* rp, const int* ci,
+                 const int* agg, int* count, int* tmp_cols, int cap, int* err, cudaStream_t s) {
+    if (nc <= 0) return BAMG_OK;
+    const size_t smem = sizeof(int) * (size_t)cap * kRapWarps;
+    rap_symbolic_kernel<<<ceil_div(nc, kRapWarps), kRapWarps * 32, smem, s>>>(
+        nc, agg_ptr, members, rp, ci, agg, count, tmp_cols, cap, err);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+__global__ void rap_fill_cols_kernel(int nc, const int* __restrict__ rp_c, const int* __restrict__ tmp,
+                                     int cap, int* __restrict__ ci_c) {
+    const int I = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (I >= nc) return;
+    for (int p = rp_c[I] + lane; p < rp_c[I + 1]; p += 32) ci_c[p] = tmp[(size_t)I * cap + (p - rp_c[I])];
+}
+
+int rap_fill_cols(int nc, const int* rp_c, const int* tmp_cols, int cap, int* ci_c, cudaStream_t s) {
+    if (nc <= 0) return BAMG_OK;
+    rap_fill_cols_kernel<<<ceil_div((long)nc * 32, 256), 256, 0, s>>>(nc, rp_c, tmp_cols, cap, ci_c);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+__global__ void __launch_bounds__(kRapWarps * 32)
+    rap_numeric_kernel(int b, int nc, const int* __restrict__ agg_ptr, const int* __restrict__ members,
+                       const int* __restrict__ rp, const int* __restrict__ ci,
+                       const double* __restrict__ vals, const int* __restrict__ agg,
+                       const int* __restrict__ rp_c, const int* __restrict__ ci_c,
+                       double* __restrict__ vals_c) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * kRapWarps + wid;
+    if (I >= nc) return;
+    const int bb = b * b;
+    const int c0 = rp_c[I], c1 = rp_c[I + 1];
+    double* out = vals_c + (size_t)c0 * bb;
+    for (int e = lane; e < (c1 - c0) * bb; e += 32) out[e] = 0.0;
+    __syncwarp();
+    for (int q = agg_ptr[I]; q < agg_ptr[I + 1]; ++q) {
+        const int i = members[q];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int J = agg[ci[k]];
+            int lo = c0, hi = c1;  // binary search of J in the sorted coarse row
+            while (lo < hi) {
+                int m = (lo + hi) >> 1;
+                if (ci_c[m] < J) lo = m + 1;
+                else hi = m;
+            }
+            double* dst = vals_c + (size_t)lo * bb;
+            const double* src = vals + (size_t)k * bb;
+            for (int e = lane; e < bb; e += 32) dst[e] = __dadd_rn(dst[e], src[e]);
+        }
+    }
+}
+
+int rap_numeric(int b, int nc, const int* agg_ptr, const int* members, const int* rp, const int* ci,
+                const double* vals, const int* agg, const int* rp_c, const int* ci_c, double* vals_c,
+                cudaStream_t s) {
+    if (nc <= 0) return BAMG_OK;
+    rap_numeric_kernel<<<ceil_div(nc, kRapWarps), kRapWarps * 32, 0, s>>>(b, nc, agg_ptr, members, rp, ci,
+                                                                        vals, agg, rp_c, ci_c, vals_c);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// per-node, per-field inverses of the diagonal blocks: Gauss-Jordan with
+// partial pivoting (first maximum wins); singular when a pivot magnitude is
+// below 1e-14 * (infinity norm of the block)
+// ---------------------------------------------------------------------------
+template <int FB>
+__global__ void block_inverse_kernel(int b, int F, int n, const int* __restrict__ diag,
+                                     const double* __restrict__ vals, double* __restrict__ dinv, int* err) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)n * F) return;
+    const int i = (int)(t / F), f = (int)(t - (long)i * F);
+    const double* blk = vals + (size_t)diag[i] * b * b;
+    double w[FB][FB], v[FB][FB];
+    double norm = 0.0;
+#pragma unroll
+    for (int r = 0; r < FB; ++r) {
+        double sum = 0.0;
+#pragma unroll
+        for (int c = 0; c < FB; ++c) {
+            w[r][c] = blk[(f * FB + r) * b + f * FB + c];
+            v[r][c] = (r == c) ? 1.0 : 0.0;
+            sum += fabs(w[r][c]);
+        }
+        norm = fmax(norm, sum);
+    }
+    bool singular = norm == 0.0;
+#pragma unroll
+    for (int k = 0; k < FB; ++k) {
+        int p = k;
+#pragma unroll
+        for (int r = k + 1; r < FB; ++r)
+            if (fabs(w[r][k]) > fabs(w[p][k])) p = r;
+        if (!(fabs(w[p][k]) >= 1e-14 * norm)) singular = true;
+        // swap rows k and p (register arrays: select by predicate)
+#pragma unroll
+        for (int r = k + 1; r < FB; ++r) {
+            if (r == p) {
+#pragma unroll
+                for (int c = 0; c < FB; ++c) {
+                    double tw = w[k][c];
+                    w[k][c] = w[r][c];
+                    w[r][c] = tw;
+                    double tv = v[k][c];
+                    v[k][c] = v[r][c];
+                    v[r][c] = tv;
+                }
+            }
+        }
+        const double piv = w[k][k];
+#pragma unroll
+        for (int c = 0; c < FB; ++c) {
+            w[k][c] = __ddiv_rn(w[k][c], piv);
+            v[k][c] = __ddiv_rn(v[k][c], piv);
+        }
+#pragma unroll
+        for (int r = 0; r < FB; ++r) {
+            if (r == k) continue;
+            const double fr = w[r][k];
+#pragma unroll
+            for (int c = 0; c < FB; ++c) {
+                w[r][c] = __dsub_rn(w[r][c], __dmul_rn(fr, w[k][c]));
+                v[r][c] = __dsub_rn(v[r][c], __dmul_rn(fr, v[k][c]));
+            }
+        }
+    }
+    if (singular) set_error(err, kDevSingularBlock);
+    double* out = dinv + (size_t)t * FB * FB;
+#pragma unroll
+    for (int r = 0; r < FB; ++r)
+#pragma unroll
+        for (int c = 0; c < FB; ++c) out[r * FB + c] = v[r][c];
+}
+
+int block_inverses(int b, int fb, int n, const int* diag, const double* vals, double* dinv64, int* err,
+                   cudaStream_t s) {
+    const int F = b / fb;
+    const int blocks = ceil_div((long)n * F, 128);
+    if (n <= 0) return BAMG_OK;
+    switch (fb) {
+#define CASE(FF) \
+    case FF: block_inverse_kernel<FF><<<blocks, 128, 0, s>>>(b, F, n, diag, vals, dinv64, err); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(6)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: dense FP64 copy, LU with partial pivoting (first maximum
+// wins; multiplier l = a[r][k] / a[k][k], update a[r][c] -= l * a[k][c] as a
+// rounded product then a rounded difference, no fused multiply-add), then
+// the inverse from L U X = P.
+// ---------------------------------------------------------------------------
+__global__ void coarse_dense_kernel(int b, int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    const double* __restrict__ vals, double* __restrict__ dense) {
+    const int i = blockIdx.x;
+    const int nd = n * b;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+            const int r = e / b, c = e - r * b;
+            dense[(size_t)(i * b + r) * nd + j * b + c] = vals[(size_t)k * b * b + e];
+        }
+    }
+}
+
+int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals, double* dense,
+                 cudaStream_t s) {
+    const long nd = (long)n * b;
+    BAMG_CUDA_TRY(cudaMemsetAsync(dense, 0, sizeof(double) * nd * nd, s));
+    coarse_dense_kernel<<<n, 64, 0, s>>>(b, n, rp, ci, vals, dense);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+// Single-CTA LU + inverse for small nd (the coarsest level of a 2D system).
+// a: nd*nd row-major in global memory (L2-resident); inv: nd*nd row-major.
+constexpr int kLuThreads = 1024;
+
+__global__ void __launch_bounds__(kLuThreads) lu_inverse_small_kernel(int nd, double* a, int* piv,
+                                                                      double* inv, double* col, int* err) {
+    __shared__ double red_v[kLuThreads / 32];
+    __shared__ int red_i[kLuThreads / 32];
+    __shared__ double s_norm;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // infinity norm (max row sum) for the singularity threshold
+    {
+        double m = 0.0;
+        for (int r = tid; r < nd; r += blockDim.x) {
+            double sum = 0.0;
+            for (int c = 0; c < nd; ++c) sum += fabs(a[(size_t)r * nd + c]);
+            m = fmax(m, sum);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red_v[wid] = m;
+        __syncthreads();
+        if (tid == 0) {
+            double mm = 0.0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmax(mm, red_v[w]);
+            s_norm = mm;
+        }
+        __syncthreads();
+    }
+    const double norm = s_norm;
+    bool singular = norm == 0.0;
+    for (int k = 0; k < nd; ++k) {
+        // pivot: first row r >= k of maximal |a[r][k]|
+        double best = -1.0;
+        int bi = nd;
+        for (int r = k + tid; r < nd; r += blockDim.x) {
+            double v = fabs(a[(size_t)r * nd + k]);
+            if (v > best) {
+                best = v;
+                bi = r;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            red_v[wid] = best;
+            red_i[wid] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = red_v[0];
+            int bx = red_i[0];
+            for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+                if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
+                    bv = red_v[w];
+                    bx = red_i[w];
+                }
+            red_i[0] = bx;
+            red_v[0] = bv;
+            piv[k] = bx;
+        }
+        __syncthreads();
+        const int p = red_i[0];
+        if (!(red_v[0] >= 1e-14 * norm)) singular = true;
+        if (p != k)
+            for (int c = tid; c < nd; c += blockDim.x) {
+                double t = a[(size_t)k * nd + c];
+                a[(size_t)k * nd + c] = a[(size_t)p * nd + c];
+                a[(size_t)p * nd + c] = t;
+            }
+        __syncthreads();
+        const double akk = a[(size_t)k * nd + k];
+        for (int r = k + 1 + tid; r < nd; r += blockDim.x) col[r] = __ddiv_rn(a[(size_t)r * nd + k], akk);
+        __syncthreads();
+        const int m = nd - k - 1;
+        for (long e = tid; e < (long)m * m; e += blockDim.x) {
+            const int r = k + 1 + (int)(e / m), c = k + 1 + (int)(e % m);
+            a[(size_t)r * nd + c] = __dsub_rn(a[(size_t)r * nd + c], __dmul_rn(col[r], a[(size_t)k * nd + c]));
+        }
+        for (int r = k + 1 + tid; r < nd; r += blockDim.x) a[(size_t)r * nd + k] = col[r];
+        __syncthreads();
+    }
+    if (singular) {
+        if (tid == 0) set_error(err, kDevSingularCoarse);
+        return;
+    }
+    // inverse: column c of X solves L U x = P e_c.  Thread per column c.
+    // X is built in inv row-major (inv[r*nd + c]): consecutive threads touch
+    // consecutive addresses of every row.
+    for (long e = tid; e < (long)nd * nd; e += blockDim.x) inv[e] = 0.0;
+    __syncthreads();
+    for (int c = tid; c < nd; c += blockDim.x) {
+        // P e_c: apply the row swaps in order to the unit vector
+        int pos = c;
+        for (int k = 0; k < nd; ++k) {
+            if (piv[k] == pos) pos = k;
+            else if (k == pos) pos = piv[k];
+        }
+        inv[(size_t)pos * nd + c] = 1.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < nd; ++k) {  // forward, unit L, column oriented
+        for (long e = tid; e < (long)(nd - k - 1) * nd; e += blockDim.x) {
+            const int r = k + 1 + (int)(e / nd), c = (int)(e % nd);
+            inv[(size_t)r * nd + c] -= a[(size_t)r * nd + k] * inv[(size_t)k * nd + c];
+        }
+        __syncthreads();
+    }
+    for (int k = nd - 1; k >= 0; --k) {  // backward, U
+        const double ukk = a[(size_t)k * nd + k];
+        for (int c = tid; c < nd; c += blockDim.x) inv[(size_t)k * nd + c] /= ukk;
+        __syncthreads();
+        for (long e = tid; e < (long)k * nd; e += blockDim.x) {
+            const int r = (int)(e / nd), c = (int)(e % nd);
+            inv[(size_t)r * nd + c] -= a[(size_t)r * nd + k] * inv[(size_t)k * nd + c];
+        }
+        __syncthreads();
+    }
+}
+
+// col: nd doubles of scratch
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, int* err, cudaStream_t s) {
+    if (nd <= 0) return BAMG_OK;
+    double* col = inv;  // multipliers live in the first row of inv until the inverse is built
+    lu_inverse_small_kernel<<<1, kLuThreads, 0, s>>>(nd, a, piv, inv, col, err);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+__global__ void convert_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (long)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
+}
+int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s) {
+    if (m <= 0) return BAMG_OK;
+    long g = (m + 255) / 256;
+    convert_d2f_kernel<<<(int)(g < 4096 ? g : 4096), 256, 0, s>>>(m, x, y);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
+}  // namespace bamg

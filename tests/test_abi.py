@@ -1,0 +1,58 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point
+that include/bamg.h declares.  CPU only: no compute call is made."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2103_07537_gb300 import bamg, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bamg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for name in ["amg_setup", "amg_apply", "fgmres_solve", "amg_destroy", "amg_stats", "amg_strerror",
+                 "bsr_spmv", "amg_solve_host"]:
+        assert name in fns
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    assert sorted(bamg.EXPORTS) == sorted(declared_functions())
+    lib = bamg.load()
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_host_side_validation_without_gpu():
+    # argument checks that return before any CUDA call
+    lib = bamg.load()
+    h = ctypes.c_void_p()
+    fm = np.zeros(3, np.int32)
+    assert lib.amg_setup(None, None, None, 1, 1, 3, fm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), None, None,
+                         ctypes.byref(h)) == bamg.BAMG_EINVAL
+    assert lib.amg_apply(None, None, None, None) == bamg.BAMG_EINVAL
+    assert lib.amg_destroy(None) == bamg.BAMG_OK
+    assert bamg.amg_strerror(bamg.BAMG_ESINGULAR_COARSE) == "singular coarsest operator"
+    p = bamg.amg_default_params()
+    assert (p.max_levels, p.max_coarse, p.n_pre, p.n_post, p.omega, p.cycle_prec) == (10, 2500, 1, 1, 0.5, 64)
+
+
+def test_oracle_is_not_linked_into_the_library():
+    out = subprocess.run(["nm", "-D", build.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    assert "oracle_" not in out

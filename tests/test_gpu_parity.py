@@ -1,0 +1,266 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (stated per test): bit-exact aggregates, colourings, every level's
+sparsity pattern and the Galerkin values (both sides add the same FP64
+numbers in the same order); node-block inverses within 1e-12; FP64 V-cycle
+output within 1e-12 of the oracle relative to its largest entry; FGMRES
+iteration counts within +-1 at a relative residual of 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07537_gb300 import bamg, problems as P
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+VCYCLE_TOL = 1e-12  # relative to max |z| of the oracle
+DINV_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    bamg.load()
+    torch.cuda.set_device(0)
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def device_system(s):
+    return dev(s.row_ptr), dev(s.col_idx), dev(s.vals.reshape(-1))
+
+
+def make_solver(s, **kw):
+    rp, ci, va = device_system(s)
+    return bamg.Solver(rp, ci, va, s.b, s.field_of_dof, **kw)
+
+
+def make_oracle(s, **kw):
+    okw = {k: kw[k] for k in ("max_levels", "max_coarse", "n_pre", "n_post", "omega") if k in kw}
+    return oracle.Hierarchy.from_system(s, **okw)
+
+
+def rel_max(a, ref):
+    scale = np.abs(ref).max()
+    return np.abs(a - ref).max() / (scale if scale > 0 else 1.0)
+
+
+SYSTEMS = {
+    "stokes2d_32": lambda: (P.stokes2d(32, 1), dict(max_levels=3, max_coarse=0)),
+    "mhd2d_16": lambda: (P.mhd2d(16, 2), dict(max_levels=3, max_coarse=0)),
+    "mhd2d_41_ragged": lambda: (P.mhd2d(41, 3), dict(max_levels=4, max_coarse=0)),
+    "stokes3d_9": lambda: (P.stokes3d(9, 1), dict(max_levels=3, max_coarse=0)),
+    "random_b4_f2": lambda: (P.random_block_system(23, 4, [0, 0, 1, 1], seed=5), dict(max_levels=3, max_coarse=0)),
+    "random_b6_f1": lambda: (P.random_block_system(19, 6, [0] * 6, seed=6), dict(max_levels=3, max_coarse=0)),
+    "poisson_b1": lambda: (P.poisson_block(50, 1), dict(max_levels=4, max_coarse=0)),
+    "poisson_b2": lambda: (P.poisson_block(30, 2), dict(max_levels=10, max_coarse=100)),
+}
+
+
+# ---------------------------------------------------------------------------
+# SpMV
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("b", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_bsr_spmv_matches_oracle(b):
+    s = P.random_block_system(37, b, [0] * b, seed=40 + b)  # 1369 block rows: several CTAs and a ragged tail
+    rp, ci, va = device_system(s)
+    x = np.random.default_rng(b).standard_normal(s.n_unknowns)
+    y = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    bamg.bsr_spmv(rp, ci, va, s.n_nodes, b, dev(x), y)
+    torch.cuda.synchronize()
+    ref = oracle.spmv(s.row_ptr, s.col_idx, s.vals, x)
+    assert rel_max(y.cpu().numpy(), ref) <= 1e-14
+
+
+def test_bsr_spmv_empty_and_single_node():
+    s = P.random_block_system(1, 3, [0] * 3, seed=1)
+    rp, ci, va = device_system(s)
+    x = dev(np.ones(3))
+    y = torch.empty(3, dtype=torch.float64, device="cuda")
+    bamg.bsr_spmv(rp, ci, va, 1, 3, x, y)
+    torch.cuda.synchronize()
+    assert np.allclose(y.cpu().numpy(), s.vals[0] @ np.ones(3), rtol=1e-15)
+    bamg.bsr_spmv(rp, ci, va, 0, 3, x, y)  # zero rows: no work, no error
+
+
+# ---------------------------------------------------------------------------
+# hierarchy structure
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_hierarchy_matches_oracle(name):
+    s, kw = SYSTEMS[name]()
+    g = make_solver(s, **kw)
+    o = make_oracle(s, **kw)
+    assert g.num_levels == o.num_levels
+    F = max(s.field_of_dof) + 1
+    for l in range(o.num_levels):
+        Lg, Lo = g.level(l), o.level(l)
+        assert (Lg["n"], Lg["nnzb"]) == (Lo["n"], Lo["nnzb"]), l
+        assert np.array_equal(Lg["row_ptr"], Lo["row_ptr"]), l
+        assert np.array_equal(Lg["col_idx"], Lo["col_idx"]), l
+        # Galerkin values: the same FP64 additions in the same order
+        assert np.array_equal(Lg["vals"], Lo["vals"]), (l, rel_max(Lg["vals"], Lo["vals"]))
+        if l < o.num_levels - 1:
+            assert Lg["n_colours"] == Lo["n_colours"] and Lg["n_agg"] == Lo["n_agg"]
+            assert np.array_equal(Lg["agg"], Lo["agg"]), l
+            assert np.array_equal(Lg["colour"], Lo["colour"]), l
+            assert rel_max(Lg["dinv"].reshape(-1), Lo["dinv"].reshape(-1)) <= DINV_TOL
+            assert Lg["dinv"].shape[1] == F
+
+
+# ---------------------------------------------------------------------------
+# V-cycle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_vcycle_fp64_matches_oracle(name):
+    s, kw = SYSTEMS[name]()
+    g = make_solver(s, **kw)
+    o = make_oracle(s, **kw)
+    r = np.random.default_rng(7).standard_normal(s.n_unknowns)
+    z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    g.apply(dev(r), z)
+    torch.cuda.synchronize()
+    assert rel_max(z.cpu().numpy(), o.vcycle(r)) <= VCYCLE_TOL
+
+
+@pytest.mark.parametrize("variant", [dict(n_pre=0, n_post=2), dict(n_pre=2, n_post=0), dict(omega=0.8),
+                                     dict(n_pre=2, n_post=3, omega=0.6), dict(max_levels=1)])
+def test_vcycle_variants_match_oracle(variant):
+    s = P.mhd2d(12, 4)
+    kw = dict(max_levels=3, max_coarse=0)
+    kw.update(variant)
+    g = make_solver(s, **kw)
+    o = make_oracle(s, **kw)
+    r = s.rhs
+    z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    g.apply(dev(r), z)
+    torch.cuda.synchronize()
+    assert rel_max(z.cpu().numpy(), o.vcycle(r)) <= VCYCLE_TOL
+
+
+def test_vcycle_graph_and_direct_launch_agree_bitwise_and_repeat():
+    s = P.mhd2d(20, 5)
+    kw = dict(max_levels=3, max_coarse=0)
+    g1 = make_solver(s, use_graph=1, **kw)
+    g0 = make_solver(s, use_graph=0, **kw)
+    r = dev(s.rhs)
+    z1 = torch.empty_like(r)
+    z2 = torch.empty_like(r)
+    z0 = torch.empty_like(r)
+    g1.apply(r, z1)
+    g1.apply(r, z2)
+    g0.apply(r, z0)
+    torch.cuda.synchronize()
+    assert torch.equal(z1, z2) and torch.equal(z1, z0)
+
+
+# ---------------------------------------------------------------------------
+# FGMRES
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,restart", [("stokes2d_32", 30), ("mhd2d_16", 30), ("mhd2d_41_ragged", 10),
+                                          ("random_b4_f2", 5)])
+def test_fgmres_iterations_match_oracle(name, restart):
+    s, kw = SYSTEMS[name]()
+    g = make_solver(s, **kw)
+    o = make_oracle(s, **kw)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, it, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=restart, max_iter=3000)
+    _, it_ref, rr_ref, conv = o.fgmres(s.rhs, tol=1e-8, restart=restart, max_iter=3000)
+    assert conv and st == bamg.BAMG_OK
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    xs = x.cpu().numpy()
+    true_rel = np.linalg.norm(s.rhs - oracle.spmv(s.row_ptr, s.col_idx, s.vals, xs)) / np.linalg.norm(s.rhs)
+    assert true_rel <= 1e-8 and rr <= 1e-8
+
+
+def test_fgmres_not_converged_and_zero_rhs():
+    s, kw = SYSTEMS["mhd2d_16"]()
+    g = make_solver(s, **kw)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, it, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=3)
+    assert st == bamg.BAMG_NOT_CONVERGED and it == 3 and rr > 1e-8
+    zero = torch.zeros_like(x)
+    x.fill_(1.0)
+    st, it, rr = g.solve(zero, x)
+    assert st == bamg.BAMG_OK and it == 0 and float(x.abs().max()) == 0.0
+
+
+def test_fp32_cycle_reaches_fp64_residual():
+    s, kw = SYSTEMS["mhd2d_41_ragged"]()
+    g64 = make_solver(s, **kw)
+    g32 = make_solver(s, cycle_prec=32, **kw)
+    r = dev(s.rhs)
+    z64 = torch.empty_like(r)
+    z32 = torch.empty_like(r)
+    g64.apply(r, z64)
+    g32.apply(r, z32)
+    torch.cuda.synchronize()
+    err = float((z32 - z64).norm() / z64.norm())
+    assert err < 1e-4, err
+    x = torch.zeros_like(r)
+    st, it, rr = g32.solve(r, x, tol=1e-8, restart=30, max_iter=3000)
+    xs = x.cpu().numpy()
+    true_rel = np.linalg.norm(s.rhs - oracle.spmv(s.row_ptr, s.col_idx, s.vals, xs)) / np.linalg.norm(s.rhs)
+    assert st == bamg.BAMG_OK and true_rel <= 1e-8
+
+
+def test_host_entry_point_matches_device_path():
+    s, kw = SYSTEMS["mhd2d_16"]()
+    g = make_solver(s, **kw)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, it, rr = g.solve(dev(s.rhs), x)
+    xh = np.zeros(s.n_unknowns)
+    p = bamg.amg_default_params(**kw)
+    st2, it2, rr2 = bamg.amg_solve_host(s.row_ptr, s.col_idx, np.ascontiguousarray(s.vals.reshape(-1)),
+                                        s.n_nodes, s.nnzb, s.b, s.field_of_dof, s.rhs, xh, params=p)
+    assert st == st2 == 0 and it == it2
+    assert np.array_equal(xh, x.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# errors reported as statuses (the device is never trapped)
+# ---------------------------------------------------------------------------
+def expect_status(status, fn):
+    with pytest.raises(bamg.BamgError) as e:
+        fn()
+    assert e.value.status == status
+
+
+def test_invalid_inputs_are_rejected():
+    s = P.mhd2d(6, 1)
+    rp, ci, va = device_system(s)
+    kw = dict(max_levels=2, max_coarse=0)
+    # bad field maps
+    expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, ci, va, 6, [0, 0, 1, 1, 1, 1], **kw))
+    expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, ci, va, 6, [1, 1, 1, 0, 0, 0], **kw))
+    # unsupported block shape for the smoother (b = 5)
+    s5 = P.random_block_system(5, 5, [0] * 5, seed=1)
+    expect_status(bamg.BAMG_EUNSUPPORTED, lambda: make_solver(s5, **kw))
+    # unsorted columns in one row
+    ci_bad = s.col_idx.copy()
+    k0 = s.row_ptr[7]
+    ci_bad[k0], ci_bad[k0 + 1] = ci_bad[k0 + 1], ci_bad[k0]
+    expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, dev(ci_bad), va, 6, s.field_of_dof, **kw))
+    # singular node block of one field
+    v_bad = s.vals.copy()
+    diag = [k for k in range(s.row_ptr[9], s.row_ptr[10]) if s.col_idx[k] == 9][0]
+    v_bad[diag, 3:, 3:] = 0.0
+    expect_status(bamg.BAMG_ESINGULAR_BLOCK,
+                  lambda: bamg.Solver(rp, ci, dev(v_bad.reshape(-1)), 6, s.field_of_dof, **kw))
+
+
+def test_nonfinite_rhs_reported():
+    s = P.mhd2d(6, 1)
+    g = make_solver(s, max_levels=2, max_coarse=0)
+    rhs = s.rhs.copy()
+    rhs[5] = np.nan
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    expect_status(bamg.BAMG_ENAN, lambda: g.solve(dev(rhs), x))
