@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark of the block-AMG-preconditioned FGMRES solve on one GB300.
+
+Workload (default ``mhd2d_128``): the 2D coupled 4-field block system (velocity
+u, v, pressure p, magnetic field Bx, By, Lagrange multiplier psi; 6 dofs per
+node, 2 field blocks) on a 128 x 128 Q1 grid, 16,641 nodes, 99,846 unknowns,
+148,225 stored 6 x 6 blocks, viscosity and resistivity drawn log-uniformly in
+[1e-3, 1] from the seed; FP64 plain monolithic AMG with 4 levels, V(1,1)
+damped block Gauss-Seidel (omega 0.5), FGMRES(30) to a relative residual of
+1e-8.  Synthetic seeded data (the paper's MHD systems are not available).
+
+One step = one complete solve from the matrix already in HBM: hierarchy setup
+(aggregation, colouring, Galerkin products, block inverses, coarse LU),
+FGMRES with the V-cycle preconditioner to 1e-8, and release of the
+hierarchy.  value = solves/s over all ranks (one independent system per rank,
+weak scaling, no collective on the data path).  L2 is flushed between steps
+(a 256 MiB write, outside the timed step).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "V-cycle ms & solves/s to 1e-8 rel. residual (FP64 vs mixed/learned); HBM GB/s"
+UNIT = "solves/s"
+TOL = 1e-8
+RESTART = 30
+MAX_ITER = 5000
+FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+SMS = 152
+
+WORKLOADS = {
+    "mhd2d_128": dict(
+        make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d(128, seed),
+        levels=4, max_coarse=0,
+        desc="2D coupled 4-field Q1 system (u,v,p | Bx,By,psi), 128x128 cells, 6 dofs/node, 99,846 unknowns, "
+             "148,225 blocks, nu/eta log-U[1e-3,1], FP64 V(1,1) BGS omega=0.5, 4 levels, FGMRES(30) to 1e-8"),
+    "stokes2d_32": dict(
+        make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes2d(32, seed),
+        levels=3, max_coarse=0,
+        desc="2D Stokes Q1-Q1 stabilised, 32x32 cells, 3 dofs/node, 3,267 unknowns, FP64, 3 levels, "
+             "FGMRES(30) to 1e-8"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mhd2d_128", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--ref-iters", type=int, default=30,
+                    help="reference arm: inner FGMRES steps timed per step (the sample)")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_07537_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu_index), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        try:
+            for line in open(self.file.name):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_median": statistics.median(float(r[3]) for r in rows
+                                                                          if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def physical_gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids) and ids[local].isdigit():
+            return int(ids[local])
+    return local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_full_solve(sys_, wl):
+    import oracle
+
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
+    t1 = time.perf_counter()
+    _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=RESTART, max_iter=MAX_ITER)
+    t2 = time.perf_counter()
+    return dict(setup_s=t1 - t0, solve_s=t2 - t1, iters=it, relres=rr, converged=conv)
+
+
+def oracle_sample(sys_, wl, iters):
+    """setup + `iters` inner FGMRES steps of the oracle (a bounded sample)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
+    t1 = time.perf_counter()
+    _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=RESTART, max_iter=iters)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(it, 1)
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    s = wl["make"](1)
+    # one full untimed solve gives the iteration count the sample is scaled by
+    full = oracle_full_solve(s, wl)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(s, wl, min(args.ref_iters, 5))
+    times = []
+    for _ in range(args.steps):
+        t_setup, t_iter = oracle_sample(s, wl, args.ref_iters)
+        times.append(t_setup + t_iter * full["iters"])
+    total = sum(times)
+    value = args.steps / total
+    sample = (f"per step: oracle setup + {args.ref_iters} inner FGMRES(30) steps of {args.workload} seed 1, "
+              f"scaled to one full solve of {full['iters']} inner steps (the count of an untimed full oracle "
+              f"solve, relres {full['relres']:.2e})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "seed": 1},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2103_07537_gb300 import bamg
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    bamg.load()
+    wl = WORKLOADS[args.workload]
+    seed = 1 + rank
+    s = wl["make"](seed)
+    rp = torch.from_numpy(s.row_ptr).to(dev)
+    ci = torch.from_numpy(s.col_idx).to(dev)
+    va = torch.from_numpy(np.ascontiguousarray(s.vals.reshape(-1))).to(dev)
+    b = torch.from_numpy(s.rhs).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=64)
+
+    def step(params, profile=False):
+        h = bamg.amg_setup(rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params, stream)
+        try:
+            if profile:
+                bamg.amg_profile(h, True)
+            x.zero_()
+            st, it, rr = bamg.fgmres_solve(h, b, x, TOL, RESTART, MAX_ITER, stream)
+            prof = None
+            if profile:
+                prof = {k: bamg.amg_profile_read(h, k) for k in bamg.KERNEL_KINDS}
+        finally:
+            bamg.amg_destroy(h)
+        return st, it, rr, prof
+
+    def timed(params, k_steps):
+        tot = 0.0
+        last = None
+        for _ in range(k_steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(params)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot, last
+
+    for _ in range(max(args.warmup, 0)):
+        step(params64)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = bamg.amg_launch_count()
+    with ClockSampler(physical_gpu_index(local)) as clk:
+        total_ms, (st, iters, relres, _) = timed(params64, args.steps)
+    launches = bamg.amg_launch_count() - launches0
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    t_max = total_ms
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+    clocks = clk.summary()
+
+    # --- V-cycle and setup timings (the metric's "V-cycle ms") -------------------
+    h = bamg.amg_setup(rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params64, stream)
+    r = b.clone()
+    z = torch.empty_like(b)
+    for _ in range(5):
+        bamg.amg_apply(h, r, z, stream)
+    vt = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bamg.amg_apply(h, r, z, stream)
+        e1.record(stream)
+        e1.synchronize()
+        vt.append(e0.elapsed_time(e1))
+    stats = bamg.amg_stats(h)
+    bamg.amg_destroy(h)
+    st_times = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hh = bamg.amg_setup(rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params64, stream)
+        e1.record(stream)
+        e1.synchronize()
+        bamg.amg_destroy(hh)
+        st_times.append(e0.elapsed_time(e1))
+
+    # --- mixed precision variant: FP32 cycle inside FP64 FGMRES -------------------
+    params32 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=32)
+    step(params32)
+    k32 = max(1, min(args.steps, 5))
+    ms32, (st32, it32, rr32, _) = timed(params32, k32)
+    mixed = {"cycle": "fp32 (fp64 outer FGMRES, fp64 coarse solve)", "value": k32 / (ms32 / 1e3), "unit": UNIT,
+             "iterations": it32, "relres": rr32, "converged": st32 == 0}
+
+    # --- per-kernel profile pass (events around every launch) --------------------
+    kernels = {}
+    for _ in range(max(1, args.profile_steps)):
+        flush.zero_()
+        _, _, _, prof = step(params64, profile=True)
+        for k, v in prof.items():
+            acc = kernels.setdefault(k, dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
+            for f in acc:
+                acc[f] += v[f]
+    peak_gbs, peak_src = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or 1920.0
+    fp64_peak_tflops = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA / clk / SM on GB300
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    tfl = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    t_mem = d["bytes"] / (peak_gbs * 1e9)
+    t_alu = d["flops"] / (fp64_peak_tflops * 1e12)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("source_digest") == source_digest() and tj.get("kind") == dom:
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    if t_alu > t_mem:
+        roofline = {"bound": "alu", "achieved": tfl, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                    "frac": tfl / fp64_peak_tflops, "traffic": traffic,
+                    "peak_source": f"derived FP64 FMA peak: {SMS} SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz",
+                    "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs}
+    else:
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+                    "traffic": traffic, "peak_source": peak_src}
+    roofline.update({"kernel": dom, "launches": d["launches"] // max(1, args.profile_steps),
+                     "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+                     "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                     "flops_per_launch": d["flops"] / max(1, d["launches"])})
+    ksum = {k: {"ms_per_solve": v["ms"] / max(1, args.profile_steps), "launches": v["launches"] // max(1, args.profile_steps),
+                "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
+                "TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else 0.0}
+            for k, v in kernels.items() if v["launches"]}
+
+    # --- end to end through the host-buffer entry point ---------------------------
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(s.row_ptr).pin_memory().numpy()
+        ci_h = torch.from_numpy(s.col_idx).pin_memory().numpy()
+        va_h = torch.from_numpy(np.ascontiguousarray(s.vals.reshape(-1))).pin_memory().numpy()
+        b_h = torch.from_numpy(s.rhs).pin_memory().numpy()
+        x_h = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory().numpy()
+        k_e = max(1, min(args.steps, 5))
+        bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL, RESTART,
+                            MAX_ITER, params64, stream)
+        tot = 0.0
+        for _ in range(k_e):
+            x_h[:] = 0.0
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL,
+                                RESTART, MAX_ITER, params64, stream)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        h2d = rp_h.nbytes + ci_h.nbytes + va_h.nbytes + b_h.nbytes + x_h.nbytes
+        e2e = {"value": world * k_e / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(x_h.nbytes), "api": "amg_solve_host (pinned host buffers)"}
+
+    # --- CPU baseline: the oracle on this host ------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full = oracle_full_solve(s, wl)
+        t = full["setup_s"] + full["solve_s"]
+        cpu = {"kind": "oracle", "value": 1.0 / t, "unit": UNIT, "cores": 1,
+               "sample": f"one full solve (setup + FGMRES(30) to 1e-8, {full['iters']} inner steps) of "
+                         f"{args.workload} seed {seed}, single-threaded C oracle",
+               "host_cores_available": os.cpu_count(), "iterations": full["iters"]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["desc"], "name": args.workload, "seed": seed,
+                           "l2": "flushed between steps (256 MiB write outside the timed step)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "step": "amg_setup + fgmres_solve to 1e-8 + amg_destroy, inputs resident in HBM"},
+                "iterations": iters, "relres": relres, "converged": st == 0,
+                "vcycle_ms": statistics.median(vt), "setup_ms": statistics.median(st_times),
+                "levels": [lv["n"] for lv in stats["levels"]],
+                "mixed": mixed, "kernels": ksum, "roofline": roofline, "clocks": clocks,
+                "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,6 +156,30 @@ int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, double* vals
  * returns the length written (without the terminating zero) or a negative status. */
 int amg_stats(bamg_t h, char* json, int cap);
 
+/* ---- measurement ----
+ * amg_profile(h, 1) makes the handle record a CUDA event pair around every
+ * kernel it launches from then on (V-cycles run as direct launches, not from
+ * the captured graph, while profiling is on) and prepares the per-launch
+ * algorithmic byte and flop counts; amg_profile(h, 0) stops it.
+ * amg_profile_read synchronises, returns for one kernel kind the summed
+ * device time (ms), the number of launches and the summed algorithmic bytes
+ * and flops since the last read of that kind, and clears them. */
+#define BAMG_K_SMOOTH 0   /* one colour of one field step of block Gauss-Seidel */
+#define BAMG_K_RESIDUAL 1 /* r = b - A u inside the cycle                     */
+#define BAMG_K_RESTRICT 2
+#define BAMG_K_PROLONG 3
+#define BAMG_K_COARSE 4   /* dense coarsest solve                             */
+#define BAMG_K_SPMV 5     /* FP64 SpMV / residual of the outer Krylov method  */
+#define BAMG_K_KRYLOV 6   /* Gram-Schmidt, norms, rotations, updates          */
+#define BAMG_K_CAST 7
+#define BAMG_K_COUNT 8
+int amg_profile(bamg_t h, int enable);
+int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes, double* flops);
+
+/* number of kernels this library has launched in the process so far (kernels
+ * replayed from a captured graph count once per replay) */
+long long amg_launch_count(void);
+
 /* frees every device buffer of the handle; NULL is accepted */
 int amg_destroy(bamg_t h);
 

@@ -23,7 +23,11 @@ BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 
 #: every symbol the C header declares
 EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
-           "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror"]
+           "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror",
+           "amg_profile", "amg_profile_read", "amg_launch_count"]
+
+#: kernel kinds of amg_profile_read
+KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast"]
 
 _lock = threading.Lock()
 _lib = None
@@ -77,6 +81,10 @@ def load(build_if_missing: bool = True):
         lib.amg_destroy.argtypes = [_vp]
         lib.amg_strerror.argtypes = [C.c_int]
         lib.amg_strerror.restype = C.c_char_p
+        lib.amg_profile.argtypes = [_vp, C.c_int]
+        lib.amg_profile_read.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_longlong), _dp, _dp]
+        lib.amg_launch_count.argtypes = []
+        lib.amg_launch_count.restype = C.c_longlong
         _lib = lib
         return lib
 
@@ -217,6 +225,26 @@ def amg_stats(handle: int) -> dict:
 
 def amg_destroy(handle: int) -> None:
     load().amg_destroy(handle)
+
+
+def amg_profile(handle: int, enable: bool) -> None:
+    st = load().amg_profile(handle, 1 if enable else 0)
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_profile")
+
+
+def amg_profile_read(handle: int, kind) -> dict:
+    """{'ms', 'launches', 'bytes', 'flops'} for one kernel kind since the last read."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ms, n, by, fl = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+    st = load().amg_profile_read(handle, k, C.byref(ms), C.byref(n), C.byref(by), C.byref(fl))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_profile_read")
+    return dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
+
+
+def amg_launch_count() -> int:
+    return int(load().amg_launch_count())
 
 
 class Solver:

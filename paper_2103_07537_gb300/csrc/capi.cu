@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -13,6 +14,18 @@
 #include "common.cuh"
 
 using namespace bamg;
+
+namespace {
+std::atomic<long long> g_launches{0};
+thread_local long long* t_capture_sink = nullptr;  // set while a graph is captured
+}  // namespace
+
+void bamg::note_launch(int count) {
+    if (t_capture_sink) *t_capture_sink += count;
+    else g_launches += count;
+}
+
+extern "C" long long amg_launch_count(void) { return g_launches.load(); }
 
 namespace {
 
@@ -31,6 +44,14 @@ struct Level {
     int *agg = nullptr, *agg_ptr = nullptr, *members = nullptr;
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
+    // per-colour counts for the algorithmic byte / flop model (profiling only)
+    std::vector<long> colour_nnz, colour_nnz_lower;
+};
+
+struct ProfRec {
+    cudaEvent_t e0, e1;
+    int kind;
+    double bytes, flops;
 };
 
 int map_dev_error(int code) {
@@ -72,6 +93,11 @@ struct bamg_ctx {
     float *r32 = nullptr, *z32 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    long long graph_kernels = 0;
+    // profiling
+    int prof = 0;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> ev_free;
     // FGMRES workspace
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *h1 = nullptr, *h2 = nullptr,
@@ -98,6 +124,11 @@ struct bamg_ctx {
             }
     }
     ~bamg_ctx() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+        for (auto e : ev_free) cudaEventDestroy(e);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         for (void* a : allocs)
@@ -120,6 +151,46 @@ static int check_dev(bamg_ctx* h, cudaStream_t s) {
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
     return map_dev_error(h->h_pin[0]);
 }
+
+// ---------------------------------------------------------------------------
+// per-launch event timing (only while profiling is enabled)
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(bamg_ctx* h) {
+    if (!h->ev_free.empty()) {
+        cudaEvent_t e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static int prof_begin(bamg_ctx* h, cudaStream_t s) {
+    if (!h->prof) return -1;
+    ProfRec r{take_event(h), take_event(h), -1, 0.0, 0.0};
+    cudaEventRecord(r.e0, s);
+    h->recs.push_back(r);
+    return (int)h->recs.size() - 1;
+}
+
+static void prof_end(bamg_ctx* h, cudaStream_t s, int idx, int kind, double bytes, double flops) {
+    if (idx < 0) return;
+    ProfRec& r = h->recs[(size_t)idx];
+    cudaEventRecord(r.e1, s);
+    r.kind = kind;
+    r.bytes = bytes;
+    r.flops = flops;
+}
+
+// launch with optional timing: needs h and s in scope
+#define PL(kind, bytes, flops, expr)                     \
+    do {                                                 \
+        const int _pi = prof_begin(h, s);                \
+        const int _st = (expr);                          \
+        prof_end(h, s, _pi, (kind), (bytes), (flops));   \
+        if (_st != BAMG_OK) return _st;                  \
+    } while (0)
 
 extern "C" void amg_default_params(amg_params* p) {
     if (!p) return;
@@ -399,7 +470,15 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.field = f;
         a.F = h->F;
         a.omega = h->p.omega;
-        TRY(launch_bgs_colour<T>(h->b, h->fb, a, s));
+        double bytes = 0.0, flops = 0.0;
+        if (h->prof) {
+            const double es = sizeof(T), B = h->b, FB = h->fb, nc = a.n_in_colour;
+            const double nnz = (double)L.colour_nnz[c], low = (double)L.colour_nnz_lower[c];
+            bytes = nnz * (FB * B * es + 4.0) + nc * 8.0 + nc * FB * FB * es + nc * FB * es +
+                    (x_in ? nc * B * es : 0.0) + nc * B * es + nc * FB * es + (c > 0 ? nc * FB * es : 0.0);
+            flops = 2.0 * ((x_in ? nnz * FB * B : 0.0) + low * FB * FB + nc * FB * FB);
+        }
+        PL(BAMG_K_SMOOTH, bytes, flops, launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
     return BAMG_OK;
 }
@@ -409,7 +488,12 @@ template <typename T>
 static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const Level& L = h->lev[l];
     const int b = h->b;
-    if (l == h->nlev - 1) return launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s);
+    if (l == h->nlev - 1) {
+        const double nd = h->nd;
+        PL(BAMG_K_COARSE, nd * nd * 8.0 + 2.0 * nd * sizeof(T), 2.0 * nd * nd,
+           launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s));
+        return BAMG_OK;
+    }
     T* xa = static_cast<T*>(L.xa);
     T* xb = static_cast<T*>(L.xb);
     T* cur = nullptr;  // nullptr = the zero initial guess
@@ -425,10 +509,14 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     }
     const Level& C = h->lev[l + 1];
     T* res = static_cast<T*>(L.res);
-    TRY(launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
-    TRY(launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
+    const double es = sizeof(T), nb = (double)L.n * b, ncb = (double)C.n * b;
+    PL(BAMG_K_RESIDUAL, (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es,
+       2.0 * L.nnzb * b * b, launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+    PL(BAMG_K_RESTRICT, L.n * 4.0 + (C.n + 1) * 4.0 + nb * es + ncb * es, nb,
+       launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
-    TRY(launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
+    PL(BAMG_K_PROLONG, L.n * 4.0 + 2.0 * nb * es + ncb * es, nb,
+       launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
     const int S_post = h->p.n_post * h->F;
     if (S_post == 0)
         BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
@@ -444,16 +532,21 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
 static int cycle_direct(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
     const long N = (long)h->lev[0].n * h->b;
     if (h->p.cycle_prec == 64) return mgv<double>(h, 0, r, z, s);
-    TRY(launch_cast_d2f(N, r, h->r32, s));
+    PL(BAMG_K_CAST, N * 12.0, 0.0, launch_cast_d2f(N, r, h->r32, s));
     TRY(mgv<float>(h, 0, h->r32, h->z32, s));
-    return launch_cast_f2d(N, h->z32, z, s);
+    PL(BAMG_K_CAST, N * 12.0, 0.0, launch_cast_f2d(N, h->z32, z, s));
+    return BAMG_OK;
 }
 
 static int ensure_graph(bamg_ctx* h) {
     if (h->graph_exec) return BAMG_OK;
     cudaStream_t cs = h->cap_stream;
     BAMG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    long long kernels = 0;
+    t_capture_sink = &kernels;
     int st = cycle_direct(h, h->cyc_in, h->cyc_out, cs);
+    t_capture_sink = nullptr;
+    h->graph_kernels = kernels;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (st != BAMG_OK) {
@@ -467,11 +560,12 @@ static int ensure_graph(bamg_ctx* h) {
 }
 
 static int apply_impl(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
-    if (!h->p.use_graph) return cycle_direct(h, r, z, s);
+    if (!h->p.use_graph || h->prof) return cycle_direct(h, r, z, s);
     TRY(ensure_graph(h));
     const size_t nbytes = sizeof(double) * (size_t)h->lev[0].n * h->b;
     BAMG_CUDA_TRY(cudaMemcpyAsync(h->cyc_in, r, nbytes, cudaMemcpyDeviceToDevice, s));
     BAMG_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+    note_launch((int)h->graph_kernels);
     BAMG_CUDA_TRY(cudaMemcpyAsync(z, h->cyc_out, nbytes, cudaMemcpyDeviceToDevice, s));
     return BAMG_OK;
 }
@@ -511,8 +605,9 @@ static int ensure_krylov(bamg_ctx* h, int m) {
 
 // ||x||^2 into dst (device), via the deterministic chunked reduction
 static int norm_sq(bamg_ctx* h, long N, const double* x, double* dst, cudaStream_t s) {
-    TRY(launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, s));
-    return launch_finish(1, N, h->partial, dst, s);
+    PL(BAMG_K_KRYLOV, N * 8.0, 2.0 * N, launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, s));
+    PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(1, N, h->partial, dst, s));
+    return BAMG_OK;
 }
 
 extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
@@ -538,8 +633,12 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         converged = 1;
     }
+    const double spmv_bytes = (double)L0.nnzb * (bsz * bsz * 8.0 + 4.0) + (L0.n + 1) * 4.0 + 2.0 * N * 8.0;
+    const double spmv_flops = 2.0 * L0.nnzb * bsz * bsz;
+    const double vN = N * 8.0;
     while (!converged) {
-        TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
+        PL(BAMG_K_SPMV, spmv_bytes + vN, spmv_flops,
+           launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
         TRY(norm_sq(h, N, h->w, h->wsq, s));
         BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->wsq, sizeof(double), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -551,23 +650,29 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             break;
         }
         if (total >= max_iter) break;
-        TRY(launch_init_g(m, h->wsq, h->g, h->scal, s));
-        TRY(launch_scale(N, h->w, h->scal, h->V, 0, s));  // v_0 = r / beta
+        PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_init_g(m, h->wsq, h->g, h->scal, s));
+        PL(BAMG_K_KRYLOV, 2.0 * vN, N, launch_scale(N, h->w, h->scal, h->V, 0, s));  // v_0 = r / beta
         int k = 0;
         for (int j = 0; j < m; ++j) {
             const double* vj = h->V + (size_t)j * N;
             double* zj = h->Z + (size_t)j * N;
             TRY(apply_impl(h, vj, zj, s));
-            TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
+            PL(BAMG_K_SPMV, spmv_bytes, spmv_flops,
+               launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
             // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
-            TRY(launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, s));
-            TRY(launch_finish(j + 2, N, h->partial, h->h1, s));
-            TRY(launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, s));
-            TRY(launch_finish(j + 1, N, h->partial, h->h2, s));
-            TRY(launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, s));
-            TRY(launch_finish(1, N, h->partial, h->wsq, s));
-            TRY(launch_givens(j, m, h->h1, h->h2, h->wsq, h->H, h->cs, h->sn, h->g, h->scal, s));
-            TRY(launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
+            const double nv = j + 1;
+            PL(BAMG_K_KRYLOV, (nv + 1) * vN, 2.0 * N * (nv + 1),
+               launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, s));
+            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(j + 2, N, h->partial, h->h1, s));
+            PL(BAMG_K_KRYLOV, (2 * nv + 2) * vN, 4.0 * N * nv,
+               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, s));
+            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(j + 1, N, h->partial, h->h2, s));
+            PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
+               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, s));
+            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(1, N, h->partial, h->wsq, s));
+            PL(BAMG_K_KRYLOV, 0.0, 0.0,
+               launch_givens(j, m, h->h1, h->h2, h->wsq, h->H, h->cs, h->sn, h->g, h->scal, s));
+            PL(BAMG_K_KRYLOV, 2.0 * vN, N, launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
             total++;
             k = j + 1;
             BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -575,8 +680,9 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             if (!isfinite(hs[1])) return BAMG_ENAN;
             if (hs[1] / bnorm <= tol || hs[2] != 0.0 || total >= max_iter) break;
         }
-        TRY(launch_solve_upper(k, m, h->H, h->g, h->y, s));
-        TRY(launch_axpy_dot(N, x, h->Z, N, k, h->y, -1.0, 0, nullptr, s));  // x += Z y
+        PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_solve_upper(k, m, h->H, h->g, h->y, s));
+        PL(BAMG_K_KRYLOV, (k + 2.0) * vN, 2.0 * N * k,
+           launch_axpy_dot(N, x, h->Z, N, k, h->y, -1.0, 0, nullptr, s));  // x += Z y
     }
     if (iters) *iters = total;
     if (relres) *relres = rel;
@@ -694,4 +800,59 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     memcpy(json, o.data(), (size_t)w);
     json[w] = 0;
     return len;
+}
+
+// ---------------------------------------------------------------------------
+// measurement
+// ---------------------------------------------------------------------------
+extern "C" int amg_profile(bamg_t h, int enable) {
+    if (!h) return BAMG_EINVAL;
+    if (enable && !h->prof) {
+        // per-colour stored-block counts (all, and those to a lower colour)
+        for (int l = 0; l + 1 < h->nlev; ++l) {
+            Level& L = h->lev[l];
+            std::vector<int> rp((size_t)L.n + 1), ci((size_t)L.nnzb), col((size_t)L.n);
+            BAMG_CUDA_TRY(cudaMemcpy(rp.data(), L.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+            BAMG_CUDA_TRY(cudaMemcpy(ci.data(), L.ci, sizeof(int) * ci.size(), cudaMemcpyDeviceToHost));
+            BAMG_CUDA_TRY(cudaMemcpy(col.data(), L.colour, sizeof(int) * col.size(), cudaMemcpyDeviceToHost));
+            L.colour_nnz.assign((size_t)L.n_colours, 0);
+            L.colour_nnz_lower.assign((size_t)L.n_colours, 0);
+            for (int i = 0; i < L.n; ++i) {
+                L.colour_nnz[(size_t)col[i]] += rp[i + 1] - rp[i];
+                for (int k = rp[i]; k < rp[i + 1]; ++k)
+                    if (ci[k] != i && col[ci[k]] < col[i]) L.colour_nnz_lower[(size_t)col[i]]++;
+            }
+        }
+    }
+    h->prof = enable ? 1 : 0;
+    return BAMG_OK;
+}
+
+extern "C" int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes,
+                                double* flops) {
+    if (!h || kind < 0 || kind >= BAMG_K_COUNT) return BAMG_EINVAL;
+    double t = 0.0, by = 0.0, fl = 0.0;
+    long long cnt = 0;
+    std::vector<ProfRec> keep;
+    for (auto& r : h->recs) {
+        if (r.kind != kind) {
+            keep.push_back(r);
+            continue;
+        }
+        BAMG_CUDA_TRY(cudaEventSynchronize(r.e1));
+        float e = 0.0f;
+        BAMG_CUDA_TRY(cudaEventElapsedTime(&e, r.e0, r.e1));
+        t += e;
+        by += r.bytes;
+        fl += r.flops;
+        cnt++;
+        h->ev_free.push_back(r.e0);
+        h->ev_free.push_back(r.e1);
+    }
+    h->recs.swap(keep);
+    if (ms) *ms = t;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = by;
+    if (flops) *flops = fl;
+    return BAMG_OK;
 }

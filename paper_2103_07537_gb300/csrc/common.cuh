@@ -76,6 +76,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
+// counts kernel launches (defined in capi.cu); while a CUDA graph is being
+// captured on this thread the count goes to the graph instead
+void note_launch(int count = 1);
+// status after k kernel launches (counted)
+inline int launched(int k) {
+    note_launch(k);
+    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+}
+
 }  // namespace bamg
 
 // ---------------------------------------------------------------------------

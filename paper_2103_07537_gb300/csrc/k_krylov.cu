@@ -121,16 +121,16 @@ __global__ void finish_kernel(int nv, int nchunk, const double* __restrict__ par
 int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx,
                      double* partial, cudaStream_t s) {
     multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign,
                     int mode, double* partial, cudaStream_t s) {
     axpy_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, h, sign, mode, partial);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_finish(int nv, long N, const double* partial, double* out, cudaStream_t s) {
     finish_kernel<<<1, 512, 0, s>>>(nv, krylov_chunks(N), partial, out);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -205,20 +205,20 @@ __global__ void init_g_kernel(int m, const double* __restrict__ bsq, double* __r
 int launch_givens(int j, int m, const double* h1, const double* h2, const double* wsq, double* H, double* cs,
                   double* sn, double* g, double* scal, cudaStream_t s) {
     givens_kernel<<<1, 32, 0, s>>>(j, m, h1, h2, wsq, H, cs, sn, g, scal);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s) {
     solve_upper_kernel<<<1, 32, 0, s>>>(k, m, H, g, y);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_scale(long N, const double* x, const double* scal, double* y, int check_breakdown, cudaStream_t s) {
     long g = (N + 255) / 256;
     scale_kernel<<<(int)(g < 1216 ? (g > 0 ? g : 1) : 1216), 256, 0, s>>>(N, x, scal, y, check_breakdown);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_init_g(int m, const double* bsq, double* g, double* scal, cudaStream_t s) {
     init_g_kernel<<<1, 64, 0, s>>>(m, bsq, g, scal);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 }  // namespace bamg

@@ -101,7 +101,7 @@ int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, c
     scan_sums_kernel<<<1, kScanThreads, 0, s>>>(ntiles, d_tmp);
     if (n > 0) scan_add_kernel<<<ntiles, kScanThreads, 0, s>>>(n, out, d_tmp);
     BAMG_CUDA_TRY(cudaMemcpyAsync(out + n, d_tmp + ntiles, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(n > 0 ? 3 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -148,7 +148,7 @@ __global__ void check_pattern_kernel(int n, const int* __restrict__ rp, const in
 int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* err, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
     check_pattern_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, ci, diag, err);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +255,7 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
             mis2_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.flag);
         }
+        note_launch(batch);
         rounds += batch;
         BAMG_CUDA_TRY(cudaMemcpyAsync(w.host_flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -268,6 +269,7 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
     if (st) return st;
     assign_phase1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.rootid, w.agg1);
     attach_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.agg1, agg, d_count + 1);
+    note_launch(3);
     BAMG_CUDA_TRY(cudaMemcpyAsync(d_count, w.rootid + n, sizeof(int), cudaMemcpyDeviceToDevice, s));
     BAMG_CUDA_TRY(cudaMemcpyAsync(w.host_flag, d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -317,7 +319,7 @@ int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int
     BAMG_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(nc + 1), s));
     scatter_by_key_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, agg, agg_ptr, count, members);
     sort_segments_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(nc, agg_ptr, members);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(3);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,6 +377,7 @@ int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, 
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
             colour_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, colour, d_flag);
         }
+        note_launch(batch);
         rounds += batch;
         BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -385,6 +388,7 @@ int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, 
     if (rounds_out) *rounds_out = (int)rounds;
     BAMG_CUDA_TRY(cudaMemsetAsync(d_flag + 2, 0xff, sizeof(int), s));
     max_kernel<<<min(ceil_div(n, 256), 1024), 256, 0, s>>>(n, colour, d_flag + 2);
+    note_launch(1);
     BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag + 2, d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
     *n_colours = h_flag[2] + 1;
@@ -418,7 +422,7 @@ int colour_order(int n, int C, const int* colour, int* colour_ptr, int* nodes, i
         compact_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, colour, c, pos, colour_ptr + c, nodes);
         advance_kernel<<<1, 1, 0, s>>>(colour_ptr, c, pos, n);
     }
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(3 * C);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,7 +496,7 @@ int rap_symbolic(int nc, const int* agg_ptr, const int* members, const int* rp, 
     const size_t smem = sizeof(int) * (size_t)cap * kRapWarps;
     rap_symbolic_kernel<<<ceil_div(nc, kRapWarps), kRapWarps * 32, smem, s>>>(
         nc, agg_ptr, members, rp, ci, agg, count, tmp_cols, cap, err);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 __global__ void rap_fill_cols_kernel(int nc, const int* __restrict__ rp_c, const int* __restrict__ tmp,
@@ -506,7 +510,7 @@ __global__ void rap_fill_cols_kernel(int nc, const int* __restrict__ rp_c, const
 int rap_fill_cols(int nc, const int* rp_c, const int* tmp_cols, int cap, int* ci_c, cudaStream_t s) {
     if (nc <= 0) return BAMG_OK;
     rap_fill_cols_kernel<<<ceil_div((long)nc * 32, 256), 256, 0, s>>>(nc, rp_c, tmp_cols, cap, ci_c);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 __global__ void __launch_bounds__(kRapWarps * 32)
@@ -546,7 +550,7 @@ int rap_numeric(int b, int nc, const int* agg_ptr, const int* members, const int
     if (nc <= 0) return BAMG_OK;
     rap_numeric_kernel<<<ceil_div(nc, kRapWarps), kRapWarps * 32, 0, s>>>(b, nc, agg_ptr, members, rp, ci,
                                                                         vals, agg, rp_c, ci_c, vals_c);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,7 +638,7 @@ int block_inverses(int b, int fb, int n, const int* diag, const double* vals, do
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -661,7 +665,7 @@ int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals,
     const long nd = (long)n * b;
     BAMG_CUDA_TRY(cudaMemsetAsync(dense, 0, sizeof(double) * nd * nd, s));
     coarse_dense_kernel<<<n, 64, 0, s>>>(b, n, rp, ci, vals, dense);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 // Single-CTA LU + inverse for small nd (the coarsest level of a 2D system).
@@ -794,7 +798,7 @@ int dense_lu_inverse(int nd, double* a, int* piv, double* inv, int* err, cudaStr
     if (nd <= 0) return BAMG_OK;
     double* col = inv;  // multipliers live in the first row of inv until the inverse is built
     lu_inverse_small_kernel<<<1, kLuThreads, 0, s>>>(nd, a, piv, inv, col, err);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 __global__ void convert_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
@@ -805,7 +809,7 @@ int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s) {
     if (m <= 0) return BAMG_OK;
     long g = (m + 255) / 256;
     convert_d2f_kernel<<<(int)(g < 4096 ? g : 4096), 256, 0, s>>>(m, x, y);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 }  // namespace bamg

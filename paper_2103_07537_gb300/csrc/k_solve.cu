@@ -51,7 +51,7 @@ int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 template int launch_spmv<double>(int, int, const int*, const int*, const double*, const double*,
                                  const double*, double*, cudaStream_t);
@@ -80,7 +80,7 @@ int launch_restrict(int b, int nc, const int* agg_ptr, const int* members, const
                     cudaStream_t s) {
     if (nc <= 0) return BAMG_OK;
     restrict_kernel<T><<<ceil_div((long)nc * b, 256), 256, 0, s>>>(b, nc, agg_ptr, members, res, rc);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 template int launch_restrict<double>(int, int, const int*, const int*, const double*, double*, cudaStream_t);
 template int launch_restrict<float>(int, int, const int*, const int*, const float*, float*, cudaStream_t);
@@ -102,7 +102,7 @@ template <typename T>
 int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
     prolong_kernel<T><<<ceil_div((long)n * b, 256), 256, 0, s>>>(b, n, agg, uc, u);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 template int launch_prolong<double>(int, int, const int*, const double*, double*, cudaStream_t);
 template int launch_prolong<float>(int, int, const int*, const float*, float*, cudaStream_t);
@@ -195,7 +195,7 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 template int launch_bgs_colour<double>(int, int, const BgsArgs&, cudaStream_t);
 template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
@@ -220,7 +220,7 @@ template <typename T>
 int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
     dense_gemv_kernel<T><<<ceil_div((long)nd * kWarp, 256), 256, 0, s>>>(nd, ainv, x, y);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 template int launch_dense_gemv<double>(int, const double*, const double*, double*, cudaStream_t);
 template int launch_dense_gemv<float>(int, const double*, const float*, float*, cudaStream_t);
@@ -243,12 +243,12 @@ static int grid_for(long m) {
 int launch_cast_d2f(long m, const double* x, float* y, cudaStream_t s) {
     if (m <= 0) return BAMG_OK;
     cast_d2f_kernel<<<grid_for(m), 256, 0, s>>>(m, x, y);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 int launch_cast_f2d(long m, const float* x, double* y, cudaStream_t s) {
     if (m <= 0) return BAMG_OK;
     cast_f2d_kernel<<<grid_for(m), 256, 0, s>>>(m, x, y);
-    return cudaGetLastError() == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+    return launched(1);
 }
 
 }  // namespace bamg
