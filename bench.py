@@ -434,6 +434,8 @@ def run_ours(args):
                 "iterations": iters, "relres": relres, "converged": st == 0,
                 "vcycle_ms": statistics.median(vt), "setup_ms": statistics.median(st_times),
                 "levels": [lv["n"] for lv in stats["levels"]],
+                "colours": [lv["colours"] for lv in stats["levels"]],
+                "setup_phase_ms": stats.get("setup_phase_ms"),
                 "mixed": mixed, "kernels": ksum, "roofline": roofline, "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

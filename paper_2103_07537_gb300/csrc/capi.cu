@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
 #include <new>
 #include <string>
 #include <vector>
@@ -104,6 +105,8 @@ struct bamg_ctx {
            *wsq = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr,
            *scal = nullptr;
     double* h_scal = nullptr;  // pinned [4]
+    // host wall time of the setup phases (ms): pattern, aggregate, rap, colour, inverse, coarse, vectors
+    double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
     template <typename T>
     int alloc(T** ptr, size_t count) {
@@ -221,8 +224,14 @@ extern "C" const char* amg_strerror(int status) {
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
+using Clock = std::chrono::steady_clock;
+static double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
 static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const double* vals, int n,
                       int nnzb, cudaStream_t s) {
+    auto tp = Clock::now();
     const int b = h->b;
     const size_t bb = (size_t)b * b;
     TRY(h->alloc(&h->d_err, 4));
@@ -250,6 +259,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&L.diag, (size_t)L.n));
         TRY(launch_check_pattern(L.n, L.rp, L.ci, L.diag, h->d_err, s));
         TRY(check_dev(h, s));
+        h->t_phase[0] += ms_since(tp);
+        tp = Clock::now();
         const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
         if (!coarsen) break;
         // aggregation (clone for every field: one aggregate map per level)
@@ -279,6 +290,9 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         int* tmp = nullptr;
         TRY(h->alloc(&tmp, (size_t)nc + 1 + scan_tmp_bytes(nc) / sizeof(int) + 16));
         TRY(build_members(L.n, nc, L.agg, L.agg_ptr, L.members, tmp, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        h->t_phase[1] += ms_since(tp);
+        tp = Clock::now();
         // Galerkin product
         Level& C = h->lev[l + 1];
         C.n = nc;
@@ -307,6 +321,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(tmp_cols);
         h->release(scan2);
         h->nlev++;
+        h->t_phase[2] += ms_since(tp);
+        tp = Clock::now();
     }
     // smoother data on every level but the coarsest
     for (int l = 0; l + 1 < h->nlev; ++l) {
@@ -329,6 +345,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->release(tmp);
         if (L.colour_ptr[L.n_colours] != L.n) return BAMG_ECUDA;
+        h->t_phase[3] += ms_since(tp);
+        tp = Clock::now();
         TRY(h->alloc(&L.dinv64, (size_t)L.n * h->F * h->fb * h->fb));
         TRY(block_inverses(b, h->fb, L.n, L.diag, L.vals64, L.dinv64, h->d_err, s));
         TRY(check_dev(h, s));
@@ -338,6 +356,9 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
             TRY(launch_convert_d2f((long)L.nnzb * bb, L.vals64, L.vals32, s));
             TRY(launch_convert_d2f((long)L.n * h->F * h->fb * h->fb, L.dinv64, L.dinv32, s));
         }
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        h->t_phase[4] += ms_since(tp);
+        tp = Clock::now();
     }
     // coarsest level: dense FP64 LU and inverse
     {
@@ -351,6 +372,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(coarse_dense(b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, s));
         TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, h->d_err, s));
         TRY(check_dev(h, s));
+        h->t_phase[5] += ms_since(tp);
+        tp = Clock::now();
     }
     // work vectors in the cycle precision
     const size_t es = h->p.cycle_prec == 32 ? sizeof(float) : sizeof(double);
@@ -377,6 +400,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&h->z32, N));
     }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->t_phase[6] += ms_since(tp);
     return BAMG_OK;
 }
 
@@ -450,8 +474,11 @@ template <>
 const float* level_dinv<float>(const Level& L) { return L.dinv32; }
 
 // one field step of Algorithm 1 on level l: x_out = x_in updated in field f
+// uc != nullptr: the coarse correction P uc is added to x_in on the fly (x_in is
+// then the state before prolongation and x_out receives the corrected values)
 template <typename T>
-static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x_out, cudaStream_t s) {
+static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x_out, const T* uc,
+                    cudaStream_t s) {
     const Level& L = h->lev[l];
     for (int c = 0; c < L.n_colours; ++c) {
         BgsArgs a;
@@ -467,6 +494,8 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.x_in = x_in;
         a.x_out = x_out;
         a.xt = L.xt;
+        a.uc = uc;
+        a.agg = uc ? L.agg : nullptr;
         a.field = f;
         a.F = h->F;
         a.omega = h->p.omega;
@@ -475,7 +504,8 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
             const double es = sizeof(T), B = h->b, FB = h->fb, nc = a.n_in_colour;
             const double nnz = (double)L.colour_nnz[c], low = (double)L.colour_nnz_lower[c];
             bytes = nnz * (FB * B * es + 4.0) + nc * 8.0 + nc * FB * FB * es + nc * FB * es +
-                    (x_in ? nc * B * es : 0.0) + nc * B * es + nc * FB * es + (c > 0 ? nc * FB * es : 0.0);
+                    (x_in ? nc * B * es : 0.0) + nc * B * es + nc * FB * es + (c > 0 ? nc * FB * es : 0.0) +
+                    (uc ? nc * (B * es + 4.0) : 0.0);
             flops = 2.0 * ((x_in ? nnz * FB * B : 0.0) + low * FB * FB + nc * FB * FB);
         }
         PL(BAMG_K_SMOOTH, bytes, flops, launch_bgs_colour<T>(h->b, h->fb, a, s));
@@ -500,7 +530,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const int S_pre = h->p.n_pre * h->F;
     for (int t = 0; t < S_pre; ++t) {
         T* dst = (cur == xa) ? xb : xa;
-        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, s));
+        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, nullptr, s));
         cur = dst;
     }
     if (!cur) {
@@ -515,14 +545,16 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     PL(BAMG_K_RESTRICT, L.n * 4.0 + (C.n + 1) * 4.0 + nb * es + ncb * es, nb,
        launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
-    PL(BAMG_K_PROLONG, L.n * 4.0 + 2.0 * nb * es + ncb * es, nb,
-       launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
     const int S_post = h->p.n_post * h->F;
-    if (S_post == 0)
+    if (S_post == 0) {
+        PL(BAMG_K_PROLONG, L.n * 4.0 + 2.0 * nb * es + ncb * es, nb,
+           launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
         BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
+    }
+    // the first post-smoothing step applies u <- u + P u_c on the fly
     for (int t = 0; t < S_post; ++t) {
         T* dst = (t == S_post - 1) ? out : ((cur == xa) ? xb : xa);
-        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, s));
+        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, t == 0 ? static_cast<const T*>(C.uc) : nullptr, s));
         cur = dst;
     }
     return BAMG_OK;
@@ -785,7 +817,14 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) + ",\"coarse_unknowns\":" +
-                    std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"levels\":[";
+                    std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
+    const char* names[7] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors"};
+    for (int q = 0; q < 7; ++q) {
+        char buf[64];
+        snprintf(buf, sizeof buf, "%s\"%s\":%.4f", q ? "," : "", names[q], h->t_phase[q]);
+        o += buf;
+    }
+    o += "},\"levels\":[";
     for (int l = 0; l < h->nlev; ++l) {
         const Level& L = h->lev[l];
         if (l) o += ",";

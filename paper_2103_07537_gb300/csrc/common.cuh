@@ -118,6 +118,8 @@ struct BgsArgs {
     const void* x_in;    // nullptr = zero vector
     void* x_out;
     void* xt;            // [n][fb]
+    const void* uc;      // optional: coarse correction added to x_in on the fly (x_in + P uc)
+    const int* agg;      // aggregate of every node (with uc)
     int field;
     int F;
     double omega;

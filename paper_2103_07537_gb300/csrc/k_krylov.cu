@@ -13,10 +13,12 @@
 namespace bamg {
 
 constexpr int kKThreads = 256;
-constexpr int kDotGroup = 8;  // dot products accumulated together per pass
+constexpr int kDotGroup = 16;  // dot products accumulated together per pass
 
+// fixed chunking of a vector of length N: up to two CTAs per SM of the GB300
+// (152 SMs), at least 256 elements per chunk
 int krylov_chunks(long N) {
-    long c = (N + 4095) / 4096;
+    long c = (N + 255) / 256;
     if (c > 2 * 152) c = 2 * 152;
     return (int)(c < 1 ? 1 : c);
 }

@@ -4,38 +4,68 @@
 // Gauss-Seidel smoother of Algorithm 1 (Sec. 4.3.2), the dense coarsest
 // solve, and precision casts at the cycle boundary.
 //
-// Thread mapping.  Every scalar row (node i, dof r) of a b x b block row is
-// one thread; the b threads of a block row are consecutive, so one load
-// instruction of a warp reads whole contiguous blocks (every 32-byte sector
-// of A that is touched is fully used).  Values are loaded with the widest
-// aligned vector type for the block size.
+// Thread mapping.  One warp per block row (node): its lanes cover (block,
+// scalar row) pairs of the row, so one load instruction of a warp reads a
+// contiguous run of the row's blocks, and values are loaded with the widest
+// aligned vector type for the block size.  Short rows (9 blocks in 2D) are
+// covered in one or two passes, which keeps the dependent-load chain of a
+// warp short: these kernels are latency bound on L2-resident levels.
 #include "common.cuh"
 
 namespace bamg {
 
 // ---------------------------------------------------------------------------
-// y = A x, or y = rhs - A x
+// Row reductions.  One warp owns one block row; lane = kk * R + r handles
+// row r (r < R) of block kk + pass * G (G = 32 / R blocks per pass), so the
+// lanes of a pass read consecutive rows of consecutive blocks (contiguous
+// memory).  The partial sums of the lanes with the same r are then added by
+// a shuffle tree whose offsets are multiples of R.
+// ---------------------------------------------------------------------------
+// largest R * 2^p below the warp size: the first offset of the shuffle tree
+template <int R>
+struct RowTree {
+    static constexpr int kStart = (R * 16 < kWarp) ? R * 16 : (R * 8 < kWarp) ? R * 8 : (R * 4 < kWarp) ? R * 4
+                                  : (R * 2 < kWarp) ? R * 2 : R;
+};
+
+template <typename T, int R>
+__device__ __forceinline__ T reduce_rows(T v, int lane) {
+#pragma unroll
+    for (int off = RowTree<R>::kStart; off >= R; off >>= 1) {
+        const T o = __shfl_down_sync(0xffffffffu, v, off);
+        if (lane + off < kWarp) v += o;
+    }
+    return v;  // lanes 0..R-1 hold the row sums
+}
+
+// ---------------------------------------------------------------------------
+// y = A x, or y = rhs - A x: one warp per block row
 // ---------------------------------------------------------------------------
 template <typename T, int B>
 __global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict__ rp,
                                                    const int* __restrict__ ci,
                                                    const T* __restrict__ vals, const T* __restrict__ x,
                                                    const T* __restrict__ rhs, T* __restrict__ y) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / B);
-    const int r = (int)(t - (long)i * B);
-    if (i >= n) return;
+    constexpr int G = kWarp / B;
+    const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // uniform per warp
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int kk = lane / B;
+    const int r = lane - kk * B;
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
     T acc = T(0);
-    for (int k = k0; k < k1; ++k) {
-        const int j = __ldg(ci + k);
-        T a[B], xv[B];
-        load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
-        load_row<T, B>(x + (size_t)j * B, xv);
+    if (kk < G) {
+        for (int k = k0 + kk; k < k1; k += G) {
+            const int j = __ldg(ci + k);
+            T a[B], xv[B];
+            load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
+            load_row<T, B>(x + (size_t)j * B, xv);
 #pragma unroll
-        for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+            for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+        }
     }
-    y[(size_t)i * B + r] = rhs ? rhs[(size_t)i * B + r] - acc : acc;
+    acc = reduce_rows<T, B>(acc, lane);
+    if (lane < B) y[(size_t)i * B + lane] = rhs ? rhs[(size_t)i * B + lane] - acc : acc;
 }
 
 template <typename T>
@@ -43,7 +73,7 @@ int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const
                 T* y, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
     const int threads = 256;
-    const int blocks = ceil_div((long)n * b, threads);
+    const int blocks = ceil_div((long)n * kWarp, threads);
     switch (b) {
 #define CASE(BB) \
     case BB: spmv_kernel<T, BB><<<blocks, threads, 0, s>>>(n, rp, ci, vals, x, rhs, y); break;
@@ -126,58 +156,76 @@ template int launch_prolong<float>(int, int, const int*, const float*, float*, c
 // ---------------------------------------------------------------------------
 template <typename T, int B, int FB>
 __global__ void __launch_bounds__(256) bgs_colour_kernel(BgsArgs a) {
-    constexpr int G = kWarp / FB;  // nodes per warp
+    constexpr int G = kWarp / FB;  // blocks of the row per pass
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= a.n_in_colour) return;  // uniform per warp
     const int lane = threadIdx.x & (kWarp - 1);
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int g = lane / FB;
-    const int r = lane - g * FB;
-    const long q = warp * G + g;
-    const bool active = (g < G) && (q < a.n_in_colour);
+    const int kk = lane / FB;
+    const int r = lane - kk * FB;
     const int f0 = a.field * FB;
     const T* __restrict__ vals = static_cast<const T*>(a.vals);
     const T* __restrict__ x_in = static_cast<const T*>(a.x_in);
-    const T* __restrict__ rhs = static_cast<const T*>(a.rhs);
-    T* __restrict__ xt = static_cast<T*>(a.xt);
+    const T* __restrict__ uc = static_cast<const T*>(a.uc);
+    const T* __restrict__ xt = static_cast<const T*>(a.xt);
+    const int i = __ldg(a.nodes + q);
+    const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+    // the fb x fb inverse row of this lane (lanes r < FB), loaded early
+    T drow[FB];
+    if (lane < FB) {
+        const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)lane * FB;
+#pragma unroll
+        for (int c = 0; c < FB; ++c) drow[c] = D[c];
+    }
     T acc = T(0);
-    int i = 0;
-    if (active) {
-        i = __ldg(a.nodes + q);
-        acc = rhs[(size_t)i * B + f0 + r];
-        const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
-        for (int k = k0; k < k1; ++k) {
+    if (kk < G) {
+        for (int k = k0 + kk; k < k1; k += G) {
             const int j = __ldg(a.ci + k);
             T arow[B];
             load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
             if (x_in) {
                 T xv[B];
                 load_row<T, B>(x_in + (size_t)j * B, xv);
+                if (uc) {  // prolongation fused in: x = x_in + P uc
+                    T pv[B];
+                    load_row<T, B>(uc + (size_t)__ldg(a.agg + j) * B, pv);
 #pragma unroll
-                for (int c = 0; c < B; ++c) acc = fma(-arow[c], xv[c], acc);
+                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
             }
             if (j != i && __ldg(a.colours + j) < a.colour) {
                 const T* tv = xt + (size_t)j * FB;
+                // field-f columns of the row with compile-time register indices
 #pragma unroll
-                for (int c = 0; c < FB; ++c) acc = fma(-arow[f0 + c], tv[c], acc);
+                for (int ff = 0; ff < B / FB; ++ff)
+                    if (ff == a.field) {
+#pragma unroll
+                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
+                    }
             }
         }
     }
-    T t[FB];
-#pragma unroll
-    for (int c = 0; c < FB; ++c) t[c] = __shfl_sync(0xffffffffu, acc, (g * FB + c) & (kWarp - 1));
-    if (!active) return;
-    const T* __restrict__ D =
-        static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)r * FB;
+    acc = reduce_rows<T, FB>(acc, lane);
+    // lanes 0..FB-1: the row sums of A_{f,*} x + A_ff x~ for this node
+    T t = T(0);
+    if (lane < FB) t = static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + lane] - acc;
     T xn = T(0);
 #pragma unroll
-    for (int c = 0; c < FB; ++c) xn = fma(D[c], t[c], xn);
-    xt[(size_t)i * FB + r] = xn;
-    T* __restrict__ x_out = static_cast<T*>(a.x_out);
-    const T om = T(a.omega);
-    for (int m = 0; m < a.F; ++m) {
-        const size_t e = (size_t)i * B + m * FB + r;
+    for (int c = 0; c < FB; ++c) {
+        const T tc = __shfl_sync(0xffffffffu, t, c);
+        if (lane < FB) xn = fma(drow[c], tc, xn);
+    }
+    if (lane < FB) static_cast<T*>(a.xt)[(size_t)i * FB + lane] = xn;
+    // x_out for node i: every component copied (with the prolongation when
+    // fused), field f corrected by omega x~
+    const T xf = __shfl_sync(0xffffffffu, xn, (lane - f0) & (kWarp - 1));
+    if (lane < B) {
+        const size_t e = (size_t)i * B + lane;
         T v = x_in ? x_in[e] : T(0);
-        if (m == a.field) v = fma(om, xn, v);
-        x_out[e] = v;
+        if (x_in && uc) v += uc[(size_t)__ldg(a.agg + i) * B + lane];
+        if (lane >= f0 && lane < f0 + FB) v = fma(T(a.omega), xf, v);
+        static_cast<T*>(a.x_out)[e] = v;
     }
 }
 
@@ -185,9 +233,7 @@ template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
     if (a.n_in_colour <= 0) return BAMG_OK;
     const int threads = 256;
-    const int G = kWarp / fb;
-    const long warps = (a.n_in_colour + G - 1) / G;
-    const int blocks = ceil_div(warps * kWarp, threads);
+    const int blocks = ceil_div((long)a.n_in_colour * kWarp, threads);
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF: bgs_colour_kernel<T, BB, FF><<<blocks, threads, 0, s>>>(a); break;
