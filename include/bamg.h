@@ -63,6 +63,9 @@ typedef struct {
     int cycle_prec;   /* 64: the V-cycle in FP64; 32: FP32 storage and arithmetic inside the
                          cycle (the outer FGMRES, its SpMV and the coarsest solve stay FP64)   */
     int use_graph;    /* 1: replay the V-cycle from a captured CUDA graph; default 1           */
+    int tail_dofs;    /* levels whose n_nodes*b is at most this (and every level below them) run
+                         as one thread-block-cluster launch per V-cycle; 0 = one launch per
+                         step on every level; default 65536                                    */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64). */
@@ -172,7 +175,8 @@ int amg_stats(bamg_t h, char* json, int cap);
 #define BAMG_K_SPMV 5     /* FP64 SpMV / residual of the outer Krylov method  */
 #define BAMG_K_KRYLOV 6   /* Gram-Schmidt, norms, rotations, updates          */
 #define BAMG_K_CAST 7
-#define BAMG_K_COUNT 8
+#define BAMG_K_TAIL 8     /* the cluster launch that runs the coarse levels of one V-cycle */
+#define BAMG_K_COUNT 9
 int amg_profile(bamg_t h, int enable);
 int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes, double* flops);
 

@@ -27,7 +27,7 @@ EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_
            "amg_profile", "amg_profile_read", "amg_launch_count"]
 
 #: kernel kinds of amg_profile_read
-KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast"]
+KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast", "tail"]
 
 _lock = threading.Lock()
 _lib = None
@@ -35,7 +35,7 @@ _lib = None
 
 class AmgParams(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
-                ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int)]
+                ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int), ("tail_dofs", C.c_int)]
 
 
 class BamgError(RuntimeError):

@@ -95,6 +95,14 @@ struct bamg_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_kernels = 0;
+    // cluster tail (every level from l_tail down in one launch)
+    int l_tail = -1, n_tail = 0, tail_cluster = 0;
+    TailPhase* tail_d = nullptr;
+    const void* tail_rhs = nullptr;
+    const void* tail_out = nullptr;
+    double tail_bytes = 0.0, tail_flops = 0.0;
+    std::vector<TailPhase>* rec = nullptr;  // set while the tail phases are recorded
+    double rec_bytes = 0.0, rec_flops = 0.0;
     // profiling
     int prof = 0;
     std::vector<ProfRec> recs;
@@ -204,6 +212,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->omega = 0.5;
     p->cycle_prec = 64;
     p->use_graph = 1;
+    p->tail_dofs = 65536;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -224,6 +233,9 @@ extern "C" const char* amg_strerror(int status) {
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
+static int setup_tail(bamg_ctx* h, cudaStream_t s);
+static int record_tail(bamg_ctx* h, cudaStream_t s, bool only_counts);
+
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
@@ -400,6 +412,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&h->z32, N));
     }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    TRY(setup_tail(h, s));
     h->t_phase[6] += ms_since(tp);
     return BAMG_OK;
 }
@@ -414,7 +427,7 @@ extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* v
     if (p) prm = *p;
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
-        !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64))
+        !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0)
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -473,6 +486,14 @@ const double* level_dinv<double>(const Level& L) { return L.dinv64; }
 template <>
 const float* level_dinv<float>(const Level& L) { return L.dinv32; }
 
+// A V-cycle step is launched now or, while h->rec is set, appended to the
+// phase list of the cluster tail kernel (with its algorithmic bytes / flops).
+static void record(bamg_ctx* h, const TailPhase& ph, double bytes, double flops) {
+    h->rec->push_back(ph);
+    h->rec_bytes += bytes;
+    h->rec_flops += flops;
+}
+
 // one field step of Algorithm 1 on level l: x_out = x_in updated in field f
 // uc != nullptr: the coarse correction P uc is added to x_in on the fly (x_in is
 // then the state before prolongation and x_out receives the corrected values)
@@ -480,6 +501,7 @@ template <typename T>
 static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x_out, const T* uc,
                     cudaStream_t s) {
     const Level& L = h->lev[l];
+    const bool have_counts = (int)L.colour_nnz.size() == L.n_colours;
     for (int c = 0; c < L.n_colours; ++c) {
         BgsArgs a;
         a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
@@ -500,13 +522,21 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.F = h->F;
         a.omega = h->p.omega;
         double bytes = 0.0, flops = 0.0;
-        if (h->prof) {
+        if (h->prof && have_counts) {
             const double es = sizeof(T), B = h->b, FB = h->fb, nc = a.n_in_colour;
             const double nnz = (double)L.colour_nnz[c], low = (double)L.colour_nnz_lower[c];
             bytes = nnz * (FB * B * es + 4.0) + nc * 8.0 + nc * FB * FB * es + nc * FB * es +
                     (x_in ? nc * B * es : 0.0) + nc * B * es + nc * FB * es + (c > 0 ? nc * FB * es : 0.0) +
                     (uc ? nc * (B * es + 4.0) : 0.0);
             flops = 2.0 * ((x_in ? nnz * FB * B : 0.0) + low * FB * FB + nc * FB * FB);
+        }
+        if (h->rec) {
+            TailPhase ph{};
+            ph.type = kPhaseBgs;
+            ph.n = a.n_in_colour;
+            ph.bgs = a;
+            record(h, ph, bytes, flops);
+            continue;
         }
         PL(BAMG_K_SMOOTH, bytes, flops, launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
@@ -518,10 +548,26 @@ template <typename T>
 static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const Level& L = h->lev[l];
     const int b = h->b;
+    if (!h->rec && l == h->l_tail && h->tail_d && rhs == h->tail_rhs && out == h->tail_out) {
+        // every level from l down runs as one cluster launch of the recorded phases
+        PL(BAMG_K_TAIL, h->tail_bytes, h->tail_flops,
+           launch_tail<T>(b, h->fb, h->tail_d, h->n_tail, h->tail_cluster, s));
+        return BAMG_OK;
+    }
     if (l == h->nlev - 1) {
         const double nd = h->nd;
-        PL(BAMG_K_COARSE, nd * nd * 8.0 + 2.0 * nd * sizeof(T), 2.0 * nd * nd,
-           launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s));
+        const double bytes = nd * nd * 8.0 + 2.0 * nd * sizeof(T), flops = 2.0 * nd * nd;
+        if (h->rec) {
+            TailPhase ph{};
+            ph.type = kPhaseGemv;
+            ph.n = h->nd;
+            ph.vals = h->coarse_inv;
+            ph.x = rhs;
+            ph.y = out;
+            record(h, ph, bytes, flops);
+            return BAMG_OK;
+        }
+        PL(BAMG_K_COARSE, bytes, flops, launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s));
         return BAMG_OK;
     }
     T* xa = static_cast<T*>(L.xa);
@@ -534,22 +580,65 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         cur = dst;
     }
     if (!cur) {
-        BAMG_CUDA_TRY(cudaMemsetAsync(xa, 0, sizeof(T) * (size_t)L.n * b, s));
+        if (h->rec) {
+            TailPhase ph{};
+            ph.type = kPhaseZero;
+            ph.n = L.n;
+            ph.y = xa;
+            record(h, ph, (double)L.n * b * sizeof(T), 0.0);
+        } else {
+            BAMG_CUDA_TRY(cudaMemsetAsync(xa, 0, sizeof(T) * (size_t)L.n * b, s));
+        }
         cur = xa;
     }
     const Level& C = h->lev[l + 1];
     T* res = static_cast<T*>(L.res);
     const double es = sizeof(T), nb = (double)L.n * b, ncb = (double)C.n * b;
-    PL(BAMG_K_RESIDUAL, (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es,
-       2.0 * L.nnzb * b * b, launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
-    PL(BAMG_K_RESTRICT, L.n * 4.0 + (C.n + 1) * 4.0 + nb * es + ncb * es, nb,
-       launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
+    const double res_bytes = (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es;
+    const double res_flops = 2.0 * L.nnzb * b * b;
+    const double rst_bytes = L.n * 4.0 + (C.n + 1) * 4.0 + nb * es + ncb * es;
+    if (h->rec) {
+        TailPhase ph{};
+        ph.type = kPhaseResidual;
+        ph.n = L.n;
+        ph.rp = L.rp;
+        ph.ci = L.ci;
+        ph.vals = level_vals<T>(L);
+        ph.x = cur;
+        ph.rhs = rhs;
+        ph.y = res;
+        record(h, ph, res_bytes, res_flops);
+        TailPhase pr{};
+        pr.type = kPhaseRestrict;
+        pr.n = L.n_agg;
+        pr.rp = L.agg_ptr;
+        pr.ci = L.members;
+        pr.x = res;
+        pr.y = C.rhs;
+        record(h, pr, rst_bytes, nb);
+    } else {
+        PL(BAMG_K_RESIDUAL, res_bytes, res_flops,
+           launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+        PL(BAMG_K_RESTRICT, rst_bytes, nb,
+           launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
+    }
     TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
     const int S_post = h->p.n_post * h->F;
     if (S_post == 0) {
-        PL(BAMG_K_PROLONG, L.n * 4.0 + 2.0 * nb * es + ncb * es, nb,
-           launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
-        BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
+        const double pb = L.n * 4.0 + 2.0 * nb * es + ncb * es;
+        if (h->rec) {
+            TailPhase ph{};
+            ph.type = kPhaseProlongCopy;
+            ph.n = L.n;
+            ph.x = cur;
+            ph.rhs = C.uc;
+            ph.ci = L.agg;
+            ph.y = out;
+            record(h, ph, pb, nb);
+        } else {
+            PL(BAMG_K_PROLONG, pb, nb, launch_prolong<T>(b, L.n, L.agg, static_cast<const T*>(C.uc), cur, s));
+            BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
+        }
     }
     // the first post-smoothing step applies u <- u + P u_c on the fly
     for (int t = 0; t < S_post; ++t) {
@@ -563,11 +652,71 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
 // z = M r on the finest level (r, z FP64, distinct)
 static int cycle_direct(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
     const long N = (long)h->lev[0].n * h->b;
-    if (h->p.cycle_prec == 64) return mgv<double>(h, 0, r, z, s);
+    if (h->p.cycle_prec == 64) {
+        if (h->tail_d && h->l_tail == 0 && (r != h->cyc_in || z != h->cyc_out)) {
+            // the recorded single-launch cycle reads and writes the staging vectors
+            BAMG_CUDA_TRY(cudaMemcpyAsync(h->cyc_in, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            TRY(mgv<double>(h, 0, h->cyc_in, h->cyc_out, s));
+            BAMG_CUDA_TRY(cudaMemcpyAsync(z, h->cyc_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            return BAMG_OK;
+        }
+        return mgv<double>(h, 0, r, z, s);
+    }
     PL(BAMG_K_CAST, N * 12.0, 0.0, launch_cast_d2f(N, r, h->r32, s));
     TRY(mgv<float>(h, 0, h->r32, h->z32, s));
     PL(BAMG_K_CAST, N * 12.0, 0.0, launch_cast_f2d(N, h->z32, z, s));
     return BAMG_OK;
+}
+
+// Record the phases of every level from l_tail down (device copy in tail_d).
+// With only_counts the phases are recorded to refresh the byte / flop totals.
+static int record_tail(bamg_ctx* h, cudaStream_t s, bool only_counts) {
+    std::vector<TailPhase> phases;
+    h->rec = &phases;
+    h->rec_bytes = h->rec_flops = 0.0;
+    const int lt = h->l_tail;
+    int st;
+    if (h->p.cycle_prec == 64) {
+        const double* rhs = lt == 0 ? h->cyc_in : static_cast<const double*>(h->lev[lt].rhs);
+        double* out = lt == 0 ? h->cyc_out : static_cast<double*>(h->lev[lt].uc);
+        h->tail_rhs = rhs;
+        h->tail_out = out;
+        st = mgv<double>(h, lt, rhs, out, s);
+    } else {
+        const float* rhs = lt == 0 ? h->r32 : static_cast<const float*>(h->lev[lt].rhs);
+        float* out = lt == 0 ? h->z32 : static_cast<float*>(h->lev[lt].uc);
+        h->tail_rhs = rhs;
+        h->tail_out = out;
+        st = mgv<float>(h, lt, rhs, out, s);
+    }
+    h->rec = nullptr;
+    if (st != BAMG_OK) return st;
+    h->tail_bytes = h->rec_bytes;
+    h->tail_flops = h->rec_flops;
+    if (only_counts) return BAMG_OK;
+    TailPhase* d = nullptr;
+    TRY(h->alloc(&d, phases.size()));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(d, phases.data(), sizeof(TailPhase) * phases.size(), cudaMemcpyHostToDevice, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->n_tail = (int)phases.size();
+    h->tail_d = d;
+    return BAMG_OK;
+}
+
+// choose the first level of the cluster tail and record its phases
+static int setup_tail(bamg_ctx* h, cudaStream_t s) {
+    h->tail_d = nullptr;
+    h->l_tail = -1;
+    if (h->p.tail_dofs <= 0 || h->nlev < 2) return BAMG_OK;
+    int lt = h->nlev - 1;
+    while (lt > 0 && (long)h->lev[lt - 1].n * h->b <= h->p.tail_dofs) --lt;
+    if (lt >= h->nlev - 1) return BAMG_OK;  // only the coarsest solve would remain: no gain
+    const int cl = h->p.cycle_prec == 64 ? tail_cluster_size<double>(h->b, h->fb, 16)
+                                         : tail_cluster_size<float>(h->b, h->fb, 16);
+    if (cl < 1) return BAMG_OK;
+    h->tail_cluster = cl;
+    h->l_tail = lt;
+    return record_tail(h, s, false);
 }
 
 static int ensure_graph(bamg_ctx* h) {
@@ -824,7 +973,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
         snprintf(buf, sizeof buf, "%s\"%s\":%.4f", q ? "," : "", names[q], h->t_phase[q]);
         o += buf;
     }
-    o += "},\"levels\":[";
+    o += "},\"tail_level\":" + std::to_string(h->l_tail) + ",\"tail_phases\":" + std::to_string(h->n_tail) +
+         ",\"tail_cluster\":" + std::to_string(h->tail_cluster) + ",\"levels\":[";
     for (int l = 0; l < h->nlev; ++l) {
         const Level& L = h->lev[l];
         if (l) o += ",";
@@ -864,6 +1014,7 @@ extern "C" int amg_profile(bamg_t h, int enable) {
         }
     }
     h->prof = enable ? 1 : 0;
+    if (enable && h->tail_d) TRY(record_tail(h, nullptr, true));
     return BAMG_OK;
 }
 

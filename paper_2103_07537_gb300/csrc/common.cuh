@@ -126,6 +126,34 @@ struct BgsArgs {
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+
+// One recorded step of the V-cycle below the tail level, executed by the
+// cluster tail kernel (see k_solve.cu).
+enum PhaseType : int {
+    kPhaseBgs = 0,       // one colour of one field step: bgs
+    kPhaseResidual = 1,  // y = rhs - A x: rp, ci, vals, x, rhs, y, n rows
+    kPhaseRestrict = 2,  // y = R x: rp = agg_ptr, ci = members, x, y, n coarse nodes
+    kPhaseGemv = 3,      // y = Ainv x: vals = FP64 inverse, x, y, n = nd
+    kPhaseProlongCopy = 4,  // y = x + P rhs: ci = agg, n fine nodes
+    kPhaseZero = 5,      // y = 0 over n nodes
+};
+struct TailPhase {
+    int type;
+    int n;
+    BgsArgs bgs;
+    const int* rp;
+    const int* ci;
+    const void* vals;
+    const void* x;
+    const void* rhs;
+    void* y;
+};
+constexpr int kTailThreads = 512;
+template <typename T>
+int launch_tail(int b, int fb, const TailPhase* phases, int nphase, int cluster, cudaStream_t s);
+// largest resident cluster size <= want for the tail kernel (0: none)
+template <typename T>
+int tail_cluster_size(int b, int fb, int want);
 // y = Ainv x for the dense FP64 nd x nd inverse (x, y of type T)
 template <typename T>
 int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s);

@@ -2,7 +2,8 @@
 // blocks: block-CSR SpMV / residual, restriction and prolongation with the
 // piecewise-constant transfers of Sec. 4.3.1, one colour of the block
 // Gauss-Seidel smoother of Algorithm 1 (Sec. 4.3.2), the dense coarsest
-// solve, and precision casts at the cycle boundary.
+// solve, precision casts at the cycle boundary, and the cluster "tail"
+// kernel that runs every step of the cycle below a given level in one launch.
 //
 // Thread mapping.  One warp per block row (node): its lanes cover (block,
 // scalar row) pairs of the row, so one load instruction of a warp reads a
@@ -10,9 +11,57 @@
 // aligned vector type for the block size.  Short rows (9 blocks in 2D) are
 // covered in one or two passes, which keeps the dependent-load chain of a
 // warp short: these kernels are latency bound on L2-resident levels.
+//
+// The warp-level bodies are device functions shared by the one-step kernels
+// and the tail kernel.  Their template flag CG selects L2-coherent loads
+// (ld.global.cg) for vectors that the same launch writes (the tail kernel);
+// matrix data is read through the read-only path in both.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace bamg {
+
+// ---------------------------------------------------------------------------
+// loads of B consecutive values of a vector (coherent variant for the tail)
+// ---------------------------------------------------------------------------
+template <typename T, int B, bool CG>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&out)[B]) {
+    if constexpr (!CG) {
+        load_row<T, B>(p, out);
+    } else {
+        constexpr int bytes_row = B * (int)sizeof(T);
+        if constexpr (sizeof(T) == 4 && bytes_row % 16 == 0) {
+#pragma unroll
+            for (int c = 0; c < B; c += 4) {
+                float4 v = __ldcg(reinterpret_cast<const float4*>(p + c));
+                out[c] = v.x;
+                out[c + 1] = v.y;
+                out[c + 2] = v.z;
+                out[c + 3] = v.w;
+            }
+        } else if constexpr (bytes_row % 16 == 0 || (sizeof(T) == 4 && bytes_row % 8 == 0)) {
+            using V2 = typename VecOf<T>::v2;
+#pragma unroll
+            for (int c = 0; c < B; c += 2) {
+                V2 v = __ldcg(reinterpret_cast<const V2*>(p + c));
+                out[c] = v.x;
+                out[c + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < B; ++c) out[c] = __ldcg(p + c);
+        }
+    }
+}
+
+template <typename T, bool CG>
+__device__ __forceinline__ T ld1(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
 
 // ---------------------------------------------------------------------------
 // Row reductions.  One warp owns one block row; lane = kk * R + r handles
@@ -38,18 +87,11 @@ __device__ __forceinline__ T reduce_rows(T v, int lane) {
     return v;  // lanes 0..R-1 hold the row sums
 }
 
-// ---------------------------------------------------------------------------
-// y = A x, or y = rhs - A x: one warp per block row
-// ---------------------------------------------------------------------------
-template <typename T, int B>
-__global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict__ rp,
-                                                   const int* __restrict__ ci,
-                                                   const T* __restrict__ vals, const T* __restrict__ x,
-                                                   const T* __restrict__ rhs, T* __restrict__ y) {
+// y_i = (rhs_i -) sum_j A_ij x_j for block row i; whole warp
+template <typename T, int B, bool CG>
+__device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict__ rp, const int* __restrict__ ci,
+                                         const T* __restrict__ vals, const T* x, const T* rhs, T* y) {
     constexpr int G = kWarp / B;
-    const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;  // uniform per warp
-    const int lane = threadIdx.x & (kWarp - 1);
     const int kk = lane / B;
     const int r = lane - kk * B;
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
@@ -59,13 +101,138 @@ __global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict_
             const int j = __ldg(ci + k);
             T a[B], xv[B];
             load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
-            load_row<T, B>(x + (size_t)j * B, xv);
+            load_vec<T, B, CG>(x + (size_t)j * B, xv);
 #pragma unroll
             for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
         }
     }
     acc = reduce_rows<T, B>(acc, lane);
-    if (lane < B) y[(size_t)i * B + lane] = rhs ? rhs[(size_t)i * B + lane] - acc : acc;
+    if (lane < B) y[(size_t)i * B + lane] = rhs ? ld1<T, CG>(rhs + (size_t)i * B + lane) - acc : acc;
+}
+
+// ---------------------------------------------------------------------------
+// One colour of one field step of the damped block Gauss-Seidel smoother
+// (Algorithm 1), one node per warp.  For field f the step computes
+//   r_f = rhs_f - A_{f,*} x                 (x = x_in, fixed for the whole step)
+//   x~  = one multicolour node-block GS sweep on A_ff r_f from x~ = 0:
+//         x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j)
+//   x_f = x_f + omega x~_f
+// The residual and the Gauss-Seidel sum read the same f-rows of each block,
+// so they are fused into one pass: node i of colour c accumulates
+//   rhs_f,i - sum_j A_{f,*}[i,j] x_in,j - sum_{j: colour(j) < c} A_ff[i,j] x~_j
+// (neighbours of later colours still have x~ = 0, neighbours of the same
+// colour do not exist).  x_in is never written during the step; node i writes
+// its updated values to x_out (all b components: field f corrected, the
+// others copied), so the field update of Algorithm 1 needs no extra pass.
+// With uc set, x_in + P uc (the coarse correction) is read in place of x_in.
+// ---------------------------------------------------------------------------
+template <typename T, int B, int FB, bool CG>
+__device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
+    constexpr int G = kWarp / FB;  // blocks of the row per pass
+    const int kk = lane / FB;
+    const int r = lane - kk * FB;
+    const int f0 = a.field * FB;
+    const T* __restrict__ vals = static_cast<const T*>(a.vals);
+    const T* x_in = static_cast<const T*>(a.x_in);
+    const T* uc = static_cast<const T*>(a.uc);
+    const T* xt = static_cast<const T*>(a.xt);
+    const int i = __ldg(a.nodes + q);
+    const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+    // the fb x fb inverse row of this lane (lanes r < FB), loaded early
+    T drow[FB];
+    if (lane < FB) {
+        const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)lane * FB;
+#pragma unroll
+        for (int c = 0; c < FB; ++c) drow[c] = __ldg(D + c);
+    }
+    T acc = T(0);
+    if (kk < G) {
+        for (int k = k0 + kk; k < k1; k += G) {
+            const int j = __ldg(a.ci + k);
+            T arow[B];
+            load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+            if (x_in) {
+                T xv[B];
+                load_vec<T, B, CG>(x_in + (size_t)j * B, xv);
+                if (uc) {
+                    T pv[B];
+                    load_vec<T, B, CG>(uc + (size_t)__ldg(a.agg + j) * B, pv);
+#pragma unroll
+                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
+            }
+            if (j != i && __ldg(a.colours + j) < a.colour) {
+                const T* tv = xt + (size_t)j * FB;
+                // field-f columns of the row with compile-time register indices
+#pragma unroll
+                for (int ff = 0; ff < B / FB; ++ff)
+                    if (ff == a.field) {
+#pragma unroll
+                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], ld1<T, CG>(tv + c), acc);
+                    }
+            }
+        }
+    }
+    acc = reduce_rows<T, FB>(acc, lane);
+    // lanes 0..FB-1: the row sums of A_{f,*} x + A_ff x~ for this node
+    T t = T(0);
+    if (lane < FB) t = ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) - acc;
+    T xn = T(0);
+#pragma unroll
+    for (int c = 0; c < FB; ++c) {
+        const T tc = __shfl_sync(0xffffffffu, t, c);
+        if (lane < FB) xn = fma(drow[c], tc, xn);
+    }
+    if (lane < FB) static_cast<T*>(a.xt)[(size_t)i * FB + lane] = xn;
+    // x_out for node i: every component copied (with the prolongation when
+    // fused), field f corrected by omega x~
+    const T xf = __shfl_sync(0xffffffffu, xn, (lane - f0) & (kWarp - 1));
+    if (lane < B) {
+        const size_t e = (size_t)i * B + lane;
+        T v = x_in ? ld1<T, CG>(x_in + e) : T(0);
+        if (x_in && uc) v += ld1<T, CG>(uc + (size_t)__ldg(a.agg + i) * B + lane);
+        if (lane >= f0 && lane < f0 + FB) v = fma(T(a.omega), xf, v);
+        static_cast<T*>(a.x_out)[e] = v;
+    }
+}
+
+// coarsest level: y_row = sum_c Ainv[row][c] x_c in FP64; whole warp
+template <typename T, bool CG>
+__device__ __forceinline__ void gemv_row(int row, int lane, int nd, const double* __restrict__ ainv, const T* x,
+                                         T* y) {
+    const double* a = ainv + (size_t)row * nd;
+    double acc = 0.0;
+    for (int c = lane; c < nd; c += kWarp) acc = fma(__ldg(a + c), (double)ld1<T, CG>(x + c), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = (T)acc;
+}
+
+// restriction with R = P^T, P piecewise constant: rc[I,d] = sum_{m in I} res[m,d],
+// members ascending, so the sum order is fixed (deterministic)
+template <typename T, bool CG>
+__device__ __forceinline__ void restrict_dof(long t, int b, const int* __restrict__ agg_ptr,
+                                             const int* __restrict__ members, const T* res, T* rc) {
+    const int I = (int)(t / b);
+    const int d = (int)(t - (long)I * b);
+    T acc = T(0);
+    for (int q = __ldg(agg_ptr + I); q < __ldg(agg_ptr + I + 1); ++q)
+        acc += ld1<T, CG>(res + (size_t)__ldg(members + q) * b + d);
+    rc[(size_t)I * b + d] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// one-step kernels
+// ---------------------------------------------------------------------------
+template <typename T, int B>
+__global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict__ rp,
+                                                   const int* __restrict__ ci,
+                                                   const T* __restrict__ vals, const T* __restrict__ x,
+                                                   const T* __restrict__ rhs, T* __restrict__ y) {
+    const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // uniform per warp
+    spmv_row<T, B, false>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
 }
 
 template <typename T>
@@ -88,21 +255,11 @@ template int launch_spmv<double>(int, int, const int*, const int*, const double*
 template int launch_spmv<float>(int, int, const int*, const int*, const float*, const float*,
                                 const float*, float*, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// restriction with R = P^T, P piecewise constant: rc[I,d] = sum_{m in I} res[m,d]
-// members ascending, so the sum order is fixed (deterministic).
-// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void restrict_kernel(int b, int nc, const int* __restrict__ agg_ptr,
-                                const int* __restrict__ members, const T* __restrict__ res,
-                                T* __restrict__ rc) {
+__global__ void restrict_kernel(int b, int nc, const int* __restrict__ agg_ptr, const int* __restrict__ members,
+                                const T* __restrict__ res, T* __restrict__ rc) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int I = (int)(t / b);
-    const int d = (int)(t - (long)I * b);
-    if (I >= nc) return;
-    T acc = T(0);
-    for (int q = agg_ptr[I]; q < agg_ptr[I + 1]; ++q) acc += res[(size_t)members[q] * b + d];
-    rc[(size_t)I * b + d] = acc;
+    if (t < (long)nc * b) restrict_dof<T, false>(t, b, agg_ptr, members, res, rc);
 }
 
 template <typename T>
@@ -115,9 +272,7 @@ int launch_restrict(int b, int nc, const int* agg_ptr, const int* members, const
 template int launch_restrict<double>(int, int, const int*, const int*, const double*, double*, cudaStream_t);
 template int launch_restrict<float>(int, int, const int*, const int*, const float*, float*, cudaStream_t);
 
-// ---------------------------------------------------------------------------
 // prolongation and correction u += P uc, P piecewise constant per dof
-// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void prolong_kernel(int b, int n, const int* __restrict__ agg, const T* __restrict__ uc,
                                T* __restrict__ u) {
@@ -137,96 +292,11 @@ int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t
 template int launch_prolong<double>(int, int, const int*, const double*, double*, cudaStream_t);
 template int launch_prolong<float>(int, int, const int*, const float*, float*, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// One colour of one field step of the damped block Gauss-Seidel smoother
-// (Algorithm 1).  For field f the step computes
-//   r_f = rhs_f - A_{f,*} x                 (x = x_in, fixed for the whole step)
-//   x~  = one multicolour node-block GS sweep on A_ff r_f from x~ = 0:
-//         x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j)
-//   x_f = x_f + omega x~_f
-// The residual and the Gauss-Seidel sum read the same f-rows of each block,
-// so they are fused into one pass: node i of colour c accumulates
-//   rhs_f,i - sum_j A_{f,*}[i,j] x_in,j - sum_{j: colour(j) < c} A_ff[i,j] x~_j
-// (neighbours of later colours still have x~ = 0, neighbours of the same
-// colour do not exist).  x_in is never written during the step; node i writes
-// its updated values to x_out (all b components: field f corrected, the
-// others copied), so the fields' update of Algorithm 1 needs no extra pass.
-// The fb threads of node i sit in one warp and exchange their row sums by
-// shuffles for the fb x fb inverse.
-// ---------------------------------------------------------------------------
 template <typename T, int B, int FB>
 __global__ void __launch_bounds__(256) bgs_colour_kernel(BgsArgs a) {
-    constexpr int G = kWarp / FB;  // blocks of the row per pass
     const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_in_colour) return;  // uniform per warp
-    const int lane = threadIdx.x & (kWarp - 1);
-    const int kk = lane / FB;
-    const int r = lane - kk * FB;
-    const int f0 = a.field * FB;
-    const T* __restrict__ vals = static_cast<const T*>(a.vals);
-    const T* __restrict__ x_in = static_cast<const T*>(a.x_in);
-    const T* __restrict__ uc = static_cast<const T*>(a.uc);
-    const T* __restrict__ xt = static_cast<const T*>(a.xt);
-    const int i = __ldg(a.nodes + q);
-    const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
-    // the fb x fb inverse row of this lane (lanes r < FB), loaded early
-    T drow[FB];
-    if (lane < FB) {
-        const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)lane * FB;
-#pragma unroll
-        for (int c = 0; c < FB; ++c) drow[c] = D[c];
-    }
-    T acc = T(0);
-    if (kk < G) {
-        for (int k = k0 + kk; k < k1; k += G) {
-            const int j = __ldg(a.ci + k);
-            T arow[B];
-            load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
-            if (x_in) {
-                T xv[B];
-                load_row<T, B>(x_in + (size_t)j * B, xv);
-                if (uc) {  // prolongation fused in: x = x_in + P uc
-                    T pv[B];
-                    load_row<T, B>(uc + (size_t)__ldg(a.agg + j) * B, pv);
-#pragma unroll
-                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
-                }
-#pragma unroll
-                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
-            }
-            if (j != i && __ldg(a.colours + j) < a.colour) {
-                const T* tv = xt + (size_t)j * FB;
-                // field-f columns of the row with compile-time register indices
-#pragma unroll
-                for (int ff = 0; ff < B / FB; ++ff)
-                    if (ff == a.field) {
-#pragma unroll
-                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
-                    }
-            }
-        }
-    }
-    acc = reduce_rows<T, FB>(acc, lane);
-    // lanes 0..FB-1: the row sums of A_{f,*} x + A_ff x~ for this node
-    T t = T(0);
-    if (lane < FB) t = static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + lane] - acc;
-    T xn = T(0);
-#pragma unroll
-    for (int c = 0; c < FB; ++c) {
-        const T tc = __shfl_sync(0xffffffffu, t, c);
-        if (lane < FB) xn = fma(drow[c], tc, xn);
-    }
-    if (lane < FB) static_cast<T*>(a.xt)[(size_t)i * FB + lane] = xn;
-    // x_out for node i: every component copied (with the prolongation when
-    // fused), field f corrected by omega x~
-    const T xf = __shfl_sync(0xffffffffu, xn, (lane - f0) & (kWarp - 1));
-    if (lane < B) {
-        const size_t e = (size_t)i * B + lane;
-        T v = x_in ? x_in[e] : T(0);
-        if (x_in && uc) v += uc[(size_t)__ldg(a.agg + i) * B + lane];
-        if (lane >= f0 && lane < f0 + FB) v = fma(T(a.omega), xf, v);
-        static_cast<T*>(a.x_out)[e] = v;
-    }
+    bgs_node<T, B, FB, false>(a, q, threadIdx.x & (kWarp - 1));
 }
 
 template <typename T>
@@ -246,20 +316,12 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
 template int launch_bgs_colour<double>(int, int, const BgsArgs&, cudaStream_t);
 template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// coarsest level: y = A_L^{-1} x with the FP64 inverse, one warp per row
-// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void dense_gemv_kernel(int nd, const double* __restrict__ ainv, const T* __restrict__ x,
                                   T* __restrict__ y) {
     const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
     if (row >= nd) return;
-    const double* a = ainv + (size_t)row * nd;
-    double acc = 0.0;
-    for (int c = lane; c < nd; c += kWarp) acc = fma(a[c], (double)x[c], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) y[row] = (T)acc;
+    gemv_row<T, false>(row, threadIdx.x & 31, nd, ainv, x, y);
 }
 
 template <typename T>
@@ -270,6 +332,135 @@ int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t
 }
 template int launch_dense_gemv<double>(int, const double*, const double*, double*, cudaStream_t);
 template int launch_dense_gemv<float>(int, const double*, const float*, float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Tail kernel: one thread-block cluster executes a recorded list of V-cycle
+// phases (every colour of every field step, residuals, restrictions, the
+// coarsest solve and the post-smoothing with the fused prolongation) for the
+// levels below a given one.  Inside a phase the work items are spread over
+// all warps (or threads) of the cluster; between phases the cluster barrier
+// (barrier.cluster arrive.release / wait.acquire) orders the global-memory
+// writes of one phase before the reads of the next, and the reads of data
+// written inside the launch bypass L1 (ld.global.cg).  Every thread executes
+// every phase and every barrier (no early exit), so the hardware barrier
+// never waits for a thread that has left.
+// ---------------------------------------------------------------------------
+template <typename T, int B, int FB>
+__global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(const TailPhase* __restrict__ phases, int nphase) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warps_per_cta = blockDim.x >> 5;
+    const long gw = (long)cl.block_rank() * warps_per_cta + (threadIdx.x >> 5);
+    const long W = (long)cl.num_blocks() * warps_per_cta;
+    const long gt = (long)cl.block_rank() * blockDim.x + threadIdx.x;
+    const long NT = (long)cl.num_blocks() * blockDim.x;
+    for (int p = 0; p < nphase; ++p) {
+        const TailPhase& ph = phases[p];
+        switch (ph.type) {
+            case kPhaseBgs:
+                for (long q = gw; q < ph.n; q += W) bgs_node<T, B, FB, true>(ph.bgs, q, lane);
+                break;
+            case kPhaseResidual:
+                for (long i = gw; i < ph.n; i += W)
+                    spmv_row<T, B, true>(i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals),
+                                         static_cast<const T*>(ph.x), static_cast<const T*>(ph.rhs),
+                                         static_cast<T*>(ph.y));
+                break;
+            case kPhaseRestrict:
+                for (long t = gt; t < (long)ph.n * B; t += NT)
+                    restrict_dof<T, true>(t, B, ph.rp, ph.ci, static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+                break;
+            case kPhaseGemv:
+                for (long row = gw; row < ph.n; row += W)
+                    gemv_row<T, true>((int)row, lane, ph.n, static_cast<const double*>(ph.vals),
+                                      static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+                break;
+            case kPhaseProlongCopy:  // y = x + P uc over n fine nodes (x may equal y); uc in rhs, agg in ci
+                for (long e = gt; e < (long)ph.n * B; e += NT) {
+                    const int i = (int)(e / B), d = (int)(e - (long)i * B);
+                    static_cast<T*>(ph.y)[e] =
+                        ld1<T, true>(static_cast<const T*>(ph.x) + e) +
+                        ld1<T, true>(static_cast<const T*>(ph.rhs) + (size_t)__ldg(ph.ci + i) * B + d);
+                }
+                break;
+            case kPhaseZero:
+                for (long e = gt; e < (long)ph.n * B; e += NT) static_cast<T*>(ph.y)[e] = T(0);
+                break;
+            default:
+                break;
+        }
+        cl.sync();
+    }
+}
+
+static void fill_cluster_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, int cluster, cudaStream_t s) {
+    *cfg = cudaLaunchConfig_t{};
+    cfg->gridDim = dim3((unsigned)cluster, 1, 1);
+    cfg->blockDim = dim3(kTailThreads, 1, 1);
+    cfg->dynamicSmemBytes = 0;
+    cfg->stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg->attrs = attr;
+    cfg->numAttrs = 1;
+}
+
+template <typename T, int B, int FB>
+static int launch_tail_t(const TailPhase* phases, int nphase, int cluster, cudaStream_t s) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    fill_cluster_config(&cfg, attr, cluster, s);
+    BAMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail_kernel<T, B, FB>, phases, nphase));
+    return launched(1);
+}
+
+// largest cluster size <= want (a power of two) that can be resident
+template <typename T, int B, int FB>
+static int tail_cluster_size_t(int want) {
+    if (cudaFuncSetAttribute(tail_kernel<T, B, FB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        if (want > 8) want = 8;
+    }
+    for (int c = want; c >= 1; c >>= 1) {
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr[1];
+        fill_cluster_config(&cfg, attr, c, nullptr);
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, tail_kernel<T, B, FB>, &cfg) == cudaSuccess && clusters >= 1)
+            return c;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+template <typename T>
+int launch_tail(int b, int fb, const TailPhase* phases, int nphase, int cluster, cudaStream_t s) {
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF: return launch_tail_t<T, BB, FF>(phases, nphase, cluster, s);
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+}
+template int launch_tail<double>(int, int, const TailPhase*, int, int, cudaStream_t);
+template int launch_tail<float>(int, int, const TailPhase*, int, int, cudaStream_t);
+
+template <typename T>
+int tail_cluster_size(int b, int fb, int want) {
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF: return tail_cluster_size_t<T, BB, FF>(want);
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+#undef CASE
+        default: return 0;
+    }
+}
+template int tail_cluster_size<double>(int, int, int);
+template int tail_cluster_size<float>(int, int, int);
 
 // ---------------------------------------------------------------------------
 // precision casts at the cycle boundary (FP64 Krylov vectors <-> FP32 cycle)

@@ -119,10 +119,11 @@ def test_hierarchy_matches_oracle(name):
 # ---------------------------------------------------------------------------
 # V-cycle
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tail_dofs", [0, 65536])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_vcycle_fp64_matches_oracle(name):
+def test_vcycle_fp64_matches_oracle(name, tail_dofs):
     s, kw = SYSTEMS[name]()
-    g = make_solver(s, **kw)
+    g = make_solver(s, tail_dofs=tail_dofs, **kw)
     o = make_oracle(s, **kw)
     r = np.random.default_rng(7).standard_normal(s.n_unknowns)
     z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
@@ -144,6 +145,24 @@ def test_vcycle_variants_match_oracle(variant):
     g.apply(dev(r), z)
     torch.cuda.synchronize()
     assert rel_max(z.cpu().numpy(), o.vcycle(r)) <= VCYCLE_TOL
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", ["stokes2d_32", "mhd2d_41_ragged", "stokes3d_9", "poisson_b2"])
+def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
+    s, kw = SYSTEMS[name]()
+    with_tail = make_solver(s, tail_dofs=1 << 30, cycle_prec=prec, **kw)  # every level in the tail
+    some_tail = make_solver(s, tail_dofs=2000, cycle_prec=prec, **kw)
+    no_tail = make_solver(s, tail_dofs=0, cycle_prec=prec, **kw)
+    assert with_tail.stats()["tail_level"] == 0 and no_tail.stats()["tail_level"] == -1
+    r = dev(np.random.default_rng(3).standard_normal(s.n_unknowns))
+    outs = []
+    for g in (with_tail, some_tail, no_tail):
+        z = torch.empty_like(r)
+        g.apply(r, z)
+        outs.append(z)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2])
 
 
 def test_vcycle_graph_and_direct_launch_agree_bitwise_and_repeat():
