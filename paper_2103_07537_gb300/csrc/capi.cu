@@ -112,6 +112,7 @@ struct bamg_ctx {
     double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *h1 = nullptr, *h2 = nullptr,
            *wsq = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr,
            *scal = nullptr;
+    unsigned* ticket = nullptr;  // last-CTA counter of the chunked reductions
     double* h_scal = nullptr;  // pinned [4]
     // host wall time of the setup phases (ms): pattern, aggregate, rap, colour, inverse, coarse, vectors
     double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -763,7 +764,7 @@ static int ensure_krylov(bamg_ctx* h, int m) {
     if (h->m_alloc >= m) return BAMG_OK;
     for (void* q : {(void*)h->V, (void*)h->Z, (void*)h->w, (void*)h->partial, (void*)h->h1, (void*)h->h2,
                     (void*)h->wsq, (void*)h->H, (void*)h->cs, (void*)h->sn, (void*)h->g, (void*)h->y,
-                    (void*)h->scal})
+                    (void*)h->scal, (void*)h->ticket})
         if (q) h->release(q);
     const size_t N = (size_t)h->lev[0].n * h->b;
     const int nchunk = krylov_chunks((long)N);
@@ -780,14 +781,15 @@ static int ensure_krylov(bamg_ctx* h, int m) {
     TRY(h->alloc(&h->g, (size_t)m + 1));
     TRY(h->alloc(&h->y, (size_t)m));
     TRY(h->alloc(&h->scal, 4));
+    TRY(h->alloc(&h->ticket, 4));
+    BAMG_CUDA_TRY(cudaMemset(h->ticket, 0, 4 * sizeof(unsigned)));
     h->m_alloc = m;
     return BAMG_OK;
 }
 
 // ||x||^2 into dst (device), via the deterministic chunked reduction
 static int norm_sq(bamg_ctx* h, long N, const double* x, double* dst, cudaStream_t s) {
-    PL(BAMG_K_KRYLOV, N * 8.0, 2.0 * N, launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, s));
-    PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(1, N, h->partial, dst, s));
+    PL(BAMG_K_KRYLOV, N * 8.0, 2.0 * N, launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, dst, h->ticket, s));
     return BAMG_OK;
 }
 
@@ -842,17 +844,13 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
                launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
             // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
             const double nv = j + 1;
+            GivensArgs ga{j, m, h->h1, h->h2, h->H, h->cs, h->sn, h->g, h->scal};
             PL(BAMG_K_KRYLOV, (nv + 1) * vN, 2.0 * N * (nv + 1),
-               launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, s));
-            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(j + 2, N, h->partial, h->h1, s));
+               launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, h->h1, h->ticket, s));
             PL(BAMG_K_KRYLOV, (2 * nv + 2) * vN, 4.0 * N * nv,
-               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, s));
-            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(j + 1, N, h->partial, h->h2, s));
+               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, h->h2, h->ticket, nullptr, s));
             PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
-               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, s));
-            PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_finish(1, N, h->partial, h->wsq, s));
-            PL(BAMG_K_KRYLOV, 0.0, 0.0,
-               launch_givens(j, m, h->h1, h->h2, h->wsq, h->H, h->cs, h->sn, h->g, h->scal, s));
+               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, h->wsq, h->ticket, &ga, s));
             PL(BAMG_K_KRYLOV, 2.0 * vN, N, launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
             total++;
             k = j + 1;
@@ -863,7 +861,7 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
         }
         PL(BAMG_K_KRYLOV, 0.0, 0.0, launch_solve_upper(k, m, h->H, h->g, h->y, s));
         PL(BAMG_K_KRYLOV, (k + 2.0) * vN, 2.0 * N * k,
-           launch_axpy_dot(N, x, h->Z, N, k, h->y, -1.0, 0, nullptr, s));  // x += Z y
+           launch_axpy_dot(N, x, h->Z, N, k, h->y, -1.0, 0, nullptr, nullptr, h->ticket, nullptr, s));  // x += Z y
     }
     if (iters) *iters = total;
     if (relres) *relres = rel;

@@ -204,16 +204,24 @@ int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);
 
 // ---- Krylov kernels (k_krylov.cu) ----
 int krylov_chunks(long N);
-// partial[v*nchunk + c] = chunk c of x . Y_v (v < nv); if want_xx also x . x at v = nv
-int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx,
-                     double* partial, cudaStream_t s);
-// x -= sign * sum_v h[v] Y_v; then mode 1: dots with Y_v, mode 2: x . x, mode 0: none
-int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign,
-                    int mode, double* partial, cudaStream_t s);
-// out[v] = sum of the chunk partials of v (v < nv)
-int launch_finish(int nv, long N, const double* partial, double* out, cudaStream_t s);
-int launch_givens(int j, int m, const double* h1, const double* h2, const double* wsq, double* H, double* cs,
-                  double* sn, double* g, double* scal, cudaStream_t s);
+// device pointers of the Arnoldi bookkeeping for step j of FGMRES(m)
+struct GivensArgs {
+    int j, m;
+    const double* h1;  // projections of pass 1 (h1[j+1] = ||w||^2 before orthogonalising)
+    const double* h2;  // projections of pass 2
+    double* H;         // (m+1) x m Hessenberg, row-major
+    double* cs;
+    double* sn;
+    double* g;
+    double* scal;      // {h_{j+1,j}, |g_{j+1}|, breakdown, ||w|| before}
+};
+// out[v] = x . Y_v (v < nv) and, if want_xx, out[nv] = x . x; deterministic chunked sums
+int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx, double* partial,
+                     double* out, unsigned* ticket, cudaStream_t s);
+// x -= sign * sum_v h[v] Y_v; then mode 1: out[v] = x . Y_v, mode 2: out[0] = x . x (+ Givens if ga),
+// mode 0: nothing
+int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign, int mode,
+                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s);
 int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s);
 int launch_scale(long N, const double* x, const double* scal, double* y, int check_breakdown, cudaStream_t s);
 int launch_init_g(int m, const double* bsq, double* g, double* scal, cudaStream_t s);

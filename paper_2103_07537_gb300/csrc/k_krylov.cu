@@ -4,8 +4,11 @@
 // (The paper applies its V-cycle inside GMRES: Sec. 3 and Sec. 5.1.)
 //
 // Reductions are deterministic: every vector is cut into the same fixed
-// chunks (one CTA each), every chunk reduces in a fixed tree, and a single
-// CTA adds the chunk partials in chunk order.
+// chunks (one CTA each), every chunk reduces in a fixed tree, and the sums
+// of the chunk partials are formed in chunk order by the last CTA to finish
+// (it takes a ticket with an atomic after a memory fence; no CTA waits for
+// another).  The Givens update of the Hessenberg column runs in that same
+// last CTA of the final reduction of an Arnoldi step.
 #include <math.h>
 
 #include "common.cuh"
@@ -79,20 +82,88 @@ __device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const
     }
 }
 
+// True in every thread of the CTA that finishes last; that CTA has seen the
+// partials of every other CTA.  Resets the ticket for the next launch.
+__device__ __forceinline__ bool last_cta(unsigned* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+        if (last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[v] = sum over chunks c (in order) of partial[v * nchunk + c], one warp per v
+__device__ __forceinline__ void finish_sums(int nv, const double* partial, double* out) {
+    const int lane = threadIdx.x & 31;
+    const int nchunk = gridDim.x;
+    for (int v = threadIdx.x >> 5; v < nv; v += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int c = lane; c < nchunk; c += 32) s += __ldcg(partial + (size_t)v * nchunk + c);
+        s = warp_sum(s);
+        if (lane == 0) out[v] = s;
+    }
+}
+
+// Arnoldi bookkeeping (one thread): column j of the Hessenberg matrix from
+// h1 + h2 and ||w||, breakdown test, previous rotations, the new rotation,
+// the residual estimate |g_{j+1}|.  scal = {h_{j+1,j}, |g_{j+1}|, breakdown,
+// ||w|| before orthogonalising}.
+__device__ void givens_update(const GivensArgs& a, double wsq) {
+    const int j = a.j, m = a.m;
+    double* H = a.H;
+    const double wn0 = sqrt(__ldcg(a.h1 + j + 1));  // ||w||^2 before orthogonalising
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = __ldcg(a.h1 + i) + __ldcg(a.h2 + i);
+    const double hn = sqrt(wsq);
+    H[(size_t)(j + 1) * m + j] = hn;
+    const int breakdown = !(hn > 1e-14 * wn0);
+    for (int i = 0; i < j; ++i) {
+        const double x0 = H[(size_t)i * m + j], x1 = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = a.cs[i] * x0 + a.sn[i] * x1;
+        H[(size_t)(i + 1) * m + j] = -a.sn[i] * x0 + a.cs[i] * x1;
+    }
+    const double x0 = H[(size_t)j * m + j], x1 = H[(size_t)(j + 1) * m + j];
+    const double d = sqrt(x0 * x0 + x1 * x1);
+    if (d == 0.0) {
+        a.cs[j] = 1.0;
+        a.sn[j] = 0.0;
+    } else {
+        a.cs[j] = x0 / d;
+        a.sn[j] = x1 / d;
+    }
+    H[(size_t)j * m + j] = d;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    a.g[j + 1] = -a.sn[j] * a.g[j];
+    a.g[j] = a.cs[j] * a.g[j];
+    a.scal[0] = hn;
+    a.scal[1] = fabs(a.g[j + 1]);
+    a.scal[2] = breakdown ? 1.0 : 0.0;
+    a.scal[3] = wn0;
+}
+
 __global__ void __launch_bounds__(kKThreads) multi_dot_kernel(long N, const double* __restrict__ x,
                                                               const double* __restrict__ Y, long ld, int nv,
-                                                              int want_xx, double* __restrict__ partial) {
+                                                              int want_xx, double* __restrict__ partial,
+                                                              double* __restrict__ out, unsigned* ticket) {
     long e0, e1;
     chunk_range(N, &e0, &e1);
     chunk_dots(e0, e1, x, Y, ld, nv, want_xx, partial);
+    if (last_cta(ticket)) finish_sums(nv + want_xx, partial, out);
 }
 
 // x -= sign * sum_v h[v] Y_v over the chunk, then (mode 1) the dots of the new
-// x with Y_0..Y_{nv-1}, (mode 2) its squared norm, (mode 0) nothing
+// x with Y_0..Y_{nv-1} into out, (mode 2) its squared norm into out (and the
+// Givens update when do_givens), (mode 0) nothing
 __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __restrict__ x,
                                                              const double* __restrict__ Y, long ld, int nv,
-                                                             const double* __restrict__ h, double sign,
-                                                             int mode, double* __restrict__ partial) {
+                                                             const double* __restrict__ h, double sign, int mode,
+                                                             double* __restrict__ partial, double* __restrict__ out,
+                                                             unsigned* ticket, GivensArgs ga, int do_givens) {
     __shared__ double sh_h[kMaxRestart + 1];
     for (int v = threadIdx.x; v < nv; v += blockDim.x) sh_h[v] = sign * h[v];
     __syncthreads();
@@ -107,72 +178,27 @@ __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __r
     __syncthreads();
     if (mode == 1) chunk_dots(e0, e1, x, Y, ld, nv, 0, partial);
     else chunk_dots(e0, e1, x, Y, ld, 0, 1, partial);
-}
-
-// out[v] = sum over chunks of partial[v * nchunk + c], one warp per v
-__global__ void finish_kernel(int nv, int nchunk, const double* __restrict__ partial, double* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    for (int v = threadIdx.x >> 5; v < nv; v += blockDim.x >> 5) {
-        double s = 0.0;
-        for (int c = lane; c < nchunk; c += 32) s += partial[(size_t)v * nchunk + c];
-        s = warp_sum(s);
-        if (lane == 0) out[v] = s;
+    if (last_cta(ticket)) {
+        finish_sums(mode == 1 ? nv : 1, partial, out);
+        if (do_givens) {
+            __syncthreads();
+            if (threadIdx.x == 0) givens_update(ga, __ldcg(out));
+        }
     }
 }
 
-int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx,
-                     double* partial, cudaStream_t s) {
-    multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial);
+int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx, double* partial,
+                     double* out, unsigned* ticket, cudaStream_t s) {
+    multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial, out, ticket);
     return launched(1);
 }
-int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign,
-                    int mode, double* partial, cudaStream_t s) {
-    axpy_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, h, sign, mode, partial);
+int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign, int mode,
+                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s) {
+    GivensArgs g{};
+    if (ga) g = *ga;
+    axpy_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, h, sign, mode, partial, out, ticket, g,
+                                                           ga ? 1 : 0);
     return launched(1);
-}
-int launch_finish(int nv, long N, const double* partial, double* out, cudaStream_t s) {
-    finish_kernel<<<1, 512, 0, s>>>(nv, krylov_chunks(N), partial, out);
-    return launched(1);
-}
-
-// ---------------------------------------------------------------------------
-// Arnoldi bookkeeping on the device (one thread): column j of the Hessenberg
-// matrix from h1 + h2 and ||w||, breakdown test, previous rotations, the new
-// rotation, and the residual estimate |g_{j+1}|.
-// st layout: see GmresDev in capi.cu (passed as raw pointers here).
-// ---------------------------------------------------------------------------
-__global__ void givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
-                              const double* __restrict__ wsq, double* __restrict__ H, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    // scal[0] = h_{j+1,j}, scal[1] = |g_{j+1}|, scal[2] = breakdown, scal[3] = ||w|| before
-    const double wn0 = sqrt(h1[j + 1]);  // h1[j+1] holds ||w||^2 before orthogonalising
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
-    const double hn = sqrt(wsq[0]);
-    H[(size_t)(j + 1) * m + j] = hn;
-    const int breakdown = !(hn > 1e-14 * wn0);
-    for (int i = 0; i < j; ++i) {
-        const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-    }
-    const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
-    const double d = sqrt(a * a + bb * bb);
-    if (d == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-    } else {
-        cs[j] = a / d;
-        sn[j] = bb / d;
-    }
-    H[(size_t)j * m + j] = d;
-    H[(size_t)(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    scal[0] = hn;
-    scal[1] = fabs(g[j + 1]);
-    scal[2] = breakdown ? 1.0 : 0.0;
-    scal[3] = wn0;
 }
 
 // y = H(0:k, 0:k)^{-1} g(0:k), upper triangular
@@ -190,9 +216,9 @@ __global__ void solve_upper_kernel(int k, int m, const double* __restrict__ H, c
 __global__ void scale_kernel(long N, const double* __restrict__ x, const double* __restrict__ scal,
                              double* __restrict__ y, int check_breakdown) {
     if (check_breakdown && scal[2] != 0.0) return;
-    const double inv_den = scal[0];
+    const double den = scal[0];
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long)gridDim.x * blockDim.x)
-        y[e] = x[e] / inv_den;
+        y[e] = x[e] / den;
 }
 
 // g = (beta, 0, ..., 0) with beta = sqrt(*bsq); scal[0] = beta
@@ -204,11 +230,6 @@ __global__ void init_g_kernel(int m, const double* __restrict__ bsq, double* __r
     if (t == 0) scal[0] = beta;
 }
 
-int launch_givens(int j, int m, const double* h1, const double* h2, const double* wsq, double* H, double* cs,
-                  double* sn, double* g, double* scal, cudaStream_t s) {
-    givens_kernel<<<1, 32, 0, s>>>(j, m, h1, h2, wsq, H, cs, sn, g, scal);
-    return launched(1);
-}
 int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s) {
     solve_upper_kernel<<<1, 32, 0, s>>>(k, m, H, g, y);
     return launched(1);

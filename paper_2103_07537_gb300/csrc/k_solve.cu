@@ -95,6 +95,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
     const int kk = lane / B;
     const int r = lane - kk * B;
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    const T bi = (rhs && lane < B) ? ld1<T, CG>(rhs + (size_t)i * B + lane) : T(0);  // issued early
     T acc = T(0);
     if (kk < G) {
         for (int k = k0 + kk; k < k1; k += G) {
@@ -107,7 +108,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
         }
     }
     acc = reduce_rows<T, B>(acc, lane);
-    if (lane < B) y[(size_t)i * B + lane] = rhs ? ld1<T, CG>(rhs + (size_t)i * B + lane) - acc : acc;
+    if (lane < B) y[(size_t)i * B + lane] = rhs ? bi - acc : acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -145,12 +146,18 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
 #pragma unroll
         for (int c = 0; c < FB; ++c) drow[c] = __ldg(D + c);
     }
+    const T bi = lane < FB ? ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) : T(0);
     T acc = T(0);
     if (kk < G) {
         for (int k = k0 + kk; k < k1; k += G) {
             const int j = __ldg(a.ci + k);
             T arow[B];
             load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+            // x~_j is read together with colour(j) and used only if j precedes i
+            // in the colour order (stale values of later colours are masked)
+            T tv[FB];
+            load_vec<T, FB, CG>(xt + (size_t)j * FB, tv);
+            const bool lower = j != i && __ldg(a.colours + j) < a.colour;
             if (x_in) {
                 T xv[B];
                 load_vec<T, B, CG>(x_in + (size_t)j * B, xv);
@@ -163,14 +170,13 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
 #pragma unroll
                 for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
             }
-            if (j != i && __ldg(a.colours + j) < a.colour) {
-                const T* tv = xt + (size_t)j * FB;
+            if (lower) {
                 // field-f columns of the row with compile-time register indices
 #pragma unroll
                 for (int ff = 0; ff < B / FB; ++ff)
                     if (ff == a.field) {
 #pragma unroll
-                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], ld1<T, CG>(tv + c), acc);
+                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
                     }
             }
         }
@@ -178,7 +184,7 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     acc = reduce_rows<T, FB>(acc, lane);
     // lanes 0..FB-1: the row sums of A_{f,*} x + A_ff x~ for this node
     T t = T(0);
-    if (lane < FB) t = ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) - acc;
+    if (lane < FB) t = bi - acc;
     T xn = T(0);
 #pragma unroll
     for (int c = 0; c < FB; ++c) {
@@ -216,9 +222,20 @@ __device__ __forceinline__ void restrict_dof(long t, int b, const int* __restric
                                              const int* __restrict__ members, const T* res, T* rc) {
     const int I = (int)(t / b);
     const int d = (int)(t - (long)I * b);
+    const int q0 = __ldg(agg_ptr + I), q1 = __ldg(agg_ptr + I + 1);
     T acc = T(0);
-    for (int q = __ldg(agg_ptr + I); q < __ldg(agg_ptr + I + 1); ++q)
-        acc += ld1<T, CG>(res + (size_t)__ldg(members + q) * b + d);
+    int q = q0;
+    for (; q + 4 <= q1; q += 4) {  // four independent loads in flight, added in member order
+        const int m0 = __ldg(members + q), m1 = __ldg(members + q + 1);
+        const int m2 = __ldg(members + q + 2), m3 = __ldg(members + q + 3);
+        const T v0 = ld1<T, CG>(res + (size_t)m0 * b + d), v1 = ld1<T, CG>(res + (size_t)m1 * b + d);
+        const T v2 = ld1<T, CG>(res + (size_t)m2 * b + d), v3 = ld1<T, CG>(res + (size_t)m3 * b + d);
+        acc += v0;
+        acc += v1;
+        acc += v2;
+        acc += v3;
+    }
+    for (; q < q1; ++q) acc += ld1<T, CG>(res + (size_t)__ldg(members + q) * b + d);
     rc[(size_t)I * b + d] = acc;
 }
 
