@@ -65,7 +65,7 @@ typedef struct {
     int use_graph;    /* 1: replay the V-cycle from a captured CUDA graph; default 1           */
     int tail_dofs;    /* levels whose n_nodes*b is at most this (and every level below them) run
                          as one thread-block-cluster launch per V-cycle; 0 = one launch per
-                         step on every level; default 65536                                    */
+                         step on every level; default 0                                        */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64). */

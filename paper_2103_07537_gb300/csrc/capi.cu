@@ -31,7 +31,7 @@ extern "C" long long amg_launch_count(void) { return g_launches.load(); }
 namespace {
 
 constexpr int kRapCap = 256;        // maximum stored blocks per coarse row
-constexpr int kMaxCoarseDense = 1536;  // coarsest unknowns handled by the dense solve
+constexpr int kMaxCoarseDense = 4096;  // coarsest unknowns handled by the dense solve
 
 struct Level {
     int n = 0, nnzb = 0, n_colours = 0, n_agg = 0;
@@ -213,7 +213,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->omega = 0.5;
     p->cycle_prec = 64;
     p->use_graph = 1;
-    p->tail_dofs = 65536;
+    p->tail_dofs = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -341,12 +341,14 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     for (int l = 0; l + 1 < h->nlev; ++l) {
         Level& L = h->lev[l];
         TRY(h->alloc(&L.colour, (size_t)L.n));
-        int* cflag = nullptr;
+        int *cflag = nullptr, *queue = nullptr;
         TRY(h->alloc(&cflag, 4));
+        TRY(h->alloc(&queue, 2 * (size_t)L.n));
         int rounds = 0;
-        TRY(colour_nodes(L.n, L.rp, L.ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds));
+        TRY(colour_nodes(L.n, L.rp, L.ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds, queue));
         L.colour_rounds = rounds;
         h->release(cflag);
+        h->release(queue);
         TRY(h->alloc(&L.colour_ptr_d, (size_t)L.n_colours + 1));
         TRY(h->alloc(&L.colour_nodes, (size_t)L.n));
         int* tmp = nullptr;
@@ -382,9 +384,14 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&h->coarse_a, (size_t)(nd * nd)));
         TRY(h->alloc(&h->coarse_inv, (size_t)(nd * nd)));
         TRY(h->alloc(&h->coarse_piv, (size_t)nd));
+        double *lt = nullptr, *col = nullptr;
+        TRY(h->alloc(&lt, (size_t)(nd * nd)));
+        TRY(h->alloc(&col, (size_t)nd + 1));
         TRY(coarse_dense(b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, s));
-        TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, h->d_err, s));
+        TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, lt, col, h->d_err, s));
         TRY(check_dev(h, s));
+        h->release(lt);
+        h->release(col);
         h->t_phase[5] += ms_since(tp);
         tp = Clock::now();
     }

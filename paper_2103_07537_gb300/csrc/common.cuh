@@ -179,8 +179,9 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
                     int* d_scan_tmp, long scan_tmp_bytes, cudaStream_t s, int* rounds_out);
 int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int* d_tmp,
                   cudaStream_t s);
+// d_queue: 2n device ints of scratch (nullptr: always use the multi-launch rounds)
 int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
-                 cudaStream_t s, int* n_colours, int* rounds_out);
+                 cudaStream_t s, int* n_colours, int* rounds_out, int* d_queue);
 // colour_ptr[C+1] and nodes sorted by (colour, index)
 int colour_order(int n, int C, const int* colour, int* colour_ptr, int* nodes, int* d_tmp,
                  cudaStream_t s);
@@ -197,7 +198,9 @@ int block_inverses(int b, int fb, int n, const int* diag, const double* vals, do
 // dense FP64 coarsest matrix, LU with partial pivoting, inverse
 int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals, double* dense,
                  cudaStream_t s);
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, int* err, cudaStream_t s);
+// a (nd x nd, row-major) is factored in place; inv receives A^{-1}; lt: nd*nd
+// doubles of scratch; col: nd + 1 doubles of scratch
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* col, int* err, cudaStream_t s);
 int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s);
 long scan_tmp_bytes(int n);
 int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);

@@ -161,34 +161,44 @@ int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* er
 // ---------------------------------------------------------------------------
 enum : int { kUndecided = 0, kRoot = 1, kOut = 2 };
 
-__global__ void mis2_round_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                  int* state, int* any_undecided) {
+// One round in two one-hop passes over the states at the start of the round.
+// Pass 1: m1[i] = smallest undecided index in {i} + N(i) (INT_MAX if none),
+//         r1[i] = 1 if a root is in {i} + N(i).
+// Pass 2: an undecided node with r1 set on {i} + N(i) (a root within distance
+//         2) is out; one whose smallest m1 over {i} + N(i) is i itself (no
+//         undecided lower node within distance 2) becomes a root.
+// New roots of one round are pairwise at distance >= 3, and a node becomes a
+// root exactly when every lower node within distance 2 is out: the rounds
+// reach the sequential ascending-order result.
+__global__ void mis2_pass1_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const int* __restrict__ state, int* __restrict__ m1, int* __restrict__ r1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    volatile int* st = state;
-    if (st[i] != kUndecided) return;
-    bool blocked = false;
+    int mn = 0x7fffffff, root = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {  // the row contains i itself (diagonal block)
+        const int j = ci[k];
+        const int sj = state[j];
+        if (sj == kUndecided) mn = min(mn, j);
+        if (sj == kRoot) root = 1;
+    }
+    m1[i] = mn;
+    r1[i] = root;
+}
+
+__global__ void mis2_pass2_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const int* __restrict__ m1, const int* __restrict__ r1, int* __restrict__ state,
+                                  int* __restrict__ any_undecided) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] != kUndecided) return;
+    int mn = 0x7fffffff, root = 0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
         const int j = ci[k];
-        if (j == i) continue;
-        const int sj = st[j];
-        if (sj == kRoot) {
-            st[i] = kOut;
-            return;
-        }
-        if (sj == kUndecided && j < i) blocked = true;
-        for (int k2 = rp[j]; k2 < rp[j + 1]; ++k2) {
-            const int m = ci[k2];
-            if (m == i || m == j) continue;
-            const int sm = st[m];
-            if (sm == kRoot) {
-                st[i] = kOut;
-                return;
-            }
-            if (sm == kUndecided && m < i) blocked = true;
-        }
+        mn = min(mn, m1[j]);
+        root |= r1[j];
     }
-    if (!blocked) st[i] = kRoot;
+    if (root) state[i] = kOut;
+    else if (mn == i) state[i] = kRoot;
     else *any_undecided = 1;
 }
 
@@ -247,15 +257,17 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
                     int* d_scan_tmp, long scan_tmp_b, cudaStream_t s, int* rounds_out) {
     const int threads = 256, blocks = ceil_div(n, threads);
     BAMG_CUDA_TRY(cudaMemsetAsync(w.state, 0, sizeof(int) * (size_t)n, s));
-    const int batch = 8;
+    const int batch = 16;
     const long max_rounds = 4L * n + 64;
     long rounds = 0;
     for (;;) {
         for (int r = 0; r < batch; ++r) {
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
-            mis2_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.flag);
+            // agg1 and rootid serve as m1 and r1 during the rounds
+            mis2_pass1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.agg1, w.rootid);
+            mis2_pass2_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.agg1, w.rootid, w.state, w.flag);
         }
-        note_launch(batch);
+        note_launch(2 * batch);
         rounds += batch;
         BAMG_CUDA_TRY(cudaMemcpyAsync(w.host_flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -363,10 +375,98 @@ __global__ void max_kernel(int n, const int* __restrict__ v, int* out) {
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+// Single-CTA Jones-Plassmann for graphs that fit in shared memory: a node is
+// coloured (smallest colour unused by its lower-index neighbours) as soon as
+// its count of uncoloured lower-index neighbours reaches zero; the frontier
+// of such nodes advances one step per iteration.  Same result as the rounds.
+constexpr int kWorklistMaxNodes = 40000;  // 5 bytes per node of shared memory
+__global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int* __restrict__ rp,
+                                                               const int* __restrict__ ci, int* __restrict__ colour,
+                                                               int* __restrict__ qa, int* __restrict__ qb,
+                                                               int* __restrict__ out) {
+    extern __shared__ int smem_i[];
+    int* cnt = smem_i;                                            // n
+    unsigned char* col = reinterpret_cast<unsigned char*>(cnt + n);  // n
+    __shared__ int qn_cur, qn_next, cmax, bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        qn_cur = 0;
+        qn_next = 0;
+        cmax = -1;
+        bad = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+        int c = 0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) c += ci[k] < i;
+        cnt[i] = c;
+        col[i] = 255;
+        if (c == 0) qa[atomicAdd(&qn_cur, 1)] = i;
+    }
+    __syncthreads();
+    int* cur = qa;
+    int* nxt = qb;
+    for (int guard = 0; guard <= n; ++guard) {
+        const int nc = qn_cur;
+        if (nc == 0) break;
+        for (int q = tid; q < nc; q += blockDim.x) {
+            const int i = cur[q];
+            unsigned long long used[4] = {0ull, 0ull, 0ull, 0ull};
+            for (int k = rp[i]; k < rp[i + 1]; ++k) {
+                const int j = ci[k];
+                if (j < i) {
+                    const int cj = col[j];
+                    used[cj >> 6] |= 1ull << (cj & 63);
+                }
+            }
+            int c = 0;
+            while (c < 255 && (used[c >> 6] >> (c & 63) & 1ull)) ++c;
+            if (c >= 255) bad = 1;
+            col[i] = (unsigned char)c;
+            atomicMax(&cmax, c);
+        }
+        __syncthreads();
+        for (int q = tid; q < nc; q += blockDim.x) {
+            const int i = cur[q];
+            for (int k = rp[i]; k < rp[i + 1]; ++k) {
+                const int j = ci[k];
+                if (j > i && atomicSub(&cnt[j], 1) == 1) nxt[atomicAdd(&qn_next, 1)] = j;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            qn_cur = qn_next;
+            qn_next = 0;
+        }
+        int* t = cur;
+        cur = nxt;
+        nxt = t;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) colour[i] = col[i] == 255 ? -1 : col[i];
+    if (tid == 0) {
+        out[0] = cmax + 1;
+        out[1] = bad || qn_cur != 0;
+    }
+}
+
 // d_flag: 3 device ints, h_flag: 3 pinned host ints
 int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
-                 cudaStream_t s, int* n_colours, int* rounds_out) {
+                 cudaStream_t s, int* n_colours, int* rounds_out, int* d_queue) {
     const int threads = 256, blocks = ceil_div(n, threads);
+    if (n <= kWorklistMaxNodes && d_queue) {
+        const size_t smem = (size_t)n * 5 + 16;
+        BAMG_CUDA_TRY(cudaFuncSetAttribute(colour_worklist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        colour_worklist_kernel<<<1, 1024, smem, s>>>(n, rp, ci, colour, d_queue, d_queue + n, d_flag);
+        note_launch(1);
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_flag[1]) return BAMG_EUNSUPPORTED;
+        *n_colours = h_flag[0];
+        if (rounds_out) *rounds_out = 0;
+        return BAMG_OK;
+    }
     BAMG_CUDA_TRY(cudaMemsetAsync(colour, 0xff, sizeof(int) * (size_t)n, s));
     BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, 3 * sizeof(int), s));
     const int batch = 16;
@@ -668,137 +768,244 @@ int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals,
     return launched(1);
 }
 
-// Single-CTA LU + inverse for small nd (the coarsest level of a 2D system).
-// a: nd*nd row-major in global memory (L2-resident); inv: nd*nd row-major.
+// LU factorisation.  nd <= kLuSmemMax: one CTA factors the matrix held in
+// shared memory; larger: one pivot kernel and one rank-1 update kernel per
+// column.  Both perform the same rounded operations in the same order per
+// entry, so the factors do not depend on the variant.
 constexpr int kLuThreads = 1024;
+constexpr int kLuSmemMax = 158;  // 158^2 doubles = 199.7 KB of shared memory
 
-__global__ void __launch_bounds__(kLuThreads) lu_inverse_small_kernel(int nd, double* a, int* piv,
-                                                                      double* inv, double* col, int* err) {
+// first row r >= k of maximal |a[r][k]| over the CTA (ties: smallest r)
+__device__ __forceinline__ void pivot_search(const double* a, int nd, int k, double* red_v, int* red_i,
+                                             double* best_out, int* idx_out) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double best = -1.0;
+    int bi = nd;
+    for (int r = k + tid; r < nd; r += blockDim.x) {
+        const double v = fabs(a[(size_t)r * nd + k]);
+        if (v > best) {
+            best = v;
+            bi = r;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        red_v[wid] = best;
+        red_i[wid] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double bv = red_v[0];
+        int bx = red_i[0];
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+            if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
+                bv = red_v[w];
+                bx = red_i[w];
+            }
+        red_v[0] = bv;
+        red_i[0] = bx;
+    }
+    __syncthreads();
+    *best_out = red_v[0];
+    *idx_out = red_i[0];
+    __syncthreads();
+}
+
+// infinity norm (largest absolute row sum) of the nd x nd matrix a
+__device__ __forceinline__ double inf_norm(const double* a, int nd, double* red_v) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double m = 0.0;
+    for (int r = tid; r < nd; r += blockDim.x) {
+        double sum = 0.0;
+        for (int c = 0; c < nd; ++c) sum += fabs(a[(size_t)r * nd + c]);
+        m = fmax(m, sum);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red_v[wid] = m;
+    __syncthreads();
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmax(mm, red_v[w]);
+    __syncthreads();
+    return mm;
+}
+
+__global__ void __launch_bounds__(kLuThreads) lu_smem_kernel(int nd, double* __restrict__ g, int* __restrict__ piv,
+                                                             int* err) {
+    extern __shared__ double sa[];
     __shared__ double red_v[kLuThreads / 32];
     __shared__ int red_i[kLuThreads / 32];
-    __shared__ double s_norm;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // infinity norm (max row sum) for the singularity threshold
-    {
-        double m = 0.0;
-        for (int r = tid; r < nd; r += blockDim.x) {
-            double sum = 0.0;
-            for (int c = 0; c < nd; ++c) sum += fabs(a[(size_t)r * nd + c]);
-            m = fmax(m, sum);
-        }
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) red_v[wid] = m;
-        __syncthreads();
-        if (tid == 0) {
-            double mm = 0.0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmax(mm, red_v[w]);
-            s_norm = mm;
-        }
-        __syncthreads();
-    }
-    const double norm = s_norm;
+    __shared__ double col[kLuSmemMax];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nd * nd; e += blockDim.x) sa[e] = g[e];
+    __syncthreads();
+    const double norm = inf_norm(sa, nd, red_v);
     bool singular = norm == 0.0;
     for (int k = 0; k < nd; ++k) {
-        // pivot: first row r >= k of maximal |a[r][k]|
-        double best = -1.0;
-        int bi = nd;
-        for (int r = k + tid; r < nd; r += blockDim.x) {
-            double v = fabs(a[(size_t)r * nd + k]);
-            if (v > best) {
-                best = v;
-                bi = r;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) {
-                best = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            red_v[wid] = best;
-            red_i[wid] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double bv = red_v[0];
-            int bx = red_i[0];
-            for (int w = 1; w < (int)(blockDim.x / 32); ++w)
-                if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
-                    bv = red_v[w];
-                    bx = red_i[w];
-                }
-            red_i[0] = bx;
-            red_v[0] = bv;
-            piv[k] = bx;
-        }
-        __syncthreads();
-        const int p = red_i[0];
-        if (!(red_v[0] >= 1e-14 * norm)) singular = true;
+        double best;
+        int p;
+        pivot_search(sa, nd, k, red_v, red_i, &best, &p);
+        if (!(best >= 1e-14 * norm)) singular = true;
+        if (tid == 0) piv[k] = p;
         if (p != k)
             for (int c = tid; c < nd; c += blockDim.x) {
-                double t = a[(size_t)k * nd + c];
-                a[(size_t)k * nd + c] = a[(size_t)p * nd + c];
-                a[(size_t)p * nd + c] = t;
+                const double t = sa[k * nd + c];
+                sa[k * nd + c] = sa[p * nd + c];
+                sa[p * nd + c] = t;
             }
         __syncthreads();
-        const double akk = a[(size_t)k * nd + k];
-        for (int r = k + 1 + tid; r < nd; r += blockDim.x) col[r] = __ddiv_rn(a[(size_t)r * nd + k], akk);
+        const double akk = sa[k * nd + k];
+        for (int r = k + 1 + tid; r < nd; r += blockDim.x) col[r] = __ddiv_rn(sa[r * nd + k], akk);
         __syncthreads();
         const int m = nd - k - 1;
-        for (long e = tid; e < (long)m * m; e += blockDim.x) {
-            const int r = k + 1 + (int)(e / m), c = k + 1 + (int)(e % m);
-            a[(size_t)r * nd + c] = __dsub_rn(a[(size_t)r * nd + c], __dmul_rn(col[r], a[(size_t)k * nd + c]));
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int r = k + 1 + e / m, c = k + 1 + e % m;
+            sa[r * nd + c] = __dsub_rn(sa[r * nd + c], __dmul_rn(col[r], sa[k * nd + c]));
         }
-        for (int r = k + 1 + tid; r < nd; r += blockDim.x) a[(size_t)r * nd + k] = col[r];
+        for (int r = k + 1 + tid; r < nd; r += blockDim.x) sa[r * nd + k] = col[r];
         __syncthreads();
     }
-    if (singular) {
-        if (tid == 0) set_error(err, kDevSingularCoarse);
-        return;
+    if (singular && tid == 0) set_error(err, kDevSingularCoarse);
+    for (int e = tid; e < nd * nd; e += blockDim.x) g[e] = sa[e];
+}
+
+__global__ void lu_norm_kernel(int nd, const double* __restrict__ a, double* __restrict__ norm_out) {
+    __shared__ double red_v[kLuThreads / 32];
+    const double n = inf_norm(a, nd, red_v);
+    if (threadIdx.x == 0) *norm_out = n;
+}
+
+// column k: pivot, row swap, multipliers (stored in column k and in col)
+__global__ void __launch_bounds__(kLuThreads) lu_pivot_kernel(int nd, int k, double* __restrict__ a,
+                                                              int* __restrict__ piv, double* __restrict__ col,
+                                                              const double* __restrict__ norm, int* err) {
+    __shared__ double red_v[kLuThreads / 32];
+    __shared__ int red_i[kLuThreads / 32];
+    const int tid = threadIdx.x;
+    double best;
+    int p;
+    pivot_search(a, nd, k, red_v, red_i, &best, &p);
+    if (tid == 0) {
+        piv[k] = p;
+        if (!(best >= 1e-14 * norm[0]) || norm[0] == 0.0) set_error(err, kDevSingularCoarse);
     }
-    // inverse: column c of X solves L U x = P e_c.  Thread per column c.
-    // X is built in inv row-major (inv[r*nd + c]): consecutive threads touch
-    // consecutive addresses of every row.
-    for (long e = tid; e < (long)nd * nd; e += blockDim.x) inv[e] = 0.0;
+    if (p != k)
+        for (int c = tid; c < nd; c += blockDim.x) {
+            const double t = a[(size_t)k * nd + c];
+            a[(size_t)k * nd + c] = a[(size_t)p * nd + c];
+            a[(size_t)p * nd + c] = t;
+        }
     __syncthreads();
-    for (int c = tid; c < nd; c += blockDim.x) {
-        // P e_c: apply the row swaps in order to the unit vector
-        int pos = c;
-        for (int k = 0; k < nd; ++k) {
-            if (piv[k] == pos) pos = k;
-            else if (k == pos) pos = piv[k];
-        }
-        inv[(size_t)pos * nd + c] = 1.0;
+    const double akk = a[(size_t)k * nd + k];
+    for (int r = k + 1 + tid; r < nd; r += blockDim.x) {
+        const double l = __ddiv_rn(a[(size_t)r * nd + k], akk);
+        col[r] = l;
+        a[(size_t)r * nd + k] = l;
+    }
+}
+
+// trailing update a[r][c] -= col[r] * a[k][c] for r, c > k
+__global__ void lu_update_kernel(int nd, int k, double* __restrict__ a, const double* __restrict__ col) {
+    const int m = nd - k - 1;
+    const long total = (long)m * m;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int r = k + 1 + (int)(e / m), c = k + 1 + (int)(e % m);
+        a[(size_t)r * nd + c] = __dsub_rn(a[(size_t)r * nd + c], __dmul_rn(col[r], a[(size_t)k * nd + c]));
+    }
+}
+
+// lt = transpose of the packed LU factors (column k of L and U contiguous)
+__global__ void transpose_kernel(int nd, const double* __restrict__ a, double* __restrict__ lt) {
+    __shared__ double tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = by + y, c = bx + threadIdx.x;
+        if (r < nd && c < nd) tile[y][threadIdx.x] = a[(size_t)r * nd + c];
     }
     __syncthreads();
-    for (int k = 0; k < nd; ++k) {  // forward, unit L, column oriented
-        for (long e = tid; e < (long)(nd - k - 1) * nd; e += blockDim.x) {
-            const int r = k + 1 + (int)(e / nd), c = (int)(e % nd);
-            inv[(size_t)r * nd + c] -= a[(size_t)r * nd + k] * inv[(size_t)k * nd + c];
-        }
-        __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = bx + y, c = by + threadIdx.x;
+        if (r < nd && c < nd) lt[(size_t)r * nd + c] = tile[threadIdx.x][y];
     }
-    for (int k = nd - 1; k >= 0; --k) {  // backward, U
-        const double ukk = a[(size_t)k * nd + k];
-        for (int c = tid; c < nd; c += blockDim.x) inv[(size_t)k * nd + c] /= ukk;
-        __syncthreads();
-        for (long e = tid; e < (long)k * nd; e += blockDim.x) {
-            const int r = (int)(e / nd), c = (int)(e % nd);
-            inv[(size_t)r * nd + c] -= a[(size_t)r * nd + k] * inv[(size_t)k * nd + c];
+}
+
+// Inverse column by column: column c of A^{-1} solves L U x = P e_c.  One CTA
+// per column (grid-stride over columns), x in shared memory; lt holds the
+// factors column-major so that the threads of a step read consecutive
+// addresses.
+constexpr int kInvThreads = 256;
+__global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, const double* __restrict__ lt,
+                                                                      const int* __restrict__ piv,
+                                                                      double* __restrict__ inv) {
+    extern __shared__ double x[];
+    __shared__ int pos0;
+    const int tid = threadIdx.x;
+    for (int c = blockIdx.x; c < nd; c += gridDim.x) {
+        if (tid == 0) {  // P e_c: the swaps applied in order to the unit vector
+            int pos = c;
+            for (int k = 0; k < nd; ++k) {
+                const int pk = piv[k];
+                if (pk == pos) pos = k;
+                else if (k == pos) pos = pk;
+            }
+            pos0 = pos;
         }
+        for (int r = tid; r < nd; r += blockDim.x) x[r] = 0.0;
+        __syncthreads();
+        if (tid == 0) x[pos0] = 1.0;
+        __syncthreads();
+        for (int k = pos0; k < nd; ++k) {  // unit lower triangle (entries above pos0 stay zero)
+            const double xk = x[k];
+            if (xk != 0.0)
+                for (int r = k + 1 + tid; r < nd; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
+            __syncthreads();
+        }
+        for (int k = nd - 1; k >= 0; --k) {  // upper triangle
+            if (tid == 0) x[k] /= lt[(size_t)k * nd + k];
+            __syncthreads();
+            const double xk = x[k];
+            for (int r = tid; r < k; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
+            __syncthreads();
+        }
+        for (int r = tid; r < nd; r += blockDim.x) inv[(size_t)r * nd + c] = x[r];
         __syncthreads();
     }
 }
 
-// col: nd doubles of scratch
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, int* err, cudaStream_t s) {
+// a: the dense matrix (factored in place), inv: its inverse, lt: nd*nd scratch
+// (the transposed factors), col: nd + 1 doubles of scratch
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* col, int* err, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
-    double* col = inv;  // multipliers live in the first row of inv until the inverse is built
-    lu_inverse_small_kernel<<<1, kLuThreads, 0, s>>>(nd, a, piv, inv, col, err);
-    return launched(1);
+    int n = 0;
+    if (nd <= kLuSmemMax) {
+        const size_t smem = sizeof(double) * (size_t)nd * nd;
+        BAMG_CUDA_TRY(cudaFuncSetAttribute(lu_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        lu_smem_kernel<<<1, kLuThreads, smem, s>>>(nd, a, piv, err);
+        n += 1;
+    } else {
+        lu_norm_kernel<<<1, kLuThreads, 0, s>>>(nd, a, col + nd);
+        n += 1;
+        for (int k = 0; k < nd; ++k) {
+            lu_pivot_kernel<<<1, kLuThreads, 0, s>>>(nd, k, a, piv, col, col + nd, err);
+            const long m = (long)(nd - k - 1) * (nd - k - 1);
+            if (m > 0) {
+                const int blocks = (int)((m + 255) / 256 < 152L * 8 ? (m + 255) / 256 : 152L * 8);
+                lu_update_kernel<<<blocks, 256, 0, s>>>(nd, k, a, col);
+                n += 1;
+            }
+            n += 1;
+        }
+    }
+    transpose_kernel<<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, lt);
+    const int cols = nd < 152 * 8 ? nd : 152 * 8;
+    lu_inverse_cols_kernel<<<cols, kInvThreads, sizeof(double) * (size_t)nd, s>>>(nd, lt, piv, inv);
+    return launched(n + 2);
 }
 
 __global__ void convert_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
