@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,6 +20,64 @@ using namespace bamg;
 namespace {
 std::atomic<long long> g_launches{0};
 thread_local long long* t_capture_sink = nullptr;  // set while a graph is captured
+}  // namespace
+
+// Stream-ordered device memory: one pool per device, owned by the library,
+// that keeps freed memory for the next hierarchy (no cudaMalloc / cudaFree on
+// the setup and destroy paths once the pool is warm).
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<cudaMemPool_t> g_pool[kMaxDevices];
+
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    cudaMemPool_t p = g_pool[dev].load();
+    if (p) return p;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaMemPool_t expected = nullptr;
+    if (!g_pool[dev].compare_exchange_strong(expected, p)) {
+        cudaMemPoolDestroy(p);
+        return expected;
+    }
+    return p;
+}
+
+// small pinned host slots (128 bytes) for flags read back during setup and
+// FGMRES, carved from process-wide blocks so that a hierarchy needs no
+// cudaMallocHost of its own
+std::mutex g_pin_mu;
+std::vector<char*> g_pin_free;
+
+char* pin_slot() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        char* blk = nullptr;
+        if (cudaMallocHost(&blk, 64 * 128) != cudaSuccess) return nullptr;
+        for (int i = 0; i < 64; ++i) g_pin_free.push_back(blk + 128 * i);
+    }
+    char* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pin_release(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(static_cast<char*>(p));
+}
+
+cudaError_t pool_alloc(void** q, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t p = device_pool();
+    if (!p) return cudaMalloc(q, bytes);
+    return cudaMallocFromPoolAsync(q, bytes, p, s);
+}
 }  // namespace
 
 void bamg::note_launch(int count) {
@@ -105,8 +164,15 @@ struct bamg_ctx {
     double rec_bytes = 0.0, rec_flops = 0.0;
     // profiling
     int prof = 0;
-    std::vector<ProfRec> recs;
+    std::vector<ProfRec> recs;        // direct launches, resolved when read
     std::vector<cudaEvent_t> ev_free;
+    bool capturing_prof = false;      // recording event nodes into prof_graph
+    std::vector<ProfRec> graph_recs;  // event-record nodes of prof_graph
+    cudaGraph_t prof_graph = nullptr;
+    cudaGraphExec_t prof_exec = nullptr;
+    long long prof_graph_kernels = 0;
+    double acc_ms[BAMG_K_COUNT] = {}, acc_bytes[BAMG_K_COUNT] = {}, acc_flops[BAMG_K_COUNT] = {};
+    long long acc_n[BAMG_K_COUNT] = {};
     // FGMRES workspace
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *h1 = nullptr, *h2 = nullptr,
@@ -117,12 +183,14 @@ struct bamg_ctx {
     // host wall time of the setup phases (ms): pattern, aggregate, rap, colour, inverse, coarse, vectors
     double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
+    cudaStream_t stream = nullptr;  // the setup stream: allocations and frees are ordered on it
+
     template <typename T>
     int alloc(T** ptr, size_t count) {
         *ptr = nullptr;
         if (count == 0) count = 1;
         void* q = nullptr;
-        if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return BAMG_ECUDA;
+        if (pool_alloc(&q, count * sizeof(T), stream) != cudaSuccess) return BAMG_ECUDA;
         allocs.push_back(q);
         bytes += (long)(count * sizeof(T));
         *ptr = static_cast<T*>(q);
@@ -131,22 +199,26 @@ struct bamg_ctx {
     void release(void* q) {
         for (auto& a : allocs)
             if (a == q) {
-                cudaFree(a);
+                cudaFreeAsync(a, stream);
                 a = nullptr;
             }
     }
     ~bamg_ctx() {
-        for (auto& r : recs) {
-            cudaEventDestroy(r.e0);
-            cudaEventDestroy(r.e1);
-        }
-        for (auto e : ev_free) cudaEventDestroy(e);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
+        if (prof_exec) cudaGraphExecDestroy(prof_exec);
+        if (prof_graph) cudaGraphDestroy(prof_graph);
+        for (auto* v : {&recs, &graph_recs})
+            for (auto& r : *v) {
+                cudaEventDestroy(r.e0);
+                cudaEventDestroy(r.e1);
+            }
+        for (auto e : ev_free) cudaEventDestroy(e);
         for (void* a : allocs)
-            if (a) cudaFree(a);
-        if (h_pin) cudaFreeHost(h_pin);
-        if (h_scal) cudaFreeHost(h_scal);
+            if (a) cudaFreeAsync(a, stream);
+        cudaStreamSynchronize(stream);
+        pin_release(h_pin);
+        pin_release(h_scal);
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
@@ -178,18 +250,23 @@ static cudaEvent_t take_event(bamg_ctx* h) {
     return e;
 }
 
+// While a profiling graph is captured the events become event-record nodes of
+// the graph (timestamps taken by the GPU between the kernels, no host gaps).
 static int prof_begin(bamg_ctx* h, cudaStream_t s) {
     if (!h->prof) return -1;
     ProfRec r{take_event(h), take_event(h), -1, 0.0, 0.0};
-    cudaEventRecord(r.e0, s);
-    h->recs.push_back(r);
-    return (int)h->recs.size() - 1;
+    std::vector<ProfRec>& v = h->capturing_prof ? h->graph_recs : h->recs;
+    if (h->capturing_prof) cudaEventRecordWithFlags(r.e0, s, cudaEventRecordExternal);
+    else cudaEventRecord(r.e0, s);
+    v.push_back(r);
+    return (int)v.size() - 1;
 }
 
 static void prof_end(bamg_ctx* h, cudaStream_t s, int idx, int kind, double bytes, double flops) {
     if (idx < 0) return;
-    ProfRec& r = h->recs[(size_t)idx];
-    cudaEventRecord(r.e1, s);
+    ProfRec& r = (h->capturing_prof ? h->graph_recs : h->recs)[(size_t)idx];
+    if (h->capturing_prof) cudaEventRecordWithFlags(r.e1, s, cudaEventRecordExternal);
+    else cudaEventRecord(r.e1, s);
     r.kind = kind;
     r.bytes = bytes;
     r.flops = flops;
@@ -248,8 +325,9 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     const int b = h->b;
     const size_t bb = (size_t)b * b;
     TRY(h->alloc(&h->d_err, 4));
-    BAMG_CUDA_TRY(cudaMallocHost(&h->h_pin, 8 * sizeof(int)));
-    BAMG_CUDA_TRY(cudaMallocHost(&h->h_scal, 4 * sizeof(double)));
+    h->h_pin = reinterpret_cast<int*>(pin_slot());
+    h->h_scal = reinterpret_cast<double*>(pin_slot());
+    if (!h->h_pin || !h->h_scal) return BAMG_ECUDA;
     BAMG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s));
     Level& L0 = h->lev[0];
     L0.n = n;
@@ -457,6 +535,7 @@ extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* v
     h->fb = fb;
     h->p = prm;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->stream = s;
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return BAMG_ECUDA;
@@ -473,7 +552,7 @@ extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* v
 
 extern "C" int amg_destroy(bamg_t h) {
     if (!h) return BAMG_OK;
-    cudaDeviceSynchronize();
+    cudaStreamSynchronize(h->stream);
     delete h;
     return BAMG_OK;
 }
@@ -748,7 +827,51 @@ static int ensure_graph(bamg_ctx* h) {
     return BAMG_OK;
 }
 
+// the V-cycle captured with an event-record node around every kernel
+static int ensure_prof_graph(bamg_ctx* h) {
+    if (h->prof_exec) return BAMG_OK;
+    cudaStream_t cs = h->cap_stream;
+    BAMG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    long long kernels = 0;
+    t_capture_sink = &kernels;
+    h->capturing_prof = true;
+    int st = cycle_direct(h, h->cyc_in, h->cyc_out, cs);
+    h->capturing_prof = false;
+    t_capture_sink = nullptr;
+    h->prof_graph_kernels = kernels;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (st != BAMG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return BAMG_ECUDA;
+    h->prof_graph = g;
+    BAMG_CUDA_TRY(cudaGraphInstantiate(&h->prof_exec, g, 0));
+    return BAMG_OK;
+}
+
+static int apply_profiled(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
+    TRY(ensure_prof_graph(h));
+    const size_t nbytes = sizeof(double) * (size_t)h->lev[0].n * h->b;
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->cyc_in, r, nbytes, cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaGraphLaunch(h->prof_exec, s));
+    note_launch((int)h->prof_graph_kernels);
+    BAMG_CUDA_TRY(cudaMemcpyAsync(z, h->cyc_out, nbytes, cudaMemcpyDeviceToDevice, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    for (const ProfRec& rec : h->graph_recs) {
+        float e = 0.0f;
+        BAMG_CUDA_TRY(cudaEventElapsedTime(&e, rec.e0, rec.e1));
+        h->acc_ms[rec.kind] += e;
+        h->acc_bytes[rec.kind] += rec.bytes;
+        h->acc_flops[rec.kind] += rec.flops;
+        h->acc_n[rec.kind] += 1;
+    }
+    return BAMG_OK;
+}
+
 static int apply_impl(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
+    if (h->prof && h->p.use_graph) return apply_profiled(h, r, z, s);
     if (!h->p.use_graph || h->prof) return cycle_direct(h, r, z, s);
     TRY(ensure_graph(h));
     const size_t nbytes = sizeof(double) * (size_t)h->lev[0].n * h->b;
@@ -789,7 +912,8 @@ static int ensure_krylov(bamg_ctx* h, int m) {
     TRY(h->alloc(&h->y, (size_t)m));
     TRY(h->alloc(&h->scal, 4));
     TRY(h->alloc(&h->ticket, 4));
-    BAMG_CUDA_TRY(cudaMemset(h->ticket, 0, 4 * sizeof(unsigned)));
+    BAMG_CUDA_TRY(cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned), h->stream));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->m_alloc = m;
     return BAMG_OK;
 }
@@ -890,10 +1014,11 @@ extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const doub
     double *d_v = nullptr, *d_b = nullptr, *d_x = nullptr;
     int st = BAMG_OK;
     bamg_t h = nullptr;
-    if (cudaMalloc(&d_rp, sizeof(int) * (n_nodes + 1)) != cudaSuccess ||
-        cudaMalloc(&d_ci, sizeof(int) * (size_t)nnzb) != cudaSuccess ||
-        cudaMalloc(&d_v, sizeof(double) * (size_t)nnzb * b * b) != cudaSuccess ||
-        cudaMalloc(&d_b, sizeof(double) * N) != cudaSuccess || cudaMalloc(&d_x, sizeof(double) * N) != cudaSuccess)
+    if (pool_alloc((void**)&d_rp, sizeof(int) * (n_nodes + 1), s) != cudaSuccess ||
+        pool_alloc((void**)&d_ci, sizeof(int) * (size_t)nnzb, s) != cudaSuccess ||
+        pool_alloc((void**)&d_v, sizeof(double) * (size_t)nnzb * b * b, s) != cudaSuccess ||
+        pool_alloc((void**)&d_b, sizeof(double) * N, s) != cudaSuccess ||
+        pool_alloc((void**)&d_x, sizeof(double) * N, s) != cudaSuccess)
         st = BAMG_ECUDA;
     if (st == BAMG_OK &&
         (cudaMemcpyAsync(d_rp, row_ptr, sizeof(int) * (n_nodes + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -913,11 +1038,9 @@ extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const doub
     }
     cudaStreamSynchronize(s);
     amg_destroy(h);
-    cudaFree(d_rp);
-    cudaFree(d_ci);
-    cudaFree(d_v);
-    cudaFree(d_b);
-    cudaFree(d_x);
+    for (void* q : {(void*)d_rp, (void*)d_ci, (void*)d_v, (void*)d_b, (void*)d_x})
+        if (q) cudaFreeAsync(q, s);
+    cudaStreamSynchronize(s);
     return st != BAMG_OK ? st : solve_st;
 }
 
@@ -1045,6 +1168,12 @@ extern "C" int amg_profile_read(bamg_t h, int kind, double* ms, long long* launc
         h->ev_free.push_back(r.e1);
     }
     h->recs.swap(keep);
+    t += h->acc_ms[kind];
+    by += h->acc_bytes[kind];
+    fl += h->acc_flops[kind];
+    cnt += h->acc_n[kind];
+    h->acc_ms[kind] = h->acc_bytes[kind] = h->acc_flops[kind] = 0.0;
+    h->acc_n[kind] = 0;
     if (ms) *ms = t;
     if (launches) *launches = cnt;
     if (bytes) *bytes = by;
