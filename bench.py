@@ -359,15 +359,20 @@ def run_ours(args):
     tfl = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
     t_mem = d["bytes"] / (peak_gbs * 1e9)
     t_alu = d["flops"] / (fp64_peak_tflops * 1e12)
+    # DRAM bytes per launch of the dominant kernel from a committed ncu capture,
+    # only when the kernel sources are unchanged since that capture
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not f.endswith("_traffic.json"):
+            continue
         try:
-            tj = json.load(open(tpath))
-            if tj.get("source_digest") == source_digest() and tj.get("kind") == dom:
-                traffic = tj.get("dram_bytes_per_launch")
+            tj = json.load(open(os.path.join(pdir, f)))
         except Exception:
-            traffic = None
+            continue
+        if tj.get("source_digest") == source_digest() and tj.get("kind") == dom and \
+                tj.get("workload") == args.workload:
+            traffic = tj.get("dram_bytes_per_launch")
     if t_alu > t_mem:
         roofline = {"bound": "alu", "achieved": tfl, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                     "frac": tfl / fp64_peak_tflops, "traffic": traffic,
