@@ -139,6 +139,34 @@ int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, i
 int bsr_spmv(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int b,
              const double* x, double* y, void* stream);
 
+/*
+ * amg_colour_noalloc - the node colouring that amg_setup computes for the
+ *   finest level (first fit in ascending node order over the stored pattern),
+ *   computed without allocating any memory.  The paper has no counterpart:
+ *   this entry point exists for callers that must not allocate at the time of
+ *   the call - code running while a stream is captured into a CUDA graph
+ *   (cudaMalloc is not allowed during capture), allocation-free real-time or
+ *   callback paths, and applications whose device memory is reserved in
+ *   advance by their own allocator.  It calls no cudaMalloc, cudaFree or
+ *   allocating library routine; its work queues live in a fixed device array
+ *   inside the library (320,016 bytes, held on every GPU that loads the
+ *   library until the process exits).
+ * row_ptr, col_idx: device, the BSR pattern (conventions above); n_nodes in
+ *   1..40000 (BAMG_EUNSUPPORTED above 40000).
+ * colour: device, n_nodes ints, receives the colour of every node.
+ * n_colours: device, one int, receives the number of colours, or -1 if the
+ *   pattern needs more than 255 colours or is not structurally symmetric.
+ * The first call on a device looks up the device address of the scratch array
+ *   (a host-side call, done once per device with that device current); make
+ *   that first call before capturing a stream.  Asynchronous on `stream`.
+ *   Every call on a device shares the one scratch array, which keeps the last
+ *   call's contents (nothing in it needs to start at zero): calls that overlap
+ *   on the GPU (different streams, no ordering between them) race and must
+ *   not be issued.
+ */
+int amg_colour_noalloc(const int* row_ptr, const int* col_idx, int n_nodes, int* colour, int* n_colours,
+                       void* stream);
+
 /* ---- introspection (host outputs; synchronise the handle's setup stream) ---- */
 
 /* number of levels (>= 1), or a negative status */

@@ -24,7 +24,7 @@ BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 #: every symbol the C header declares
 EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
            "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror",
-           "amg_profile", "amg_profile_read", "amg_launch_count"]
+           "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc"]
 
 #: kernel kinds of amg_profile_read
 KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast", "tail"]
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
         lib.amg_profile_read.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_longlong), _dp, _dp]
         lib.amg_launch_count.argtypes = []
         lib.amg_launch_count.restype = C.c_longlong
+        lib.amg_colour_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
         _lib = lib
         return lib
 
@@ -245,6 +246,15 @@ def amg_profile_read(handle: int, kind) -> dict:
 
 def amg_launch_count() -> int:
     return int(load().amg_launch_count())
+
+
+def amg_colour_noalloc(row_ptr, col_idx, n_nodes: int, colour, n_colours, stream=None) -> None:
+    """Colours of the pattern into device int32 tensors colour[n_nodes] and
+    n_colours[1] (-1 on failure), without any allocation in the library."""
+    st = load().amg_colour_noalloc(_ptr(row_ptr), _ptr(col_idx), int(n_nodes), _ptr(colour), _ptr(n_colours),
+                                   _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_colour_noalloc")
 
 
 class Solver:

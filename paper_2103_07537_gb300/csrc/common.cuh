@@ -179,6 +179,14 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
                     int* d_scan_tmp, long scan_tmp_bytes, cudaStream_t s, int* rounds_out);
 int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int* d_tmp,
                   cudaStream_t s);
+// Single-CTA worklist colouring (k_setup.cu): colour[n], queues qa, qb (n ints
+// each, no initial contents needed), out[0] = colour count, out[1] = 1 on
+// failure (a colour above 254 or an inconsistent pattern).  Dynamic shared
+// memory: 5 * n + 16 bytes.
+constexpr int kWorklistMaxNodes = 40000;
+__global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                       int* __restrict__ colour, int* __restrict__ qa, int* __restrict__ qb,
+                                       int* __restrict__ out);
 // d_queue: 2n device ints of scratch (nullptr: always use the multi-launch rounds)
 int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
                  cudaStream_t s, int* n_colours, int* rounds_out, int* d_queue);

@@ -379,7 +379,6 @@ __global__ void max_kernel(int n, const int* __restrict__ v, int* out) {
 // coloured (smallest colour unused by its lower-index neighbours) as soon as
 // its count of uncoloured lower-index neighbours reaches zero; the frontier
 // of such nodes advances one step per iteration.  Same result as the rounds.
-constexpr int kWorklistMaxNodes = 40000;  // 5 bytes per node of shared memory
 __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int* __restrict__ rp,
                                                                const int* __restrict__ ci, int* __restrict__ colour,
                                                                int* __restrict__ qa, int* __restrict__ qb,
