@@ -39,7 +39,6 @@ import numpy as np  # noqa: E402
 METRIC = "V-cycle ms & solves/s to 1e-8 rel. residual (FP64 vs mixed/learned); HBM GB/s"
 UNIT = "solves/s"
 TOL = 1e-8
-RESTART = 30
 MAX_ITER = 5000
 FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
@@ -48,14 +47,19 @@ SMS = 152
 WORKLOADS = {
     "mhd2d_128": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d(128, seed),
-        levels=4, max_coarse=0,
+        levels=4, max_coarse=0, restart=30, prec=64,
         desc="2D coupled 4-field Q1 system (u,v,p | Bx,By,psi), 128x128 cells, 6 dofs/node, 99,846 unknowns, "
              "148,225 blocks, nu/eta log-U[1e-3,1], FP64 V(1,1) BGS omega=0.5, 4 levels, FGMRES(30) to 1e-8"),
     "stokes2d_32": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes2d(32, seed),
-        levels=3, max_coarse=0,
+        levels=3, max_coarse=0, restart=30, prec=64,
         desc="2D Stokes Q1-Q1 stabilised, 32x32 cells, 3 dofs/node, 3,267 unknowns, FP64, 3 levels, "
              "FGMRES(30) to 1e-8"),
+    "stokes3d_64": dict(
+        make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes3d(64, seed),
+        levels=10, max_coarse=2500, restart=50, prec=32, cpu_sample_iters=5,
+        desc="3D Stokes Q1-Q1 stabilised, 64^3 hex cells, 4 dofs/node, 1,098,500 unknowns, 7,189,057 blocks "
+             "(115 M scalars), FP32 V(1,1) BGS omega=0.5 inside FP64 FGMRES(50) to 1e-8, 3 levels"),
 }
 
 
@@ -179,7 +183,7 @@ def oracle_full_solve(sys_, wl):
     t0 = time.perf_counter()
     h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
     t1 = time.perf_counter()
-    _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=RESTART, max_iter=MAX_ITER)
+    _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=wl["restart"], max_iter=MAX_ITER)
     t2 = time.perf_counter()
     return dict(setup_s=t1 - t0, solve_s=t2 - t1, iters=it, relres=rr, converged=conv)
 
@@ -191,7 +195,7 @@ def oracle_sample(sys_, wl, iters):
     t0 = time.perf_counter()
     h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
     t1 = time.perf_counter()
-    _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=RESTART, max_iter=iters)
+    _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=wl["restart"], max_iter=iters)
     t2 = time.perf_counter()
     return t1 - t0, (t2 - t1) / max(it, 1)
 
@@ -253,7 +257,10 @@ def run_ours(args):
     x = torch.zeros_like(b)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=64)
+    restart = wl["restart"]
+    main_prec = wl["prec"]
+    other_prec = 32 if main_prec == 64 else 64
+    params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec)
 
     def step(params, profile=False):
         h = bamg.amg_setup(rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params, stream)
@@ -261,7 +268,7 @@ def run_ours(args):
             if profile:
                 bamg.amg_profile(h, True)
             x.zero_()
-            st, it, rr = bamg.fgmres_solve(h, b, x, TOL, RESTART, MAX_ITER, stream)
+            st, it, rr = bamg.fgmres_solve(h, b, x, TOL, restart, MAX_ITER, stream)
             prof = None
             if profile:
                 prof = {k: bamg.amg_profile_read(h, k) for k in bamg.KERNEL_KINDS}
@@ -333,13 +340,14 @@ def run_ours(args):
         bamg.amg_destroy(hh)
         st_times.append(e0.elapsed_time(e1))
 
-    # --- mixed precision variant: FP32 cycle inside FP64 FGMRES -------------------
-    params32 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=32)
-    step(params32)
-    k32 = max(1, min(args.steps, 5))
-    ms32, (st32, it32, rr32, _) = timed(params32, k32)
-    mixed = {"cycle": "fp32 (fp64 outer FGMRES, fp64 coarse solve)", "value": k32 / (ms32 / 1e3), "unit": UNIT,
-             "iterations": it32, "relres": rr32, "converged": st32 == 0}
+    # --- the other cycle precision (FP32 cycle inside FP64 FGMRES, or FP64 cycle) --
+    params_o = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=other_prec)
+    step(params_o)
+    k_o = max(1, min(args.steps, 5))
+    ms_o, (st_o, it_o, rr_o, _) = timed(params_o, k_o)
+    variant = {"cycle": (f"fp{other_prec} V-cycle inside fp64 FGMRES (fp64 outer SpMV, Arnoldi, coarse solve)"),
+               "value": k_o / (ms_o / 1e3), "unit": UNIT, "iterations": it_o, "relres": rr_o,
+               "converged": st_o == 0}
 
     # --- per-kernel profile pass (events around every launch) --------------------
     kernels = {}
@@ -399,7 +407,7 @@ def run_ours(args):
         b_h = torch.from_numpy(s.rhs).pin_memory().numpy()
         x_h = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory().numpy()
         k_e = max(1, min(args.steps, 5))
-        bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL, RESTART,
+        bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL, restart,
                             MAX_ITER, params64, stream)
         tot = 0.0
         for _ in range(k_e):
@@ -410,7 +418,7 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL,
-                                RESTART, MAX_ITER, params64, stream)
+                                restart, MAX_ITER, params64, stream)
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
@@ -421,17 +429,30 @@ def run_ours(args):
     # --- CPU baseline: the oracle on this host ------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        full = oracle_full_solve(s, wl)
-        t = full["setup_s"] + full["solve_s"]
-        cpu = {"kind": "oracle", "value": 1.0 / t, "unit": UNIT, "cores": 1,
-               "sample": f"one full solve (setup + FGMRES(30) to 1e-8, {full['iters']} inner steps) of "
-                         f"{args.workload} seed {seed}, single-threaded C oracle",
-               "host_cores_available": os.cpu_count(), "iterations": full["iters"]}
+        if wl.get("cpu_sample_iters"):
+            # bounded sample: oracle setup + a few inner steps, scaled to the
+            # inner-step count of this solve (the oracle's count agrees within
+            # one iteration, see the parity tests)
+            k = wl["cpu_sample_iters"]
+            t_setup, t_iter = oracle_sample(s, wl, k)
+            t = t_setup + t_iter * iters
+            cpu = {"kind": "oracle", "value": 1.0 / t, "unit": UNIT, "cores": 1,
+                   "sample": f"oracle setup + {k} inner FGMRES({restart}) steps of {args.workload} seed {seed}, "
+                             f"scaled to {iters} inner steps; single-threaded C oracle",
+                   "host_cores_available": os.cpu_count()}
+        else:
+            full = oracle_full_solve(s, wl)
+            t = full["setup_s"] + full["solve_s"]
+            cpu = {"kind": "oracle", "value": 1.0 / t, "unit": UNIT, "cores": 1,
+                   "sample": f"one full solve (setup + FGMRES({restart}) to 1e-8, {full['iters']} inner steps) of "
+                             f"{args.workload} seed {seed}, single-threaded C oracle",
+                   "host_cores_available": os.cpu_count(), "iterations": full["iters"]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_prec == 64 else "f32+f64",
+                "data": "synthetic",
                 "config": {"workload": wl["desc"], "name": args.workload, "seed": seed,
                            "l2": "flushed between steps (256 MiB write outside the timed step)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
@@ -441,7 +462,7 @@ def run_ours(args):
                 "levels": [lv["n"] for lv in stats["levels"]],
                 "colours": [lv["colours"] for lv in stats["levels"]],
                 "setup_phase_ms": stats.get("setup_phase_ms"),
-                "mixed": mixed, "kernels": ksum, "roofline": roofline, "clocks": clocks,
+                "cycle_prec": main_prec, "variant": variant, "kernels": ksum, "roofline": roofline, "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if pg:
