@@ -360,13 +360,18 @@ def run_ours(args):
                 acc[f] += v[f]
     peak_gbs, peak_src = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or 1920.0
-    fp64_peak_tflops = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA / clk / SM on GB300
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
+    # kernels inside the V-cycle run in the cycle precision; the outer Krylov
+    # kernels and the coarse solve in FP64
+    cycle_kinds = {"smooth", "residual", "restrict", "prolong", "tail", "cast"}
+    kernel_prec = main_prec if dom in cycle_kinds else 64
+    fma_per_clk = 2 if kernel_prec == 64 else 128  # per SM on GB300 (FP64: measured 2.08 / clk / SM)
+    alu_peak_tflops = SMS * fma_per_clk * 2 * sm_mhz * 1e6 / 1e12
     gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
     tfl = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
     t_mem = d["bytes"] / (peak_gbs * 1e9)
-    t_alu = d["flops"] / (fp64_peak_tflops * 1e12)
+    t_alu = d["flops"] / (alu_peak_tflops * 1e12)
     # DRAM bytes per launch of the dominant kernel from a committed ncu capture,
     # only when the kernel sources are unchanged since that capture
     traffic = None
@@ -382,14 +387,17 @@ def run_ours(args):
                 tj.get("workload") == args.workload:
             traffic = tj.get("dram_bytes_per_launch")
     if t_alu > t_mem:
-        roofline = {"bound": "alu", "achieved": tfl, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                    "frac": tfl / fp64_peak_tflops, "traffic": traffic,
-                    "peak_source": f"derived FP64 FMA peak: {SMS} SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz",
+        roofline = {"bound": "alu", "achieved": tfl, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                    "frac": tfl / alu_peak_tflops, "traffic": traffic,
+                    "peak_source": f"derived FP{kernel_prec} FMA peak: {SMS} SMs x {fma_per_clk} FMA/clk x 2 flop "
+                                   f"x {sm_mhz:.0f} MHz",
                     "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
-                    "traffic": traffic, "peak_source": peak_src}
-    roofline.update({"kernel": dom, "launches": d["launches"] // max(1, args.profile_steps),
+                    "traffic": traffic, "peak_source": f"{peak_src} HBM copy bandwidth",
+                    "alu_tflops": tfl, "alu_frac": tfl / alu_peak_tflops}
+    roofline.update({"kernel": dom, "kernel_prec": f"fp{kernel_prec}",
+                     "launches": d["launches"] // max(1, args.profile_steps),
                      "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
                      "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                      "flops_per_launch": d["flops"] / max(1, d["launches"])})

@@ -98,6 +98,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
     const T bi = (rhs && lane < B) ? ld1<T, CG>(rhs + (size_t)i * B + lane) : T(0);  // issued early
     T acc = T(0);
     if (kk < G) {
+#pragma unroll 4
         for (int k = k0 + kk; k < k1; k += G) {
             const int j = __ldg(ci + k);
             T a[B], xv[B];
@@ -149,6 +150,7 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     const T bi = lane < FB ? ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) : T(0);
     T acc = T(0);
     if (kk < G) {
+#pragma unroll 4
         for (int k = k0 + kk; k < k1; k += G) {
             const int j = __ldg(a.ci + k);
             T arow[B];
@@ -243,7 +245,7 @@ __device__ __forceinline__ void restrict_dof(long t, int b, const int* __restric
 // one-step kernels
 // ---------------------------------------------------------------------------
 template <typename T, int B>
-__global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict__ rp,
+__global__ void __launch_bounds__(256, 4) spmv_kernel(int n, const int* __restrict__ rp,
                                                    const int* __restrict__ ci,
                                                    const T* __restrict__ vals, const T* __restrict__ x,
                                                    const T* __restrict__ rhs, T* __restrict__ y) {
@@ -310,7 +312,7 @@ template int launch_prolong<double>(int, int, const int*, const double*, double*
 template int launch_prolong<float>(int, int, const int*, const float*, float*, cudaStream_t);
 
 template <typename T, int B, int FB>
-__global__ void __launch_bounds__(256) bgs_colour_kernel(BgsArgs a) {
+__global__ void __launch_bounds__(256, 4) bgs_colour_kernel(BgsArgs a) {
     const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_in_colour) return;  // uniform per warp
     bgs_node<T, B, FB, false>(a, q, threadIdx.x & (kWarp - 1));
