@@ -133,6 +133,42 @@ int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, i
                    void* stream);
 
 /*
+ * amg_setup_batched - one hierarchy for nsys independent systems given as a
+ *   single block-diagonal BSR matrix: system q owns the block rows
+ *   sys_node_off[q] .. sys_node_off[q+1]-1 and couples only within them
+ *   (column indices are global).  Every V-cycle step is one launch over all
+ *   systems' rows; the aggregation, colouring and Galerkin products of the
+ *   block-diagonal matrix are those of the systems separately (the greedy rules
+ *   run in ascending node order and never cross a system); the coarsest level
+ *   keeps one dense FP64 inverse per system.  All systems get the same number
+ *   of levels (coarsening stops for the batch as a whole).
+ * nsys >= 1; sys_node_off: HOST, nsys+1 strictly increasing ints, 0 and n_nodes
+ *   at the ends.  Other arguments and errors as amg_setup; BAMG_EINVAL when a
+ *   block couples two systems.
+ */
+int amg_setup_batched(int nsys, const int* sys_node_off, const int* row_ptr, const int* col_idx,
+                      const double* vals, int n_nodes, int nnzb, int b, const int* field_of_dof,
+                      const amg_params* p, void* stream, bamg_t* out);
+
+/*
+ * fgmres_solve_batched - FGMRES(restart) for every system of a batch, each
+ *   with its own Krylov basis, Hessenberg matrix, rotations, stopping test and
+ *   count (restarts happen for all systems together, after `restart` steps or
+ *   when every system in the cycle has stopped); reductions are per system.
+ * b, x: device, concatenated vectors (x: initial guess in, solution out).
+ * iters, relres: host, nsys entries each (may be NULL): inner steps and the
+ *   true relative residual of every system at exit.
+ * Returns BAMG_OK when every system converged, BAMG_NOT_CONVERGED otherwise.
+ */
+int fgmres_solve_batched(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
+                         int* iters, double* relres, void* stream);
+
+/* number of systems of the handle (1 for amg_setup) */
+int amg_num_systems(bamg_t h);
+/* node range of every system on level l: sys_node_off[nsys+1] (host) */
+int amg_level_systems(bamg_t h, int level, int* sys_node_off);
+
+/*
  * bsr_spmv - y = A x for a BSR matrix (the SpMV of the outer Krylov method and
  *   of every residual).  All pointers device; b in 1..8.  Asynchronous.
  */

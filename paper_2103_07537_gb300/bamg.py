@@ -24,7 +24,8 @@ BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 #: every symbol the C header declares
 EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
            "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror",
-           "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc"]
+           "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
+           "fgmres_solve_batched", "amg_num_systems", "amg_level_systems"]
 
 #: kernel kinds of amg_profile_read
 KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast", "tail"]
@@ -86,6 +87,11 @@ def load(build_if_missing: bool = True):
         lib.amg_launch_count.argtypes = []
         lib.amg_launch_count.restype = C.c_longlong
         lib.amg_colour_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
+        lib.amg_setup_batched.argtypes = [C.c_int, _ip, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip,
+                                          C.POINTER(AmgParams), _vp, C.POINTER(_vp)]
+        lib.fgmres_solve_batched.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
+        lib.amg_num_systems.argtypes = [_vp]
+        lib.amg_level_systems.argtypes = [_vp, C.c_int, _ip]
         _lib = lib
         return lib
 
@@ -257,6 +263,46 @@ def amg_colour_noalloc(row_ptr, col_idx, n_nodes: int, colour, n_colours, stream
         raise BamgError(st, "amg_colour_noalloc")
 
 
+def amg_setup_batched(sys_node_off, row_ptr, col_idx, vals, n_nodes: int, nnzb: int, b: int, field_of_dof,
+                      params=None, stream=None) -> int:
+    off = np.ascontiguousarray(sys_node_off, dtype=np.int32)
+    fm = np.ascontiguousarray(field_of_dof, dtype=np.int32)
+    h = _vp()
+    st = load().amg_setup_batched(int(off.shape[0] - 1), off.ctypes.data_as(_ip), _ptr(row_ptr), _ptr(col_idx),
+                                  _ptr(vals), int(n_nodes), int(nnzb), int(b), fm.ctypes.data_as(_ip),
+                                  C.byref(params) if params is not None else None, _stream(stream), C.byref(h))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_setup_batched")
+    return h.value
+
+
+def fgmres_solve_batched(handle: int, b, x, tol=1e-8, restart=30, max_iter=10000, stream=None):
+    """Returns (status, iterations[nsys], true relative residuals[nsys])."""
+    ns = amg_num_systems(handle)
+    it = np.zeros(ns, np.int32)
+    rr = np.zeros(ns)
+    st = load().fgmres_solve_batched(handle, _ptr(b), _ptr(x), float(tol), int(restart), int(max_iter),
+                                     it.ctypes.data_as(_ip), rr.ctypes.data_as(_dp), _stream(stream))
+    if st < 0:
+        raise BamgError(st, "fgmres_solve_batched")
+    return st, it, rr
+
+
+def amg_num_systems(handle: int) -> int:
+    n = load().amg_num_systems(handle)
+    if n < 0:
+        raise BamgError(n, "amg_num_systems")
+    return n
+
+
+def amg_level_systems(handle: int, level: int) -> np.ndarray:
+    off = np.zeros(amg_num_systems(handle) + 1, np.int32)
+    st = load().amg_level_systems(handle, level, off.ctypes.data_as(_ip))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_systems")
+    return off
+
+
 class Solver:
     """Owns one hierarchy built from a block system held in device tensors."""
 
@@ -294,3 +340,27 @@ class Solver:
 
     def stats(self) -> dict:
         return amg_stats(self.handle)
+
+
+class BatchSolver(Solver):
+    """Owns one hierarchy for a batch of independent systems (block-diagonal
+    device BSR with the node range of every system in sys_node_off)."""
+
+    def __init__(self, sys_node_off, row_ptr, col_idx, vals, b: int, field_of_dof, stream=None, **params):
+        self.b = int(b)
+        self.F = int(max(field_of_dof)) + 1
+        self.n = int(row_ptr.shape[0]) - 1
+        self.row_ptr, self.col_idx, self.vals = row_ptr, col_idx, vals
+        self.params = amg_default_params(**params)
+        self.handle = amg_setup_batched(sys_node_off, row_ptr, col_idx, vals, self.n, int(col_idx.shape[0]),
+                                        self.b, field_of_dof, self.params, stream)
+
+    @property
+    def num_systems(self) -> int:
+        return amg_num_systems(self.handle)
+
+    def level_systems(self, l: int) -> np.ndarray:
+        return amg_level_systems(self.handle, l)
+
+    def solve(self, b, x, tol=1e-8, restart=30, max_iter=10000, stream=None):
+        return fgmres_solve_batched(self.handle, b, x, tol, restart, max_iter, stream)

@@ -3,6 +3,8 @@
 // in include/bamg.h.  Every compute step runs in the kernels of k_*.cu; this
 // file only allocates, sequences launches and reads back sizes and flags.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -104,6 +106,9 @@ struct Level {
     int *agg = nullptr, *agg_ptr = nullptr, *members = nullptr;
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
+    // node range of every system of a batch on this level (host and device)
+    std::vector<int> sys_off;
+    int* sys_off_d = nullptr;
     // per-colour counts for the algorithmic byte / flop model (profiling only)
     std::vector<long> colour_nnz, colour_nnz_lower;
 };
@@ -138,6 +143,20 @@ bool supported_block(int b, int fb) {
 
 struct bamg_ctx {
     int b = 0, F = 1, fb = 0, nlev = 0;
+    int nsys = 1;  // independent systems solved together (block-diagonal operator)
+    // coarsest level of a batch: one dense inverse per system
+    long* inv_off_d = nullptr;
+    int* row_sys_d = nullptr;
+    double* binv = nullptr;
+    int nd_total = 0;
+    // chunks of the level-0 vectors per system (segmented reductions)
+    SegTable seg{};
+    // batched FGMRES workspace
+    int mb_alloc = 0;
+    double *bh1 = nullptr, *bh2 = nullptr, *bwsq = nullptr, *bH = nullptr, *bcs = nullptr, *bsn = nullptr,
+           *bg = nullptr, *by = nullptr, *bscal = nullptr, *bsq = nullptr;
+    int *bk = nullptr, *bactive = nullptr, *bincycle = nullptr;
+    std::vector<double> hb_scal;
     amg_params p{};
     Level lev[kMaxLevels];
     int nd = 0;
@@ -344,6 +363,19 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
     if (h->h_pin[0] != nnzb || h->h_pin[1] != 0) return BAMG_EINVAL;
 
+    // node ranges of the systems on level 0 (one range for a single system)
+    TRY(h->alloc(&L0.sys_off_d, L0.sys_off.size()));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L0.sys_off_d, L0.sys_off.data(), sizeof(int) * L0.sys_off.size(),
+                                  cudaMemcpyHostToDevice, s));
+    if (h->nsys > 1) {  // every stored block stays inside its system
+        int* node_sys = nullptr;
+        TRY(h->alloc(&node_sys, (size_t)n));
+        TRY(launch_fill_sys(h->nsys, L0.sys_off_d, 1, node_sys, s));
+        TRY(launch_check_batch(n, L0.rp, L0.ci, node_sys, L0.sys_off_d, h->d_err, s));
+        TRY(check_dev(h, s));
+        h->release(node_sys);
+    }
+
     h->nlev = 1;
     for (int l = 0;; ++l) {
         Level& L = h->lev[l];
@@ -371,6 +403,15 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         const int nc = aggregate_nodes(L.n, L.rp, L.ci, L.agg, w, d_count, scan_tmp, stb, s, &rounds);
         if (nc < 0) return nc;
         L.agg_rounds = rounds;
+        // node ranges of the systems on the coarse level: the aggregates of a
+        // system are numbered by the ranks of its roots, a contiguous range
+        Level& Cn = h->lev[l + 1];
+        TRY(h->alloc(&Cn.sys_off_d, (size_t)h->nsys + 1));
+        TRY(launch_coarse_offsets(h->nsys, L.sys_off_d, w.rootid, Cn.sys_off_d, s));
+        Cn.sys_off.assign((size_t)h->nsys + 1, 0);
+        BAMG_CUDA_TRY(cudaMemcpyAsync(Cn.sys_off.data(), Cn.sys_off_d, sizeof(int) * (h->nsys + 1),
+                                      cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->release(w.state);
         h->release(w.rootid);
         h->release(w.agg1);
@@ -453,8 +494,39 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->t_phase[4] += ms_since(tp);
         tp = Clock::now();
     }
-    // coarsest level: dense FP64 LU and inverse
-    {
+    // coarsest level of a batch: one dense FP64 LU and inverse per system
+    if (h->nsys > 1) {
+        Level& L = h->lev[h->nlev - 1];
+        std::vector<long> inv_off((size_t)h->nsys + 1, 0);
+        int max_nd = 0;
+        for (int q = 0; q < h->nsys; ++q) {
+            const long nd = (long)(L.sys_off[q + 1] - L.sys_off[q]) * b;
+            if (nd > kMaxCoarseDense) return BAMG_EUNSUPPORTED;
+            max_nd = nd > max_nd ? (int)nd : max_nd;
+            inv_off[q + 1] = inv_off[q] + nd * nd;
+        }
+        h->nd_total = L.n * b;
+        TRY(h->alloc(&h->inv_off_d, inv_off.size()));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h->inv_off_d, inv_off.data(), sizeof(long) * inv_off.size(),
+                                      cudaMemcpyHostToDevice, s));
+        TRY(h->alloc(&h->binv, (size_t)inv_off.back()));
+        TRY(h->alloc(&h->row_sys_d, (size_t)h->nd_total));
+        TRY(launch_fill_sys(h->nsys, L.sys_off_d, b, h->row_sys_d, s));
+        double *work = nullptr, *col = nullptr;
+        int* piv = nullptr;
+        TRY(h->alloc(&work, max_nd > 156 ? (size_t)inv_off.back() : 1));
+        TRY(h->alloc(&col, (size_t)h->nd_total));
+        TRY(h->alloc(&piv, (size_t)h->nd_total));
+        TRY(batched_lu_inverse(h->nsys, b, max_nd, L.sys_off_d, h->inv_off_d, L.rp, L.ci, L.vals64, work, h->binv,
+                               piv, col, h->d_err, s));
+        TRY(check_dev(h, s));
+        h->release(work);
+        h->release(col);
+        h->release(piv);
+        h->nd = 0;
+        h->t_phase[5] += ms_since(tp);
+        tp = Clock::now();
+    } else {
         Level& L = h->lev[h->nlev - 1];
         const long nd = (long)L.n * b;
         if (nd > kMaxCoarseDense) return BAMG_EUNSUPPORTED;
@@ -497,18 +569,51 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&h->r32, N));
         TRY(h->alloc(&h->z32, N));
     }
+    // chunks of the level-0 vectors for the per-system reductions
+    {
+        std::vector<int> csys, sc(1, 0);
+        std::vector<long> ce0, ce1;
+        const long kChunk = 4096;
+        for (int q = 0; q < h->nsys; ++q) {
+            const long e0 = (long)L0.sys_off[q] * b, e1 = (long)L0.sys_off[q + 1] * b;
+            for (long e = e0; e < e1; e += kChunk) {
+                csys.push_back(q);
+                ce0.push_back(e);
+                ce1.push_back(e + kChunk < e1 ? e + kChunk : e1);
+            }
+            sc.push_back((int)csys.size());
+        }
+        int *d_csys = nullptr, *d_sc = nullptr;
+        long *d_e0 = nullptr, *d_e1 = nullptr;
+        TRY(h->alloc(&d_csys, csys.size()));
+        TRY(h->alloc(&d_sc, sc.size()));
+        TRY(h->alloc(&d_e0, ce0.size()));
+        TRY(h->alloc(&d_e1, ce1.size()));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(d_csys, csys.data(), sizeof(int) * csys.size(), cudaMemcpyHostToDevice, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(d_e0, ce0.data(), sizeof(long) * ce0.size(), cudaMemcpyHostToDevice, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(d_e1, ce1.data(), sizeof(long) * ce1.size(), cudaMemcpyHostToDevice, s));
+        h->seg = SegTable{h->nsys, (int)csys.size(), d_csys, d_e0, d_e1, d_sc};
+    }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
-    TRY(setup_tail(h, s));
+    if (h->nsys == 1) TRY(setup_tail(h, s));
     h->t_phase[6] += ms_since(tp);
     return BAMG_OK;
 }
 
-extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
-                         int b, const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out) {
+static int setup_common(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb, int b,
+                        const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out, int nsys,
+                        const int* sys_node_off) {
     if (!out) return BAMG_EINVAL;
     *out = nullptr;
     if (!row_ptr || !col_idx || !vals || !field_of_dof || n_nodes < 1 || nnzb < n_nodes || b < 1 || b > kMaxB)
         return BAMG_EINVAL;
+    if (nsys < 1 || nsys > n_nodes) return BAMG_EINVAL;
+    if (nsys > 1) {
+        if (!sys_node_off || sys_node_off[0] != 0 || sys_node_off[nsys] != n_nodes) return BAMG_EINVAL;
+        for (int q = 0; q < nsys; ++q)
+            if (sys_node_off[q + 1] <= sys_node_off[q]) return BAMG_EINVAL;
+    }
     amg_params prm;
     if (p) prm = *p;
     else amg_default_params(&prm);
@@ -534,6 +639,9 @@ extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* v
     h->F = F;
     h->fb = fb;
     h->p = prm;
+    h->nsys = nsys;
+    if (nsys > 1) h->lev[0].sys_off.assign(sys_node_off, sys_node_off + nsys + 1);
+    else h->lev[0].sys_off = {0, n_nodes};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->stream = s;
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -548,6 +656,17 @@ extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* v
     }
     *out = h;
     return BAMG_OK;
+}
+
+extern "C" int amg_setup(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
+                         int b, const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out) {
+    return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, field_of_dof, p, stream, out, 1, nullptr);
+}
+
+extern "C" int amg_setup_batched(int nsys, const int* sys_node_off, const int* row_ptr, const int* col_idx,
+                                 const double* vals, int n_nodes, int nnzb, int b, const int* field_of_dof,
+                                 const amg_params* p, void* stream, bamg_t* out) {
+    return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, field_of_dof, p, stream, out, nsys, sys_node_off);
 }
 
 extern "C" int amg_destroy(bamg_t h) {
@@ -639,6 +758,12 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         // every level from l down runs as one cluster launch of the recorded phases
         PL(BAMG_K_TAIL, h->tail_bytes, h->tail_flops,
            launch_tail<T>(b, h->fb, h->tail_d, h->n_tail, h->tail_cluster, s));
+        return BAMG_OK;
+    }
+    if (l == h->nlev - 1 && h->nsys > 1) {  // one dense inverse per system
+        const Level& Lc = h->lev[l];
+        PL(BAMG_K_COARSE, 0.0, 0.0,
+           launch_batched_gemv<T>(h->nd_total, b, h->row_sys_d, Lc.sys_off_d, h->inv_off_d, h->binv, rhs, out, s));
         return BAMG_OK;
     }
     if (l == h->nlev - 1) {
@@ -997,6 +1122,155 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
     if (iters) *iters = total;
     if (relres) *relres = rel;
     return converged ? BAMG_OK : BAMG_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES for a batch: every system runs its own FGMRES(m) (own Krylov basis,
+// Hessenberg matrix, rotations, stopping test and iteration count); the
+// V-cycle and the SpMV act on all systems at once, reductions are per system.
+// ---------------------------------------------------------------------------
+static int ensure_batched_krylov(bamg_ctx* h, int m) {
+    if (h->mb_alloc >= m) return BAMG_OK;
+    for (void* q : {(void*)h->bh1, (void*)h->bh2, (void*)h->bwsq, (void*)h->bH, (void*)h->bcs, (void*)h->bsn,
+                    (void*)h->bg, (void*)h->by, (void*)h->bscal, (void*)h->bsq, (void*)h->bk, (void*)h->bactive,
+                    (void*)h->bincycle})
+        if (q) h->release(q);
+    const size_t S = (size_t)h->nsys;
+    TRY(h->alloc(&h->bh1, S * (m + 2)));
+    TRY(h->alloc(&h->bh2, S * (m + 2)));
+    TRY(h->alloc(&h->bwsq, S));
+    TRY(h->alloc(&h->bH, S * (m + 1) * m));
+    TRY(h->alloc(&h->bcs, S * m));
+    TRY(h->alloc(&h->bsn, S * m));
+    TRY(h->alloc(&h->bg, S * (m + 1)));
+    TRY(h->alloc(&h->by, S * m));
+    TRY(h->alloc(&h->bscal, S * 4));
+    TRY(h->alloc(&h->bsq, S));
+    TRY(h->alloc(&h->bk, S));
+    TRY(h->alloc(&h->bactive, S));
+    TRY(h->alloc(&h->bincycle, S));
+    h->hb_scal.assign(S * 4, 0.0);
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->mb_alloc = m;
+    return BAMG_OK;
+}
+
+extern "C" int fgmres_solve_batched(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
+                                    int* iters, double* relres, void* stream) {
+    if (!h || !b || !x || restart < 1 || restart > kMaxRestart || max_iter < 0 || !(tol >= 0.0)) return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = restart, S = h->nsys;
+    TRY(ensure_krylov(h, m));
+    TRY(ensure_batched_krylov(h, m));
+    if (h->m_alloc == m)  // a fresh basis: keep unused systems' chunks finite
+        BAMG_CUDA_TRY(cudaMemsetAsync(h->V, 0, sizeof(double) * (size_t)h->lev[0].n * h->b * (m + 1), s));
+    const Level& L0 = h->lev[0];
+    const long N = (long)L0.n * h->b;
+    const int bsz = h->b;
+    const SegTable& T = h->seg;
+    double* partial = nullptr;
+    TRY(h->alloc(&partial, (size_t)(m + 2) * T.nchunk));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<double> bn((size_t)S), rel((size_t)S, 0.0), tmp((size_t)S);
+    std::vector<int> conv((size_t)S, 0), tot((size_t)S, 0), active((size_t)S), incycle((size_t)S), kk((size_t)S);
+    auto download = [&](const double* d, double* hp, size_t cnt) -> int {
+        BAMG_CUDA_TRY(cudaMemcpyAsync(hp, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        return BAMG_OK;
+    };
+    auto upload = [&](int* d, const std::vector<int>& v) -> int {
+        BAMG_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+        return BAMG_OK;
+    };
+    // ||b_s||
+    TRY(launch_seg_dots(T, b, nullptr, 0, 0, 1, partial, h->bsq, 1, s));
+    TRY(download(h->bsq, tmp.data(), (size_t)S));
+    for (int q = 0; q < S; ++q) {
+        bn[q] = sqrt(tmp[q]);
+        if (!std::isfinite(bn[q])) {
+            h->release(partial);
+            return BAMG_ENAN;
+        }
+        if (bn[q] == 0.0) {  // x_s = 0 solves it
+            conv[q] = 1;
+            const size_t e0 = (size_t)L0.sys_off[q] * bsz, e1 = (size_t)L0.sys_off[q + 1] * bsz;
+            BAMG_CUDA_TRY(cudaMemsetAsync(x + e0, 0, sizeof(double) * (e1 - e0), s));
+        }
+    }
+    int st = BAMG_OK;
+    for (;;) {
+        TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
+        TRY(launch_seg_dots(T, h->w, nullptr, 0, 0, 1, partial, h->bsq, 1, s));
+        TRY(download(h->bsq, tmp.data(), (size_t)S));
+        int n_active = 0;
+        for (int q = 0; q < S; ++q) {
+            if (bn[q] == 0.0) continue;
+            rel[q] = sqrt(tmp[q]) / bn[q];
+            if (!std::isfinite(rel[q])) st = BAMG_ENAN;
+            if (rel[q] <= tol) conv[q] = 1;
+            active[q] = !conv[q] && tot[q] < max_iter;
+            incycle[q] = active[q];
+            kk[q] = 0;
+            n_active += active[q];
+        }
+        for (int q = 0; q < S; ++q)
+            if (bn[q] == 0.0) active[q] = incycle[q] = kk[q] = 0;
+        if (st != BAMG_OK || n_active == 0) break;
+        TRY(upload(h->bactive, active));
+        TRY(upload(h->bincycle, incycle));
+        TRY(launch_seg_init_g(S, m, h->bsq, h->bg, h->bscal, s));
+        TRY(launch_seg_scale(T, h->w, h->bscal, h->V, h->bactive, 0, s));  // v_0 = r / beta per system
+        for (int j = 0; j < m; ++j) {
+            const double* vj = h->V + (size_t)j * N;
+            double* zj = h->Z + (size_t)j * N;
+            TRY(apply_impl(h, vj, zj, s));
+            TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
+            TRY(launch_seg_dots(T, h->w, h->V, N, j + 1, 1, partial, h->bh1, m + 2, s));
+            TRY(launch_seg_axpy_dots(T, h->w, h->V, N, j + 1, h->bh1, m + 2, 1.0, 1, h->bincycle, partial, h->bh2,
+                                     m + 2, s));
+            TRY(launch_seg_axpy_dots(T, h->w, h->V, N, j + 1, h->bh2, m + 2, 1.0, 2, h->bincycle, partial, h->bwsq,
+                                     1, s));
+            TRY(launch_seg_givens(S, j, m, h->bh1, h->bh2, h->bwsq, h->bH, h->bcs, h->bsn, h->bg, h->bscal,
+                                  h->bincycle, s));
+            TRY(launch_seg_scale(T, h->w, h->bscal, h->V + (size_t)(j + 1) * N, h->bincycle, 1, s));
+            TRY(download(h->bscal, h->hb_scal.data(), (size_t)S * 4));
+            int left = 0;
+            for (int q = 0; q < S; ++q) {
+                if (!incycle[q]) continue;
+                kk[q] = j + 1;
+                tot[q]++;
+                const double est = h->hb_scal[(size_t)q * 4 + 1];
+                if (!std::isfinite(est)) st = BAMG_ENAN;
+                if (est / bn[q] <= tol || h->hb_scal[(size_t)q * 4 + 2] != 0.0 || tot[q] >= max_iter) incycle[q] = 0;
+                left += incycle[q];
+            }
+            if (st != BAMG_OK || left == 0) break;
+            TRY(upload(h->bincycle, incycle));
+        }
+        if (st != BAMG_OK) break;
+        TRY(upload(h->bk, kk));
+        TRY(launch_seg_solve_upper(S, m, h->bk, h->bH, h->bg, h->by, s));
+        TRY(launch_seg_axpy_dots(T, x, h->Z, N, m, h->by, m, -1.0, 0, h->bactive, nullptr, nullptr, 0, s));  // x += Z y
+    }
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->release(partial);
+    int all = 1;
+    for (int q = 0; q < S; ++q) {
+        if (iters) iters[q] = tot[q];
+        if (relres) relres[q] = rel[q];
+        all &= conv[q];
+    }
+    if (st != BAMG_OK) return st;
+    return all ? BAMG_OK : BAMG_NOT_CONVERGED;
+}
+
+extern "C" int amg_num_systems(bamg_t h) { return h ? h->nsys : BAMG_EINVAL; }
+
+extern "C" int amg_level_systems(bamg_t h, int level, int* sys_node_off) {
+    if (!h || level < 0 || level >= h->nlev || !sys_node_off) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    for (size_t q = 0; q < L.sys_off.size(); ++q) sys_node_off[q] = L.sys_off[q];
+    return BAMG_OK;
 }
 
 // ---------------------------------------------------------------------------

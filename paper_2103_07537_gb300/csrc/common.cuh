@@ -213,6 +213,43 @@ int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, c
 long scan_tmp_bytes(int n);
 int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);
 
+// ---- batches of independent systems (k_batched.cu) ----
+// chunks of the concatenated vectors: chunk c covers [chunk_e0[c], chunk_e1[c])
+// of system chunk_sys[c]; the chunks of system s are sys_chunk[s] .. sys_chunk[s+1]-1
+struct SegTable {
+    int nsys;
+    int nchunk;
+    const int* chunk_sys;
+    const long* chunk_e0;
+    const long* chunk_e1;
+    const int* sys_chunk;
+};
+// out[s * ldo + v] = x_s . Y_v,s (v < nv) and x_s . x_s at v = nv when want_xx
+int launch_seg_dots(const SegTable& t, const double* x, const double* Y, long ld, int nv, int want_xx,
+                    double* partial, double* out, int ldo, cudaStream_t s);
+// on systems with active[s] (all when active is null): x_s -= sign * sum_v h[s*ldh + v] Y_v,s; then
+// mode 1: out[s*ldo + v] = x_s . Y_v,s, mode 2: out[s*ldo] = x_s . x_s, mode 0: nothing
+int launch_seg_axpy_dots(const SegTable& t, double* x, const double* Y, long ld, int nv, const double* h, int ldh,
+                         double sign, int mode, const int* active, double* partial, double* out, int ldo,
+                         cudaStream_t s);
+int launch_seg_givens(int nsys, int j, int m, const double* h1, const double* h2, const double* wsq, double* H,
+                      double* cs, double* sn, double* g, double* scal, const int* incycle, cudaStream_t s);
+int launch_seg_scale(const SegTable& t, const double* x, const double* scal, double* y, const int* on,
+                     int check_breakdown, cudaStream_t s);
+int launch_seg_init_g(int nsys, int m, const double* bsq, double* g, double* scal, cudaStream_t s);
+int launch_seg_solve_upper(int nsys, int m, const int* k, const double* H, const double* g, double* y,
+                           cudaStream_t s);
+int batched_lu_inverse(int nsys, int b, int max_nd, const int* node_off, const long* inv_off, const int* rp,
+                       const int* ci, const double* vals, double* work, double* inv, int* piv, double* col, int* err,
+                       cudaStream_t s);
+template <typename T>
+int launch_batched_gemv(int nd_total, int b, const int* row_sys, const int* node_off, const long* inv_off,
+                        const double* inv, const T* x, T* y, cudaStream_t s);
+int launch_check_batch(int n, const int* rp, const int* ci, const int* node_sys, const int* node_off, int* err,
+                       cudaStream_t s);
+int launch_fill_sys(int nsys, const int* node_off, int scale, int* out, cudaStream_t s);
+int launch_coarse_offsets(int nsys, const int* off, const int* rank, int* off_c, cudaStream_t s);
+
 // ---- Krylov kernels (k_krylov.cu) ----
 int krylov_chunks(long N);
 // device pointers of the Arnoldi bookkeeping for step j of FGMRES(m)

@@ -442,3 +442,50 @@ def random_block_system(n_side: int, b: int, field_of_dof, seed: int, d: int = 2
     rhs = uniform_pm1(seed, nnzb * b * b, n * b)
     return BlockSystem(f"random{d}d_{n_side}_b{b}_s{seed}", n, b, row_ptr, col_idx, vals,
                        rhs, list(field_of_dof), dict(kind="random", seed=seed))
+
+
+# ----------------------------------------------------------------------------
+# batches of independent systems
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Batch:
+    """Independent systems concatenated into one block-diagonal BSR system."""
+
+    system: BlockSystem          # the concatenation (global column indices)
+    sys_node_off: np.ndarray     # int32 [nsys + 1]
+    members: list                # the individual BlockSystems
+
+
+def concatenate(systems) -> Batch:
+    b = systems[0].b
+    fm = systems[0].field_of_dof
+    off = [0]
+    rps, cis, vals, rhss = [], [], [], []
+    blk = 0
+    for s in systems:
+        assert s.b == b and s.field_of_dof == fm
+        rps.append(s.row_ptr[:-1].astype(np.int64) + blk)
+        cis.append(s.col_idx.astype(np.int64) + off[-1])
+        vals.append(s.vals)
+        rhss.append(s.rhs)
+        blk += s.nnzb
+        off.append(off[-1] + s.n_nodes)
+    row_ptr = np.concatenate(rps + [np.array([blk])]).astype(np.int32)
+    col_idx = np.concatenate(cis).astype(np.int32)
+    cat = BlockSystem(f"batch{len(systems)}", off[-1], b, row_ptr, col_idx, np.concatenate(vals),
+                      np.concatenate(rhss), list(fm), dict(kind="batch", nsys=len(systems)))
+    return Batch(cat, np.array(off, dtype=np.int32), list(systems))
+
+
+def batch_sizes(nsys: int, seed: int, nmin: int = 16, nmax: int = 160) -> list:
+    """Cells per side of every system, uniform integers in [nmin, nmax]."""
+    u = uniform01(seed, 0, nsys)
+    return [int(nmin + min(int(v * (nmax - nmin + 1)), nmax - nmin)) for v in u]
+
+
+def mhd2d_batch(nsys: int = 256, seed: int = 1, nmin: int = 16, nmax: int = 160) -> Batch:
+    """nsys 4-field systems of uneven sizes (cells per side uniform in
+    [nmin, nmax] from `seed`), system q drawn with seed 1000 * seed + q."""
+    sizes = batch_sizes(nsys, seed, nmin, nmax)
+    return concatenate([mhd2d(N, 1000 * seed + q) for q, N in enumerate(sizes)])

@@ -1,0 +1,104 @@
+"""A batch of independent 4-field systems of uneven sizes solved together
+(one block-diagonal operator, every V-cycle step one launch over all systems)
+against each system solved alone by the FP64 oracle: bit-exact hierarchy per
+system, V-cycle within 1e-12 per system, FGMRES iterations within +-1 per
+system at 1e-8."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07537_gb300 import bamg, problems as P
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make_batch():
+    # sizes chosen so that every system coarsens to the same 4 levels alone
+    return P.concatenate([P.mhd2d(N, 50 + q) for q, N in enumerate([16, 23, 40, 17, 31, 28])])
+
+
+@pytest.fixture(scope="module")
+def batch():
+    bt = make_batch()
+    s = bt.system
+    kw = dict(max_levels=4, max_coarse=0)
+    g = bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(s.col_idx), dev(s.vals.reshape(-1)), s.b,
+                         s.field_of_dof, **kw)
+    orcs = [oracle.Hierarchy.from_system(m, **kw) for m in bt.members]
+    return bt, g, orcs
+
+
+def test_batch_hierarchy_is_per_system_hierarchy(batch):
+    bt, g, orcs = batch
+    assert g.num_systems == len(bt.members)
+    for o in orcs:
+        assert o.num_levels == g.num_levels
+    for l in range(g.num_levels):
+        L = g.level(l)
+        off = g.level_systems(l)
+        for q, o in enumerate(orcs):
+            Lo = o.level(l)
+            n0, n1 = off[q], off[q + 1]
+            assert n1 - n0 == Lo["n"]
+            k0, k1 = L["row_ptr"][n0], L["row_ptr"][n1]
+            assert np.array_equal(L["row_ptr"][n0:n1 + 1] - k0, Lo["row_ptr"])
+            assert np.array_equal(L["col_idx"][k0:k1] - n0, Lo["col_idx"])
+            assert np.array_equal(L["vals"][k0:k1], Lo["vals"])
+            if l < g.num_levels - 1:
+                offc = g.level_systems(l + 1)
+                assert np.array_equal(L["agg"][n0:n1] - offc[q], Lo["agg"])
+                assert np.array_equal(L["colour"][n0:n1], Lo["colour"])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_batch_vcycle_is_per_system_vcycle(batch, prec):
+    bt, g64, orcs = batch
+    s = bt.system
+    g = g64 if prec == 64 else bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(s.col_idx),
+                                                dev(s.vals.reshape(-1)), s.b, s.field_of_dof, max_levels=4,
+                                                max_coarse=0, cycle_prec=32)
+    r = np.random.default_rng(4).standard_normal(s.n_unknowns)
+    z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    g.apply(dev(r), z)
+    torch.cuda.synchronize()
+    zg = z.cpu().numpy()
+    off = bt.sys_node_off * s.b
+    for q, o in enumerate(orcs):
+        zo = o.vcycle(r[off[q]:off[q + 1]])
+        err = np.abs(zg[off[q]:off[q + 1]] - zo).max() / np.abs(zo).max()
+        assert err <= (1e-12 if prec == 64 else 1e-4), (q, err)
+
+
+def test_batch_fgmres_per_system_iterations(batch):
+    bt, g, orcs = batch
+    s = bt.system
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, its, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=3000)
+    assert st == bamg.BAMG_OK
+    xs = x.cpu().numpy()
+    off = bt.sys_node_off * s.b
+    for q, (m, o) in enumerate(zip(bt.members, orcs)):
+        _, it_ref, rr_ref, conv = o.fgmres(m.rhs, tol=1e-8, restart=30, max_iter=3000)
+        assert conv and abs(its[q] - it_ref) <= 1, (q, its[q], it_ref)
+        xq = xs[off[q]:off[q + 1]]
+        true_rel = np.linalg.norm(m.rhs - oracle.spmv(m.row_ptr, m.col_idx, m.vals, xq)) / np.linalg.norm(m.rhs)
+        assert true_rel <= 1e-8 and rr[q] <= 1e-8
+
+
+def test_batch_rejects_coupled_systems():
+    bt = make_batch()
+    s = bt.system
+    ci = s.col_idx.copy()
+    # make the first block of system 1 point into system 0 (keeps ascending order)
+    k = s.row_ptr[bt.sys_node_off[1]]
+    ci[k] = 0
+    with pytest.raises(bamg.BamgError) as e:
+        bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(ci), dev(s.vals.reshape(-1)), s.b, s.field_of_dof,
+                         max_levels=3, max_coarse=0)
+    assert e.value.status == bamg.BAMG_EINVAL
