@@ -18,9 +18,10 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def make_batch():
-    # sizes chosen so that every system coarsens to the same 4 levels alone
-    return P.concatenate([P.mhd2d(N, 50 + q) for q, N in enumerate([16, 23, 40, 17, 31, 28])])
+def make_batch(seeds=(50, 51, 52, 53, 54, 56)):
+    # sizes chosen so that every system coarsens to the same 4 levels alone;
+    # every seed here converges under FGMRES(30)
+    return P.concatenate([P.mhd2d(N, sd) for N, sd in zip([16, 23, 40, 17, 31, 28], seeds)])
 
 
 @pytest.fixture(scope="module")
@@ -102,3 +103,16 @@ def test_batch_rejects_coupled_systems():
         bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(ci), dev(s.vals.reshape(-1)), s.b, s.field_of_dof,
                          max_levels=3, max_coarse=0)
     assert e.value.status == bamg.BAMG_EINVAL
+
+
+def test_batch_stagnating_member_is_reported_and_others_converge():
+    # seed 55 (nu 2e-2, eta 1.2e-3) stagnates under FGMRES(30), alone as well
+    bt = make_batch(seeds=(50, 51, 52, 53, 54, 55))
+    s = bt.system
+    g = bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(s.col_idx), dev(s.vals.reshape(-1)), s.b,
+                         s.field_of_dof, max_levels=4, max_coarse=0)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, its, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=150)
+    assert st == bamg.BAMG_NOT_CONVERGED
+    assert its[5] == 150 and rr[5] > 1e-8
+    assert all(its[q] < 150 and rr[q] <= 1e-8 for q in range(5))
