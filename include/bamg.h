@@ -66,6 +66,9 @@ typedef struct {
     int tail_dofs;    /* levels whose n_nodes*b is at most this (and every level below them) run
                          as one thread-block-cluster launch per V-cycle; 0 = one launch per
                          step on every level; default 0                                        */
+    int autotune;     /* row mapping of the smoother and SpMV kernels: 1 = time warp-per-row and
+                         thread-per-row on every level at setup and keep the faster (default);
+                         0 = warp-per-row everywhere; 2 = thread-per-row everywhere             */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64). */

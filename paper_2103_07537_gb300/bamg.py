@@ -36,7 +36,8 @@ _lib = None
 
 class AmgParams(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
-                ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int), ("tail_dofs", C.c_int)]
+                ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int), ("tail_dofs", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class BamgError(RuntimeError):

@@ -106,6 +106,8 @@ struct Level {
     int *agg = nullptr, *agg_ptr = nullptr, *members = nullptr;
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
+    int bgs_tpr = 0, spmv_tpr = 0;  // row mapping chosen for this level (1: thread per row)
+    float tune_us[4] = {0, 0, 0, 0};  // measured: smoother warp / thread, residual warp / thread
     // node range of every system of a batch on this level (host and device)
     std::vector<int> sys_off;
     int* sys_off_d = nullptr;
@@ -143,6 +145,7 @@ bool supported_block(int b, int fb) {
 
 struct bamg_ctx {
     int b = 0, F = 1, fb = 0, nlev = 0;
+    int outer_spmv_tpr = 0;  // row mapping of the FP64 outer SpMV
     int nsys = 1;  // independent systems solved together (block-diagonal operator)
     // coarsest level of a batch: one dense inverse per system
     long* inv_off_d = nullptr;
@@ -310,6 +313,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->cycle_prec = 64;
     p->use_graph = 1;
     p->tail_dofs = 0;
+    p->autotune = 1;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -336,6 +340,96 @@ static int record_tail(bamg_ctx* h, cudaStream_t s, bool only_counts);
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+template <typename T>
+static const T* level_vals(const Level& L);
+template <>
+const double* level_vals<double>(const Level& L) { return L.vals64; }
+template <>
+const float* level_vals<float>(const Level& L) { return L.vals32; }
+template <typename T>
+static const T* level_dinv(const Level& L);
+template <>
+const double* level_dinv<double>(const Level& L) { return L.dinv64; }
+template <>
+const float* level_dinv<float>(const Level& L) { return L.dinv32; }
+
+// average device time (us) of `reps` launches of f after one warm-up launch
+template <class F>
+static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& f) {
+    if (f() != BAMG_OK) return 1e30f;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r)
+        if (f() != BAMG_OK) return 1e30f;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return 1e3f * ms / reps;
+}
+
+// Autotuner: per level, time the warp-per-row and thread-per-row mappings of
+// the smoother (first colour, first field) and of the residual SpMV on the
+// level's own operator, and keep the faster; likewise for the FP64 outer SpMV.
+template <typename T>
+static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    BAMG_CUDA_TRY(cudaEventCreate(&e0));
+    BAMG_CUDA_TRY(cudaEventCreate(&e1));
+    const int b = h->b;
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+        Level& L = h->lev[l];
+        const size_t nb = (size_t)L.n * b;
+        BAMG_CUDA_TRY(cudaMemsetAsync(L.xa, 0, nb * sizeof(T), s));
+        BAMG_CUDA_TRY(cudaMemsetAsync(L.res, 0, nb * sizeof(T), s));
+        BAMG_CUDA_TRY(cudaMemsetAsync(L.xt, 0, (size_t)L.n * h->fb * sizeof(T), s));
+        BgsArgs a;
+        a.n_in_colour = L.colour_ptr[1] - L.colour_ptr[0];
+        a.nodes = L.colour_nodes;
+        a.colour = 0;
+        a.colours = L.colour;
+        a.rp = L.rp;
+        a.ci = L.ci;
+        a.vals = level_vals<T>(L);
+        a.dinv = level_dinv<T>(L);
+        a.rhs = L.res;
+        a.x_in = L.xa;
+        a.x_out = L.xb;
+        a.xt = L.xt;
+        a.uc = nullptr;
+        a.agg = nullptr;
+        a.field = 0;
+        a.F = h->F;
+        a.omega = h->p.omega;
+        const int reps = 3;
+        L.tune_us[0] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
+        L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s); });
+        const T* x = static_cast<const T*>(L.xa);
+        const T* r = static_cast<const T*>(L.res);
+        T* y = static_cast<T*>(L.xb);
+        L.tune_us[2] = time_launch(s, e0, e1, reps,
+                                   [&] { return launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
+        L.tune_us[3] = time_launch(
+            s, e0, e1, reps, [&] { return launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
+        L.bgs_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && L.tune_us[1] < L.tune_us[0]);
+        L.spmv_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && L.tune_us[3] < L.tune_us[2]);
+    }
+    {
+        const Level& L0 = h->lev[0];
+        BAMG_CUDA_TRY(cudaMemsetAsync(h->cyc_in, 0, sizeof(double) * (size_t)L0.n * b, s));
+        const float t0 = time_launch(s, e0, e1, 3, [&] {
+            return launch_spmv<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
+        });
+        const float t1 = time_launch(s, e0, e1, 3, [&] {
+            return launch_spmv_tpr<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
+        });
+        h->outer_spmv_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && t1 < t0);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return BAMG_OK;
 }
 
 static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const double* vals, int n,
@@ -596,6 +690,10 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->seg = SegTable{h->nsys, (int)csys.size(), d_csys, d_e0, d_e1, d_sc};
     }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->p.autotune == 1 || h->p.autotune == 2) {
+        if (h->p.cycle_prec == 64) TRY(autotune_levels<double>(h, s));
+        else TRY(autotune_levels<float>(h, s));
+    }
     if (h->nsys == 1) TRY(setup_tail(h, s));
     h->t_phase[6] += ms_since(tp);
     return BAMG_OK;
@@ -618,7 +716,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     if (p) prm = *p;
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
-        !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0)
+        !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
+        prm.autotune < 0 || prm.autotune > 2)
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -679,18 +778,6 @@ extern "C" int amg_destroy(bamg_t h) {
 // ---------------------------------------------------------------------------
 // V-cycle
 // ---------------------------------------------------------------------------
-template <typename T>
-static const T* level_vals(const Level& L);
-template <>
-const double* level_vals<double>(const Level& L) { return L.vals64; }
-template <>
-const float* level_vals<float>(const Level& L) { return L.vals32; }
-template <typename T>
-static const T* level_dinv(const Level& L);
-template <>
-const double* level_dinv<double>(const Level& L) { return L.dinv64; }
-template <>
-const float* level_dinv<float>(const Level& L) { return L.dinv32; }
 
 // A V-cycle step is launched now or, while h->rec is set, appended to the
 // phase list of the cluster tail kernel (with its algorithmic bytes / flops).
@@ -744,7 +831,8 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
             record(h, ph, bytes, flops);
             continue;
         }
-        PL(BAMG_K_SMOOTH, bytes, flops, launch_bgs_colour<T>(h->b, h->fb, a, s));
+        PL(BAMG_K_SMOOTH, bytes, flops,
+           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s) : launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
     return BAMG_OK;
 }
@@ -830,7 +918,8 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         record(h, pr, rst_bytes, nb);
     } else {
         PL(BAMG_K_RESIDUAL, res_bytes, res_flops,
-           launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+           L.spmv_tpr ? launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
+                      : launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
         PL(BAMG_K_RESTRICT, rst_bytes, nb,
            launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     }
@@ -1043,6 +1132,13 @@ static int ensure_krylov(bamg_ctx* h, int m) {
     return BAMG_OK;
 }
 
+// y = A x (or rhs - A x) with the finest FP64 operator, in the tuned row mapping
+static int outer_spmv(bamg_ctx* h, const double* x, const double* rhs, double* y, cudaStream_t s) {
+    const Level& L0 = h->lev[0];
+    return h->outer_spmv_tpr ? launch_spmv_tpr<double>(h->b, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s)
+                             : launch_spmv<double>(h->b, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s);
+}
+
 // ||x||^2 into dst (device), via the deterministic chunked reduction
 static int norm_sq(bamg_ctx* h, long N, const double* x, double* dst, cudaStream_t s) {
     PL(BAMG_K_KRYLOV, N * 8.0, 2.0 * N, launch_multi_dot(N, x, nullptr, 0, 0, 1, h->partial, dst, h->ticket, s));
@@ -1077,7 +1173,7 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
     const double vN = N * 8.0;
     while (!converged) {
         PL(BAMG_K_SPMV, spmv_bytes + vN, spmv_flops,
-           launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
+           outer_spmv(h, x, b, h->w, s));  // w = b - A x
         TRY(norm_sq(h, N, h->w, h->wsq, s));
         BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->wsq, sizeof(double), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1097,7 +1193,7 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             double* zj = h->Z + (size_t)j * N;
             TRY(apply_impl(h, vj, zj, s));
             PL(BAMG_K_SPMV, spmv_bytes, spmv_flops,
-               launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
+               outer_spmv(h, zj, nullptr, h->w, s));
             // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
             const double nv = j + 1;
             GivensArgs ga{j, m, h->h1, h->h2, h->H, h->cs, h->sn, h->g, h->scal};
@@ -1199,7 +1295,7 @@ extern "C" int fgmres_solve_batched(bamg_t h, const double* b, double* x, double
     }
     int st = BAMG_OK;
     for (;;) {
-        TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, x, b, h->w, s));  // w = b - A x
+        TRY(outer_spmv(h, x, b, h->w, s));  // w = b - A x
         TRY(launch_seg_dots(T, h->w, nullptr, 0, 0, 1, partial, h->bsq, 1, s));
         TRY(download(h->bsq, tmp.data(), (size_t)S));
         int n_active = 0;
@@ -1224,7 +1320,7 @@ extern "C" int fgmres_solve_batched(bamg_t h, const double* b, double* x, double
             const double* vj = h->V + (size_t)j * N;
             double* zj = h->Z + (size_t)j * N;
             TRY(apply_impl(h, vj, zj, s));
-            TRY(launch_spmv<double>(bsz, L0.n, L0.rp, L0.ci, L0.vals64, zj, nullptr, h->w, s));
+            TRY(outer_spmv(h, zj, nullptr, h->w, s));
             TRY(launch_seg_dots(T, h->w, h->V, N, j + 1, 1, partial, h->bh1, m + 2, s));
             TRY(launch_seg_axpy_dots(T, h->w, h->V, N, j + 1, h->bh1, m + 2, 1.0, 1, h->bincycle, partial, h->bh2,
                                      m + 2, s));
@@ -1383,7 +1479,11 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
         o += "{\"n\":" + std::to_string(L.n) + ",\"nnzb\":" + std::to_string(L.nnzb) +
              ",\"colours\":" + std::to_string(L.n_colours) + ",\"aggregates\":" + std::to_string(L.n_agg) +
              ",\"aggregation_rounds\":" + std::to_string(L.agg_rounds) +
-             ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) + "}";
+             ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
+             ",\"smoother_mapping\":\"" + (L.bgs_tpr ? "thread" : "warp") + "\",\"residual_mapping\":\"" +
+             (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
+             std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
+             std::to_string(L.tune_us[3]) + "]}";
     }
     o += "]}";
     const int len = (int)o.size();

@@ -126,6 +126,12 @@ struct BgsArgs {
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// thread-per-row variants (more loads in flight per warp; for large levels)
+template <typename T>
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s);
+template <typename T>
+int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
+                    cudaStream_t s);
 
 // One recorded step of the V-cycle below the tail level, executed by the
 // cluster tail kernel (see k_solve.cu).

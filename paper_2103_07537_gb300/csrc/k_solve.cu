@@ -353,6 +353,152 @@ template int launch_dense_gemv<double>(int, const double*, const double*, double
 template int launch_dense_gemv<float>(int, const double*, const float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// Thread-per-row variants for large levels.  One thread owns one scalar row
+// and walks the blocks of its block row with the loop unrolled, so every
+// thread keeps several block-row loads in flight (the warp-per-row mapping
+// above keeps one short row per warp in flight, which leaves HBM idle on
+// levels far larger than L2).  The setup autotuner picks the mapping per
+// level and kernel by timing both.
+// ---------------------------------------------------------------------------
+template <typename T, int B>
+__global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restrict__ rp,
+                                                       const int* __restrict__ ci, const T* __restrict__ vals,
+                                                       const T* __restrict__ x, const T* __restrict__ rhs,
+                                                       T* __restrict__ y) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / B);
+    if (i >= n) return;
+    const int r = (int)(t - (long)i * B);
+    const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    T acc = T(0);
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(ci + k);
+        T a[B], xv[B];
+        load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
+        load_row<T, B>(x + (size_t)j * B, xv);
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+    }
+    y[(size_t)i * B + r] = rhs ? rhs[(size_t)i * B + r] - acc : acc;
+}
+
+template <typename T>
+int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
+                    cudaStream_t s) {
+    if (n <= 0) return BAMG_OK;
+    const int blocks = ceil_div((long)n * b, 256);
+    switch (b) {
+#define CASE(BB) \
+    case BB: spmv_tpr_kernel<T, BB><<<blocks, 256, 0, s>>>(n, rp, ci, vals, x, rhs, y); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return launched(1);
+}
+template int launch_spmv_tpr<double>(int, int, const int*, const int*, const double*, const double*,
+                                     const double*, double*, cudaStream_t);
+template int launch_spmv_tpr<float>(int, int, const int*, const int*, const float*, const float*, const float*,
+                                    float*, cudaStream_t);
+
+// threads per CTA: a multiple of both FB and the warp size
+template <int FB>
+struct TprBlock {
+    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
+    static constexpr int kNodes = kThreads / FB;
+};
+
+// One colour of one field step (same arithmetic as bgs_node), FB threads per
+// node; the FB row sums meet in shared memory for the inverse.
+template <typename T, int B, int FB>
+__global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs a) {
+    __shared__ T sh_t[TprBlock<FB>::kNodes * FB];
+    const int tloc = threadIdx.x;
+    const int nloc = tloc / FB;
+    const int r = tloc - nloc * FB;
+    const long q = (long)blockIdx.x * TprBlock<FB>::kNodes + nloc;
+    const bool act = q < a.n_in_colour;
+    const int f0 = a.field * FB;
+    const T* __restrict__ vals = static_cast<const T*>(a.vals);
+    const T* __restrict__ x_in = static_cast<const T*>(a.x_in);
+    const T* __restrict__ uc = static_cast<const T*>(a.uc);
+    const T* __restrict__ xt = static_cast<const T*>(a.xt);
+    int i = 0;
+    T t = T(0);
+    if (act) {
+        i = __ldg(a.nodes + q);
+        const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+        T acc = T(0);
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const int j = __ldg(a.ci + k);
+            T arow[B];
+            load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+            T tv[FB];
+            load_row<T, FB>(xt + (size_t)j * FB, tv);
+            const bool lower = j != i && __ldg(a.colours + j) < a.colour;
+            if (x_in) {
+                T xv[B];
+                load_row<T, B>(x_in + (size_t)j * B, xv);
+                if (uc) {
+                    T pv[B];
+                    load_row<T, B>(uc + (size_t)__ldg(a.agg + j) * B, pv);
+#pragma unroll
+                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
+            }
+            if (lower) {
+#pragma unroll
+                for (int ff = 0; ff < B / FB; ++ff)
+                    if (ff == a.field) {
+#pragma unroll
+                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
+                    }
+            }
+        }
+        t = static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + r] - acc;
+    }
+    sh_t[tloc] = t;
+    __syncthreads();
+    if (!act) return;
+    const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)r * FB;
+    T xn = T(0);
+#pragma unroll
+    for (int c = 0; c < FB; ++c) xn = fma(__ldg(D + c), sh_t[nloc * FB + c], xn);
+    static_cast<T*>(a.xt)[(size_t)i * FB + r] = xn;
+    T* __restrict__ x_out = static_cast<T*>(a.x_out);
+    const T om = T(a.omega);
+    const int ag = (x_in && uc) ? __ldg(a.agg + i) : 0;
+    for (int m = 0; m < a.F; ++m) {
+        const size_t e = (size_t)i * B + m * FB + r;
+        T v = x_in ? x_in[e] : T(0);
+        if (x_in && uc) v += uc[(size_t)ag * B + m * FB + r];
+        if (m == a.field) v = fma(om, xn, v);
+        x_out[e] = v;
+    }
+}
+
+template <typename T>
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s) {
+    if (a.n_in_colour <= 0) return BAMG_OK;
+    switch (b * 16 + fb) {
+#define CASE(BB, FF)                                                                              \
+    case BB * 16 + FF:                                                                            \
+        bgs_tpr_kernel<T, BB, FF><<<ceil_div(a.n_in_colour, TprBlock<FF>::kNodes), TprBlock<FF>::kThreads, 0, s>>>(a); \
+        break;
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return launched(1);
+}
+template int launch_bgs_colour_tpr<double>(int, int, const BgsArgs&, cudaStream_t);
+template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Tail kernel: one thread-block cluster executes a recorded list of V-cycle
 // phases (every colour of every field step, residuals, restrictions, the
 // coarsest solve and the post-smoothing with the fused prolongation) for the

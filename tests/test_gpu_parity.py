@@ -119,11 +119,12 @@ def test_hierarchy_matches_oracle(name):
 # ---------------------------------------------------------------------------
 # V-cycle
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("tail_dofs", [0, 65536])
+@pytest.mark.parametrize("mapping", [dict(tail_dofs=0, autotune=0), dict(tail_dofs=65536, autotune=0),
+                                     dict(tail_dofs=0, autotune=2)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_vcycle_fp64_matches_oracle(name, tail_dofs):
+def test_vcycle_fp64_matches_oracle(name, mapping):
     s, kw = SYSTEMS[name]()
-    g = make_solver(s, tail_dofs=tail_dofs, **kw)
+    g = make_solver(s, **mapping, **kw)
     o = make_oracle(s, **kw)
     r = np.random.default_rng(7).standard_normal(s.n_unknowns)
     z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
@@ -151,9 +152,10 @@ def test_vcycle_variants_match_oracle(variant):
 @pytest.mark.parametrize("name", ["stokes2d_32", "mhd2d_41_ragged", "stokes3d_9", "poisson_b2"])
 def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
     s, kw = SYSTEMS[name]()
-    with_tail = make_solver(s, tail_dofs=1 << 30, cycle_prec=prec, **kw)  # every level in the tail
-    some_tail = make_solver(s, tail_dofs=2000, cycle_prec=prec, **kw)
-    no_tail = make_solver(s, tail_dofs=0, cycle_prec=prec, **kw)
+    # the tail replays the warp-per-row device functions: compare with that mapping
+    with_tail = make_solver(s, tail_dofs=1 << 30, cycle_prec=prec, autotune=0, **kw)  # every level in the tail
+    some_tail = make_solver(s, tail_dofs=2000, cycle_prec=prec, autotune=0, **kw)
+    no_tail = make_solver(s, tail_dofs=0, cycle_prec=prec, autotune=0, **kw)
     assert with_tail.stats()["tail_level"] == 0 and no_tail.stats()["tail_level"] == -1
     r = dev(np.random.default_rng(3).standard_normal(s.n_unknowns))
     outs = []
@@ -165,11 +167,31 @@ def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
     assert torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2])
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_row_mappings_agree_and_solve(prec):
+    # warp-per-row and thread-per-row kernels: same cycle up to summation order
+    s, kw = SYSTEMS["mhd2d_41_ragged"]()
+    gw = make_solver(s, autotune=0, cycle_prec=prec, **kw)
+    gt = make_solver(s, autotune=2, cycle_prec=prec, **kw)
+    st = gt.stats()["levels"]
+    assert all(lv["smoother_mapping"] == "thread" for lv in st[:-1])
+    r = dev(np.random.default_rng(9).standard_normal(s.n_unknowns))
+    zw, zt = torch.empty_like(r), torch.empty_like(r)
+    gw.apply(r, zw)
+    gt.apply(r, zt)
+    torch.cuda.synchronize()
+    tol = 1e-12 if prec == 64 else 1e-5
+    assert float((zw - zt).abs().max() / zw.abs().max()) <= tol
+    x = torch.zeros_like(r)
+    status, it, rr = gt.solve(r, x, tol=1e-8, restart=10, max_iter=2000)
+    assert status == bamg.BAMG_OK and rr <= 1e-8
+
+
 def test_vcycle_graph_and_direct_launch_agree_bitwise_and_repeat():
     s = P.mhd2d(20, 5)
     kw = dict(max_levels=3, max_coarse=0)
-    g1 = make_solver(s, use_graph=1, **kw)
-    g0 = make_solver(s, use_graph=0, **kw)
+    g1 = make_solver(s, use_graph=1, autotune=0, **kw)
+    g0 = make_solver(s, use_graph=0, autotune=0, **kw)
     r = dev(s.rhs)
     z1 = torch.empty_like(r)
     z2 = torch.empty_like(r)
@@ -233,6 +255,7 @@ def test_fp32_cycle_reaches_fp64_residual():
 
 def test_host_entry_point_matches_device_path():
     s, kw = SYSTEMS["mhd2d_16"]()
+    kw = dict(kw, autotune=0)  # both paths with the same row mapping: bitwise equal results
     g = make_solver(s, **kw)
     x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
     st, it, rr = g.solve(dev(s.rhs), x)
