@@ -14,6 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bamg_oracle.c")
+_SRC2 = os.path.join(_HERE, "learned_oracle.c")
 _HDR = os.path.join(_HERE, "bamg_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libbamg_oracle.so")
@@ -26,11 +27,11 @@ OK, EINVAL, ENOMEM, ESINGULAR_BLOCK, ESINGULAR_COARSE, NOT_CONVERGED = 0, -1, -2
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, no fused multiply-add)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest_src = max(os.path.getmtime(f) for f in (_SRC, _SRC2, _HDR))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest_src:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, _SRC, _SRC2, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -51,7 +52,14 @@ _dp = C.POINTER(C.c_double)
 
 class Params(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int),
-                ("n_post", C.c_int), ("omega", C.c_double)]
+                ("n_post", C.c_int), ("omega", C.c_double), ("smooth_p", C.c_int), ("omega_p", C.c_double),
+                ("omega_s_arr", _dp), ("omega_s_len", C.c_longlong), ("omega_p_arr", _dp),
+                ("omega_p_len", C.c_longlong), ("mlp", _dp)]
+
+
+NFEAT, MLP_H, MLP_OUT = 8, 64, 2
+MLP_NTRAIN = MLP_H * NFEAT + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
+MLP_NPARAMS = MLP_NTRAIN + 2 * NFEAT
 
 
 def _declare(L):
@@ -72,6 +80,17 @@ def _declare(L):
     L.oracle_bgs.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_int]
     L.oracle_vcycle.argtypes = [C.c_void_p, _dp, _dp]
     L.oracle_fgmres.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_int, C.c_int, C.c_int, _ip, _dp]
+    L.oracle_prolongator.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, _ip, C.c_int, _dp, _ip, _ip, _dp]
+    L.oracle_rap_general.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, C.c_int, _ip, _ip, _dp, _ip, _ip, _dp]
+    L.oracle_level_p_nnz.argtypes = [C.c_void_p, C.c_int]
+    L.oracle_level_get_p.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _dp]
+    L.oracle_level_omega.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+    L.oracle_features.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, _ip, C.c_int, C.c_int, _dp, _dp]
+    L.oracle_mlp_forward.argtypes = [_dp, _dp, C.c_int, _dp]
+    L.oracle_mlp_grad.argtypes = [_dp, _dp, _dp, _ip, C.c_int, _dp, _dp]
+    L.oracle_adam.argtypes = [_dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.oracle_mlp_clip.argtypes = [C.c_int, C.c_double]
+    L.oracle_mlp_clip.restype = C.c_double
 
 
 def _i(a):
@@ -142,6 +161,95 @@ def rap_tentative(row_ptr, col_idx, vals, b, agg, nc):
     return rpc, cic, vc
 
 
+def _fields(field_of_dof):
+    fm = _int32(field_of_dof)
+    F = int(fm.max()) + 1
+    return fm, F, fm.size // F
+
+
+def prolongator(row_ptr, col_idx, vals, field_of_dof, agg, nc, omega_p):
+    """Smoothed prolongator: (p_rp, p_ci, p_v[nnz, F, fb, fb]); omega_p[nc, F]."""
+    rp, ci, v, ag = _int32(row_ptr), _int32(col_idx), _f64(vals), _int32(agg)
+    fm, F, fb = _fields(field_of_dof)
+    n, b = rp.shape[0] - 1, fm.size
+    om = _f64(np.broadcast_to(np.asarray(omega_p, dtype=np.float64), (nc, F)))
+    prp = np.zeros(n + 1, np.int32)
+    nnz = lib().oracle_prolongator(n, b, _i(fm), _i(rp), _i(ci), _d(v), _i(ag), nc, _d(om), _i(prp), None, None)
+    if nnz < 0:
+        raise OracleError(nnz, "prolongator symbolic")
+    pci = np.zeros(nnz, np.int32)
+    pv = np.zeros((nnz, F, fb, fb))
+    st = lib().oracle_prolongator(n, b, _i(fm), _i(rp), _i(ci), _d(v), _i(ag), nc, _d(om), _i(prp), _i(pci),
+                                  _d(pv))
+    if st < 0:
+        raise OracleError(st, "prolongator")
+    return prp, pci, pv
+
+
+def rap_general(row_ptr, col_idx, vals, field_of_dof, nc, p_rp, p_ci, p_v):
+    """A_c = P^T A P with a field-block-diagonal P: (rp_c, ci_c, vals_c[nnz, b, b])."""
+    rp, ci, v = _int32(row_ptr), _int32(col_idx), _f64(vals)
+    fm, F, fb = _fields(field_of_dof)
+    prp, pci, pv = _int32(p_rp), _int32(p_ci), _f64(p_v)
+    n, b = rp.shape[0] - 1, fm.size
+    rpc = np.zeros(nc + 1, np.int32)
+    nnz = lib().oracle_rap_general(n, b, _i(fm), _i(rp), _i(ci), _d(v), nc, _i(prp), _i(pci), _d(pv), _i(rpc),
+                                   None, None)
+    if nnz < 0:
+        raise OracleError(nnz, "rap_general symbolic")
+    cic = np.zeros(nnz, np.int32)
+    vc = np.zeros((nnz, b, b))
+    st = lib().oracle_rap_general(n, b, _i(fm), _i(rp), _i(ci), _d(v), nc, _i(prp), _i(pci), _d(pv), _i(rpc),
+                                  _i(cic), _d(vc))
+    if st < 0:
+        raise OracleError(st, "rap_general")
+    return rpc, cic, vc
+
+
+def features(row_ptr, col_idx, vals, field_of_dof, agg, nc, level):
+    """(node_feat[n, F, NFEAT], agg_feat[nc, F, NFEAT])."""
+    rp, ci, v, ag = _int32(row_ptr), _int32(col_idx), _f64(vals), _int32(agg)
+    fm, F, _ = _fields(field_of_dof)
+    n = rp.shape[0] - 1
+    nf = np.zeros((n, F, NFEAT))
+    af = np.zeros((nc, F, NFEAT))
+    st = lib().oracle_features(n, fm.size, _i(fm), _i(rp), _i(ci), _d(v), _i(ag), nc, level, _d(nf), _d(af))
+    if st:
+        raise OracleError(st, "features")
+    return nf, af
+
+
+def mlp_forward(params, x):
+    p, x = _f64(params), _f64(x).reshape(-1, NFEAT)
+    assert p.size == MLP_NPARAMS
+    y = np.zeros((x.shape[0], MLP_OUT))
+    lib().oracle_mlp_forward(_d(p), _d(x), x.shape[0], _d(y))
+    return y
+
+
+def mlp_grad(params, x, t, head):
+    """(loss, grad[MLP_NTRAIN]) of the mean squared error of the selected heads."""
+    p, x, t, hd = _f64(params), _f64(x).reshape(-1, NFEAT), _f64(t), _int32(head)
+    assert p.size == MLP_NPARAMS and t.size == x.shape[0] == hd.size
+    g = np.zeros(MLP_NTRAIN)
+    loss = C.c_double()
+    st = lib().oracle_mlp_grad(_d(p), _d(x), _d(t), _i(hd), x.shape[0], _d(g), C.byref(loss))
+    if st:
+        raise OracleError(st, "mlp_grad")
+    return loss.value, g
+
+
+def adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on params[:MLP_NTRAIN], m, v (float64 arrays)."""
+    st = lib().oracle_adam(_d(params), _d(_f64(grad)), _d(m), _d(v), t, lr, beta1, beta2, eps)
+    if st:
+        raise OracleError(st, "adam")
+
+
+def mlp_clip(head, w):
+    return np.vectorize(lambda z: lib().oracle_mlp_clip(head, float(z)))(np.asarray(w, dtype=np.float64))
+
+
 def block_inverse(a):
     a = _f64(a)
     m = a.shape[0]
@@ -173,14 +281,26 @@ class Hierarchy:
     """The oracle's AMG hierarchy for one block system."""
 
     def __init__(self, row_ptr, col_idx, vals, b, field_of_dof, max_levels=10, max_coarse=2500,
-                 n_pre=1, n_post=1, omega=0.5):
+                 n_pre=1, n_post=1, omega=0.5, smooth_p=0, omega_p=0.0, omega_s_arr=None, omega_p_arr=None,
+                 mlp=None):
         self.rp, self.ci, self.v = _int32(row_ptr), _int32(col_idx), _f64(vals)
         self.b = int(b)
         self.n = self.rp.shape[0] - 1
         fm = _int32(field_of_dof)
         self.F = int(fm.max()) + 1
         self.fb = self.b // self.F
-        self.params = Params(max_levels, max_coarse, n_pre, n_post, omega)
+        # keep the weight arrays alive for the duration of the setup call
+        self._ws = None if omega_s_arr is None else _f64(omega_s_arr).ravel()
+        self._wp = None if omega_p_arr is None else _f64(omega_p_arr).ravel()
+        self._mlp = None if mlp is None else _f64(mlp).ravel()
+        if self._mlp is not None:
+            assert self._mlp.size == MLP_NPARAMS
+        self.params = Params(max_levels, max_coarse, n_pre, n_post, omega, int(smooth_p), float(omega_p),
+                             None if self._ws is None else _d(self._ws),
+                             0 if self._ws is None else self._ws.size,
+                             None if self._wp is None else _d(self._wp),
+                             0 if self._wp is None else self._wp.size,
+                             None if self._mlp is None else _d(self._mlp))
         h = C.c_void_p()
         st = lib().oracle_setup(self.n, self.ci.shape[0], self.b, _i(self.rp), _i(self.ci), _d(self.v),
                                 _i(fm), C.byref(self.params), C.byref(h))
@@ -225,6 +345,30 @@ class Hierarchy:
                                _d(dinv) if dinv is not None else None)
         return dict(n=n, nnzb=nnz, n_colours=ncol, n_agg=nagg, row_ptr=rp, col_idx=ci, vals=v,
                     agg=agg, colour=col, dinv=dinv)
+
+    def prolongator(self, l):
+        """(p_rp, p_ci, p_v[nnz, F, fb, fb]) of a level coarsened with smooth_p = 1."""
+        n = self.level_sizes(l)[0]
+        nnz = lib().oracle_level_p_nnz(self._h, l)
+        if nnz <= 0:
+            raise OracleError(nnz, "level_p")
+        prp = np.zeros(n + 1, np.int32)
+        pci = np.zeros(nnz, np.int32)
+        pv = np.zeros((nnz, self.F, self.fb, self.fb))
+        st = lib().oracle_level_get_p(self._h, l, _i(prp), _i(pci), _d(pv))
+        if st:
+            raise OracleError(st, "level_get_p")
+        return prp, pci, pv
+
+    def omega(self, l):
+        """(omega_s[n, F], omega_p[n_agg, F]) of a level with a smoother."""
+        n, _, _, nagg = self.level_sizes(l)
+        ws = np.zeros((n, self.F))
+        wp = np.zeros((max(nagg, 0), self.F))
+        st = lib().oracle_level_omega(self._h, l, _d(ws), _d(wp))
+        if st:
+            raise OracleError(st, "level_omega")
+        return ws, wp
 
     def bgs(self, l, x, rhs, sweeps=1):
         x = _f64(x).copy()

@@ -236,6 +236,292 @@ int oracle_rap_tentative(int n, int b, const int* row_ptr, const int* col_idx, c
 }
 
 /* ------------------------------------------------------------------------ */
+/* Smoothed transfers (beyond the paper, whose P is the tentative one).     */
+/* Per field f the prolongator is P_f = (I - W_f D_ff^{-1} A_ff) P^_f:      */
+/* the tentative P^_f of the cloned aggregates, smoothed by one damped      */
+/* block-Jacobi step on the field-f block A_ff only, so P keeps the         */
+/* field-block-diagonal form of eq. (blocktransfers).  Entry (i, J):        */
+/*   P_f[i,J] = [J = agg(i)] I - w_{agg(i),f} D_ff,i^{-1} S_f[i,J],         */
+/*   S_f[i,J] = sum over stored j of row i with agg(j) = J of A_ff[i,j]     */
+/* (stored order), D^{-1} S summed over the inner index ascending.          */
+/* ------------------------------------------------------------------------ */
+static int field_layout(int b, const int* fmap, int* F, int* fb, int* fstart) {
+    int nf = 0;
+    if (b < 1 || b > ORACLE_MAX_B || fmap[0] != 0) return ORACLE_EINVAL;
+    for (int d = 0; d < b; ++d) {
+        if (d > 0 && fmap[d] != fmap[d - 1] && fmap[d] != fmap[d - 1] + 1) return ORACLE_EINVAL;
+        if (fmap[d] + 1 > nf) nf = fmap[d] + 1;
+    }
+    if (b % nf) return ORACLE_EINVAL;
+    *F = nf;
+    *fb = b / nf;
+    for (int f = 0; f < nf; ++f) {
+        fstart[f] = -1;
+        int cnt = 0;
+        for (int d = 0; d < b; ++d)
+            if (fmap[d] == f) {
+                if (fstart[f] < 0) fstart[f] = d;
+                cnt++;
+            }
+        if (cnt != *fb) return ORACLE_EINVAL;
+    }
+    return ORACLE_OK;
+}
+
+/* distinct values of list[0..m) ascending, in place; returns the count */
+static int sort_unique(int* list, int m) {
+    if (m == 0) return 0;
+    qsort(list, (size_t)m, sizeof(int), cmp_int);
+    int u = 1;
+    for (int q = 1; q < m; ++q)
+        if (list[q] != list[u - 1]) list[u++] = list[q];
+    return u;
+}
+
+/* position of col in the ascending ci[k0..k1), or -1 */
+static int find_pos(const int* ci, int k0, int k1, int col) {
+    for (int k = k0; k < k1; ++k)
+        if (ci[k] == col) return k;
+    return -1;
+}
+
+int oracle_prolongator(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                       const double* vals, const int* agg, int nc, const double* omega_p, int* p_rp,
+                       int* p_ci, double* p_v) {
+    int F, fb, fstart[ORACLE_MAX_B];
+    if (!p_rp || field_layout(b, field_of_dof, &F, &fb, fstart)) return ORACLE_EINVAL;
+    const size_t bb = (size_t)b * b, pbs = (size_t)F * fb * fb;
+    int maxrow = 1;
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > maxrow) maxrow = row_ptr[i + 1] - row_ptr[i];
+    int* cols = (int*)malloc(sizeof(int) * (size_t)maxrow);
+    if (!cols) return ORACLE_ENOMEM;
+    if (!p_ci) {
+        p_rp[0] = 0;
+        for (int i = 0; i < n; ++i) {
+            int m = 0;
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int J = agg[col_idx[k]];
+                if (J < 0 || J >= nc) {
+                    free(cols);
+                    return ORACLE_EINVAL;
+                }
+                cols[m++] = J;
+            }
+            p_rp[i + 1] = p_rp[i] + sort_unique(cols, m);
+        }
+        free(cols);
+        return p_rp[n];
+    }
+    for (int i = 0; i < n; ++i) {
+        int m = 0;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) cols[m++] = agg[col_idx[k]];
+        m = sort_unique(cols, m);
+        if (m != p_rp[i + 1] - p_rp[i]) {
+            free(cols);
+            return ORACLE_EINVAL;
+        }
+        int kd = find_pos(col_idx, row_ptr[i], row_ptr[i + 1], i);
+        if (kd < 0) {
+            free(cols);
+            return ORACLE_EINVAL;
+        }
+        for (int f = 0; f < F; ++f) {
+            const int f0 = fstart[f];
+            double dblk[ORACLE_MAX_B * ORACLE_MAX_B], dinv[ORACLE_MAX_B * ORACLE_MAX_B];
+            for (int r = 0; r < fb; ++r)
+                for (int c = 0; c < fb; ++c) dblk[r * fb + c] = vals[(size_t)kd * bb + (f0 + r) * b + (f0 + c)];
+            int st = oracle_block_inverse(fb, dblk, dinv);
+            if (st) {
+                free(cols);
+                return st;
+            }
+            const double w = omega_p[(size_t)agg[i] * F + f];
+            for (int q = 0; q < m; ++q) {
+                const int J = cols[q];
+                const size_t K = (size_t)p_rp[i] + q;
+                p_ci[K] = J;
+                double S[ORACLE_MAX_B * ORACLE_MAX_B];
+                for (int e = 0; e < fb * fb; ++e) S[e] = 0.0;
+                for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                    if (agg[col_idx[k]] != J) continue;
+                    for (int r = 0; r < fb; ++r)
+                        for (int c = 0; c < fb; ++c) S[r * fb + c] += vals[(size_t)k * bb + (f0 + r) * b + (f0 + c)];
+                }
+                double* P = p_v + K * pbs + (size_t)f * fb * fb;
+                for (int r = 0; r < fb; ++r)
+                    for (int c = 0; c < fb; ++c) {
+                        double t = 0.0;
+                        for (int s = 0; s < fb; ++s) t += dinv[r * fb + s] * S[s * fb + c];
+                        const double delta = (J == agg[i] && r == c) ? 1.0 : 0.0;
+                        P[r * fb + c] = delta - w * t;
+                    }
+            }
+        }
+    }
+    free(cols);
+    return p_rp[n];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Galerkin product A_c = P^T (A P) with a field-block-diagonal P (Sec. 3). */
+/*   (A P)[i,J] = sum over stored j of row i (stored order), then over the  */
+/*                stored J of P's row j, of A[i,j] P[j,J];                  */
+/*   A_c[I,J]   = sum over fine i ascending with P[i,I] stored, then over   */
+/*                the stored J of (AP)'s row i, of P[i,I]^T (A P)[i,J];     */
+/* each block product sums over the inner field index ascending.  Patterns: */
+/* the structural unions, ascending.                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int *rp, *ci;
+    double* v;
+} obsr;
+
+/* A P: pattern and values (b x b blocks) */
+static int product_ap(int n, int b, int F, int fb, const int* fstart, const int* fmap, const int* rp,
+                      const int* ci, const double* vals, int nc, const int* p_rp, const int* p_ci,
+                      const double* p_v, obsr* ap) {
+    const size_t bb = (size_t)b * b, pbs = (size_t)F * fb * fb;
+    (void)nc;
+    int maxc = 1;
+    for (int i = 0; i < n; ++i) {
+        int c = 0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) c += p_rp[ci[k] + 1] - p_rp[ci[k]];
+        if (c > maxc) maxc = c;
+    }
+    int* cols = (int*)malloc(sizeof(int) * (size_t)maxc);
+    ap->rp = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+    if (!cols || !ap->rp) return ORACLE_ENOMEM;
+    ap->rp[0] = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            ap->ci = (int*)malloc(sizeof(int) * (size_t)(ap->rp[n] > 0 ? ap->rp[n] : 1));
+            ap->v = (double*)calloc((size_t)(ap->rp[n] > 0 ? ap->rp[n] : 1) * bb, sizeof(double));
+            if (!ap->ci || !ap->v) return ORACLE_ENOMEM;
+        }
+        for (int i = 0; i < n; ++i) {
+            int m = 0;
+            for (int k = rp[i]; k < rp[i + 1]; ++k)
+                for (int q = p_rp[ci[k]]; q < p_rp[ci[k] + 1]; ++q) cols[m++] = p_ci[q];
+            m = sort_unique(cols, m);
+            if (pass == 0) {
+                ap->rp[i + 1] = ap->rp[i] + m;
+                continue;
+            }
+            memcpy(ap->ci + ap->rp[i], cols, sizeof(int) * (size_t)m);
+            for (int k = rp[i]; k < rp[i + 1]; ++k) {
+                const int j = ci[k];
+                const double* A = vals + (size_t)k * bb;
+                for (int q = p_rp[j]; q < p_rp[j + 1]; ++q) {
+                    const int pos = find_pos(ap->ci, ap->rp[i], ap->rp[i + 1], p_ci[q]);
+                    double* out = ap->v + (size_t)pos * bb;
+                    const double* P = p_v + (size_t)q * pbs;
+                    for (int r = 0; r < b; ++r)
+                        for (int c = 0; c < b; ++c) {
+                            const int g = fmap[c], g0 = fstart[g], cl = c - g0;
+                            double t = 0.0;
+                            for (int s = 0; s < fb; ++s) t += A[r * b + g0 + s] * P[(size_t)g * fb * fb + s * fb + cl];
+                            out[r * b + c] += t;
+                        }
+                }
+            }
+        }
+    }
+    free(cols);
+    return ORACLE_OK;
+}
+
+/* transpose pattern of P: for every coarse I the positions q of P's stored
+ * (i, I), i ascending */
+static int transpose_p(int n, int nc, const int* p_rp, const int* p_ci, int** r_rp, int** r_q, int** r_i) {
+    int* rr = (int*)calloc((size_t)nc + 1, sizeof(int));
+    const int nnz = p_rp[n];
+    int* rq = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int* ri = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int* fill = (int*)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    if (!rr || !rq || !ri || !fill) return ORACLE_ENOMEM;
+    for (int q = 0; q < nnz; ++q) rr[p_ci[q] + 1]++;
+    for (int I = 0; I < nc; ++I) rr[I + 1] += rr[I];
+    for (int I = 0; I < nc; ++I) fill[I] = rr[I];
+    for (int i = 0; i < n; ++i)
+        for (int q = p_rp[i]; q < p_rp[i + 1]; ++q) {
+            const int p = fill[p_ci[q]]++;
+            rq[p] = q;
+            ri[p] = i;
+        }
+    free(fill);
+    *r_rp = rr;
+    *r_q = rq;
+    *r_i = ri;
+    return ORACLE_OK;
+}
+
+int oracle_rap_general(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                       const double* vals, int nc, const int* p_rp, const int* p_ci, const double* p_v,
+                       int* rp_c, int* ci_c, double* vals_c) {
+    int F, fb, fstart[ORACLE_MAX_B];
+    if (!rp_c || field_layout(b, field_of_dof, &F, &fb, fstart)) return ORACLE_EINVAL;
+    const size_t bb = (size_t)b * b, pbs = (size_t)F * fb * fb;
+    obsr ap = {0, 0, 0};
+    int st = product_ap(n, b, F, fb, fstart, field_of_dof, row_ptr, col_idx, vals, nc, p_rp, p_ci, p_v, &ap);
+    if (st) return st;
+    int *r_rp, *r_q, *r_i;
+    st = transpose_p(n, nc, p_rp, p_ci, &r_rp, &r_q, &r_i);
+    if (st) return st;
+    int maxc = 1;
+    for (int I = 0; I < nc; ++I) {
+        int c = 0;
+        for (int t = r_rp[I]; t < r_rp[I + 1]; ++t) c += ap.rp[r_i[t] + 1] - ap.rp[r_i[t]];
+        if (c > maxc) maxc = c;
+    }
+    int* cols = (int*)malloc(sizeof(int) * (size_t)maxc);
+    if (!cols) return ORACLE_ENOMEM;
+    if (!ci_c) rp_c[0] = 0;
+    else memset(vals_c, 0, sizeof(double) * bb * (size_t)rp_c[nc]);
+    for (int I = 0; I < nc && st == ORACLE_OK; ++I) {
+        int m = 0;
+        for (int t = r_rp[I]; t < r_rp[I + 1]; ++t)
+            for (int a = ap.rp[r_i[t]]; a < ap.rp[r_i[t] + 1]; ++a) cols[m++] = ap.ci[a];
+        m = sort_unique(cols, m);
+        if (!ci_c) {
+            rp_c[I + 1] = rp_c[I] + m;
+            continue;
+        }
+        if (m != rp_c[I + 1] - rp_c[I]) {
+            st = ORACLE_EINVAL;
+            break;
+        }
+        memcpy(ci_c + rp_c[I], cols, sizeof(int) * (size_t)m);
+        for (int t = r_rp[I]; t < r_rp[I + 1]; ++t) {
+            const int i = r_i[t];
+            const double* P = p_v + (size_t)r_q[t] * pbs;
+            for (int a = ap.rp[i]; a < ap.rp[i + 1]; ++a) {
+                const int pos = find_pos(ci_c, rp_c[I], rp_c[I + 1], ap.ci[a]);
+                double* out = vals_c + (size_t)pos * bb;
+                const double* X = ap.v + (size_t)a * bb;
+                for (int r = 0; r < b; ++r) {
+                    const int f = field_of_dof[r], f0 = fstart[f], rl = r - f0;
+                    for (int c = 0; c < b; ++c) {
+                        double s = 0.0;
+                        for (int u = 0; u < fb; ++u) s += P[(size_t)f * fb * fb + u * fb + rl] * X[(f0 + u) * b + c];
+                        out[r * b + c] += s;
+                    }
+                }
+            }
+        }
+    }
+    free(cols);
+    free(ap.rp);
+    free(ap.ci);
+    free(ap.v);
+    free(r_rp);
+    free(r_q);
+    free(r_i);
+    if (st) return st;
+    return rp_c[nc];
+}
+
+/* ------------------------------------------------------------------------ */
 /* Small dense inverses (node-block diagonal of one field): Gauss-Jordan    */
 /* elimination with partial pivoting on [a | I].                            */
 /* ------------------------------------------------------------------------ */
@@ -348,6 +634,15 @@ typedef struct {
     int* colour;    /* [n] */
     double* dinv;   /* [n][F][fb*fb] */
     double *u, *rhs, *res; /* work vectors of n*b */
+    double* omega_s; /* [n][F] smoother damping of every node and field */
+    double* omega_p; /* [n_agg][F] prolongator smoothing weights (smooth_p) */
+    /* smoothed prolongator (smooth_p): field-block-diagonal blocks, and the
+     * positions of its entries by coarse column (i ascending) for R = P^T */
+    int smoothed; /* this level's P is the smoothed one */
+    int p_nnz;
+    int *p_rp, *p_ci;
+    double* p_v;
+    int *r_rp, *r_q, *r_i;
 } olevel;
 
 struct oracle_hier {
@@ -373,6 +668,86 @@ static void level_free(olevel* L) {
     free(L->u);
     free(L->rhs);
     free(L->res);
+    free(L->omega_s);
+    free(L->omega_p);
+    free(L->p_rp);
+    free(L->p_ci);
+    free(L->p_v);
+    free(L->r_rp);
+    free(L->r_q);
+    free(L->r_i);
+}
+
+/* per-field inverses of the node diagonal blocks of level L */
+static int level_dinv(oracle_hier* h, olevel* L) {
+    const int b = h->b, F = h->F, fb = h->fb;
+    const size_t bb = (size_t)b * b;
+    L->dinv = (double*)malloc(sizeof(double) * (size_t)L->n * F * fb * fb);
+    if (!L->dinv) return ORACLE_ENOMEM;
+    for (int i = 0; i < L->n; ++i) {
+        int kd = find_pos(L->col_idx, L->row_ptr[i], L->row_ptr[i + 1], i);
+        if (kd < 0) return ORACLE_EINVAL;
+        for (int f = 0; f < F; ++f) {
+            double blk[ORACLE_MAX_B * ORACLE_MAX_B];
+            int s = h->fstart[f];
+            for (int r = 0; r < fb; ++r)
+                for (int c = 0; c < fb; ++c) blk[r * fb + c] = L->vals[(size_t)kd * bb + (s + r) * b + (s + c)];
+            int st = oracle_block_inverse(fb, blk, L->dinv + ((size_t)i * F + f) * fb * fb);
+            if (st != ORACLE_OK) return st;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* the damping weights of a level that is being coarsened: from the MLP on
+ * the level's features, from the caller's arrays, or the constants */
+static int level_weights(oracle_hier* h, int l, olevel* L, long long* used_s, long long* used_p) {
+    const int F = h->F;
+    const oracle_params* p = &h->p;
+    const size_t ns = (size_t)L->n * F, np = (size_t)L->n_agg * F;
+    L->omega_s = (double*)malloc(sizeof(double) * ns);
+    L->omega_p = (double*)calloc(np > 0 ? np : 1, sizeof(double));
+    if (!L->omega_s || !L->omega_p) return ORACLE_ENOMEM;
+    if (p->mlp) {
+        double* nf = (double*)malloc(sizeof(double) * ns * ORACLE_NFEAT);
+        double* af = (double*)malloc(sizeof(double) * (np > 0 ? np : 1) * ORACLE_NFEAT);
+        double* yn = (double*)malloc(sizeof(double) * ns * ORACLE_MLP_OUT);
+        double* ya = (double*)malloc(sizeof(double) * (np > 0 ? np : 1) * ORACLE_MLP_OUT);
+        if (!nf || !af || !yn || !ya) return ORACLE_ENOMEM;
+        int fmap[ORACLE_MAX_B];
+        for (int d = 0; d < h->b; ++d) fmap[d] = h->field_of_dof[d];
+        int st = oracle_features(L->n, h->b, fmap, L->row_ptr, L->col_idx, L->vals, L->agg, L->n_agg, l, nf, af);
+        if (st == ORACLE_OK) st = oracle_mlp_forward(p->mlp, nf, (int)ns, yn);
+        if (st == ORACLE_OK) st = oracle_mlp_forward(p->mlp, af, (int)np, ya);
+        for (size_t e = 0; e < ns && st == ORACLE_OK; ++e) L->omega_s[e] = oracle_mlp_clip(0, yn[e * ORACLE_MLP_OUT]);
+        /* P is smoothed on this level only where a weight survives the clip */
+        L->smoothed = 0;
+        for (size_t e = 0; e < np && st == ORACLE_OK; ++e) {
+            L->omega_p[e] = oracle_mlp_clip(1, ya[e * ORACLE_MLP_OUT + 1]);
+            if (L->omega_p[e] > 0.0) L->smoothed = 1;
+        }
+        free(nf);
+        free(af);
+        free(yn);
+        free(ya);
+        return st;
+    }
+    L->smoothed = p->smooth_p != 0;
+    if (p->omega_s_arr) {
+        if (*used_s + (long long)ns > p->omega_s_len) return ORACLE_EINVAL;
+        memcpy(L->omega_s, p->omega_s_arr + *used_s, sizeof(double) * ns);
+        *used_s += (long long)ns;
+    } else {
+        for (size_t e = 0; e < ns; ++e) L->omega_s[e] = p->omega;
+    }
+    if (p->smooth_p && p->omega_p_arr) {
+        if (*used_p + (long long)np > p->omega_p_len) return ORACLE_EINVAL;
+        memcpy(L->omega_p, p->omega_p_arr + *used_p, sizeof(double) * np);
+        *used_p += (long long)np;
+    } else if (p->smooth_p) {
+        for (size_t e = 0; e < np; ++e) L->omega_p[e] = p->omega_p;
+    }
+    return ORACLE_OK;
 }
 
 void oracle_free(oracle_hier* h) {
@@ -437,6 +812,8 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     memcpy(L0->vals, vals, sizeof(double) * bb * (size_t)nnzb);
     h->nlev = 1;
     int st = ORACLE_OK;
+    long long used_s = 0, used_p = 0;
+    if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0)) st = ORACLE_EINVAL;
     /* coarsen while n*b > max_coarse and fewer than max_levels levels */
     while (h->nlev < p->max_levels && (long)h->lev[h->nlev - 1].n * b > p->max_coarse) {
         olevel* F_ = &h->lev[h->nlev - 1];
@@ -454,18 +831,61 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
             break;
         }
         F_->n_agg = nc;
+        st = level_dinv(h, F_);
+        if (st == ORACLE_OK) st = level_weights(h, h->nlev - 1, F_, &used_s, &used_p);
+        if (st != ORACLE_OK) break;
         olevel* C = &h->lev[h->nlev];
         C->n = nc;
         C->row_ptr = (int*)malloc(sizeof(int) * (size_t)(nc + 1));
-        int nnzc = oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc,
-                                        C->row_ptr, NULL, NULL);
-        C->nnzb = nnzc;
-        C->col_idx = (int*)malloc(sizeof(int) * (size_t)nnzc);
-        C->vals = (double*)malloc(sizeof(double) * bb * (size_t)nnzc);
-        oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc, C->row_ptr,
-                             C->col_idx, C->vals);
+        if (F_->smoothed) {
+            /* A_c = P^T A P with the smoothed prolongator */
+            F_->p_rp = (int*)malloc(sizeof(int) * (size_t)(F_->n + 1));
+            int nnzp = oracle_prolongator(F_->n, b, h->field_of_dof, F_->row_ptr, F_->col_idx, F_->vals, F_->agg,
+                                          nc, F_->omega_p, F_->p_rp, NULL, NULL);
+            if (nnzp < 0) {
+                st = nnzp;
+                break;
+            }
+            F_->p_nnz = nnzp;
+            F_->p_ci = (int*)malloc(sizeof(int) * (size_t)(nnzp > 0 ? nnzp : 1));
+            F_->p_v = (double*)malloc(sizeof(double) * (size_t)(nnzp > 0 ? nnzp : 1) * F * h->fb * h->fb);
+            nnzp = oracle_prolongator(F_->n, b, h->field_of_dof, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc,
+                                      F_->omega_p, F_->p_rp, F_->p_ci, F_->p_v);
+            if (nnzp < 0) {
+                st = nnzp;
+                break;
+            }
+            st = transpose_p(F_->n, nc, F_->p_rp, F_->p_ci, &F_->r_rp, &F_->r_q, &F_->r_i);
+            if (st) break;
+            int nnzc = oracle_rap_general(F_->n, b, h->field_of_dof, F_->row_ptr, F_->col_idx, F_->vals, nc,
+                                          F_->p_rp, F_->p_ci, F_->p_v, C->row_ptr, NULL, NULL);
+            if (nnzc < 0) {
+                st = nnzc;
+                break;
+            }
+            C->nnzb = nnzc;
+            C->col_idx = (int*)malloc(sizeof(int) * (size_t)(nnzc > 0 ? nnzc : 1));
+            C->vals = (double*)malloc(sizeof(double) * bb * (size_t)(nnzc > 0 ? nnzc : 1));
+            nnzc = oracle_rap_general(F_->n, b, h->field_of_dof, F_->row_ptr, F_->col_idx, F_->vals, nc, F_->p_rp,
+                                      F_->p_ci, F_->p_v, C->row_ptr, C->col_idx, C->vals);
+            if (nnzc < 0) {
+                st = nnzc;
+                break;
+            }
+        } else {
+            int nnzc = oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc,
+                                            C->row_ptr, NULL, NULL);
+            C->nnzb = nnzc;
+            C->col_idx = (int*)malloc(sizeof(int) * (size_t)nnzc);
+            C->vals = (double*)malloc(sizeof(double) * bb * (size_t)nnzc);
+            oracle_rap_tentative(F_->n, b, F_->row_ptr, F_->col_idx, F_->vals, F_->agg, nc, C->row_ptr,
+                                 C->col_idx, C->vals);
+        }
         h->nlev++;
     }
+    if (st == ORACLE_OK && p->mlp == NULL &&
+        ((p->omega_s_arr && used_s != p->omega_s_len) || (p->smooth_p && p->omega_p_arr && used_p != p->omega_p_len)))
+        st = ORACLE_EINVAL;
     if (st != ORACLE_OK) {
         oracle_free(h);
         return st;
@@ -481,24 +901,8 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         if (l == h->nlev - 1) break;
         L->colour = (int*)malloc(sizeof(int) * (size_t)L->n);
         L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
-        L->dinv = (double*)malloc(sizeof(double) * (size_t)L->n * F * h->fb * h->fb);
-        for (int i = 0; i < L->n && st == ORACLE_OK; ++i) {
-            int kd = -1;
-            for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k)
-                if (L->col_idx[k] == i) kd = k;
-            if (kd < 0) {
-                st = ORACLE_EINVAL;
-                break;
-            }
-            for (int f = 0; f < F; ++f) {
-                double blk[ORACLE_MAX_B * ORACLE_MAX_B];
-                int s = h->fstart[f], fb = h->fb;
-                for (int r = 0; r < fb; ++r)
-                    for (int c = 0; c < fb; ++c) blk[r * fb + c] = L->vals[(size_t)kd * bb + (s + r) * b + (s + c)];
-                st = oracle_block_inverse(fb, blk, L->dinv + ((size_t)i * F + f) * fb * fb);
-                if (st != ORACLE_OK) break;
-            }
-        }
+        if (!L->dinv) st = level_dinv(h, L); /* computed while coarsening */
+        if (st != ORACLE_OK) break;
     }
     if (st == ORACLE_OK) {
         h->xt = (double*)calloc(max_n * h->fb, sizeof(double));
@@ -555,6 +959,28 @@ int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, do
     return ORACLE_OK;
 }
 
+int oracle_level_p_nnz(const oracle_hier* h, int l) {
+    if (l < 0 || l >= h->nlev) return ORACLE_EINVAL;
+    return h->lev[l].p_v ? h->lev[l].p_nnz : 0;
+}
+
+int oracle_level_get_p(const oracle_hier* h, int l, int* p_rp, int* p_ci, double* p_v) {
+    if (l < 0 || l >= h->nlev || !h->lev[l].p_v) return ORACLE_EINVAL;
+    const olevel* L = &h->lev[l];
+    if (p_rp) memcpy(p_rp, L->p_rp, sizeof(int) * (size_t)(L->n + 1));
+    if (p_ci) memcpy(p_ci, L->p_ci, sizeof(int) * (size_t)L->p_nnz);
+    if (p_v) memcpy(p_v, L->p_v, sizeof(double) * (size_t)L->p_nnz * h->F * h->fb * h->fb);
+    return ORACLE_OK;
+}
+
+int oracle_level_omega(const oracle_hier* h, int l, double* omega_s, double* omega_p) {
+    if (l < 0 || l >= h->nlev - 1) return ORACLE_EINVAL;
+    const olevel* L = &h->lev[l];
+    if (omega_s) memcpy(omega_s, L->omega_s, sizeof(double) * (size_t)L->n * h->F);
+    if (omega_p) memcpy(omega_p, L->omega_p, sizeof(double) * (size_t)L->n_agg * h->F);
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Damped block Gauss-Seidel smoother, Algorithm 1 (Sec. 4.3.2), for F      */
 /* field blocks.  One sweep visits the fields in order; for field f:        */
@@ -565,7 +991,8 @@ int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, do
 /*     c: x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j));        */
 /*   x_f := x_f + omega x~_f.                                               */
 /* ------------------------------------------------------------------------ */
-int oracle_bgs(oracle_hier* h, int l, double* x, const double* rhs, int sweeps) {
+/* unit_damping: omega = 1 everywhere (used by the training targets) */
+static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int sweeps, int unit_damping) {
     if (l < 0 || l >= h->nlev - 1) return ORACLE_EINVAL;
     olevel* L = &h->lev[l];
     const int b = h->b, F = h->F, fb = h->fb;
@@ -610,12 +1037,18 @@ int oracle_bgs(oracle_hier* h, int l, double* x, const double* rhs, int sweeps) 
                     }
                 }
             }
-            /* damped update of field f */
-            for (int i = 0; i < L->n; ++i)
-                for (int r = 0; r < fb; ++r) x[(size_t)i * b + f0 + r] += h->p.omega * xt[(size_t)i * fb + r];
+            /* damped update of field f, damping omega_{i,f} of node i */
+            for (int i = 0; i < L->n; ++i) {
+                const double om = unit_damping ? 1.0 : L->omega_s[(size_t)i * F + f];
+                for (int r = 0; r < fb; ++r) x[(size_t)i * b + f0 + r] += om * xt[(size_t)i * fb + r];
+            }
         }
     }
     return ORACLE_OK;
+}
+
+int oracle_bgs(oracle_hier* h, int l, double* x, const double* rhs, int sweeps) {
+    return bgs_impl(h, l, x, rhs, sweeps, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -641,12 +1074,47 @@ static int mgv(oracle_hier* h, int l, double* u, const double* rhs) {
         C->rhs[e] = 0.0;
         C->u[e] = 0.0;
     }
-    for (int i = 0; i < L->n; ++i)
-        for (int d = 0; d < b; ++d) C->rhs[(size_t)L->agg[i] * b + d] += L->res[(size_t)i * b + d];
+    if (L->p_v) {
+        /* R r = P^T r: coarse row I sums P_f[i,I]^T r_f,i over i ascending */
+        const int F = h->F, fb = h->fb;
+        const size_t pbs = (size_t)F * fb * fb;
+        for (int I = 0; I < C->n; ++I)
+            for (int t = L->r_rp[I]; t < L->r_rp[I + 1]; ++t) {
+                const int i = L->r_i[t];
+                const double* P = L->p_v + (size_t)L->r_q[t] * pbs;
+                for (int r = 0; r < b; ++r) {
+                    const int f = h->field_of_dof[r], f0 = h->fstart[f], rl = r - f0;
+                    double s = 0.0;
+                    for (int m = 0; m < fb; ++m) s += P[(size_t)f * fb * fb + m * fb + rl] * L->res[(size_t)i * b + f0 + m];
+                    C->rhs[(size_t)I * b + r] += s;
+                }
+            }
+    } else {
+        for (int i = 0; i < L->n; ++i)
+            for (int d = 0; d < b; ++d) C->rhs[(size_t)L->agg[i] * b + d] += L->res[(size_t)i * b + d];
+    }
     st = mgv(h, l + 1, C->u, C->rhs);
     if (st) return st;
-    for (int i = 0; i < L->n; ++i)
-        for (int d = 0; d < b; ++d) u[(size_t)i * b + d] += C->u[(size_t)L->agg[i] * b + d];
+    if (L->p_v) {
+        /* u += P u_c: row i sums P_f[i,J] u_c,J over its stored J ascending */
+        const int F = h->F, fb = h->fb;
+        const size_t pbs = (size_t)F * fb * fb;
+        for (int i = 0; i < L->n; ++i)
+            for (int r = 0; r < b; ++r) {
+                const int f = h->field_of_dof[r], f0 = h->fstart[f], rl = r - f0;
+                double y = 0.0;
+                for (int q = L->p_rp[i]; q < L->p_rp[i + 1]; ++q) {
+                    const double* P = L->p_v + (size_t)q * pbs + (size_t)f * fb * fb;
+                    double s = 0.0;
+                    for (int m = 0; m < fb; ++m) s += P[rl * fb + m] * C->u[(size_t)L->p_ci[q] * b + f0 + m];
+                    y += s;
+                }
+                u[(size_t)i * b + r] += y;
+            }
+    } else {
+        for (int i = 0; i < L->n; ++i)
+            for (int d = 0; d < b; ++d) u[(size_t)i * b + d] += C->u[(size_t)L->agg[i] * b + d];
+    }
     return oracle_bgs(h, l, u, rhs, h->p.n_post);
 }
 
@@ -655,6 +1123,7 @@ int oracle_vcycle(oracle_hier* h, const double* r, double* z) {
     for (size_t e = 0; e < nb; ++e) z[e] = 0.0;
     return mgv(h, 0, z, r);
 }
+
 
 /* ------------------------------------------------------------------------ */
 /* Restarted flexible GMRES (Saad 1993) with right preconditioning:         */

@@ -76,6 +76,27 @@ int oracle_block_inverse(int m, const double* a, double* ainv);
 int oracle_lu_factor(int n, double* a, int* piv);
 int oracle_lu_solve(int n, const double* lu, const int* piv, const double* rhs, double* x);
 
+/* Smoothed prolongator of one level (beyond the paper; the paper's P is
+ * the tentative one).  Per field f, P_f = (I - W_f D_ff^{-1} A_ff) P^_f with
+ * P^ the piecewise-constant prolongator of agg[], D_ff,i the field-f
+ * diagonal sub-block of A[i,i] and W_f = diag over fine nodes i of
+ * omega_p[agg(i)*F + f].  P keeps the field-block-diagonal form of the
+ * transfers (Sec. 4.3.1), so a stored block (i, J) holds F sub-blocks of
+ * fb x fb, field-major, row-major: p_v[(k*F + f)*fb*fb + r*fb + c].
+ * Pattern of row i: the distinct agg(j) over the stored j of row i,
+ * ascending.  Two calls like oracle_rap_tentative (p_ci == NULL: fills
+ * p_rp[n+1], returns nnz). */
+int oracle_prolongator(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                       const double* vals, const int* agg, int nc, const double* omega_p, int* p_rp,
+                       int* p_ci, double* p_v);
+
+/* Galerkin product A_c = P^T A P (Sec. 3) with a field-block-diagonal P in
+ * the layout of oracle_prolongator.  Pattern: the structural union,
+ * ascending.  Two calls (ci_c == NULL: fills rp_c[nc+1], returns nnz). */
+int oracle_rap_general(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                       const double* vals, int nc, const int* p_rp, const int* p_ci, const double* p_v,
+                       int* rp_c, int* ci_c, double* vals_c);
+
 /* ---- hierarchy ---- */
 
 typedef struct {
@@ -84,6 +105,24 @@ typedef struct {
     int n_pre;        /* BGS sweeps before the coarse correction */
     int n_post;       /* BGS sweeps after it */
     double omega;     /* BGS damping */
+    /* ---- beyond the paper: smoothed transfers and per-node damping ---- */
+    int smooth_p;     /* 0: tentative P; 1: P_f = (I - W_f D_ff^{-1} A_ff) P^_f per field */
+    double omega_p;   /* W_f weight of every aggregate when omega_p_arr is NULL */
+    /* per-level weights, consumed level by level from the finest: omega_s_arr
+     * holds n_l*F values (node-major, then field) for every level that gets a
+     * smoother, omega_p_arr n_agg_l*F values for every level that is coarsened.
+     * NULL: omega / omega_p everywhere.  A length that does not match the
+     * hierarchy exactly is ORACLE_EINVAL. */
+    const double* omega_s_arr;
+    long long omega_s_len;
+    const double* omega_p_arr;
+    long long omega_p_len;
+    /* learned weights: MLP parameters (ORACLE_MLP_NPARAMS values) or NULL.
+     * When set, every coarsened level takes omega_s and omega_p from the MLP
+     * applied to its features, clipped by oracle_mlp_clip (overriding the
+     * arrays above and smooth_p); a level smooths P only when some weight
+     * of its aggregates is nonzero after the clip. */
+    const double* mlp;
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
@@ -99,6 +138,14 @@ int oracle_level_sizes(const oracle_hier* h, int l, int* n, int* nnzb, int* n_co
 int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, double* vals,
                      int* agg, int* colour, double* dinv);
 
+/* Smoothed prolongator of level l (levels that were coarsened with
+ * smooth_p = 1): stored blocks, then the copies (any pointer may be NULL). */
+int oracle_level_p_nnz(const oracle_hier* h, int l);
+int oracle_level_get_p(const oracle_hier* h, int l, int* p_rp, int* p_ci, double* p_v);
+/* damping weights of level l: omega_s[n*F] (smoother), omega_p[n_agg*F]
+ * (prolongator smoothing; zeros with smooth_p = 0) */
+int oracle_level_omega(const oracle_hier* h, int l, double* omega_s, double* omega_p);
+
 /* The smoother S on level l applied in place to x for `sweeps` sweeps. */
 int oracle_bgs(oracle_hier* h, int l, double* x, const double* rhs, int sweeps);
 /* z = MGV(0, r, 0): one V-cycle from a zero initial guess. */
@@ -110,6 +157,39 @@ int oracle_vcycle(oracle_hier* h, const double* r, double* z);
  * Returns 0 when converged, ORACLE_NOT_CONVERGED otherwise. */
 int oracle_fgmres(oracle_hier* h, const double* b, double* x, double tol, int restart,
                   int max_iter, int prec, int* iters, double* relres);
+
+/* ---- learned damping (beyond the paper) ---- */
+
+
+#define ORACLE_NFEAT 8
+#define ORACLE_MLP_H 64
+#define ORACLE_MLP_OUT 2
+/* parameters: W1[H][NFEAT], b1[H], W2[H][H], b2[H], W3[OUT][H], b3[OUT]
+ * (trained), then the fixed input normalisation xm[NFEAT], xs[NFEAT] */
+#define ORACLE_MLP_NTRAIN (ORACLE_MLP_H * ORACLE_NFEAT + ORACLE_MLP_H + ORACLE_MLP_H * ORACLE_MLP_H + \
+                           ORACLE_MLP_H + ORACLE_MLP_OUT * ORACLE_MLP_H + ORACLE_MLP_OUT)
+#define ORACLE_MLP_NPARAMS (ORACLE_MLP_NTRAIN + 2 * ORACLE_NFEAT)
+
+/* Features of every node and field of one level (NFEAT per row, rows
+ * node-major then field) and of every aggregate and field (the mean over its
+ * members, ascending).  See the definition in bamg_oracle.c. */
+int oracle_features(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                    const double* vals, const int* agg, int nc, int level, double* node_feat,
+                    double* agg_feat);
+
+/* y[n][OUT] = MLP(x[n][NFEAT]): h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2),
+ * y = W3 h2 + b3, with xh = (x - xm) * xs. */
+int oracle_mlp_forward(const double* params, const double* x, int n, double* y);
+/* loss = (1/n) sum_r (y[r][head[r]] - t[r])^2 and its gradient with respect
+ * to the trained parameters (grad[NTRAIN]). */
+int oracle_mlp_grad(const double* params, const double* x, const double* t, const int* head, int n,
+                    double* grad, double* loss);
+/* one Adam step (step count t >= 1) on the trained parameters */
+int oracle_adam(double* params, const double* grad, double* m, double* v, int t, double lr, double beta1,
+                double beta2, double eps);
+/* the weight ranges: head 0 (smoother damping) [0.05, 1.5]; head 1 (P
+ * smoothing) [0, 1.5], values below 0.05 set to 0 (no smoothing) */
+double oracle_mlp_clip(int head, double w);
 
 #ifdef __cplusplus
 }

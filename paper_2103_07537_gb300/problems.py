@@ -298,7 +298,7 @@ def frozen_field(c: np.ndarray, x: np.ndarray, y: np.ndarray):
 
 
 def mhd2d(N: int = 128, seed: int = 1, nu: float | None = None, eta: float | None = None,
-          eta_range=(1e-3, 1.0), nu_range=(1e-3, 1.0)) -> BlockSystem:
+          eta_range=(1e-3, 1.0), nu_range=(1e-3, 1.0), eta_cells: bool = False) -> BlockSystem:
     """Two-field 2D system with the block structure of the paper's 4x4 MHD
     Jacobian (Sec. 2) grouped into the 2x2 split of Sec. 3.
 
@@ -313,7 +313,10 @@ def mhd2d(N: int = 128, seed: int = 1, nu: float | None = None, eta: float | Non
     pressure pinned at node 0.
 
     Stream layout for ``seed``: [0] nu, [1] eta, [2..17] Fourier
-    coefficients of B0, then the right-hand side (uniform[-1, 1]).
+    coefficients of B0, then the right-hand side (uniform[-1, 1]); with
+    ``eta_cells`` the resistivity of every cell is drawn log-uniformly from
+    ``eta_range`` from the N*N values that follow the right-hand side (cells
+    x-fastest), and tau_psi follows it cell by cell.
     """
     d = 2
     h = 1.0 / N
@@ -337,6 +340,9 @@ def mhd2d(N: int = 128, seed: int = 1, nu: float | None = None, eta: float | Non
     grad = dphi * (2.0 / h)
     K = np.einsum("qla,qma->lm", grad, grad) * jac
     G = -np.einsum("qla,qm->lam", grad, phi) * jac
+    if eta_cells:
+        u = uniform01(seed, rhs_start + (N + 1) ** d * b, N ** d)
+        eta = 10.0 ** (lo + (hi - lo) * u)  # [E], one per cell (x fastest)
     tau_p = h * h / (12.0 * nu)
     tau_s = h * h / (12.0 * eta)
 
@@ -380,8 +386,14 @@ def mhd2d(N: int = 128, seed: int = 1, nu: float | None = None, eta: float | Non
     rhs = uniform_pm1(seed, rhs_start, n * b)
     return BlockSystem(f"mhd2d_{N}_s{seed}", n, b, row_ptr, col_idx, vals, rhs,
                        [0, 0, 0, 1, 1, 1],
-                       dict(kind="mhd2d", N=N, seed=seed, nu=nu, eta=eta, tau_p=tau_p,
-                            tau_psi=tau_s, h=h))
+                       dict(kind="mhd2d", N=N, seed=seed, nu=nu, eta="per-cell" if eta_cells else eta,
+                            tau_p=tau_p, tau_psi="per-cell" if eta_cells else tau_s, h=h))
+
+
+def mhd2d_cells(N: int = 256, seed: int = 1) -> BlockSystem:
+    """The 4-field system with a resistivity drawn per cell, log-uniform in
+    [1e-4, 1] (the workload of the learned damping)."""
+    return mhd2d(N, seed, eta_range=(1e-4, 1.0), eta_cells=True)
 
 
 # ----------------------------------------------------------------------------
@@ -397,6 +409,8 @@ WORKLOADS = {
                       restart=30, cycle="f64"),
     "stokes3d_64": dict(make=lambda seed=1: stokes3d(64, seed), max_levels=10, max_coarse=2500,
                         restart=50, cycle="f32"),
+    "mhd2d_cells_256": dict(make=lambda seed=1: mhd2d_cells(256, seed), max_levels=10, max_coarse=2500,
+                            restart=30, cycle="f32"),
 }
 
 
