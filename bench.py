@@ -62,6 +62,14 @@ WORKLOADS = {
              "nodes, 12 M unknowns), coefficients as the 2D 4-field workload, one block-diagonal operator "
              "(every V-cycle step one launch over all systems, replayed from a CUDA graph), FP32 V(1,1) "
              "inside per-system FP64 FGMRES(30) to 1e-8, at most 400 inner steps per system"),
+    "mhd2d_cells_256": dict(
+        make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d_cells(256, seed),
+        levels=10, max_coarse=2500, restart=30, prec=32, learned=True, cpu_sample_iters=5,
+        desc="2D coupled 4-field Q1 system, 256x256 cells, 66,049 nodes, 396,294 unknowns, resistivity drawn per "
+             "cell log-U[1e-4,1] (viscosity log-U[1e-3,1]); learned damping: network 8-64-64-2 (FP16 weights, "
+             "FP32 arithmetic, trained on 2000 instances of 64^2..128^2 cells) gives the smoother damping per node "
+             "and field and the prolongator smoothing per aggregate and field; FP32 V(1,1) inside FP64 FGMRES(30) "
+             "to 1e-8; variants: the plain hierarchy (omega 0.5, tentative P) in FP64 and FP32"),
     "stokes3d_64": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes3d(64, seed),
         levels=10, max_coarse=2500, restart=50, prec=32, cpu_sample_iters=5,
@@ -80,6 +88,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--weights", default=None, help="damping network parameters (default: the committed file)")
     ap.add_argument("--ref-iters", type=int, default=30,
                     help="reference arm: inner FGMRES steps timed per step (the sample)")
     return ap.parse_args()
@@ -184,11 +193,20 @@ def physical_gpu_index(local):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
+def oracle_mlp(wl):
+    """The learned workloads' network as the oracle reads it (FP16-rounded)."""
+    if not wl.get("learned"):
+        return None
+    from paper_2103_07537_gb300 import learn
+
+    return learn.load_weights(wl.get("weights") or learn.WEIGHTS_PATH).astype(np.float16).astype(np.float64)
+
+
 def oracle_full_solve(sys_, wl):
     import oracle
 
     t0 = time.perf_counter()
-    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl))
     t1 = time.perf_counter()
     _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=wl["restart"], max_iter=wl.get("max_iter", MAX_ITER))
     t2 = time.perf_counter()
@@ -200,7 +218,7 @@ def oracle_sample(sys_, wl, iters):
     import oracle
 
     t0 = time.perf_counter()
-    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"])
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl))
     t1 = time.perf_counter()
     _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=wl["restart"], max_iter=iters)
     t2 = time.perf_counter()
@@ -254,7 +272,15 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     bamg.load()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.weights:
+        wl["weights"] = args.weights
+    learned = bool(wl.get("learned"))
+    weights = None
+    if learned:
+        from paper_2103_07537_gb300 import learn
+
+        weights = learn.load_weights(wl.get("weights") or learn.WEIGHTS_PATH)
     seed = 1 + rank
     batched = bool(wl.get("batched"))
     made = wl["make"](seed)
@@ -271,7 +297,8 @@ def run_ours(args):
     restart = wl["restart"]
     main_prec = wl["prec"]
     other_prec = 32 if main_prec == 64 else 64
-    params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec)
+    params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
+                                       mlp=weights)
 
     def setup(params):
         if batched:
@@ -370,13 +397,38 @@ def run_ours(args):
         st_times.append(e0.elapsed_time(e1))
 
     # --- the other cycle precision (FP32 cycle inside FP64 FGMRES, or FP64 cycle) --
-    params_o = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=other_prec)
+    params_o = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=other_prec,
+                                       mlp=weights)
     step(params_o)
     k_o = max(1, min(args.steps, 5))
     ms_o, (st_o, it_o, rr_o, _) = timed(params_o, k_o)
     variant = {"cycle": (f"fp{other_prec} V-cycle inside fp64 FGMRES (fp64 outer SpMV, Arnoldi, coarse solve)"),
                "value": timed.solved / (ms_o / 1e3), "unit": UNIT, "iterations": it_o, "relres": rr_o,
                "converged": st_o == 0}
+    if learned:
+        variant["cycle"] = f"learned damping, {variant['cycle']}"
+    # --- learned workloads: the plain hierarchy, and the fallback rule --------
+    plain = None
+    if learned:
+        plain = {}
+        for prec in (64, 32):
+            pp = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=prec)
+            step(pp)
+            ms_p, (st_p, it_p, rr_p, _) = timed(pp, k_o)
+            plain[f"fp{prec}"] = {"value": timed.solved / (ms_p / 1e3), "unit": UNIT, "iterations": it_p,
+                                  "relres": rr_p, "converged": st_p == 0,
+                                  "cycle": f"plain hierarchy (omega 0.5, tentative P), fp{prec} V-cycle"}
+        hl = setup(params64)
+        hp = setup(bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec))
+        ch, il, ip = bamg.amg_select(hl, hp, b, TOL, restart, max_iter, stream)
+        lstats = bamg.amg_stats(hl)
+        bamg.amg_destroy(hl)
+        bamg.amg_destroy(hp)
+        plain["fallback"] = {"rule": "amg_select: the plain hierarchy is kept unless the learned one converges in "
+                                     "no more iterations", "choice": "learned" if ch == 0 else "plain",
+                             "iterations_learned": il, "iterations_plain": ip,
+                             "smoothed_p_levels": [lv.get("smoothed_p", 0) for lv in lstats["levels"]]}
+        plain["learned_vs_plain_fp64"] = value / plain["fp64"]["value"] if plain["fp64"]["value"] else None
 
     # --- per-kernel profile pass (events around every launch) --------------------
     kernels = {}
@@ -548,7 +600,8 @@ def run_ours(args):
                 "levels": [lv["n"] for lv in stats["levels"]],
                 "colours": [lv["colours"] for lv in stats["levels"]],
                 "setup_phase_ms": stats.get("setup_phase_ms"),
-                "cycle_prec": main_prec, "variant": variant, "kernels": ksum, "roofline": roofline, "clocks": clocks,
+                "cycle_prec": main_prec, "variant": variant, "plain": plain, "kernels": ksum, "roofline": roofline,
+                "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if pg:

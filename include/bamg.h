@@ -38,6 +38,8 @@
 #ifndef BAMG_H
 #define BAMG_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -69,9 +71,31 @@ typedef struct {
     int autotune;     /* row mapping of the smoother and SpMV kernels: 1 = time warp-per-row and
                          thread-per-row on every level at setup and keep the faster (default);
                          0 = warp-per-row everywhere; 2 = thread-per-row everywhere             */
+    /* ---- beyond the paper: smoothed transfers, per-node damping, learned weights ---- */
+    int smooth_p;     /* 0: tentative P (default); 1: on every coarsened level the smoothed
+                         P_f = (I - W_f D_ff^{-1} A_ff) P^_f per field (see amg_setup)        */
+    double omega_p;   /* W_f of every aggregate when omega_p_arr is NULL; default 0           */
+    /* host arrays read during amg_setup only, consumed level by level from the finest:
+     * omega_s_arr holds n_l*F smoother dampings (node-major, then field) for every level
+     * that gets a smoother, omega_p_arr n_agg_l*F smoothing weights for every coarsened
+     * level (with smooth_p = 1).  NULL: omega / omega_p everywhere.  Lengths that do not
+     * match the hierarchy exactly are BAMG_EINVAL. */
+    const double* omega_s_arr;
+    long long omega_s_len;
+    const double* omega_p_arr;
+    long long omega_p_len;
+    /* learned weights: host, BAMG_MLP_NPARAMS floats (layout at mlp_forward) or NULL.
+     * When set, every coarsened level takes its smoother damping (head 0) and its P
+     * smoothing weights (head 1) from the network applied to the level's features
+     * (amg_features) with FP16 weights, clipped as in mlp_clip; a level smooths P only
+     * when a weight of its aggregates is nonzero after the clip.  Overrides the arrays
+     * above and smooth_p. */
+    const float* mlp;
+    int pr_storage;   /* values of explicit (smoothed) P and R inside an FP32 cycle: 32 (default)
+                         or 16 = BF16 storage, FP32 arithmetic                                 */
 } amg_params;
 
-/* Fills *p with the defaults above (cycle_prec 64). */
+/* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */
 void amg_default_params(amg_params* p);
 
 /*
@@ -88,6 +112,14 @@ void amg_default_params(amg_params* p);
  * row_ptr, col_idx, vals: device, the BSR matrix (read only; may be freed
  *   after the call returns - the hierarchy holds its own copy).
  * n_nodes >= 1, nnzb >= n_nodes, b: see the conventions above.
+ *   With smooth_p = 1 (or learned weights) the prolongator of a coarsened
+ *   level is P_f = (I - W_f D_ff^{-1} A_ff) P^_f for every field f: the
+ *   tentative P^ smoothed by one damped block-Jacobi step on the field block
+ *   A_ff only, so P stays block diagonal across fields; W_f = diag over fine
+ *   nodes i of the weight of agg(i).  Stored block (i, J) has F sub-blocks of
+ *   fb x fb; pattern of row i = the distinct agg(j) over the stored j of row
+ *   i.  R = P^T is stored explicitly, and A_{l+1} = R (A_l P) is a general
+ *   sparse triple product whose patterns are structural unions (no dropping).
  * field_of_dof: host, b entries.  p: host; NULL = defaults.
  * out: host; receives the handle (NULL on failure).
  * Errors: BAMG_EINVAL, BAMG_EUNSUPPORTED, BAMG_ECUDA, BAMG_ESINGULAR_BLOCK,
@@ -206,6 +238,96 @@ int bsr_spmv(const int* row_ptr, const int* col_idx, const double* vals, int n_n
 int amg_colour_noalloc(const int* row_ptr, const int* col_idx, int n_nodes, int* colour, int* n_colours,
                        void* stream);
 
+/* ---- learned damping (beyond the paper: the paper fixes one damping near 0.5,
+ *      Sec. 5, and shows that its value decides convergence for small viscosity) ---- */
+
+#define BAMG_NFEAT 8
+#define BAMG_MLP_H 64
+#define BAMG_MLP_OUT 2
+/* trained parameters: W1[H][NFEAT], b1[H], W2[H][H], b2[H], W3[OUT][H], b3[OUT] */
+#define BAMG_MLP_NTRAIN (BAMG_MLP_H * BAMG_NFEAT + BAMG_MLP_H + BAMG_MLP_H * BAMG_MLP_H + BAMG_MLP_H + \
+                         BAMG_MLP_OUT * BAMG_MLP_H + BAMG_MLP_OUT)
+/* followed by the fixed input normalisation xm[NFEAT], xs[NFEAT] */
+#define BAMG_MLP_NPARAMS (BAMG_MLP_NTRAIN + 2 * BAMG_NFEAT)
+
+/*
+ * amg_features - the network inputs of one level (computed in FP64, stored
+ * FP32).  Node i, field f (Frobenius norms of fb x fb sub-blocks of row i):
+ * d = ||A_ff[i,i]||, o = sum_{j!=i} ||A_ff[i,j]||, c = sum_j sum_{g!=f}
+ * ||A_fg[i,j]||; features: log d, o/d, c/(d+o), log d - mean_g log d_g,
+ * tr(A_ff[i,i])/(sqrt(fb) d), log |agg(i)|, level, f.  Aggregate I, field f:
+ * the mean of its members' rows.
+ * row_ptr, col_idx, vals, agg (n_nodes), node_feat ([n_nodes][F][NFEAT]),
+ * agg_feat ([n_agg][F][NFEAT], may be NULL): device.  field_of_dof: host.
+ * Errors: BAMG_EINVAL (sizes, aggregate ids out of range), BAMG_EUNSUPPORTED
+ * (block layout), BAMG_ESINGULAR_BLOCK (a zero diagonal sub-block), BAMG_ECUDA.
+ */
+int amg_features(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int b,
+                 const int* field_of_dof, const int* agg, int n_agg, int level, float* node_feat,
+                 float* agg_feat, void* stream);
+
+/* params (device, BAMG_MLP_NPARAMS floats) -> params16 (device, FP16 bit patterns, same
+ * count, round to nearest even).  Errors: BAMG_EINVAL (NULL), BAMG_ECUDA. */
+int mlp_pack(const float* params, uint16_t* params16, void* stream);
+
+/*
+ * mlp_forward - y[n][OUT] = MLP(x[n][NFEAT]) with FP16 parameters and FP32
+ * arithmetic: xh = (x - xm) * xs, h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2),
+ * y = W3 h2 + b3.  All pointers device.  n = 0 is a no-op.
+ * Errors: BAMG_EINVAL (n < 0, NULL), BAMG_ECUDA.
+ */
+int mlp_forward(const uint16_t* params16, const float* x, int n, float* y, void* stream);
+
+/*
+ * mlp_grad - loss = (1/n) sum_r (y[r][head[r]] - t[r])^2 over the rows of x
+ * and its gradient grad[BAMG_MLP_NTRAIN] with respect to the trained
+ * parameters, evaluated at the FP16 parameters (FP32 arithmetic; the sum
+ * over rows is deterministic).  All pointers device; loss: 1 float.
+ * Errors: BAMG_EINVAL (n < 1, head outside 0..OUT-1 is not checked), BAMG_ECUDA.
+ */
+int mlp_grad(const uint16_t* params16, const float* x, const float* t, const int* head, int n, float* grad,
+             float* loss, void* stream);
+
+/*
+ * mlp_adam - one Adam step (bias-corrected moments, step count t >= 1) on
+ * the trained parameters of params (FP32 master copy), then params16 =
+ * FP16(params).  params, params16, grad, m, v: device.
+ * Errors: BAMG_EINVAL (t < 1, NULL), BAMG_ECUDA.
+ */
+int mlp_adam(float* params, uint16_t* params16, const float* grad, float* m, float* v, int t, float lr,
+             float beta1, float beta2, float eps, void* stream);
+
+/* the weight ranges applied to the network outputs: head 0 (smoother damping)
+ * [0.05, 1.5]; head 1 (P smoothing) [0, 1.5] with values below 0.05 set to 0 */
+double mlp_clip(int head, double w);
+
+/*
+ * amg_set_omega - replace the smoother damping of level `level` (< levels-1)
+ * by omega_s (device, n_nodes*F doubles, node-major then field); the
+ * hierarchy is otherwise unchanged (used to search dampings without a new
+ * setup).  Errors: BAMG_EINVAL, BAMG_ECUDA.
+ */
+int amg_set_omega(bamg_t h, int level, const double* omega_s, void* stream);
+
+/*
+ * amg_select - the fallback rule of the learned hierarchy: solve A x = b
+ * (device, x0 = 0) with FGMRES preconditioned by each hierarchy (same matrix)
+ * and keep the plain one unless the learned one converges in no more
+ * iterations.  *choice = 0 (learned) or 1 (plain); iters_learned /
+ * iters_plain (host, may be NULL) receive the counts.
+ * Errors: those of fgmres_solve other than BAMG_NOT_CONVERGED; BAMG_EINVAL on
+ * hierarchies of different sizes.
+ */
+int amg_select(bamg_t learned, bamg_t plain, const double* b, double tol, int restart, int max_iter,
+               int* choice, int* iters_learned, int* iters_plain, void* stream);
+
+/* damping weights of level l < levels-1 (host copies): omega_s[n*F],
+ * omega_p[n_agg*F] (zeros on a level with the tentative P); either may be NULL */
+int amg_level_omega(bamg_t h, int level, double* omega_s, double* omega_p);
+/* explicit prolongator of level l (host): *nnz = stored blocks (0: tentative P);
+ * then copies into p_rp[n+1], p_ci[nnz], p_v[nnz][F][fb][fb] where not NULL */
+int amg_level_p(bamg_t h, int level, int* nnz, int* p_rp, int* p_ci, double* p_v);
+
 /* ---- introspection (host outputs; synchronise the handle's setup stream) ---- */
 
 /* number of levels (>= 1), or a negative status */
@@ -215,7 +337,8 @@ int amg_num_levels(bamg_t h);
  * number of aggregates it is coarsened into (0 on the coarsest). */
 int amg_level_info(bamg_t h, int level, int* n_nodes, int* nnzb, int* n_colours, int* n_agg);
 
-/* host copies of level l (any pointer may be NULL): row_ptr[n+1], col_idx[nnzb],
+/* copies of level l into host or device memory (any pointer the CUDA runtime
+ * addresses; any may be NULL): row_ptr[n+1], col_idx[nnzb],
  * vals[nnzb*b*b] (FP64), agg[n] and colour[n] (not on the coarsest level),
  * dinv[n*F*fb*fb] (FP64 node-major, then field, then the fb x fb inverse
  * row-major; not on the coarsest level). */

@@ -25,7 +25,14 @@ BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
            "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror",
            "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
-           "fgmres_solve_batched", "amg_num_systems", "amg_level_systems"]
+           "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
+           "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
+           "amg_level_p"]
+
+#: network sizes (include/bamg.h)
+NFEAT, MLP_H, MLP_OUT = 8, 64, 2
+MLP_NTRAIN = MLP_H * NFEAT + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
+MLP_NPARAMS = MLP_NTRAIN + 2 * NFEAT
 
 #: kernel kinds of amg_profile_read
 KERNEL_KINDS = ["smooth", "residual", "restrict", "prolong", "coarse", "spmv", "krylov", "cast", "tail"]
@@ -37,7 +44,10 @@ _lib = None
 class AmgParams(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
                 ("omega", C.c_double), ("cycle_prec", C.c_int), ("use_graph", C.c_int), ("tail_dofs", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("smooth_p", C.c_int), ("omega_p", C.c_double),
+                ("omega_s_arr", C.POINTER(C.c_double)), ("omega_s_len", C.c_longlong),
+                ("omega_p_arr", C.POINTER(C.c_double)), ("omega_p_len", C.c_longlong),
+                ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int)]
 
 
 class BamgError(RuntimeError):
@@ -93,6 +103,17 @@ def load(build_if_missing: bool = True):
         lib.fgmres_solve_batched.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
         lib.amg_num_systems.argtypes = [_vp]
         lib.amg_level_systems.argtypes = [_vp, C.c_int, _ip]
+        lib.amg_features.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _ip, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
+        lib.mlp_pack.argtypes = [_vp, _vp, _vp]
+        lib.mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
+        lib.mlp_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp]
+        lib.mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _vp]
+        lib.mlp_clip.argtypes = [C.c_int, C.c_double]
+        lib.mlp_clip.restype = C.c_double
+        lib.amg_set_omega.argtypes = [_vp, C.c_int, _vp, _vp]
+        lib.amg_select.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _ip, _ip, _vp]
+        lib.amg_level_omega.argtypes = [_vp, C.c_int, _vp, _vp]
+        lib.amg_level_p.argtypes = [_vp, C.c_int, _ip, _vp, _vp, _vp]
         _lib = lib
         return lib
 
@@ -123,12 +144,29 @@ def amg_strerror(status: int) -> str:
 
 
 def amg_default_params(**overrides) -> AmgParams:
+    """Defaults with overrides; the host arrays omega_s_arr, omega_p_arr
+    (float64) and mlp (float32, MLP_NPARAMS) are given as numpy arrays and
+    kept alive by the returned structure."""
     p = AmgParams()
     load().amg_default_params(C.byref(p))
+    keep = []
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise KeyError(k)
-        setattr(p, k, v)
+        if k in ("omega_s_arr", "omega_p_arr") and v is not None:
+            a = np.ascontiguousarray(v, dtype=np.float64).ravel()
+            keep.append(a)
+            setattr(p, k, a.ctypes.data_as(C.POINTER(C.c_double)))
+            setattr(p, k.replace("_arr", "_len"), a.size)
+        elif k == "mlp" and v is not None:
+            a = np.ascontiguousarray(v, dtype=np.float32).ravel()
+            if a.size != MLP_NPARAMS:
+                raise ValueError(f"mlp needs {MLP_NPARAMS} parameters")
+            keep.append(a)
+            p.mlp = a.ctypes.data_as(C.POINTER(C.c_float))
+        elif v is not None:
+            setattr(p, k, v)
+    p._keep = keep
     return p
 
 
@@ -304,6 +342,91 @@ def amg_level_systems(handle: int, level: int) -> np.ndarray:
     return off
 
 
+def amg_features(row_ptr, col_idx, vals, n_nodes: int, b: int, field_of_dof, agg, n_agg: int, level: int,
+                 node_feat, agg_feat=None, stream=None) -> None:
+    fm = np.ascontiguousarray(field_of_dof, dtype=np.int32)
+    st = load().amg_features(_ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(n_nodes), int(b), fm.ctypes.data_as(_ip),
+                             _ptr(agg), int(n_agg), int(level), _ptr(node_feat),
+                             _ptr(agg_feat) if agg_feat is not None else None, _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_features")
+
+
+def mlp_pack(params, params16, stream=None) -> None:
+    st = load().mlp_pack(_ptr(params), _ptr(params16), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "mlp_pack")
+
+
+def mlp_forward(params16, x, n: int, y, stream=None) -> None:
+    st = load().mlp_forward(_ptr(params16), _ptr(x), int(n), _ptr(y), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "mlp_forward")
+
+
+def mlp_grad(params16, x, t, head, n: int, grad, loss, stream=None) -> None:
+    st = load().mlp_grad(_ptr(params16), _ptr(x), _ptr(t), _ptr(head), int(n), _ptr(grad), _ptr(loss),
+                         _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "mlp_grad")
+
+
+def mlp_adam(params, params16, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    st = load().mlp_adam(_ptr(params), _ptr(params16), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr), float(beta1),
+                         float(beta2), float(eps), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "mlp_adam")
+
+
+def mlp_clip(head: int, w: float) -> float:
+    return float(load().mlp_clip(int(head), float(w)))
+
+
+def amg_set_omega(handle: int, level: int, omega_s, stream=None) -> None:
+    st = load().amg_set_omega(handle, int(level), _ptr(omega_s), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_set_omega")
+
+
+def amg_select(learned: int, plain: int, b, tol=1e-8, restart=30, max_iter=10000, stream=None):
+    """Returns (choice, iterations learned, iterations plain); choice 0 keeps the learned hierarchy."""
+    ch, il, ip = C.c_int(), C.c_int(), C.c_int()
+    st = load().amg_select(learned, plain, _ptr(b), float(tol), int(restart), int(max_iter), C.byref(ch),
+                           C.byref(il), C.byref(ip), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_select")
+    return ch.value, il.value, ip.value
+
+
+def amg_level_omega(handle: int, level: int, F: int):
+    """(omega_s[n, F], omega_p[n_agg, F]) host copies of one level."""
+    n, _, _, nagg = amg_level_info(handle, level)
+    ws = np.zeros((n, F))
+    wp = np.zeros((max(nagg, 0), F))
+    st = load().amg_level_omega(handle, level, _hp(ws), _hp(wp) if wp.size else None)
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_omega")
+    return ws, wp
+
+
+def amg_level_p(handle: int, level: int, F: int, fb: int):
+    """(p_rp, p_ci, p_v[nnz, F, fb, fb]) of a level with a smoothed P, else None."""
+    nnz = C.c_int()
+    st = load().amg_level_p(handle, level, C.byref(nnz), None, None, None)
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_p")
+    if nnz.value == 0:
+        return None
+    n = amg_level_info(handle, level)[0]
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(nnz.value, np.int32)
+    v = np.zeros((nnz.value, F, fb, fb))
+    st = load().amg_level_p(handle, level, C.byref(nnz), _hp(rp), _hp(ci), _hp(v))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_p")
+    return rp, ci, v
+
+
 class Solver:
     """Owns one hierarchy built from a block system held in device tensors."""
 
@@ -341,6 +464,15 @@ class Solver:
 
     def stats(self) -> dict:
         return amg_stats(self.handle)
+
+    def omega(self, l: int):
+        return amg_level_omega(self.handle, l, self.F)
+
+    def prolongator(self, l: int):
+        return amg_level_p(self.handle, l, self.F, self.b // self.F)
+
+    def set_omega(self, l: int, omega_s, stream=None):
+        amg_set_omega(self.handle, l, omega_s, stream)
 
 
 class BatchSolver(Solver):

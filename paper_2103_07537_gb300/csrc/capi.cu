@@ -2,6 +2,7 @@
 // end-to-end solve, introspection.  Declarations and argument contracts are
 // in include/bamg.h.  Every compute step runs in the kernels of k_*.cu; this
 // file only allocates, sequences launches and reads back sizes and flags.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <cmath>
@@ -113,6 +114,17 @@ struct Level {
     int* sys_off_d = nullptr;
     // per-colour counts for the algorithmic byte / flop model (profiling only)
     std::vector<long> colour_nnz, colour_nnz_lower;
+    // per-node smoother damping [n][F] (nullptr: the scalar omega) and P smoothing weights [n_agg][F]
+    double* omega_s64 = nullptr;
+    float* omega_s32 = nullptr;
+    double* omega_p64 = nullptr;
+    // smoothed prolongator of this level (F sub-blocks of fb x fb per stored block) and R = P^T
+    int smoothed = 0;
+    int p_nnz = 0;
+    int *p_rp = nullptr, *p_ci = nullptr;
+    double* p_v64 = nullptr;
+    int *r_rp = nullptr, *r_i = nullptr, *r_q = nullptr;
+    void *p_vc = nullptr, *r_vc = nullptr;  // P and R values in the cycle's storage type
 };
 
 struct ProfRec {
@@ -202,8 +214,10 @@ struct bamg_ctx {
            *scal = nullptr;
     unsigned* ticket = nullptr;  // last-CTA counter of the chunked reductions
     double* h_scal = nullptr;  // pinned [4]
-    // host wall time of the setup phases (ms): pattern, aggregate, rap, colour, inverse, coarse, vectors
+    // host wall time of the setup phases (ms): pattern, aggregate, rap, colour, inverse, coarse, vectors,
+    // learned weights
     double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint16_t* mlp16 = nullptr;  // FP16 network parameters (learned setup)
 
     cudaStream_t stream = nullptr;  // the setup stream: allocations and frees are ordered on it
 
@@ -314,6 +328,14 @@ extern "C" void amg_default_params(amg_params* p) {
     p->use_graph = 1;
     p->tail_dofs = 0;
     p->autotune = 1;
+    p->smooth_p = 0;
+    p->omega_p = 0.0;
+    p->omega_s_arr = nullptr;
+    p->omega_s_len = 0;
+    p->omega_p_arr = nullptr;
+    p->omega_p_len = 0;
+    p->mlp = nullptr;
+    p->pr_storage = 32;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -354,6 +376,153 @@ template <>
 const double* level_dinv<double>(const Level& L) { return L.dinv64; }
 template <>
 const float* level_dinv<float>(const Level& L) { return L.dinv32; }
+template <typename T>
+static const T* level_omega(const Level& L);
+template <>
+const double* level_omega<double>(const Level& L) { return L.omega_s64; }
+template <>
+const float* level_omega<float>(const Level& L) { return L.omega_s32; }
+
+// The damping weights of level l, which is being coarsened (its aggregates
+// and member lists exist): from the network on the level's features, from
+// the caller's per-level arrays, or the constants.  Sets L.smoothed.
+static int level_weights(bamg_ctx* h, int l, cudaStream_t s, long long* used_s, long long* used_p) {
+    Level& L = h->lev[l];
+    const amg_params& p = h->p;
+    const int F = h->F;
+    const size_t ns = (size_t)L.n * F, np = (size_t)L.n_agg * F;
+    if (p.mlp) {
+        float *nf = nullptr, *af = nullptr, *yn = nullptr, *ya = nullptr;
+        int* cnt = nullptr;
+        TRY(h->alloc(&nf, ns * BAMG_NFEAT));
+        TRY(h->alloc(&af, np * BAMG_NFEAT));
+        TRY(h->alloc(&yn, ns * BAMG_MLP_OUT));
+        TRY(h->alloc(&ya, np * BAMG_MLP_OUT));
+        TRY(h->alloc(&cnt, (size_t)L.n_agg + 1));
+        TRY(h->alloc(&L.omega_s64, ns));
+        TRY(h->alloc(&L.omega_p64, np));
+        TRY(launch_agg_count(L.n, L.n_agg, L.agg, cnt, h->d_err, s));
+        TRY(launch_features(h->b, h->fb, L.n, L.rp, L.ci, L.vals64, L.agg, cnt, l, nf, h->d_err, s));
+        TRY(launch_agg_features(L.n_agg, F, L.agg_ptr, L.members, nf, af, s));
+        TRY(launch_mlp_forward(h->mlp16, nf, (int)ns, yn, s));
+        TRY(launch_mlp_forward(h->mlp16, af, (int)np, ya, s));
+        BAMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        TRY(launch_omega_from_mlp((int)ns, 0, yn, L.omega_s64, nullptr, s));
+        TRY(launch_omega_from_mlp((int)np, 1, ya, L.omega_p64, cnt, s));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 4, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRY(check_dev(h, s));
+        L.smoothed = h->h_pin[4] != 0;  // P smoothed only where a weight survived the clip
+        for (void* q : {(void*)nf, (void*)af, (void*)yn, (void*)ya, (void*)cnt}) h->release(q);
+        return BAMG_OK;
+    }
+    if (p.omega_s_arr) {
+        if (*used_s + (long long)ns > p.omega_s_len) return BAMG_EINVAL;
+        TRY(h->alloc(&L.omega_s64, ns));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(L.omega_s64, p.omega_s_arr + *used_s, sizeof(double) * ns,
+                                      cudaMemcpyHostToDevice, s));
+        *used_s += (long long)ns;
+    }
+    L.smoothed = p.smooth_p;
+    if (p.smooth_p) {
+        TRY(h->alloc(&L.omega_p64, np));
+        if (p.omega_p_arr) {
+            if (*used_p + (long long)np > p.omega_p_len) return BAMG_EINVAL;
+            BAMG_CUDA_TRY(cudaMemcpyAsync(L.omega_p64, p.omega_p_arr + *used_p, sizeof(double) * np,
+                                          cudaMemcpyHostToDevice, s));
+            *used_p += (long long)np;
+        } else {
+            TRY(launch_fill((long)np, p.omega_p, L.omega_p64, s));
+        }
+    }
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));  // the host arrays are the caller's
+    return BAMG_OK;
+}
+
+// rows, columns of a row-wise product into (rp, ci): symbolic pass, scan, fill
+static int product_pattern(bamg_ctx* h, int nrows, const int* xrp, const int* xci, const int* xmap, const int* yrp,
+                           const int* yci, int** rp_out, int** ci_out, int* nnz_out, cudaStream_t s) {
+    int *count = nullptr, *tmp_cols = nullptr, *scan = nullptr;
+    TRY(h->alloc(&count, (size_t)nrows + 1));
+    TRY(h->alloc(&tmp_cols, (size_t)nrows * kRapCap));
+    TRY(h->alloc(&scan, (size_t)scan_tmp_bytes(nrows) / sizeof(int) + 16));
+    TRY(h->alloc(rp_out, (size_t)nrows + 1));
+    TRY(spgemm_symbolic(nrows, xrp, xci, xmap, yrp, yci, count, tmp_cols, kRapCap, h->d_err, s));
+    TRY(check_dev(h, s));
+    TRY(exclusive_scan(nrows, count, *rp_out, scan, scan_tmp_bytes(nrows) + 64, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, *rp_out + nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *nnz_out = h->h_pin[0];
+    TRY(h->alloc(ci_out, (size_t)*nnz_out));
+    TRY(rap_fill_cols(nrows, *rp_out, tmp_cols, kRapCap, *ci_out, s));
+    h->release(count);
+    h->release(tmp_cols);
+    h->release(scan);
+    return BAMG_OK;
+}
+
+// Smoothed prolongator of level l, R = P^T, and A_{l+1} = R (A_l P).
+static int smoothed_galerkin(bamg_ctx* h, int l, cudaStream_t s) {
+    Level& L = h->lev[l];
+    Level& C = h->lev[l + 1];
+    const int b = h->b, F = h->F, fb = h->fb, n = L.n, nc = L.n_agg;
+    if (!L.dinv64) {
+        TRY(h->alloc(&L.dinv64, (size_t)n * F * fb * fb));
+        TRY(block_inverses(b, fb, n, L.diag, L.vals64, L.dinv64, h->d_err, s));
+        TRY(check_dev(h, s));
+    }
+    // P: row i holds the distinct agg(j) of its stored j
+    TRY(product_pattern(h, n, L.rp, L.ci, L.agg, nullptr, nullptr, &L.p_rp, &L.p_ci, &L.p_nnz, s));
+    TRY(h->alloc(&L.p_v64, (size_t)L.p_nnz * F * fb * fb));
+    TRY(prolongator_numeric(b, fb, n, L.rp, L.ci, L.vals64, L.dinv64, L.agg, L.omega_p64, L.p_rp, L.p_ci, L.p_v64,
+                            s));
+    // R = P^T: coarse row I holds the neighbours of I's members, ascending
+    int nnz_r = 0;
+    TRY(product_pattern(h, nc, L.agg_ptr, L.members, nullptr, L.rp, L.ci, &L.r_rp, &L.r_i, &nnz_r, s));
+    if (nnz_r != L.p_nnz) return BAMG_ECUDA;
+    TRY(h->alloc(&L.r_q, (size_t)nnz_r));
+    TRY(transpose_index(nc, L.r_rp, L.r_i, L.p_rp, L.p_ci, L.r_q, h->d_err, s));
+    // A P, then R (A P)
+    int *ap_rp = nullptr, *ap_ci = nullptr, nnz_ap = 0;
+    TRY(product_pattern(h, n, L.rp, L.ci, nullptr, L.p_rp, L.p_ci, &ap_rp, &ap_ci, &nnz_ap, s));
+    double* ap_v = nullptr;
+    TRY(h->alloc(&ap_v, (size_t)nnz_ap * b * b));
+    TRY(ap_numeric(b, fb, n, L.rp, L.ci, L.vals64, L.p_rp, L.p_ci, L.p_v64, ap_rp, ap_ci, ap_v, s));
+    C.n = nc;
+    TRY(product_pattern(h, nc, L.r_rp, L.r_i, nullptr, ap_rp, ap_ci, &C.rp, &C.ci, &C.nnzb, s));
+    TRY(h->alloc(&C.vals64, (size_t)C.nnzb * b * b));
+    TRY(rap_general_numeric(b, fb, nc, L.r_rp, L.r_i, L.r_q, L.p_v64, ap_rp, ap_ci, ap_v, C.rp, C.ci, C.vals64, s));
+    TRY(check_dev(h, s));
+    h->release(ap_rp);
+    h->release(ap_ci);
+    h->release(ap_v);
+    // transfer values in the cycle's storage type
+    const long nnz = L.p_nnz;
+    const size_t m = (size_t)nnz * F * fb * fb;
+    if (h->p.cycle_prec == 64) {
+        double *pv = nullptr, *rv = nullptr;
+        TRY(h->alloc(&pv, m));
+        TRY(h->alloc(&rv, m));
+        TRY(transfer_values<double>(nnz, F, fb, L.r_q, L.p_v64, pv, rv, s));
+        L.p_vc = pv;
+        L.r_vc = rv;
+    } else if (h->p.pr_storage == 16) {
+        __nv_bfloat16 *pv = nullptr, *rv = nullptr;
+        TRY(h->alloc(&pv, m));
+        TRY(h->alloc(&rv, m));
+        TRY(transfer_values<__nv_bfloat16>(nnz, F, fb, L.r_q, L.p_v64, pv, rv, s));
+        L.p_vc = pv;
+        L.r_vc = rv;
+    } else {
+        float *pv = nullptr, *rv = nullptr;
+        TRY(h->alloc(&pv, m));
+        TRY(h->alloc(&rv, m));
+        TRY(transfer_values<float>(nnz, F, fb, L.r_q, L.p_v64, pv, rv, s));
+        L.p_vc = pv;
+        L.r_vc = rv;
+    }
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return BAMG_OK;
+}
 
 // average device time (us) of `reps` launches of f after one warm-up launch
 template <class F>
@@ -402,6 +571,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         a.field = 0;
         a.F = h->F;
         a.omega = h->p.omega;
+        a.omega_node = level_omega<T>(L);
         const int reps = 3;
         L.tune_us[0] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
         L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s); });
@@ -470,6 +640,16 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(node_sys);
     }
 
+    if (h->p.mlp) {  // FP16 copy of the network parameters
+        float* p32 = nullptr;
+        TRY(h->alloc(&p32, BAMG_MLP_NPARAMS));
+        TRY(h->alloc(&h->mlp16, BAMG_MLP_NPARAMS));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(p32, h->p.mlp, sizeof(float) * BAMG_MLP_NPARAMS, cudaMemcpyHostToDevice, s));
+        TRY(launch_pack_half(p32, h->mlp16, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        h->release(p32);
+    }
+    long long used_s = 0, used_p = 0;
     h->nlev = 1;
     for (int l = 0;; ++l) {
         Level& L = h->lev[l];
@@ -519,6 +699,20 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->t_phase[1] += ms_since(tp);
         tp = Clock::now();
+        TRY(level_weights(h, l, s, &used_s, &used_p));
+        h->t_phase[7] += ms_since(tp);
+        tp = Clock::now();
+        if (L.smoothed) {
+            TRY(smoothed_galerkin(h, l, s));
+            h->release(w.flag);
+            h->release(d_count);
+            h->release(scan_tmp);
+            h->release(tmp);
+            h->nlev++;
+            h->t_phase[2] += ms_since(tp);
+            tp = Clock::now();
+            continue;
+        }
         // Galerkin product
         Level& C = h->lev[l + 1];
         C.n = nc;
@@ -550,6 +744,13 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->t_phase[2] += ms_since(tp);
         tp = Clock::now();
     }
+    if (!h->p.mlp && ((h->p.omega_s_arr && used_s != h->p.omega_s_len) ||
+                      (h->p.smooth_p && h->p.omega_p_arr && used_p != h->p.omega_p_len)))
+        return BAMG_EINVAL;  // the per-level arrays must match the hierarchy exactly
+    // the caller's host arrays are not kept
+    h->p.omega_s_arr = nullptr;
+    h->p.omega_p_arr = nullptr;
+    h->p.mlp = nullptr;
     // smoother data on every level but the coarsest
     for (int l = 0; l + 1 < h->nlev; ++l) {
         Level& L = h->lev[l];
@@ -575,9 +776,15 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         if (L.colour_ptr[L.n_colours] != L.n) return BAMG_ECUDA;
         h->t_phase[3] += ms_since(tp);
         tp = Clock::now();
-        TRY(h->alloc(&L.dinv64, (size_t)L.n * h->F * h->fb * h->fb));
-        TRY(block_inverses(b, h->fb, L.n, L.diag, L.vals64, L.dinv64, h->d_err, s));
-        TRY(check_dev(h, s));
+        if (!L.dinv64) {  // (already there when P was smoothed)
+            TRY(h->alloc(&L.dinv64, (size_t)L.n * h->F * h->fb * h->fb));
+            TRY(block_inverses(b, h->fb, L.n, L.diag, L.vals64, L.dinv64, h->d_err, s));
+            TRY(check_dev(h, s));
+        }
+        if (h->p.cycle_prec == 32 && L.omega_s64) {
+            TRY(h->alloc(&L.omega_s32, (size_t)L.n * h->F));
+            TRY(launch_convert_d2f((long)L.n * h->F, L.omega_s64, L.omega_s32, s));
+        }
         if (h->p.cycle_prec == 32) {
             TRY(h->alloc(&L.vals32, (size_t)L.nnzb * bb));
             TRY(h->alloc(&L.dinv32, (size_t)L.n * h->F * h->fb * h->fb));
@@ -717,7 +924,10 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 2)
+        prm.autotune < 0 || prm.autotune > 2 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
+        (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
+        (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp))
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -814,6 +1024,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.field = f;
         a.F = h->F;
         a.omega = h->p.omega;
+        a.omega_node = level_omega<T>(L);
         double bytes = 0.0, flops = 0.0;
         if (h->prof && have_counts) {
             const double es = sizeof(T), B = h->b, FB = h->fb, nc = a.n_in_colour;
@@ -835,6 +1046,39 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
            L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s) : launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
     return BAMG_OK;
+}
+
+// transfers with the explicit (smoothed) P and R of a level, values stored
+// in the cycle type or, inside an FP32 cycle, optionally in BF16
+template <typename T>
+static int restrict_explicit(bamg_ctx* h, const Level& L, const T* res, T* rc, cudaStream_t s);
+template <>
+int restrict_explicit<double>(bamg_ctx* h, const Level& L, const double* res, double* rc, cudaStream_t s) {
+    return launch_fdiag_spmv<double, double>(h->b, h->fb, L.n_agg, L.r_rp, L.r_i,
+                                             static_cast<const double*>(L.r_vc), res, rc, false, s);
+}
+template <>
+int restrict_explicit<float>(bamg_ctx* h, const Level& L, const float* res, float* rc, cudaStream_t s) {
+    if (h->p.pr_storage == 16)
+        return launch_fdiag_spmv<float, __nv_bfloat16>(h->b, h->fb, L.n_agg, L.r_rp, L.r_i,
+                                                       static_cast<const __nv_bfloat16*>(L.r_vc), res, rc, false, s);
+    return launch_fdiag_spmv<float, float>(h->b, h->fb, L.n_agg, L.r_rp, L.r_i, static_cast<const float*>(L.r_vc),
+                                           res, rc, false, s);
+}
+template <typename T>
+static int prolong_explicit(bamg_ctx* h, const Level& L, const T* uc, T* u, cudaStream_t s);
+template <>
+int prolong_explicit<double>(bamg_ctx* h, const Level& L, const double* uc, double* u, cudaStream_t s) {
+    return launch_fdiag_spmv<double, double>(h->b, h->fb, L.n, L.p_rp, L.p_ci, static_cast<const double*>(L.p_vc),
+                                             uc, u, true, s);
+}
+template <>
+int prolong_explicit<float>(bamg_ctx* h, const Level& L, const float* uc, float* u, cudaStream_t s) {
+    if (h->p.pr_storage == 16)
+        return launch_fdiag_spmv<float, __nv_bfloat16>(h->b, h->fb, L.n, L.p_rp, L.p_ci,
+                                                       static_cast<const __nv_bfloat16*>(L.p_vc), uc, u, true, s);
+    return launch_fdiag_spmv<float, float>(h->b, h->fb, L.n, L.p_rp, L.p_ci, static_cast<const float*>(L.p_vc), uc, u,
+                                           true, s);
 }
 
 // MGV(0, rhs, l) of Fig. 1 written to out
@@ -894,6 +1138,31 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const Level& C = h->lev[l + 1];
     T* res = static_cast<T*>(L.res);
     const double es = sizeof(T), nb = (double)L.n * b, ncb = (double)C.n * b;
+    if (L.smoothed) {
+        // explicit transfers: r_c = R (rhs - A u), u += P u_c, then the post-smoother
+        const double vs = h->p.cycle_prec == 32 && h->p.pr_storage == 16 ? 2.0 : es;
+        const double tb = (double)L.p_nnz * (h->F * h->fb * h->fb * vs + 4.0);
+        PL(BAMG_K_RESIDUAL, (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es,
+           2.0 * L.nnzb * b * b,
+           L.spmv_tpr ? launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
+                      : launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+        PL(BAMG_K_RESTRICT, tb + (C.n + 1) * 4.0 + nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
+           restrict_explicit<T>(h, L, res, static_cast<T*>(C.rhs), s));
+        TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
+        PL(BAMG_K_PROLONG, tb + (L.n + 1) * 4.0 + 2.0 * nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
+           prolong_explicit<T>(h, L, static_cast<const T*>(C.uc), cur, s));
+        const int S_post = h->p.n_post * h->F;
+        if (S_post == 0) {
+            BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
+            return BAMG_OK;
+        }
+        for (int t = 0; t < S_post; ++t) {
+            T* dst = (t == S_post - 1) ? out : ((cur == xa) ? xb : xa);
+            TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, nullptr, s));
+            cur = dst;
+        }
+        return BAMG_OK;
+    }
     const double res_bytes = (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es;
     const double res_flops = 2.0 * L.nnzb * b * b;
     const double rst_bytes = L.n * 4.0 + (C.n + 1) * 4.0 + nb * es + ncb * es;
@@ -1009,6 +1278,8 @@ static int setup_tail(bamg_ctx* h, cudaStream_t s) {
     h->tail_d = nullptr;
     h->l_tail = -1;
     if (h->p.tail_dofs <= 0 || h->nlev < 2) return BAMG_OK;
+    for (int l = 0; l + 1 < h->nlev; ++l)
+        if (h->lev[l].smoothed) return BAMG_OK;  // the tail kernel has no explicit-transfer phase
     int lt = h->nlev - 1;
     while (lt > 0 && (long)h->lev[lt - 1].n * h->b <= h->p.tail_dofs) --lt;
     if (lt >= h->nlev - 1) return BAMG_OK;  // only the coarsest solve would remain: no gain
@@ -1447,15 +1718,15 @@ extern "C" int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, d
     const Level& L = h->lev[level];
     const bool coarsest = level == h->nlev - 1;
     const size_t bb = (size_t)h->b * h->b;
-    if (row_ptr) BAMG_CUDA_TRY(cudaMemcpy(row_ptr, L.rp, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
-    if (col_idx) BAMG_CUDA_TRY(cudaMemcpy(col_idx, L.ci, sizeof(int) * (size_t)L.nnzb, cudaMemcpyDeviceToHost));
-    if (vals) BAMG_CUDA_TRY(cudaMemcpy(vals, L.vals64, sizeof(double) * bb * L.nnzb, cudaMemcpyDeviceToHost));
+    if (row_ptr) BAMG_CUDA_TRY(cudaMemcpy(row_ptr, L.rp, sizeof(int) * (L.n + 1), cudaMemcpyDefault));
+    if (col_idx) BAMG_CUDA_TRY(cudaMemcpy(col_idx, L.ci, sizeof(int) * (size_t)L.nnzb, cudaMemcpyDefault));
+    if (vals) BAMG_CUDA_TRY(cudaMemcpy(vals, L.vals64, sizeof(double) * bb * L.nnzb, cudaMemcpyDefault));
     if (!coarsest) {
-        if (agg) BAMG_CUDA_TRY(cudaMemcpy(agg, L.agg, sizeof(int) * (size_t)L.n, cudaMemcpyDeviceToHost));
-        if (colour) BAMG_CUDA_TRY(cudaMemcpy(colour, L.colour, sizeof(int) * (size_t)L.n, cudaMemcpyDeviceToHost));
+        if (agg) BAMG_CUDA_TRY(cudaMemcpy(agg, L.agg, sizeof(int) * (size_t)L.n, cudaMemcpyDefault));
+        if (colour) BAMG_CUDA_TRY(cudaMemcpy(colour, L.colour, sizeof(int) * (size_t)L.n, cudaMemcpyDefault));
         if (dinv)
             BAMG_CUDA_TRY(cudaMemcpy(dinv, L.dinv64, sizeof(double) * (size_t)L.n * h->F * h->fb * h->fb,
-                                     cudaMemcpyDeviceToHost));
+                                     cudaMemcpyDefault));
     }
     return BAMG_OK;
 }
@@ -1465,8 +1736,9 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
-    const char* names[7] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors"};
-    for (int q = 0; q < 7; ++q) {
+    const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
+                            "weights"};
+    for (int q = 0; q < 8; ++q) {
         char buf[64];
         snprintf(buf, sizeof buf, "%s\"%s\":%.4f", q ? "," : "", names[q], h->t_phase[q]);
         o += buf;
@@ -1483,7 +1755,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"smoother_mapping\":\"" + (L.bgs_tpr ? "thread" : "warp") + "\",\"residual_mapping\":\"" +
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
-             std::to_string(L.tune_us[3]) + "]}";
+             std::to_string(L.tune_us[3]) + "],\"smoothed_p\":" + std::to_string(L.smoothed) +
+             ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0") + "}";
     }
     o += "]}";
     const int len = (int)o.size();
@@ -1552,5 +1825,196 @@ extern "C" int amg_profile_read(bamg_t h, int kind, double* ms, long long* launc
     if (launches) *launches = cnt;
     if (bytes) *bytes = by;
     if (flops) *flops = fl;
+    return BAMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned damping
+// ---------------------------------------------------------------------------
+namespace {
+// stream-ordered scratch of one entry point, returned to the pool on exit
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> q;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        if (pool_alloc(&p, (count ? count : 1) * sizeof(T), s) != cudaSuccess) return nullptr;
+        q.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~Scratch() {
+        for (void* p : q) cudaFreeAsync(p, s);
+    }
+};
+
+int read_flag(int* d_err, cudaStream_t s) {
+    int v = 0;
+    if (cudaMemcpyAsync(&v, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BAMG_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BAMG_ECUDA;
+    return map_dev_error(v);
+}
+}  // namespace
+
+extern "C" int amg_features(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int b,
+                            const int* field_of_dof, const int* agg, int n_agg, int level, float* node_feat,
+                            float* agg_feat, void* stream) {
+    if (!row_ptr || !col_idx || !vals || !field_of_dof || !agg || !node_feat || n_nodes < 1 || n_agg < 1 ||
+        n_agg > n_nodes || b < 1 || b > kMaxB || level < 0)
+        return BAMG_EINVAL;
+    int F = 1;
+    if (field_of_dof[0] != 0) return BAMG_EINVAL;
+    for (int d = 1; d < b; ++d) {
+        const int step = field_of_dof[d] - field_of_dof[d - 1];
+        if (step != 0 && step != 1) return BAMG_EINVAL;
+        F = field_of_dof[d] + 1;
+    }
+    if (b % F) return BAMG_EINVAL;
+    const int fb = b / F;
+    for (int d = 0; d < b; ++d)
+        if (field_of_dof[d] != d / fb) return BAMG_EINVAL;
+    if (!supported_block(b, fb)) return BAMG_EUNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch w(s);
+    int* err = w.get<int>(4);
+    int* cnt = w.get<int>((size_t)n_agg + 1);
+    if (!err || !cnt) return BAMG_ECUDA;
+    BAMG_CUDA_TRY(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+    TRY(launch_agg_count(n_nodes, n_agg, agg, cnt, err, s));
+    TRY(read_flag(err, s));  // aggregate ids in range before they index anything
+    TRY(launch_features(b, fb, n_nodes, row_ptr, col_idx, vals, agg, cnt, level, node_feat, err, s));
+    if (agg_feat) {
+        int* agg_ptr = w.get<int>((size_t)n_agg + 1);
+        int* members = w.get<int>((size_t)n_nodes);
+        int* tmp = w.get<int>((size_t)n_agg + 1 + scan_tmp_bytes(n_agg) / sizeof(int) + 16);
+        if (!agg_ptr || !members || !tmp) return BAMG_ECUDA;
+        TRY(build_members(n_nodes, n_agg, agg, agg_ptr, members, tmp, s));
+        TRY(launch_agg_features(n_agg, F, agg_ptr, members, node_feat, agg_feat, s));
+    }
+    return read_flag(err, s);
+}
+
+extern "C" int mlp_pack(const float* params, uint16_t* params16, void* stream) {
+    if (!params || !params16) return BAMG_EINVAL;
+    return launch_pack_half(params, params16, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mlp_forward(const uint16_t* params16, const float* x, int n, float* y, void* stream) {
+    if (n < 0 || (n > 0 && (!params16 || !x || !y))) return BAMG_EINVAL;
+    return launch_mlp_forward(params16, x, n, y, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mlp_grad(const uint16_t* params16, const float* x, const float* t, const int* head, int n, float* grad,
+                        float* loss, void* stream) {
+    if (n < 1 || !params16 || !x || !t || !head || !grad || !loss) return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch w(s);
+    float* work = w.get<float>(mlp_grad_workspace(n) / sizeof(float) + 1);
+    if (!work) return BAMG_ECUDA;
+    return launch_mlp_grad(params16, x, t, head, n, grad, loss, work, s);
+}
+
+extern "C" int mlp_adam(float* params, uint16_t* params16, const float* grad, float* m, float* v, int t, float lr,
+                        float beta1, float beta2, float eps, void* stream) {
+    if (t < 1 || !params || !params16 || !grad || !m || !v) return BAMG_EINVAL;
+    const float c1 = (float)(1.0 - std::pow((double)beta1, t)), c2 = (float)(1.0 - std::pow((double)beta2, t));
+    return launch_adam(params, params16, grad, m, v, lr, beta1, beta2, eps, c1, c2, static_cast<cudaStream_t>(stream));
+}
+
+// the captured cycles hold the damping pointers of their kernels: drop them
+static void drop_graphs(bamg_ctx* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->prof_exec) cudaGraphExecDestroy(h->prof_exec);
+    if (h->prof_graph) cudaGraphDestroy(h->prof_graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    h->prof_exec = nullptr;
+    h->prof_graph = nullptr;
+    for (auto& r : h->graph_recs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    h->graph_recs.clear();
+}
+
+extern "C" int amg_set_omega(bamg_t h, int level, const double* omega_s, void* stream) {
+    if (!h || !omega_s || level < 0 || level >= h->nlev - 1) return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Level& L = h->lev[level];
+    const size_t m = (size_t)L.n * h->F;
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (!L.omega_s64) {
+        // the hierarchy used the scalar damping so far: give this level arrays
+        TRY(h->alloc(&L.omega_s64, m));
+        if (h->p.cycle_prec == 32) TRY(h->alloc(&L.omega_s32, m));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        if (h->tail_d) TRY(record_tail(h, h->stream, false));
+    }
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L.omega_s64, omega_s, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    if (h->p.cycle_prec == 32) TRY(launch_convert_d2f((long)m, L.omega_s64, L.omega_s32, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return BAMG_OK;
+}
+
+extern "C" int amg_select(bamg_t learned, bamg_t plain, const double* b, double tol, int restart, int max_iter,
+                          int* choice, int* iters_learned, int* iters_plain, void* stream) {
+    if (!learned || !plain || !b || !choice || learned->nsys != 1 || plain->nsys != 1 || learned->b != plain->b ||
+        learned->lev[0].n != plain->lev[0].n)
+        return BAMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t N = (size_t)plain->lev[0].n * plain->b;
+    Scratch w(s);
+    double* x = w.get<double>(N);
+    if (!x) return BAMG_ECUDA;
+    int it_l = 0, it_p = 0;
+    double rr = 0.0;
+    BAMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+    const int st_l = fgmres_solve(learned, b, x, tol, restart, max_iter, &it_l, &rr, stream);
+    if (st_l < 0) return st_l;
+    BAMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+    const int st_p = fgmres_solve(plain, b, x, tol, restart, max_iter, &it_p, &rr, stream);
+    if (st_p < 0) return st_p;
+    // the plain hierarchy judges: the learned one is kept only if it converged in no more iterations
+    *choice = (st_l == BAMG_OK && (st_p != BAMG_OK || it_l <= it_p)) ? 0 : 1;
+    if (iters_learned) *iters_learned = it_l;
+    if (iters_plain) *iters_plain = it_p;
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return BAMG_OK;
+}
+
+extern "C" int amg_level_omega(bamg_t h, int level, double* omega_s, double* omega_p) {
+    if (!h || level < 0 || level >= h->nlev - 1) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (omega_s) {
+        const size_t m = (size_t)L.n * h->F;
+        if (L.omega_s64) BAMG_CUDA_TRY(cudaMemcpy(omega_s, L.omega_s64, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        else
+            for (size_t e = 0; e < m; ++e) omega_s[e] = h->p.omega;
+    }
+    if (omega_p) {
+        const size_t m = (size_t)L.n_agg * h->F;
+        if (L.omega_p64 && L.smoothed)
+            BAMG_CUDA_TRY(cudaMemcpy(omega_p, L.omega_p64, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        else
+            for (size_t e = 0; e < m; ++e) omega_p[e] = 0.0;
+    }
+    return BAMG_OK;
+}
+
+extern "C" int amg_level_p(bamg_t h, int level, int* nnz, int* p_rp, int* p_ci, double* p_v) {
+    if (!h || !nnz || level < 0 || level >= h->nlev - 1) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    *nnz = L.smoothed ? L.p_nnz : 0;
+    if (!L.smoothed) return BAMG_OK;
+    BAMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (p_rp) BAMG_CUDA_TRY(cudaMemcpy(p_rp, L.p_rp, sizeof(int) * (size_t)(L.n + 1), cudaMemcpyDeviceToHost));
+    if (p_ci) BAMG_CUDA_TRY(cudaMemcpy(p_ci, L.p_ci, sizeof(int) * (size_t)L.p_nnz, cudaMemcpyDeviceToHost));
+    if (p_v)
+        BAMG_CUDA_TRY(cudaMemcpy(p_v, L.p_v64, sizeof(double) * (size_t)L.p_nnz * h->F * h->fb * h->fb,
+                                 cudaMemcpyDeviceToHost));
     return BAMG_OK;
 }

@@ -106,23 +106,24 @@ template <typename T>
 int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s);
 // One colour of one field step of the block Gauss-Seidel smoother.
 struct BgsArgs {
-    int n_in_colour;
-    const int* nodes;    // node ids of this colour
-    int colour;          // colour index (neighbours of lower colour carry x~)
-    const int* colours;  // colour of every node
-    const int* rp;
-    const int* ci;
-    const void* vals;
-    const void* dinv;    // [n][F][fb*fb]
-    const void* rhs;
-    const void* x_in;    // nullptr = zero vector
-    void* x_out;
-    void* xt;            // [n][fb]
-    const void* uc;      // optional: coarse correction added to x_in on the fly (x_in + P uc)
-    const int* agg;      // aggregate of every node (with uc)
-    int field;
-    int F;
-    double omega;
+    int n_in_colour = 0;
+    const int* nodes = nullptr;    // node ids of this colour
+    int colour = 0;                // colour index (neighbours of lower colour carry x~)
+    const int* colours = nullptr;  // colour of every node
+    const int* rp = nullptr;
+    const int* ci = nullptr;
+    const void* vals = nullptr;
+    const void* dinv = nullptr;    // [n][F][fb*fb]
+    const void* rhs = nullptr;
+    const void* x_in = nullptr;    // nullptr = zero vector
+    void* x_out = nullptr;
+    void* xt = nullptr;            // [n][fb]
+    const void* uc = nullptr;      // optional: coarse correction added to x_in on the fly (x_in + P uc)
+    const int* agg = nullptr;      // aggregate of every node (with uc)
+    int field = 0;
+    int F = 1;
+    double omega = 0.5;
+    const void* omega_node = nullptr;  // optional: damping of every node and field ([n][F], type T) in place of omega
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
@@ -255,6 +256,45 @@ int launch_check_batch(int n, const int* rp, const int* ci, const int* node_sys,
                        cudaStream_t s);
 int launch_fill_sys(int nsys, const int* node_off, int scale, int* out, cudaStream_t s);
 int launch_coarse_offsets(int nsys, const int* off, const int* rank, int* off_c, cudaStream_t s);
+
+// ---- smoothed transfers and the general Galerkin product (k_transfer.cu) ----
+// Row-wise product symbolic phase: count[row] distinct keys, tmp_cols[row*cap ..]
+// ascending (see k_transfer.cu for the key sources); cap <= 256.
+int spgemm_symbolic(int nrows, const int* xrp, const int* xci, const int* xmap, const int* yrp, const int* yci,
+                    int* count, int* tmp_cols, int cap, int* err, cudaStream_t s);
+int prolongator_numeric(int b, int fb, int n, const int* rp, const int* ci, const double* vals, const double* dinv,
+                        const int* agg, const double* omega_p, const int* p_rp, const int* p_ci, double* p_v,
+                        cudaStream_t s);
+int transpose_index(int nc, const int* r_rp, const int* r_i, const int* p_rp, const int* p_ci, int* r_q, int* err,
+                    cudaStream_t s);
+int ap_numeric(int b, int fb, int n, const int* rp, const int* ci, const double* vals, const int* p_rp,
+               const int* p_ci, const double* p_v, const int* ap_rp, const int* ap_ci, double* ap_v, cudaStream_t s);
+int rap_general_numeric(int b, int fb, int nc, const int* r_rp, const int* r_i, const int* r_q, const double* p_v,
+                        const int* ap_rp, const int* ap_ci, const double* ap_v, const int* rp_c, const int* ci_c,
+                        double* vals_c, cudaStream_t s);
+// P and R values in the cycle's storage type V (double, float, __nv_bfloat16)
+template <typename V>
+int transfer_values(long nnz, int F, int fb, const int* r_q, const double* p_v, V* p_out, V* r_out, cudaStream_t s);
+// y (+)= M x with a field-block-diagonal M (restriction with R, prolongation with P)
+template <typename T, typename V>
+int launch_fdiag_spmv(int b, int fb, int nrows, const int* rp, const int* ci, const V* vals, const T* x, T* y,
+                      bool add, cudaStream_t s);
+
+// ---- learned weights (k_learned.cu) ----
+int launch_features(int b, int fb, int n, const int* rp, const int* ci, const double* vals, const int* agg,
+                    const int* agg_cnt, int level, float* out, int* err, cudaStream_t s);
+int launch_agg_count(int n, int nc, const int* agg, int* cnt, int* err, cudaStream_t s);
+int launch_agg_features(int nc, int F, const int* agg_ptr, const int* members, const float* node_feat, float* out,
+                        cudaStream_t s);
+int launch_pack_half(const float* p, uint16_t* p16, cudaStream_t s);
+int launch_mlp_forward(const uint16_t* p16, const float* x, int n, float* y, cudaStream_t s);
+size_t mlp_grad_workspace(int n);
+int launch_mlp_grad(const uint16_t* p16, const float* x, const float* t, const int* head, int n, float* grad,
+                    float* loss, float* work, cudaStream_t s);
+int launch_adam(float* p, uint16_t* p16, const float* g, float* m, float* v, float lr, float beta1, float beta2,
+                float eps, float c1, float c2, cudaStream_t s);
+int launch_omega_from_mlp(int rows, int head, const float* y, double* out, int* any, cudaStream_t s);
+int launch_fill(long m, double v, double* out, cudaStream_t s);
 
 // ---- Krylov kernels (k_krylov.cu) ----
 int krylov_chunks(long N);

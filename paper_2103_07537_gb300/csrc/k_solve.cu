@@ -118,7 +118,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
 //   r_f = rhs_f - A_{f,*} x                 (x = x_in, fixed for the whole step)
 //   x~  = one multicolour node-block GS sweep on A_ff r_f from x~ = 0:
 //         x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j)
-//   x_f = x_f + omega x~_f
+//   x_f = x_f + omega x~_f      (omega_i,f of node i when omega_node is set)
 // The residual and the Gauss-Seidel sum read the same f-rows of each block,
 // so they are fused into one pass: node i of colour c accumulates
 //   rhs_f,i - sum_j A_{f,*}[i,j] x_in,j - sum_{j: colour(j) < c} A_ff[i,j] x~_j
@@ -201,7 +201,10 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
         const size_t e = (size_t)i * B + lane;
         T v = x_in ? ld1<T, CG>(x_in + e) : T(0);
         if (x_in && uc) v += ld1<T, CG>(uc + (size_t)__ldg(a.agg + i) * B + lane);
-        if (lane >= f0 && lane < f0 + FB) v = fma(T(a.omega), xf, v);
+        if (lane >= f0 && lane < f0 + FB) {
+            const T om = a.omega_node ? static_cast<const T*>(a.omega_node)[(size_t)i * a.F + a.field] : T(a.omega);
+            v = fma(om, xf, v);
+        }
         static_cast<T*>(a.x_out)[e] = v;
     }
 }
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
     for (int c = 0; c < FB; ++c) xn = fma(__ldg(D + c), sh_t[nloc * FB + c], xn);
     static_cast<T*>(a.xt)[(size_t)i * FB + r] = xn;
     T* __restrict__ x_out = static_cast<T*>(a.x_out);
-    const T om = T(a.omega);
+    const T om = a.omega_node ? static_cast<const T*>(a.omega_node)[(size_t)i * a.F + a.field] : T(a.omega);
     const int ag = (x_in && uc) ? __ldg(a.agg + i) : 0;
     for (int m = 0; m < a.F; ++m) {
         const size_t e = (size_t)i * B + m * FB + r;
