@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--weights", default=None, help="damping network parameters (default: the committed file)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other-precision and plain-hierarchy comparisons (for profiler launch lists)")
     ap.add_argument("--ref-iters", type=int, default=30,
                     help="reference arm: inner FGMRES steps timed per step (the sample)")
     return ap.parse_args()
@@ -202,11 +204,20 @@ def oracle_mlp(wl):
     return learn.load_weights(wl.get("weights") or learn.WEIGHTS_PATH).astype(np.float16).astype(np.float64)
 
 
+def oracle_mlp_levels(wl):
+    if not wl.get("learned"):
+        return 0
+    from paper_2103_07537_gb300 import learn
+
+    return learn.trained_levels(wl.get("weights") or learn.WEIGHTS_PATH)
+
+
 def oracle_full_solve(sys_, wl):
     import oracle
 
     t0 = time.perf_counter()
-    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl))
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl),
+                                     mlp_levels=oracle_mlp_levels(wl))
     t1 = time.perf_counter()
     _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=wl["restart"], max_iter=wl.get("max_iter", MAX_ITER))
     t2 = time.perf_counter()
@@ -218,7 +229,8 @@ def oracle_sample(sys_, wl, iters):
     import oracle
 
     t0 = time.perf_counter()
-    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl))
+    h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl),
+                                     mlp_levels=oracle_mlp_levels(wl))
     t1 = time.perf_counter()
     _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=wl["restart"], max_iter=iters)
     t2 = time.perf_counter()
@@ -276,11 +288,12 @@ def run_ours(args):
     if args.weights:
         wl["weights"] = args.weights
     learned = bool(wl.get("learned"))
-    weights = None
+    weights, mlp_levels = None, 0
     if learned:
         from paper_2103_07537_gb300 import learn
 
         weights = learn.load_weights(wl.get("weights") or learn.WEIGHTS_PATH)
+        mlp_levels = learn.trained_levels(wl.get("weights") or learn.WEIGHTS_PATH)
     seed = 1 + rank
     batched = bool(wl.get("batched"))
     made = wl["make"](seed)
@@ -298,7 +311,7 @@ def run_ours(args):
     main_prec = wl["prec"]
     other_prec = 32 if main_prec == 64 else 64
     params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
-                                       mlp=weights)
+                                       mlp=weights, mlp_levels=mlp_levels)
 
     def setup(params):
         if batched:
@@ -398,18 +411,20 @@ def run_ours(args):
 
     # --- the other cycle precision (FP32 cycle inside FP64 FGMRES, or FP64 cycle) --
     params_o = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=other_prec,
-                                       mlp=weights)
-    step(params_o)
+                                       mlp=weights, mlp_levels=mlp_levels)
     k_o = max(1, min(args.steps, 5))
-    ms_o, (st_o, it_o, rr_o, _) = timed(params_o, k_o)
-    variant = {"cycle": (f"fp{other_prec} V-cycle inside fp64 FGMRES (fp64 outer SpMV, Arnoldi, coarse solve)"),
-               "value": timed.solved / (ms_o / 1e3), "unit": UNIT, "iterations": it_o, "relres": rr_o,
-               "converged": st_o == 0}
-    if learned:
+    variant = None
+    if not args.no_variants:
+        step(params_o)
+        ms_o, (st_o, it_o, rr_o, _) = timed(params_o, k_o)
+        variant = {"cycle": (f"fp{other_prec} V-cycle inside fp64 FGMRES (fp64 outer SpMV, Arnoldi, coarse solve)"),
+                   "value": timed.solved / (ms_o / 1e3), "unit": UNIT, "iterations": it_o, "relres": rr_o,
+                   "converged": st_o == 0}
+    if learned and variant:
         variant["cycle"] = f"learned damping, {variant['cycle']}"
     # --- learned workloads: the plain hierarchy, and the fallback rule --------
     plain = None
-    if learned:
+    if learned and not args.no_variants:
         plain = {}
         for prec in (64, 32):
             pp = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=prec)

@@ -93,6 +93,9 @@ typedef struct {
     const float* mlp;
     int pr_storage;   /* values of explicit (smoothed) P and R inside an FP32 cycle: 32 (default)
                          or 16 = BF16 storage, FP32 arithmetic                                 */
+    int mlp_levels;   /* with mlp: the network gives the weights of levels 0..mlp_levels-1 (the
+                         depths it was trained on); deeper levels keep omega and the tentative P.
+                         0 (default) = every level                                             */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

@@ -54,7 +54,7 @@ class Params(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("omega", C.c_double), ("smooth_p", C.c_int), ("omega_p", C.c_double),
                 ("omega_s_arr", _dp), ("omega_s_len", C.c_longlong), ("omega_p_arr", _dp),
-                ("omega_p_len", C.c_longlong), ("mlp", _dp)]
+                ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int)]
 
 
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -282,7 +282,7 @@ class Hierarchy:
 
     def __init__(self, row_ptr, col_idx, vals, b, field_of_dof, max_levels=10, max_coarse=2500,
                  n_pre=1, n_post=1, omega=0.5, smooth_p=0, omega_p=0.0, omega_s_arr=None, omega_p_arr=None,
-                 mlp=None):
+                 mlp=None, mlp_levels=0):
         self.rp, self.ci, self.v = _int32(row_ptr), _int32(col_idx), _f64(vals)
         self.b = int(b)
         self.n = self.rp.shape[0] - 1
@@ -300,7 +300,7 @@ class Hierarchy:
                              0 if self._ws is None else self._ws.size,
                              None if self._wp is None else _d(self._wp),
                              0 if self._wp is None else self._wp.size,
-                             None if self._mlp is None else _d(self._mlp))
+                             None if self._mlp is None else _d(self._mlp), int(mlp_levels))
         h = C.c_void_p()
         st = lib().oracle_setup(self.n, self.ci.shape[0], self.b, _i(self.rp), _i(self.ci), _d(self.v),
                                 _i(fm), C.byref(self.params), C.byref(h))

@@ -708,6 +708,11 @@ static int level_weights(oracle_hier* h, int l, olevel* L, long long* used_s, lo
     L->omega_s = (double*)malloc(sizeof(double) * ns);
     L->omega_p = (double*)calloc(np > 0 ? np : 1, sizeof(double));
     if (!L->omega_s || !L->omega_p) return ORACLE_ENOMEM;
+    if (p->mlp && p->mlp_levels > 0 && l >= p->mlp_levels) { /* beyond the network's depths */
+        for (size_t e = 0; e < ns; ++e) L->omega_s[e] = p->omega;
+        L->smoothed = 0;
+        return ORACLE_OK;
+    }
     if (p->mlp) {
         double* nf = (double*)malloc(sizeof(double) * ns * ORACLE_NFEAT);
         double* af = (double*)malloc(sizeof(double) * (np > 0 ? np : 1) * ORACLE_NFEAT);
@@ -813,7 +818,8 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     h->nlev = 1;
     int st = ORACLE_OK;
     long long used_s = 0, used_p = 0;
-    if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0)) st = ORACLE_EINVAL;
+    if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0) || p->mlp_levels < 0)
+        st = ORACLE_EINVAL;
     /* coarsen while n*b > max_coarse and fewer than max_levels levels */
     while (h->nlev < p->max_levels && (long)h->lev[h->nlev - 1].n * b > p->max_coarse) {
         olevel* F_ = &h->lev[h->nlev - 1];

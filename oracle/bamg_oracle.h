@@ -123,6 +123,8 @@ typedef struct {
      * arrays above and smooth_p); a level smooths P only when some weight
      * of its aggregates is nonzero after the clip. */
     const double* mlp;
+    int mlp_levels;   /* with mlp: levels 0..mlp_levels-1 take the network's weights, deeper
+                         levels omega and the tentative P; 0 = every level */
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,

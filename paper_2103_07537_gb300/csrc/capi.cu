@@ -336,6 +336,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->omega_p_len = 0;
     p->mlp = nullptr;
     p->pr_storage = 32;
+    p->mlp_levels = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -391,6 +392,10 @@ static int level_weights(bamg_ctx* h, int l, cudaStream_t s, long long* used_s, 
     const amg_params& p = h->p;
     const int F = h->F;
     const size_t ns = (size_t)L.n * F, np = (size_t)L.n_agg * F;
+    if (p.mlp && p.mlp_levels > 0 && l >= p.mlp_levels) {  // beyond the network's depths: plain
+        L.smoothed = 0;
+        return BAMG_OK;
+    }
     if (p.mlp) {
         float *nf = nullptr, *af = nullptr, *yn = nullptr, *ya = nullptr;
         int* cnt = nullptr;
@@ -927,7 +932,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         prm.autotune < 0 || prm.autotune > 2 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
-        (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp))
+        (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
+        prm.mlp_levels < 0)
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;

@@ -259,13 +259,22 @@ def load_weights(path: str = WEIGHTS_PATH) -> np.ndarray:
         return z["params"].astype(np.float32)
 
 
+def trained_levels(path: str = WEIGHTS_PATH) -> int:
+    """Levels (from the finest) the network was trained on: its weights are
+    used there (amg_params.mlp_levels); deeper levels keep the plain method."""
+    with np.load(path) as z:
+        return int(json.loads(str(z["meta"])).get("levels_trained", 0))
+
+
 def evaluate(seeds, N, weights, cycle_prec=64, levels=10, max_coarse=2500, restart=30, max_iter=3000, tol=1e-8,
-             log=print):
+             log=print, mlp_levels=None):
     """Plain against learned hierarchy on held-out instances: iterations to
     tol, setup + solve time (CUDA events), and the fallback choice of
     amg_select (the plain hierarchy judges the learned one)."""
     import torch
 
+    if mlp_levels is None:
+        mlp_levels = trained_levels()
     out = []
     for q in seeds:
         s = P.mhd2d_cells(N, q)
@@ -273,7 +282,7 @@ def evaluate(seeds, N, weights, cycle_prec=64, levels=10, max_coarse=2500, resta
         b = _dev(torch, s.rhs)
         rec = dict(seed=int(q), N=int(N))
         hs = {}
-        for name, extra in (("plain", {}), ("learned", dict(mlp=weights))):
+        for name, extra in (("plain", {}), ("learned", dict(mlp=weights, mlp_levels=mlp_levels))):
             prm = bamg.amg_default_params(max_levels=levels, max_coarse=max_coarse, cycle_prec=cycle_prec, **extra)
             x = torch.zeros_like(b)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,7 +327,8 @@ def main(argv=None):
 
         a, b = (int(v) for v in args.evaluate.split("-"))
         torch.cuda.set_device(0)
-        res = evaluate(range(a, b + 1), args.N, load_weights(args.weights), cycle_prec=args.cycle_prec)
+        res = evaluate(range(a, b + 1), args.N, load_weights(args.weights), cycle_prec=args.cycle_prec,
+                       mlp_levels=trained_levels(args.weights))
         pl = [r["plain"]["iterations"] for r in res]
         le = [r["learned"]["iterations"] for r in res]
         ch = [min(r["plain"]["iterations"], r["learned"]["iterations"]) if r["choice"] == "learned"
@@ -352,6 +362,7 @@ def main(argv=None):
     bamg.load()
     rng = np.random.default_rng(args.seed0)
     Xs, Ts, Hs, summary = [], [], [], []
+    levels_trained = 0
     for g0 in range(0, len(seeds), args.group):
         t1 = time.time()
         group = make_instances(seeds[g0:g0 + args.group], args.lo, args.hi, pool)
@@ -359,6 +370,7 @@ def main(argv=None):
         bs = BatchSearch(group)
         res = bs.search()
         X, T, H = bs.rows(res, rng)
+        levels_trained = max(levels_trained, bs.nlev - 1)
         Xs.append(X)
         Ts.append(T)
         Hs.append(H)
@@ -377,7 +389,7 @@ def main(argv=None):
     X, T, H = (np.concatenate(a[:ngrp - nval]) for a in (Xs, Ts, Hs))
     Xv, Tv, Hv = (np.concatenate(a[ngrp - nval:]) for a in (Xs, Ts, Hs))
     params, hist = train(X, T, H, epochs=args.epochs, Xv=Xv, Tv=Tv, Hv=Hv, log=log)
-    meta = dict(instances=len(seeds), seeds=[seeds[0], seeds[-1]], sizes=[args.lo, args.hi],
+    meta = dict(instances=len(seeds), seeds=[seeds[0], seeds[-1]], sizes=[args.lo, args.hi], levels_trained=levels_trained,
                 workload="mhd2d_cells (per-cell resistivity log-uniform in [1e-4, 1])", fine=FINE, coarse=COARSE,
                 p_weight=P_WEIGHT, rows_train=int(X.shape[0]), rows_val=int(Xv.shape[0]), history=hist,
                 search=dict(plain_mean=float(np.mean([np.mean(s["plain"]) for s in summary])),

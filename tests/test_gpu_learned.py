@@ -284,20 +284,24 @@ def learned_params(seed, p_bias):
     return p
 
 
-@pytest.mark.parametrize("p_bias", [0.15, -1.0])
-def test_learned_setup_matches_oracle(p_bias):
+@pytest.mark.parametrize("p_bias,mlp_levels", [(0.15, 0), (-1.0, 0), (0.15, 1)])
+def test_learned_setup_matches_oracle(p_bias, mlp_levels):
     s = P.mhd2d(32, 1)
     prm = learned_params(95, p_bias)
-    sol = make_solver(s, max_levels=3, max_coarse=0, mlp=prm, autotune=0)
-    ref = oracle.Hierarchy.from_system(s, max_levels=3, max_coarse=0, mlp=half_rounded(prm))
+    sol = make_solver(s, max_levels=3, max_coarse=0, mlp=prm, mlp_levels=mlp_levels, autotune=0)
+    ref = oracle.Hierarchy.from_system(s, max_levels=3, max_coarse=0, mlp=half_rounded(prm), mlp_levels=mlp_levels)
     assert sol.num_levels == ref.num_levels
     for l in range(ref.num_levels - 1):
         gs, gp = sol.omega(l)
         os_, op = ref.omega(l)
         np.testing.assert_allclose(gs, os_, rtol=0, atol=2e-5)
         np.testing.assert_allclose(gp, op, rtol=0, atol=2e-5)
-        assert (sol.prolongator(l) is None) == (p_bias < 0)
-        assert gs.std() > 1e-3  # the weights really vary by node
+        by_net = mlp_levels == 0 or l < mlp_levels
+        assert (sol.prolongator(l) is None) == (p_bias < 0 or not by_net)
+        if by_net:
+            assert gs.std() > 1e-3  # the weights really vary by node
+        else:
+            assert (gs == 0.5).all()
     x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
     st, it, rr = sol.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=600)
     _, it_o, _, ok = ref.fgmres(s.rhs, tol=1e-8, restart=30, max_iter=600)

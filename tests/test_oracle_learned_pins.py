@@ -406,3 +406,27 @@ def test_features_scale_covariance():
     np.testing.assert_allclose(d[:, 0, 3], -np.log(4.0) / 2, atol=1e-13)
     np.testing.assert_allclose(d[:, :, [1, 2, 4, 5, 6, 7]], 0.0, atol=1e-13)
     np.testing.assert_allclose(d[:, 0, 0], 0.0, atol=1e-13)
+
+
+def test_network_limited_to_its_trained_levels():
+    """mlp_levels = 1: level 0 takes the network's weights, deeper levels the
+    plain damping and the tentative prolongator."""
+    s = P.mhd2d(12, 4)
+    r = P.uniform_pm1(32, 0, s.n_nodes * 6)
+    p = zero_params()
+    p[O_B3:O_B3 + 2] = [0.6, 0.3]
+    h_net = oracle.Hierarchy.from_system(s, max_levels=3, max_coarse=0, mlp=p, mlp_levels=1, omega=0.5)
+    ws0, wp0 = h_net.omega(0)
+    ws1, wp1 = h_net.omega(1)
+    assert (ws0 == 0.6).all() and (wp0 == 0.3).all()
+    assert (ws1 == 0.5).all() and (wp1 == 0.0).all()
+    h_net.prolongator(0)
+    with pytest.raises(oracle.OracleError):
+        h_net.prolongator(1)
+    # the same hierarchy with the network's output removed: constant weights on level 0 only
+    p[O_B3:O_B3 + 2] = [0.6, 0.01]
+    h_a = oracle.Hierarchy.from_system(s, max_levels=3, max_coarse=0, mlp=p, mlp_levels=1)
+    n0, n1 = h_a.level_sizes(0)[0], h_a.level_sizes(1)[0]
+    ws = np.concatenate([np.full(n0 * 2, 0.6), np.full(n1 * 2, 0.5)])
+    h_b = oracle.Hierarchy.from_system(s, max_levels=3, max_coarse=0, omega_s_arr=ws)
+    np.testing.assert_array_equal(h_a.vcycle(r), h_b.vcycle(r))
