@@ -19,7 +19,8 @@ constexpr int kKThreads = 256;
 constexpr int kDotGroup = 16;  // dot products accumulated together per pass
 
 // fixed chunking of a vector of length N: up to two CTAs per SM of the GB300
-// (152 SMs), at least 256 elements per chunk
+// (152 SMs), at least 256 elements per chunk (four per SM measured slower:
+// the per-CTA reduction and the last CTA's sum over the chunk partials grow)
 int krylov_chunks(long N) {
     long c = (N + 255) / 256;
     if (c > 2 * 152) c = 2 * 152;
@@ -169,9 +170,20 @@ __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __r
     __syncthreads();
     long e0, e1;
     chunk_range(N, &e0, &e1);
+    // the basis vectors in groups of 8: the 8 loads are issued before the
+    // dependent FMA chain (same order of the sum as one vector at a time)
+    constexpr int kAxpyGroup = 8;
     for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         double t = x[e];
-        for (int v = 0; v < nv; ++v) t = fma(-sh_h[v], Y[(size_t)v * ld + e], t);
+        int v = 0;
+        for (; v + kAxpyGroup <= nv; v += kAxpyGroup) {
+            double yv[kAxpyGroup];
+#pragma unroll
+            for (int g = 0; g < kAxpyGroup; ++g) yv[g] = Y[(size_t)(v + g) * ld + e];
+#pragma unroll
+            for (int g = 0; g < kAxpyGroup; ++g) t = fma(-sh_h[v + g], yv[g], t);
+        }
+        for (; v < nv; ++v) t = fma(-sh_h[v], Y[(size_t)v * ld + e], t);
         x[e] = t;
     }
     if (mode == 0) return;
