@@ -69,8 +69,9 @@ typedef struct {
                          as one thread-block-cluster launch per V-cycle; 0 = one launch per
                          step on every level; default 0                                        */
     int autotune;     /* row mapping of the smoother and SpMV kernels: 1 = time warp-per-row and
-                         thread-per-row on every level at setup and keep the faster (default);
-                         0 = warp-per-row everywhere; 2 = thread-per-row everywhere             */
+                         thread-per-row (smoother: also in half-size CTAs) on every level at setup
+                         and keep the fastest (default); 0 = warp-per-row everywhere; 2 =
+                         thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs       */
     /* ---- beyond the paper: smoothed transfers, per-node damping, learned weights ---- */
     int smooth_p;     /* 0: tentative P (default); 1: on every coarsened level the smoothed
                          P_f = (I - W_f D_ff^{-1} A_ff) P^_f per field (see amg_setup)        */
@@ -96,6 +97,10 @@ typedef struct {
     int mlp_levels;   /* with mlp: the network gives the weights of levels 0..mlp_levels-1 (the
                          depths it was trained on); deeper levels keep omega and the tentative P.
                          0 (default) = every level                                             */
+    int use_pdl;      /* 1: the V-cycle's kernels are launched as programmatic dependent launches
+                         (each may be scheduled while its predecessor drains and waits for its
+                         inputs in hardware); 0 (default): ordinary launches. Same results; on
+                         GB300 within a few percent either way, so off by default.            */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

@@ -47,7 +47,8 @@ class AmgParams(C.Structure):
                 ("autotune", C.c_int), ("smooth_p", C.c_int), ("omega_p", C.c_double),
                 ("omega_s_arr", C.POINTER(C.c_double)), ("omega_s_len", C.c_longlong),
                 ("omega_p_arr", C.POINTER(C.c_double)), ("omega_p_len", C.c_longlong),
-                ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int)]
+                ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int),
+                ("use_pdl", C.c_int)]
 
 
 class BamgError(RuntimeError):

@@ -25,6 +25,17 @@ std::atomic<long long> g_launches{0};
 thread_local long long* t_capture_sink = nullptr;  // set while a graph is captured
 }  // namespace
 
+thread_local bool bamg::t_pdl = false;
+
+namespace {
+// programmatic dependent launch for the kernels of one V-cycle (scoped)
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(t_pdl) { t_pdl = on; }
+    ~PdlScope() { t_pdl = prev; }
+};
+}  // namespace
+
 // Stream-ordered device memory: one pool per device, owned by the library,
 // that keeps freed memory for the next hierarchy (no cudaMalloc / cudaFree on
 // the setup and destroy paths once the pool is warm).
@@ -107,8 +118,11 @@ struct Level {
     int *agg = nullptr, *agg_ptr = nullptr, *members = nullptr;
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
-    int bgs_tpr = 0, spmv_tpr = 0;  // row mapping chosen for this level (1: thread per row)
-    float tune_us[4] = {0, 0, 0, 0};  // measured: smoother warp / thread, residual warp / thread
+    // row mapping chosen for this level: smoother 0 warp per node, 1 thread per row, 2 thread per
+    // row in half-size CTAs; residual 0 warp per row, 1 thread per row
+    int bgs_tpr = 0, spmv_tpr = 0;
+    // measured: smoother warp / thread / thread-half, residual warp / thread
+    float tune_us[5] = {0, 0, 0, 0, 0};
     // node range of every system of a batch on this level (host and device)
     std::vector<int> sys_off;
     int* sys_off_d = nullptr;
@@ -337,6 +351,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->mlp = nullptr;
     p->pr_storage = 32;
     p->mlp_levels = 0;
+    p->use_pdl = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -579,7 +594,8 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         a.omega_node = level_omega<T>(L);
         const int reps = 3;
         L.tune_us[0] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
-        L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s); });
+        L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 0); });
+        L.tune_us[4] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 1); });
         const T* x = static_cast<const T*>(L.xa);
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
@@ -587,8 +603,14 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
                                    [&] { return launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
         L.tune_us[3] = time_launch(
             s, e0, e1, reps, [&] { return launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
-        L.bgs_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && L.tune_us[1] < L.tune_us[0]);
-        L.spmv_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && L.tune_us[3] < L.tune_us[2]);
+        if (h->p.autotune == 2) L.bgs_tpr = 1;
+        else if (h->p.autotune == 3) L.bgs_tpr = 2;
+        else if (h->p.autotune == 1) {
+            L.bgs_tpr = 0;
+            if (L.tune_us[1] < L.tune_us[0]) L.bgs_tpr = 1;
+            if (L.tune_us[4] < L.tune_us[L.bgs_tpr]) L.bgs_tpr = 2;
+        }
+        L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < L.tune_us[2]);
     }
     {
         const Level& L0 = h->lev[0];
@@ -902,7 +924,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->seg = SegTable{h->nsys, (int)csys.size(), d_csys, d_e0, d_e1, d_sc};
     }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h->p.autotune == 1 || h->p.autotune == 2) {
+    if (h->p.autotune >= 1) {
         if (h->p.cycle_prec == 64) TRY(autotune_levels<double>(h, s));
         else TRY(autotune_levels<float>(h, s));
     }
@@ -929,11 +951,11 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 2 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        prm.autotune < 0 || prm.autotune > 3 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
-        prm.mlp_levels < 0)
+        prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1))
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -1049,7 +1071,8 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
             continue;
         }
         PL(BAMG_K_SMOOTH, bytes, flops,
-           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s) : launch_bgs_colour<T>(h->b, h->fb, a, s));
+           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr == 2 ? 1 : 0)
+                     : launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
     return BAMG_OK;
 }
@@ -1228,6 +1251,10 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
 // z = M r on the finest level (r, z FP64, distinct)
 static int cycle_direct(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
     const long N = (long)h->lev[0].n * h->b;
+    // the cycle's kernels may start while their predecessor drains (each waits
+    // for its inputs); profiling keeps plain launches so that the event pairs
+    // bracket one kernel each
+    PdlScope pdl(h->p.use_pdl != 0 && !h->prof);
     if (h->p.cycle_prec == 64) {
         if (h->tail_d && h->l_tail == 0 && (r != h->cyc_in || z != h->cyc_out)) {
             // the recorded single-launch cycle reads and writes the staging vectors
@@ -1758,10 +1785,12 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colours\":" + std::to_string(L.n_colours) + ",\"aggregates\":" + std::to_string(L.n_agg) +
              ",\"aggregation_rounds\":" + std::to_string(L.agg_rounds) +
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
-             ",\"smoother_mapping\":\"" + (L.bgs_tpr ? "thread" : "warp") + "\",\"residual_mapping\":\"" +
+             ",\"smoother_mapping\":\"" + (L.bgs_tpr == 2 ? "thread-half" : L.bgs_tpr ? "thread" : "warp") +
+             "\",\"residual_mapping\":\"" +
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
-             std::to_string(L.tune_us[3]) + "],\"smoothed_p\":" + std::to_string(L.smoothed) +
+             std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) +
+             "],\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0") + "}";
     }
     o += "]}";

@@ -76,6 +76,41 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Programmatic dependent launch (sm_90 and later).  A V-cycle kernel launched
+// with the programmatic-serialization attribute may be scheduled while its
+// predecessor in the stream drains; before reading anything an earlier kernel
+// wrote it must pass pdl_wait(), which returns once the predecessor grid has
+// completed and its writes are visible (a hardware dependency, no polling).
+// pdl_trigger() lets the successor be scheduled early; it is issued right
+// after pdl_wait(), so at most one kernel ahead is resident and waiting (a
+// trigger at kernel entry let a chain of future kernels occupy the SMs and
+// measured slower).  Without the attribute both are no-ops.  Data that is
+// constant during a cycle (matrices, inverses, colour lists, dampings) may be
+// read before pdl_wait().
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// launch mode of the V-cycle kernels on this host thread: set by the library
+// around the launches (or the graph capture) of one cycle
+extern thread_local bool t_pdl;
+
+// kernel launch with the programmatic-serialization attribute when t_pdl is set
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = t_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // counts kernel launches (defined in capi.cu); while a CUDA graph is being
 // captured on this thread the count goes to the graph instead
 void note_launch(int count = 1);
@@ -129,7 +164,8 @@ template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
 // thread-per-row variants (more loads in flight per warp; for large levels)
 template <typename T>
-int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// half = 1: CTAs of half the threads (a small colour spread over more SMs)
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int half = 0);
 template <typename T>
 int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
                     cudaStream_t s);

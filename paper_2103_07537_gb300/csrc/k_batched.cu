@@ -372,6 +372,8 @@ template <typename T>
 __global__ void batched_gemv_kernel(int nd_total, int b, const int* __restrict__ row_sys,
                                     const int* __restrict__ node_off, const long* __restrict__ inv_off,
                                     const double* __restrict__ inv, const T* __restrict__ x, T* __restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     const int r = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= nd_total) return;
@@ -388,8 +390,9 @@ template <typename T>
 int launch_batched_gemv(int nd_total, int b, const int* row_sys, const int* node_off, const long* inv_off,
                         const double* inv, const T* x, T* y, cudaStream_t s) {
     if (nd_total <= 0) return BAMG_OK;
-    batched_gemv_kernel<T><<<ceil_div((long)nd_total * 32, 256), 256, 0, s>>>(nd_total, b, row_sys, node_off, inv_off,
-                                                                              inv, x, y);
+    if (launch_k(batched_gemv_kernel<T>, ceil_div((long)nd_total * 32, 256), 256, 0, s, nd_total, b, row_sys, node_off,
+                 inv_off, inv, x, y) != cudaSuccess)
+        return BAMG_ECUDA;
     return launched(1);
 }
 template int launch_batched_gemv<double>(int, int, const int*, const int*, const long*, const double*,

@@ -18,9 +18,11 @@ namespace bamg {
 constexpr int kKThreads = 256;
 constexpr int kDotGroup = 16;  // dot products accumulated together per pass
 
-// fixed chunking of a vector of length N: up to two CTAs per SM of the GB300
-// (152 SMs), at least 256 elements per chunk (four per SM measured slower:
-// the per-CTA reduction and the last CTA's sum over the chunk partials grow)
+// fixed chunking of a vector of length N: at least 256 elements per chunk, at
+// most two CTAs per SM of the GB300 (152 SMs).  The basis vectors are mostly
+// L2-resident and the rate is set by the loads in flight across the GPU:
+// measured on the solves here, 2048-element chunks (fewer CTAs) and four CTAs
+// per SM (more block sums and partials) were both slower.
 int krylov_chunks(long N) {
     long c = (N + 255) / 256;
     if (c > 2 * 152) c = 2 * 152;
@@ -33,9 +35,10 @@ __device__ __forceinline__ void chunk_range(long N, long* e0, long* e1) {
     *e1 = min(N, *e0 + per);
 }
 
-// block-wide sum of G values per thread; result valid in thread 0
+// block-wide sums of G values per thread: thread g < G returns the sum of
+// value g (warp trees, then the warp partials in warp order)
 template <int G>
-__device__ __forceinline__ void block_sum(double (&v)[G], double (*sh)[kKThreads / 32]) {
+__device__ __forceinline__ double block_sum(double (&v)[G], double (*sh)[kKThreads / 32]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -44,15 +47,11 @@ __device__ __forceinline__ void block_sum(double (&v)[G], double (*sh)[kKThreads
         if (lane == 0) sh[g][wid] = v[g];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            double s = 0.0;
-            for (int w = 0; w < kKThreads / 32; ++w) s += sh[g][w];
-            v[g] = s;
-        }
-    }
-    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < G)
+        for (int w = 0; w < kKThreads / 32; ++w) s += sh[threadIdx.x][w];
+    __syncthreads();  // sh is reused by the next group
+    return s;
 }
 
 // partial[v * nchunk + chunk] = sum_{e in chunk} x[e] * Y_v[e], v < nv, and
@@ -74,12 +73,9 @@ __device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const
                 else if (v == nv && want_xx) acc[g] = fma(xe, xe, acc[g]);
             }
         }
-        block_sum<kDotGroup>(acc, sh);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int g = 0; g < kDotGroup; ++g)
-                if (v0 + g < nv + want_xx) partial[(size_t)(v0 + g) * nchunk + blockIdx.x] = acc[g];
-        }
+        const double tot = block_sum<kDotGroup>(acc, sh);
+        if (threadIdx.x < kDotGroup && v0 + (int)threadIdx.x < nv + want_xx)
+            partial[(size_t)(v0 + threadIdx.x) * nchunk + blockIdx.x] = tot;
     }
 }
 
@@ -99,13 +95,24 @@ __device__ __forceinline__ bool last_cta(unsigned* ticket) {
     return last;
 }
 
-// out[v] = sum over chunks c (in order) of partial[v * nchunk + c], one warp per v
+// out[v] = sum of the chunk partials partial[v * nchunk + c], one warp per v;
+// lane l sums chunks l, l+32, ... in four interleaved accumulators (their loads
+// are independent), a fixed order for a fixed chunk count
 __device__ __forceinline__ void finish_sums(int nv, const double* partial, double* out) {
     const int lane = threadIdx.x & 31;
     const int nchunk = gridDim.x;
     for (int v = threadIdx.x >> 5; v < nv; v += blockDim.x >> 5) {
-        double s = 0.0;
-        for (int c = lane; c < nchunk; c += 32) s += __ldcg(partial + (size_t)v * nchunk + c);
+        const double* p = partial + (size_t)v * nchunk;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = lane;
+        for (; c + 96 < nchunk; c += 128) {
+            s0 += __ldcg(p + c);
+            s1 += __ldcg(p + c + 32);
+            s2 += __ldcg(p + c + 64);
+            s3 += __ldcg(p + c + 96);
+        }
+        for (; c < nchunk; c += 32) s0 += __ldcg(p + c);
+        double s = (s0 + s1) + (s2 + s3);
         s = warp_sum(s);
         if (lane == 0) out[v] = s;
     }

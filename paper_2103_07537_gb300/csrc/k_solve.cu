@@ -128,7 +128,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
 // others copied), so the field update of Algorithm 1 needs no extra pass.
 // With uc set, x_in + P uc (the coarse correction) is read in place of x_in.
 // ---------------------------------------------------------------------------
-template <typename T, int B, int FB, bool CG>
+template <typename T, int B, int FB, bool CG, bool PDL = false>
 __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     constexpr int G = kWarp / FB;  // blocks of the row per pass
     const int kk = lane / FB;
@@ -146,6 +146,10 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
         const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)lane * FB;
 #pragma unroll
         for (int c = 0; c < FB; ++c) drow[c] = __ldg(D + c);
+    }
+    if constexpr (PDL) {  // everything below may depend on earlier kernels
+        pdl_wait();
+        pdl_trigger();
     }
     const T bi = lane < FB ? ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) : T(0);
     T acc = T(0);
@@ -254,6 +258,8 @@ __global__ void __launch_bounds__(256, 4) spmv_kernel(int n, const int* __restri
                                                    const T* __restrict__ rhs, T* __restrict__ y) {
     const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // uniform per warp
+    pdl_wait();
+    pdl_trigger();
     spmv_row<T, B, false>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
 }
 
@@ -265,7 +271,10 @@ int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const
     const int blocks = ceil_div((long)n * kWarp, threads);
     switch (b) {
 #define CASE(BB) \
-    case BB: spmv_kernel<T, BB><<<blocks, threads, 0, s>>>(n, rp, ci, vals, x, rhs, y); break;
+    case BB:                                                                                      \
+        if (launch_k(spmv_kernel<T, BB>, blocks, threads, 0, s, n, rp, ci, vals, x, rhs, y) != cudaSuccess) \
+            return BAMG_ECUDA;                                                                    \
+        break;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
@@ -280,6 +289,8 @@ template int launch_spmv<float>(int, int, const int*, const int*, const float*, 
 template <typename T>
 __global__ void restrict_kernel(int b, int nc, const int* __restrict__ agg_ptr, const int* __restrict__ members,
                                 const T* __restrict__ res, T* __restrict__ rc) {
+    pdl_wait();
+    pdl_trigger();
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < (long)nc * b) restrict_dof<T, false>(t, b, agg_ptr, members, res, rc);
 }
@@ -288,7 +299,9 @@ template <typename T>
 int launch_restrict(int b, int nc, const int* agg_ptr, const int* members, const T* res, T* rc,
                     cudaStream_t s) {
     if (nc <= 0) return BAMG_OK;
-    restrict_kernel<T><<<ceil_div((long)nc * b, 256), 256, 0, s>>>(b, nc, agg_ptr, members, res, rc);
+    if (launch_k(restrict_kernel<T>, ceil_div((long)nc * b, 256), 256, 0, s, b, nc, agg_ptr, members, res, rc) !=
+        cudaSuccess)
+        return BAMG_ECUDA;
     return launched(1);
 }
 template int launch_restrict<double>(int, int, const int*, const int*, const double*, double*, cudaStream_t);
@@ -298,6 +311,8 @@ template int launch_restrict<float>(int, int, const int*, const int*, const floa
 template <typename T>
 __global__ void prolong_kernel(int b, int n, const int* __restrict__ agg, const T* __restrict__ uc,
                                T* __restrict__ u) {
+    pdl_wait();
+    pdl_trigger();
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int i = (int)(e / b);
     if (i >= n) return;
@@ -308,7 +323,8 @@ __global__ void prolong_kernel(int b, int n, const int* __restrict__ agg, const 
 template <typename T>
 int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
-    prolong_kernel<T><<<ceil_div((long)n * b, 256), 256, 0, s>>>(b, n, agg, uc, u);
+    if (launch_k(prolong_kernel<T>, ceil_div((long)n * b, 256), 256, 0, s, b, n, agg, uc, u) != cudaSuccess)
+        return BAMG_ECUDA;
     return launched(1);
 }
 template int launch_prolong<double>(int, int, const int*, const double*, double*, cudaStream_t);
@@ -318,7 +334,7 @@ template <typename T, int B, int FB>
 __global__ void __launch_bounds__(256, 4) bgs_colour_kernel(BgsArgs a) {
     const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_in_colour) return;  // uniform per warp
-    bgs_node<T, B, FB, false>(a, q, threadIdx.x & (kWarp - 1));
+    bgs_node<T, B, FB, false, true>(a, q, threadIdx.x & (kWarp - 1));
 }
 
 template <typename T>
@@ -328,7 +344,9 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
     const int blocks = ceil_div((long)a.n_in_colour * kWarp, threads);
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
-    case BB * 16 + FF: bgs_colour_kernel<T, BB, FF><<<blocks, threads, 0, s>>>(a); break;
+    case BB * 16 + FF:                                                                          \
+        if (launch_k(bgs_colour_kernel<T, BB, FF>, blocks, threads, 0, s, a) != cudaSuccess) return BAMG_ECUDA; \
+        break;
         CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
@@ -341,6 +359,8 @@ template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
 template <typename T>
 __global__ void dense_gemv_kernel(int nd, const double* __restrict__ ainv, const T* __restrict__ x,
                                   T* __restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (row >= nd) return;
     gemv_row<T, false>(row, threadIdx.x & 31, nd, ainv, x, y);
@@ -349,7 +369,8 @@ __global__ void dense_gemv_kernel(int nd, const double* __restrict__ ainv, const
 template <typename T>
 int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
-    dense_gemv_kernel<T><<<ceil_div((long)nd * kWarp, 256), 256, 0, s>>>(nd, ainv, x, y);
+    if (launch_k(dense_gemv_kernel<T>, ceil_div((long)nd * kWarp, 256), 256, 0, s, nd, ainv, x, y) != cudaSuccess)
+        return BAMG_ECUDA;
     return launched(1);
 }
 template int launch_dense_gemv<double>(int, const double*, const double*, double*, cudaStream_t);
@@ -373,6 +394,8 @@ __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restr
     if (i >= n) return;
     const int r = (int)(t - (long)i * B);
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    pdl_wait();
+    pdl_trigger();
     T acc = T(0);
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
@@ -393,7 +416,10 @@ int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, c
     const int blocks = ceil_div((long)n * b, 256);
     switch (b) {
 #define CASE(BB) \
-    case BB: spmv_tpr_kernel<T, BB><<<blocks, 256, 0, s>>>(n, rp, ci, vals, x, rhs, y); break;
+    case BB:                                                                                        \
+        if (launch_k(spmv_tpr_kernel<T, BB>, blocks, 256, 0, s, n, rp, ci, vals, x, rhs, y) != cudaSuccess) \
+            return BAMG_ECUDA;                                                                      \
+        break;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
@@ -405,22 +431,22 @@ template int launch_spmv_tpr<double>(int, int, const int*, const int*, const dou
 template int launch_spmv_tpr<float>(int, int, const int*, const int*, const float*, const float*, const float*,
                                     float*, cudaStream_t);
 
-// threads per CTA: a multiple of both FB and the warp size
+// threads per CTA: a multiple of both FB and the warp size (the launch may use
+// half of it: smaller CTAs spread a small colour over more SMs)
 template <int FB>
 struct TprBlock {
     static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
-    static constexpr int kNodes = kThreads / FB;
 };
 
 // One colour of one field step (same arithmetic as bgs_node), FB threads per
 // node; the FB row sums meet in shared memory for the inverse.
 template <typename T, int B, int FB>
 __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs a) {
-    __shared__ T sh_t[TprBlock<FB>::kNodes * FB];
+    __shared__ T sh_t[TprBlock<FB>::kThreads];
     const int tloc = threadIdx.x;
     const int nloc = tloc / FB;
     const int r = tloc - nloc * FB;
-    const long q = (long)blockIdx.x * TprBlock<FB>::kNodes + nloc;
+    const long q = (long)blockIdx.x * (blockDim.x / FB) + nloc;
     const bool act = q < a.n_in_colour;
     const int f0 = a.field * FB;
     const T* __restrict__ vals = static_cast<const T*>(a.vals);
@@ -432,6 +458,8 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
     if (act) {
         i = __ldg(a.nodes + q);
         const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+        pdl_wait();
+        pdl_trigger();
         T acc = T(0);
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
@@ -485,21 +513,25 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
 }
 
 template <typename T>
-int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s) {
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int half) {
     if (a.n_in_colour <= 0) return BAMG_OK;
     switch (b * 16 + fb) {
-#define CASE(BB, FF)                                                                              \
-    case BB * 16 + FF:                                                                            \
-        bgs_tpr_kernel<T, BB, FF><<<ceil_div(a.n_in_colour, TprBlock<FF>::kNodes), TprBlock<FF>::kThreads, 0, s>>>(a); \
-        break;
+#define CASE(BB, FF)                                                                                         \
+    case BB * 16 + FF: {                                                                                     \
+        const int threads = TprBlock<FF>::kThreads >> (half ? 1 : 0);                                       \
+        if (launch_k(bgs_tpr_kernel<T, BB, FF>, ceil_div(a.n_in_colour, threads / FF), threads, 0, s, a) !=   \
+            cudaSuccess)                                                                                     \
+            return BAMG_ECUDA;                                                                               \
+        break;                                                                                               \
+    }
         CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
     return launched(1);
 }
-template int launch_bgs_colour_tpr<double>(int, int, const BgsArgs&, cudaStream_t);
-template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t);
+template int launch_bgs_colour_tpr<double>(int, int, const BgsArgs&, cudaStream_t, int);
+template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // Tail kernel: one thread-block cluster executes a recorded list of V-cycle
@@ -634,10 +666,14 @@ template int tail_cluster_size<float>(int, int, int);
 // precision casts at the cycle boundary (FP64 Krylov vectors <-> FP32 cycle)
 // ---------------------------------------------------------------------------
 __global__ void cast_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (long)gridDim.x * blockDim.x)
         y[e] = (float)x[e];
 }
 __global__ void cast_f2d_kernel(long m, const float* __restrict__ x, double* __restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (long)gridDim.x * blockDim.x)
         y[e] = (double)x[e];
 }
@@ -647,12 +683,12 @@ static int grid_for(long m) {
 }
 int launch_cast_d2f(long m, const double* x, float* y, cudaStream_t s) {
     if (m <= 0) return BAMG_OK;
-    cast_d2f_kernel<<<grid_for(m), 256, 0, s>>>(m, x, y);
+    if (launch_k(cast_d2f_kernel, grid_for(m), 256, 0, s, m, x, y) != cudaSuccess) return BAMG_ECUDA;
     return launched(1);
 }
 int launch_cast_f2d(long m, const float* x, double* y, cudaStream_t s) {
     if (m <= 0) return BAMG_OK;
-    cast_f2d_kernel<<<grid_for(m), 256, 0, s>>>(m, x, y);
+    if (launch_k(cast_f2d_kernel, grid_for(m), 256, 0, s, m, x, y) != cudaSuccess) return BAMG_ECUDA;
     return launched(1);
 }
 

@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(256) fdiag_spmv_kernel(int nrows, const int* _
     const int row = (int)(e / B), d = (int)(e % B);
     const int f = d / FB, rl = d % FB;
     const int k0 = __ldg(rp + row), k1 = __ldg(rp + row + 1);
+    pdl_wait();
+    pdl_trigger();
     T acc = T(0);
     for (int k = k0; k < k1; ++k) {
         const int col = __ldg(ci + k);
@@ -407,8 +409,10 @@ int launch_fdiag_spmv(int b, int fb, int nrows, const int* rp, const int* ci, co
     switch (b * 16 + fb) {
 #define CASE(BB, FF)                                                                                             \
     case BB * 16 + FF:                                                                                           \
-        if (add) fdiag_spmv_kernel<T, V, BB, FF, true><<<grid, 256, 0, s>>>(nrows, rp, ci, vals, x, y);          \
-        else fdiag_spmv_kernel<T, V, BB, FF, false><<<grid, 256, 0, s>>>(nrows, rp, ci, vals, x, y);             \
+        if ((add ? launch_k(fdiag_spmv_kernel<T, V, BB, FF, true>, grid, 256, 0, s, nrows, rp, ci, vals, x, y)     \
+                 : launch_k(fdiag_spmv_kernel<T, V, BB, FF, false>, grid, 256, 0, s, nrows, rp, ci, vals, x, y)) != \
+            cudaSuccess)                                                                                          \
+            return BAMG_ECUDA;                                                                                    \
         break;
         BAMG_FDIAG_CASES(CASE)
 #undef CASE

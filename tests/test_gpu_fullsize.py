@@ -7,6 +7,11 @@ benchmark times (default parameters, graph replay).
   V-cycle within 1e-12; the FP32 cycle inside FP64 FGMRES(50) reaches a true
   FP64 relative residual of 1e-8 (checked with the oracle's SpMV), and its
   V-cycle output differs from the FP64 cycle by less than 1e-4 relative.
+* 2D 4-field system with per-cell resistivity, 256 x 256 cells (396,294
+  unknowns, the learned workload): with seeded per-level weights the smoothed
+  hierarchy has every pattern (levels and P) bit-exact, values within
+  1e-13 / 1e-12 and the FP64 V-cycle within 1e-12; the learned FP32 form with
+  the committed network reaches a true FP64 relative residual of 1e-8.
 """
 import numpy as np
 import pytest
@@ -76,6 +81,47 @@ def test_stokes3d_64_full_size():
     assert np.linalg.norm(z32.cpu().numpy() - zo) / np.linalg.norm(zo) < 1e-4
     x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
     st, it, rr = g32.solve(dev(s.rhs), x, tol=1e-8, restart=50, max_iter=2000)
+    xs = x.cpu().numpy()
+    true_rel = np.linalg.norm(s.rhs - oracle.spmv(s.row_ptr, s.col_idx, s.vals, xs)) / np.linalg.norm(s.rhs)
+    assert st == 0 and rr <= 1e-8 and true_rel <= 1e-8, (st, it, rr, true_rel)
+
+
+def test_mhd2d_cells_256_smoothed_full_size():
+    from paper_2103_07537_gb300 import learn
+
+    s = P.mhd2d_cells(256, 1)
+    kw = dict(max_levels=10, max_coarse=2500)
+    probe = oracle.Hierarchy.from_system(s, smooth_p=1, omega_p=0.1, **kw)  # sizes depend on patterns only
+    sizes = [probe.level_sizes(l) for l in range(probe.num_levels - 1)]
+    del probe
+    ns = sum(n for n, _, _, _ in sizes) * 2
+    na = sum(a for _, _, _, a in sizes) * 2
+    ws = 0.4 + 0.3 * P.uniform01(21, 0, ns)
+    wp = 0.05 + 0.1 * P.uniform01(21, ns, na)
+    wkw = dict(smooth_p=1, omega_s_arr=ws, omega_p_arr=wp, **kw)
+    o = oracle.Hierarchy.from_system(s, **wkw)
+    rp, ci, va = dev(s.row_ptr), dev(s.col_idx), dev(s.vals.reshape(-1))
+    g = bamg.Solver(rp, ci, va, s.b, s.field_of_dof, **wkw)
+    assert g.num_levels == o.num_levels
+    for l in range(o.num_levels):
+        Lg, Lo = g.level(l), o.level(l)
+        assert np.array_equal(Lg["row_ptr"], Lo["row_ptr"]) and np.array_equal(Lg["col_idx"], Lo["col_idx"]), l
+        assert rel_max(Lg["vals"], Lo["vals"]) <= 1e-12, l
+        if l < o.num_levels - 1:
+            assert np.array_equal(Lg["agg"], Lo["agg"]) and np.array_equal(Lg["colour"], Lo["colour"]), l
+            gp, op = g.prolongator(l), o.prolongator(l)
+            assert np.array_equal(gp[0], op[0]) and np.array_equal(gp[1], op[1]), l
+            assert rel_max(gp[2], op[2]) <= 1e-13, l
+    r = np.random.default_rng(13).standard_normal(s.n_unknowns)
+    z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    g.apply(dev(r), z)
+    torch.cuda.synchronize()
+    assert rel_max(z.cpu().numpy(), o.vcycle(r)) <= 1e-12
+    del g, o
+    g32 = bamg.Solver(rp, ci, va, s.b, s.field_of_dof, cycle_prec=32, mlp=learn.load_weights(),
+                      mlp_levels=learn.trained_levels(), **kw)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, it, rr = g32.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=3000)
     xs = x.cpu().numpy()
     true_rel = np.linalg.norm(s.rhs - oracle.spmv(s.row_ptr, s.col_idx, s.vals, xs)) / np.linalg.norm(s.rhs)
     assert st == 0 and rr <= 1e-8 and true_rel <= 1e-8, (st, it, rr, true_rel)

@@ -307,3 +307,19 @@ def test_learned_setup_matches_oracle(p_bias, mlp_levels):
     _, it_o, _, ok = ref.fgmres(s.rhs, tol=1e-8, restart=30, max_iter=600)
     assert st == bamg.BAMG_OK and ok
     assert abs(it - it_o) <= 1, (it, it_o)
+
+
+def test_smoothed_cycle_with_and_without_programmatic_launch():
+    s = P.mhd2d_cells(40, 12)
+    ws, wp = weight_arrays(s, 13, 3)
+    r = dev(P.uniform_pm1(14, 0, s.n_unknowns))
+    zs = []
+    for pdl in (1, 0):
+        sol = make_solver(s, max_levels=3, max_coarse=0, smooth_p=1, omega_s_arr=ws, omega_p_arr=wp, cycle_prec=32,
+                          use_pdl=pdl, autotune=0)
+        z = torch.empty_like(r)
+        sol.apply(r, z)
+        sol.apply(r, z)
+        torch.cuda.synchronize()
+        zs.append(z)
+    assert torch.equal(zs[0], zs[1])

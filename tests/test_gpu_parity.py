@@ -120,7 +120,7 @@ def test_hierarchy_matches_oracle(name):
 # V-cycle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mapping", [dict(tail_dofs=0, autotune=0), dict(tail_dofs=65536, autotune=0),
-                                     dict(tail_dofs=0, autotune=2)])
+                                     dict(tail_dofs=0, autotune=2), dict(tail_dofs=0, autotune=3)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_vcycle_fp64_matches_oracle(name, mapping):
     s, kw = SYSTEMS[name]()
@@ -306,3 +306,23 @@ def test_nonfinite_rhs_reported():
     rhs[5] = np.nan
     x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
     expect_status(bamg.BAMG_ENAN, lambda: g.solve(dev(rhs), x))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_programmatic_dependent_launch_gives_identical_cycles(prec):
+    """The V-cycle with programmatic dependent launches (default) and with
+    ordinary launches: identical bits, replayed from the graph and direct."""
+    s = P.mhd2d(41, 3)
+    r = dev(P.uniform_pm1(5, 0, s.n_unknowns))
+    outs = []
+    for pdl in (1, 0):
+        for graph in (1, 0):
+            sol = make_solver(s, max_levels=4, max_coarse=0, cycle_prec=prec, use_pdl=pdl, use_graph=graph,
+                              autotune=0)
+            z = torch.empty_like(r)
+            for _ in range(3):  # repeated cycles reuse every buffer
+                sol.apply(r, z)
+            torch.cuda.synchronize()
+            outs.append(z.clone())
+    for z in outs[1:]:
+        assert torch.equal(z, outs[0])
