@@ -155,6 +155,7 @@ int map_dev_error(int code) {
         case kDevBadPattern: return BAMG_EINVAL;
         case kDevRowTooLong: return BAMG_EUNSUPPORTED;
         case kDevNonFinite: return BAMG_ENAN;
+        case kDevTimeout: return BAMG_ETIMEOUT;
         default: return BAMG_ECUDA;
     }
 }
@@ -864,7 +865,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&h->coarse_piv, (size_t)nd));
         double *lt = nullptr, *col = nullptr;
         TRY(h->alloc(&lt, (size_t)(nd * nd)));
-        TRY(h->alloc(&col, (size_t)nd + 1));
+        TRY(h->alloc(&col, (size_t)dense_lu_scratch((int)nd)));
         TRY(coarse_dense(b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, s));
         TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, lt, col, h->d_err, s));
         TRY(check_dev(h, s));

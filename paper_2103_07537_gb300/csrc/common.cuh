@@ -22,6 +22,7 @@ enum DevErr : int {
     kDevBadPattern = 3,   // unsorted columns / missing diagonal / out-of-range index
     kDevRowTooLong = 4,   // a coarse row exceeded the RAP row capacity
     kDevNonFinite = 5,
+    kDevTimeout = 6,      // a bounded wait of a cooperative kernel ran out
 };
 
 __device__ __forceinline__ void set_error(int* flag, int code) { atomicCAS(flag, 0, code); }
@@ -249,9 +250,11 @@ int block_inverses(int b, int fb, int n, const int* diag, const double* vals, do
 // dense FP64 coarsest matrix, LU with partial pivoting, inverse
 int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals, double* dense,
                  cudaStream_t s);
-// a (nd x nd, row-major) is factored in place; inv receives A^{-1}; lt: nd*nd
-// doubles of scratch; col: nd + 1 doubles of scratch
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* col, int* err, cudaStream_t s);
+// a (nd x nd, row-major) is factored in place; inv receives A^{-1}; piv (nd
+// ints) receives the logical row position of every row; lt: nd*nd doubles of
+// scratch; work: dense_lu_scratch(nd) doubles of scratch
+long dense_lu_scratch(int nd);
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* work, int* err, cudaStream_t s);
 int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s);
 long scan_tmp_bytes(int n);
 int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);

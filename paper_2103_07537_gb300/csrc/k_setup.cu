@@ -919,13 +919,15 @@ __global__ void lu_update_kernel(int nd, int k, double* __restrict__ a, const do
     }
 }
 
-// lt = transpose of the packed LU factors (column k of L and U contiguous)
-__global__ void transpose_kernel(int nd, const double* __restrict__ a, double* __restrict__ lt) {
+// lt = transpose of the packed LU factors (column k of L and U contiguous);
+// logical row r of the factors is row perm[r] of a
+__global__ void transpose_kernel(int nd, const double* __restrict__ a, const int* __restrict__ perm,
+                                 double* __restrict__ lt) {
     __shared__ double tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int r = by + y, c = bx + threadIdx.x;
-        if (r < nd && c < nd) tile[y][threadIdx.x] = a[(size_t)r * nd + c];
+        if (r < nd && c < nd) tile[y][threadIdx.x] = a[(size_t)perm[r] * nd + c];
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -934,27 +936,21 @@ __global__ void transpose_kernel(int nd, const double* __restrict__ a, double* _
     }
 }
 
-// Inverse column by column: column c of A^{-1} solves L U x = P e_c.  One CTA
-// per column (grid-stride over columns), x in shared memory; lt holds the
-// factors column-major so that the threads of a step read consecutive
-// addresses.
+// Inverse column by column: column c of A^{-1} solves L U x = P e_c, whose
+// one sits at the logical position pos[c].  One CTA per column (grid-stride
+// over columns), x in shared memory; lt holds the factors column-major so
+// that the threads of a step read consecutive addresses.  (Several columns
+// per CTA measured slower: the larger shared-memory share cuts the CTAs per
+// SM that hide the steps' latency.)
 constexpr int kInvThreads = 256;
 __global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, const double* __restrict__ lt,
-                                                                      const int* __restrict__ piv,
+                                                                      const int* __restrict__ pos,
                                                                       double* __restrict__ inv) {
     extern __shared__ double x[];
     __shared__ int pos0;
     const int tid = threadIdx.x;
     for (int c = blockIdx.x; c < nd; c += gridDim.x) {
-        if (tid == 0) {  // P e_c: the swaps applied in order to the unit vector
-            int pos = c;
-            for (int k = 0; k < nd; ++k) {
-                const int pk = piv[k];
-                if (pk == pos) pos = k;
-                else if (k == pos) pos = pk;
-            }
-            pos0 = pos;
-        }
+        if (tid == 0) pos0 = pos[c];
         for (int r = tid; r < nd; r += blockDim.x) x[r] = 0.0;
         __syncthreads();
         if (tid == 0) x[pos0] = 1.0;
@@ -977,11 +973,243 @@ __global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, co
     }
 }
 
-// a: the dense matrix (factored in place), inv: its inverse, lt: nd*nd scratch
-// (the transposed factors), col: nd + 1 doubles of scratch
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* col, int* err, cudaStream_t s) {
+// Row order of factors computed with physical row swaps (the shared-memory and
+// per-column paths): the factors are already in logical order (perm = the
+// identity); pos[c] = where row c of A ends up after the swaps piv[0..nd).
+__global__ void swaps_to_pos_kernel(int nd, const int* __restrict__ piv, int* __restrict__ perm,
+                                    int* __restrict__ pos) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nd; c += gridDim.x * blockDim.x) {
+        int p = c;
+        for (int k = 0; k < nd; ++k) {
+            const int pk = piv[k];
+            if (pk == p) p = k;
+            else if (k == p) p = pk;
+        }
+        pos[c] = p;
+        perm[c] = c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LU of a larger coarsest matrix in one cooperative launch (one CTA per SM).
+// The arithmetic per entry is that of the per-column path (multiplier by a
+// rounded division, update as a rounded product then a rounded difference,
+// columns in order), so the factors are the same bits; only the schedule
+// differs:
+//  * rows are never moved: every CTA keeps the same permutation perm
+//    (logical -> physical row) and its inverse pos in shared memory and
+//    applies each pivot swap to them;
+//  * CTA q owns the physical rows q, q + G, ...; in step k it forms the
+//    multipliers of its owned rows below the pivot (shared memory), then all
+//    its threads sweep the columns c > k, each loading the pivot-row entry
+//    once and updating it into every owned row; the thread of column k + 1
+//    offers the largest |a[row][k+1]| as the pivot candidate of the next step
+//    (ties: smallest logical row);
+//  * one grid barrier per column separates the steps; the per-CTA
+//    candidates go through a two-slot buffer (step parity), so a fast CTA
+//    never overwrites candidates that a slow one still reads.
+// The barrier is a counter plus a generation word in global memory; a wait
+// that exceeds its bound sets kDevTimeout and the CTA returns (the others then
+// run out at their next barrier), so the kernel always ends.
+// ---------------------------------------------------------------------------
+constexpr int kCoopThreads = 512;
+constexpr int kCoopMaxCtas = 256;
+constexpr long kBarrierSpins = 1L << 24;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            bar[0] = 0u;  // nobody arrives again before the generation moves
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long spins = 0;  // one L2 round trip per spin: the bound is well over a second
+            while (*gen == g) {
+                if (++spins > kBarrierSpins) {
+                    set_error(err, kDevTimeout);
+                    s_ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// (v, i) -> the CTA's maximum v, ties to the smallest i; valid in thread 0
+__device__ __forceinline__ void cta_argmax(double& v, int& i, double* red_v, int* red_i) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+    if (lane == 0) {
+        red_v[wid] = v;
+        red_i[wid] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (red_v[w] > v || (red_v[w] == v && red_i[w] < i)) {
+                v = red_v[w];
+                i = red_i[w];
+            }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* __restrict__ a,
+                                                                const double* __restrict__ norm,
+                                                                double* __restrict__ cand_v, int* __restrict__ cand_i,
+                                                                unsigned* __restrict__ bar, int* __restrict__ perm_out,
+                                                                int* __restrict__ pos_out, int* err) {
+    const int G = gridDim.x, q = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int M = (nd - q + G - 1) / G;  // owned physical rows q + G m, m < M
+    extern __shared__ int sh_rows[];
+    int* perm = sh_rows;                 // [nd] logical -> physical
+    int* pos = sh_rows + nd;             // [nd] physical -> logical
+    int* s_act = sh_rows + 2 * nd;       // [M] 1 if the owned row is below the pivot
+    double* s_l = reinterpret_cast<double*>(sh_rows + 2 * nd + ((M + 1) & ~1));  // [M] multipliers
+    __shared__ double red_v[kCoopThreads / 32];
+    __shared__ int red_i[kCoopThreads / 32];
+    __shared__ int s_piv;
+    for (int r = tid; r < nd; r += blockDim.x) {
+        perm[r] = r;
+        pos[r] = r;
+    }
+    // candidates for column 0: the owned rows
+    double bv = -1.0;
+    int bi = nd;
+    for (int m = tid; m < M; m += blockDim.x) {
+        const int ph = q + G * m;
+        const double v = fabs(__ldcg(a + (size_t)ph * nd));
+        if (v > bv || (v == bv && ph < bi)) {
+            bv = v;
+            bi = ph;
+        }
+    }
+    cta_argmax(bv, bi, red_v, red_i);
+    if (tid == 0) {
+        cand_v[q] = bv;
+        cand_i[q] = bi;
+    }
+    if (!grid_barrier(bar, err)) return;
+    for (int k = 0; k < nd; ++k) {
+        const int buf = (k & 1) * G;
+        if (warp == 0) {  // the pivot of column k from the G candidates
+            double v = -1.0;
+            int i = nd;
+            for (int c = lane; c < G; c += 32) {
+                const double cv = __ldcg(cand_v + buf + c);
+                const int ci = __ldcg(cand_i + buf + c);
+                if (cv > v || (cv == v && ci < i)) {
+                    v = cv;
+                    i = ci;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+                if (ov > v || (ov == v && oi < i)) {
+                    v = ov;
+                    i = oi;
+                }
+            }
+            if (lane == 0) {
+                s_piv = i;
+                const int pk = perm[k], pp = perm[i];
+                perm[k] = pp;
+                perm[i] = pk;
+                pos[pp] = k;
+                pos[pk] = i;
+                if (q == 0 && (!(v >= 1e-14 * norm[0]) || norm[0] == 0.0)) set_error(err, kDevSingularCoarse);
+            }
+        }
+        __syncthreads();
+        const int pr = perm[k];
+        const double* prow = a + (size_t)pr * nd;
+        const double akk = __ldcg(prow + k);
+        // multipliers of the owned rows below the pivot (stored in column k)
+        for (int m = tid; m < M; m += blockDim.x) {
+            const int ph = q + G * m;
+            const int act = pos[ph] > k;
+            s_act[m] = act;
+            if (act) {
+                const double l = __ddiv_rn(__ldcg(a + (size_t)ph * nd + k), akk);
+                s_l[m] = l;
+                a[(size_t)ph * nd + k] = l;
+            }
+        }
+        __syncthreads();
+        // trailing update of the owned rows; thread 0 holds column k + 1
+        // (loading every owned row's entry before the stores measured slower:
+        // the register tile lowers the occupancy more than it overlaps loads)
+        bv = -1.0;
+        bi = nd;
+        for (int c = k + 1 + tid; c < nd; c += blockDim.x) {
+            const double pc = __ldcg(prow + c);
+            for (int m = 0; m < M; ++m) {
+                if (!s_act[m]) continue;
+                double* e = a + (size_t)(q + G * m) * nd + c;
+                const double v = __dsub_rn(__ldcg(e), __dmul_rn(s_l[m], pc));
+                *e = v;
+                if (c == k + 1) {
+                    const int lr = pos[q + G * m];
+                    const double av = fabs(v);
+                    if (av > bv || (av == bv && lr < bi)) {
+                        bv = av;
+                        bi = lr;
+                    }
+                }
+            }
+        }
+        if (tid == 0) {  // candidates of column k + 1 into the other slot
+            cand_v[(G - buf) + q] = bv;
+            cand_i[(G - buf) + q] = bi;
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+    if (q == 0)
+        for (int r = tid; r < nd; r += blockDim.x) {
+            perm_out[r] = perm[r];
+            pos_out[r] = pos[r];
+        }
+}
+
+// shared memory of lu_coop_kernel with G CTAs: perm, pos, the owned-row flags
+// (padded to an even count) and multipliers
+static size_t coop_smem(int nd, int G) {
+    const int M = (nd + G - 1) / G;
+    return sizeof(int) * (2 * (size_t)nd + (size_t)((M + 1) & ~1)) + sizeof(double) * (size_t)M;
+}
+
+long dense_lu_scratch(int nd) { return (long)nd + 1 + 3L * kCoopMaxCtas + 2 + nd + 2; }
+
+// a: the dense matrix (factored in place), inv: its inverse, lt: nd*nd
+// scratch (the transposed factors), work: dense_lu_scratch(nd) doubles
+int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* work, int* err, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
     int n = 0;
+    double* col = work;                                      // [nd] multipliers, [nd] the norm
+    double* cand_v = work + nd + 1;                          // [2 * kCoopMaxCtas]
+    int* cand_i = reinterpret_cast<int*>(cand_v + 2 * kCoopMaxCtas);  // [2 * kCoopMaxCtas]
+    unsigned* bar = reinterpret_cast<unsigned*>(cand_v + 3 * kCoopMaxCtas);  // [2]
+    int* perm = reinterpret_cast<int*>(cand_v + 3 * kCoopMaxCtas + 2);       // [nd]
+    int* pos_tmp = perm + nd;                                                // [nd]
+    int* pos = piv;  // on return piv holds the logical position of every row
+    bool coop_done = false;
     if (nd <= kLuSmemMax) {
         const size_t smem = sizeof(double) * (size_t)nd * nd;
         BAMG_CUDA_TRY(cudaFuncSetAttribute(lu_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -990,20 +1218,49 @@ int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, doubl
     } else {
         lu_norm_kernel<<<1, kLuThreads, 0, s>>>(nd, a, col + nd);
         n += 1;
-        for (int k = 0; k < nd; ++k) {
-            lu_pivot_kernel<<<1, kLuThreads, 0, s>>>(nd, k, a, piv, col, col + nd, err);
-            const long m = (long)(nd - k - 1) * (nd - k - 1);
-            if (m > 0) {
-                const int blocks = (int)((m + 255) / 256 < 152L * 8 ? (m + 255) / 256 : 152L * 8);
-                lu_update_kernel<<<blocks, 256, 0, s>>>(nd, k, a, col);
+        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        size_t smem = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms <= kCoopMaxCtas &&
+            (smem = coop_smem(nd, sms)) > 0 &&
+            cudaFuncSetAttribute(lu_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel, kCoopThreads, smem) ==
+                cudaSuccess &&
+            per_sm >= 1) {
+            BAMG_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+            const double* normp = col + nd;
+            void* args[] = {&nd, &a, (void*)&normp, &cand_v, &cand_i, &bar, &perm, &pos, &err};
+            if (cudaLaunchCooperativeKernel((void*)lu_coop_kernel, dim3(sms), dim3(kCoopThreads), args, smem, s) ==
+                cudaSuccess) {
+                coop_done = true;
+                n += 1;
+            } else {
+                (void)cudaGetLastError();  // not launched: the per-column path below
+            }
+        }
+        if (!coop_done) {
+            for (int k = 0; k < nd; ++k) {
+                lu_pivot_kernel<<<1, kLuThreads, 0, s>>>(nd, k, a, piv, col, col + nd, err);
+                const long m = (long)(nd - k - 1) * (nd - k - 1);
+                if (m > 0) {
+                    const int blocks = (int)((m + 255) / 256 < 152L * 8 ? (m + 255) / 256 : 152L * 8);
+                    lu_update_kernel<<<blocks, 256, 0, s>>>(nd, k, a, col);
+                    n += 1;
+                }
                 n += 1;
             }
-            n += 1;
         }
     }
-    transpose_kernel<<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, lt);
+    if (!coop_done) {  // rows were swapped in place: identity order, positions from the swaps
+        swaps_to_pos_kernel<<<ceil_div(nd, 256), 256, 0, s>>>(nd, piv, perm, pos_tmp);
+        BAMG_CUDA_TRY(cudaMemcpyAsync(pos, pos_tmp, sizeof(int) * (size_t)nd, cudaMemcpyDeviceToDevice, s));
+        n += 1;
+    }
+    transpose_kernel<<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, perm, lt);
     const int cols = nd < 152 * 8 ? nd : 152 * 8;
-    lu_inverse_cols_kernel<<<cols, kInvThreads, sizeof(double) * (size_t)nd, s>>>(nd, lt, piv, inv);
+    lu_inverse_cols_kernel<<<cols, kInvThreads, sizeof(double) * (size_t)nd, s>>>(nd, lt, pos, inv);
     return launched(n + 2);
 }
 

@@ -326,3 +326,25 @@ def test_programmatic_dependent_launch_gives_identical_cycles(prec):
             outs.append(z.clone())
     for z in outs[1:]:
         assert torch.equal(z, outs[0])
+
+
+@pytest.mark.parametrize("s_fn,levels", [(lambda: P.mhd2d(40, 4), 2), (lambda: P.stokes2d(40, 3), 2),
+                                         (lambda: P.random_block_system(24, 4, [0, 0, 1, 1], seed=9), 2)])
+def test_large_coarsest_factorisation(s_fn, levels):
+    """Coarsest operators above the shared-memory LU size (the cooperative
+    factorisation): V-cycle and FGMRES against the oracle's dense LU."""
+    s = s_fn()
+    kw = dict(max_levels=levels, max_coarse=0)
+    ref = make_oracle(s, **kw)
+    sol = make_solver(s, **kw)
+    nc = sol.level(sol.num_levels - 1)["n"] * s.b
+    assert 158 < nc <= 4096, nc
+    r = P.uniform_pm1(15, 0, s.n_unknowns)
+    z = torch.empty(s.n_unknowns, dtype=torch.float64, device="cuda")
+    sol.apply(dev(r), z)
+    torch.cuda.synchronize()
+    assert rel_max(z.cpu().numpy(), ref.vcycle(r)) <= 1e-12
+    x = torch.zeros_like(z)
+    st, it, rr = sol.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=500)
+    _, it_o, _, ok = ref.fgmres(s.rhs, tol=1e-8, restart=30, max_iter=500)
+    assert st == 0 and ok and abs(it - it_o) <= 1
