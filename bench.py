@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--weights", default=None, help="damping network parameters (default: the committed file)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="row mappings: 1 = timed at setup (default); 0 / 2 = warp / thread per row everywhere "
+                         "(for profiler runs that must use the mappings a timed run chose)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and plain-hierarchy comparisons (for profiler launch lists)")
     ap.add_argument("--ref-iters", type=int, default=30,
@@ -322,7 +325,7 @@ def run_ours(args):
     main_prec = wl["prec"]
     other_prec = 32 if main_prec == 64 else 64
     params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
-                                       mlp=weights, mlp_levels=mlp_levels)
+                                       mlp=weights, mlp_levels=mlp_levels, autotune=args.autotune)
 
     def setup(params):
         if batched:
@@ -490,8 +493,10 @@ def run_ours(args):
             tj = json.load(open(os.path.join(pdir, f)))
         except Exception:
             continue
+        mapping = tj.get("smoother_mapping")
         if tj.get("source_digest") == source_digest(dom) and tj.get("kind") == dom and \
-                tj.get("workload") == args.workload:
+                tj.get("workload") == args.workload and \
+                (mapping is None or mapping == [lv.get("smoother_mapping") for lv in stats["levels"][:-1]]):
             traffic = tj.get("dram_bytes_per_launch")
     if t_alu > t_mem:
         roofline = {"bound": "alu", "achieved": tfl, "peak": alu_peak_tflops, "unit": "TFLOP/s",
@@ -625,6 +630,8 @@ def run_ours(args):
                 "vcycle_ms": statistics.median(vt), "setup_ms": statistics.median(st_times),
                 "levels": [lv["n"] for lv in stats["levels"]],
                 "colours": [lv["colours"] for lv in stats["levels"]],
+                "mappings": {"smoother": [lv.get("smoother_mapping") for lv in stats["levels"][:-1]],
+                             "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
                 "cycle_prec": main_prec, "variant": variant, "plain": plain, "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,

@@ -545,6 +545,9 @@ static int smoothed_galerkin(bamg_ctx* h, int l, cudaStream_t s) {
     return BAMG_OK;
 }
 
+// a non-default row mapping must beat warp-per-row by more than 3%
+constexpr float kTuneMargin = 0.97f;
+
 // average device time (us) of `reps` launches of f after one warm-up launch
 template <class F>
 static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& f) {
@@ -593,7 +596,10 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         a.F = h->F;
         a.omega = h->p.omega;
         a.omega_node = level_omega<T>(L);
-        const int reps = 3;
+        // 10 timed launches per candidate; a thread-per-row mapping replaces the
+        // warp-per-row one only when it is faster by more than kTuneMargin (3
+        // launches and a plain minimum flipped between runs on near ties)
+        const int reps = 10;
         L.tune_us[0] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
         L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 0); });
         L.tune_us[4] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 1); });
@@ -608,21 +614,21 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         else if (h->p.autotune == 3) L.bgs_tpr = 2;
         else if (h->p.autotune == 1) {
             L.bgs_tpr = 0;
-            if (L.tune_us[1] < L.tune_us[0]) L.bgs_tpr = 1;
-            if (L.tune_us[4] < L.tune_us[L.bgs_tpr]) L.bgs_tpr = 2;
+            if (L.tune_us[1] < kTuneMargin * L.tune_us[0]) L.bgs_tpr = 1;
+            if (L.tune_us[4] < (L.bgs_tpr ? L.tune_us[1] : kTuneMargin * L.tune_us[0])) L.bgs_tpr = 2;
         }
-        L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < L.tune_us[2]);
+        L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
     }
     {
         const Level& L0 = h->lev[0];
         BAMG_CUDA_TRY(cudaMemsetAsync(h->cyc_in, 0, sizeof(double) * (size_t)L0.n * b, s));
-        const float t0 = time_launch(s, e0, e1, 3, [&] {
+        const float t0 = time_launch(s, e0, e1, 10, [&] {
             return launch_spmv<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
         });
-        const float t1 = time_launch(s, e0, e1, 3, [&] {
+        const float t1 = time_launch(s, e0, e1, 10, [&] {
             return launch_spmv_tpr<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
         });
-        h->outer_spmv_tpr = h->p.autotune == 2 || (h->p.autotune == 1 && t1 < t0);
+        h->outer_spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && t1 < kTuneMargin * t0);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
