@@ -90,8 +90,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--weights", default=None, help="damping network parameters (default: the committed file)")
     ap.add_argument("--autotune", type=int, default=1,
-                    help="row mappings: 1 = timed at setup (default); 0 / 2 = warp / thread per row everywhere "
-                         "(for profiler runs that must use the mappings a timed run chose)")
+                    help="row mappings: 1 = timed at setup (default); 0 / 2 / 3 / 4 = warp per row, thread per "
+                         "row, thread per row in half-size CTAs, four lanes per row everywhere (for profiler runs "
+                         "that must use the mappings a timed run chose)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and plain-hierarchy comparisons (for profiler launch lists)")
     ap.add_argument("--ref-iters", type=int, default=30,
@@ -631,7 +632,8 @@ def run_ours(args):
                 "levels": [lv["n"] for lv in stats["levels"]],
                 "colours": [lv["colours"] for lv in stats["levels"]],
                 "mappings": {"smoother": [lv.get("smoother_mapping") for lv in stats["levels"][:-1]],
-                             "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]]},
+                             "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
+                             "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
                 "cycle_prec": main_prec, "variant": variant, "plain": plain, "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,

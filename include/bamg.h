@@ -71,7 +71,9 @@ typedef struct {
     int autotune;     /* row mapping of the smoother and SpMV kernels: 1 = time warp-per-row and
                          thread-per-row (smoother: also in half-size CTAs) on every level at setup
                          and keep the fastest (default); 0 = warp-per-row everywhere; 2 =
-                         thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs       */
+                         thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
+                         4 = as 2 with four lanes per smoother row (each a quarter of the
+                         row's blocks); 1 also times the variants of 3 and 4                    */
     /* ---- beyond the paper: smoothed transfers, per-node damping, learned weights ---- */
     int smooth_p;     /* 0: tentative P (default); 1: on every coarsened level the smoothed
                          P_f = (I - W_f D_ff^{-1} A_ff) P^_f per field (see amg_setup)        */

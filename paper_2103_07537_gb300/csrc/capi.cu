@@ -119,10 +119,10 @@ struct Level {
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
     // row mapping chosen for this level: smoother 0 warp per node, 1 thread per row, 2 thread per
-    // row in half-size CTAs; residual 0 warp per row, 1 thread per row
+    // row in half-size CTAs, 3 four lanes per row; residual 0 warp per row, 1 thread per row
     int bgs_tpr = 0, spmv_tpr = 0;
-    // measured: smoother warp / thread / thread-half, residual warp / thread
-    float tune_us[5] = {0, 0, 0, 0, 0};
+    // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split
+    float tune_us[6] = {0, 0, 0, 0, 0, 0};
     // node range of every system of a batch on this level (host and device)
     std::vector<int> sys_off;
     int* sys_off_d = nullptr;
@@ -603,6 +603,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         L.tune_us[0] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
         L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 0); });
         L.tune_us[4] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 1); });
+        L.tune_us[5] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 2); });
         const T* x = static_cast<const T*>(L.xa);
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
@@ -610,12 +611,14 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
                                    [&] { return launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
         L.tune_us[3] = time_launch(
             s, e0, e1, reps, [&] { return launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
-        if (h->p.autotune == 2) L.bgs_tpr = 1;
-        else if (h->p.autotune == 3) L.bgs_tpr = 2;
+        if (h->p.autotune >= 2) L.bgs_tpr = h->p.autotune - 1;
         else if (h->p.autotune == 1) {
-            L.bgs_tpr = 0;
-            if (L.tune_us[1] < kTuneMargin * L.tune_us[0]) L.bgs_tpr = 1;
-            if (L.tune_us[4] < (L.bgs_tpr ? L.tune_us[1] : kTuneMargin * L.tune_us[0])) L.bgs_tpr = 2;
+            // the fastest thread-per-row variant replaces warp per node only by the margin
+            const float tv[3] = {L.tune_us[1], L.tune_us[4], L.tune_us[5]};
+            int best = 0;
+            for (int v = 1; v < 3; ++v)
+                if (tv[v] < tv[best]) best = v;
+            L.bgs_tpr = tv[best] < kTuneMargin * L.tune_us[0] ? best + 1 : 0;
         }
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
     }
@@ -958,7 +961,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 3 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        prm.autotune < 0 || prm.autotune > 4 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
@@ -1078,7 +1081,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
             continue;
         }
         PL(BAMG_K_SMOOTH, bytes, flops,
-           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr == 2 ? 1 : 0)
+           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr - 1)
                      : launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
     return BAMG_OK;
@@ -1792,11 +1795,15 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colours\":" + std::to_string(L.n_colours) + ",\"aggregates\":" + std::to_string(L.n_agg) +
              ",\"aggregation_rounds\":" + std::to_string(L.agg_rounds) +
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
-             ",\"smoother_mapping\":\"" + (L.bgs_tpr == 2 ? "thread-half" : L.bgs_tpr ? "thread" : "warp") +
+             ",\"smoother_mapping\":\"" + (L.bgs_tpr == 3   ? "thread-split"
+                                          : L.bgs_tpr == 2 ? "thread-half"
+                                          : L.bgs_tpr      ? "thread"
+                                                           : "warp") +
              "\",\"residual_mapping\":\"" +
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
-             std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) +
+             std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
+             std::to_string(L.tune_us[5]) +
              "],\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0") + "}";
     }

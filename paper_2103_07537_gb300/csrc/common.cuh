@@ -165,8 +165,10 @@ template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
 // thread-per-row variants (more loads in flight per warp; for large levels)
 template <typename T>
-// half = 1: CTAs of half the threads (a small colour spread over more SMs)
-int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int half = 0);
+// variant 0: one thread per scalar row; 1: as 0 in CTAs of half the threads (a
+// small colour spread over more SMs); 2: four lanes per scalar row, each
+// taking every fourth block (shorter dependent-load chains per thread)
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
 template <typename T>
 int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
                     cudaStream_t s);

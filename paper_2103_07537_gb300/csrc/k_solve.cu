@@ -438,15 +438,20 @@ struct TprBlock {
     static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
 };
 
-// One colour of one field step (same arithmetic as bgs_node), FB threads per
-// node; the FB row sums meet in shared memory for the inverse.
-template <typename T, int B, int FB>
+// One colour of one field step (same arithmetic as bgs_node up to the order
+// of the row sum), G * FB threads per node: the G consecutive lanes of scalar
+// row r take every G-th block of the row (G = 1: the whole row), their
+// partial sums meet by a shuffle, and the FB row sums in shared memory for
+// the inverse.  G > 1 shortens each thread's chain of index-then-gather loads
+// (one block row after another), the latency that bounds large colours.
+template <typename T, int B, int FB, int G>
 __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs a) {
     __shared__ T sh_t[TprBlock<FB>::kThreads];
     const int tloc = threadIdx.x;
-    const int nloc = tloc / FB;
-    const int r = tloc - nloc * FB;
-    const long q = (long)blockIdx.x * (blockDim.x / FB) + nloc;
+    const int nloc = tloc / (FB * G);
+    const int w = tloc - nloc * (FB * G);
+    const int r = w / G, sl = w - r * G;  // scalar row, slice of the row's blocks
+    const long q = (long)blockIdx.x * (blockDim.x / (FB * G)) + nloc;
     const bool act = q < a.n_in_colour;
     const int f0 = a.field * FB;
     const T* __restrict__ vals = static_cast<const T*>(a.vals);
@@ -455,14 +460,14 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
     const T* __restrict__ xt = static_cast<const T*>(a.xt);
     int i = 0;
     T t = T(0);
+    T acc = T(0);
     if (act) {
         i = __ldg(a.nodes + q);
         const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
         pdl_wait();
         pdl_trigger();
-        T acc = T(0);
 #pragma unroll 4
-        for (int k = k0; k < k1; ++k) {
+        for (int k = k0 + sl; k < k1; k += G) {
             const int j = __ldg(a.ci + k);
             T arow[B];
             load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
@@ -490,11 +495,15 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
                     }
             }
         }
-        t = static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + r] - acc;
     }
-    sh_t[tloc] = t;
+    if constexpr (G > 1) {  // the G slices of a row are consecutive lanes of one warp
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
+    if (act && sl == 0) t = static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + r] - acc;
+    if (sl == 0) sh_t[nloc * FB + r] = t;
     __syncthreads();
-    if (!act) return;
+    if (!act || sl != 0) return;
     const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)r * FB;
     T xn = T(0);
 #pragma unroll
@@ -513,16 +522,21 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
 }
 
 template <typename T>
-int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int half) {
+int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant) {
     if (a.n_in_colour <= 0) return BAMG_OK;
     switch (b * 16 + fb) {
-#define CASE(BB, FF)                                                                                         \
-    case BB * 16 + FF: {                                                                                     \
-        const int threads = TprBlock<FF>::kThreads >> (half ? 1 : 0);                                       \
-        if (launch_k(bgs_tpr_kernel<T, BB, FF>, ceil_div(a.n_in_colour, threads / FF), threads, 0, s, a) !=   \
-            cudaSuccess)                                                                                     \
-            return BAMG_ECUDA;                                                                               \
-        break;                                                                                               \
+#define CASE(BB, FF)                                                                                          \
+    case BB * 16 + FF: {                                                                                      \
+        const int threads = TprBlock<FF>::kThreads >> (variant == 1 ? 1 : 0);                                 \
+        cudaError_t e;                                                                                        \
+        if (variant == 2)                                                                                     \
+            e = launch_k(bgs_tpr_kernel<T, BB, FF, 4>, ceil_div(a.n_in_colour, threads / (FF * 4)), threads,  \
+                         0, s, a);                                                                            \
+        else                                                                                                  \
+            e = launch_k(bgs_tpr_kernel<T, BB, FF, 1>, ceil_div(a.n_in_colour, threads / FF), threads, 0, s, \
+                         a);                                                                                  \
+        if (e != cudaSuccess) return BAMG_ECUDA;                                                              \
+        break;                                                                                                \
     }
         CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
 #undef CASE

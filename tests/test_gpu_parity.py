@@ -120,7 +120,8 @@ def test_hierarchy_matches_oracle(name):
 # V-cycle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mapping", [dict(tail_dofs=0, autotune=0), dict(tail_dofs=65536, autotune=0),
-                                     dict(tail_dofs=0, autotune=2), dict(tail_dofs=0, autotune=3)])
+                                     dict(tail_dofs=0, autotune=2), dict(tail_dofs=0, autotune=3),
+                                     dict(tail_dofs=0, autotune=4)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_vcycle_fp64_matches_oracle(name, mapping):
     s, kw = SYSTEMS[name]()
@@ -167,14 +168,15 @@ def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
     assert torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2])
 
 
+@pytest.mark.parametrize("tuned", [(2, "thread"), (4, "thread-split")])
 @pytest.mark.parametrize("prec", [64, 32])
-def test_row_mappings_agree_and_solve(prec):
+def test_row_mappings_agree_and_solve(prec, tuned):
     # warp-per-row and thread-per-row kernels: same cycle up to summation order
     s, kw = SYSTEMS["mhd2d_41_ragged"]()
     gw = make_solver(s, autotune=0, cycle_prec=prec, **kw)
-    gt = make_solver(s, autotune=2, cycle_prec=prec, **kw)
+    gt = make_solver(s, autotune=tuned[0], cycle_prec=prec, **kw)
     st = gt.stats()["levels"]
-    assert all(lv["smoother_mapping"] == "thread" for lv in st[:-1])
+    assert all(lv["smoother_mapping"] == tuned[1] for lv in st[:-1])
     r = dev(np.random.default_rng(9).standard_normal(s.n_unknowns))
     zw, zt = torch.empty_like(r), torch.empty_like(r)
     gw.apply(r, zw)
