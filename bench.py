@@ -93,6 +93,8 @@ def parse():
                     help="row mappings: 1 = timed at setup (default); 0 / 2 / 3 / 4 = warp per row, thread per "
                          "row, thread per row in half-size CTAs, four lanes per row everywhere (for profiler runs "
                          "that must use the mappings a timed run chose)")
+    ap.add_argument("--coarse-prec", type=int, default=None, choices=[32, 64],
+                    help="precision of the coarsest direct solve of FP32 cycles (default: the workload's)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and plain-hierarchy comparisons (for profiler launch lists)")
     ap.add_argument("--ref-iters", type=int, default=30,
@@ -325,8 +327,10 @@ def run_ours(args):
     restart = wl["restart"]
     main_prec = wl["prec"]
     other_prec = 32 if main_prec == 64 else 64
+    coarse_prec = (args.coarse_prec or wl.get("coarse_prec", 64)) if main_prec == 32 else 64
     params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
-                                       mlp=weights, mlp_levels=mlp_levels, autotune=args.autotune)
+                                       mlp=weights, mlp_levels=mlp_levels, autotune=args.autotune,
+                                       coarse_prec=coarse_prec)
 
     def setup(params):
         if batched:
@@ -635,7 +639,8 @@ def run_ours(args):
                              "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
                              "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
-                "cycle_prec": main_prec, "variant": variant, "plain": plain, "kernels": ksum, "roofline": roofline,
+                "cycle_prec": main_prec, "coarse_prec": coarse_prec, "variant": variant, "plain": plain,
+                "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -103,6 +103,12 @@ typedef struct {
                          (each may be scheduled while its predecessor drains and waits for its
                          inputs in hardware); 0 (default): ordinary launches. Same results; on
                          GB300 within a few percent either way, so off by default.            */
+    int coarse_prec;  /* precision of the coarsest direct solve (LU with partial pivoting, its
+                         inverse, and the per-cycle product with it) of a single system:
+                         64 (default) or 32 (FP32, only with cycle_prec 32: GB300 runs FP32 at
+                         64 times its FP64 rate). The LU is of the coarsest Galerkin matrix
+                         rounded to FP32; a pivot below 1e-6 times its infinity norm reports
+                         BAMG_ESINGULAR_COARSE. Batches keep FP64 per-system inverses.        */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

@@ -191,6 +191,7 @@ struct bamg_ctx {
     Level lev[kMaxLevels];
     int nd = 0;
     double *coarse_a = nullptr, *coarse_inv = nullptr;
+    float* coarse_inv32 = nullptr;  // the FP32 inverse (coarse_prec 32), else null
     int* coarse_piv = nullptr;
     std::vector<void*> allocs;
     long bytes = 0;
@@ -353,6 +354,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->pr_storage = 32;
     p->mlp_levels = 0;
     p->use_pdl = 0;
+    p->coarse_prec = 64;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -870,15 +872,28 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         if (nd > kMaxCoarseDense) return BAMG_EUNSUPPORTED;
         h->nd = (int)nd;
         TRY(h->alloc(&h->coarse_a, (size_t)(nd * nd)));
-        TRY(h->alloc(&h->coarse_inv, (size_t)(nd * nd)));
         TRY(h->alloc(&h->coarse_piv, (size_t)nd));
-        double *lt = nullptr, *col = nullptr;
-        TRY(h->alloc(&lt, (size_t)(nd * nd)));
+        double* col = nullptr;
         TRY(h->alloc(&col, (size_t)dense_lu_scratch((int)nd)));
         TRY(coarse_dense(b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, s));
-        TRY(dense_lu_inverse((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, lt, col, h->d_err, s));
-        TRY(check_dev(h, s));
-        h->release(lt);
+        if (h->p.coarse_prec == 32) {
+            float *a32 = nullptr, *lt32 = nullptr;
+            TRY(h->alloc(&a32, (size_t)(nd * nd)));
+            TRY(h->alloc(&lt32, (size_t)(nd * nd)));
+            TRY(h->alloc(&h->coarse_inv32, (size_t)(nd * nd)));
+            TRY(launch_convert_d2f(nd * nd, h->coarse_a, a32, s));
+            TRY(dense_lu_inverse<float>((int)nd, a32, h->coarse_piv, h->coarse_inv32, lt32, col, h->d_err, s));
+            TRY(check_dev(h, s));
+            h->release(lt32);
+            h->release(a32);
+        } else {
+            double* lt = nullptr;
+            TRY(h->alloc(&h->coarse_inv, (size_t)(nd * nd)));
+            TRY(h->alloc(&lt, (size_t)(nd * nd)));
+            TRY(dense_lu_inverse<double>((int)nd, h->coarse_a, h->coarse_piv, h->coarse_inv, lt, col, h->d_err, s));
+            TRY(check_dev(h, s));
+            h->release(lt);
+        }
         h->release(col);
         h->t_phase[5] += ms_since(tp);
         tp = Clock::now();
@@ -965,7 +980,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
-        prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1))
+        prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1) ||
+        (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32))
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -1139,18 +1155,21 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     }
     if (l == h->nlev - 1) {
         const double nd = h->nd;
-        const double bytes = nd * nd * 8.0 + 2.0 * nd * sizeof(T), flops = 2.0 * nd * nd;
+        const double bytes = nd * nd * (h->coarse_inv32 ? 4.0 : 8.0) + 2.0 * nd * sizeof(T), flops = 2.0 * nd * nd;
         if (h->rec) {
             TailPhase ph{};
-            ph.type = kPhaseGemv;
+            ph.type = h->coarse_inv32 ? kPhaseGemv32 : kPhaseGemv;
             ph.n = h->nd;
-            ph.vals = h->coarse_inv;
+            ph.vals = h->coarse_inv32 ? (const void*)h->coarse_inv32 : (const void*)h->coarse_inv;
             ph.x = rhs;
             ph.y = out;
             record(h, ph, bytes, flops);
             return BAMG_OK;
         }
-        PL(BAMG_K_COARSE, bytes, flops, launch_dense_gemv<T>(h->nd, h->coarse_inv, rhs, out, s));
+        if (h->coarse_inv32)
+            PL(BAMG_K_COARSE, bytes, flops, (launch_dense_gemv<T, float>(h->nd, h->coarse_inv32, rhs, out, s)));
+        else
+            PL(BAMG_K_COARSE, bytes, flops, (launch_dense_gemv<T, double>(h->nd, h->coarse_inv, rhs, out, s)));
         return BAMG_OK;
     }
     T* xa = static_cast<T*>(L.xa);
@@ -1777,7 +1796,8 @@ extern "C" int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, d
 extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
-                    ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) + ",\"coarse_unknowns\":" +
+                    ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};

@@ -180,6 +180,7 @@ enum PhaseType : int {
     kPhaseResidual = 1,  // y = rhs - A x: rp, ci, vals, x, rhs, y, n rows
     kPhaseRestrict = 2,  // y = R x: rp = agg_ptr, ci = members, x, y, n coarse nodes
     kPhaseGemv = 3,      // y = Ainv x: vals = FP64 inverse, x, y, n = nd
+    kPhaseGemv32 = 6,    // as kPhaseGemv with the FP32 inverse
     kPhaseProlongCopy = 4,  // y = x + P rhs: ci = agg, n fine nodes
     kPhaseZero = 5,      // y = 0 over n nodes
 };
@@ -200,9 +201,10 @@ int launch_tail(int b, int fb, const TailPhase* phases, int nphase, int cluster,
 // largest resident cluster size <= want for the tail kernel (0: none)
 template <typename T>
 int tail_cluster_size(int b, int fb, int want);
-// y = Ainv x for the dense FP64 nd x nd inverse (x, y of type T)
-template <typename T>
-int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s);
+// y = Ainv x for the dense nd x nd inverse of type S (double or float; the
+// sum in S), x, y of type T
+template <typename T, typename S>
+int launch_dense_gemv(int nd, const S* ainv, const T* x, T* y, cudaStream_t s);
 int launch_cast_d2f(long m, const double* x, float* y, cudaStream_t s);
 int launch_cast_f2d(long m, const float* x, double* y, cudaStream_t s);
 
@@ -252,11 +254,12 @@ int block_inverses(int b, int fb, int n, const int* diag, const double* vals, do
 // dense FP64 coarsest matrix, LU with partial pivoting, inverse
 int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals, double* dense,
                  cudaStream_t s);
-// a (nd x nd, row-major) is factored in place; inv receives A^{-1}; piv (nd
-// ints) receives the logical row position of every row; lt: nd*nd doubles of
-// scratch; work: dense_lu_scratch(nd) doubles of scratch
+// a (nd x nd, row-major, T = double or float) is factored in place; inv
+// receives A^{-1}; piv (nd ints) receives the logical row position of every
+// row; lt: nd*nd T of scratch; work: dense_lu_scratch(nd) doubles of scratch
 long dense_lu_scratch(int nd);
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* work, int* err, cudaStream_t s);
+template <typename T>
+int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* err, cudaStream_t s);
 int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s);
 long scan_tmp_bytes(int n);
 int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);

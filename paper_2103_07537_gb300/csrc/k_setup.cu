@@ -767,28 +767,50 @@ int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals,
     return launched(1);
 }
 
-// LU factorisation.  nd <= kLuSmemMax: one CTA factors the matrix held in
-// shared memory; larger: one pivot kernel and one rank-1 update kernel per
-// column.  Both perform the same rounded operations in the same order per
-// entry, so the factors do not depend on the variant.
+// LU factorisation.  Small nd: one CTA factors the matrix held in shared
+// memory; larger: one cooperative launch (below), else one pivot kernel and
+// one rank-1 update kernel per column.  All perform the same rounded
+// operations in the same order per entry, so the factors do not depend on
+// the variant.  T = double is the coarse solve of the method; T = float
+// factors the FP32 copy of the coarsest matrix for FP32 cycles (GB300 issues
+// FP32 at 64 times its FP64 rate).
 constexpr int kLuThreads = 1024;
-constexpr int kLuSmemMax = 158;  // 158^2 doubles = 199.7 KB of shared memory
+// largest nd whose nd^2 entries fit 199.7 KB of shared memory (158^2 doubles)
+template <typename T>
+struct LuSmem {
+    static constexpr int kMax = sizeof(T) == 8 ? 158 : 223;
+};
+// a smallest pivot of 1e-14 (FP64) or 1e-6 (FP32) times the infinity norm
+// marks the matrix numerically singular
+template <typename T>
+__host__ __device__ constexpr T lu_tiny() {
+    return sizeof(T) == 8 ? T(1e-14) : T(1e-6);
+}
+
+// correctly rounded single operations (no contraction into fused multiply-adds)
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
 
 // first row r >= k of maximal |a[r][k]| over the CTA (ties: smallest r)
-__device__ __forceinline__ void pivot_search(const double* a, int nd, int k, double* red_v, int* red_i,
-                                             double* best_out, int* idx_out) {
+template <typename T>
+__device__ __forceinline__ void pivot_search(const T* a, int nd, int k, T* red_v, int* red_i, T* best_out,
+                                             int* idx_out) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double best = -1.0;
+    T best = T(-1);
     int bi = nd;
     for (int r = k + tid; r < nd; r += blockDim.x) {
-        const double v = fabs(a[(size_t)r * nd + k]);
+        const T v = fabs(a[(size_t)r * nd + k]);
         if (v > best) {
             best = v;
             bi = r;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) {
             best = ov;
@@ -801,7 +823,7 @@ __device__ __forceinline__ void pivot_search(const double* a, int nd, int k, dou
     }
     __syncthreads();
     if (tid == 0) {
-        double bv = red_v[0];
+        T bv = red_v[0];
         int bx = red_i[0];
         for (int w = 1; w < (int)(blockDim.x / 32); ++w)
             if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
@@ -818,54 +840,57 @@ __device__ __forceinline__ void pivot_search(const double* a, int nd, int k, dou
 }
 
 // infinity norm (largest absolute row sum) of the nd x nd matrix a
-__device__ __forceinline__ double inf_norm(const double* a, int nd, double* red_v) {
+template <typename T>
+__device__ __forceinline__ T inf_norm(const T* a, int nd, T* red_v) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double m = 0.0;
+    T m = T(0);
     for (int r = tid; r < nd; r += blockDim.x) {
-        double sum = 0.0;
+        T sum = T(0);
         for (int c = 0; c < nd; ++c) sum += fabs(a[(size_t)r * nd + c]);
         m = fmax(m, sum);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) red_v[wid] = m;
     __syncthreads();
-    double mm = 0.0;
+    T mm = T(0);
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmax(mm, red_v[w]);
     __syncthreads();
     return mm;
 }
 
-__global__ void __launch_bounds__(kLuThreads) lu_smem_kernel(int nd, double* __restrict__ g, int* __restrict__ piv,
+template <typename T>
+__global__ void __launch_bounds__(kLuThreads) lu_smem_kernel(int nd, T* __restrict__ g, int* __restrict__ piv,
                                                              int* err) {
-    extern __shared__ double sa[];
-    __shared__ double red_v[kLuThreads / 32];
+    extern __shared__ __align__(16) unsigned char lu_sh[];
+    T* sa = reinterpret_cast<T*>(lu_sh);
+    __shared__ T red_v[kLuThreads / 32];
     __shared__ int red_i[kLuThreads / 32];
-    __shared__ double col[kLuSmemMax];
+    __shared__ T col[LuSmem<T>::kMax];
     const int tid = threadIdx.x;
     for (int e = tid; e < nd * nd; e += blockDim.x) sa[e] = g[e];
     __syncthreads();
-    const double norm = inf_norm(sa, nd, red_v);
-    bool singular = norm == 0.0;
+    const T norm = inf_norm(sa, nd, red_v);
+    bool singular = norm == T(0);
     for (int k = 0; k < nd; ++k) {
-        double best;
+        T best;
         int p;
         pivot_search(sa, nd, k, red_v, red_i, &best, &p);
-        if (!(best >= 1e-14 * norm)) singular = true;
+        if (!(best >= lu_tiny<T>() * norm)) singular = true;
         if (tid == 0) piv[k] = p;
         if (p != k)
             for (int c = tid; c < nd; c += blockDim.x) {
-                const double t = sa[k * nd + c];
+                const T t = sa[k * nd + c];
                 sa[k * nd + c] = sa[p * nd + c];
                 sa[p * nd + c] = t;
             }
         __syncthreads();
-        const double akk = sa[k * nd + k];
-        for (int r = k + 1 + tid; r < nd; r += blockDim.x) col[r] = __ddiv_rn(sa[r * nd + k], akk);
+        const T akk = sa[k * nd + k];
+        for (int r = k + 1 + tid; r < nd; r += blockDim.x) col[r] = rn_div(sa[r * nd + k], akk);
         __syncthreads();
         const int m = nd - k - 1;
         for (int e = tid; e < m * m; e += blockDim.x) {
             const int r = k + 1 + e / m, c = k + 1 + e % m;
-            sa[r * nd + c] = __dsub_rn(sa[r * nd + c], __dmul_rn(col[r], sa[k * nd + c]));
+            sa[r * nd + c] = rn_sub(sa[r * nd + c], rn_mul(col[r], sa[k * nd + c]));
         }
         for (int r = k + 1 + tid; r < nd; r += blockDim.x) sa[r * nd + k] = col[r];
         __syncthreads();
@@ -874,56 +899,59 @@ __global__ void __launch_bounds__(kLuThreads) lu_smem_kernel(int nd, double* __r
     for (int e = tid; e < nd * nd; e += blockDim.x) g[e] = sa[e];
 }
 
-__global__ void lu_norm_kernel(int nd, const double* __restrict__ a, double* __restrict__ norm_out) {
-    __shared__ double red_v[kLuThreads / 32];
-    const double n = inf_norm(a, nd, red_v);
+template <typename T>
+__global__ void lu_norm_kernel(int nd, const T* __restrict__ a, T* __restrict__ norm_out) {
+    __shared__ T red_v[kLuThreads / 32];
+    const T n = inf_norm(a, nd, red_v);
     if (threadIdx.x == 0) *norm_out = n;
 }
 
 // column k: pivot, row swap, multipliers (stored in column k and in col)
-__global__ void __launch_bounds__(kLuThreads) lu_pivot_kernel(int nd, int k, double* __restrict__ a,
-                                                              int* __restrict__ piv, double* __restrict__ col,
-                                                              const double* __restrict__ norm, int* err) {
-    __shared__ double red_v[kLuThreads / 32];
+template <typename T>
+__global__ void __launch_bounds__(kLuThreads) lu_pivot_kernel(int nd, int k, T* __restrict__ a,
+                                                              int* __restrict__ piv, T* __restrict__ col,
+                                                              const T* __restrict__ norm, int* err) {
+    __shared__ T red_v[kLuThreads / 32];
     __shared__ int red_i[kLuThreads / 32];
     const int tid = threadIdx.x;
-    double best;
+    T best;
     int p;
     pivot_search(a, nd, k, red_v, red_i, &best, &p);
     if (tid == 0) {
         piv[k] = p;
-        if (!(best >= 1e-14 * norm[0]) || norm[0] == 0.0) set_error(err, kDevSingularCoarse);
+        if (!(best >= lu_tiny<T>() * norm[0]) || norm[0] == T(0)) set_error(err, kDevSingularCoarse);
     }
     if (p != k)
         for (int c = tid; c < nd; c += blockDim.x) {
-            const double t = a[(size_t)k * nd + c];
+            const T t = a[(size_t)k * nd + c];
             a[(size_t)k * nd + c] = a[(size_t)p * nd + c];
             a[(size_t)p * nd + c] = t;
         }
     __syncthreads();
-    const double akk = a[(size_t)k * nd + k];
+    const T akk = a[(size_t)k * nd + k];
     for (int r = k + 1 + tid; r < nd; r += blockDim.x) {
-        const double l = __ddiv_rn(a[(size_t)r * nd + k], akk);
+        const T l = rn_div(a[(size_t)r * nd + k], akk);
         col[r] = l;
         a[(size_t)r * nd + k] = l;
     }
 }
 
 // trailing update a[r][c] -= col[r] * a[k][c] for r, c > k
-__global__ void lu_update_kernel(int nd, int k, double* __restrict__ a, const double* __restrict__ col) {
+template <typename T>
+__global__ void lu_update_kernel(int nd, int k, T* __restrict__ a, const T* __restrict__ col) {
     const int m = nd - k - 1;
     const long total = (long)m * m;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         const int r = k + 1 + (int)(e / m), c = k + 1 + (int)(e % m);
-        a[(size_t)r * nd + c] = __dsub_rn(a[(size_t)r * nd + c], __dmul_rn(col[r], a[(size_t)k * nd + c]));
+        a[(size_t)r * nd + c] = rn_sub(a[(size_t)r * nd + c], rn_mul(col[r], a[(size_t)k * nd + c]));
     }
 }
 
 // lt = transpose of the packed LU factors (column k of L and U contiguous);
 // logical row r of the factors is row perm[r] of a
-__global__ void transpose_kernel(int nd, const double* __restrict__ a, const int* __restrict__ perm,
-                                 double* __restrict__ lt) {
-    __shared__ double tile[32][33];
+template <typename T>
+__global__ void transpose_kernel(int nd, const T* __restrict__ a, const int* __restrict__ perm, T* __restrict__ lt) {
+    __shared__ T tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int r = by + y, c = bx + threadIdx.x;
@@ -943,28 +971,30 @@ __global__ void transpose_kernel(int nd, const double* __restrict__ a, const int
 // per CTA measured slower: the larger shared-memory share cuts the CTAs per
 // SM that hide the steps' latency.)
 constexpr int kInvThreads = 256;
-__global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, const double* __restrict__ lt,
+template <typename T>
+__global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, const T* __restrict__ lt,
                                                                       const int* __restrict__ pos,
-                                                                      double* __restrict__ inv) {
-    extern __shared__ double x[];
+                                                                      T* __restrict__ inv) {
+    extern __shared__ __align__(16) unsigned char inv_sh[];
+    T* x = reinterpret_cast<T*>(inv_sh);
     __shared__ int pos0;
     const int tid = threadIdx.x;
     for (int c = blockIdx.x; c < nd; c += gridDim.x) {
         if (tid == 0) pos0 = pos[c];
-        for (int r = tid; r < nd; r += blockDim.x) x[r] = 0.0;
+        for (int r = tid; r < nd; r += blockDim.x) x[r] = T(0);
         __syncthreads();
-        if (tid == 0) x[pos0] = 1.0;
+        if (tid == 0) x[pos0] = T(1);
         __syncthreads();
         for (int k = pos0; k < nd; ++k) {  // unit lower triangle (entries above pos0 stay zero)
-            const double xk = x[k];
-            if (xk != 0.0)
+            const T xk = x[k];
+            if (xk != T(0))
                 for (int r = k + 1 + tid; r < nd; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
             __syncthreads();
         }
         for (int k = nd - 1; k >= 0; --k) {  // upper triangle
             if (tid == 0) x[k] /= lt[(size_t)k * nd + k];
             __syncthreads();
-            const double xk = x[k];
+            const T xk = x[k];
             for (int r = tid; r < k; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
             __syncthreads();
         }
@@ -1045,10 +1075,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 // (v, i) -> the CTA's maximum v, ties to the smallest i; valid in thread 0
-__device__ __forceinline__ void cta_argmax(double& v, int& i, double* red_v, int* red_i) {
+template <typename T>
+__device__ __forceinline__ void cta_argmax(T& v, int& i, T* red_v, int* red_i) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, i, o);
         if (ov > v || (ov == v && oi < i)) {
             v = ov;
@@ -1069,20 +1100,20 @@ __device__ __forceinline__ void cta_argmax(double& v, int& i, double* red_v, int
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* __restrict__ a,
-                                                                const double* __restrict__ norm,
-                                                                double* __restrict__ cand_v, int* __restrict__ cand_i,
+template <typename T>
+__global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, T* __restrict__ a, const T* __restrict__ norm,
+                                                                T* __restrict__ cand_v, int* __restrict__ cand_i,
                                                                 unsigned* __restrict__ bar, int* __restrict__ perm_out,
                                                                 int* __restrict__ pos_out, int* err) {
     const int G = gridDim.x, q = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int M = (nd - q + G - 1) / G;  // owned physical rows q + G m, m < M
-    extern __shared__ int sh_rows[];
+    extern __shared__ __align__(16) int sh_rows[];
     int* perm = sh_rows;                 // [nd] logical -> physical
     int* pos = sh_rows + nd;             // [nd] physical -> logical
     int* s_act = sh_rows + 2 * nd;       // [M] 1 if the owned row is below the pivot
-    double* s_l = reinterpret_cast<double*>(sh_rows + 2 * nd + ((M + 1) & ~1));  // [M] multipliers
-    __shared__ double red_v[kCoopThreads / 32];
+    T* s_l = reinterpret_cast<T*>(sh_rows + 2 * nd + ((M + 1) & ~1));  // [M] multipliers
+    __shared__ T red_v[kCoopThreads / 32];
     __shared__ int red_i[kCoopThreads / 32];
     __shared__ int s_piv;
     for (int r = tid; r < nd; r += blockDim.x) {
@@ -1090,11 +1121,11 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
         pos[r] = r;
     }
     // candidates for column 0: the owned rows
-    double bv = -1.0;
+    T bv = T(-1);
     int bi = nd;
     for (int m = tid; m < M; m += blockDim.x) {
         const int ph = q + G * m;
-        const double v = fabs(__ldcg(a + (size_t)ph * nd));
+        const T v = fabs(__ldcg(a + (size_t)ph * nd));
         if (v > bv || (v == bv && ph < bi)) {
             bv = v;
             bi = ph;
@@ -1109,10 +1140,10 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
     for (int k = 0; k < nd; ++k) {
         const int buf = (k & 1) * G;
         if (warp == 0) {  // the pivot of column k from the G candidates
-            double v = -1.0;
+            T v = T(-1);
             int i = nd;
             for (int c = lane; c < G; c += 32) {
-                const double cv = __ldcg(cand_v + buf + c);
+                const T cv = __ldcg(cand_v + buf + c);
                 const int ci = __ldcg(cand_i + buf + c);
                 if (cv > v || (cv == v && ci < i)) {
                     v = cv;
@@ -1120,7 +1151,7 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const T ov = __shfl_xor_sync(0xffffffffu, v, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, i, o);
                 if (ov > v || (ov == v && oi < i)) {
                     v = ov;
@@ -1134,20 +1165,21 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
                 perm[i] = pk;
                 pos[pp] = k;
                 pos[pk] = i;
-                if (q == 0 && (!(v >= 1e-14 * norm[0]) || norm[0] == 0.0)) set_error(err, kDevSingularCoarse);
+                if (q == 0 && (!(v >= lu_tiny<T>() * norm[0]) || norm[0] == T(0)))
+                    set_error(err, kDevSingularCoarse);
             }
         }
         __syncthreads();
         const int pr = perm[k];
-        const double* prow = a + (size_t)pr * nd;
-        const double akk = __ldcg(prow + k);
+        const T* prow = a + (size_t)pr * nd;
+        const T akk = __ldcg(prow + k);
         // multipliers of the owned rows below the pivot (stored in column k)
         for (int m = tid; m < M; m += blockDim.x) {
             const int ph = q + G * m;
             const int act = pos[ph] > k;
             s_act[m] = act;
             if (act) {
-                const double l = __ddiv_rn(__ldcg(a + (size_t)ph * nd + k), akk);
+                const T l = rn_div(__ldcg(a + (size_t)ph * nd + k), akk);
                 s_l[m] = l;
                 a[(size_t)ph * nd + k] = l;
             }
@@ -1156,18 +1188,18 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
         // trailing update of the owned rows; thread 0 holds column k + 1
         // (loading every owned row's entry before the stores measured slower:
         // the register tile lowers the occupancy more than it overlaps loads)
-        bv = -1.0;
+        bv = T(-1);
         bi = nd;
         for (int c = k + 1 + tid; c < nd; c += blockDim.x) {
-            const double pc = __ldcg(prow + c);
+            const T pc = __ldcg(prow + c);
             for (int m = 0; m < M; ++m) {
                 if (!s_act[m]) continue;
-                double* e = a + (size_t)(q + G * m) * nd + c;
-                const double v = __dsub_rn(__ldcg(e), __dmul_rn(s_l[m], pc));
+                T* e = a + (size_t)(q + G * m) * nd + c;
+                const T v = rn_sub(__ldcg(e), rn_mul(s_l[m], pc));
                 *e = v;
                 if (c == k + 1) {
                     const int lr = pos[q + G * m];
-                    const double av = fabs(v);
+                    const T av = fabs(v);
                     if (av > bv || (av == bv && lr < bi)) {
                         bv = av;
                         bi = lr;
@@ -1190,49 +1222,60 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, double* _
 
 // shared memory of lu_coop_kernel with G CTAs: perm, pos, the owned-row flags
 // (padded to an even count) and multipliers
+template <typename T>
 static size_t coop_smem(int nd, int G) {
     const int M = (nd + G - 1) / G;
-    return sizeof(int) * (2 * (size_t)nd + (size_t)((M + 1) & ~1)) + sizeof(double) * (size_t)M;
+    return sizeof(int) * (2 * (size_t)nd + (size_t)((M + 1) & ~1)) + sizeof(T) * (size_t)M;
 }
 
+// scratch of dense_lu_inverse in doubles: multipliers and the norm (nd + 1
+// values), two candidate slots (values and rows), the barrier words, perm and
+// the positions before the copy to piv
 long dense_lu_scratch(int nd) { return (long)nd + 1 + 3L * kCoopMaxCtas + 2 + nd + 2; }
 
 // a: the dense matrix (factored in place), inv: its inverse, lt: nd*nd
 // scratch (the transposed factors), work: dense_lu_scratch(nd) doubles
-int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, double* work, int* err, cudaStream_t s) {
+template <typename T>
+int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* err, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
     int n = 0;
-    double* col = work;                                      // [nd] multipliers, [nd] the norm
-    double* cand_v = work + nd + 1;                          // [2 * kCoopMaxCtas]
-    int* cand_i = reinterpret_cast<int*>(cand_v + 2 * kCoopMaxCtas);  // [2 * kCoopMaxCtas]
-    unsigned* bar = reinterpret_cast<unsigned*>(cand_v + 3 * kCoopMaxCtas);  // [2]
-    int* perm = reinterpret_cast<int*>(cand_v + 3 * kCoopMaxCtas + 2);       // [nd]
-    int* pos_tmp = perm + nd;                                                // [nd]
+    // carve the scratch by bytes (each piece 8-byte aligned)
+    char* w = reinterpret_cast<char*>(work);
+    T* col = reinterpret_cast<T*>(w);                     // [nd] multipliers, [1] the norm
+    w += 8 * ((size_t)nd + 1);
+    T* cand_v = reinterpret_cast<T*>(w);                  // [2 * kCoopMaxCtas]
+    w += 8 * (size_t)(2 * kCoopMaxCtas);
+    int* cand_i = reinterpret_cast<int*>(w);              // [2 * kCoopMaxCtas]
+    w += 8 * (size_t)kCoopMaxCtas;
+    unsigned* bar = reinterpret_cast<unsigned*>(w);       // [2]
+    w += 8 * 2;
+    int* perm = reinterpret_cast<int*>(w);                // [nd]
+    int* pos_tmp = perm + nd;                             // [nd]
     int* pos = piv;  // on return piv holds the logical position of every row
     bool coop_done = false;
-    if (nd <= kLuSmemMax) {
-        const size_t smem = sizeof(double) * (size_t)nd * nd;
-        BAMG_CUDA_TRY(cudaFuncSetAttribute(lu_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        lu_smem_kernel<<<1, kLuThreads, smem, s>>>(nd, a, piv, err);
+    if (nd <= LuSmem<T>::kMax) {
+        const size_t smem = sizeof(T) * (size_t)nd * nd;
+        BAMG_CUDA_TRY(cudaFuncSetAttribute(lu_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        lu_smem_kernel<T><<<1, kLuThreads, smem, s>>>(nd, a, piv, err);
         n += 1;
     } else {
-        lu_norm_kernel<<<1, kLuThreads, 0, s>>>(nd, a, col + nd);
+        lu_norm_kernel<T><<<1, kLuThreads, 0, s>>>(nd, a, col + nd);
         n += 1;
         int dev = 0, coop = 0, sms = 0, per_sm = 0;
         size_t smem = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms <= kCoopMaxCtas &&
-            (smem = coop_smem(nd, sms)) > 0 &&
-            cudaFuncSetAttribute(lu_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+            (smem = coop_smem<T>(nd, sms)) > 0 &&
+            cudaFuncSetAttribute(lu_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                 cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel, kCoopThreads, smem) ==
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel<T>, kCoopThreads, smem) ==
                 cudaSuccess &&
             per_sm >= 1) {
             BAMG_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-            const double* normp = col + nd;
+            const T* normp = col + nd;
             void* args[] = {&nd, &a, (void*)&normp, &cand_v, &cand_i, &bar, &perm, &pos, &err};
-            if (cudaLaunchCooperativeKernel((void*)lu_coop_kernel, dim3(sms), dim3(kCoopThreads), args, smem, s) ==
+            if (cudaLaunchCooperativeKernel((void*)lu_coop_kernel<T>, dim3(sms), dim3(kCoopThreads), args, smem, s) ==
                 cudaSuccess) {
                 coop_done = true;
                 n += 1;
@@ -1242,11 +1285,11 @@ int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, doubl
         }
         if (!coop_done) {
             for (int k = 0; k < nd; ++k) {
-                lu_pivot_kernel<<<1, kLuThreads, 0, s>>>(nd, k, a, piv, col, col + nd, err);
+                lu_pivot_kernel<T><<<1, kLuThreads, 0, s>>>(nd, k, a, piv, col, col + nd, err);
                 const long m = (long)(nd - k - 1) * (nd - k - 1);
                 if (m > 0) {
                     const int blocks = (int)((m + 255) / 256 < 152L * 8 ? (m + 255) / 256 : 152L * 8);
-                    lu_update_kernel<<<blocks, 256, 0, s>>>(nd, k, a, col);
+                    lu_update_kernel<T><<<blocks, 256, 0, s>>>(nd, k, a, col);
                     n += 1;
                 }
                 n += 1;
@@ -1258,11 +1301,13 @@ int dense_lu_inverse(int nd, double* a, int* piv, double* inv, double* lt, doubl
         BAMG_CUDA_TRY(cudaMemcpyAsync(pos, pos_tmp, sizeof(int) * (size_t)nd, cudaMemcpyDeviceToDevice, s));
         n += 1;
     }
-    transpose_kernel<<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, perm, lt);
+    transpose_kernel<T><<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, perm, lt);
     const int cols = nd < 152 * 8 ? nd : 152 * 8;
-    lu_inverse_cols_kernel<<<cols, kInvThreads, sizeof(double) * (size_t)nd, s>>>(nd, lt, pos, inv);
+    lu_inverse_cols_kernel<T><<<cols, kInvThreads, sizeof(T) * (size_t)nd, s>>>(nd, lt, pos, inv);
     return launched(n + 2);
 }
+template int dense_lu_inverse<double>(int, double*, int*, double*, double*, double*, int*, cudaStream_t);
+template int dense_lu_inverse<float>(int, float*, int*, float*, float*, double*, int*, cudaStream_t);
 
 __global__ void convert_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (long)gridDim.x * blockDim.x)

@@ -213,13 +213,14 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     }
 }
 
-// coarsest level: y_row = sum_c Ainv[row][c] x_c in FP64; whole warp
-template <typename T, bool CG>
-__device__ __forceinline__ void gemv_row(int row, int lane, int nd, const double* __restrict__ ainv, const T* x,
+// coarsest level: y_row = sum_c Ainv[row][c] x_c, summed in the inverse's
+// type S; whole warp
+template <typename T, typename S, bool CG>
+__device__ __forceinline__ void gemv_row(int row, int lane, int nd, const S* __restrict__ ainv, const T* x,
                                          T* y) {
-    const double* a = ainv + (size_t)row * nd;
-    double acc = 0.0;
-    for (int c = lane; c < nd; c += kWarp) acc = fma(__ldg(a + c), (double)ld1<T, CG>(x + c), acc);
+    const S* a = ainv + (size_t)row * nd;
+    S acc = S(0);
+    for (int c = lane; c < nd; c += kWarp) acc = fma(__ldg(a + c), (S)ld1<T, CG>(x + c), acc);
     acc = warp_sum(acc);
     if (lane == 0) y[row] = (T)acc;
 }
@@ -356,25 +357,28 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
 template int launch_bgs_colour<double>(int, int, const BgsArgs&, cudaStream_t);
 template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
 
-template <typename T>
-__global__ void dense_gemv_kernel(int nd, const double* __restrict__ ainv, const T* __restrict__ x,
+template <typename T, typename S>
+__global__ void dense_gemv_kernel(int nd, const S* __restrict__ ainv, const T* __restrict__ x,
                                   T* __restrict__ y) {
     pdl_wait();
     pdl_trigger();
     const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (row >= nd) return;
-    gemv_row<T, false>(row, threadIdx.x & 31, nd, ainv, x, y);
+    gemv_row<T, S, false>(row, threadIdx.x & 31, nd, ainv, x, y);
 }
 
-template <typename T>
-int launch_dense_gemv(int nd, const double* ainv, const T* x, T* y, cudaStream_t s) {
+template <typename T, typename S>
+int launch_dense_gemv(int nd, const S* ainv, const T* x, T* y, cudaStream_t s) {
     if (nd <= 0) return BAMG_OK;
-    if (launch_k(dense_gemv_kernel<T>, ceil_div((long)nd * kWarp, 256), 256, 0, s, nd, ainv, x, y) != cudaSuccess)
+    if (launch_k(dense_gemv_kernel<T, S>, ceil_div((long)nd * kWarp, 256), 256, 0, s, nd, ainv, x, y) !=
+        cudaSuccess)
         return BAMG_ECUDA;
     return launched(1);
 }
-template int launch_dense_gemv<double>(int, const double*, const double*, double*, cudaStream_t);
-template int launch_dense_gemv<float>(int, const double*, const float*, float*, cudaStream_t);
+template int launch_dense_gemv<double, double>(int, const double*, const double*, double*, cudaStream_t);
+template int launch_dense_gemv<float, double>(int, const double*, const float*, float*, cudaStream_t);
+template int launch_dense_gemv<float, float>(int, const float*, const float*, float*, cudaStream_t);
+template int launch_dense_gemv<double, float>(int, const float*, const double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Thread-per-row variants for large levels.  One thread owns one scalar row
@@ -586,8 +590,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(const TailPhase* 
                 break;
             case kPhaseGemv:
                 for (long row = gw; row < ph.n; row += W)
-                    gemv_row<T, true>((int)row, lane, ph.n, static_cast<const double*>(ph.vals),
-                                      static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+                    gemv_row<T, double, true>((int)row, lane, ph.n, static_cast<const double*>(ph.vals),
+                                              static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+                break;
+            case kPhaseGemv32:
+                for (long row = gw; row < ph.n; row += W)
+                    gemv_row<T, float, true>((int)row, lane, ph.n, static_cast<const float*>(ph.vals),
+                                             static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
                 break;
             case kPhaseProlongCopy:  // y = x + P uc over n fine nodes (x may equal y); uc in rhs, agg in ci
                 for (long e = gt; e < (long)ph.n * B; e += NT) {
