@@ -93,6 +93,12 @@ def parse():
                     help="row mappings: 1 = timed at setup (default); 0 / 2 / 3 / 4 = warp per row, thread per "
                          "row, thread per row in half-size CTAs, four lanes per row everywhere (for profiler runs "
                          "that must use the mappings a timed run chose)")
+    ap.add_argument("--tail-dofs", type=int, default=None,
+                    help="levels of at most this many unknowns run as one recorded launch (amg_params.tail_dofs)")
+    ap.add_argument("--tail-grid", type=int, default=None, choices=[0, 1],
+                    help="1: that launch is cooperative over every SM with grid barriers (amg_params.tail_grid)")
+    ap.add_argument("--pdl", type=int, default=1, choices=[0, 1],
+                    help="1 (default): programmatic dependent launches of the V-cycle kernels (amg_params.use_pdl)")
     ap.add_argument("--coarse-prec", type=int, default=None, choices=[32, 64],
                     help="precision of the coarsest direct solve of FP32 cycles (default: the workload's)")
     ap.add_argument("--no-variants", action="store_true",
@@ -330,7 +336,9 @@ def run_ours(args):
     coarse_prec = (args.coarse_prec or wl.get("coarse_prec", 64)) if main_prec == 32 else 64
     params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
                                        mlp=weights, mlp_levels=mlp_levels, autotune=args.autotune,
-                                       coarse_prec=coarse_prec)
+                                       coarse_prec=coarse_prec, use_pdl=args.pdl,
+                                       tail_dofs=args.tail_dofs if args.tail_dofs is not None else wl.get("tail_dofs", 0),
+                                       tail_grid=args.tail_grid if args.tail_grid is not None else wl.get("tail_grid", 0))
 
     def setup(params):
         if batched:
@@ -639,7 +647,10 @@ def run_ours(args):
                              "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
                              "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
-                "cycle_prec": main_prec, "coarse_prec": coarse_prec, "variant": variant, "plain": plain,
+                "cycle_prec": main_prec, "coarse_prec": coarse_prec, "use_pdl": args.pdl,
+                "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
+                         "cluster": stats.get("tail_cluster")}, "variant": variant,
+                "plain": plain,
                 "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}

@@ -69,9 +69,9 @@ typedef struct {
                          as one thread-block-cluster launch per V-cycle; 0 = one launch per
                          step on every level; default 0                                        */
     int autotune;     /* row mapping of the smoother and SpMV kernels: 1 = time warp-per-row and
-                         thread-per-row (smoother: also in half-size CTAs) on every level at setup
-                         and keep the fastest (default); 0 = warp-per-row everywhere; 2 =
-                         thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
+                         thread-per-row on every level at setup (smoother: also in half-size
+                         CTAs) and keep the fastest (default); 0 = warp-per-row everywhere;
+                         2 = thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
                          4 = as 2 with four lanes per smoother row (each a quarter of the
                          row's blocks); 1 also times the variants of 3 and 4                    */
     /* ---- beyond the paper: smoothed transfers, per-node damping, learned weights ---- */
@@ -99,16 +99,22 @@ typedef struct {
     int mlp_levels;   /* with mlp: the network gives the weights of levels 0..mlp_levels-1 (the
                          depths it was trained on); deeper levels keep omega and the tentative P.
                          0 (default) = every level                                             */
-    int use_pdl;      /* 1: the V-cycle's kernels are launched as programmatic dependent launches
-                         (each may be scheduled while its predecessor drains and waits for its
-                         inputs in hardware); 0 (default): ordinary launches. Same results; on
-                         GB300 within a few percent either way, so off by default.            */
+    int use_pdl;      /* 1 (default): the V-cycle's kernels are launched as programmatic
+                         dependent launches (each is scheduled while its predecessor drains,
+                         loads the matrix entries of its first block, then waits for its
+                         inputs in hardware); 0: ordinary launches. Same results (bitwise).   */
     int coarse_prec;  /* precision of the coarsest direct solve (LU with partial pivoting, its
                          inverse, and the per-cycle product with it) of a single system:
                          64 (default) or 32 (FP32, only with cycle_prec 32: GB300 runs FP32 at
                          64 times its FP64 rate). The LU is of the coarsest Galerkin matrix
                          rounded to FP32; a pivot below 1e-6 times its infinity norm reports
                          BAMG_ESINGULAR_COARSE. Batches keep FP64 per-system inverses.        */
+    int tail_grid;    /* with tail_dofs: 1 = the levels of the tail run as one cooperative
+                         launch over every SM with a grid barrier between the recorded phases
+                         (instead of one thread-block cluster); the V-cycle is then launched
+                         directly, not from a CUDA graph. A barrier wait that runs out (it
+                         cannot while all CTAs are resident, which the cooperative launch
+                         guarantees) is reported as BAMG_ETIMEOUT by fgmres_solve. Default 0. */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

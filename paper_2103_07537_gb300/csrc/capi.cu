@@ -206,6 +206,8 @@ struct bamg_ctx {
     long long graph_kernels = 0;
     // cluster tail (every level from l_tail down in one launch)
     int l_tail = -1, n_tail = 0, tail_cluster = 0;
+    int tail_grid = 0;            // CTAs of the cooperative grid tail (0: cluster tail)
+    unsigned* tail_bar = nullptr;  // its barrier words
     TailPhase* tail_d = nullptr;
     const void* tail_rhs = nullptr;
     const void* tail_out = nullptr;
@@ -353,8 +355,9 @@ extern "C" void amg_default_params(amg_params* p) {
     p->mlp = nullptr;
     p->pr_storage = 32;
     p->mlp_levels = 0;
-    p->use_pdl = 0;
+    p->use_pdl = 1;
     p->coarse_prec = 64;
+    p->tail_grid = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -564,9 +567,10 @@ static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int rep
     return 1e3f * ms / reps;
 }
 
-// Autotuner: per level, time the warp-per-row and thread-per-row mappings of
-// the smoother (first colour, first field) and of the residual SpMV on the
-// level's own operator, and keep the faster; likewise for the FP64 outer SpMV.
+// Autotuner: per level, time the row mappings of the smoother (first colour,
+// first field) and of the residual SpMV on the level's own operator, and keep
+// the faster; likewise for the FP64 outer SpMV.  (Timing whole sweeps instead
+// doubled the setup of the 2D workload and picked no better mappings.)
 template <typename T>
 static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
     cudaEvent_t e0, e1;
@@ -981,7 +985,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
         prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1) ||
-        (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32))
+        (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32) ||
+        (prm.tail_grid != 0 && prm.tail_grid != 1))
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -1143,8 +1148,12 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const int b = h->b;
     if (!h->rec && l == h->l_tail && h->tail_d && rhs == h->tail_rhs && out == h->tail_out) {
         // every level from l down runs as one cluster launch of the recorded phases
-        PL(BAMG_K_TAIL, h->tail_bytes, h->tail_flops,
-           launch_tail<T>(b, h->fb, h->tail_d, h->n_tail, h->tail_cluster, s));
+        if (h->tail_grid)
+            PL(BAMG_K_TAIL, h->tail_bytes, h->tail_flops,
+               (launch_grid_tail<T>(b, h->fb, h->tail_d, h->n_tail, h->tail_grid, h->tail_bar, h->d_err, s)));
+        else
+            PL(BAMG_K_TAIL, h->tail_bytes, h->tail_flops,
+               launch_tail<T>(b, h->fb, h->tail_d, h->n_tail, h->tail_cluster, s));
         return BAMG_OK;
     }
     if (l == h->nlev - 1 && h->nsys > 1) {  // one dense inverse per system
@@ -1345,10 +1354,18 @@ static int setup_tail(bamg_ctx* h, cudaStream_t s) {
     int lt = h->nlev - 1;
     while (lt > 0 && (long)h->lev[lt - 1].n * h->b <= h->p.tail_dofs) --lt;
     if (lt >= h->nlev - 1) return BAMG_OK;  // only the coarsest solve would remain: no gain
-    const int cl = h->p.cycle_prec == 64 ? tail_cluster_size<double>(h->b, h->fb, 16)
-                                         : tail_cluster_size<float>(h->b, h->fb, 16);
-    if (cl < 1) return BAMG_OK;
-    h->tail_cluster = cl;
+    if (h->p.tail_grid) {
+        const int g = h->p.cycle_prec == 64 ? grid_tail_size<double>(h->b, h->fb) : grid_tail_size<float>(h->b, h->fb);
+        if (g < 1) return BAMG_OK;  // no cooperative launch: per-kernel cycle
+        TRY(h->alloc(&h->tail_bar, 2));
+        BAMG_CUDA_TRY(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), s));
+        h->tail_grid = g;
+    } else {
+        const int cl = h->p.cycle_prec == 64 ? tail_cluster_size<double>(h->b, h->fb, 16)
+                                             : tail_cluster_size<float>(h->b, h->fb, 16);
+        if (cl < 1) return BAMG_OK;
+        h->tail_cluster = cl;
+    }
     h->l_tail = lt;
     return record_tail(h, s, false);
 }
@@ -1419,7 +1436,8 @@ static int apply_profiled(bamg_ctx* h, const double* r, double* z, cudaStream_t 
 
 static int apply_impl(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
     if (h->prof && h->p.use_graph) return apply_profiled(h, r, z, s);
-    if (!h->p.use_graph || h->prof) return cycle_direct(h, r, z, s);
+    // (a cycle with the cooperative grid tail is one launch plus casts: direct)
+    if (!h->p.use_graph || h->prof || h->tail_grid) return cycle_direct(h, r, z, s);
     TRY(ensure_graph(h));
     const size_t nbytes = sizeof(double) * (size_t)h->lev[0].n * h->b;
     BAMG_CUDA_TRY(cudaMemcpyAsync(h->cyc_in, r, nbytes, cudaMemcpyDeviceToDevice, s));
@@ -1540,7 +1558,10 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             total++;
             k = j + 1;
             BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (h->tail_grid)  // a grid-barrier timeout of the cycle's cooperative launch
+                BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
             BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h->tail_grid && h->h_pin[0] != 0) return map_dev_error(h->h_pin[0]);
             if (!isfinite(hs[1])) return BAMG_ENAN;
             if (hs[1] / bnorm <= tol || hs[2] != 0.0 || total >= max_iter) break;
         }
@@ -1807,7 +1828,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
         o += buf;
     }
     o += "},\"tail_level\":" + std::to_string(h->l_tail) + ",\"tail_phases\":" + std::to_string(h->n_tail) +
-         ",\"tail_cluster\":" + std::to_string(h->tail_cluster) + ",\"levels\":[";
+         ",\"tail_cluster\":" + std::to_string(h->tail_cluster) + ",\"tail_grid\":" + std::to_string(h->tail_grid) +
+         ",\"levels\":[";
     for (int l = 0; l < h->nlev; ++l) {
         const Level& L = h->lev[l];
         if (l) o += ",";

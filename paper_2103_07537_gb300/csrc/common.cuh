@@ -27,6 +27,43 @@ enum DevErr : int {
 
 __device__ __forceinline__ void set_error(int* flag, int code) { atomicCAS(flag, 0, code); }
 
+// Barrier over every CTA of a cooperative launch: an arrival counter and a
+// generation word in global memory (bar[0], bar[1], zero before the first
+// launch; the last arriver resets the counter before it moves the
+// generation, so the pair is ready for the next barrier and launch).  Thread
+// 0 of each CTA spins on the generation; a wait beyond kBarrierSpins sets
+// kDevTimeout and returns false, and the caller's CTA leaves, so the others
+// run out at their next barrier and the kernel always ends.
+constexpr long kBarrierSpins = 1L << 24;  // one L2 round trip per spin: well over a second
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            bar[0] = 0u;  // nobody arrives again before the generation moves
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpins) {
+                    set_error(err, kDevTimeout);
+                    s_ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 template <typename T>
 struct VecOf;
 template <>
@@ -198,6 +235,16 @@ struct TailPhase {
 constexpr int kTailThreads = 512;
 template <typename T>
 int launch_tail(int b, int fb, const TailPhase* phases, int nphase, int cluster, cudaStream_t s);
+// the same phases on every SM: a cooperative launch of grid CTAs with a grid
+// barrier (bar: two zeroed words) between phases; a barrier timeout sets
+// kDevTimeout in err
+template <typename T>
+int launch_grid_tail(int b, int fb, const TailPhase* phases, int nphase, int grid, unsigned* bar, int* err,
+                     cudaStream_t s);
+// CTAs of the grid tail that are resident at once on the device (0: no
+// cooperative launch)
+template <typename T>
+int grid_tail_size(int b, int fb);
 // largest resident cluster size <= want for the tail kernel (0: none)
 template <typename T>
 int tail_cluster_size(int b, int fb, int want);

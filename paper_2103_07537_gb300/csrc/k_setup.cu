@@ -1044,36 +1044,6 @@ __global__ void swaps_to_pos_kernel(int nd, const int* __restrict__ piv, int* __
 // ---------------------------------------------------------------------------
 constexpr int kCoopThreads = 512;
 constexpr int kCoopMaxCtas = 256;
-constexpr long kBarrierSpins = 1L << 24;
-
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-            bar[0] = 0u;  // nobody arrives again before the generation moves
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long spins = 0;  // one L2 round trip per spin: the bound is well over a second
-            while (*gen == g) {
-                if (++spins > kBarrierSpins) {
-                    set_error(err, kDevTimeout);
-                    s_ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // (v, i) -> the CTA's maximum v, ties to the smallest i; valid in thread 0
 template <typename T>
 __device__ __forceinline__ void cta_argmax(T& v, int& i, T* red_v, int* red_i) {

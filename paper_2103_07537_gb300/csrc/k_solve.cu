@@ -87,19 +87,39 @@ __device__ __forceinline__ T reduce_rows(T v, int lane) {
     return v;  // lanes 0..R-1 hold the row sums
 }
 
-// y_i = (rhs_i -) sum_j A_ij x_j for block row i; whole warp
-template <typename T, int B, bool CG>
+// y_i = (rhs_i -) sum_j A_ij x_j for block row i; whole warp.  With PDL the
+// lane's first block (column and matrix row, fixed for the cycle) is loaded
+// before the wait on the previous kernel.
+template <typename T, int B, bool CG, bool PDL = false>
 __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict__ rp, const int* __restrict__ ci,
                                          const T* __restrict__ vals, const T* x, const T* rhs, T* y) {
     constexpr int G = kWarp / B;
     const int kk = lane / B;
     const int r = lane - kk * B;
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    const int kf = k0 + kk;
+    const bool have = kk < G && kf < k1;
+    int jf = 0;
+    T af[B];
+    if (have) {
+        jf = __ldg(ci + kf);
+        load_row<T, B>(vals + (size_t)kf * B * B + r * B, af);
+    }
+    if constexpr (PDL) {
+        pdl_wait();
+        pdl_trigger();
+    }
     const T bi = (rhs && lane < B) ? ld1<T, CG>(rhs + (size_t)i * B + lane) : T(0);  // issued early
     T acc = T(0);
-    if (kk < G) {
+    if (have) {
+        {
+            T xv[B];
+            load_vec<T, B, CG>(x + (size_t)jf * B, xv);
+#pragma unroll
+            for (int c = 0; c < B; ++c) acc = fma(af[c], xv[c], acc);
+        }
 #pragma unroll 4
-        for (int k = k0 + kk; k < k1; k += G) {
+        for (int k = kf + G; k < k1; k += G) {
             const int j = __ldg(ci + k);
             T a[B], xv[B];
             load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
@@ -128,6 +148,41 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
 // others copied), so the field update of Algorithm 1 needs no extra pass.
 // With uc set, x_in + P uc (the coarse correction) is read in place of x_in.
 // ---------------------------------------------------------------------------
+// one block of a field step of the smoother: acc += A_{f,*}[i,j] x_in,j (x_in
+// plus P uc when fused), and acc += A_ff[i,j] x~_j when j precedes i in the
+// colour order (x~ of later colours is stale and masked); arow = row f0 + r of
+// the block.  Forced inline so that arow stays in registers.
+template <typename T, int B, int FB, bool CG>
+__device__ __forceinline__ void bgs_block(const BgsArgs& a, const T* xt, const T* x_in, const T* uc, int j,
+                                          const T (&arow)[B], bool lower, int ag, T& acc) {
+    T tv[FB];
+    load_vec<T, FB, CG>(xt + (size_t)j * FB, tv);
+    if (x_in) {
+        T xv[B];
+        load_vec<T, B, CG>(x_in + (size_t)j * B, xv);
+        if (uc) {
+            T pv[B];
+            load_vec<T, B, CG>(uc + (size_t)ag * B, pv);
+#pragma unroll
+            for (int c = 0; c < B; ++c) xv[c] += pv[c];
+        }
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
+    }
+    if (lower) {
+        // the field-f columns of the row, picked by selects over compile-time
+        // register indices (an index computed from the field would put arow
+        // in local memory)
+#pragma unroll
+        for (int c = 0; c < FB; ++c) {
+            T av = arow[c];
+#pragma unroll
+            for (int ff = 1; ff < B / FB; ++ff) av = (ff == a.field) ? arow[ff * FB + c] : av;
+            acc = fma(av, tv[c], acc);
+        }
+    }
+}
+
 template <typename T, int B, int FB, bool CG, bool PDL = false>
 __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     constexpr int G = kWarp / FB;  // blocks of the row per pass
@@ -147,44 +202,35 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
 #pragma unroll
         for (int c = 0; c < FB; ++c) drow[c] = __ldg(D + c);
     }
+    // the lane's first block: its column, matrix row, colour test and
+    // aggregate are fixed for the whole cycle, so they are loaded before the
+    // wait on the previous kernel (with programmatic dependent launch they
+    // overlap its tail)
+    // (rows hold at least their diagonal block: the clamped index stays in
+    // the row, and lanes without a first block load but never use it)
+    const int kf = k0 + kk;
+    const bool have = kk < G && kf < k1;
+    const int kq = min(kf, k1 - 1);
+    const int jf = __ldg(a.ci + kq);
+    T arf[B];
+    load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
+    const bool lowf = jf != i && __ldg(a.colours + jf) < a.colour;
+    const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
     if constexpr (PDL) {  // everything below may depend on earlier kernels
         pdl_wait();
         pdl_trigger();
     }
     const T bi = lane < FB ? ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) : T(0);
     T acc = T(0);
-    if (kk < G) {
+    if (have) {
+        bgs_block<T, B, FB, CG>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
 #pragma unroll 4
-        for (int k = k0 + kk; k < k1; k += G) {
+        for (int k = kf + G; k < k1; k += G) {
             const int j = __ldg(a.ci + k);
             T arow[B];
             load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
-            // x~_j is read together with colour(j) and used only if j precedes i
-            // in the colour order (stale values of later colours are masked)
-            T tv[FB];
-            load_vec<T, FB, CG>(xt + (size_t)j * FB, tv);
             const bool lower = j != i && __ldg(a.colours + j) < a.colour;
-            if (x_in) {
-                T xv[B];
-                load_vec<T, B, CG>(x_in + (size_t)j * B, xv);
-                if (uc) {
-                    T pv[B];
-                    load_vec<T, B, CG>(uc + (size_t)__ldg(a.agg + j) * B, pv);
-#pragma unroll
-                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
-                }
-#pragma unroll
-                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
-            }
-            if (lower) {
-                // field-f columns of the row with compile-time register indices
-#pragma unroll
-                for (int ff = 0; ff < B / FB; ++ff)
-                    if (ff == a.field) {
-#pragma unroll
-                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
-                    }
-            }
+            bgs_block<T, B, FB, CG>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0, acc);
         }
     }
     acc = reduce_rows<T, FB>(acc, lane);
@@ -259,9 +305,7 @@ __global__ void __launch_bounds__(256, 4) spmv_kernel(int n, const int* __restri
                                                    const T* __restrict__ rhs, T* __restrict__ y) {
     const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // uniform per warp
-    pdl_wait();
-    pdl_trigger();
-    spmv_row<T, B, false>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
+    spmv_row<T, B, false, true>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
 }
 
 template <typename T>
@@ -398,11 +442,24 @@ __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restr
     if (i >= n) return;
     const int r = (int)(t - (long)i * B);
     const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    // the first block before the wait (fixed for the cycle)
+    int jf = 0;
+    T af[B];
+    if (k0 < k1) {
+        jf = __ldg(ci + k0);
+        load_row<T, B>(vals + (size_t)k0 * B * B + r * B, af);
+    }
     pdl_wait();
     pdl_trigger();
     T acc = T(0);
+    if (k0 < k1) {
+        T xv[B];
+        load_row<T, B>(x + (size_t)jf * B, xv);
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fma(af[c], xv[c], acc);
+    }
 #pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
+    for (int k = k0 + 1; k < k1; ++k) {
         const int j = __ldg(ci + k);
         T a[B], xv[B];
         load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
@@ -468,35 +525,27 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
     if (act) {
         i = __ldg(a.nodes + q);
         const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+        // the first block's static loads before the wait (as in bgs_node)
+        const int kf = k0 + sl;
+        const bool have = kf < k1;
+        const int kq = min(kf, k1 - 1);  // rows hold their diagonal block
+        const int jf = __ldg(a.ci + kq);
+        T arf[B];
+        load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
+        const bool lowf = jf != i && __ldg(a.colours + jf) < a.colour;
+        const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
         pdl_wait();
         pdl_trigger();
+        if (have) {
+            bgs_block<T, B, FB, false>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
 #pragma unroll 4
-        for (int k = k0 + sl; k < k1; k += G) {
-            const int j = __ldg(a.ci + k);
-            T arow[B];
-            load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
-            T tv[FB];
-            load_row<T, FB>(xt + (size_t)j * FB, tv);
-            const bool lower = j != i && __ldg(a.colours + j) < a.colour;
-            if (x_in) {
-                T xv[B];
-                load_row<T, B>(x_in + (size_t)j * B, xv);
-                if (uc) {
-                    T pv[B];
-                    load_row<T, B>(uc + (size_t)__ldg(a.agg + j) * B, pv);
-#pragma unroll
-                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
-                }
-#pragma unroll
-                for (int c = 0; c < B; ++c) acc = fma(arow[c], xv[c], acc);
-            }
-            if (lower) {
-#pragma unroll
-                for (int ff = 0; ff < B / FB; ++ff)
-                    if (ff == a.field) {
-#pragma unroll
-                        for (int c = 0; c < FB; ++c) acc = fma(arow[ff * FB + c], tv[c], acc);
-                    }
+            for (int k = kf + G; k < k1; k += G) {
+                const int j = __ldg(a.ci + k);
+                T arow[B];
+                load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+                const bool lower = j != i && __ldg(a.colours + j) < a.colour;
+                bgs_block<T, B, FB, false>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0,
+                                           acc);
             }
         }
     }
@@ -563,6 +612,50 @@ template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t
 // every phase and every barrier (no early exit), so the hardware barrier
 // never waits for a thread that has left.
 // ---------------------------------------------------------------------------
+// one recorded phase over the work items of the calling thread: warp w of W
+// warps (gw), thread t of NT threads (gt)
+template <typename T, int B, int FB>
+__device__ __forceinline__ void run_phase(const TailPhase& ph, int lane, long gw, long W, long gt, long NT) {
+    switch (ph.type) {
+        case kPhaseBgs:
+            for (long q = gw; q < ph.n; q += W) bgs_node<T, B, FB, true>(ph.bgs, q, lane);
+            break;
+        case kPhaseResidual:
+            for (long i = gw; i < ph.n; i += W)
+                spmv_row<T, B, true>(i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals),
+                                     static_cast<const T*>(ph.x), static_cast<const T*>(ph.rhs),
+                                     static_cast<T*>(ph.y));
+            break;
+        case kPhaseRestrict:
+            for (long t = gt; t < (long)ph.n * B; t += NT)
+                restrict_dof<T, true>(t, B, ph.rp, ph.ci, static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+            break;
+        case kPhaseGemv:
+            for (long row = gw; row < ph.n; row += W)
+                gemv_row<T, double, true>((int)row, lane, ph.n, static_cast<const double*>(ph.vals),
+                                          static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+            break;
+        case kPhaseGemv32:
+            for (long row = gw; row < ph.n; row += W)
+                gemv_row<T, float, true>((int)row, lane, ph.n, static_cast<const float*>(ph.vals),
+                                         static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
+            break;
+        case kPhaseProlongCopy:  // y = x + P uc over n fine nodes (x may equal y); uc in rhs, agg in ci
+            for (long e = gt; e < (long)ph.n * B; e += NT) {
+                const int i = (int)(e / B), d = (int)(e - (long)i * B);
+                static_cast<T*>(ph.y)[e] =
+                    ld1<T, true>(static_cast<const T*>(ph.x) + e) +
+                    ld1<T, true>(static_cast<const T*>(ph.rhs) + (size_t)__ldg(ph.ci + i) * B + d);
+            }
+            break;
+        case kPhaseZero:
+            for (long e = gt; e < (long)ph.n * B; e += NT) static_cast<T*>(ph.y)[e] = T(0);
+            break;
+        default:
+            break;
+    }
+}
+
 template <typename T, int B, int FB>
 __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(const TailPhase* __restrict__ phases, int nphase) {
     cg::cluster_group cl = cg::this_cluster();
@@ -573,48 +666,91 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(const TailPhase* 
     const long gt = (long)cl.block_rank() * blockDim.x + threadIdx.x;
     const long NT = (long)cl.num_blocks() * blockDim.x;
     for (int p = 0; p < nphase; ++p) {
-        const TailPhase& ph = phases[p];
-        switch (ph.type) {
-            case kPhaseBgs:
-                for (long q = gw; q < ph.n; q += W) bgs_node<T, B, FB, true>(ph.bgs, q, lane);
-                break;
-            case kPhaseResidual:
-                for (long i = gw; i < ph.n; i += W)
-                    spmv_row<T, B, true>(i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals),
-                                         static_cast<const T*>(ph.x), static_cast<const T*>(ph.rhs),
-                                         static_cast<T*>(ph.y));
-                break;
-            case kPhaseRestrict:
-                for (long t = gt; t < (long)ph.n * B; t += NT)
-                    restrict_dof<T, true>(t, B, ph.rp, ph.ci, static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
-                break;
-            case kPhaseGemv:
-                for (long row = gw; row < ph.n; row += W)
-                    gemv_row<T, double, true>((int)row, lane, ph.n, static_cast<const double*>(ph.vals),
-                                              static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
-                break;
-            case kPhaseGemv32:
-                for (long row = gw; row < ph.n; row += W)
-                    gemv_row<T, float, true>((int)row, lane, ph.n, static_cast<const float*>(ph.vals),
-                                             static_cast<const T*>(ph.x), static_cast<T*>(ph.y));
-                break;
-            case kPhaseProlongCopy:  // y = x + P uc over n fine nodes (x may equal y); uc in rhs, agg in ci
-                for (long e = gt; e < (long)ph.n * B; e += NT) {
-                    const int i = (int)(e / B), d = (int)(e - (long)i * B);
-                    static_cast<T*>(ph.y)[e] =
-                        ld1<T, true>(static_cast<const T*>(ph.x) + e) +
-                        ld1<T, true>(static_cast<const T*>(ph.rhs) + (size_t)__ldg(ph.ci + i) * B + d);
-                }
-                break;
-            case kPhaseZero:
-                for (long e = gt; e < (long)ph.n * B; e += NT) static_cast<T*>(ph.y)[e] = T(0);
-                break;
-            default:
-                break;
-        }
+        run_phase<T, B, FB>(phases[p], lane, gw, W, gt, NT);
         cl.sync();
     }
 }
+
+// ---------------------------------------------------------------------------
+// Grid tail: the same recorded phases executed by every CTA of a cooperative
+// launch (all SMs), with the bounded grid barrier between phases.  Writes of
+// one phase reach L2 before the barrier (the barrier fences) and the next
+// phase reads data written inside the launch through L2 (ld.global.cg).  A
+// CTA whose barrier wait ran out leaves; every other CTA then runs out at its
+// own next barrier, so the launch ends with kDevTimeout set.
+// ---------------------------------------------------------------------------
+template <typename T, int B, int FB>
+__global__ void __launch_bounds__(kTailThreads, 1) grid_tail_kernel(const TailPhase* __restrict__ phases, int nphase,
+                                                                    unsigned* bar, int* err) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warps_per_cta = blockDim.x >> 5;
+    const long gw = (long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+    const long W = (long)gridDim.x * warps_per_cta;
+    const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long NT = (long)gridDim.x * blockDim.x;
+    for (int p = 0; p < nphase; ++p) {
+        run_phase<T, B, FB>(phases[p], lane, gw, W, gt, NT);
+        if (!grid_barrier(bar, err)) return;
+    }
+}
+
+template <typename T, int B, int FB>
+static int launch_grid_tail_t(const TailPhase* phases, int nphase, int grid, unsigned* bar, int* err,
+                              cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(kTailThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BAMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, grid_tail_kernel<T, B, FB>, phases, nphase, bar, err));
+    return launched(1);
+}
+
+template <typename T, int B, int FB>
+static int grid_tail_size_t() {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_tail_kernel<T, B, FB>, kTailThreads, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * per_sm;
+}
+
+template <typename T>
+int launch_grid_tail(int b, int fb, const TailPhase* phases, int nphase, int grid, unsigned* bar, int* err,
+                     cudaStream_t s) {
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF: return launch_grid_tail_t<T, BB, FF>(phases, nphase, grid, bar, err, s);
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+}
+template int launch_grid_tail<double>(int, int, const TailPhase*, int, int, unsigned*, int*, cudaStream_t);
+template int launch_grid_tail<float>(int, int, const TailPhase*, int, int, unsigned*, int*, cudaStream_t);
+
+template <typename T>
+int grid_tail_size(int b, int fb) {
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF: return grid_tail_size_t<T, BB, FF>();
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+#undef CASE
+        default: return 0;
+    }
+}
+template int grid_tail_size<double>(int, int);
+template int grid_tail_size<float>(int, int);
 
 static void fill_cluster_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, int cluster, cudaStream_t s) {
     *cfg = cudaLaunchConfig_t{};

@@ -149,15 +149,19 @@ def test_vcycle_variants_match_oracle(variant):
     assert rel_max(z.cpu().numpy(), o.vcycle(r)) <= VCYCLE_TOL
 
 
+@pytest.mark.parametrize("grid", [0, 1])
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("name", ["stokes2d_32", "mhd2d_41_ragged", "stokes3d_9", "poisson_b2"])
-def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
+def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec, grid):
     s, kw = SYSTEMS[name]()
-    # the tail replays the warp-per-row device functions: compare with that mapping
-    with_tail = make_solver(s, tail_dofs=1 << 30, cycle_prec=prec, autotune=0, **kw)  # every level in the tail
-    some_tail = make_solver(s, tail_dofs=2000, cycle_prec=prec, autotune=0, **kw)
+    # the tail (one cluster, or every SM with grid barriers) replays the
+    # warp-per-row device functions: compare with that mapping
+    with_tail = make_solver(s, tail_dofs=1 << 30, tail_grid=grid, cycle_prec=prec, autotune=0, **kw)
+    some_tail = make_solver(s, tail_dofs=2000, tail_grid=grid, cycle_prec=prec, autotune=0, **kw)
     no_tail = make_solver(s, tail_dofs=0, cycle_prec=prec, autotune=0, **kw)
-    assert with_tail.stats()["tail_level"] == 0 and no_tail.stats()["tail_level"] == -1
+    st = with_tail.stats()
+    assert st["tail_level"] == 0 and no_tail.stats()["tail_level"] == -1
+    assert (st["tail_grid"] > 0) == bool(grid) and (st["tail_cluster"] > 0) == (not grid)
     r = dev(np.random.default_rng(3).standard_normal(s.n_unknowns))
     outs = []
     for g in (with_tail, some_tail, no_tail):
@@ -166,6 +170,16 @@ def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec):
         outs.append(z)
     torch.cuda.synchronize()
     assert torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2])
+    # repeated launches reuse the barrier words: the same bits again, and a solve
+    z = torch.empty_like(r)
+    with_tail.apply(r, z)
+    torch.cuda.synchronize()
+    assert torch.equal(z, outs[2])
+    x = torch.zeros_like(r)
+    st_, it, rr = with_tail.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=3000)
+    x0 = torch.zeros_like(r)
+    _, it0, _ = no_tail.solve(dev(s.rhs), x0, tol=1e-8, restart=30, max_iter=3000)
+    assert st_ == bamg.BAMG_OK and rr <= 1e-8 and it == it0
 
 
 @pytest.mark.parametrize("tuned", [(2, "thread"), (4, "thread-split")])
