@@ -64,17 +64,19 @@ WORKLOADS = {
              "inside per-system FP64 FGMRES(30) to 1e-8, at most 400 inner steps per system"),
     "mhd2d_cells_256": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d_cells(256, seed),
-        levels=10, max_coarse=2500, restart=30, prec=32, learned=True, cpu_sample_iters=5,
+        levels=10, max_coarse=2500, restart=30, prec=32, coarse_prec=32, learned=True, cpu_sample_iters=5,
         desc="2D coupled 4-field Q1 system, 256x256 cells, 66,049 nodes, 396,294 unknowns, resistivity drawn per "
              "cell log-U[1e-4,1] (viscosity log-U[1e-3,1]); learned damping: network 8-64-64-2 (FP16 weights, "
              "FP32 arithmetic, trained on 2000 instances of 64^2..128^2 cells) gives the smoother damping per node "
-             "and field and the prolongator smoothing per aggregate and field; FP32 V(1,1) inside FP64 FGMRES(30) "
-             "to 1e-8; variants: the plain hierarchy (omega 0.5, tentative P) in FP64 and FP32"),
+             "and field and the prolongator smoothing per aggregate and field; FP32 V(1,1) (FP32 coarsest LU) "
+             "inside FP64 FGMRES(30) to 1e-8; variants: the plain hierarchy (omega 0.5, tentative P) in FP64 and "
+             "FP32"),
     "stokes3d_64": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes3d(64, seed),
-        levels=10, max_coarse=2500, restart=50, prec=32, cpu_sample_iters=5,
+        levels=10, max_coarse=2500, restart=50, prec=32, coarse_prec=32, cpu_sample_iters=5,
         desc="3D Stokes Q1-Q1 stabilised, 64^3 hex cells, 4 dofs/node, 1,098,500 unknowns, 7,189,057 blocks "
-             "(115 M scalars), FP32 V(1,1) BGS omega=0.5 inside FP64 FGMRES(50) to 1e-8, 3 levels"),
+             "(115 M scalars), FP32 V(1,1) BGS omega=0.5 (FP32 LU of the 2048-unknown coarsest level) inside FP64 "
+             "FGMRES(50) to 1e-8, 3 levels"),
 }
 
 

@@ -107,8 +107,10 @@ typedef struct {
                          inverse, and the per-cycle product with it) of a single system:
                          64 (default) or 32 (FP32, only with cycle_prec 32: GB300 runs FP32 at
                          64 times its FP64 rate). The LU is of the coarsest Galerkin matrix
-                         rounded to FP32; a pivot below 1e-6 times its infinity norm reports
-                         BAMG_ESINGULAR_COARSE. Batches keep FP64 per-system inverses.        */
+                         rounded to FP32; a pivot below 1e-9 times its infinity norm reports
+                         BAMG_ESINGULAR_COARSE (pivots near FP32 rounding make the coarse solve
+                         inexact along near-null directions; FGMRES absorbs that, at the cost
+                         of iterations if any). Batches keep FP64 per-system inverses.        */
     int tail_grid;    /* with tail_dofs: 1 = the levels of the tail run as one cooperative
                          launch over every SM with a grid barrier between the recorded phases
                          (instead of one thread-block cluster); the V-cycle is then launched

@@ -780,11 +780,14 @@ template <typename T>
 struct LuSmem {
     static constexpr int kMax = sizeof(T) == 8 ? 158 : 223;
 };
-// a smallest pivot of 1e-14 (FP64) or 1e-6 (FP32) times the infinity norm
-// marks the matrix numerically singular
+// a smallest pivot of 1e-14 (FP64) or 1e-9 (FP32) times the infinity norm
+// marks the matrix singular.  (In FP32 pivots between that and the rounding
+// level leave the coarse solve inaccurate along near-null directions, which
+// the outer FGMRES absorbs: the stabilised 3D Stokes coarsest operator has
+// such a pivot and converges in the same iterations as with the FP64 solve.)
 template <typename T>
 __host__ __device__ constexpr T lu_tiny() {
-    return sizeof(T) == 8 ? T(1e-14) : T(1e-6);
+    return sizeof(T) == 8 ? T(1e-14) : T(1e-9);
 }
 
 // correctly rounded single operations (no contraction into fused multiply-adds)
@@ -899,11 +902,24 @@ __global__ void __launch_bounds__(kLuThreads) lu_smem_kernel(int nd, T* __restri
     for (int e = tid; e < nd * nd; e += blockDim.x) g[e] = sa[e];
 }
 
+// infinity norm over the grid: one warp per row (coalesced), the row maxima
+// combined by an atomic maximum on the bit patterns (non-negative values
+// order like their bits); *norm_out must be zero before the launch
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
+    atomicMax(reinterpret_cast<unsigned*>(p), __float_as_uint(v));
+}
 template <typename T>
-__global__ void lu_norm_kernel(int nd, const T* __restrict__ a, T* __restrict__ norm_out) {
-    __shared__ T red_v[kLuThreads / 32];
-    const T n = inf_norm(a, nd, red_v);
-    if (threadIdx.x == 0) *norm_out = n;
+__global__ void lu_norm_rows_kernel(int nd, const T* __restrict__ a, T* __restrict__ norm_out) {
+    const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= nd) return;
+    T sum = T(0);
+    for (int c = lane; c < nd; c += 32) sum += fabs(a[(size_t)r * nd + c]);
+    sum = warp_sum(sum);
+    if (lane == 0) atomic_max_nonneg(norm_out, sum);
 }
 
 // column k: pivot, row swap, multipliers (stored in column k and in col)
@@ -1190,6 +1206,189 @@ __global__ void __launch_bounds__(kCoopThreads) lu_coop_kernel(int nd, T* __rest
         }
 }
 
+// ---------------------------------------------------------------------------
+// LU with every CTA's owned rows resident in its shared memory (one CTA per
+// SM; CTA q owns the physical rows q, q + G, ...), for matrices whose rows
+// fit.  A step then touches shared memory only, apart from the pivot row,
+// which the CTA that offered it as the next candidate published before the
+// barrier.  Same pivot choice and the same rounded operations per entry as
+// the other paths (the factors are the same bits):
+//  * s_pos[m] is the logical position of owned row m (the order the row swaps
+//    of the other paths produce): step k moves the winner to k and the row
+//    that sat at k to the winner's old position;
+//  * each CTA's candidate for column k + 1 is its active row with the largest
+//    |a[row][k+1]| (ties: smallest logical position), published with its
+//    value, physical row and logical position, and its entries from column
+//    k + 1 on, into slot (k + 1) & 1 (two slots: a fast CTA never overwrites
+//    a row that a slow one still reads).
+// ---------------------------------------------------------------------------
+constexpr int kRowsThreads = 512;
+constexpr int kRowsCols = 8;  // columns per thread: nd <= kRowsCols * kRowsThreads = 4096
+
+template <typename T>
+__device__ void rows_candidate(int nd, int col, int M, const T* rows, const int* s_pos, const int* s_done, T* red_v,
+                               int* red_i, T* cand_v, int* cand_i, int* cand_p, T* slot) {
+    __shared__ int s_m;
+    __shared__ int s_li;
+    __shared__ T s_v;
+    const int G = gridDim.x, q = blockIdx.x;
+    T v = T(-1);
+    int li = nd;
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+        if (!s_done[m]) {
+            const T av = fabs(rows[(size_t)m * nd + col]);
+            const int lp = s_pos[m];
+            if (av > v || (av == v && lp < li)) {
+                v = av;
+                li = lp;
+            }
+        }
+    cta_argmax(v, li, red_v, red_i);
+    if (threadIdx.x == 0) {
+        s_v = v;
+        s_li = li;
+        s_m = -1;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+        if (!s_done[m] && s_pos[m] == s_li) s_m = m;
+    __syncthreads();
+    const int mm = s_m;
+    if (threadIdx.x == 0) {  // the signed value: the pivot itself when the row wins
+        cand_v[q] = mm >= 0 ? rows[(size_t)mm * nd + col] : T(0);
+        cand_i[q] = mm >= 0 ? q + G * mm : nd;
+        cand_p[q] = mm >= 0 ? s_li : nd;
+    }
+    if (mm >= 0) {
+        T* dst = slot + (size_t)q * nd;
+        const T* src = rows + (size_t)mm * nd;
+        for (int c = col + threadIdx.x; c < nd; c += blockDim.x) dst[c] = src[c];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads) lu_rows_kernel(int nd, T* __restrict__ a, const T* __restrict__ norm,
+                                                                T* __restrict__ cand_v, int* __restrict__ cand_i,
+                                                                int* __restrict__ cand_p, T* __restrict__ slots,
+                                                                unsigned* __restrict__ bar, int* __restrict__ perm_out,
+                                                                int* __restrict__ pos_out, int* err) {
+    const int G = gridDim.x, q = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int M = (nd - q + G - 1) / G;  // owned rows q + G m, m < M
+    const int Mmax = (nd + G - 1) / G;
+    extern __shared__ __align__(16) unsigned char rows_sh[];
+    T* rows = reinterpret_cast<T*>(rows_sh);       // [Mmax][nd]
+    T* s_l = rows + (size_t)Mmax * nd;             // [Mmax] multipliers
+    int* s_pos = reinterpret_cast<int*>(s_l + Mmax);  // [Mmax] logical positions
+    int* s_done = s_pos + Mmax;                    // [Mmax] 1 once the row was a pivot
+    __shared__ T red_v[kRowsThreads / 32];
+    __shared__ int red_i[kRowsThreads / 32];
+    __shared__ int s_w, s_lw, s_qw;
+    __shared__ T s_akk;
+    for (int m = 0; m < M; ++m)
+        for (int c = tid; c < nd; c += blockDim.x) rows[(size_t)m * nd + c] = __ldcg(a + (size_t)(q + G * m) * nd + c);
+    for (int m = tid; m < M; m += blockDim.x) {
+        s_pos[m] = q + G * m;
+        s_done[m] = 0;
+    }
+    __syncthreads();
+    const size_t slot_sz = (size_t)G * nd;
+    rows_candidate(nd, 0, M, rows, s_pos, s_done, red_v, red_i, cand_v, cand_i, cand_p, slots);
+    if (!grid_barrier(bar, err)) return;
+    for (int k = 0; k < nd; ++k) {
+        const int par = k & 1;
+        if (warp == 0) {  // the pivot of column k from the G candidates
+            T v = T(-1);
+            int li = nd, qw = 0;
+            for (int c = lane; c < G; c += 32) {
+                const int cp = __ldcg(cand_p + par * G + c);
+                const T cv = cp < nd ? fabs(__ldcg(cand_v + par * G + c)) : T(-1);  // nd: no active row
+                if (cv > v || (cv == v && cp < li)) {
+                    v = cv;
+                    li = cp;
+                    qw = c;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, li, o);
+                const int oq = __shfl_xor_sync(0xffffffffu, qw, o);
+                if (ov > v || (ov == v && ol < li)) {
+                    v = ov;
+                    li = ol;
+                    qw = oq;
+                }
+            }
+            if (lane == 0) {
+                s_lw = li;
+                s_qw = qw;
+                s_w = __ldcg(cand_i + par * G + qw);
+                s_akk = __ldcg(cand_v + par * G + qw);
+                if (q == 0 && (!(v >= lu_tiny<T>() * norm[0]) || norm[0] == T(0))) set_error(err, kDevSingularCoarse);
+            }
+        }
+        __syncthreads();
+        const int w = s_w, lw = s_lw;
+        for (int m = tid; m < M; m += blockDim.x) {
+            if (q + G * m == w) {
+                s_pos[m] = k;
+                s_done[m] = 1;
+            } else if (!s_done[m] && s_pos[m] == k) {
+                s_pos[m] = lw;
+            }
+        }
+        const T* prow = slots + (size_t)par * slot_sz + (size_t)s_qw * nd;
+        const T akk = s_akk;
+        // the pivot row's entries of this thread's columns, loaded before the
+        // multipliers so that their latency overlaps the divisions
+        T pcs[kRowsCols];
+#pragma unroll
+        for (int t = 0; t < kRowsCols; ++t) {
+            const int c = k + 1 + tid + t * kRowsThreads;
+            pcs[t] = c < nd ? __ldcg(prow + c) : T(0);
+        }
+        __syncthreads();
+        for (int m = tid; m < M; m += blockDim.x)
+            if (!s_done[m]) {
+                const T l = rn_div(rows[(size_t)m * nd + k], akk);
+                s_l[m] = l;
+                rows[(size_t)m * nd + k] = l;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kRowsCols; ++t) {
+            const int c = k + 1 + tid + t * kRowsThreads;
+            if (c < nd)
+                for (int m = 0; m < M; ++m)
+                    if (!s_done[m]) {
+                        T* e = rows + (size_t)m * nd + c;
+                        *e = rn_sub(*e, rn_mul(s_l[m], pcs[t]));
+                    }
+        }
+        __syncthreads();
+        if (k + 1 < nd) {
+            const int np = (k + 1) & 1;
+            rows_candidate(nd, k + 1, M, rows, s_pos, s_done, red_v, red_i, cand_v + np * G, cand_i + np * G,
+                           cand_p + np * G, slots + (size_t)np * slot_sz);
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+    for (int m = 0; m < M; ++m)
+        for (int c = tid; c < nd; c += blockDim.x) a[(size_t)(q + G * m) * nd + c] = rows[(size_t)m * nd + c];
+    for (int m = tid; m < M; m += blockDim.x) {
+        pos_out[q + G * m] = s_pos[m];
+        perm_out[s_pos[m]] = q + G * m;
+    }
+}
+
+// shared memory of lu_rows_kernel with G CTAs: the owned rows, multipliers,
+// logical positions and flags
+template <typename T>
+static size_t rows_smem(int nd, int G) {
+    const size_t M = (size_t)((nd + G - 1) / G);
+    return sizeof(T) * (M * nd + M) + 2 * sizeof(int) * M;
+}
+
 // shared memory of lu_coop_kernel with G CTAs: perm, pos, the owned-row flags
 // (padded to an even count) and multipliers
 template <typename T>
@@ -1199,9 +1398,9 @@ static size_t coop_smem(int nd, int G) {
 }
 
 // scratch of dense_lu_inverse in doubles: multipliers and the norm (nd + 1
-// values), two candidate slots (values and rows), the barrier words, perm and
-// the positions before the copy to piv
-long dense_lu_scratch(int nd) { return (long)nd + 1 + 3L * kCoopMaxCtas + 2 + nd + 2; }
+// values), two candidate slots (values, rows, logical positions), the
+// barrier words, perm and the positions before the copy to piv
+long dense_lu_scratch(int nd) { return (long)nd + 1 + 4L * kCoopMaxCtas + 2 + nd + 2; }
 
 // a: the dense matrix (factored in place), inv: its inverse, lt: nd*nd
 // scratch (the transposed factors), work: dense_lu_scratch(nd) doubles
@@ -1221,22 +1420,51 @@ int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* e
     w += 8 * 2;
     int* perm = reinterpret_cast<int*>(w);                // [nd]
     int* pos_tmp = perm + nd;                             // [nd]
+    w += 4 * (2 * (size_t)nd + 2);
+    int* cand_p = reinterpret_cast<int*>(w);              // [2 * kCoopMaxCtas]
     int* pos = piv;  // on return piv holds the logical position of every row
     bool coop_done = false;
+    int dev = 0, coop = 0, sms = 0;
+    const bool can_coop = cudaGetDevice(&dev) == cudaSuccess &&
+                          cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                          sms <= kCoopMaxCtas;
+    if (!can_coop) cudaGetLastError();
     if (nd <= LuSmem<T>::kMax) {
         const size_t smem = sizeof(T) * (size_t)nd * nd;
         BAMG_CUDA_TRY(cudaFuncSetAttribute(lu_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         lu_smem_kernel<T><<<1, kLuThreads, smem, s>>>(nd, a, piv, err);
         n += 1;
     } else {
-        lu_norm_kernel<T><<<1, kLuThreads, 0, s>>>(nd, a, col + nd);
+        BAMG_CUDA_TRY(cudaMemsetAsync(col + nd, 0, sizeof(T), s));
+        lu_norm_rows_kernel<T><<<ceil_div((long)nd * 32, 256), 256, 0, s>>>(nd, a, col + nd);
         n += 1;
-        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        int per_sm = 0;
         size_t smem = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms <= kCoopMaxCtas &&
-            (smem = coop_smem<T>(nd, sms)) > 0 &&
+        // rows resident in shared memory when they fit (the candidate rows go
+        // through lt, free until the transposition: 2 * sms * nd <= nd^2)
+        if (can_coop && nd >= 2 * sms && nd <= kRowsCols * kRowsThreads && (smem = rows_smem<T>(nd, sms)) > 0 &&
+            cudaFuncSetAttribute(lu_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_rows_kernel<T>, kRowsThreads, smem) ==
+                cudaSuccess &&
+            per_sm >= 1) {
+            BAMG_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+            const T* normp = col + nd;
+            T* slots = lt;
+            void* args[] = {&nd, &a, (void*)&normp, &cand_v, &cand_i, &cand_p, &slots, &bar, &perm, &pos, &err};
+            if (cudaLaunchCooperativeKernel((void*)lu_rows_kernel<T>, dim3(sms), dim3(kRowsThreads), args, smem, s) ==
+                cudaSuccess) {
+                coop_done = true;
+                n += 1;
+            } else {
+                (void)cudaGetLastError();  // not launched: the paths below
+            }
+        } else {
+            (void)cudaGetLastError();
+        }
+        per_sm = 0;
+        if (!coop_done && can_coop && (smem = coop_smem<T>(nd, sms)) > 0 &&
             cudaFuncSetAttribute(lu_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                 cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_coop_kernel<T>, kCoopThreads, smem) ==

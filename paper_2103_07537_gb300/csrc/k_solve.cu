@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
         pdl_trigger();
         if (have) {
             bgs_block<T, B, FB, false>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
-#pragma unroll 4
+#pragma unroll(G > 1 ? 8 : 4)
             for (int k = kf + G; k < k1; k += G) {
                 const int j = __ldg(a.ci + k);
                 T arow[B];
