@@ -557,14 +557,20 @@ constexpr float kTuneMargin = 0.97f;
 template <class F>
 static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& f) {
     if (f() != BAMG_OK) return 1e30f;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; ++r)
-        if (f() != BAMG_OK) return 1e30f;
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    return 1e3f * ms / reps;
+    auto timed = [&](int n) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < n; ++r)
+            if (f() != BAMG_OK) return 1e30f;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return 1e3f * ms / n;
+    };
+    // launches of 40 us and more are timed over 3 (their noise is small
+    // against the tuning margin); shorter ones over reps
+    const float first = timed(3);
+    return first >= 40.0f ? first : timed(reps);
 }
 
 // Autotuner: per level, time the row mappings of the smoother (first colour,

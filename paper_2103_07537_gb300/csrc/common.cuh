@@ -36,6 +36,42 @@ __device__ __forceinline__ void set_error(int* flag, int code) { atomicCAS(flag,
 // run out at their next barrier and the kernel always ends.
 constexpr long kBarrierSpins = 1L << 24;  // one L2 round trip per spin: well over a second
 
+// Block-wide sums of the first gn of G values per thread (NT threads): the
+// values go to shared memory (one row of G + 1 per thread), thread t adds
+// value t % G over the G rows of slice t / G (S = NT / G slices) in row
+// order, and thread g < gn adds the S slice sums in slice order and returns
+// the total (a fixed order).  About G + S adds per thread, where a shuffle
+// tree per value issues 5 adds per value in every thread: on GB300 (2 FP64
+// operations per clock per SM) that work rivals the dot products themselves.
+// sh: NT * (G + 1) + S * (G + 1) doubles.
+template <int G, int NT>
+__device__ __forceinline__ double block_sums(const double (&v)[G], int gn, double* sh) {
+    constexpr int S = NT / G;
+    static_assert(NT % G == 0, "NT must be a multiple of G");
+    const int t = threadIdx.x;
+    double* rows = sh;                      // [NT][G + 1]
+    double* part = sh + NT * (G + 1);       // [S][G + 1]
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        if (g < gn) rows[t * (G + 1) + g] = v[g];
+    __syncthreads();
+    {
+        const int g = t % G, sl = t / G;
+        if (g < gn) {
+            double s = 0.0;
+#pragma unroll 4
+            for (int i = 0; i < G; ++i) s += rows[(sl * G + i) * (G + 1) + g];
+            part[sl * (G + 1) + g] = s;
+        }
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (t < gn)
+        for (int sl = 0; sl < S; ++sl) tot += part[sl * (G + 1) + t];
+    __syncthreads();  // sh is reused by the next call
+    return tot;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
     __shared__ int s_ok;
     __syncthreads();

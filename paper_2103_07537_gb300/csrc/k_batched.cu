@@ -20,8 +20,7 @@ constexpr int kBGroup = 16;
 // at v = nv when want_xx; CTA per chunk
 __device__ void seg_chunk_dots(long e0, long e1, const double* __restrict__ x, const double* __restrict__ Y,
                                long ld, int nv, int want_xx, double* __restrict__ partial, int c, int nchunk) {
-    __shared__ double sh[kBGroup][kBThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double sh[(kBThreads + kBThreads / kBGroup) * (kBGroup + 1)];
     for (int v0 = 0; v0 < nv + want_xx; v0 += kBGroup) {
         double acc[kBGroup];
 #pragma unroll
@@ -35,19 +34,9 @@ __device__ void seg_chunk_dots(long e0, long e1, const double* __restrict__ x, c
                 else if (v == nv && want_xx) acc[g] = fma(xe, xe, acc[g]);
             }
         }
-#pragma unroll
-        for (int g = 0; g < kBGroup; ++g) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], o);
-            if (lane == 0) sh[g][wid] = acc[g];
-        }
-        __syncthreads();
-        if (threadIdx.x < kBGroup && v0 + (int)threadIdx.x < nv + want_xx) {
-            double s = 0.0;
-            for (int w = 0; w < kBThreads / 32; ++w) s += sh[threadIdx.x][w];
-            partial[(size_t)(v0 + threadIdx.x) * nchunk + c] = s;
-        }
-        __syncthreads();
+        const int gn = min(kBGroup, nv + want_xx - v0);
+        const double tot = block_sums<kBGroup, kBThreads>(acc, gn, sh);
+        if ((int)threadIdx.x < gn) partial[(size_t)(v0 + threadIdx.x) * nchunk + c] = tot;
     }
 }
 

@@ -35,30 +35,11 @@ __device__ __forceinline__ void chunk_range(long N, long* e0, long* e1) {
     *e1 = min(N, *e0 + per);
 }
 
-// block-wide sums of G values per thread: thread g < G returns the sum of
-// value g (warp trees, then the warp partials in warp order)
-template <int G>
-__device__ __forceinline__ double block_sum(double (&v)[G], double (*sh)[kKThreads / 32]) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
-        if (lane == 0) sh[g][wid] = v[g];
-    }
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x < G)
-        for (int w = 0; w < kKThreads / 32; ++w) s += sh[threadIdx.x][w];
-    __syncthreads();  // sh is reused by the next group
-    return s;
-}
-
 // partial[v * nchunk + chunk] = sum_{e in chunk} x[e] * Y_v[e], v < nv, and
 // if want_xx, partial[nv * nchunk + chunk] = sum x[e]^2
 __device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const double* __restrict__ Y,
                            long ld, int nv, int want_xx, double* __restrict__ partial) {
-    __shared__ double sh[kDotGroup][kKThreads / 32];
+    __shared__ double sh[(kKThreads + kKThreads / kDotGroup) * (kDotGroup + 1)];
     const int nchunk = gridDim.x;
     for (int v0 = 0; v0 < nv + want_xx; v0 += kDotGroup) {
         double acc[kDotGroup];
@@ -73,9 +54,9 @@ __device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const
                 else if (v == nv && want_xx) acc[g] = fma(xe, xe, acc[g]);
             }
         }
-        const double tot = block_sum<kDotGroup>(acc, sh);
-        if (threadIdx.x < kDotGroup && v0 + (int)threadIdx.x < nv + want_xx)
-            partial[(size_t)(v0 + threadIdx.x) * nchunk + blockIdx.x] = tot;
+        const int gn = min(kDotGroup, nv + want_xx - v0);
+        const double tot = block_sums<kDotGroup, kKThreads>(acc, gn, sh);
+        if ((int)threadIdx.x < gn) partial[(size_t)(v0 + threadIdx.x) * nchunk + blockIdx.x] = tot;
     }
 }
 

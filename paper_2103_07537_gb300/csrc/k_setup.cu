@@ -1381,6 +1381,170 @@ __global__ void __launch_bounds__(kRowsThreads) lu_rows_kernel(int nd, T* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked LU (panels of NB columns), same pivots and the same rounded
+// operations per entry as the column-by-column paths (the factors are the
+// same bits), with three grid barriers per panel instead of one per column:
+//  1. one CTA (the last) loads the panel's columns of every active row in
+//     logical order into shared memory and factors them column by column
+//     (pivot = first largest |value| in logical order, row swaps applied to
+//     its copy of the permutation, multipliers, updates of the panel's later
+//     columns), then writes the panel back and publishes the permutation;
+//  2. all CTAs compute U12, the pivot rows' entries right of the panel, by
+//     column slices: each entry minus the panel's earlier columns in order;
+//  3. the other CTAs, each holding its cyclically owned rows in shared
+//     memory, take the panel's multipliers (and, for pivot rows, U12) and
+//     apply the panel's columns in order to their remaining rows right of the
+//     panel, then publish those rows for the next panel.
+// Every entry thus receives the rounded product and difference of each
+// earlier column in column order, as in the column-by-column factorisation.
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(kRowsThreads) lu_panel_kernel(int nd, T* __restrict__ a, const T* __restrict__ norm,
+                                                                 int* __restrict__ perm_g, int* __restrict__ pos_g,
+                                                                 unsigned* __restrict__ bar, int* err) {
+    const int G = gridDim.x, Gr = G - 1, q = blockIdx.x, tid = threadIdx.x;
+    const bool panel_cta = q == Gr;
+    const int M = panel_cta ? 0 : (nd - q + Gr - 1) / Gr;  // row CTA q owns physical rows q + Gr m
+    const int Mmax = (nd + Gr - 1) / Gr;
+    extern __shared__ __align__(16) unsigned char lu_panel_sh[];
+    T* rows = reinterpret_cast<T*>(lu_panel_sh);                       // row CTAs: [Mmax][nd]
+    int* s_pos = reinterpret_cast<int*>(rows + (size_t)Mmax * nd);      // [Mmax] logical positions
+    constexpr int PS = NB + 1;  // padded panel row: the threads of a warp hit distinct banks
+    T* P = reinterpret_cast<T*>(lu_panel_sh);                          // panel CTA: [nd][PS]
+    int* perm_s = reinterpret_cast<int*>(P + (size_t)nd * PS);          // [nd] logical -> physical
+    __shared__ T red_v[kRowsThreads / 32];
+    __shared__ int red_i[kRowsThreads / 32];
+    __shared__ int s_lp;
+    __shared__ int s_piv[NB];
+    for (int m = 0; m < M; ++m)
+        for (int c = tid; c < nd; c += blockDim.x) rows[(size_t)m * nd + c] = __ldcg(a + (size_t)(q + Gr * m) * nd + c);
+    for (int m = tid; m < M; m += blockDim.x) s_pos[m] = q + Gr * m;
+    for (int r = q * blockDim.x + tid; r < nd; r += G * blockDim.x) {
+        perm_g[r] = r;
+        pos_g[r] = r;
+    }
+    if (!grid_barrier(bar, err)) return;
+    for (int p0 = 0; p0 < nd; p0 += NB) {
+        const int nb = min(NB, nd - p0);
+        const int c0 = p0 + nb;
+        if (panel_cta) {  // 1. the panel
+            const int R = nd - p0;
+            for (int l = tid; l < R; l += blockDim.x) perm_s[l] = __ldcg(perm_g + p0 + l);
+            __syncthreads();
+            for (int e = tid; e < R * nb; e += blockDim.x) {
+                const int l = e / nb, c = e - l * nb;
+                P[(size_t)l * PS + c] = __ldcg(a + (size_t)perm_s[l] * nd + p0 + c);
+            }
+            __syncthreads();
+            for (int j = 0; j < nb; ++j) {
+                T v = T(-1);
+                int li = R;
+                for (int l = j + tid; l < R; l += blockDim.x) {  // ascending: the first maximum per thread
+                    const T av = fabs(P[(size_t)l * PS + j]);
+                    if (av > v) {
+                        v = av;
+                        li = l;
+                    }
+                }
+                cta_argmax(v, li, red_v, red_i);
+                if (tid == 0) {
+                    s_lp = li;
+                    if (!(v >= lu_tiny<T>() * norm[0]) || norm[0] == T(0)) set_error(err, kDevSingularCoarse);
+                }
+                __syncthreads();
+                const int lp = s_lp < R ? s_lp : j;
+                if (lp != j) {
+                    if (tid < nb) {
+                        const T t = P[(size_t)j * PS + tid];
+                        P[(size_t)j * PS + tid] = P[(size_t)lp * PS + tid];
+                        P[(size_t)lp * PS + tid] = t;
+                    }
+                    if (tid == 0) {
+                        const int t = perm_s[j];
+                        perm_s[j] = perm_s[lp];
+                        perm_s[lp] = t;
+                    }
+                }
+                __syncthreads();
+                const T akk = P[(size_t)j * PS + j];
+                for (int l = j + 1 + tid; l < R; l += blockDim.x) {
+                    const T lv = rn_div(P[(size_t)l * PS + j], akk);
+                    P[(size_t)l * PS + j] = lv;
+                    for (int c = j + 1; c < nb; ++c)
+                        P[(size_t)l * PS + c] = rn_sub(P[(size_t)l * PS + c], rn_mul(lv, P[(size_t)j * PS + c]));
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < R * nb; e += blockDim.x) {
+                const int l = e / nb, c = e - l * nb;
+                a[(size_t)perm_s[l] * nd + p0 + c] = P[(size_t)l * PS + c];
+            }
+            for (int l = tid; l < R; l += blockDim.x) {
+                perm_g[p0 + l] = perm_s[l];
+                pos_g[perm_s[l]] = p0 + l;
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+        // 2. U12 by column slices over every CTA
+        if (tid < nb) s_piv[tid] = __ldcg(perm_g + p0 + tid);
+        __syncthreads();
+        for (int c = c0 + q * (int)blockDim.x + tid; c < nd; c += G * (int)blockDim.x) {
+            T u[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                if (k < nb) {
+                    const T* pr = a + (size_t)s_piv[k] * nd;
+                    T x = __ldcg(pr + c);
+#pragma unroll
+                    for (int j = 0; j < k; ++j) x = rn_sub(x, rn_mul(__ldcg(pr + p0 + j), u[j]));
+                    u[k] = x;
+                    a[(size_t)s_piv[k] * nd + c] = x;
+                }
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+        if (!panel_cta) {  // 3. the owned rows
+            for (int m = tid; m < M; m += blockDim.x) s_pos[m] = __ldcg(pos_g + q + Gr * m);
+            __syncthreads();
+            for (int m = 0; m < M; ++m) {
+                const int lp = s_pos[m];
+                if (lp < p0) continue;
+                const int cend = lp < c0 ? nd : c0;  // pivot rows take U12 as well
+                const T* src = a + (size_t)(q + Gr * m) * nd;
+                for (int c = p0 + tid; c < cend; c += blockDim.x) rows[(size_t)m * nd + c] = __ldcg(src + c);
+            }
+            __syncthreads();
+            for (int c = c0 + tid; c < nd; c += blockDim.x) {
+                T u[NB];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) u[k] = k < nb ? __ldcg(a + (size_t)s_piv[k] * nd + c) : T(0);
+                for (int m = 0; m < M; ++m) {
+                    if (s_pos[m] < c0) continue;
+                    T* row = rows + (size_t)m * nd;
+                    T x = row[c];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (k < nb) x = rn_sub(x, rn_mul(row[p0 + k], u[k]));
+                    row[c] = x;
+                    a[(size_t)(q + Gr * m) * nd + c] = x;  // published for the next panel
+                }
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+    for (int m = 0; m < M; ++m)
+        for (int c = tid; c < nd; c += blockDim.x) a[(size_t)(q + Gr * m) * nd + c] = rows[(size_t)m * nd + c];
+}
+
+template <typename T, int NB>
+static size_t panel_smem(int nd, int G) {
+    const size_t Mmax = (size_t)((nd + G - 2) / (G - 1));
+    const size_t row_cta = sizeof(T) * Mmax * nd + sizeof(int) * Mmax;
+    const size_t panel_cta = sizeof(T) * (size_t)nd * (NB + 1) + sizeof(int) * (size_t)nd;
+    return row_cta > panel_cta ? row_cta : panel_cta;
+}
+
 // shared memory of lu_rows_kernel with G CTAs: the owned rows, multipliers,
 // logical positions and flags
 template <typename T>
@@ -1441,9 +1605,38 @@ int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* e
         n += 1;
         int per_sm = 0;
         size_t smem = 0;
+        // FP32: blocked, with the owned rows resident in shared memory, when
+        // they fit (2048 unknowns: 9.7 ms against 17.8 ms for the per-column
+        // kernel below).  FP64 keeps the per-column kernel: there the panel's
+        // FP64 work on one SM (nd^2 NB / 2 products and differences, 2 per
+        // clock) made the blocked form slower (42.5 against 34.6 ms).
+        if constexpr (sizeof(T) == 4) {
+            constexpr int NB = 16;  // the panel's nd x (NB + 1) values: 139 KB at nd 2048
+            if (can_coop && nd >= 2 * sms && (smem = panel_smem<T, NB>(nd, sms)) > 0 &&
+                cudaFuncSetAttribute(lu_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<T, NB>, kRowsThreads, smem) ==
+                    cudaSuccess &&
+                per_sm >= 1) {
+                BAMG_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+                const T* normp = col + nd;
+                void* args[] = {&nd, &a, (void*)&normp, &perm, &pos, &bar, &err};
+                if (cudaLaunchCooperativeKernel((void*)lu_panel_kernel<T, NB>, dim3(sms), dim3(kRowsThreads), args,
+                                                smem, s) == cudaSuccess) {
+                    coop_done = true;
+                    n += 1;
+                } else {
+                    (void)cudaGetLastError();  // not launched: the paths below
+                }
+            } else {
+                (void)cudaGetLastError();
+            }
+        }
+        per_sm = 0;
         // rows resident in shared memory when they fit (the candidate rows go
         // through lt, free until the transposition: 2 * sms * nd <= nd^2)
-        if (can_coop && nd >= 2 * sms && nd <= kRowsCols * kRowsThreads && (smem = rows_smem<T>(nd, sms)) > 0 &&
+        if (!coop_done && can_coop && nd >= 2 * sms && nd <= kRowsCols * kRowsThreads &&
+            (smem = rows_smem<T>(nd, sms)) > 0 &&
             cudaFuncSetAttribute(lu_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                 cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_rows_kernel<T>, kRowsThreads, smem) ==
