@@ -112,6 +112,7 @@ struct Level {
     double* vals64 = nullptr;
     float* vals32 = nullptr;
     int *colour = nullptr, *colour_nodes = nullptr, *colour_ptr_d = nullptr;
+    unsigned char* lowk = nullptr;  // per block: its column has a lower colour than its row
     std::vector<int> colour_ptr;
     double* dinv64 = nullptr;
     float* dinv32 = nullptr;
@@ -594,6 +595,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         a.nodes = L.colour_nodes;
         a.colour = 0;
         a.colours = L.colour;
+        a.lowk = L.lowk;
         a.rp = L.rp;
         a.ci = L.ci;
         a.vals = level_vals<T>(L);
@@ -823,6 +825,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->release(tmp);
         if (L.colour_ptr[L.n_colours] != L.n) return BAMG_ECUDA;
+        TRY(h->alloc(&L.lowk, (size_t)L.nnzb));
+        TRY(launch_lower_flags(L.n, L.rp, L.ci, L.colour, L.lowk, s));
         h->t_phase[3] += ms_since(tp);
         tp = Clock::now();
         if (!L.dinv64) {  // (already there when P was smoothed)
@@ -1076,6 +1080,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.nodes = L.colour_nodes + L.colour_ptr[c];
         a.colour = c;
         a.colours = L.colour;
+        a.lowk = L.lowk;
         a.rp = L.rp;
         a.ci = L.ci;
         a.vals = level_vals<T>(L);

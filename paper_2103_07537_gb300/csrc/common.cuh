@@ -233,9 +233,14 @@ struct BgsArgs {
     int F = 1;
     double omega = 0.5;
     const void* omega_node = nullptr;  // optional: damping of every node and field ([n][F], type T) in place of omega
+    // 1 where block k of row i has a column j != i of lower colour than i
+    // (fixed for the level: no gather of the neighbour's colour in the cycle)
+    const unsigned char* lowk = nullptr;
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// lowk[k] = 1 where block k of row i has a column j != i with colour[j] < colour[i]
+int launch_lower_flags(int n, const int* rp, const int* ci, const int* colour, unsigned char* lowk, cudaStream_t s);
 // thread-per-row variants (more loads in flight per warp; for large levels)
 template <typename T>
 // variant 0: one thread per scalar row; 1: as 0 in CTAs of half the threads (a

@@ -156,7 +156,7 @@ template <typename T, int B, int FB, bool CG>
 __device__ __forceinline__ void bgs_block(const BgsArgs& a, const T* xt, const T* x_in, const T* uc, int j,
                                           const T (&arow)[B], bool lower, int ag, T& acc) {
     T tv[FB];
-    load_vec<T, FB, CG>(xt + (size_t)j * FB, tv);
+    if (lower) load_vec<T, FB, CG>(xt + (size_t)j * FB, tv);
     if (x_in) {
         T xv[B];
         load_vec<T, B, CG>(x_in + (size_t)j * B, xv);
@@ -212,9 +212,11 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     const bool have = kk < G && kf < k1;
     const int kq = min(kf, k1 - 1);
     const int jf = __ldg(a.ci + kq);
+    const bool lowf = __ldg(a.lowk + kq) != 0;
+    // from a zero iterate only blocks of lower colour contribute: the others'
+    // matrix rows are not loaded
     T arf[B];
-    load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
-    const bool lowf = jf != i && __ldg(a.colours + jf) < a.colour;
+    if (x_in || lowf) load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
     const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
     if constexpr (PDL) {  // everything below may depend on earlier kernels
         pdl_wait();
@@ -226,10 +228,11 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
         bgs_block<T, B, FB, CG>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
 #pragma unroll 4
         for (int k = kf + G; k < k1; k += G) {
+            const bool lower = __ldg(a.lowk + k) != 0;
+            if (!x_in && !lower) continue;
             const int j = __ldg(a.ci + k);
             T arow[B];
             load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
-            const bool lower = j != i && __ldg(a.colours + j) < a.colour;
             bgs_block<T, B, FB, CG>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0, acc);
         }
     }
@@ -401,6 +404,23 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
 template int launch_bgs_colour<double>(int, int, const BgsArgs&, cudaStream_t);
 template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
 
+// lowk[k] for every block of row i: its column j != i has a lower colour
+__global__ void lower_flags_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                   const int* __restrict__ colour, unsigned char* __restrict__ lowk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ci_ = colour[i];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        lowk[k] = (j != i && colour[j] < ci_) ? 1 : 0;
+    }
+}
+int launch_lower_flags(int n, const int* rp, const int* ci, const int* colour, unsigned char* lowk, cudaStream_t s) {
+    if (n <= 0) return BAMG_OK;
+    lower_flags_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, ci, colour, lowk);
+    return launched(1);
+}
+
 template <typename T, typename S>
 __global__ void dense_gemv_kernel(int nd, const S* __restrict__ ainv, const T* __restrict__ x,
                                   T* __restrict__ y) {
@@ -530,9 +550,9 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
         const bool have = kf < k1;
         const int kq = min(kf, k1 - 1);  // rows hold their diagonal block
         const int jf = __ldg(a.ci + kq);
+        const bool lowf = __ldg(a.lowk + kq) != 0;
         T arf[B];
-        load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
-        const bool lowf = jf != i && __ldg(a.colours + jf) < a.colour;
+        if (x_in || lowf) load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
         const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
         pdl_wait();
         pdl_trigger();
@@ -540,10 +560,11 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
             bgs_block<T, B, FB, false>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
 #pragma unroll(G > 1 ? 8 : 4)
             for (int k = kf + G; k < k1; k += G) {
+                const bool lower = __ldg(a.lowk + k) != 0;
+                if (!x_in && !lower) continue;
                 const int j = __ldg(a.ci + k);
                 T arow[B];
                 load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
-                const bool lower = j != i && __ldg(a.colours + j) < a.colour;
                 bgs_block<T, B, FB, false>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0,
                                            acc);
             }
