@@ -647,7 +647,8 @@ def run_ours(args):
                 "colours": [lv["colours"] for lv in stats["levels"]],
                 "mappings": {"smoother": [lv.get("smoother_mapping") for lv in stats["levels"][:-1]],
                              "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
-                             "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]]},
+                             "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]],
+                             "field_major": [lv.get("field_major") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
                 "cycle_prec": main_prec, "coarse_prec": coarse_prec, "use_pdl": args.pdl,
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),

@@ -117,6 +117,11 @@ typedef struct {
                          directly, not from a CUDA graph. A barrier wait that runs out (it
                          cannot while all CTAs are resident, which the cooperative launch
                          guarantees) is reported as BAMG_ETIMEOUT by fgmres_solve. Default 0. */
+    int value_layout; /* FP32 copy of a level's values in a cycle with F > 1 fields: 0 (default) =
+                         field-major rows (each block row holds field 0's rows of all its blocks,
+                         then field 1's, ...) on levels whose FP32 values exceed the L2 cache,
+                         block-major elsewhere; 1 = block-major everywhere; 2 = field-major
+                         everywhere. Same results either way (bitwise).                       */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

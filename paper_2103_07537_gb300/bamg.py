@@ -48,7 +48,8 @@ class AmgParams(C.Structure):
                 ("omega_s_arr", C.POINTER(C.c_double)), ("omega_s_len", C.c_longlong),
                 ("omega_p_arr", C.POINTER(C.c_double)), ("omega_p_len", C.c_longlong),
                 ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int),
-                ("use_pdl", C.c_int), ("coarse_prec", C.c_int), ("tail_grid", C.c_int)]
+                ("use_pdl", C.c_int), ("coarse_prec", C.c_int), ("tail_grid", C.c_int),
+                ("value_layout", C.c_int)]
 
 
 class BamgError(RuntimeError):

@@ -113,6 +113,7 @@ struct Level {
     float* vals32 = nullptr;
     int *colour = nullptr, *colour_nodes = nullptr, *colour_ptr_d = nullptr;
     unsigned char* lowk = nullptr;  // per block: its column has a lower colour than its row
+    int fm = 0;                     // vals32 in the field-major layout (see vrow)
     std::vector<int> colour_ptr;
     double* dinv64 = nullptr;
     float* dinv32 = nullptr;
@@ -359,6 +360,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->use_pdl = 1;
     p->coarse_prec = 64;
     p->tail_grid = 0;
+    p->value_layout = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -389,6 +391,11 @@ static double ms_since(Clock::time_point t0) {
 
 template <typename T>
 static const T* level_vals(const Level& L);
+// layout flag of level_vals<T>: the FP64 values are always block-major
+template <typename T>
+static int level_fm(const Level& L) {
+    return sizeof(T) == 4 ? L.fm : 0;
+}
 template <>
 const double* level_vals<double>(const Level& L) { return L.vals64; }
 template <>
@@ -596,6 +603,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         a.colour = 0;
         a.colours = L.colour;
         a.lowk = L.lowk;
+        a.fm = level_fm<T>(L);
         a.rp = L.rp;
         a.ci = L.ci;
         a.vals = level_vals<T>(L);
@@ -622,9 +630,15 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
         L.tune_us[2] = time_launch(s, e0, e1, reps,
-                                   [&] { return launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
+                                   [&] {
+                                       return launch_spmv<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci,
+                                                             level_vals<T>(L), x, r, y, s);
+                                   });
         L.tune_us[3] = time_launch(
-            s, e0, e1, reps, [&] { return launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s); });
+            s, e0, e1, reps,
+            [&] {
+                return launch_spmv_tpr<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci, level_vals<T>(L), x, r, y, s);
+            });
         if (h->p.autotune >= 2) L.bgs_tpr = h->p.autotune - 1;
         else if (h->p.autotune == 1) {
             // the fastest thread-per-row variant replaces warp per node only by the margin
@@ -640,10 +654,11 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         const Level& L0 = h->lev[0];
         BAMG_CUDA_TRY(cudaMemsetAsync(h->cyc_in, 0, sizeof(double) * (size_t)L0.n * b, s));
         const float t0 = time_launch(s, e0, e1, 10, [&] {
-            return launch_spmv<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
+            return launch_spmv<double>(b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
         });
         const float t1 = time_launch(s, e0, e1, 10, [&] {
-            return launch_spmv_tpr<double>(b, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out, s);
+            return launch_spmv_tpr<double>(b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out,
+                                           s);
         });
         h->outer_spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && t1 < kTuneMargin * t0);
     }
@@ -841,7 +856,18 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         if (h->p.cycle_prec == 32) {
             TRY(h->alloc(&L.vals32, (size_t)L.nnzb * bb));
             TRY(h->alloc(&L.dinv32, (size_t)L.n * h->F * h->fb * h->fb));
-            TRY(launch_convert_d2f((long)L.nnzb * bb, L.vals64, L.vals32, s));
+            // field-major rows on levels larger than L2 (a field step streams
+            // contiguous runs there; see vrow)
+            int l2 = 0, dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+                l2 = 0;
+            L.fm = h->F > 1 && (h->p.value_layout == 2 ||
+                                (h->p.value_layout == 0 && l2 > 0 && (double)L.nnzb * bb * sizeof(float) > (double)l2));
+            if (L.fm)
+                TRY(launch_convert_fieldmajor(L.n, b, h->fb, L.rp, L.vals64, L.vals32, s));
+            else
+                TRY(launch_convert_d2f((long)L.nnzb * bb, L.vals64, L.vals32, s));
             TRY(launch_convert_d2f((long)L.n * h->F * h->fb * h->fb, L.dinv64, L.dinv32, s));
         }
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -996,7 +1022,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
         prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1) ||
         (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32) ||
-        (prm.tail_grid != 0 && prm.tail_grid != 1))
+        (prm.tail_grid != 0 && prm.tail_grid != 1) || prm.value_layout < 0 || prm.value_layout > 2)
         return BAMG_EINVAL;
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
@@ -1081,6 +1107,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.colour = c;
         a.colours = L.colour;
         a.lowk = L.lowk;
+        a.fm = level_fm<T>(L);
         a.rp = L.rp;
         a.ci = L.ci;
         a.vals = level_vals<T>(L);
@@ -1222,8 +1249,9 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         const double tb = (double)L.p_nnz * (h->F * h->fb * h->fb * vs + 4.0);
         PL(BAMG_K_RESIDUAL, (double)L.nnzb * (b * b * es + 4.0) + (L.n + 1) * 4.0 + 3.0 * nb * es,
            2.0 * L.nnzb * b * b,
-           L.spmv_tpr ? launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
-                      : launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+           L.spmv_tpr
+               ? launch_spmv_tpr<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
+               : launch_spmv<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
         PL(BAMG_K_RESTRICT, tb + (C.n + 1) * 4.0 + nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
            restrict_explicit<T>(h, L, res, static_cast<T*>(C.rhs), s));
         TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
@@ -1251,6 +1279,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         ph.rp = L.rp;
         ph.ci = L.ci;
         ph.vals = level_vals<T>(L);
+        ph.fm = level_fm<T>(L);
         ph.x = cur;
         ph.rhs = rhs;
         ph.y = res;
@@ -1265,8 +1294,9 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         record(h, pr, rst_bytes, nb);
     } else {
         PL(BAMG_K_RESIDUAL, res_bytes, res_flops,
-           L.spmv_tpr ? launch_spmv_tpr<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
-                      : launch_spmv<T>(b, L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
+           L.spmv_tpr
+               ? launch_spmv_tpr<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s)
+               : launch_spmv<T>(b, h->fb, level_fm<T>(L), L.n, L.rp, L.ci, level_vals<T>(L), cur, rhs, res, s));
         PL(BAMG_K_RESTRICT, rst_bytes, nb,
            launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     }
@@ -1497,8 +1527,8 @@ static int ensure_krylov(bamg_ctx* h, int m) {
 // y = A x (or rhs - A x) with the finest FP64 operator, in the tuned row mapping
 static int outer_spmv(bamg_ctx* h, const double* x, const double* rhs, double* y, cudaStream_t s) {
     const Level& L0 = h->lev[0];
-    return h->outer_spmv_tpr ? launch_spmv_tpr<double>(h->b, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s)
-                             : launch_spmv<double>(h->b, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s);
+    return h->outer_spmv_tpr ? launch_spmv_tpr<double>(h->b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s)
+                             : launch_spmv<double>(h->b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s);
 }
 
 // ||x||^2 into dst (device), via the deterministic chunked reduction
@@ -1786,7 +1816,7 @@ extern "C" int bsr_spmv(const int* row_ptr, const int* col_idx, const double* va
                         const double* x, double* y, void* stream) {
     if (!row_ptr || !col_idx || !vals || !x || !y || n_nodes < 0 || b < 1 || b > kMaxB || x == y)
         return BAMG_EINVAL;
-    return launch_spmv<double>(b, n_nodes, row_ptr, col_idx, vals, x, nullptr, y,
+    return launch_spmv<double>(b, b, 0, n_nodes, row_ptr, col_idx, vals, x, nullptr, y,
                                static_cast<cudaStream_t>(stream));
 }
 
@@ -1857,7 +1887,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
              std::to_string(L.tune_us[5]) +
-             "],\"smoothed_p\":" + std::to_string(L.smoothed) +
+             "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0") + "}";
     }
     o += "]}";

@@ -36,6 +36,34 @@ __device__ __forceinline__ void set_error(int* flag, int code) { atomicCAS(flag,
 // run out at their next barrier and the kernel always ends.
 constexpr long kBarrierSpins = 1L << 24;  // one L2 round trip per spin: well over a second
 
+// Scalar row rr of block k of block row [k0, k1) in a level's values.  FP64
+// values (the setup's and the outer SpMV's) are block-major: block k holds
+// its B x B entries row by row.  The FP32 copy of a level larger than L2 in a
+// cycle with F > 1 fields is field-major (fm) inside each block row: the FB
+// rows of field f of all the row's blocks are contiguous (field 0 of every
+// block, then field 1, ...), so a field step of the smoother streams one
+// contiguous run per node instead of every other FB x B piece of the blocks.
+// (On L2-resident levels the block-major copy measured faster.)
+// (FM: the kernel instance for field-major values; launchers pick it from the
+// level's flag, so block-major code is compiled exactly as without it)
+template <typename T, int B, int FB>
+struct HasFm {
+    static constexpr bool value = sizeof(T) == 4 && FB < B;
+};
+template <typename T, int B, int FB, bool FM>
+__host__ __device__ constexpr int vstride() {
+    return (FM && HasFm<T, B, FB>::value) ? FB * B : B * B;  // same row of consecutive blocks
+}
+template <typename T, int B, int FB, bool FM>
+__host__ __device__ __forceinline__ const T* vrow(const T* vals, int k0, int k1, int k, int rr) {
+    if constexpr (FM && HasFm<T, B, FB>::value) {
+        const int f = rr / FB, r = rr - f * FB;
+        return vals + (size_t)k0 * B * B + ((size_t)f * (k1 - k0) + (k - k0)) * (FB * B) + (size_t)r * B;
+    } else {
+        return vals + (size_t)k * B * B + (size_t)rr * B;
+    }
+}
+
 // Block-wide sums of the first gn of G values per thread (NT threads): the
 // values go to shared memory (one row of G + 1 per thread), thread t adds
 // value t % G over the G rows of slice t / G (S = NT / G slices) in row
@@ -202,9 +230,10 @@ inline int launched(int k) {
 namespace bamg {
 
 // ---- solve-phase kernels (k_solve.cu) ----
-// y = A x (+ optional: y = rhs - A x when rhs != nullptr).  T = matrix/vector type.
+// y = A x (+ optional: y = rhs - A x when rhs != nullptr).  T = matrix/vector
+// type; vals in the layout of vrow for (b, fb) (fb = b: block-major)
 template <typename T>
-int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs,
+int launch_spmv(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs,
                 T* y, cudaStream_t s);
 // rc[I*b+d] = sum over members m of aggregate I (ascending) of res[m*b+d]
 template <typename T>
@@ -236,9 +265,12 @@ struct BgsArgs {
     // 1 where block k of row i has a column j != i of lower colour than i
     // (fixed for the level: no gather of the neighbour's colour in the cycle)
     const unsigned char* lowk = nullptr;
+    int fm = 0;  // vals in the field-major layout (see vrow)
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// FP32 copy of block-major FP64 values in the field-major layout of vrow
+int launch_convert_fieldmajor(int n, int b, int fb, const int* rp, const double* x, float* y, cudaStream_t s);
 // lowk[k] = 1 where block k of row i has a column j != i with colour[j] < colour[i]
 int launch_lower_flags(int n, const int* rp, const int* ci, const int* colour, unsigned char* lowk, cudaStream_t s);
 // thread-per-row variants (more loads in flight per warp; for large levels)
@@ -248,8 +280,8 @@ template <typename T>
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
 template <typename T>
-int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
-                    cudaStream_t s);
+int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
+                    const T* rhs, T* y, cudaStream_t s);
 
 // One recorded step of the V-cycle below the tail level, executed by the
 // cluster tail kernel (see k_solve.cu).
@@ -272,6 +304,7 @@ struct TailPhase {
     const void* x;
     const void* rhs;
     void* y;
+    int fm;  // residual phase: vals field-major (see vrow)
 };
 constexpr int kTailThreads = 512;
 template <typename T>

@@ -1700,6 +1700,28 @@ int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* e
 template int dense_lu_inverse<double>(int, double*, int*, double*, double*, double*, int*, cudaStream_t);
 template int dense_lu_inverse<float>(int, float*, int*, float*, float*, double*, int*, cudaStream_t);
 
+// FP32 copy of a level's values in the field-major layout of vrow (F > 1):
+// one warp per block row, entry (k, rr, c) of the block-major FP64 values to
+// k0 B^2 + (f len + k - k0) fb B + r B + c with rr = f fb + r, len = k1 - k0
+__global__ void convert_fieldmajor_kernel(int n, int b, int fb, const int* __restrict__ rp,
+                                          const double* __restrict__ x, float* __restrict__ y) {
+    const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int k0 = rp[i], k1 = rp[i + 1], len = k1 - k0, bb = b * b;
+    for (long e = lane; e < (long)len * bb; e += 32) {
+        const int kk = (int)(e / bb), w = (int)(e - (long)kk * bb);
+        const int rr = w / b, c = w - rr * b, f = rr / fb, r = rr - f * fb;
+        y[(size_t)k0 * bb + ((size_t)f * len + kk) * (fb * b) + (size_t)r * b + c] =
+            (float)x[(size_t)(k0 + kk) * bb + w];
+    }
+}
+int launch_convert_fieldmajor(int n, int b, int fb, const int* rp, const double* x, float* y, cudaStream_t s) {
+    if (n <= 0) return BAMG_OK;
+    convert_fieldmajor_kernel<<<ceil_div((long)n * 32, 256), 256, 0, s>>>(n, b, fb, rp, x, y);
+    return launched(1);
+}
+
 __global__ void convert_d2f_kernel(long m, const double* __restrict__ x, float* __restrict__ y) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (long)gridDim.x * blockDim.x)
         y[e] = (float)x[e];

@@ -90,7 +90,7 @@ __device__ __forceinline__ T reduce_rows(T v, int lane) {
 // y_i = (rhs_i -) sum_j A_ij x_j for block row i; whole warp.  With PDL the
 // lane's first block (column and matrix row, fixed for the cycle) is loaded
 // before the wait on the previous kernel.
-template <typename T, int B, bool CG, bool PDL = false>
+template <typename T, int B, int FB, bool CG, bool PDL = false, bool FM = false>
 __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict__ rp, const int* __restrict__ ci,
                                          const T* __restrict__ vals, const T* x, const T* rhs, T* y) {
     constexpr int G = kWarp / B;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
     T af[B];
     if (have) {
         jf = __ldg(ci + kf);
-        load_row<T, B>(vals + (size_t)kf * B * B + r * B, af);
+        load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, kf, r), af);
     }
     if constexpr (PDL) {
         pdl_wait();
@@ -122,7 +122,7 @@ __device__ __forceinline__ void spmv_row(long i, int lane, const int* __restrict
         for (int k = kf + G; k < k1; k += G) {
             const int j = __ldg(ci + k);
             T a[B], xv[B];
-            load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
+            load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k, r), a);
             load_vec<T, B, CG>(x + (size_t)j * B, xv);
 #pragma unroll
             for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
@@ -183,7 +183,7 @@ __device__ __forceinline__ void bgs_block(const BgsArgs& a, const T* xt, const T
     }
 }
 
-template <typename T, int B, int FB, bool CG, bool PDL = false>
+template <typename T, int B, int FB, bool CG, bool PDL = false, bool FM = false>
 __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     constexpr int G = kWarp / FB;  // blocks of the row per pass
     const int kk = lane / FB;
@@ -213,10 +213,13 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     const int kq = min(kf, k1 - 1);
     const int jf = __ldg(a.ci + kq);
     const bool lowf = __ldg(a.lowk + kq) != 0;
+    // this lane's matrix row in the row's first block; block k's is vstride apart
+    const T* vb = vrow<T, B, FB, FM>(vals, k0, k1, k0, f0 + r);
+    constexpr int VS = vstride<T, B, FB, FM>();
     // from a zero iterate only blocks of lower colour contribute: the others'
     // matrix rows are not loaded
     T arf[B];
-    if (x_in || lowf) load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
+    if (x_in || lowf) load_row<T, B>(vb + (size_t)(kq - k0) * VS, arf);
     const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
     if constexpr (PDL) {  // everything below may depend on earlier kernels
         pdl_wait();
@@ -232,7 +235,7 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
             if (!x_in && !lower) continue;
             const int j = __ldg(a.ci + k);
             T arow[B];
-            load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+            load_row<T, B>(vb + (size_t)(k - k0) * VS, arow);
             bgs_block<T, B, FB, CG>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0, acc);
         }
     }
@@ -301,37 +304,41 @@ __device__ __forceinline__ void restrict_dof(long t, int b, const int* __restric
 // ---------------------------------------------------------------------------
 // one-step kernels
 // ---------------------------------------------------------------------------
-template <typename T, int B>
+template <typename T, int B, int FB, bool FM>
 __global__ void __launch_bounds__(256, 4) spmv_kernel(int n, const int* __restrict__ rp,
                                                    const int* __restrict__ ci,
                                                    const T* __restrict__ vals, const T* __restrict__ x,
                                                    const T* __restrict__ rhs, T* __restrict__ y) {
     const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // uniform per warp
-    spmv_row<T, B, false, true>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
+    spmv_row<T, B, FB, false, true, FM>(i, threadIdx.x & (kWarp - 1), rp, ci, vals, x, rhs, y);
 }
 
 template <typename T>
-int launch_spmv(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs,
+int launch_spmv(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs,
                 T* y, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
     const int threads = 256;
     const int blocks = ceil_div((long)n * kWarp, threads);
-    switch (b) {
-#define CASE(BB) \
-    case BB:                                                                                      \
-        if (launch_k(spmv_kernel<T, BB>, blocks, threads, 0, s, n, rp, ci, vals, x, rhs, y) != cudaSuccess) \
-            return BAMG_ECUDA;                                                                    \
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF:                                                                                      \
+        if ((fm && HasFm<T, BB, FF>::value                                                                  \
+                 ? launch_k(spmv_kernel<T, BB, FF, HasFm<T, BB, FF>::value>, blocks, threads, 0, s, n, rp, ci, vals, \
+                            x, rhs, y)                                                                      \
+                 : launch_k(spmv_kernel<T, BB, FF, false>, blocks, threads, 0, s, n, rp, ci, vals, x, rhs, y)) != \
+            cudaSuccess)                                                                                    \
+            return BAMG_ECUDA;                                                                              \
         break;
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(5, 5) CASE(6, 6) CASE(7, 7) CASE(8, 8) CASE(4, 2) CASE(6, 3)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
     return launched(1);
 }
-template int launch_spmv<double>(int, int, const int*, const int*, const double*, const double*,
+template int launch_spmv<double>(int, int, int, int, const int*, const int*, const double*, const double*,
                                  const double*, double*, cudaStream_t);
-template int launch_spmv<float>(int, int, const int*, const int*, const float*, const float*,
+template int launch_spmv<float>(int, int, int, int, const int*, const int*, const float*, const float*,
                                 const float*, float*, cudaStream_t);
 
 template <typename T>
@@ -378,11 +385,11 @@ int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t
 template int launch_prolong<double>(int, int, const int*, const double*, double*, cudaStream_t);
 template int launch_prolong<float>(int, int, const int*, const float*, float*, cudaStream_t);
 
-template <typename T, int B, int FB>
+template <typename T, int B, int FB, bool FM>
 __global__ void __launch_bounds__(256, 4) bgs_colour_kernel(BgsArgs a) {
     const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_in_colour) return;  // uniform per warp
-    bgs_node<T, B, FB, false, true>(a, q, threadIdx.x & (kWarp - 1));
+    bgs_node<T, B, FB, false, true, FM>(a, q, threadIdx.x & (kWarp - 1));
 }
 
 template <typename T>
@@ -393,7 +400,10 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF:                                                                          \
-        if (launch_k(bgs_colour_kernel<T, BB, FF>, blocks, threads, 0, s, a) != cudaSuccess) return BAMG_ECUDA; \
+        if ((a.fm && HasFm<T, BB, FF>::value                                                    \
+                 ? launch_k(bgs_colour_kernel<T, BB, FF, HasFm<T, BB, FF>::value>, blocks, threads, 0, s, a) \
+                 : launch_k(bgs_colour_kernel<T, BB, FF, false>, blocks, threads, 0, s, a)) != cudaSuccess) \
+            return BAMG_ECUDA;                                                                  \
         break;
         CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
 #undef CASE
@@ -452,7 +462,7 @@ template int launch_dense_gemv<double, float>(int, const float*, const double*, 
 // levels far larger than L2).  The setup autotuner picks the mapping per
 // level and kernel by timing both.
 // ---------------------------------------------------------------------------
-template <typename T, int B>
+template <typename T, int B, int FB, bool FM>
 __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restrict__ rp,
                                                        const int* __restrict__ ci, const T* __restrict__ vals,
                                                        const T* __restrict__ x, const T* __restrict__ rhs,
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restr
     T af[B];
     if (k0 < k1) {
         jf = __ldg(ci + k0);
-        load_row<T, B>(vals + (size_t)k0 * B * B + r * B, af);
+        load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k0, r), af);
     }
     pdl_wait();
     pdl_trigger();
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restr
     for (int k = k0 + 1; k < k1; ++k) {
         const int j = __ldg(ci + k);
         T a[B], xv[B];
-        load_row<T, B>(vals + (size_t)k * B * B + r * B, a);
+        load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k, r), a);
         load_row<T, B>(x + (size_t)j * B, xv);
 #pragma unroll
         for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
@@ -491,26 +501,30 @@ __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restr
 }
 
 template <typename T>
-int launch_spmv_tpr(int b, int n, const int* rp, const int* ci, const T* vals, const T* x, const T* rhs, T* y,
-                    cudaStream_t s) {
+int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
+                    const T* rhs, T* y, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
     const int blocks = ceil_div((long)n * b, 256);
-    switch (b) {
-#define CASE(BB) \
-    case BB:                                                                                        \
-        if (launch_k(spmv_tpr_kernel<T, BB>, blocks, 256, 0, s, n, rp, ci, vals, x, rhs, y) != cudaSuccess) \
-            return BAMG_ECUDA;                                                                      \
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF:                                                                                      \
+        if ((fm && HasFm<T, BB, FF>::value                                                                  \
+                 ? launch_k(spmv_tpr_kernel<T, BB, FF, HasFm<T, BB, FF>::value>, blocks, 256, 0, s, n, rp, ci,     \
+                            vals, x, rhs, y)                                                                \
+                 : launch_k(spmv_tpr_kernel<T, BB, FF, false>, blocks, 256, 0, s, n, rp, ci, vals, x, rhs, y)) != \
+            cudaSuccess)                                                                                    \
+            return BAMG_ECUDA;                                                                              \
         break;
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(5, 5) CASE(6, 6) CASE(7, 7) CASE(8, 8) CASE(4, 2) CASE(6, 3)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
     return launched(1);
 }
-template int launch_spmv_tpr<double>(int, int, const int*, const int*, const double*, const double*,
+template int launch_spmv_tpr<double>(int, int, int, int, const int*, const int*, const double*, const double*,
                                      const double*, double*, cudaStream_t);
-template int launch_spmv_tpr<float>(int, int, const int*, const int*, const float*, const float*, const float*,
-                                    float*, cudaStream_t);
+template int launch_spmv_tpr<float>(int, int, int, int, const int*, const int*, const float*, const float*,
+                                    const float*, float*, cudaStream_t);
 
 // threads per CTA: a multiple of both FB and the warp size (the launch may use
 // half of it: smaller CTAs spread a small colour over more SMs)
@@ -525,7 +539,7 @@ struct TprBlock {
 // partial sums meet by a shuffle, and the FB row sums in shared memory for
 // the inverse.  G > 1 shortens each thread's chain of index-then-gather loads
 // (one block row after another), the latency that bounds large colours.
-template <typename T, int B, int FB, int G>
+template <typename T, int B, int FB, int G, bool FM>
 __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs a) {
     __shared__ T sh_t[TprBlock<FB>::kThreads];
     const int tloc = threadIdx.x;
@@ -551,8 +565,10 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
         const int kq = min(kf, k1 - 1);  // rows hold their diagonal block
         const int jf = __ldg(a.ci + kq);
         const bool lowf = __ldg(a.lowk + kq) != 0;
+        const T* vb = vrow<T, B, FB, FM>(vals, k0, k1, k0, f0 + r);
+        constexpr int VS = vstride<T, B, FB, FM>();
         T arf[B];
-        if (x_in || lowf) load_row<T, B>(vals + (size_t)kq * B * B + (size_t)(f0 + r) * B, arf);
+        if (x_in || lowf) load_row<T, B>(vb + (size_t)(kq - k0) * VS, arf);
         const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
         pdl_wait();
         pdl_trigger();
@@ -564,7 +580,7 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
                 if (!x_in && !lower) continue;
                 const int j = __ldg(a.ci + k);
                 T arow[B];
-                load_row<T, B>(vals + (size_t)k * B * B + (size_t)(f0 + r) * B, arow);
+                load_row<T, B>(vb + (size_t)(k - k0) * VS, arow);
                 bgs_block<T, B, FB, false>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0,
                                            acc);
             }
@@ -602,13 +618,15 @@ int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int v
 #define CASE(BB, FF)                                                                                          \
     case BB * 16 + FF: {                                                                                      \
         const int threads = TprBlock<FF>::kThreads >> (variant == 1 ? 1 : 0);                                 \
+        constexpr bool kFm = HasFm<T, BB, FF>::value;                                                        \
+        const int g4 = ceil_div(a.n_in_colour, threads / (FF * 4)), g1 = ceil_div(a.n_in_colour, threads / FF); \
         cudaError_t e;                                                                                        \
         if (variant == 2)                                                                                     \
-            e = launch_k(bgs_tpr_kernel<T, BB, FF, 4>, ceil_div(a.n_in_colour, threads / (FF * 4)), threads,  \
-                         0, s, a);                                                                            \
+            e = (a.fm && kFm) ? launch_k(bgs_tpr_kernel<T, BB, FF, 4, kFm>, g4, threads, 0, s, a)              \
+                              : launch_k(bgs_tpr_kernel<T, BB, FF, 4, false>, g4, threads, 0, s, a);           \
         else                                                                                                  \
-            e = launch_k(bgs_tpr_kernel<T, BB, FF, 1>, ceil_div(a.n_in_colour, threads / FF), threads, 0, s, \
-                         a);                                                                                  \
+            e = (a.fm && kFm) ? launch_k(bgs_tpr_kernel<T, BB, FF, 1, kFm>, g1, threads, 0, s, a)              \
+                              : launch_k(bgs_tpr_kernel<T, BB, FF, 1, false>, g1, threads, 0, s, a);           \
         if (e != cudaSuccess) return BAMG_ECUDA;                                                              \
         break;                                                                                                \
     }
@@ -639,13 +657,23 @@ template <typename T, int B, int FB>
 __device__ __forceinline__ void run_phase(const TailPhase& ph, int lane, long gw, long W, long gt, long NT) {
     switch (ph.type) {
         case kPhaseBgs:
-            for (long q = gw; q < ph.n; q += W) bgs_node<T, B, FB, true>(ph.bgs, q, lane);
+            if (HasFm<T, B, FB>::value && ph.bgs.fm)
+                for (long q = gw; q < ph.n; q += W)
+                    bgs_node<T, B, FB, true, false, HasFm<T, B, FB>::value>(ph.bgs, q, lane);
+            else
+                for (long q = gw; q < ph.n; q += W) bgs_node<T, B, FB, true>(ph.bgs, q, lane);
             break;
         case kPhaseResidual:
-            for (long i = gw; i < ph.n; i += W)
-                spmv_row<T, B, true>(i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals),
-                                     static_cast<const T*>(ph.x), static_cast<const T*>(ph.rhs),
-                                     static_cast<T*>(ph.y));
+            if (HasFm<T, B, FB>::value && ph.fm)
+                for (long i = gw; i < ph.n; i += W)
+                    spmv_row<T, B, FB, true, false, HasFm<T, B, FB>::value>(
+                        i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals), static_cast<const T*>(ph.x),
+                        static_cast<const T*>(ph.rhs), static_cast<T*>(ph.y));
+            else
+                for (long i = gw; i < ph.n; i += W)
+                    spmv_row<T, B, FB, true>(i, lane, ph.rp, ph.ci, static_cast<const T*>(ph.vals),
+                                             static_cast<const T*>(ph.x), static_cast<const T*>(ph.rhs),
+                                             static_cast<T*>(ph.y));
             break;
         case kPhaseRestrict:
             for (long t = gt; t < (long)ph.n * B; t += NT)

@@ -182,6 +182,35 @@ def test_cluster_tail_equals_per_kernel_cycle_bitwise(name, prec, grid):
     assert st_ == bamg.BAMG_OK and rr <= 1e-8 and it == it0
 
 
+@pytest.mark.parametrize("name", ["mhd2d_41_ragged", "random_b4_f2", "mhd2d_16"])
+def test_field_major_values_bitwise(name):
+    # FP32 values stored field-major inside each block row: the same entries
+    # in the same order, so the cycle is bitwise the block-major one, for every
+    # row mapping of the smoother and the residual
+    s, kw = SYSTEMS[name]()
+    r = dev(np.random.default_rng(11).standard_normal(s.n_unknowns))
+    for at in (0, 2, 3, 4):
+        zs = []
+        for layout in (1, 2):
+            g = make_solver(s, cycle_prec=32, autotune=at, value_layout=layout, **kw)
+            st = g.stats()["levels"]
+            assert all(lv["field_major"] == (layout == 2) for lv in st[:-1])
+            z = torch.empty_like(r)
+            g.apply(r, z)
+            zs.append(z)
+        torch.cuda.synchronize()
+        assert torch.equal(zs[0], zs[1]), at
+    # and through the cluster tail (recorded residual and smoother phases)
+    zt = []
+    for layout in (1, 2):
+        g = make_solver(s, cycle_prec=32, autotune=0, value_layout=layout, tail_dofs=1 << 30, **kw)
+        z = torch.empty_like(r)
+        g.apply(r, z)
+        zt.append(z)
+    torch.cuda.synchronize()
+    assert torch.equal(zt[0], zt[1])
+
+
 @pytest.mark.parametrize("tuned", [(2, "thread"), (4, "thread-split")])
 @pytest.mark.parametrize("prec", [64, 32])
 def test_row_mappings_agree_and_solve(prec, tuned):
