@@ -987,34 +987,64 @@ __global__ void transpose_kernel(int nd, const T* __restrict__ a, const int* __r
 // per CTA measured slower: the larger shared-memory share cuts the CTAs per
 // SM that hide the steps' latency.)
 constexpr int kInvThreads = 256;
-template <typename T>
+// NC columns per CTA: each step's factor column is loaded once for all of them
+// (FP32: two columns put the 2048 columns of the 3D coarsest level in one
+// wave of resident CTAs); the operations per column are those of NC = 1
+template <typename T, int NC>
 __global__ void __launch_bounds__(kInvThreads) lu_inverse_cols_kernel(int nd, const T* __restrict__ lt,
                                                                       const int* __restrict__ pos,
                                                                       T* __restrict__ inv) {
     extern __shared__ __align__(16) unsigned char inv_sh[];
-    T* x = reinterpret_cast<T*>(inv_sh);
-    __shared__ int pos0;
+    T* x = reinterpret_cast<T*>(inv_sh);  // [NC][nd]
+    __shared__ int pos0[NC];
+    __shared__ int kmin;
     const int tid = threadIdx.x;
-    for (int c = blockIdx.x; c < nd; c += gridDim.x) {
-        if (tid == 0) pos0 = pos[c];
-        for (int r = tid; r < nd; r += blockDim.x) x[r] = T(0);
+    for (int c0 = blockIdx.x * NC; c0 < nd; c0 += gridDim.x * NC) {
+        if (tid < NC) pos0[tid] = c0 + tid < nd ? pos[c0 + tid] : nd;
+        for (int r = tid; r < NC * nd; r += blockDim.x) x[r] = T(0);
         __syncthreads();
-        if (tid == 0) x[pos0] = T(1);
+        if (tid == 0) {
+            int m = nd;
+            for (int j = 0; j < NC; ++j) {
+                if (pos0[j] < nd) x[(size_t)j * nd + pos0[j]] = T(1);
+                m = min(m, pos0[j]);
+            }
+            kmin = m;
+        }
         __syncthreads();
-        for (int k = pos0; k < nd; ++k) {  // unit lower triangle (entries above pos0 stay zero)
-            const T xk = x[k];
-            if (xk != T(0))
-                for (int r = k + 1 + tid; r < nd; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
+        for (int k = kmin; k < nd; ++k) {  // unit lower triangle (entries above pos0 stay zero)
+            T xk[NC];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                xk[j] = x[(size_t)j * nd + k];
+                any |= xk[j] != T(0);
+            }
+            if (any)
+                for (int r = k + 1 + tid; r < nd; r += blockDim.x) {
+                    const T l = lt[(size_t)k * nd + r];
+#pragma unroll
+                    for (int j = 0; j < NC; ++j)
+                        if (xk[j] != T(0)) x[(size_t)j * nd + r] -= l * xk[j];
+                }
             __syncthreads();
         }
         for (int k = nd - 1; k >= 0; --k) {  // upper triangle
-            if (tid == 0) x[k] /= lt[(size_t)k * nd + k];
+            if (tid < NC) x[(size_t)tid * nd + k] /= lt[(size_t)k * nd + k];
             __syncthreads();
-            const T xk = x[k];
-            for (int r = tid; r < k; r += blockDim.x) x[r] -= lt[(size_t)k * nd + r] * xk;
+            T xk[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) xk[j] = x[(size_t)j * nd + k];
+            for (int r = tid; r < k; r += blockDim.x) {
+                const T u = lt[(size_t)k * nd + r];
+#pragma unroll
+                for (int j = 0; j < NC; ++j) x[(size_t)j * nd + r] -= u * xk[j];
+            }
             __syncthreads();
         }
-        for (int r = tid; r < nd; r += blockDim.x) inv[(size_t)r * nd + c] = x[r];
+        for (int j = 0; j < NC; ++j)
+            if (c0 + j < nd)
+                for (int r = tid; r < nd; r += blockDim.x) inv[(size_t)r * nd + c0 + j] = x[(size_t)j * nd + r];
         __syncthreads();
     }
 }
@@ -1693,8 +1723,10 @@ int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* e
         n += 1;
     }
     transpose_kernel<T><<<dim3(ceil_div(nd, 32), ceil_div(nd, 32)), dim3(32, 8), 0, s>>>(nd, a, perm, lt);
-    const int cols = nd < 152 * 8 ? nd : 152 * 8;
-    lu_inverse_cols_kernel<T><<<cols, kInvThreads, sizeof(T) * (size_t)nd, s>>>(nd, lt, pos, inv);
+    constexpr int NC = sizeof(T) == 4 ? 2 : 1;  // (FP64: more columns per CTA measured slower)
+    const int groups = (nd + NC - 1) / NC;
+    const int cols = groups < 152 * 8 ? groups : 152 * 8;
+    lu_inverse_cols_kernel<T, NC><<<cols, kInvThreads, sizeof(T) * (size_t)NC * nd, s>>>(nd, lt, pos, inv);
     return launched(n + 2);
 }
 template int dense_lu_inverse<double>(int, double*, int*, double*, double*, double*, int*, cudaStream_t);
