@@ -54,7 +54,7 @@ class Params(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("omega", C.c_double), ("smooth_p", C.c_int), ("omega_p", C.c_double),
                 ("omega_s_arr", _dp), ("omega_s_len", C.c_longlong), ("omega_p_arr", _dp),
-                ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int)]
+                ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int), ("sub_ilu", C.c_int)]
 
 
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -73,6 +73,8 @@ def _declare(L):
     L.oracle_setup.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _ip, C.POINTER(Params),
                                C.POINTER(C.c_void_p)]
     L.oracle_free.argtypes = [C.c_void_p]
+    L.oracle_ilu0_field.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, C.c_int, _dp]
+    L.oracle_ilu0_solve.argtypes = [C.c_int, C.c_int, _ip, _ip, _dp, _dp, _dp]
     L.oracle_free.restype = None
     L.oracle_num_levels.argtypes = [C.c_void_p]
     L.oracle_level_sizes.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip, _ip]
@@ -113,6 +115,30 @@ class OracleError(RuntimeError):
     def __init__(self, status, what):
         super().__init__(f"oracle {what} failed with status {status}")
         self.status = status
+
+
+def ilu0_field(row_ptr, col_idx, vals, b, field_of_dof, f):
+    """ILU(0) factors of the field-f part A_ff, [nnzb, fb, fb] (see oracle_ilu0_field)."""
+    rp, ci, v = _int32(row_ptr), _int32(col_idx), _f64(vals)
+    fm = _int32(field_of_dof)
+    fb = int(b) // (int(fm.max()) + 1)
+    n = rp.shape[0] - 1
+    lu = np.zeros((ci.size, fb, fb))
+    st = lib().oracle_ilu0_field(n, int(b), _i(fm), _i(rp), _i(ci), _d(v), int(f), _d(lu))
+    if st:
+        raise OracleError(st, "ilu0_field")
+    return lu
+
+
+def ilu0_solve(row_ptr, col_idx, lu, r):
+    """(L U)^{-1} r for the factors of ilu0_field."""
+    rp, ci, lu = _int32(row_ptr), _int32(col_idx), _f64(lu)
+    n, fb = rp.shape[0] - 1, lu.shape[1]
+    x = np.zeros(n * fb)
+    st = lib().oracle_ilu0_solve(n, fb, _i(rp), _i(ci), _d(lu), _d(_f64(r)), _d(x))
+    if st:
+        raise OracleError(st, "ilu0_solve")
+    return x
 
 
 def spmv(row_ptr, col_idx, vals, x):
@@ -282,7 +308,7 @@ class Hierarchy:
 
     def __init__(self, row_ptr, col_idx, vals, b, field_of_dof, max_levels=10, max_coarse=2500,
                  n_pre=1, n_post=1, omega=0.5, smooth_p=0, omega_p=0.0, omega_s_arr=None, omega_p_arr=None,
-                 mlp=None, mlp_levels=0):
+                 mlp=None, mlp_levels=0, sub_ilu=0):
         self.rp, self.ci, self.v = _int32(row_ptr), _int32(col_idx), _f64(vals)
         self.b = int(b)
         self.n = self.rp.shape[0] - 1
@@ -300,7 +326,7 @@ class Hierarchy:
                              0 if self._ws is None else self._ws.size,
                              None if self._wp is None else _d(self._wp),
                              0 if self._wp is None else self._wp.size,
-                             None if self._mlp is None else _d(self._mlp), int(mlp_levels))
+                             None if self._mlp is None else _d(self._mlp), int(mlp_levels), int(sub_ilu))
         h = C.c_void_p()
         st = lib().oracle_setup(self.n, self.ci.shape[0], self.b, _i(self.rp), _i(self.ci), _d(self.v),
                                 _i(fm), C.byref(self.params), C.byref(h))

@@ -285,6 +285,88 @@ static int find_pos(const int* ci, int k0, int k1, int col) {
     return -1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* ILU(0) of A_ff, the field-f part of the block matrix (Algorithm 1's       */
+/* sub-solve in the paper's runs, Sec. 4.3.2 and Sec. 5.1).                   */
+/* ------------------------------------------------------------------------ */
+int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                      const double* vals, int f, double* lu) {
+    int F, fb, fstart[ORACLE_MAX_B];
+    int st = field_layout(b, field_of_dof, &F, &fb, fstart);
+    if (st) return st;
+    if (f < 0 || f >= F || n < 0) return ORACLE_EINVAL;
+    const int f0 = fstart[f];
+    const size_t bb = (size_t)b * b, ff = (size_t)fb * fb;
+    const int nnzb = row_ptr[n];
+    for (int k = 0; k < nnzb; ++k)
+        for (int r = 0; r < fb; ++r)
+            for (int c = 0; c < fb; ++c) lu[k * ff + r * fb + c] = vals[k * bb + (size_t)(f0 + r) * b + f0 + c];
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < fb; ++r) {  /* scalar row p = i*fb + r */
+            const int p = i * fb + r;
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col_idx[k];
+                for (int c = 0; c < fb; ++c) {
+                    const int q = j * fb + c;
+                    if (q >= p) continue;
+                    /* u_qq: the scalar diagonal of row q (node j, dof c) */
+                    const int kd = find_pos(col_idx, row_ptr[j], row_ptr[j + 1], j);
+                    if (kd < 0) return ORACLE_EINVAL;
+                    const double uqq = lu[kd * ff + c * fb + c];
+                    if (uqq == 0.0) return ORACLE_ESINGULAR_BLOCK;
+                    const double l = lu[k * ff + r * fb + c] / uqq;
+                    lu[k * ff + r * fb + c] = l;
+                    /* a_pt -= l u_qt for t > q held by both rows p and q */
+                    for (int k2 = row_ptr[i]; k2 < row_ptr[i + 1]; ++k2) {
+                        const int j2 = col_idx[k2];
+                        const int kq = find_pos(col_idx, row_ptr[j], row_ptr[j + 1], j2);
+                        if (kq < 0) continue;
+                        for (int c2 = 0; c2 < fb; ++c2) {
+                            if (j2 * fb + c2 <= q) continue;
+                            lu[k2 * ff + r * fb + c2] -= l * lu[kq * ff + c * fb + c2];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return ORACLE_OK;
+}
+
+int oracle_ilu0_solve(int n, int fb, const int* row_ptr, const int* col_idx, const double* lu,
+                      const double* r, double* x) {
+    const size_t ff = (size_t)fb * fb;
+    /* L y = r (unit lower), rows ascending; y in x */
+    for (int i = 0; i < n; ++i)
+        for (int rr = 0; rr < fb; ++rr) {
+            const int p = i * fb + rr;
+            double s = r[p];
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col_idx[k];
+                for (int c = 0; c < fb; ++c)
+                    if (j * fb + c < p) s -= lu[k * ff + rr * fb + c] * x[j * fb + c];
+            }
+            x[p] = s;
+        }
+    /* U x = y, rows descending */
+    for (int i = n - 1; i >= 0; --i)
+        for (int rr = fb - 1; rr >= 0; --rr) {
+            const int p = i * fb + rr;
+            double s = x[p], d = 0.0;
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col_idx[k];
+                for (int c = 0; c < fb; ++c) {
+                    const int t = j * fb + c;
+                    if (t > p) s -= lu[k * ff + rr * fb + c] * x[t];
+                    else if (t == p) d = lu[k * ff + rr * fb + c];
+                }
+            }
+            if (d == 0.0) return ORACLE_ESINGULAR_BLOCK;
+            x[p] = s / d;
+        }
+    return ORACLE_OK;
+}
+
 int oracle_prolongator(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
                        const double* vals, const int* agg, int nc, const double* omega_p, int* p_rp,
                        int* p_ci, double* p_v) {
@@ -633,6 +715,7 @@ typedef struct {
     int* agg;       /* [n] aggregate of each node (levels above the coarsest) */
     int* colour;    /* [n] */
     double* dinv;   /* [n][F][fb*fb] */
+    double* ilu[ORACLE_MAX_B]; /* sub_ilu: ILU(0) factors of A_ff per field, [nnzb][fb][fb] */
     double *u, *rhs, *res; /* work vectors of n*b */
     double* omega_s; /* [n][F] smoother damping of every node and field */
     double* omega_p; /* [n_agg][F] prolongator smoothing weights (smooth_p) */
@@ -676,6 +759,7 @@ static void level_free(olevel* L) {
     free(L->r_rp);
     free(L->r_q);
     free(L->r_i);
+    for (int f = 0; f < ORACLE_MAX_B; ++f) free(L->ilu[f]);
 }
 
 /* per-field inverses of the node diagonal blocks of level L */
@@ -909,6 +993,14 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
         if (!L->dinv) st = level_dinv(h, L); /* computed while coarsening */
         if (st != ORACLE_OK) break;
+        if (p->sub_ilu)
+            for (int f = 0; f < h->F && st == ORACLE_OK; ++f) {
+                L->ilu[f] = (double*)malloc(sizeof(double) * (size_t)L->nnzb * h->fb * h->fb);
+                st = L->ilu[f] ? oracle_ilu0_field(L->n, b, h->field_of_dof, L->row_ptr, L->col_idx, L->vals, f,
+                                                   L->ilu[f])
+                               : ORACLE_ENOMEM;
+            }
+        if (st != ORACLE_OK) break;
     }
     if (st == ORACLE_OK) {
         h->xt = (double*)calloc(max_n * h->fb, sizeof(double));
@@ -1019,9 +1111,14 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
                     }
                     rf[(size_t)i * fb + r] = acc;
                 }
-            /* approximate A_ff^{-1} r_f: one multicolour node-block GS sweep from zero */
+            /* approximate A_ff^{-1} r_f: ILU(0) of A_ff, or one multicolour
+             * node-block GS sweep from zero */
             for (size_t e = 0; e < (size_t)L->n * fb; ++e) xt[e] = 0.0;
-            for (int col = 0; col < L->n_colours; ++col) {
+            if (h->p.sub_ilu) {
+                int st = oracle_ilu0_solve(L->n, fb, L->row_ptr, L->col_idx, L->ilu[f], rf, xt);
+                if (st) return st;
+            }
+            for (int col = 0; col < (h->p.sub_ilu ? 0 : L->n_colours); ++col) {
                 for (int i = 0; i < L->n; ++i) {
                     if (L->colour[i] != col) continue;
                     double t[ORACLE_MAX_B];

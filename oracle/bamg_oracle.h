@@ -97,6 +97,22 @@ int oracle_rap_general(int n, int b, const int* field_of_dof, const int* row_ptr
                        const double* vals, int nc, const int* p_rp, const int* p_ci, const double* p_v,
                        int* rp_c, int* ci_c, double* vals_c);
 
+/* ---- ILU(0) of a field's diagonal part (Algorithm 1's sub-solve, Sec. 4.3.2) ----
+ * A_ff is the scalar matrix of the fb x fb field-f sub-blocks of every stored
+ * block, rows and columns in node-then-dof order (scalar row i*fb + r).  Its
+ * incomplete LU with zero fill keeps that pattern: for the scalar rows in
+ * order, and for each entry q < p of row p in ascending column order,
+ * l_pq = a_pq / u_qq, then a_pt -= l_pq u_qt for every t > q of row p that
+ * row q also holds.  lu[nnzb][fb][fb] (sub-block layout): entry (k, r, c) of
+ * block k = (i, j) holds L (unit lower, strictly below the scalar diagonal)
+ * or U (on and above it) at scalar row i*fb + r, column j*fb + c.
+ * ORACLE_ESINGULAR_BLOCK if a pivot u_qq is zero. */
+int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                      const double* vals, int f, double* lu);
+/* x = (L U)^{-1} r with the factors of oracle_ilu0_field (r, x: n*fb) */
+int oracle_ilu0_solve(int n, int fb, const int* row_ptr, const int* col_idx, const double* lu,
+                      const double* r, double* x);
+
 /* ---- hierarchy ---- */
 
 typedef struct {
@@ -125,6 +141,9 @@ typedef struct {
     const double* mlp;
     int mlp_levels;   /* with mlp: levels 0..mlp_levels-1 take the network's weights, deeper
                          levels omega and the tentative P; 0 = every level */
+    int sub_ilu;      /* Algorithm 1's approximate sub-solve of A_ff: 0 = one multicolour
+                         node-block Gauss-Seidel sweep from zero; 1 = ILU(0) of A_ff (the
+                         paper's sub-solver, Sec. 4.3.2 and Sec. 5.1) */
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
