@@ -75,6 +75,8 @@ def _declare(L):
     L.oracle_free.argtypes = [C.c_void_p]
     L.oracle_ilu0_field.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, C.c_int, _dp]
     L.oracle_ilu0_solve.argtypes = [C.c_int, C.c_int, _ip, _ip, _dp, _dp, _dp]
+    L.oracle_ilu0_field_ordered.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, C.c_int, _ip, _dp]
+    L.oracle_ilu0_solve_ordered.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, _dp, _dp]
     L.oracle_free.restype = None
     L.oracle_num_levels.argtypes = [C.c_void_p]
     L.oracle_level_sizes.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip, _ip]
@@ -117,25 +119,30 @@ class OracleError(RuntimeError):
         self.status = status
 
 
-def ilu0_field(row_ptr, col_idx, vals, b, field_of_dof, f):
-    """ILU(0) factors of the field-f part A_ff, [nnzb, fb, fb] (see oracle_ilu0_field)."""
+def ilu0_field(row_ptr, col_idx, vals, b, field_of_dof, f, pos=None):
+    """ILU(0) factors of the field-f part A_ff, [nnzb, fb, fb] (see
+    oracle_ilu0_field); pos: elimination position of every node (None: natural)."""
     rp, ci, v = _int32(row_ptr), _int32(col_idx), _f64(vals)
     fm = _int32(field_of_dof)
     fb = int(b) // (int(fm.max()) + 1)
     n = rp.shape[0] - 1
     lu = np.zeros((ci.size, fb, fb))
-    st = lib().oracle_ilu0_field(n, int(b), _i(fm), _i(rp), _i(ci), _d(v), int(f), _d(lu))
+    ps = None if pos is None else _int32(pos)
+    st = lib().oracle_ilu0_field_ordered(n, int(b), _i(fm), _i(rp), _i(ci), _d(v), int(f),
+                                         None if ps is None else _i(ps), _d(lu))
     if st:
         raise OracleError(st, "ilu0_field")
     return lu
 
 
-def ilu0_solve(row_ptr, col_idx, lu, r):
-    """(L U)^{-1} r for the factors of ilu0_field."""
+def ilu0_solve(row_ptr, col_idx, lu, r, pos=None):
+    """(L U)^{-1} r for the factors of ilu0_field (same pos)."""
     rp, ci, lu = _int32(row_ptr), _int32(col_idx), _f64(lu)
     n, fb = rp.shape[0] - 1, lu.shape[1]
     x = np.zeros(n * fb)
-    st = lib().oracle_ilu0_solve(n, fb, _i(rp), _i(ci), _d(lu), _d(_f64(r)), _d(x))
+    ps = None if pos is None else _int32(pos)
+    st = lib().oracle_ilu0_solve_ordered(n, fb, _i(rp), _i(ci), None if ps is None else _i(ps), _d(lu),
+                                         _d(_f64(r)), _d(x))
     if st:
         raise OracleError(st, "ilu0_solve")
     return x

@@ -289,8 +289,11 @@ static int find_pos(const int* ci, int k0, int k1, int col) {
 /* ILU(0) of A_ff, the field-f part of the block matrix (Algorithm 1's       */
 /* sub-solve in the paper's runs, Sec. 4.3.2 and Sec. 5.1).                   */
 /* ------------------------------------------------------------------------ */
-int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
-                      const double* vals, int f, double* lu) {
+/* elimination position of node i: pos[i] (NULL: i) */
+static inline int epos(const int* pos, int i) { return pos ? pos[i] : i; }
+
+int oracle_ilu0_field_ordered(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                              const double* vals, int f, const int* pos, double* lu) {
     int F, fb, fstart[ORACLE_MAX_B];
     int st = field_layout(b, field_of_dof, &F, &fb, fstart);
     if (st) return st;
@@ -298,22 +301,48 @@ int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr,
     const int f0 = fstart[f];
     const size_t bb = (size_t)b * b, ff = (size_t)fb * fb;
     const int nnzb = row_ptr[n];
+    int* node_at = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));  /* inverse of pos */
+    if (!node_at) return ORACLE_ENOMEM;
+    for (int i = 0; i < n; ++i) node_at[epos(pos, i)] = i;
     for (int k = 0; k < nnzb; ++k)
         for (int r = 0; r < fb; ++r)
             for (int c = 0; c < fb; ++c) lu[k * ff + r * fb + c] = vals[k * bb + (size_t)(f0 + r) * b + f0 + c];
-    for (int i = 0; i < n; ++i) {
-        for (int r = 0; r < fb; ++r) {  /* scalar row p = i*fb + r */
-            const int p = i * fb + r;
-            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+    int order[64];  /* the blocks of a row by elimination position of their column */
+    for (int e = 0; e < n; ++e) {
+        const int i = node_at[e];
+        const int k0 = row_ptr[i], len = row_ptr[i + 1] - k0;
+        if (len > 64) {
+            free(node_at);
+            return ORACLE_EINVAL;
+        }
+        for (int t = 0; t < len; ++t) order[t] = k0 + t;
+        for (int t = 1; t < len; ++t)  /* insertion sort by epos(col) */
+            for (int u = t; u > 0 && epos(pos, col_idx[order[u]]) < epos(pos, col_idx[order[u - 1]]); --u) {
+                const int tmp = order[u];
+                order[u] = order[u - 1];
+                order[u - 1] = tmp;
+            }
+        for (int r = 0; r < fb; ++r) {  /* scalar row p = pos(i)*fb + r in elimination order */
+            const int p = e * fb + r;
+            /* the entries q < p of row p in ascending elimination order */
+            for (int t = 0; t < len; ++t) {
+                const int k = order[t];
                 const int j = col_idx[k];
+                const int e2 = epos(pos, j);
+                if (e2 > e) break;
                 for (int c = 0; c < fb; ++c) {
-                    const int q = j * fb + c;
+                    const int q = e2 * fb + c;
                     if (q >= p) continue;
-                    /* u_qq: the scalar diagonal of row q (node j, dof c) */
                     const int kd = find_pos(col_idx, row_ptr[j], row_ptr[j + 1], j);
-                    if (kd < 0) return ORACLE_EINVAL;
+                    if (kd < 0) {
+                        free(node_at);
+                        return ORACLE_EINVAL;
+                    }
                     const double uqq = lu[kd * ff + c * fb + c];
-                    if (uqq == 0.0) return ORACLE_ESINGULAR_BLOCK;
+                    if (uqq == 0.0) {
+                        free(node_at);
+                        return ORACLE_ESINGULAR_BLOCK;
+                    }
                     const double l = lu[k * ff + r * fb + c] / uqq;
                     lu[k * ff + r * fb + c] = l;
                     /* a_pt -= l u_qt for t > q held by both rows p and q */
@@ -322,7 +351,7 @@ int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr,
                         const int kq = find_pos(col_idx, row_ptr[j], row_ptr[j + 1], j2);
                         if (kq < 0) continue;
                         for (int c2 = 0; c2 < fb; ++c2) {
-                            if (j2 * fb + c2 <= q) continue;
+                            if (epos(pos, j2) * fb + c2 <= q) continue;
                             lu[k2 * ff + r * fb + c2] -= l * lu[kq * ff + c * fb + c2];
                         }
                     }
@@ -330,41 +359,63 @@ int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr,
             }
         }
     }
+    free(node_at);
+    return ORACLE_OK;
+}
+
+int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                      const double* vals, int f, double* lu) {
+    return oracle_ilu0_field_ordered(n, b, field_of_dof, row_ptr, col_idx, vals, f, NULL, lu);
+}
+
+int oracle_ilu0_solve_ordered(int n, int fb, const int* row_ptr, const int* col_idx, const int* pos,
+                              const double* lu, const double* r, double* x) {
+    const size_t ff = (size_t)fb * fb;
+    int* node_at = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!node_at) return ORACLE_ENOMEM;
+    for (int i = 0; i < n; ++i) node_at[epos(pos, i)] = i;
+    /* L y = r (unit lower), elimination order ascending; y in x */
+    for (int e = 0; e < n; ++e) {
+        const int i = node_at[e];
+        for (int rr = 0; rr < fb; ++rr) {
+            const int p = e * fb + rr;
+            double s = r[(size_t)i * fb + rr];
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col_idx[k];
+                for (int c = 0; c < fb; ++c)
+                    if (epos(pos, j) * fb + c < p) s -= lu[k * ff + rr * fb + c] * x[(size_t)j * fb + c];
+            }
+            x[(size_t)i * fb + rr] = s;
+        }
+    }
+    /* U x = y, elimination order descending */
+    for (int e = n - 1; e >= 0; --e) {
+        const int i = node_at[e];
+        for (int rr = fb - 1; rr >= 0; --rr) {
+            const int p = e * fb + rr;
+            double s = x[(size_t)i * fb + rr], d = 0.0;
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col_idx[k];
+                for (int c = 0; c < fb; ++c) {
+                    const int t = epos(pos, j) * fb + c;
+                    if (t > p) s -= lu[k * ff + rr * fb + c] * x[(size_t)j * fb + c];
+                    else if (t == p) d = lu[k * ff + rr * fb + c];
+                }
+            }
+            if (d == 0.0) {
+                free(node_at);
+                return ORACLE_ESINGULAR_BLOCK;
+            }
+            x[(size_t)i * fb + rr] = s / d;
+        }
+    }
+    free(node_at);
     return ORACLE_OK;
 }
 
 int oracle_ilu0_solve(int n, int fb, const int* row_ptr, const int* col_idx, const double* lu,
                       const double* r, double* x) {
-    const size_t ff = (size_t)fb * fb;
-    /* L y = r (unit lower), rows ascending; y in x */
-    for (int i = 0; i < n; ++i)
-        for (int rr = 0; rr < fb; ++rr) {
-            const int p = i * fb + rr;
-            double s = r[p];
-            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const int j = col_idx[k];
-                for (int c = 0; c < fb; ++c)
-                    if (j * fb + c < p) s -= lu[k * ff + rr * fb + c] * x[j * fb + c];
-            }
-            x[p] = s;
-        }
-    /* U x = y, rows descending */
-    for (int i = n - 1; i >= 0; --i)
-        for (int rr = fb - 1; rr >= 0; --rr) {
-            const int p = i * fb + rr;
-            double s = x[p], d = 0.0;
-            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const int j = col_idx[k];
-                for (int c = 0; c < fb; ++c) {
-                    const int t = j * fb + c;
-                    if (t > p) s -= lu[k * ff + rr * fb + c] * x[t];
-                    else if (t == p) d = lu[k * ff + rr * fb + c];
-                }
-            }
-            if (d == 0.0) return ORACLE_ESINGULAR_BLOCK;
-            x[p] = s / d;
-        }
-    return ORACLE_OK;
+    return oracle_ilu0_solve_ordered(n, fb, row_ptr, col_idx, NULL, lu, r, x);
 }
 
 int oracle_prolongator(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
@@ -716,6 +767,7 @@ typedef struct {
     int* colour;    /* [n] */
     double* dinv;   /* [n][F][fb*fb] */
     double* ilu[ORACLE_MAX_B]; /* sub_ilu: ILU(0) factors of A_ff per field, [nnzb][fb][fb] */
+    int* ilu_pos;   /* sub_ilu = 2: elimination position of every node (colour, then index) */
     double *u, *rhs, *res; /* work vectors of n*b */
     double* omega_s; /* [n][F] smoother damping of every node and field */
     double* omega_p; /* [n_agg][F] prolongator smoothing weights (smooth_p) */
@@ -760,6 +812,7 @@ static void level_free(olevel* L) {
     free(L->r_q);
     free(L->r_i);
     for (int f = 0; f < ORACLE_MAX_B; ++f) free(L->ilu[f]);
+    free(L->ilu_pos);
 }
 
 /* per-field inverses of the node diagonal blocks of level L */
@@ -993,11 +1046,19 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
         if (!L->dinv) st = level_dinv(h, L); /* computed while coarsening */
         if (st != ORACLE_OK) break;
+        if (p->sub_ilu == 2) {  /* colour order: colour ascending, then node index */
+            L->ilu_pos = (int*)malloc(sizeof(int) * (size_t)L->n);
+            if (!L->ilu_pos) st = ORACLE_ENOMEM;
+            int e = 0;
+            for (int c = 0; c < L->n_colours && st == ORACLE_OK; ++c)
+                for (int i = 0; i < L->n; ++i)
+                    if (L->colour[i] == c) L->ilu_pos[i] = e++;
+        }
         if (p->sub_ilu)
             for (int f = 0; f < h->F && st == ORACLE_OK; ++f) {
                 L->ilu[f] = (double*)malloc(sizeof(double) * (size_t)L->nnzb * h->fb * h->fb);
-                st = L->ilu[f] ? oracle_ilu0_field(L->n, b, h->field_of_dof, L->row_ptr, L->col_idx, L->vals, f,
-                                                   L->ilu[f])
+                st = L->ilu[f] ? oracle_ilu0_field_ordered(L->n, b, h->field_of_dof, L->row_ptr, L->col_idx,
+                                                           L->vals, f, L->ilu_pos, L->ilu[f])
                                : ORACLE_ENOMEM;
             }
         if (st != ORACLE_OK) break;
@@ -1115,7 +1176,7 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
              * node-block GS sweep from zero */
             for (size_t e = 0; e < (size_t)L->n * fb; ++e) xt[e] = 0.0;
             if (h->p.sub_ilu) {
-                int st = oracle_ilu0_solve(L->n, fb, L->row_ptr, L->col_idx, L->ilu[f], rf, xt);
+                int st = oracle_ilu0_solve_ordered(L->n, fb, L->row_ptr, L->col_idx, L->ilu_pos, L->ilu[f], rf, xt);
                 if (st) return st;
             }
             for (int col = 0; col < (h->p.sub_ilu ? 0 : L->n_colours); ++col) {

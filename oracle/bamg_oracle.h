@@ -112,6 +112,14 @@ int oracle_ilu0_field(int n, int b, const int* field_of_dof, const int* row_ptr,
 /* x = (L U)^{-1} r with the factors of oracle_ilu0_field (r, x: n*fb) */
 int oracle_ilu0_solve(int n, int fb, const int* row_ptr, const int* col_idx, const double* lu,
                       const double* r, double* x);
+/* The same in the elimination order given by pos[i] (the position of node i;
+ * scalar row i*fb + r is eliminated as pos[i]*fb + r).  With nodes ordered by
+ * colour (sub_ilu = 2) the nodes of one colour do not couple, so each colour's
+ * rows of the triangular solves depend on earlier colours only. */
+int oracle_ilu0_field_ordered(int n, int b, const int* field_of_dof, const int* row_ptr, const int* col_idx,
+                              const double* vals, int f, const int* pos, double* lu);
+int oracle_ilu0_solve_ordered(int n, int fb, const int* row_ptr, const int* col_idx, const int* pos,
+                              const double* lu, const double* r, double* x);
 
 /* ---- hierarchy ---- */
 
@@ -143,7 +151,8 @@ typedef struct {
                          levels omega and the tentative P; 0 = every level */
     int sub_ilu;      /* Algorithm 1's approximate sub-solve of A_ff: 0 = one multicolour
                          node-block Gauss-Seidel sweep from zero; 1 = ILU(0) of A_ff (the
-                         paper's sub-solver, Sec. 4.3.2 and Sec. 5.1) */
+                         paper's sub-solver, Sec. 4.3.2 and Sec. 5.1), natural order; 2 = ILU(0)
+                         with the nodes eliminated in colour order (colour, then index) */
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
