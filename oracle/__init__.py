@@ -54,7 +54,8 @@ class Params(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("max_coarse", C.c_int), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("omega", C.c_double), ("smooth_p", C.c_int), ("omega_p", C.c_double),
                 ("omega_s_arr", _dp), ("omega_s_len", C.c_longlong), ("omega_p_arr", _dp),
-                ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int), ("sub_ilu", C.c_int)]
+                ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int), ("sub_ilu", C.c_int),
+                ("n_node_fields", C.c_int), ("node_field_off", _ip)]
 
 
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -78,6 +79,7 @@ def _declare(L):
     L.oracle_ilu0_field_ordered.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, C.c_int, _ip, _dp]
     L.oracle_ilu0_solve_ordered.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip, _dp, _dp, _dp]
     L.oracle_free.restype = None
+    L.oracle_level_fields.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
     L.oracle_num_levels.argtypes = [C.c_void_p]
     L.oracle_level_sizes.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip, _ip]
     L.oracle_level_get.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _dp, _ip, _ip, _dp]
@@ -315,7 +317,10 @@ class Hierarchy:
 
     def __init__(self, row_ptr, col_idx, vals, b, field_of_dof, max_levels=10, max_coarse=2500,
                  n_pre=1, n_post=1, omega=0.5, smooth_p=0, omega_p=0.0, omega_s_arr=None, omega_p_arr=None,
-                 mlp=None, mlp_levels=0, sub_ilu=0):
+                 mlp=None, mlp_levels=0, sub_ilu=0, node_field_off=None):
+        """``node_field_off``: node ranges of fields on disjoint node sets
+        (non-co-located fields; every dof of a node in the node's field, so
+        ``field_of_dof`` is all zero); None for co-located fields."""
         self.rp, self.ci, self.v = _int32(row_ptr), _int32(col_idx), _f64(vals)
         self.b = int(b)
         self.n = self.rp.shape[0] - 1
@@ -333,7 +338,14 @@ class Hierarchy:
                              0 if self._ws is None else self._ws.size,
                              None if self._wp is None else _d(self._wp),
                              0 if self._wp is None else self._wp.size,
-                             None if self._mlp is None else _d(self._mlp), int(mlp_levels), int(sub_ilu))
+                             None if self._mlp is None else _d(self._mlp), int(mlp_levels), int(sub_ilu),
+                             0, None)
+        self._foff = None if node_field_off is None else _int32(node_field_off)
+        self.NF = 1
+        if self._foff is not None:
+            self.NF = self._foff.size - 1
+            self.params.n_node_fields = self.NF
+            self.params.node_field_off = _i(self._foff)
         h = C.c_void_p()
         st = lib().oracle_setup(self.n, self.ci.shape[0], self.b, _i(self.rp), _i(self.ci), _d(self.v),
                                 _i(fm), C.byref(self.params), C.byref(h))
@@ -378,6 +390,16 @@ class Hierarchy:
                                _d(dinv) if dinv is not None else None)
         return dict(n=n, nnzb=nnz, n_colours=ncol, n_agg=nagg, row_ptr=rp, col_idx=ci, vals=v,
                     agg=agg, colour=col, dinv=dinv)
+
+    def fields(self, l):
+        """(node_off[NF+1], colour_off[NF+1]) of level l; colour_off is None
+        on the coarsest level."""
+        no = np.zeros(self.NF + 1, np.int32)
+        co = np.zeros(self.NF + 1, np.int32)
+        st = lib().oracle_level_fields(self._h, l, _i(no), _i(co))
+        if st < 0:
+            raise OracleError(st, "level_fields")
+        return no, (None if l == self.num_levels - 1 else co)
 
     def prolongator(self, l):
         """(p_rp, p_ci, p_v[nnz, F, fb, fb]) of a level coarsened with smooth_p = 1."""

@@ -778,10 +778,14 @@ typedef struct {
     int *p_rp, *p_ci;
     double* p_v;
     int *r_rp, *r_q, *r_i;
+    /* fields on disjoint node sets (n_node_fields > 1) */
+    int* foff; /* [NF+1] nodes of field g: foff[g] <= i < foff[g+1] */
+    int* coff; /* [NF+1] colours of field g: coff[g] <= c < coff[g+1] */
 } olevel;
 
 struct oracle_hier {
     int nlev, b, F, fb;
+    int NF; /* fields on disjoint node sets (1: co-located fields only) */
     int field_of_dof[ORACLE_MAX_B];
     int fstart[ORACLE_MAX_B]; /* first dof of each field inside a node */
     oracle_params p;
@@ -813,6 +817,83 @@ static void level_free(olevel* L) {
     free(L->r_i);
     for (int f = 0; f < ORACLE_MAX_B; ++f) free(L->ilu[f]);
     free(L->ilu_pos);
+    free(L->foff);
+    free(L->coff);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fields on disjoint node sets (Sec. 4.3.1; Sec. 5, mixed elements).       */
+/* The graph of A_gg: the nodes of field g renumbered from 0 and the stored */
+/* blocks between two of them (columns keep their ascending order).         */
+/* ------------------------------------------------------------------------ */
+static int field_subgraph(const olevel* L, int g, int** rp_out, int** ci_out) {
+    const int o0 = L->foff[g], o1 = L->foff[g + 1], m = o1 - o0;
+    int* rp = (int*)malloc(sizeof(int) * (size_t)(m + 1));
+    int* ci = (int*)malloc(sizeof(int) * (size_t)(L->row_ptr[o1] - L->row_ptr[o0] + 1));
+    if (!rp || !ci) {
+        free(rp);
+        free(ci);
+        return ORACLE_ENOMEM;
+    }
+    int e = 0;
+    rp[0] = 0;
+    for (int i = o0; i < o1; ++i) {
+        for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+            const int j = L->col_idx[k];
+            if (j >= o0 && j < o1) ci[e++] = j - o0;
+        }
+        rp[i - o0 + 1] = e;
+    }
+    *rp_out = rp;
+    *ci_out = ci;
+    return ORACLE_OK;
+}
+
+/* separate aggregation of every field on the graph of its own diagonal
+ * block; field g's aggregate ids follow those of fields 0..g-1, so the
+ * piecewise-constant P = diag(P_0, P_1, ...) (eq. blocktransfers) and the
+ * coarse field ranges are foff_c[g] = the aggregates of fields before g.
+ * Returns the total number of aggregates. */
+static int aggregate_node_fields(const oracle_hier* h, const olevel* L, int* agg, int* foff_c) {
+    int base = 0;
+    foff_c[0] = 0;
+    for (int g = 0; g < h->NF; ++g) {
+        const int o0 = L->foff[g], m = L->foff[g + 1] - o0;
+        int *rp = NULL, *ci = NULL;
+        int st = field_subgraph(L, g, &rp, &ci);
+        if (st) return st;
+        int* is_root = (int*)malloc(sizeof(int) * (size_t)m);
+        int nc = is_root ? oracle_aggregate(m, rp, ci, agg + o0, is_root) : ORACLE_ENOMEM;
+        free(is_root);
+        free(rp);
+        free(ci);
+        if (nc < 0) return nc;
+        for (int i = 0; i < m; ++i) agg[o0 + i] += base;
+        base += nc;
+        foff_c[g + 1] = base;
+    }
+    return base;
+}
+
+/* first-fit colours of every field on the graph of its diagonal block,
+ * numbered after the colours of the earlier fields (coff) */
+static int colour_node_fields(const oracle_hier* h, olevel* L) {
+    int base = 0;
+    L->coff[0] = 0;
+    for (int g = 0; g < h->NF; ++g) {
+        const int o0 = L->foff[g], m = L->foff[g + 1] - o0;
+        int *rp = NULL, *ci = NULL;
+        int st = field_subgraph(L, g, &rp, &ci);
+        if (st) return st;
+        int nc = oracle_colour(m, rp, ci, L->colour + o0);
+        free(rp);
+        free(ci);
+        if (nc < 0) return nc;
+        for (int i = 0; i < m; ++i) L->colour[o0 + i] += base;
+        base += nc;
+        L->coff[g + 1] = base;
+    }
+    return base;
 }
 
 /* per-field inverses of the node diagonal blocks of level L */
@@ -941,9 +1022,30 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         }
         h->fstart[f] = first;
     }
+    /* fields on disjoint node sets: contiguous non-empty node ranges, one
+     * field per node, and only the plain method (tentative P, constant
+     * damping, the multicolour sub-solve) */
+    h->NF = p->n_node_fields > 1 ? p->n_node_fields : 1;
+    if (h->NF > 1) {
+        const int* off = p->node_field_off;
+        int bad = h->NF > ORACLE_MAX_NODE_FIELDS || !off || F != 1 || p->smooth_p || p->sub_ilu ||
+                  p->omega_s_arr || p->omega_p_arr || p->mlp;
+        if (!bad) {
+            bad = off[0] != 0 || off[h->NF] != n;
+            for (int g = 0; g < h->NF && !bad; ++g) bad = off[g + 1] <= off[g];
+        }
+        if (bad) {
+            free(h);
+            return ORACLE_EINVAL;
+        }
+    }
     const size_t bb = (size_t)b * b;
     /* level 0 = a copy of A */
     olevel* L0 = &h->lev[0];
+    if (h->NF > 1) {
+        L0->foff = (int*)malloc(sizeof(int) * (size_t)(h->NF + 1));
+        memcpy(L0->foff, p->node_field_off, sizeof(int) * (size_t)(h->NF + 1));
+    }
     L0->n = n;
     L0->nnzb = nnzb;
     L0->row_ptr = (int*)malloc(sizeof(int) * (size_t)(n + 1));
@@ -961,16 +1063,28 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     while (h->nlev < p->max_levels && (long)h->lev[h->nlev - 1].n * b > p->max_coarse) {
         olevel* F_ = &h->lev[h->nlev - 1];
         F_->agg = (int*)malloc(sizeof(int) * (size_t)F_->n);
-        int* is_root = (int*)malloc(sizeof(int) * (size_t)F_->n);
-        int nc = oracle_aggregate(F_->n, F_->row_ptr, F_->col_idx, F_->agg, is_root);
-        free(is_root);
+        int nc;
+        if (h->NF > 1) {
+            /* separate aggregates per field block (Sec. 4.3.1) */
+            olevel* Cf = &h->lev[h->nlev];
+            Cf->foff = (int*)malloc(sizeof(int) * (size_t)(h->NF + 1));
+            nc = Cf->foff ? aggregate_node_fields(h, F_, F_->agg, Cf->foff) : ORACLE_ENOMEM;
+        } else {
+            int* is_root = (int*)malloc(sizeof(int) * (size_t)F_->n);
+            nc = oracle_aggregate(F_->n, F_->row_ptr, F_->col_idx, F_->agg, is_root);
+            free(is_root);
+        }
         if (nc < 0) {
+            free(h->lev[h->nlev].foff);
+            h->lev[h->nlev].foff = NULL;
             st = nc;
             break;
         }
         if (nc == 0 || nc == F_->n) { /* no coarsening possible */
             free(F_->agg);
             F_->agg = NULL;
+            free(h->lev[h->nlev].foff);
+            h->lev[h->nlev].foff = NULL;
             break;
         }
         F_->n_agg = nc;
@@ -1043,7 +1157,16 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         L->res = (double*)calloc((size_t)L->n * b, sizeof(double));
         if (l == h->nlev - 1) break;
         L->colour = (int*)malloc(sizeof(int) * (size_t)L->n);
-        L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
+        if (h->NF > 1) {
+            L->coff = (int*)malloc(sizeof(int) * (size_t)(h->NF + 1));
+            L->n_colours = L->coff ? colour_node_fields(h, L) : ORACLE_ENOMEM;
+            if (L->n_colours < 0) {
+                st = L->n_colours;
+                break;
+            }
+        } else {
+            L->n_colours = oracle_colour(L->n, L->row_ptr, L->col_idx, L->colour);
+        }
         if (!L->dinv) st = level_dinv(h, L); /* computed while coarsening */
         if (st != ORACLE_OK) break;
         if (p->sub_ilu == 2) {  /* colour order: colour ascending, then node index */
@@ -1118,6 +1241,25 @@ int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, do
     return ORACLE_OK;
 }
 
+int oracle_level_fields(const oracle_hier* h, int l, int* node_off, int* colour_off) {
+    if (l < 0 || l >= h->nlev) return ORACLE_EINVAL;
+    const olevel* L = &h->lev[l];
+    if (h->NF > 1) {
+        if (node_off) memcpy(node_off, L->foff, sizeof(int) * (size_t)(h->NF + 1));
+        if (colour_off && L->coff) memcpy(colour_off, L->coff, sizeof(int) * (size_t)(h->NF + 1));
+    } else {
+        if (node_off) {
+            node_off[0] = 0;
+            node_off[1] = L->n;
+        }
+        if (colour_off) {
+            colour_off[0] = 0;
+            colour_off[1] = l < h->nlev - 1 ? L->n_colours : 0;
+        }
+    }
+    return h->NF;
+}
+
 int oracle_level_p_nnz(const oracle_hier* h, int l) {
     if (l < 0 || l >= h->nlev) return ORACLE_EINVAL;
     return h->lev[l].p_v ? h->lev[l].p_nnz : 0;
@@ -1150,9 +1292,68 @@ int oracle_level_omega(const oracle_hier* h, int l, double* omega_s, double* ome
 /*     c: x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j));        */
 /*   x_f := x_f + omega x~_f.                                               */
 /* ------------------------------------------------------------------------ */
+/* Algorithm 1 with the field blocks on disjoint node sets: field g owns the */
+/* nodes o_g <= i < o_{g+1} with all their dofs, A_gg is the block matrix    */
+/* between those nodes.  One sweep visits the fields in order; for field g: */
+/*   r_g := b_g - sum_h A_gh x_h        (rows of field g, all columns);     */
+/*   x~_g := one multicolour node-block Gauss-Seidel sweep on A_gg from 0   */
+/*     (field g's colours ascending; only columns of field g take part);    */
+/*   x_g := x_g + omega x~_g.                                               */
+static int bgs_node_fields(oracle_hier* h, int l, double* x, const double* rhs, int sweeps, int unit_damping) {
+    olevel* L = &h->lev[l];
+    const int b = h->b;
+    const size_t bb = (size_t)b * b;
+    double* rf = h->rf;
+    double* xt = h->xt;
+    for (int s = 0; s < sweeps; ++s) {
+        for (int g = 0; g < h->NF; ++g) {
+            const int o0 = L->foff[g], o1 = L->foff[g + 1];
+            for (int i = o0; i < o1; ++i)
+                for (int r = 0; r < b; ++r) {
+                    double acc = rhs[(size_t)i * b + r];
+                    for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                        const double* blk = L->vals + (size_t)k * bb;
+                        int j = L->col_idx[k];
+                        for (int c = 0; c < b; ++c) acc -= blk[r * b + c] * x[(size_t)j * b + c];
+                    }
+                    rf[(size_t)(i - o0) * b + r] = acc;
+                }
+            for (size_t e = 0; e < (size_t)(o1 - o0) * b; ++e) xt[e] = 0.0;
+            for (int col = L->coff[g]; col < L->coff[g + 1]; ++col) {
+                for (int i = o0; i < o1; ++i) {
+                    if (L->colour[i] != col) continue;
+                    double t[ORACLE_MAX_B];
+                    for (int r = 0; r < b; ++r) {
+                        double acc = rf[(size_t)(i - o0) * b + r];
+                        for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                            int j = L->col_idx[k];
+                            if (j == i || j < o0 || j >= o1) continue;
+                            const double* blk = L->vals + (size_t)k * bb;
+                            for (int c = 0; c < b; ++c) acc -= blk[r * b + c] * xt[(size_t)(j - o0) * b + c];
+                        }
+                        t[r] = acc;
+                    }
+                    const double* Di = L->dinv + (size_t)i * bb;
+                    for (int r = 0; r < b; ++r) {
+                        double acc = 0.0;
+                        for (int c = 0; c < b; ++c) acc += Di[r * b + c] * t[c];
+                        xt[(size_t)(i - o0) * b + r] = acc;
+                    }
+                }
+            }
+            for (int i = o0; i < o1; ++i) {
+                const double om = unit_damping ? 1.0 : L->omega_s[i];
+                for (int r = 0; r < b; ++r) x[(size_t)i * b + r] += om * xt[(size_t)(i - o0) * b + r];
+            }
+        }
+    }
+    return ORACLE_OK;
+}
+
 /* unit_damping: omega = 1 everywhere (used by the training targets) */
 static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int sweeps, int unit_damping) {
     if (l < 0 || l >= h->nlev - 1) return ORACLE_EINVAL;
+    if (h->NF > 1) return bgs_node_fields(h, l, x, rhs, sweeps, unit_damping);
     olevel* L = &h->lev[l];
     const int b = h->b, F = h->F, fb = h->fb;
     const size_t bb = (size_t)b * b;

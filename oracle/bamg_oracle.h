@@ -12,6 +12,8 @@
  *   - aggregates: a disjoint cover of the nodes, one coarse node each, built
  *     greedily on the graph of A00 and cloned to the Maxwell block
  *                                                  Sec. 4.3.1, cloned-aggregation figure
+ *     or, for fields on different node sets, built separately on the graph
+ *     of each diagonal block                       Sec. 4.3.1; Sec. 5, mixed elements
  *   - piecewise-constant interpolation per solution component  Sec. 4.3.1
  *   - damped block Gauss-Seidel smoother           Sec. 4.3.2, Algorithm 1
  *   - direct solve on the coarsest level           Fig. 1; Sec. 5.1
@@ -43,6 +45,7 @@ extern "C" {
 
 #define ORACLE_MAX_LEVELS 16
 #define ORACLE_MAX_B 8
+#define ORACLE_MAX_NODE_FIELDS 8
 
 typedef struct oracle_hier oracle_hier;
 
@@ -153,6 +156,20 @@ typedef struct {
                          node-block Gauss-Seidel sweep from zero; 1 = ILU(0) of A_ff (the
                          paper's sub-solver, Sec. 4.3.2 and Sec. 5.1), natural order; 2 = ILU(0)
                          with the nodes eliminated in colour order (colour, then index) */
+    /* ---- fields on disjoint node sets (fields that are not co-located: the
+     * mixed-element case of Sec. 4.3.1 and Sec. 5) ----
+     * n_node_fields > 1: the nodes form n_node_fields contiguous ranges
+     * [node_field_off[g], node_field_off[g+1]), and every dof of a node belongs
+     * to the node's field (field_of_dof all 0).  On every level the aggregates
+     * of field g are built separately on the graph of A_gg (the blocks between
+     * nodes of field g), numbered after those of the earlier fields, so that
+     * P = diag(P_0, P_1, ...) and the coarse nodes keep contiguous field ranges.
+     * Colours are per field too (first fit on the graph of A_gg), numbered after
+     * those of the earlier fields, and Algorithm 1 takes the node fields as its
+     * field blocks.  Requires smooth_p = 0, sub_ilu = 0, no weight arrays and
+     * no mlp.  n_node_fields <= 1: the co-located case above. */
+    int n_node_fields;
+    const int* node_field_off;
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
@@ -168,6 +185,10 @@ int oracle_level_sizes(const oracle_hier* h, int l, int* n, int* nnzb, int* n_co
 int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, double* vals,
                      int* agg, int* colour, double* dinv);
 
+/* Field ranges of level l with n_node_fields > 1: node_off[NF+1] (nodes of
+ * field g), colour_off[NF+1] (colours of field g; levels with a smoother).
+ * Either pointer may be NULL.  Returns NF (1 in the co-located case). */
+int oracle_level_fields(const oracle_hier* h, int l, int* node_off, int* colour_off);
 /* Smoothed prolongator of level l (levels that were coarsened with
  * smooth_p = 1): stored blocks, then the copies (any pointer may be NULL). */
 int oracle_level_p_nnz(const oracle_hier* h, int l);

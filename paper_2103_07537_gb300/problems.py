@@ -16,6 +16,10 @@ systems stand in for them with the same block structure:
   {Bx, By, psi}), dofs per node (u, v, p, Bx, By, psi), two field blocks, the
   B-u coupling being a linearised cross product with a frozen smooth field B0.
 * ``stokes3d``: Q1-Q1 stabilised Stokes on an N^3 hex grid, dofs (u, v, w, p).
+* ``mhd2d_q2q1``: the same two blocks on different element spaces (the
+  mixed-element example of Sec. 5): {u, v, p} on biquadratic Q2 nodes,
+  {Bx, By, psi} on bilinear Q1 vertices, so the two fields live on disjoint
+  node sets (hydrodynamic nodes first), three dofs per node in both.
 
 Block-row layout (shared by every consumer): nodes are numbered row-major
 (x fastest); block CSR over nodes with column indices ascending; each stored
@@ -74,6 +78,9 @@ class BlockSystem:
     rhs: np.ndarray  # float64 [n_nodes * b]
     field_of_dof: list
     params: dict
+    # fields on disjoint node sets: field g owns nodes node_field_off[g] ..
+    # node_field_off[g+1]-1 with all their dofs (None: co-located fields)
+    node_field_off: list | None = None
 
     @property
     def nnzb(self) -> int:
@@ -388,6 +395,173 @@ def mhd2d(N: int = 128, seed: int = 1, nu: float | None = None, eta: float | Non
                        [0, 0, 0, 1, 1, 1],
                        dict(kind="mhd2d", N=N, seed=seed, nu=nu, eta="per-cell" if eta_cells else eta,
                             tau_p=tau_p, tau_psi="per-cell" if eta_cells else tau_s, h=h))
+
+
+def _lagrange_1d(order, xi):
+    """Values and derivatives of the 1D Lagrange basis of ``order`` (1 or 2)
+    on the equispaced nodes of [-1, 1], at the points ``xi``."""
+    if order == 1:
+        v = np.stack([(1.0 - xi) / 2.0, (1.0 + xi) / 2.0], axis=-1)
+        d = np.stack([np.full_like(xi, -0.5), np.full_like(xi, 0.5)], axis=-1)
+    else:
+        v = np.stack([xi * (xi - 1.0) / 2.0, 1.0 - xi * xi, xi * (xi + 1.0) / 2.0], axis=-1)
+        d = np.stack([xi - 0.5, -2.0 * xi, xi + 0.5], axis=-1)
+    return v, d
+
+
+def _tensor_basis_2d(order, xi, eta):
+    """phi[q, l] and reference gradients dphi[q, l, a] of the tensor-product
+    Lagrange element (local node l = lx + (order + 1) * ly) at points (xi, eta)."""
+    vx, dx = _lagrange_1d(order, xi)
+    vy, dy = _lagrange_1d(order, eta)
+    m = order + 1
+    phi = np.einsum("qx,qy->qyx", vx, vy).reshape(-1, m * m)
+    gx = np.einsum("qx,qy->qyx", dx, vy).reshape(-1, m * m)
+    gy = np.einsum("qx,qy->qyx", vx, dy).reshape(-1, m * m)
+    return phi, np.stack([gx, gy], axis=-1)
+
+
+def mhd2d_q2q1(N: int = 64, seed: int = 1, nu: float | None = None, eta: float | None = None,
+               eta_range=(1e-3, 1.0), nu_range=(1e-3, 1.0)) -> BlockSystem:
+    """The two-field system of ``mhd2d`` on mixed elements: Q2/Q2 for the
+    hydrodynamic block {u, v, p} and Q1/Q1 for the magnetic block
+    {Bx, By, psi} (the mixed-element example of Sec. 5, in 2D), N x N cells
+    of the unit square.
+
+    Nodes: the (2N+1)^2 Q2 nodes first (row-major, x fastest), then the
+    (N+1)^2 Q1 vertices; every node carries three dofs of its own field, so
+    ``field_of_dof`` is [0, 0, 0] and ``node_field_off`` = [0, n_q2, n_q2 + n_q1].
+    Blocks (3 x 3) between
+      two Q2 nodes:  [nu K2 (x) I_2, G2; -G2^T, tau_p K2],
+      two Q1 nodes:  [eta K1 (x) I_2, G1; -G1^T, tau_psi K1],
+      a Q1 row and a Q2 column: Y (B-row against u-column, 2 x 2 corner),
+      a Q2 row and a Q1 column: Z = -Y^T,
+    with K, G and Y defined as in ``mhd2d`` (Y with Q1 test and Q2 trial
+    functions), 3 x 3 Gauss quadrature (exact for these products),
+    tau_p = (h/2)^2 / (12 nu) (the Q2 node spacing) and tau_psi = h^2 / (12 eta).
+    Dirichlet u and v on the boundary Q2 nodes, B and psi on the boundary Q1
+    nodes, pressure pinned at Q2 node 0.  The pattern holds every pair of
+    nodes that share a cell.
+
+    Stream layout for ``seed``: [0] nu, [1] eta, [2..17] Fourier coefficients
+    of B0, then the right-hand side (uniform[-1, 1]).
+    """
+    h = 1.0 / N
+    b = 3
+    m2, m1 = 2 * N + 1, N + 1
+    n2, n1 = m2 * m2, m1 * m1
+    n = n2 + n1
+    u01 = uniform01(seed, 0, 2)
+    if nu is None:
+        lo, hi = math.log10(nu_range[0]), math.log10(nu_range[1])
+        nu = 10.0 ** (lo + (hi - lo) * u01[0])
+    if eta is None:
+        lo, hi = math.log10(eta_range[0]), math.log10(eta_range[1])
+        eta = 10.0 ** (lo + (hi - lo) * u01[1])
+    coef = frozen_field_coeffs(seed, 2)
+    rhs_start = 2 + N_FOURIER * N_FOURIER
+
+    # 3 x 3 Gauss points of [-1, 1]^2 (x fastest) and their weights
+    g = math.sqrt(3.0 / 5.0)
+    x1 = np.array([-g, 0.0, g])
+    w1 = np.array([5.0, 8.0, 5.0]) / 9.0
+    xi = np.tile(x1, 3)
+    et = np.repeat(x1, 3)
+    wq = np.tile(w1, 3) * np.repeat(w1, 3)
+    phi2, dphi2 = _tensor_basis_2d(2, xi, et)
+    phi1, dphi1 = _tensor_basis_2d(1, xi, et)
+    jac = (h / 2.0) ** 2
+    grad2 = dphi2 * (2.0 / h)
+    grad1 = dphi1 * (2.0 / h)
+    K2 = np.einsum("q,qla,qma->lm", wq, grad2, grad2) * jac
+    G2 = -np.einsum("q,qla,qm->lam", wq, grad2, phi2) * jac
+    K1 = np.einsum("q,qla,qma->lm", wq, grad1, grad1) * jac
+    G1 = -np.einsum("q,qla,qm->lam", wq, grad1, phi1) * jac
+    tau_p = (h / 2.0) ** 2 / (12.0 * nu)
+    tau_s = h * h / (12.0 * eta)
+
+    # cells, x fastest; their Q2 nodes (lx + 3 ly) and Q1 vertices (lx + 2 ly)
+    ex = np.tile(np.arange(N), N)
+    ey = np.repeat(np.arange(N), N)
+    E = N * N
+    q2 = np.zeros((E, 9), dtype=np.int64)
+    for ly in range(3):
+        for lx in range(3):
+            q2[:, lx + 3 * ly] = (2 * ex + lx) + m2 * (2 * ey + ly)
+    q1 = np.zeros((E, 4), dtype=np.int64)
+    for ly in range(2):
+        for lx in range(2):
+            q1[:, lx + 2 * ly] = n2 + (ex + lx) + m1 * (ey + ly)
+
+    # B0 at the quadrature points of every cell, scaled to max |B0| = 1
+    xq = (ex[:, None] + (xi[None, :] + 1.0) / 2.0) * h
+    yq = (ey[:, None] + (et[None, :] + 1.0) / 2.0) * h
+    bx, by = frozen_field(coef, xq, yq)
+    scale = np.sqrt(bx * bx + by * by).max()
+    bx /= scale
+    by /= scale
+    curl1 = np.stack([-grad1[:, :, 1], grad1[:, :, 0]], axis=-1)  # [q, l1, a]
+    cross2 = np.stack([phi2[None] * by[:, :, None], -phi2[None] * bx[:, :, None]], axis=-1)  # [E, q, l2, c]
+    Y = np.einsum("q,qla,eqmc->elamc", wq, curl1, cross2) * jac  # [E, l1, a, l2, c]
+
+    # every (row, column, block) contribution, grouped by node pair
+    rows, cols, blks = [], [], []
+    for la in range(9):
+        for lc in range(9):
+            blk = np.zeros((b, b))
+            for a in range(2):
+                blk[a, a] = nu * K2[la, lc]
+                blk[a, 2] = G2[la, a, lc]
+                blk[2, a] = -G2[lc, a, la]
+            blk[2, 2] = tau_p * K2[la, lc]
+            rows.append(q2[:, la]); cols.append(q2[:, lc]); blks.append(np.broadcast_to(blk, (E, b, b)))
+    for la in range(4):
+        for lc in range(4):
+            blk = np.zeros((b, b))
+            for a in range(2):
+                blk[a, a] = eta * K1[la, lc]
+                blk[a, 2] = G1[la, a, lc]
+                blk[2, a] = -G1[lc, a, la]
+            blk[2, 2] = tau_s * K1[la, lc]
+            rows.append(q1[:, la]); cols.append(q1[:, lc]); blks.append(np.broadcast_to(blk, (E, b, b)))
+    for l1 in range(4):
+        for l2 in range(9):
+            yb = np.zeros((E, b, b))
+            yb[:, :2, :2] = Y[:, l1, :, l2, :]
+            rows.append(q1[:, l1]); cols.append(q2[:, l2]); blks.append(yb)
+            rows.append(q2[:, l2]); cols.append(q1[:, l1]); blks.append(-np.transpose(yb, (0, 2, 1)))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    blks = np.concatenate(blks)
+    key = rows * n + cols
+    ukey, where = np.unique(key, return_inverse=True)
+    vals = np.zeros((ukey.shape[0], b, b))
+    np.add.at(vals, where, blks)
+    r_of = (ukey // n).astype(np.int64)
+    col_idx = (ukey % n).astype(np.int32)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(r_of, minlength=n))
+
+    # Dirichlet rows and columns -> identity (pattern kept)
+    cons = np.zeros((n, b), dtype=bool)
+    X2, Y2 = np.arange(n2) % m2, np.arange(n2) // m2
+    bnd2 = (X2 == 0) | (X2 == m2 - 1) | (Y2 == 0) | (Y2 == m2 - 1)
+    X1, Y1 = np.arange(n1) % m1, np.arange(n1) // m1
+    bnd1 = (X1 == 0) | (X1 == m1 - 1) | (Y1 == 0) | (Y1 == m1 - 1)
+    cons[:n2][bnd2, 0:2] = True
+    cons[n2:][bnd1, :] = True
+    cons[0, 2] = True
+    vals *= (~cons[r_of])[:, :, None]
+    vals *= (~cons[col_idx])[:, None, :]
+    diag = np.nonzero(r_of == col_idx)[0]
+    ii, rr = np.nonzero(cons)
+    vals[diag[ii], rr, rr] = 1.0
+    rhs = uniform_pm1(seed, rhs_start, n * b)
+    return BlockSystem(f"mhd2d_q2q1_{N}_s{seed}", n, b, row_ptr.astype(np.int32), col_idx, vals, rhs,
+                       [0, 0, 0],
+                       dict(kind="mhd2d_q2q1", N=N, seed=seed, nu=nu, eta=eta, tau_p=tau_p, tau_psi=tau_s, h=h,
+                            n_q2=n2, n_q1=n1),
+                       node_field_off=[0, n2, n])
 
 
 def mhd2d_cells(N: int = 256, seed: int = 1) -> BlockSystem:
