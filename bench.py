@@ -74,6 +74,12 @@ WORKLOADS = {
              "and field and the prolongator smoothing per aggregate and field; FP32 V(1,1) (FP32 coarsest LU) "
              "inside FP64 FGMRES(30) to 1e-8; variants: the plain hierarchy (omega 0.5, tentative P) in FP64 and "
              "FP32"),
+    "mhd2d_q2q1_128": dict(
+        make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d_q2q1(128, seed),
+        levels=4, max_coarse=0, restart=30, prec=64, omega=0.6, cpu_sample_iters=5,
+        desc="2D coupled system on mixed elements: (u,v,p) on 66,049 Q2 nodes, (Bx,By,psi) on 16,641 Q1 vertices "
+             "(128x128 cells, 248,070 unknowns), 3 dofs/node, separate aggregation per field block, FP64 V(1,1) "
+             "BGS omega=0.6 with the node fields as field blocks, 4 levels, FGMRES(30) to 1e-8"),
     "stokes3d_64": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes3d(64, seed),
         levels=10, max_coarse=2500, restart=50, prec=32, coarse_prec=32, cpu_sample_iters=5,
@@ -272,7 +278,7 @@ def oracle_full_solve(sys_, wl):
 
     t0 = time.perf_counter()
     h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl),
-                                     mlp_levels=oracle_mlp_levels(wl))
+                                     mlp_levels=oracle_mlp_levels(wl), omega=wl.get("omega", 0.5))
     t1 = time.perf_counter()
     _, it, rr, conv = h.fgmres(sys_.rhs, tol=TOL, restart=wl["restart"], max_iter=wl.get("max_iter", MAX_ITER))
     t2 = time.perf_counter()
@@ -285,7 +291,7 @@ def oracle_sample(sys_, wl, iters):
 
     t0 = time.perf_counter()
     h = oracle.Hierarchy.from_system(sys_, max_levels=wl["levels"], max_coarse=wl["max_coarse"], mlp=oracle_mlp(wl),
-                                     mlp_levels=oracle_mlp_levels(wl))
+                                     mlp_levels=oracle_mlp_levels(wl), omega=wl.get("omega", 0.5))
     t1 = time.perf_counter()
     _, it, _, _ = h.fgmres(sys_.rhs, tol=1e-300, restart=wl["restart"], max_iter=iters)
     t2 = time.perf_counter()
@@ -375,7 +381,9 @@ def run_ours(args):
     main_prec = wl["prec"]
     other_prec = 32 if main_prec == 64 else 64
     coarse_prec = (args.coarse_prec or wl.get("coarse_prec", 64)) if main_prec == 32 else 64
+    node_fields = getattr(s, "node_field_off", None)
     params64 = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=main_prec,
+                                       omega=wl.get("omega", 0.5),
                                        mlp=weights, mlp_levels=mlp_levels, autotune=args.autotune,
                                        coarse_prec=coarse_prec, use_pdl=args.pdl,
                                        tail_dofs=args.tail_dofs if args.tail_dofs is not None else wl.get("tail_dofs", 0),
@@ -385,6 +393,8 @@ def run_ours(args):
         if batched:
             return bamg.amg_setup_batched(bt.sys_node_off, rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params,
                                           stream)
+        if node_fields is not None:
+            return bamg.amg_setup_fields(node_fields, rp, ci, va, s.n_nodes, s.nnzb, s.b, params, stream)
         return bamg.amg_setup(rp, ci, va, s.n_nodes, s.nnzb, s.b, s.field_of_dof, params, stream)
 
     solved = [0]  # converged systems of the last step
@@ -477,7 +487,7 @@ def run_ours(args):
 
     # --- the other cycle precision (FP32 cycle inside FP64 FGMRES, or FP64 cycle) --
     params_o = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=other_prec,
-                                       mlp=weights, mlp_levels=mlp_levels)
+                                       mlp=weights, mlp_levels=mlp_levels, omega=wl.get("omega", 0.5))
     k_o = max(1, min(args.steps, 5))
     variant = None
     if not args.no_variants:
@@ -572,7 +582,39 @@ def run_ours(args):
 
     # --- end to end through the host-buffer entry point ---------------------------
     e2e = None
-    if not args.no_e2e and batched:
+    if not args.no_e2e and node_fields is not None:
+        # through the public API with host buffers: pinned H2D of A and b,
+        # amg_setup_fields and fgmres_solve, D2H of x
+        hostbufs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                    for a in (s.row_ptr, s.col_idx, s.vals.reshape(-1), s.rhs)]
+        xh = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory()
+        k_e = max(1, min(args.steps, 3))
+        tot = 0.0
+        nsol = 0
+        for _ in range(k_e):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            drp, dci, dva, db = [t.to(dev, non_blocking=True) for t in hostbufs]
+            dx = torch.zeros_like(db)
+            hh = bamg.amg_setup_fields(node_fields, drp, dci, dva, s.n_nodes, s.nnzb, s.b, params64, stream)
+            st_e, _, _ = bamg.fgmres_solve(hh, db, dx, TOL, restart, MAX_ITER, stream)
+            bamg.amg_destroy(hh)
+            xh.copy_(dx, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            nsol += 1 if st_e == 0 else 0
+            del drp, dci, dva, db, dx
+        h2d = sum(t.numel() * t.element_size() for t in hostbufs)
+        if pg:
+            tot, nsol = reduce_timing(pg, tot, nsol, dev)
+        e2e = {"value": nsol / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(xh.numel() * 8),
+               "api": "amg_setup_fields + fgmres_solve on device copies of pinned host buffers"}
+    elif not args.no_e2e and batched:
         # through the public API with host buffers: pinned H2D of A and b,
         # batched setup and solve, D2H of x
         hostbufs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -688,13 +730,16 @@ def run_ours(args):
                 "solves_per_step": solves_per_step,
                 "vcycle_ms": statistics.median(vt), "setup_ms": statistics.median(st_times),
                 "levels": [lv["n"] for lv in stats["levels"]],
+                "field_nodes": ([lv.get("field_nodes") for lv in stats["levels"]]
+                                if stats.get("node_fields", 1) > 1 else None),
                 "colours": [lv["colours"] for lv in stats["levels"]],
                 "mappings": {"smoother": [lv.get("smoother_mapping") for lv in stats["levels"][:-1]],
                              "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
                              "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]],
                              "field_major": [lv.get("field_major") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
-                "cycle_prec": main_prec, "coarse_prec": coarse_prec, "use_pdl": args.pdl,
+                "cycle_prec": main_prec, "coarse_prec": coarse_prec,
+                "use_pdl": 0 if stats.get("node_fields", 1) > 1 else args.pdl,
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
                          "cluster": stats.get("tail_cluster")}, "variant": variant,
                 "plain": plain,

@@ -355,6 +355,8 @@ class Hierarchy:
 
     @classmethod
     def from_system(cls, sys, **kw):
+        if getattr(sys, "node_field_off", None) is not None:
+            kw.setdefault("node_field_off", sys.node_field_off)
         return cls(sys.row_ptr, sys.col_idx, sys.vals, sys.b, sys.field_of_dof, **kw)
 
     def __del__(self):

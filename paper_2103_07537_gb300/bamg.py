@@ -1,4 +1,4 @@
-"""Python binding of the bamg C ABI (include/bamg.h): argument marshalling only.
+"""Python binding of the bamg C ABI (include/bamg.h, include/bamg_fields.h): argument marshalling only.
 
 Every function here has the name of the C entry point it calls.  Device
 arguments are torch CUDA tensors (their storage is passed as a raw pointer),
@@ -27,7 +27,7 @@ EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_
            "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
            "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
            "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
-           "amg_level_p"]
+           "amg_level_p", "amg_setup_fields", "amg_level_fields"]
 
 #: network sizes (include/bamg.h)
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -116,6 +116,9 @@ def load(build_if_missing: bool = True):
         lib.amg_select.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _ip, _ip, _vp]
         lib.amg_level_omega.argtypes = [_vp, C.c_int, _vp, _vp]
         lib.amg_level_p.argtypes = [_vp, C.c_int, _ip, _vp, _vp, _vp]
+        lib.amg_setup_fields.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _ip,
+                                         C.POINTER(AmgParams), _vp, C.POINTER(_vp)]
+        lib.amg_level_fields.argtypes = [_vp, C.c_int, _ip, _ip]
         _lib = lib
         return lib
 
@@ -317,6 +320,30 @@ def amg_setup_batched(sys_node_off, row_ptr, col_idx, vals, n_nodes: int, nnzb: 
     return h.value
 
 
+def amg_setup_fields(field_node_off, row_ptr, col_idx, vals, n_nodes: int, nnzb: int, b: int, params=None,
+                     stream=None) -> int:
+    """Hierarchy of a system whose fields live on disjoint node sets
+    (include/bamg_fields.h); field g owns nodes field_node_off[g]..[g+1]-1."""
+    off = np.ascontiguousarray(field_node_off, dtype=np.int32)
+    h = _vp()
+    st = load().amg_setup_fields(_ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(n_nodes), int(nnzb), int(b),
+                                 int(off.shape[0] - 1), off.ctypes.data_as(_ip),
+                                 C.byref(params) if params is not None else None, _stream(stream), C.byref(h))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_setup_fields")
+    return h.value
+
+
+def amg_level_fields(handle: int, level: int, n_fields: int):
+    """(node_off[n_fields+1], colour_off[n_fields+1]) of one level."""
+    no = np.zeros(n_fields + 1, np.int32)
+    co = np.zeros(n_fields + 1, np.int32)
+    st = load().amg_level_fields(handle, level, no.ctypes.data_as(_ip), co.ctypes.data_as(_ip))
+    if st < 0:
+        raise BamgError(st, "amg_level_fields")
+    return no, co
+
+
 def fgmres_solve_batched(handle: int, b, x, tol=1e-8, restart=30, max_iter=10000, stream=None):
     """Returns (status, iterations[nsys], true relative residuals[nsys])."""
     ns = amg_num_systems(handle)
@@ -475,6 +502,25 @@ class Solver:
 
     def set_omega(self, l: int, omega_s, stream=None):
         amg_set_omega(self.handle, l, omega_s, stream)
+
+
+class FieldSolver(Solver):
+    """Owns one hierarchy of a system whose fields live on disjoint node sets
+    (field g owns nodes field_node_off[g]..[g+1]-1, every dof of a node in its
+    node's field): separate aggregation per field block."""
+
+    def __init__(self, field_node_off, row_ptr, col_idx, vals, b: int, stream=None, **params):
+        self.b = int(b)
+        self.F = 1
+        self.n = int(row_ptr.shape[0]) - 1
+        self.n_fields = len(field_node_off) - 1
+        self.row_ptr, self.col_idx, self.vals = row_ptr, col_idx, vals
+        self.params = amg_default_params(**params)
+        self.handle = amg_setup_fields(field_node_off, row_ptr, col_idx, vals, self.n, int(col_idx.shape[0]),
+                                       self.b, self.params, stream)
+
+    def fields(self, l: int):
+        return amg_level_fields(self.handle, l, self.n_fields)
 
 
 class BatchSolver(Solver):

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libbamg.so")
-SOURCES = ["k_solve.cu", "k_setup.cu", "k_krylov.cu", "k_batched.cu", "k_transfer.cu", "k_learned.cu", "capi.cu",
-           "noalloc.cu"]
+SOURCES = ["k_solve.cu", "k_setup.cu", "k_krylov.cu", "k_batched.cu", "k_transfer.cu", "k_learned.cu", "k_fields.cu",
+           "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -31,7 +31,7 @@ def nvcc() -> str:
 
 
 def _headers():
-    hs = [os.path.join(INCLUDE, "bamg.h")]
+    hs = [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     hs += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return hs
 

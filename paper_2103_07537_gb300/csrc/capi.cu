@@ -16,7 +16,9 @@
 #include <string>
 #include <vector>
 
+#include "bamg_fields.h"
 #include "common.cuh"
+#include "fields.cuh"
 
 using namespace bamg;
 
@@ -128,6 +130,11 @@ struct Level {
     // node range of every system of a batch on this level (host and device)
     std::vector<int> sys_off;
     int* sys_off_d = nullptr;
+    // fields on disjoint node sets: node range (host, device) and colour range
+    // of every field, and the field of every node
+    std::vector<int> fo, fcol;
+    int* fo_d = nullptr;
+    int* node_field = nullptr;
     // per-colour counts for the algorithmic byte / flop model (profiling only)
     std::vector<long> colour_nnz, colour_nnz_lower;
     // per-node smoother damping [n][F] (nullptr: the scalar omega) and P smoothing weights [n_agg][F]
@@ -176,6 +183,7 @@ struct bamg_ctx {
     int b = 0, F = 1, fb = 0, nlev = 0;
     int outer_spmv_tpr = 0;  // row mapping of the FP64 outer SpMV
     int nsys = 1;  // independent systems solved together (block-diagonal operator)
+    int nf = 1;    // fields on disjoint node sets (1: co-located fields only)
     // coarsest level of a batch: one dense inverse per system
     long* inv_off_d = nullptr;
     int* row_sys_d = nullptr;
@@ -668,6 +676,25 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
     return BAMG_OK;
 }
 
+// Fields on disjoint node sets: the graph of the diagonal field blocks of a
+// level (the stored blocks between two nodes of one field), on which every
+// field is aggregated and coloured separately (Sec. 4.3.1).  The graph is the
+// disjoint union of the fields' graphs in contiguous node ranges, so the
+// ascending-order rules of aggregation and colouring treat each field as if
+// it were alone, and aggregate ids (ranks of the roots) run field by field.
+static int level_field_graph(bamg_ctx* h, const Level& L, int** rp_f, int** ci_f, cudaStream_t s) {
+    int *count = nullptr, *tmp = nullptr;
+    const long sb = scan_tmp_bytes(L.n) + 64;
+    TRY(h->alloc(rp_f, (size_t)L.n + 1));
+    TRY(h->alloc(ci_f, (size_t)L.nnzb));
+    TRY(h->alloc(&count, (size_t)L.n + 1));
+    TRY(h->alloc(&tmp, (size_t)sb / sizeof(int) + 1));
+    TRY(field_pattern(L.n, L.rp, L.ci, L.node_field, count, tmp, sb, *rp_f, *ci_f, s));
+    h->release(count);
+    h->release(tmp);
+    return BAMG_OK;
+}
+
 static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const double* vals, int n,
                       int nnzb, cudaStream_t s) {
     auto tp = Clock::now();
@@ -706,6 +733,10 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(node_sys);
     }
 
+    if (h->nf > 1) {  // node ranges of the fields on level 0
+        TRY(h->alloc(&L0.fo_d, L0.fo.size()));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(L0.fo_d, L0.fo.data(), sizeof(int) * L0.fo.size(), cudaMemcpyHostToDevice, s));
+    }
     if (h->p.mlp) {  // FP16 copy of the network parameters
         float* p32 = nullptr;
         TRY(h->alloc(&p32, BAMG_MLP_NPARAMS));
@@ -724,6 +755,10 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(check_dev(h, s));
         h->t_phase[0] += ms_since(tp);
         tp = Clock::now();
+        if (h->nf > 1) {
+            TRY(h->alloc(&L.node_field, (size_t)L.n));
+            TRY(launch_fill_sys(h->nf, L.fo_d, 1, L.node_field, s));
+        }
         const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
         if (!coarsen) break;
         // aggregation (clone for every field: one aggregate map per level)
@@ -740,9 +775,26 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         w.host_flag = h->h_pin;
         BAMG_CUDA_TRY(cudaMemsetAsync(d_count, 0, 4 * sizeof(int), s));
         int rounds = 0;
-        const int nc = aggregate_nodes(L.n, L.rp, L.ci, L.agg, w, d_count, scan_tmp, stb, s, &rounds);
+        int *g_rp = L.rp, *g_ci = L.ci;
+        if (h->nf > 1) TRY(level_field_graph(h, L, &g_rp, &g_ci, s));
+        const int nc = aggregate_nodes(L.n, g_rp, g_ci, L.agg, w, d_count, scan_tmp, stb, s, &rounds);
         if (nc < 0) return nc;
         L.agg_rounds = rounds;
+        if (h->nf > 1) {
+            h->release(g_rp);
+            h->release(g_ci);
+            // node ranges of the fields on the coarse level: the aggregates of
+            // a field are numbered by the ranks of its roots, a contiguous range
+            Level& Cf = h->lev[l + 1];
+            TRY(h->alloc(&Cf.fo_d, (size_t)h->nf + 1));
+            TRY(launch_coarse_offsets(h->nf, L.fo_d, w.rootid, Cf.fo_d, s));
+            Cf.fo.assign((size_t)h->nf + 1, 0);
+            BAMG_CUDA_TRY(cudaMemcpyAsync(Cf.fo.data(), Cf.fo_d, sizeof(int) * (h->nf + 1), cudaMemcpyDeviceToHost, s));
+            BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int g = 0; g < h->nf; ++g)
+                if (Cf.fo[g + 1] <= Cf.fo[g]) return BAMG_ECUDA;  // every field keeps at least one node
+            if (Cf.fo[0] != 0 || Cf.fo[h->nf] != nc) return BAMG_ECUDA;
+        }
         // node ranges of the systems on the coarse level: the aggregates of a
         // system are numbered by the ranks of its roots, a contiguous range
         Level& Cn = h->lev[l + 1];
@@ -825,10 +877,34 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&cflag, 4));
         TRY(h->alloc(&queue, 2 * (size_t)L.n));
         int rounds = 0;
-        TRY(colour_nodes(L.n, L.rp, L.ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds, queue));
+        int *g_rp = L.rp, *g_ci = L.ci;
+        if (h->nf > 1) TRY(level_field_graph(h, L, &g_rp, &g_ci, s));
+        TRY(colour_nodes(L.n, g_rp, g_ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds, queue));
         L.colour_rounds = rounds;
         h->release(cflag);
         h->release(queue);
+        if (h->nf > 1) {
+            // first-fit colours per field, shifted so that field g's colours
+            // follow those of fields 0..g-1
+            h->release(g_rp);
+            h->release(g_ci);
+            int* cm = nullptr;
+            TRY(h->alloc(&cm, (size_t)h->nf + 1));
+            TRY(field_colour_counts(L.n, h->nf, L.colour, L.node_field, cm, s));
+            std::vector<int> cnt((size_t)h->nf, 0);
+            BAMG_CUDA_TRY(cudaMemcpyAsync(cnt.data(), cm, sizeof(int) * h->nf, cudaMemcpyDeviceToHost, s));
+            BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            L.fcol.assign((size_t)h->nf + 1, 0);
+            for (int g = 0; g < h->nf; ++g) {
+                if (cnt[g] < 1) return BAMG_ECUDA;
+                L.fcol[g + 1] = L.fcol[g] + cnt[g];
+            }
+            BAMG_CUDA_TRY(cudaMemcpyAsync(cm, L.fcol.data(), sizeof(int) * h->nf, cudaMemcpyHostToDevice, s));
+            TRY(field_colour_shift(L.n, cm, L.node_field, L.colour, s));
+            BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            h->release(cm);
+            L.n_colours = L.fcol[h->nf];
+        }
         TRY(h->alloc(&L.colour_ptr_d, (size_t)L.n_colours + 1));
         TRY(h->alloc(&L.colour_nodes, (size_t)L.n));
         int* tmp = nullptr;
@@ -841,7 +917,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(tmp);
         if (L.colour_ptr[L.n_colours] != L.n) return BAMG_ECUDA;
         TRY(h->alloc(&L.lowk, (size_t)L.nnzb));
-        TRY(launch_lower_flags(L.n, L.rp, L.ci, L.colour, L.lowk, s));
+        if (h->nf > 1) TRY(field_lower_flags(L.n, L.rp, L.ci, L.colour, L.node_field, L.lowk, s));
+        else TRY(launch_lower_flags(L.n, L.rp, L.ci, L.colour, L.lowk, s));
         h->t_phase[3] += ms_since(tp);
         tp = Clock::now();
         if (!L.dinv64) {  // (already there when P was smoothed)
@@ -993,14 +1070,14 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         if (h->p.cycle_prec == 64) TRY(autotune_levels<double>(h, s));
         else TRY(autotune_levels<float>(h, s));
     }
-    if (h->nsys == 1) TRY(setup_tail(h, s));
+    if (h->nsys == 1 && h->nf == 1) TRY(setup_tail(h, s));
     h->t_phase[6] += ms_since(tp);
     return BAMG_OK;
 }
 
 static int setup_common(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb, int b,
                         const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out, int nsys,
-                        const int* sys_node_off) {
+                        const int* sys_node_off, int nf = 1, const int* field_node_off = nullptr) {
     if (!out) return BAMG_EINVAL;
     *out = nullptr;
     if (!row_ptr || !col_idx || !vals || !field_of_dof || n_nodes < 1 || nnzb < n_nodes || b < 1 || b > kMaxB)
@@ -1037,6 +1114,22 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     for (int d = 0; d < b; ++d)
         if (field_of_dof[d] != d / fb) return BAMG_EINVAL;
     if (!supported_block(b, fb)) return BAMG_EUNSUPPORTED;
+    // fields on disjoint node sets: contiguous non-empty node ranges, every dof
+    // of a node in the node's field, one system, the plain method
+    if (nf < 1 || nf > BAMG_MAX_NODE_FIELDS) return BAMG_EINVAL;
+    if (nf > 1) {
+        if (!field_node_off || field_node_off[0] != 0 || field_node_off[nf] != n_nodes || F != 1 || nsys != 1 ||
+            prm.smooth_p || prm.mlp || prm.omega_s_arr || prm.omega_p_arr)
+            return BAMG_EINVAL;
+        for (int g = 0; g < nf; ++g)
+            if (field_node_off[g + 1] <= field_node_off[g]) return BAMG_EINVAL;
+        // a field step ends with plain copies of the other fields' nodes; the
+        // cycle's kernels are then launched without programmatic dependence
+        // and without the single-launch tail
+        prm.use_pdl = 0;
+        prm.tail_dofs = 0;
+        prm.tail_grid = 0;
+    }
     bamg_ctx* h = new (std::nothrow) bamg_ctx();
     if (!h) return BAMG_ECUDA;
     h->b = b;
@@ -1046,6 +1139,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     h->nsys = nsys;
     if (nsys > 1) h->lev[0].sys_off.assign(sys_node_off, sys_node_off + nsys + 1);
     else h->lev[0].sys_off = {0, n_nodes};
+    h->nf = nf;
+    if (nf > 1) h->lev[0].fo.assign(field_node_off, field_node_off + nf + 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->stream = s;
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1073,6 +1168,28 @@ extern "C" int amg_setup_batched(int nsys, const int* sys_node_off, const int* r
     return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, field_of_dof, p, stream, out, nsys, sys_node_off);
 }
 
+extern "C" int amg_setup_fields(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
+                                int b, int n_fields, const int* field_node_off, const amg_params* p, void* stream,
+                                bamg_t* out) {
+    if (!out) return BAMG_EINVAL;
+    *out = nullptr;
+    if (b < 1 || b > kMaxB || n_fields < 1 || !field_node_off) return BAMG_EINVAL;
+    int zeros[kMaxB] = {};
+    return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, zeros, p, stream, out, 1, nullptr, n_fields,
+                        field_node_off);
+}
+
+extern "C" int amg_level_fields(bamg_t h, int level, int* node_off, int* colour_off) {
+    if (!h || level < 0 || level >= h->nlev) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    const bool smoother = level + 1 < h->nlev;
+    for (int g = 0; g <= h->nf; ++g) {
+        if (node_off) node_off[g] = h->nf > 1 ? L.fo[g] : (g == 0 ? 0 : L.n);
+        if (colour_off) colour_off[g] = !smoother ? 0 : h->nf > 1 ? L.fcol[g] : (g == 0 ? 0 : L.n_colours);
+    }
+    return h->nf;
+}
+
 extern "C" int amg_destroy(bamg_t h) {
     if (!h) return BAMG_OK;
     cudaStreamSynchronize(h->stream);
@@ -1092,15 +1209,43 @@ static void record(bamg_ctx* h, const TailPhase& ph, double bytes, double flops)
     h->rec_flops += flops;
 }
 
+// the field steps of one sweep of Algorithm 1: fields on node sets, else the
+// dof fields of a node
+static int field_steps(const bamg_ctx* h) { return h->nf > 1 ? h->nf : h->F; }
+
+// Fields on node sets: a field step writes only the nodes of its own field.
+// The other fields' nodes of x_out take x_in (plus the coarse correction P u_c
+// in the first post-smoothing step), or zero from the zero initial guess.
+template <typename T>
+static int other_fields(bamg_ctx* h, const Level& L, int f, const T* x_in, T* x_out, const T* uc, cudaStream_t s) {
+    const int b = h->b;
+    for (int g = 0; g < h->nf; ++g) {
+        if (g == f) continue;
+        const int n_g = L.fo[g + 1] - L.fo[g];
+        const size_t e0 = (size_t)L.fo[g] * b, ne = (size_t)n_g * b;
+        if (!x_in) {
+            BAMG_CUDA_TRY(cudaMemsetAsync(x_out + e0, 0, sizeof(T) * ne, s));
+            continue;
+        }
+        BAMG_CUDA_TRY(cudaMemcpyAsync(x_out + e0, x_in + e0, sizeof(T) * ne, cudaMemcpyDeviceToDevice, s));
+        if (uc) TRY(launch_prolong<T>(b, n_g, L.agg + L.fo[g], uc, x_out + e0, s));
+    }
+    return BAMG_OK;
+}
+
 // one field step of Algorithm 1 on level l: x_out = x_in updated in field f
 // uc != nullptr: the coarse correction P uc is added to x_in on the fly (x_in is
 // then the state before prolongation and x_out receives the corrected values)
+// With fields on node sets, field f is the node range fo[f].. and its colours
+// are fcol[f]..fcol[f+1]-1; each node is one b x b sub-solve block.
 template <typename T>
 static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x_out, const T* uc,
                     cudaStream_t s) {
     const Level& L = h->lev[l];
     const bool have_counts = (int)L.colour_nnz.size() == L.n_colours;
-    for (int c = 0; c < L.n_colours; ++c) {
+    const bool nodef = h->nf > 1;
+    const int c_lo = nodef ? L.fcol[f] : 0, c_hi = nodef ? L.fcol[f + 1] : L.n_colours;
+    for (int c = c_lo; c < c_hi; ++c) {
         BgsArgs a;
         a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
         a.nodes = L.colour_nodes + L.colour_ptr[c];
@@ -1118,7 +1263,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         a.xt = L.xt;
         a.uc = uc;
         a.agg = uc ? L.agg : nullptr;
-        a.field = f;
+        a.field = nodef ? 0 : f;
         a.F = h->F;
         a.omega = h->p.omega;
         a.omega_node = level_omega<T>(L);
@@ -1143,6 +1288,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
            L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr - 1)
                      : launch_bgs_colour<T>(h->b, h->fb, a, s));
     }
+    if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
     return BAMG_OK;
 }
 
@@ -1222,10 +1368,11 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     T* xa = static_cast<T*>(L.xa);
     T* xb = static_cast<T*>(L.xb);
     T* cur = nullptr;  // nullptr = the zero initial guess
-    const int S_pre = h->p.n_pre * h->F;
+    const int NS = field_steps(h);
+    const int S_pre = h->p.n_pre * NS;
     for (int t = 0; t < S_pre; ++t) {
         T* dst = (cur == xa) ? xb : xa;
-        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, nullptr, s));
+        TRY(bgs_step<T>(h, l, t % NS, rhs, cur, dst, nullptr, s));
         cur = dst;
     }
     if (!cur) {
@@ -1257,14 +1404,14 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
         PL(BAMG_K_PROLONG, tb + (L.n + 1) * 4.0 + 2.0 * nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
            prolong_explicit<T>(h, L, static_cast<const T*>(C.uc), cur, s));
-        const int S_post = h->p.n_post * h->F;
+        const int S_post = h->p.n_post * NS;
         if (S_post == 0) {
             BAMG_CUDA_TRY(cudaMemcpyAsync(out, cur, sizeof(T) * (size_t)L.n * b, cudaMemcpyDeviceToDevice, s));
             return BAMG_OK;
         }
         for (int t = 0; t < S_post; ++t) {
             T* dst = (t == S_post - 1) ? out : ((cur == xa) ? xb : xa);
-            TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, nullptr, s));
+            TRY(bgs_step<T>(h, l, t % NS, rhs, cur, dst, nullptr, s));
             cur = dst;
         }
         return BAMG_OK;
@@ -1301,7 +1448,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
            launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     }
     TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
-    const int S_post = h->p.n_post * h->F;
+    const int S_post = h->p.n_post * NS;
     if (S_post == 0) {
         const double pb = L.n * 4.0 + 2.0 * nb * es + ncb * es;
         if (h->rec) {
@@ -1321,7 +1468,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     // the first post-smoothing step applies u <- u + P u_c on the fly
     for (int t = 0; t < S_post; ++t) {
         T* dst = (t == S_post - 1) ? out : ((cur == xa) ? xb : xa);
-        TRY(bgs_step<T>(h, l, t % h->F, rhs, cur, dst, t == 0 ? static_cast<const T*>(C.uc) : nullptr, s));
+        TRY(bgs_step<T>(h, l, t % NS, rhs, cur, dst, t == 0 ? static_cast<const T*>(C.uc) : nullptr, s));
         cur = dst;
     }
     return BAMG_OK;
@@ -1858,7 +2005,7 @@ extern "C" int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, d
 extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
-                    ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
+                    ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
                     ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
@@ -1888,7 +2035,13 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
              std::to_string(L.tune_us[5]) +
              "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
-             ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0") + "}";
+             ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0");
+        if (h->nf > 1) {
+            o += ",\"field_nodes\":[";
+            for (int g = 0; g < h->nf; ++g) o += (g ? "," : "") + std::to_string(L.fo[g + 1] - L.fo[g]);
+            o += "]";
+        }
+        o += "}";
     }
     o += "]}";
     const int len = (int)o.size();
@@ -1913,10 +2066,15 @@ extern "C" int amg_profile(bamg_t h, int enable) {
             BAMG_CUDA_TRY(cudaMemcpy(col.data(), L.colour, sizeof(int) * col.size(), cudaMemcpyDeviceToHost));
             L.colour_nnz.assign((size_t)L.n_colours, 0);
             L.colour_nnz_lower.assign((size_t)L.n_colours, 0);
+            // (fields on node sets: only blocks of the row's own field are read through x~)
+            std::vector<int> fld((size_t)L.n, 0);
+            for (int g = 0; h->nf > 1 && g < h->nf; ++g)
+                for (int i = L.fo[g]; i < L.fo[g + 1]; ++i) fld[(size_t)i] = g;
             for (int i = 0; i < L.n; ++i) {
                 L.colour_nnz[(size_t)col[i]] += rp[i + 1] - rp[i];
                 for (int k = rp[i]; k < rp[i + 1]; ++k)
-                    if (ci[k] != i && col[ci[k]] < col[i]) L.colour_nnz_lower[(size_t)col[i]]++;
+                    if (ci[k] != i && col[ci[k]] < col[i] && fld[(size_t)ci[k]] == fld[(size_t)i])
+                        L.colour_nnz_lower[(size_t)col[i]]++;
             }
         }
     }

@@ -1,5 +1,5 @@
 """The C ABI library builds for sm_103a, loads, and exports every entry point
-that include/bamg.h declares.  CPU only: no compute call is made."""
+that include/*.h declares.  CPU only: no compute call is made."""
 import ctypes
 import os
 import re
@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "bamg.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:long\s+|unsigned\s+)*\w+[\s\*]+(\w+)\s*\(", text,
                                  flags=re.M)))
@@ -23,7 +24,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     fns = declared_functions()
     for name in ["amg_setup", "amg_apply", "fgmres_solve", "amg_destroy", "amg_stats", "amg_strerror",
-                 "bsr_spmv", "amg_solve_host"]:
+                 "bsr_spmv", "amg_solve_host", "amg_setup_fields", "amg_level_fields"]:
         assert name in fns
 
 
@@ -50,6 +51,17 @@ def test_host_side_validation_without_gpu():
     assert lib.amg_apply(None, None, None, None) == bamg.BAMG_EINVAL
     assert lib.amg_destroy(None) == bamg.BAMG_OK
     assert bamg.amg_strerror(bamg.BAMG_ESINGULAR_COARSE) == "singular coarsest operator"
+    # fields on node sets: bad ranges, parameters the mode excludes, a null handle
+    ip = ctypes.POINTER(ctypes.c_int)
+    dummy = ctypes.c_void_p(16)
+    for off, kw in (([0, 0, 10], {}), ([0, 4, 9], {}), ([1, 4, 10], {}), ([0, 6, 4, 10], {}),
+                    ([0, 4, 10], dict(smooth_p=1)), ([0] + list(range(1, 10)) + [10], {})):
+        o = np.array(off, np.int32)
+        prm = bamg.amg_default_params(**kw)
+        assert lib.amg_setup_fields(dummy, dummy, dummy, 10, 10, 3, len(off) - 1, o.ctypes.data_as(ip),
+                                    ctypes.byref(prm), None, ctypes.byref(h)) == bamg.BAMG_EINVAL
+        assert not h.value
+    assert lib.amg_level_fields(None, 0, None, None) == bamg.BAMG_EINVAL
     p = bamg.amg_default_params()
     assert (p.max_levels, p.max_coarse, p.n_pre, p.n_post, p.omega, p.cycle_prec) == (10, 2500, 1, 1, 0.5, 64)
 
