@@ -781,6 +781,15 @@ typedef struct {
     /* fields on disjoint node sets (n_node_fields > 1) */
     int* foff; /* [NF+1] nodes of field g: foff[g] <= i < foff[g+1] */
     int* coff; /* [NF+1] colours of field g: coff[g] <= c < coff[g+1] */
+    /* sub_schwarz: subdomains, one per aggregate and field */
+    int n_sd, sd_max_m;
+    int* sd_field;         /* [n_sd] field of the subdomain */
+    int* sd_ptr;           /* [n_sd+1] into sd_nodes, sd_own */
+    int* sd_nodes;         /* nodes of each subdomain, ascending */
+    unsigned char* sd_own; /* 1: the node belongs to the subdomain's aggregate */
+    size_t* sd_lu_off;     /* [n_sd+1] dense LU factors of A_I in sd_lu */
+    double* sd_lu;
+    int* sd_piv;           /* pivots of subdomain I at sd_ptr[I] * (dofs per node) */
 } olevel;
 
 struct oracle_hier {
@@ -819,6 +828,13 @@ static void level_free(olevel* L) {
     free(L->ilu_pos);
     free(L->foff);
     free(L->coff);
+    free(L->sd_field);
+    free(L->sd_ptr);
+    free(L->sd_nodes);
+    free(L->sd_own);
+    free(L->sd_lu_off);
+    free(L->sd_lu);
+    free(L->sd_piv);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -895,6 +911,8 @@ static int colour_node_fields(const oracle_hier* h, olevel* L) {
     }
     return base;
 }
+
+static int level_schwarz(oracle_hier* h, olevel* L);
 
 /* per-field inverses of the node diagonal blocks of level L */
 static int level_dinv(oracle_hier* h, olevel* L) {
@@ -1057,8 +1075,14 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     h->nlev = 1;
     int st = ORACLE_OK;
     long long used_s = 0, used_p = 0;
-    if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0) || p->mlp_levels < 0)
+    if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0) || p->mlp_levels < 0 ||
+        p->sub_schwarz < 0 || p->sub_schwarz > 2 || p->schwarz_overlap < 0 || p->schwarz_overlap > 1 ||
+        (p->sub_schwarz && p->sub_ilu))
         st = ORACLE_EINVAL;
+    if (st != ORACLE_OK) {
+        oracle_free(h);
+        return st;
+    }
     /* coarsen while n*b > max_coarse and fewer than max_levels levels */
     while (h->nlev < p->max_levels && (long)h->lev[h->nlev - 1].n * b > p->max_coarse) {
         olevel* F_ = &h->lev[h->nlev - 1];
@@ -1177,6 +1201,7 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
                 for (int i = 0; i < L->n; ++i)
                     if (L->colour[i] == c) L->ilu_pos[i] = e++;
         }
+        if (p->sub_schwarz && st == ORACLE_OK) st = level_schwarz(h, L);
         if (p->sub_ilu)
             for (int f = 0; f < h->F && st == ORACLE_OK; ++f) {
                 L->ilu[f] = (double*)malloc(sizeof(double) * (size_t)L->nnzb * h->fb * h->fb);
@@ -1292,6 +1317,151 @@ int oracle_level_omega(const oracle_hier* h, int l, double* omega_s, double* ome
 /*     c: x~_i = D_ff,i^{-1} (r_f,i - sum_{j != i} A_ff[i,j] x~_j));        */
 /*   x_f := x_f + omega x~_f.                                               */
 /* ------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------ */
+/* Additive Schwarz with overlap as Algorithm 1's sub-solve (Sec. 5: one    */
+/* additive Schwarz iteration with overlap one approximates A_ff^{-1}).     */
+/* Subdomains are the level's aggregates, one per aggregate and field (the  */
+/* aggregates of a field on disjoint node sets carry that field only),      */
+/* extended by `overlap` layers of neighbours in the graph of A_ff.  With   */
+/* R_I the restriction to the subdomain's dofs of field f and               */
+/* A_I = R_I A_ff R_I^T:                                                    */
+/*   additive:   x~_f = sum_I R_I^T A_I^{-1} R_I r_f;                       */
+/*   restricted: every node takes its value from its own aggregate's solve. */
+/* ------------------------------------------------------------------------ */
+static int level_schwarz(oracle_hier* h, olevel* L) {
+    const int b = h->b, n = L->n;
+    const int fb = h->NF > 1 ? b : h->fb;  /* dofs of one field per node */
+    const int nfs = h->NF > 1 ? 1 : h->F;  /* subdomains per aggregate */
+    const size_t bb = (size_t)b * b;
+    int *mptr = NULL, *mem = NULL;
+    int st = aggregate_members(n, L->agg, L->n_agg, &mptr, &mem);
+    if (st) return st;
+    int* nfield = (int*)calloc((size_t)n, sizeof(int));
+    int* mark = (int*)malloc(sizeof(int) * (size_t)n);
+    int* list = (int*)malloc(sizeof(int) * (size_t)(n + L->nnzb));
+    const size_t cap = (size_t)nfs * (size_t)(n + L->nnzb);
+    L->n_sd = L->n_agg * nfs;
+    L->sd_field = (int*)malloc(sizeof(int) * (size_t)L->n_sd);
+    L->sd_ptr = (int*)malloc(sizeof(int) * (size_t)(L->n_sd + 1));
+    L->sd_nodes = (int*)malloc(sizeof(int) * cap);
+    L->sd_own = (unsigned char*)malloc(cap);
+    L->sd_lu_off = (size_t*)malloc(sizeof(size_t) * (size_t)(L->n_sd + 1));
+    if (!nfield || !mark || !list || !L->sd_field || !L->sd_ptr || !L->sd_nodes || !L->sd_own || !L->sd_lu_off) {
+        st = ORACLE_ENOMEM;
+        goto done;
+    }
+    if (h->NF > 1)
+        for (int g = 0; g < h->NF; ++g)
+            for (int i = L->foff[g]; i < L->foff[g + 1]; ++i) nfield[i] = g;
+    for (int i = 0; i < n; ++i) mark[i] = -1;
+    /* node lists */
+    int e = 0;
+    size_t lu_total = 0;
+    L->sd_max_m = 0;
+    L->sd_ptr[0] = 0;
+    L->sd_lu_off[0] = 0;
+    for (int I = 0; I < L->n_agg; ++I) {
+        int cnt = 0;
+        for (int t = mptr[I]; t < mptr[I + 1]; ++t) {
+            list[cnt++] = mem[t];
+            mark[mem[t]] = I;
+        }
+        for (int layer = 0; layer < h->p.schwarz_overlap; ++layer) {
+            const int c0 = cnt;
+            for (int t = 0; t < c0; ++t) {
+                const int i = list[t];
+                for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                    const int j = L->col_idx[k];
+                    if (mark[j] == I || nfield[j] != nfield[i]) continue;
+                    mark[j] = I;
+                    list[cnt++] = j;
+                }
+            }
+        }
+        qsort(list, (size_t)cnt, sizeof(int), cmp_int);
+        for (int fs = 0; fs < nfs; ++fs) {
+            const int q = I * nfs + fs;
+            L->sd_field[q] = h->NF > 1 ? nfield[mem[mptr[I]]] : fs;
+            for (int t = 0; t < cnt; ++t) {
+                L->sd_nodes[e + t] = list[t];
+                L->sd_own[e + t] = L->agg[list[t]] == I;
+            }
+            e += cnt;
+            L->sd_ptr[q + 1] = e;
+            const size_t m = (size_t)cnt * fb;
+            lu_total += m * m;
+            L->sd_lu_off[q + 1] = lu_total;
+            if ((int)m > L->sd_max_m) L->sd_max_m = (int)m;
+        }
+    }
+    /* dense A_I and its LU */
+    L->sd_lu = (double*)calloc(lu_total > 0 ? lu_total : 1, sizeof(double));
+    L->sd_piv = (int*)malloc(sizeof(int) * (size_t)(e > 0 ? e : 1) * fb);
+    if (!L->sd_lu || !L->sd_piv) {
+        st = ORACLE_ENOMEM;
+        goto done;
+    }
+    for (int q = 0; q < L->n_sd && st == ORACLE_OK; ++q) {
+        const int s0 = L->sd_ptr[q], cnt = L->sd_ptr[q + 1] - s0, m = cnt * fb;
+        const int f0 = h->NF > 1 ? 0 : h->fstart[L->sd_field[q]];
+        double* A = L->sd_lu + L->sd_lu_off[q];
+        for (int p = 0; p < cnt; ++p) {
+            const int i = L->sd_nodes[s0 + p];
+            for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k) {
+                /* position of column j in the subdomain's ascending node list */
+                const int j = L->col_idx[k];
+                int lo = 0, hi = cnt;
+                while (lo < hi) {
+                    const int mid = (lo + hi) / 2;
+                    if (L->sd_nodes[s0 + mid] < j) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo == cnt || L->sd_nodes[s0 + lo] != j) continue;
+                const double* blk = L->vals + (size_t)k * bb;
+                for (int r = 0; r < fb; ++r)
+                    for (int c = 0; c < fb; ++c)
+                        A[(size_t)(p * fb + r) * m + (lo * fb + c)] = blk[(f0 + r) * b + (f0 + c)];
+            }
+        }
+        if (oracle_lu_factor(m, A, L->sd_piv + (size_t)s0 * fb) != ORACLE_OK) st = ORACLE_ESINGULAR_BLOCK;
+    }
+done:
+    free(mptr);
+    free(mem);
+    free(nfield);
+    free(mark);
+    free(list);
+    return st;
+}
+
+/* x~ += the Schwarz sub-solve of r for field f; r and x~ hold the field's dofs
+ * of nodes base.. with stride fb */
+static int schwarz_apply(const oracle_hier* h, const olevel* L, int f, int base, int fb, const double* r,
+                         double* xt) {
+    const int m_max = L->sd_max_m > 0 ? L->sd_max_m : 1;
+    double* rl = (double*)malloc(sizeof(double) * (size_t)m_max);
+    double* y = (double*)malloc(sizeof(double) * (size_t)m_max);
+    if (!rl || !y) {
+        free(rl);
+        free(y);
+        return ORACLE_ENOMEM;
+    }
+    for (int q = 0; q < L->n_sd; ++q) {
+        if (L->sd_field[q] != f) continue;
+        const int s0 = L->sd_ptr[q], cnt = L->sd_ptr[q + 1] - s0, m = cnt * fb;
+        for (int p = 0; p < cnt; ++p)
+            for (int c = 0; c < fb; ++c) rl[p * fb + c] = r[(size_t)(L->sd_nodes[s0 + p] - base) * fb + c];
+        oracle_lu_solve(m, L->sd_lu + L->sd_lu_off[q], L->sd_piv + (size_t)s0 * fb, rl, y);
+        for (int p = 0; p < cnt; ++p) {
+            if (h->p.sub_schwarz == 2 && !L->sd_own[s0 + p]) continue;
+            for (int c = 0; c < fb; ++c) xt[(size_t)(L->sd_nodes[s0 + p] - base) * fb + c] += y[p * fb + c];
+        }
+    }
+    free(rl);
+    free(y);
+    return ORACLE_OK;
+}
+
 /* Algorithm 1 with the field blocks on disjoint node sets: field g owns the */
 /* nodes o_g <= i < o_{g+1} with all their dofs, A_gg is the block matrix    */
 /* between those nodes.  One sweep visits the fields in order; for field g: */
@@ -1319,7 +1489,11 @@ static int bgs_node_fields(oracle_hier* h, int l, double* x, const double* rhs, 
                     rf[(size_t)(i - o0) * b + r] = acc;
                 }
             for (size_t e = 0; e < (size_t)(o1 - o0) * b; ++e) xt[e] = 0.0;
-            for (int col = L->coff[g]; col < L->coff[g + 1]; ++col) {
+            if (h->p.sub_schwarz) {
+                int st = schwarz_apply(h, L, g, o0, b, rf, xt);
+                if (st) return st;
+            }
+            for (int col = L->coff[g]; col < (h->p.sub_schwarz ? L->coff[g] : L->coff[g + 1]); ++col) {
                 for (int i = o0; i < o1; ++i) {
                     if (L->colour[i] != col) continue;
                     double t[ORACLE_MAX_B];
@@ -1379,8 +1553,11 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
             if (h->p.sub_ilu) {
                 int st = oracle_ilu0_solve_ordered(L->n, fb, L->row_ptr, L->col_idx, L->ilu_pos, L->ilu[f], rf, xt);
                 if (st) return st;
+            } else if (h->p.sub_schwarz) {
+                int st = schwarz_apply(h, L, f, 0, fb, rf, xt);
+                if (st) return st;
             }
-            for (int col = 0; col < (h->p.sub_ilu ? 0 : L->n_colours); ++col) {
+            for (int col = 0; col < ((h->p.sub_ilu || h->p.sub_schwarz) ? 0 : L->n_colours); ++col) {
                 for (int i = 0; i < L->n; ++i) {
                     if (L->colour[i] != col) continue;
                     double t[ORACLE_MAX_B];

@@ -170,6 +170,16 @@ typedef struct {
      * no mlp.  n_node_fields <= 1: the co-located case above. */
     int n_node_fields;
     const int* node_field_off;
+    /* ---- additive Schwarz as Algorithm 1's sub-solve (the paper's choice in Sec. 5:
+     * one additive Schwarz iteration with overlap one) ----
+     * sub_schwarz: 0 = off; 1 = additive, x~_f = sum_I R_I^T A_I^{-1} R_I r_f; 2 = restricted
+     * additive (every node takes the value of its own subdomain's solve only).
+     * Subdomains: the level's aggregates (one per aggregate and field), extended by
+     * schwarz_overlap (0 or 1) layers of neighbours in the graph of A_ff; A_I = the field-f
+     * sub-blocks between the subdomain's nodes (nodes ascending, dofs in field order),
+     * solved exactly by dense LU with partial pivoting.  Not with sub_ilu. */
+    int sub_schwarz;
+    int schwarz_overlap;
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
