@@ -790,6 +790,11 @@ typedef struct {
     size_t* sd_lu_off;     /* [n_sd+1] dense LU factors of A_I in sd_lu */
     double* sd_lu;
     int* sd_piv;           /* pivots of subdomain I at sd_ptr[I] * (dofs per node) */
+    /* sub_ilu with node fields: A_gg of every field as its own block matrix
+     * (nodes renumbered from 0), its elimination positions, factors in ilu[g] */
+    int* nf_rp[ORACLE_MAX_NODE_FIELDS];
+    int* nf_ci[ORACLE_MAX_NODE_FIELDS];
+    int* nf_pos[ORACLE_MAX_NODE_FIELDS];
 } olevel;
 
 struct oracle_hier {
@@ -835,6 +840,11 @@ static void level_free(olevel* L) {
     free(L->sd_lu_off);
     free(L->sd_lu);
     free(L->sd_piv);
+    for (int g = 0; g < ORACLE_MAX_NODE_FIELDS; ++g) {
+        free(L->nf_rp[g]);
+        free(L->nf_ci[g]);
+        free(L->nf_pos[g]);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -889,6 +899,48 @@ static int aggregate_node_fields(const oracle_hier* h, const olevel* L, int* agg
         foff_c[g + 1] = base;
     }
     return base;
+}
+
+/* ILU(0) of every node field's diagonal block A_gg (Algorithm 1's sub-solve,
+ * Sec. 4.3.2), as a block matrix of its own: the field's nodes renumbered from
+ * 0, the stored blocks between them; sub_ilu = 2 eliminates the field's nodes
+ * in (colour, index) order */
+static int ilu_node_fields(oracle_hier* h, olevel* L) {
+    const int b = h->b;
+    const size_t bb = (size_t)b * b;
+    int zeros[ORACLE_MAX_B] = {0};
+    for (int g = 0; g < h->NF; ++g) {
+        const int o0 = L->foff[g], o1 = L->foff[g + 1], m = o1 - o0;
+        int st = field_subgraph(L, g, &L->nf_rp[g], &L->nf_ci[g]);
+        if (st) return st;
+        const int nnz = L->nf_rp[g][m];
+        double* v = (double*)malloc(sizeof(double) * bb * (size_t)(nnz > 0 ? nnz : 1));
+        L->ilu[g] = (double*)malloc(sizeof(double) * bb * (size_t)(nnz > 0 ? nnz : 1));
+        if (!v || !L->ilu[g]) {
+            free(v);
+            return ORACLE_ENOMEM;
+        }
+        int e = 0;
+        for (int i = o0; i < o1; ++i)
+            for (int k = L->row_ptr[i]; k < L->row_ptr[i + 1]; ++k)
+                if (L->col_idx[k] >= o0 && L->col_idx[k] < o1) memcpy(v + (size_t)(e++) * bb, L->vals + (size_t)k * bb,
+                                                                      sizeof(double) * bb);
+        if (h->p.sub_ilu == 2) {
+            L->nf_pos[g] = (int*)malloc(sizeof(int) * (size_t)m);
+            if (!L->nf_pos[g]) {
+                free(v);
+                return ORACLE_ENOMEM;
+            }
+            int q = 0;
+            for (int c = L->coff[g]; c < L->coff[g + 1]; ++c)
+                for (int i = o0; i < o1; ++i)
+                    if (L->colour[i] == c) L->nf_pos[g][i - o0] = q++;
+        }
+        st = oracle_ilu0_field_ordered(m, b, zeros, L->nf_rp[g], L->nf_ci[g], v, 0, L->nf_pos[g], L->ilu[g]);
+        free(v);
+        if (st) return st;
+    }
+    return ORACLE_OK;
 }
 
 /* first-fit colours of every field on the graph of its diagonal block,
@@ -1046,7 +1098,7 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     h->NF = p->n_node_fields > 1 ? p->n_node_fields : 1;
     if (h->NF > 1) {
         const int* off = p->node_field_off;
-        int bad = h->NF > ORACLE_MAX_NODE_FIELDS || !off || F != 1 || p->smooth_p || p->sub_ilu ||
+        int bad = h->NF > ORACLE_MAX_NODE_FIELDS || !off || F != 1 || p->smooth_p ||
                   p->omega_s_arr || p->omega_p_arr || p->mlp;
         if (!bad) {
             bad = off[0] != 0 || off[h->NF] != n;
@@ -1193,7 +1245,7 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         }
         if (!L->dinv) st = level_dinv(h, L); /* computed while coarsening */
         if (st != ORACLE_OK) break;
-        if (p->sub_ilu == 2) {  /* colour order: colour ascending, then node index */
+        if (p->sub_ilu == 2 && h->NF == 1) {  /* colour order: colour ascending, then node index */
             L->ilu_pos = (int*)malloc(sizeof(int) * (size_t)L->n);
             if (!L->ilu_pos) st = ORACLE_ENOMEM;
             int e = 0;
@@ -1202,7 +1254,9 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
                     if (L->colour[i] == c) L->ilu_pos[i] = e++;
         }
         if (p->sub_schwarz && st == ORACLE_OK) st = level_schwarz(h, L);
-        if (p->sub_ilu)
+        if (p->sub_ilu && h->NF > 1) {
+            if (st == ORACLE_OK) st = ilu_node_fields(h, L);
+        } else if (p->sub_ilu)
             for (int f = 0; f < h->F && st == ORACLE_OK; ++f) {
                 L->ilu[f] = (double*)malloc(sizeof(double) * (size_t)L->nnzb * h->fb * h->fb);
                 st = L->ilu[f] ? oracle_ilu0_field_ordered(L->n, b, h->field_of_dof, L->row_ptr, L->col_idx,
@@ -1492,8 +1546,12 @@ static int bgs_node_fields(oracle_hier* h, int l, double* x, const double* rhs, 
             if (h->p.sub_schwarz) {
                 int st = schwarz_apply(h, L, g, o0, b, rf, xt);
                 if (st) return st;
+            } else if (h->p.sub_ilu) {
+                int st = oracle_ilu0_solve_ordered(o1 - o0, b, L->nf_rp[g], L->nf_ci[g], L->nf_pos[g], L->ilu[g], rf, xt);
+                if (st) return st;
             }
-            for (int col = L->coff[g]; col < (h->p.sub_schwarz ? L->coff[g] : L->coff[g + 1]); ++col) {
+            const int sweep = !h->p.sub_schwarz && !h->p.sub_ilu;
+            for (int col = L->coff[g]; col < (sweep ? L->coff[g + 1] : L->coff[g]); ++col) {
                 for (int i = o0; i < o1; ++i) {
                     if (L->colour[i] != col) continue;
                     double t[ORACLE_MAX_B];

@@ -166,8 +166,9 @@ typedef struct {
      * P = diag(P_0, P_1, ...) and the coarse nodes keep contiguous field ranges.
      * Colours are per field too (first fit on the graph of A_gg), numbered after
      * those of the earlier fields, and Algorithm 1 takes the node fields as its
-     * field blocks.  Requires smooth_p = 0, sub_ilu = 0, no weight arrays and
-     * no mlp.  n_node_fields <= 1: the co-located case above. */
+     * field blocks (with sub_ilu, the ILU(0) of each A_gg as a block matrix of its own).
+     * Requires smooth_p = 0, no weight arrays and no mlp.  n_node_fields <= 1: the
+     * co-located case above. */
     int n_node_fields;
     const int* node_field_off;
     /* ---- additive Schwarz as Algorithm 1's sub-solve (the paper's choice in Sec. 5:

@@ -253,10 +253,11 @@ def test_vcycle_three_levels_matches_matrix_form():
     assert np.allclose(z, ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
 
 
-def test_decoupled_fields_equal_two_colocated_hierarchies():
+@pytest.mark.parametrize("sub", [{}, dict(sub_ilu=1), dict(sub_ilu=2), dict(sub_schwarz=2), dict(sub_schwarz=1)])
+def test_decoupled_fields_equal_two_colocated_hierarchies(sub):
     # with A_01 = A_10 = 0 the node-field hierarchy is the co-located
     # hierarchies of A_00 and A_11 side by side: same aggregates, colours,
-    # coarse operators and V-cycle, bit for bit
+    # coarse operators and V-cycle, bit for bit, with every sub-solve
     s = P.mhd2d_q2q1(6, 2)
     n2, n = s.node_field_off[1], s.n_nodes
     rp, ci = s.row_ptr, s.col_idx
@@ -270,7 +271,7 @@ def test_decoupled_fields_equal_two_colocated_hierarchies():
         prp[1:] = np.cumsum(np.bincount(r_of[keep] - lo, minlength=hi - lo))
         return prp, (ci[keep] - lo).astype(np.int32), v[keep]
 
-    kw = dict(max_levels=3, max_coarse=0, omega=0.6)
+    kw = dict(max_levels=3, max_coarse=0, omega=0.6, **sub)
     h = hier(rp, ci, v, s.node_field_off, **kw)
     h0 = oracle.Hierarchy(*part(0, n2), 3, [0, 0, 0], **kw)
     h1 = oracle.Hierarchy(*part(n2, n), 3, [0, 0, 0], **kw)
@@ -312,7 +313,7 @@ def test_node_field_validation():
     for off in ([0, 0, n], [0, 50, n - 1], [1, 50, n], [0, 60, 50, n]):
         with pytest.raises(oracle.OracleError):
             oracle.Hierarchy(*args, max_levels=2, max_coarse=0, node_field_off=off)
-    for kw in (dict(smooth_p=1, omega_p=0.5), dict(sub_ilu=1)):
+    for kw in (dict(smooth_p=1, omega_p=0.5), dict(sub_ilu=1, sub_schwarz=2)):
         with pytest.raises(oracle.OracleError):
             oracle.Hierarchy(*args, max_levels=2, max_coarse=0, node_field_off=s.node_field_off, **kw)
     with pytest.raises(oracle.OracleError):  # dof fields and node fields together
