@@ -113,6 +113,18 @@ def test_q2q1_system_structure():
     assert np.count_nonzero(s.vals[rp[v0]:rp[v0 + 1]]) == 3
 
 
+def test_q2q1_bench_workload_sizes():
+    # the sizes the benchmark's description states
+    import bench
+
+    wl = bench.WORKLOADS["mhd2d_q2q1_128"]
+    s = wl["make"](1)
+    assert (s.node_field_off, s.n_unknowns, s.nnzb) == ([0, 66049, 82690], 248070, 2020612)
+    for text in ("66,049 Q2 nodes", "16,641 Q1 vertices", "248,070 unknowns", "omega=0.6"):
+        assert text in wl["desc"]
+    assert wl["omega"] == 0.6 and wl["levels"] == 4
+
+
 # ----------------------------------------------------------------------------
 # separate aggregation and colouring per field block
 # ----------------------------------------------------------------------------
