@@ -496,6 +496,21 @@ def run_ours(args):
         variant = {"cycle": (f"fp{other_prec} V-cycle inside fp64 FGMRES (fp64 outer SpMV, Arnoldi, coarse solve)"),
                    "value": timed.solved / (ms_o / 1e3), "unit": UNIT, "iterations": it_o, "relres": rr_o,
                    "converged": st_o == 0}
+        # one V-cycle of each precision on the rhs: relative 2-norm distance
+        # of the two outputs, the FP64 cycle's output as the reference
+        try:
+            outs = {}
+            for prec_, pp_ in ((main_prec, params64), (other_prec, params_o)):
+                hh_ = setup(pp_)
+                try:
+                    outs[prec_] = torch.empty_like(b)
+                    bamg.amg_apply(hh_, b, outs[prec_], stream)
+                    torch.cuda.synchronize(dev)
+                finally:
+                    bamg.amg_destroy(hh_)
+            variant["vcycle_rel_diff_vs_fp64"] = float((outs[32] - outs[64]).norm() / outs[64].norm())
+        except Exception:
+            variant["vcycle_rel_diff_vs_fp64"] = None
     if learned and variant:
         variant["cycle"] = f"learned damping, {variant['cycle']}"
     # --- learned workloads: the plain hierarchy, and the fallback rule --------
