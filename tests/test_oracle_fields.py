@@ -113,6 +113,55 @@ def test_q2q1_system_structure():
     assert np.count_nonzero(s.vals[rp[v0]:rp[v0 + 1]]) == 3
 
 
+def test_q2_element_closed_form():
+    # biquadratic element on [0, h]^2 with 3 x 3 Gauss points: K = Kx (x) My + Mx (x) Ky
+    # with the 1D quadratic stiffness (1/(3h)) [[7,-8,1],[-8,16,-8],[1,-8,7]] and mass
+    # (h/30) [[4,2,-1],[2,16,2],[-1,2,4]] (local node l = lx + 3 ly)
+    h = 0.25
+    g = np.sqrt(3.0 / 5.0)
+    x1 = np.array([-g, 0.0, g])
+    w1 = np.array([5.0, 8.0, 5.0]) / 9.0
+    xi, et = np.tile(x1, 3), np.repeat(x1, 3)
+    wq = np.tile(w1, 3) * np.repeat(w1, 3)
+    phi, dphi = P._tensor_basis_2d(2, xi, et)
+    grad = dphi * (2.0 / h)
+    jac = (h / 2.0) ** 2
+    K = np.einsum("q,qla,qma->lm", wq, grad, grad) * jac
+    M = np.einsum("q,ql,qm->lm", wq, phi, phi) * jac
+    K1 = np.array([[7, -8, 1], [-8, 16, -8], [1, -8, 7]]) / (3.0 * h)
+    M1 = np.array([[4, 2, -1], [2, 16, 2], [-1, 2, 4]]) * (h / 30.0)
+    assert np.allclose(K, np.kron(K1, M1) + np.kron(M1, K1), rtol=1e-13, atol=1e-15)
+    assert np.allclose(M, np.kron(M1, M1), rtol=1e-13, atol=1e-16)
+    # partition of unity and the nodal property of the basis
+    assert np.allclose(phi.sum(axis=1), 1.0) and np.allclose(dphi.sum(axis=1), 0.0)
+    nodes = np.array([-1.0, 0.0, 1.0])
+    pv, _ = P._tensor_basis_2d(2, np.tile(nodes, 3), np.repeat(nodes, 3))
+    assert np.allclose(pv, np.eye(9))
+
+
+def test_q2q1_velocity_rows_annihilate_constants():
+    # away from the boundary, the u-u part of a Q2 node's row is nu K2 (rows sum
+    # to zero), and the B-B part of a Q1 vertex's row is eta K1
+    N = 6
+    s = P.mhd2d_q2q1(N, 2)
+    m2 = 2 * N + 1
+    rp, ci, v = s.row_ptr, s.col_idx, s.vals
+    n2 = s.node_field_off[1]
+    for X, Y in ((6, 6), (5, 7), (4, 5)):
+        i = X + m2 * Y
+        q2 = ci[rp[i]:rp[i + 1]] < n2
+        blocks = v[rp[i]:rp[i + 1]][q2]
+        for a in range(2):
+            assert abs(blocks[:, a, a].sum()) < 1e-12 * np.abs(blocks[:, a, a]).max()
+            assert np.all(blocks[:, a, 1 - a] == 0.0)
+    j = n2 + 3 + (N + 1) * 3
+    q1 = ci[rp[j]:rp[j + 1]] >= n2
+    bl = v[rp[j]:rp[j + 1]][q1]
+    for a in range(2):
+        assert abs(bl[:, a, a].sum()) < 1e-12 * np.abs(bl[:, a, a]).max()
+    assert abs(bl[:, 2, 2].sum()) < 1e-12 * np.abs(bl[:, 2, 2]).max()
+
+
 def test_q2q1_bench_workload_sizes():
     # the sizes the benchmark's description states
     import bench
