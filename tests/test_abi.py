@@ -69,3 +69,20 @@ def test_host_side_validation_without_gpu():
 def test_oracle_is_not_linked_into_the_library():
     out = subprocess.run(["nm", "-D", build.LIB_PATH], capture_output=True, text=True, check=True).stdout
     assert "oracle_" not in out
+
+
+def test_no_cpu_fallback():
+    # the binding computes nothing on the host: CPU tensors are refused before
+    # any call into the library, for every solver class
+    torch = pytest.importorskip("torch")
+    from paper_2103_07537_gb300 import problems as P
+
+    s = P.mhd2d_q2q1(2, 1)
+    rp, ci = torch.from_numpy(s.row_ptr), torch.from_numpy(s.col_idx)
+    va = torch.from_numpy(s.vals.reshape(-1))
+    with pytest.raises(ValueError, match="CUDA"):
+        bamg.Solver(rp, ci, va, 3, [0, 0, 0])
+    with pytest.raises(ValueError, match="CUDA"):
+        bamg.FieldSolver(s.node_field_off, rp, ci, va, 3)
+    with pytest.raises(ValueError, match="CUDA"):
+        bamg.BatchSolver([0, s.n_nodes], rp, ci, va, 3, [0, 0, 0])
