@@ -1,13 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the block-AMG-preconditioned FGMRES solve on one GB300.
 
-Workload (default ``mhd2d_128``): the 2D coupled 4-field block system (velocity
-u, v, pressure p, magnetic field Bx, By, Lagrange multiplier psi; 6 dofs per
-node, 2 field blocks) on a 128 x 128 Q1 grid, 16,641 nodes, 99,846 unknowns,
-148,225 stored 6 x 6 blocks, viscosity and resistivity drawn log-uniformly in
-[1e-3, 1] from the seed; FP64 plain monolithic AMG with 4 levels, V(1,1)
-damped block Gauss-Seidel (omega 0.5), FGMRES(30) to a relative residual of
-1e-8.  Synthetic seeded data (the paper's MHD systems are not available).
+Workload (default ``stokes3d_64``): the 3D Stokes-type system, Q1-Q1 with
+pressure stabilisation on a 64^3 hex grid, 4 dofs per node (u, v, w, p),
+274,625 nodes, 1,098,500 unknowns, 7,189,057 stored 4 x 4 blocks (115 M
+scalars, far larger than L2); FP32 V(1,1) cycle of damped block Gauss-Seidel
+(omega 0.5) with an FP32 LU of the 2048-unknown coarsest level, inside FP64
+FGMRES(50) to a relative residual of 1e-8 (FP64 outer SpMV, Arnoldi and
+residual test).  The line also carries the FP64 cycle and the FP32 cycle with
+a smoothed prolongator whose P and R values are stored in FP32 or in BF16,
+each with its own solve rate and true FP64 residual.  Synthetic seeded data
+(the paper's MHD systems are not available).  The other workloads (the 2D
+systems, the batch of 256, the learned 256^2 system, mixed elements) are
+selected with --workload.
 
 One step = one complete solve from the matrix already in HBM: hierarchy setup
 (aggregation, colouring, Galerkin products, block inverses, coarse LU),
@@ -44,6 +49,7 @@ UNIT = "solves/s"
 TOL = 1e-8
 MAX_ITER = 5000
 FLUSH_BYTES = 256 << 20
+PR_OMEGA_P = 0.1  # prolongator smoothing weight of the smoothed-P variants
 FALLBACK_HBM_GBS = 6800.0
 SMS = 152
 
@@ -82,7 +88,7 @@ WORKLOADS = {
              "BGS omega=0.6 with the node fields as field blocks, 4 levels, FGMRES(30) to 1e-8"),
     "stokes3d_64": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).stokes3d(64, seed),
-        levels=10, max_coarse=2500, restart=50, prec=32, coarse_prec=32, cpu_sample_iters=5,
+        levels=10, max_coarse=2500, restart=50, prec=32, coarse_prec=32, cpu_sample_iters=5, pr_variants=True,
         desc="3D Stokes Q1-Q1 stabilised, 64^3 hex cells, 4 dofs/node, 1,098,500 unknowns, 7,189,057 blocks "
              "(115 M scalars), FP32 V(1,1) BGS omega=0.5 (FP32 LU of the 2048-unknown coarsest level) inside FP64 "
              "FGMRES(50) to 1e-8, 3 levels"),
@@ -95,7 +101,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mhd2d_128", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="stokes3d_64", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
@@ -114,7 +120,7 @@ def parse():
                     help="precision of the coarsest direct solve of FP32 cycles (default: the workload's)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and plain-hierarchy comparisons (for profiler launch lists)")
-    ap.add_argument("--ref-iters", type=int, default=30,
+    ap.add_argument("--ref-iters", type=int, default=5,
                     help="reference arm: inner FGMRES steps timed per step (the sample)")
     return ap.parse_args()
 
@@ -298,30 +304,50 @@ def oracle_sample(sys_, wl, iters):
     return t1 - t0, (t2 - t1) / max(it, 1)
 
 
+SOLVE_COUNTS = os.path.join(ROOT, "oracle", "solve_counts.json")
+
+
+def oracle_solve_count(name, s, wl):
+    """Inner steps of one full oracle solve of workload `name`, seed 1: the
+    committed count (written by oracle/make_solve_counts.py, which runs the
+    oracle only), else an untimed full oracle solve here."""
+    try:
+        c = json.load(open(SOLVE_COUNTS))[name]
+        if c.get("seed") == 1 and c.get("restart") == wl["restart"]:
+            return int(c["iterations"]), float(c["relres"]), "oracle/solve_counts.json"
+    except Exception:
+        pass
+    full = oracle_full_solve(s, wl)
+    return int(full["iters"]), float(full["relres"]), "an untimed full oracle solve"
+
+
 def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]
     s = wl["make"](1)
-    # one full untimed solve gives the iteration count the sample is scaled by
-    full = oracle_full_solve(s, wl)
-    for _ in range(max(0, args.warmup - 1)):
-        oracle_sample(s, wl, min(args.ref_iters, 5))
-    times = []
+    full_iters, full_rr, src = oracle_solve_count(args.workload, s, wl)
+    for _ in range(max(0, args.warmup)):
+        oracle_sample(s, wl, 1)
+    step_s, rates = [], []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         t_setup, t_iter = oracle_sample(s, wl, args.ref_iters)
-        times.append(t_setup + t_iter * full["iters"])
-    total = sum(times)
-    value = args.steps / total
-    sample = (f"per step: oracle setup + {args.ref_iters} inner FGMRES(30) steps of {args.workload} seed 1, "
-              f"scaled to one full solve of {full['iters']} inner steps (the count of an untimed full oracle "
-              f"solve, relres {full['relres']:.2e})")
+        step_s.append(time.perf_counter() - t0)
+        rates.append(1.0 / (t_setup + t_iter * full_iters))  # one full solve, scaled from the sample
+    value = statistics.mean(rates)
+    sample = (f"per step: oracle setup + {args.ref_iters} inner FGMRES({wl['restart']}) steps of {args.workload} "
+              f"seed 1 (timed: ms_per_step); value scales each step to one full solve of {full_iters} inner steps "
+              f"(relres {full_rr:.2e}, from {src})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(step_s),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl["desc"], "seed": 1},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+            "data": "synthetic", "config": {"workload": wl["desc"], "name": args.workload, "seed": 1},
+            "full_solve_scaling": {"inner_steps_sampled": args.ref_iters, "inner_steps_full_solve": full_iters,
+                                   "source": src},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample,
+                             "host_cores_available": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -513,6 +539,36 @@ def run_ours(args):
             variant["vcycle_rel_diff_vs_fp64"] = None
     if learned and variant:
         variant["cycle"] = f"learned damping, {variant['cycle']}"
+    # --- FP32 cycle with a smoothed prolongator, P / R values in FP32 or BF16 ------
+    pr_variants = None
+    if wl.get("pr_variants") and not args.no_variants and main_prec == 32:
+        pr_variants = {}
+        z_ref = None
+        for storage in (32, 16):
+            pp = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=32,
+                                         coarse_prec=coarse_prec, omega=wl.get("omega", 0.5), smooth_p=1,
+                                         omega_p=PR_OMEGA_P, pr_storage=storage, use_pdl=args.pdl)
+            key = f"smoothed_p_{'bf16' if storage == 16 else 'fp32'}"
+            try:
+                step(pp)
+                ms_v, (st_v, it_v, rr_v, _) = timed(pp, k_o)
+                hh_ = setup(pp)
+                try:
+                    zz = torch.empty_like(b)
+                    bamg.amg_apply(hh_, b, zz, stream)
+                    torch.cuda.synchronize(dev)
+                finally:
+                    bamg.amg_destroy(hh_)
+                if z_ref is None:
+                    z_ref = zz
+                pr_variants[key] = {
+                    "cycle": f"fp32 V-cycle, smoothed prolongator (omega_P {PR_OMEGA_P}) with P and R values "
+                             f"stored in {'bf16' if storage == 16 else 'fp32'}, inside fp64 FGMRES",
+                    "value": timed.solved / (ms_v / 1e3), "unit": UNIT, "iterations": it_v, "relres": rr_v,
+                    "converged": st_v == 0,
+                    "vcycle_rel_diff_vs_fp32_storage": float((zz - z_ref).norm() / z_ref.norm())}
+            except Exception as exc:  # reported, not fatal: the main line stands
+                pr_variants[key] = {"error": str(exc)[:200]}
     # --- learned workloads: the plain hierarchy, and the fallback rule --------
     plain = None
     if learned and not args.no_variants:
@@ -538,27 +594,41 @@ def run_ours(args):
 
     # --- per-kernel profile pass (events around every launch) --------------------
     kernels = {}
+    prof_iters_tot = 0
     for _ in range(max(1, args.profile_steps)):
         flush.zero_()
-        _, _, _, prof = step(params64, profile=True)
+        _, it_p_, _, prof = step(params64, profile=True)
+        prof_iters_tot += it_p_
         for k, v in prof.items():
             acc = kernels.setdefault(k, dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
             for f in acc:
                 acc[f] += v[f]
     peak_gbs, peak_src = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or 1920.0
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    # The dominant kernel of the V-cycle (the metric's "V-cycle ms") and its
+    # time per launch in the unprofiled cycle: the graph-replayed V-cycle time
+    # times the kernel's share of the cycle's kernel time in the profiled pass
+    # (events around every launch, which also cost each launch its gap), over
+    # its launches per cycle.
+    cycle_kinds = {"smooth", "residual", "restrict", "prolong", "tail", "cast", "coarse"}
+    prof_iters = max(1, prof_iters_tot // max(1, args.profile_steps))  # V-cycles per profiled solve
+    cyc = {k: v for k, v in kernels.items() if k in cycle_kinds and v["launches"]}
+    cyc_ms = sum(v["ms"] for v in cyc.values())
+    dom = max(cyc, key=lambda k: cyc[k]["ms"])
     d = kernels[dom]
-    # kernels inside the V-cycle run in the cycle precision; the outer Krylov
-    # kernels and the coarse solve in FP64
-    cycle_kinds = {"smooth", "residual", "restrict", "prolong", "tail", "cast"}
-    kernel_prec = main_prec if dom in cycle_kinds else 64
+    share = d["ms"] / cyc_ms if cyc_ms > 0 else 0.0
+    vcycle_med = statistics.median(vt)
+    launches_per_cycle = d["launches"] / (max(1, args.profile_steps) * prof_iters)
+    us_per_launch = 1e3 * vcycle_med * share / max(launches_per_cycle, 1e-9)
+    bytes_per_launch = d["bytes"] / max(1, d["launches"])
+    flops_per_launch = d["flops"] / max(1, d["launches"])
+    kernel_prec = main_prec if dom != "coarse" else (coarse_prec if main_prec == 32 else 64)
     fma_per_clk = 2 if kernel_prec == 64 else 128  # per SM on GB300 (FP64: measured 2.08 / clk / SM)
     alu_peak_tflops = SMS * fma_per_clk * 2 * sm_mhz * 1e6 / 1e12
-    gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    tfl = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-    t_mem = d["bytes"] / (peak_gbs * 1e9)
-    t_alu = d["flops"] / (alu_peak_tflops * 1e12)
+    gbs = bytes_per_launch / (us_per_launch * 1e-6) / 1e9 if us_per_launch > 0 else 0.0
+    tfl = flops_per_launch / (us_per_launch * 1e-6) / 1e12 if us_per_launch > 0 else 0.0
+    t_mem = bytes_per_launch / (peak_gbs * 1e9)
+    t_alu = flops_per_launch / (alu_peak_tflops * 1e12)
     # DRAM bytes per launch of the dominant kernel from a committed ncu capture,
     # only when the kernel sources are unchanged since that capture
     traffic = None
@@ -583,13 +653,15 @@ def run_ours(args):
                     "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
-                    "traffic": traffic, "peak_source": f"{peak_src} HBM copy bandwidth",
+                    "traffic": traffic, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alu_tflops": tfl, "alu_frac": tfl / alu_peak_tflops}
     roofline.update({"kernel": dom, "kernel_prec": f"fp{kernel_prec}",
-                     "launches": d["launches"] // max(1, args.profile_steps),
-                     "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
-                     "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
-                     "flops_per_launch": d["flops"] / max(1, d["launches"])})
+                     "launches_per_cycle": launches_per_cycle, "us_per_launch": us_per_launch,
+                     "bytes_per_launch": bytes_per_launch, "flops_per_launch": flops_per_launch,
+                     "share_of_cycle": share, "vcycle_ms": vcycle_med,
+                     "how": "us_per_launch = vcycle_ms x share_of_cycle / launches_per_cycle (share: the "
+                            "kernel's part of the cycle's kernel time in a profiled solve); achieved = "
+                            "bytes_per_launch (algorithmic) / us_per_launch"})
     ksum = {k: {"ms_per_solve": v["ms"] / max(1, args.profile_steps), "launches": v["launches"] // max(1, args.profile_steps),
                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
                 "TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else 0.0}
@@ -716,11 +788,18 @@ def run_ours(args):
             # inner-step count of this solve (the oracle's count agrees within
             # one iteration, see the parity tests)
             k = wl["cpu_sample_iters"]
+            n_full, src = iters, "this solve's count (the oracle's agrees within one step)"
+            try:
+                c = json.load(open(SOLVE_COUNTS))[args.workload]
+                if c.get("seed") == seed and c.get("restart") == restart:
+                    n_full, src = int(c["iterations"]), "oracle/solve_counts.json"
+            except Exception:
+                pass
             t_setup, t_iter = oracle_sample(s, wl, k)
-            t = t_setup + t_iter * iters
+            t = t_setup + t_iter * n_full
             cpu = {"kind": "oracle", "value": 1.0 / t, "unit": UNIT, "cores": 1,
                    "sample": f"oracle setup + {k} inner FGMRES({restart}) steps of {args.workload} seed {seed}, "
-                             f"scaled to {iters} inner steps; single-threaded C oracle",
+                             f"scaled to {n_full} inner steps (from {src}); single-threaded C oracle",
                    "host_cores_available": os.cpu_count()}
         else:
             full = oracle_full_solve(s, wl)
@@ -756,7 +835,7 @@ def run_ours(args):
                 "cycle_prec": main_prec, "coarse_prec": coarse_prec,
                 "use_pdl": 0 if stats.get("node_fields", 1) > 1 else args.pdl,
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
-                         "cluster": stats.get("tail_cluster")}, "variant": variant,
+                         "cluster": stats.get("tail_cluster")}, "variant": variant, "pr_variants": pr_variants,
                 "plain": plain,
                 "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,

@@ -122,6 +122,37 @@ typedef struct {
                          then field 1's, ...) on levels whose FP32 values exceed the L2 cache,
                          block-major elsewhere; 1 = block-major everywhere; 2 = field-major
                          everywhere. Same results either way (bitwise).                       */
+    int sweep;        /* smoother launches per field step of Algorithm 1: 0 (default) = with
+                         autotune 1, one persistent launch for all colours of the step (tiles
+                         taken in colour order, each waiting in bounded spins for the tiles of
+                         its lower-colour neighbours) where it times faster than one launch per
+                         colour, else one launch per colour; 1 = one launch per colour always;
+                         2 = the persistent launch on every level (one thread per scalar row);
+                         3 = as 2 with four lanes per row. The persistent launch computes the
+                         values of the thread-per-row (2) or four-lanes (3) kernels bit for bit.
+                         A wait that runs out is reported as BAMG_ETIMEOUT by fgmres_solve.    */
+    int sub_solver;   /* the approximate solve of A_ff inside each field step of Algorithm 1:
+                         0 (default) = one multicolour node-block Gauss-Seidel sweep from zero;
+                         1 = ILU(0) of A_ff (Sec. 4.3.2, the paper's sub-solver; Sec. 5.1) with
+                         the nodes eliminated in colour order (colour, then index), its forward
+                         and backward solves one launch per colour each (the nodes of a colour
+                         do not couple). With 1 or 2 the cycle runs without the tail and the
+                         persistent sweep (tail_dofs, tail_grid, sweep are ignored); a zero
+                         pivot is BAMG_ESINGULAR_BLOCK, a row of more than 64 blocks of its
+                         field BAMG_EUNSUPPORTED; 2 = restricted additive Schwarz (Sec. 5: one
+                         Schwarz iteration per field block): one subdomain per aggregate and
+                         field block, the aggregate extended by schwarz_overlap layers of
+                         neighbours in the graph of A_ff, solved exactly (LU with partial
+                         pivoting in FP64 at setup; the rows of the local inverse that belong
+                         to the aggregate are kept), every node taking its own aggregate's
+                         local solution; at most 160 unknowns per subdomain (else
+                         BAMG_EUNSUPPORTED), a singular local matrix BAMG_ESINGULAR_BLOCK.     */
+    int schwarz_overlap; /* layers of neighbours added to each Schwarz subdomain: 1 (default,
+                         the paper's overlap one) or 0 (block Jacobi over the aggregates)     */
+    int ortho;        /* Arnoldi orthogonalisation of fgmres_solve: 0 (default) = classical
+                         Gram-Schmidt with a second projection only where the first removed
+                         more than half of ||w||^2 (the DGKS test); 1 = classical Gram-Schmidt
+                         applied twice at every step. Batches use 1.                          */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */
@@ -255,14 +286,19 @@ int bsr_spmv(const int* row_ptr, const int* col_idx, const double* vals, int n_n
  *   1..40000 (BAMG_EUNSUPPORTED above 40000).
  * colour: device, n_nodes ints, receives the colour of every node.
  * n_colours: device, one int, receives the number of colours, or -1 if the
- *   pattern needs more than 255 colours or is not structurally symmetric.
+ *   pattern needs more than 255 colours or breaks the conventions above (a
+ *   row bound or column out of range, columns not strictly ascending, a
+ *   missing diagonal block, or a block (i, j) stored without (j, i)); the
+ *   colours are then -1 where not computed.
  * The first call on a device looks up the device address of the scratch array
  *   (a host-side call, done once per device with that device current); make
  *   that first call before capturing a stream.  Asynchronous on `stream`.
  *   Every call on a device shares the one scratch array, which keeps the last
  *   call's contents (nothing in it needs to start at zero): calls that overlap
  *   on the GPU (different streams, no ordering between them) race and must
- *   not be issued.
+ *   not be issued.  The device address found by the first call is kept for
+ *   the life of the process: do not call this entry point after a
+ *   cudaDeviceReset.
  */
 int amg_colour_noalloc(const int* row_ptr, const int* col_idx, int n_nodes, int* colour, int* n_colours,
                        void* stream);
@@ -373,6 +409,15 @@ int amg_level_info(bamg_t h, int level, int* n_nodes, int* nnzb, int* n_colours,
  * row-major; not on the coarsest level). */
 int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, double* vals, int* agg,
                    int* colour, double* dinv);
+
+/* amg_level_ilu - the FP64 ILU(0) factors of level l (sub_solver 1: the
+ * incomplete factorisation of every field's A_ff in colour order, Sec. 4.3.2)
+ * into lu[F*nnzb*fb*fb] (host or device): field-major planes, then block k,
+ * then the fb x fb sub-block row-major; entry (k, r, c) of block (i, j)
+ * holds L (unit lower, strictly before the scalar diagonal in elimination
+ * order, whose diagonal 1 is not stored) or U.  BAMG_EINVAL on the coarsest
+ * level or without ILU. */
+int amg_level_ilu(bamg_t h, int level, double* lu);
 
 /* JSON summary of the hierarchy (levels, sizes, colours, bytes) into json[cap];
  * returns the length written (without the terminating zero) or a negative status. */

@@ -23,7 +23,7 @@ BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 
 #: every symbol the C header declares
 EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
-           "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_stats", "amg_destroy", "amg_strerror",
+           "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_level_ilu", "amg_stats", "amg_destroy", "amg_strerror",
            "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
            "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
            "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
@@ -49,7 +49,8 @@ class AmgParams(C.Structure):
                 ("omega_p_arr", C.POINTER(C.c_double)), ("omega_p_len", C.c_longlong),
                 ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int),
                 ("use_pdl", C.c_int), ("coarse_prec", C.c_int), ("tail_grid", C.c_int),
-                ("value_layout", C.c_int)]
+                ("value_layout", C.c_int), ("sweep", C.c_int), ("sub_solver", C.c_int),
+                ("schwarz_overlap", C.c_int), ("ortho", C.c_int)]
 
 
 class BamgError(RuntimeError):
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = True):
         lib.amg_num_levels.argtypes = [_vp]
         lib.amg_level_info.argtypes = [_vp, C.c_int, _ip, _ip, _ip, _ip]
         lib.amg_level_copy.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.amg_level_ilu.argtypes = [_vp, C.c_int, _vp]
         lib.amg_stats.argtypes = [_vp, C.c_char_p, C.c_int]
         lib.amg_destroy.argtypes = [_vp]
         lib.amg_strerror.argtypes = [C.c_int]
@@ -264,6 +266,17 @@ def amg_level_copy(handle: int, level: int, b: int, F: int):
         raise BamgError(st, "amg_level_copy")
     return dict(n=n, nnzb=nnz, n_colours=ncol, n_agg=nagg, row_ptr=rp, col_idx=ci, vals=v, agg=agg,
                 colour=col, dinv=dinv)
+
+
+def amg_level_ilu(handle: int, level: int, b: int, F: int):
+    """Host copy of one level's ILU(0) factors, shape (F, nnzb, fb, fb)."""
+    _, nnz, _, _ = amg_level_info(handle, level)
+    fb = b // F
+    lu = np.zeros((F, nnz, fb, fb))
+    st = load().amg_level_ilu(handle, level, _hp(lu))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_level_ilu")
+    return lu
 
 
 def amg_stats(handle: int) -> dict:
@@ -483,6 +496,9 @@ class Solver:
 
     def level(self, l: int) -> dict:
         return amg_level_copy(self.handle, l, self.b, self.F)
+
+    def ilu(self, l: int):
+        return amg_level_ilu(self.handle, l, self.b, self.F)
 
     def apply(self, r, z, stream=None):
         amg_apply(self.handle, r, z, stream)

@@ -127,6 +127,31 @@ struct Level {
     int bgs_tpr = 0, spmv_tpr = 0;
     // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split
     float tune_us[6] = {0, 0, 0, 0, 0, 0};
+    // persistent sweep: 0 = one launch per colour (bgs_tpr), 1 = every colour of a field step
+    // in one launch (thread per row), 2 = the same with four lanes per row; the plan exists
+    // when sw_tiles > 0
+    int sweep = 0;
+    int sw_tiles = 0;
+    std::vector<int> sw_tile_ptr;  // first tile of every colour (host)
+    int *sw_tile_ptr_d = nullptr, *sw_lo = nullptr, *sw_hi = nullptr;
+    unsigned *sw_flags = nullptr, *sw_ctrl = nullptr;
+    // measured field-step times (us): per-colour launches, sweep, sweep with four lanes per row
+    float tune_step_us[3] = {0, 0, 0};
+    // ILU(0) sub-solve (sub_solver 1): factors [F][nnzb][fb][fb] in FP64 and in the cycle type,
+    // elimination position of every node, higher-colour flag of every block
+    double* ilu64 = nullptr;
+    float* ilu32 = nullptr;
+    int* pos = nullptr;
+    unsigned char* upk = nullptr;
+    // restricted Schwarz sub-solve (sub_solver 2): node lists of the subdomains (one per
+    // aggregate), offsets of the restricted inverses of every (aggregate, field block) and
+    // the inverses in FP64 and in the cycle type
+    int *sd_ptr = nullptr, *sd_nodes = nullptr;
+    long* sd_xoff = nullptr;
+    double* sd_x64 = nullptr;
+    float* sd_x32 = nullptr;
+    int sd_max_m = 0;
+    long sd_xtotal = 0;
     // node range of every system of a batch on this level (host and device)
     std::vector<int> sys_off;
     int* sys_off_d = nullptr;
@@ -369,6 +394,10 @@ extern "C" void amg_default_params(amg_params* p) {
     p->coarse_prec = 64;
     p->tail_grid = 0;
     p->value_layout = 0;
+    p->sweep = 0;
+    p->sub_solver = 0;
+    p->schwarz_overlap = 1;
+    p->ortho = 0;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -408,6 +437,12 @@ template <>
 const double* level_vals<double>(const Level& L) { return L.vals64; }
 template <>
 const float* level_vals<float>(const Level& L) { return L.vals32; }
+template <typename T>
+static const T* level_ilu(const Level& L);
+template <>
+const double* level_ilu<double>(const Level& L) { return L.ilu64; }
+template <>
+const float* level_ilu<float>(const Level& L) { return L.ilu32; }
 template <typename T>
 static const T* level_dinv(const Level& L);
 template <>
@@ -566,6 +601,97 @@ static int smoothed_galerkin(bamg_ctx* h, int l, cudaStream_t s) {
     return BAMG_OK;
 }
 
+// Subdomains of the restricted Schwarz sub-solve on level l (its aggregates
+// extended by schwarz_overlap layers in the graph of A_ff) and the own rows of
+// their local inverses (FP64, and in the cycle type for FP32 cycles).
+static int schwarz_level(bamg_ctx* h, int l, cudaStream_t s) {
+    Level& L = h->lev[l];
+    const int na = L.n_agg, fb = h->fb;
+    const int nfs = h->nf > 1 ? 1 : h->F;  // subdomains per aggregate
+    const int* nfield = h->nf > 1 ? L.node_field : nullptr;
+    int* cnt = nullptr;
+    TRY(h->alloc(&cnt, (size_t)na));
+    TRY(schwarz_setup_count(na, L.agg_ptr, L.members, L.rp, L.ci, nfield, h->p.schwarz_overlap, cnt, s));
+    std::vector<int> c((size_t)na), ap((size_t)na + 1);
+    BAMG_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt, sizeof(int) * na, cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(ap.data(), L.agg_ptr, sizeof(int) * (na + 1), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->release(cnt);
+    std::vector<int> sp((size_t)na + 1, 0);
+    std::vector<long> xo((size_t)na * nfs + 1, 0);
+    int max_m = 0;
+    for (int I = 0; I < na; ++I) {
+        if (c[I] < 0) return BAMG_EUNSUPPORTED;  // a subdomain larger than the local solve takes
+        sp[I + 1] = sp[I] + c[I];
+        const int m = c[I] * fb;
+        max_m = m > max_m ? m : max_m;
+        const long own = (long)(ap[I + 1] - ap[I]) * fb;
+        for (int f = 0; f < nfs; ++f) xo[(size_t)I * nfs + f + 1] = xo[(size_t)I * nfs + f] + own * m;
+    }
+    L.sd_max_m = max_m;
+    L.sd_xtotal = xo.back();
+    TRY(h->alloc(&L.sd_ptr, (size_t)na + 1));
+    TRY(h->alloc(&L.sd_nodes, (size_t)sp.back()));
+    TRY(h->alloc(&L.sd_xoff, xo.size()));
+    TRY(h->alloc(&L.sd_x64, (size_t)L.sd_xtotal));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L.sd_ptr, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice, s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L.sd_xoff, xo.data(), sizeof(long) * xo.size(), cudaMemcpyHostToDevice, s));
+    TRY(schwarz_setup_fill(na, nfs, h->b, fb, max_m, L.agg_ptr, L.members, L.rp, L.ci, nfield,
+                           h->p.schwarz_overlap, L.sd_ptr, L.sd_nodes, L.vals64, L.sd_xoff, L.sd_x64, h->d_err, s));
+    TRY(check_dev(h, s));
+    if (h->p.cycle_prec == 32) {
+        TRY(h->alloc(&L.sd_x32, (size_t)L.sd_xtotal));
+        TRY(launch_convert_d2f(L.sd_xtotal, L.sd_x64, L.sd_x32, s));
+    }
+    return BAMG_OK;
+}
+
+// Tiles of the persistent sweep on a coloured level (colour lists and lowk
+// exist) and their dependencies; skipped when sweeps are off, for sub-block
+// sizes without a sweep kernel and for levels with more colours than it takes.
+static int build_sweep_plan(bamg_ctx* h, Level& L, cudaStream_t s) {
+    const int ntile = sweep_tile_nodes(h->fb);
+    if (h->p.sweep == 1 || ntile <= 0 || L.n_colours < 1 || L.n_colours > kSweepMaxColours) return BAMG_OK;
+    const int C = L.n_colours;
+    L.sw_tile_ptr.assign((size_t)C + 1, 0);
+    for (int c = 0; c < C; ++c)
+        L.sw_tile_ptr[c + 1] = L.sw_tile_ptr[c] + ceil_div(L.colour_ptr[c + 1] - L.colour_ptr[c], ntile);
+    L.sw_tiles = L.sw_tile_ptr[C];
+    TRY(h->alloc(&L.sw_tile_ptr_d, (size_t)C + 1));
+    TRY(h->alloc(&L.sw_lo, (size_t)L.sw_tiles * C));
+    TRY(h->alloc(&L.sw_hi, (size_t)L.sw_tiles * C));
+    TRY(h->alloc(&L.sw_flags, (size_t)L.sw_tiles));
+    TRY(h->alloc(&L.sw_ctrl, 4));
+    int* tile_of = nullptr;
+    TRY(h->alloc(&tile_of, (size_t)L.n));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(L.sw_tile_ptr_d, L.sw_tile_ptr.data(), sizeof(int) * (C + 1), cudaMemcpyHostToDevice,
+                                  s));
+    BAMG_CUDA_TRY(cudaMemsetAsync(L.sw_flags, 0, sizeof(unsigned) * (size_t)L.sw_tiles, s));
+    BAMG_CUDA_TRY(cudaMemsetAsync(L.sw_ctrl, 0, 4 * sizeof(unsigned), s));
+    TRY(sweep_plan(L.n, C, ntile, L.colour_nodes, L.colour, L.colour_ptr_d, L.sw_tile_ptr_d, L.rp, L.ci, L.lowk,
+                   L.sw_tiles, tile_of, L.sw_lo, L.sw_hi, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->release(tile_of);
+    if (h->p.sweep >= 2) L.sweep = h->p.sweep - 1;
+    return BAMG_OK;
+}
+
+// the sweep arguments of colours c_lo..c_hi-1 of level L
+static SweepArgs sweep_args(bamg_ctx* h, const Level& L, int c_lo, int c_hi) {
+    SweepArgs sw;
+    sw.c_lo = c_lo;
+    sw.c_hi = c_hi;
+    sw.C = L.n_colours;
+    sw.colour_ptr = L.colour_ptr_d;
+    sw.tile_ptr = L.sw_tile_ptr_d;
+    sw.dep_lo = L.sw_lo;
+    sw.dep_hi = L.sw_hi;
+    sw.flags = L.sw_flags;
+    sw.ctrl = L.sw_ctrl;
+    sw.err = h->d_err;
+    return sw;
+}
+
 // a non-default row mapping must beat warp-per-row by more than 3%
 constexpr float kTuneMargin = 0.97f;
 
@@ -657,6 +783,37 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             L.bgs_tpr = tv[best] < kTuneMargin * L.tune_us[0] ? best + 1 : 0;
         }
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
+        // one whole field step (every colour of field 0) as per-colour launches
+        // in the chosen mapping against the persistent sweep, in the cycle's
+        // launch mode; the sweep replaces the per-colour launches by the margin
+        if (L.sw_tiles > 0 && h->p.sweep == 0 && h->p.autotune == 1) {
+            PdlScope pdl(h->p.use_pdl != 0);
+            const int c_hi = h->nf > 1 ? L.fcol[1] : L.n_colours;
+            auto per_colour = [&]() {
+                for (int c = 0; c < c_hi; ++c) {
+                    BgsArgs ac = a;
+                    ac.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
+                    ac.nodes = L.colour_nodes + L.colour_ptr[c];
+                    ac.colour = c;
+                    const int st = L.bgs_tpr ? launch_bgs_colour_tpr<T>(b, h->fb, ac, s, L.bgs_tpr - 1)
+                                             : launch_bgs_colour<T>(b, h->fb, ac, s);
+                    if (st != BAMG_OK) return st;
+                }
+                return (int)BAMG_OK;
+            };
+            const SweepArgs sw = sweep_args(h, L, 0, c_hi);
+            const int tiles = L.sw_tile_ptr[c_hi];
+            L.tune_step_us[0] = time_launch(s, e0, e1, reps, per_colour);
+            L.tune_step_us[1] = time_launch(s, e0, e1, reps, [&] {
+                return launch_bgs_sweep<T>(b, h->fb, a, sw, tiles, 0, s);
+            });
+            L.tune_step_us[2] = time_launch(s, e0, e1, reps, [&] {
+                return launch_bgs_sweep<T>(b, h->fb, a, sw, tiles, 1, s);
+            });
+            const int best = L.tune_step_us[2] < L.tune_step_us[1] ? 2 : 1;
+            L.sweep = L.tune_step_us[best] < kTuneMargin * L.tune_step_us[0] ? best : 0;
+            TRY(check_dev(h, s));
+        }
     }
     {
         const Level& L0 = h->lev[0];
@@ -919,6 +1076,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&L.lowk, (size_t)L.nnzb));
         if (h->nf > 1) TRY(field_lower_flags(L.n, L.rp, L.ci, L.colour, L.node_field, L.lowk, s));
         else TRY(launch_lower_flags(L.n, L.rp, L.ci, L.colour, L.lowk, s));
+        TRY(build_sweep_plan(h, L, s));
         h->t_phase[3] += ms_since(tp);
         tp = Clock::now();
         if (!L.dinv64) {  // (already there when P was smoothed)
@@ -926,6 +1084,22 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
             TRY(block_inverses(b, h->fb, L.n, L.diag, L.vals64, L.dinv64, h->d_err, s));
             TRY(check_dev(h, s));
         }
+        if (h->p.sub_solver == 1) {  // ILU(0) of every field's A_ff in colour order
+            const size_t nlu = (size_t)h->F * L.nnzb * h->fb * h->fb;
+            TRY(h->alloc(&L.pos, (size_t)L.n));
+            TRY(h->alloc(&L.ilu64, nlu));
+            TRY(h->alloc(&L.upk, (size_t)L.nnzb));
+            const int* nfield = h->nf > 1 ? L.node_field : nullptr;
+            TRY(ilu_factor(L.n, b, h->fb, h->F, L.nnzb, L.n_colours, L.colour_ptr, L.colour_nodes, L.rp, L.ci,
+                           L.diag, nfield, L.vals64, L.pos, L.ilu64, h->d_err, s));
+            TRY(launch_upper_flags(L.n, L.rp, L.ci, L.colour, nfield, L.upk, s));
+            TRY(check_dev(h, s));
+            if (h->p.cycle_prec == 32) {
+                TRY(h->alloc(&L.ilu32, nlu));
+                TRY(launch_convert_d2f((long)nlu, L.ilu64, L.ilu32, s));
+            }
+        }
+        if (h->p.sub_solver == 2) TRY(schwarz_level(h, l, s));
         if (h->p.cycle_prec == 32 && L.omega_s64) {
             TRY(h->alloc(&L.omega_s32, (size_t)L.n * h->F));
             TRY(launch_convert_d2f((long)L.n * h->F, L.omega_s64, L.omega_s32, s));
@@ -1099,8 +1273,17 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
         prm.mlp_levels < 0 || (prm.use_pdl != 0 && prm.use_pdl != 1) ||
         (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32) ||
-        (prm.tail_grid != 0 && prm.tail_grid != 1) || prm.value_layout < 0 || prm.value_layout > 2)
+        (prm.tail_grid != 0 && prm.tail_grid != 1) || prm.value_layout < 0 || prm.value_layout > 2 ||
+        prm.sweep < 0 || prm.sweep > 3 || prm.sub_solver < 0 || prm.sub_solver > 2 ||
+        prm.schwarz_overlap < 0 || prm.schwarz_overlap > 1 || prm.ortho < 0 || prm.ortho > 1)
         return BAMG_EINVAL;
+    if (prm.sub_solver != 0) {
+        // the cycle with another sub-solve runs as separate launches: no
+        // recorded single-launch tail, no persistent sweep
+        prm.tail_dofs = 0;
+        prm.tail_grid = 0;
+        prm.sweep = 1;
+    }
     // fields: non-decreasing 0..F-1 in unit steps, equal sizes
     if (field_of_dof[0] != 0) return BAMG_EINVAL;
     int F = 1;
@@ -1245,6 +1428,139 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
     const bool have_counts = (int)L.colour_nnz.size() == L.n_colours;
     const bool nodef = h->nf > 1;
     const int c_lo = nodef ? L.fcol[f] : 0, c_hi = nodef ? L.fcol[f + 1] : L.n_colours;
+    if (h->p.sub_solver == 1) {
+        // ILU(0) of A_ff: forward solve over the colours ascending (the field's
+        // residual formed on the fly), backward solve descending, then x_f += omega x~
+        const T* lu = level_ilu<T>(L) + (nodef ? 0 : (size_t)f * L.nnzb * h->fb * h->fb);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int t = 0; t < c_hi - c_lo; ++t) {
+                const int c = pass == 0 ? c_lo + t : c_hi - 1 - t;
+                BgsArgs a;
+                a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
+                a.nodes = L.colour_nodes + L.colour_ptr[c];
+                a.colour = c;
+                a.colours = L.colour;
+                a.lowk = L.lowk;
+                a.fm = level_fm<T>(L);
+                a.rp = L.rp;
+                a.ci = L.ci;
+                a.vals = level_vals<T>(L);
+                a.rhs = rhs;
+                a.x_in = x_in;
+                a.x_out = x_out;
+                a.xt = L.xt;
+                a.uc = uc;
+                a.agg = uc ? L.agg : nullptr;
+                a.field = nodef ? 0 : f;
+                a.F = h->F;
+                a.omega = h->p.omega;
+                a.omega_node = level_omega<T>(L);
+                double bytes = 0.0, flops = 0.0;
+                if (h->prof && have_counts) {
+                    const double es = sizeof(T), B = h->b, FB = h->fb, nc = a.n_in_colour;
+                    const double nnz = (double)L.colour_nnz[c], low = (double)L.colour_nnz_lower[c];
+                    const double up = nnz - low - nc;
+                    if (pass == 0) {
+                        bytes = nnz * 5.0 + (x_in ? nnz * FB * B * es + nnz * B * es : 0.0) + low * FB * FB * es +
+                                low * FB * es + nc * (FB * FB * es + 12.0 + B * es + FB * es);
+                        flops = 2.0 * ((x_in ? nnz * FB * B : 0.0) + low * FB * FB + nc * FB * FB / 2.0);
+                    } else {
+                        bytes = nnz * 5.0 + up * FB * FB * es + up * FB * es +
+                                nc * (FB * FB * es + 12.0 + 2.0 * FB * es + (x_in ? 2.0 : 1.0) * B * es);
+                        flops = 2.0 * (up * FB * FB + nc * FB * FB / 2.0);
+                    }
+                }
+                PL(BAMG_K_SMOOTH, bytes, flops, launch_ilu_colour<T>(h->b, h->fb, a, lu, L.diag, L.upk, pass == 1, s));
+            }
+        if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
+        return BAMG_OK;
+    }
+    if (h->p.sub_solver == 2) {
+        // restricted Schwarz: the field's residual, then every subdomain of the
+        // field's aggregates at once; x_f += omega x~ for the own nodes
+        const int fstep = nodef ? 0 : f;
+        const int i0 = nodef ? L.fo[f] : 0, ni = nodef ? L.fo[f + 1] - L.fo[f] : L.n;
+        T* rf = static_cast<T*>(L.xt);
+        const double es = sizeof(T), B = h->b, FB = h->fb;
+        PL(BAMG_K_SMOOTH,
+           x_in ? (double)ni * (9.0 * (B * FB * es + 4.0 + B * es)) + ni * (8.0 + B * es + FB * es)
+                : ni * (B * es + FB * es),
+           x_in ? 2.0 * ni * 9.0 * B * FB : 0.0,
+           launch_field_residual<T>(h->b, h->fb, level_fm<T>(L), ni, fstep, L.rp + i0, L.ci, level_vals<T>(L),
+                                    x_in, uc, uc ? L.agg : nullptr, rhs + (size_t)i0 * h->b, rf + (size_t)i0 * h->fb,
+                                    s));
+        SchwarzArgs sa;
+        if (nodef) {
+            const Level& Cn = h->lev[l + 1];
+            sa.agg_lo = Cn.fo[f];
+            sa.agg_hi = Cn.fo[f + 1];
+        } else {
+            sa.agg_lo = 0;
+            sa.agg_hi = L.n_agg;
+        }
+        sa.nfs = nodef ? 1 : h->F;
+        sa.b = h->b;
+        sa.fb = h->fb;
+        sa.sd_ptr = L.sd_ptr;
+        sa.sd_nodes = L.sd_nodes;
+        sa.agg_ptr = L.agg_ptr;
+        sa.members = L.members;
+        sa.x_off = L.sd_xoff;
+        sa.X = h->p.cycle_prec == 32 ? (const void*)L.sd_x32 : (const void*)L.sd_x64;
+        sa.rf = rf;
+        BgsArgs a;
+        a.rhs = rhs;
+        a.x_in = x_in;
+        a.x_out = x_out;
+        a.uc = uc;
+        a.agg = uc ? L.agg : nullptr;
+        a.field = fstep;
+        a.F = h->F;
+        a.omega = h->p.omega;
+        a.omega_node = level_omega<T>(L);
+        const double xb = (double)L.sd_xtotal / (nodef ? 1.0 : h->F) * es;
+        PL(BAMG_K_SMOOTH, xb + (double)ni * (FB * es * 2.0 + B * es * (x_in ? 2.0 : 1.0)),
+           2.0 * (double)L.sd_xtotal / (nodef ? 1.0 : h->F), launch_schwarz_apply<T>(sa, a, s));
+        if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
+        return BAMG_OK;
+    }
+    if (L.sweep && L.sw_tiles > 0 && !h->rec) {
+        // every colour of the step in one persistent launch
+        BgsArgs a;
+        a.nodes = L.colour_nodes;
+        a.colours = L.colour;
+        a.lowk = L.lowk;
+        a.fm = level_fm<T>(L);
+        a.rp = L.rp;
+        a.ci = L.ci;
+        a.vals = level_vals<T>(L);
+        a.dinv = level_dinv<T>(L);
+        a.rhs = rhs;
+        a.x_in = x_in;
+        a.x_out = x_out;
+        a.xt = L.xt;
+        a.uc = uc;
+        a.agg = uc ? L.agg : nullptr;
+        a.field = nodef ? 0 : f;
+        a.F = h->F;
+        a.omega = h->p.omega;
+        a.omega_node = level_omega<T>(L);
+        double bytes = 0.0, flops = 0.0;
+        if (h->prof && have_counts)
+            for (int c = c_lo; c < c_hi; ++c) {
+                const double es = sizeof(T), B = h->b, FB = h->fb, nc = L.colour_ptr[c + 1] - L.colour_ptr[c];
+                const double nnz = (double)L.colour_nnz[c], low = (double)L.colour_nnz_lower[c];
+                bytes += nnz * (FB * B * es + 4.0) + nc * 8.0 + nc * FB * FB * es + nc * FB * es +
+                         (x_in ? nc * B * es : 0.0) + nc * B * es + nc * FB * es + (c > 0 ? nc * FB * es : 0.0) +
+                         (uc ? nc * (B * es + 4.0) : 0.0);
+                flops += 2.0 * ((x_in ? nnz * FB * B : 0.0) + low * FB * FB + nc * FB * FB);
+            }
+        const SweepArgs sw = sweep_args(h, L, c_lo, c_hi);
+        PL(BAMG_K_SMOOTH, bytes, flops,
+           launch_bgs_sweep<T>(h->b, h->fb, a, sw, L.sw_tile_ptr[c_hi] - L.sw_tile_ptr[c_lo], L.sweep == 2, s));
+        if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
+        return BAMG_OK;
+    }
     for (int c = c_lo; c < c_hi; ++c) {
         BgsArgs a;
         a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
@@ -1733,23 +2049,40 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             TRY(apply_impl(h, vj, zj, s));
             PL(BAMG_K_SPMV, spmv_bytes, spmv_flops,
                outer_spmv(h, zj, nullptr, h->w, s));
-            // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
             const double nv = j + 1;
             GivensArgs ga{j, m, h->h1, h->h2, h->H, h->cs, h->sn, h->g, h->scal};
             PL(BAMG_K_KRYLOV, (nv + 1) * vN, 2.0 * N * (nv + 1),
                launch_multi_dot(N, h->w, h->V, N, j + 1, 1, h->partial, h->h1, h->ticket, s));
-            PL(BAMG_K_KRYLOV, (2 * nv + 2) * vN, 4.0 * N * nv,
-               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, h->h2, h->ticket, nullptr, s));
-            PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
-               launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, h->wsq, h->ticket, &ga, s));
+            if (h->p.ortho == 1) {
+                // CGS2: h1 = V^T w (and ||w||^2), w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
+                PL(BAMG_K_KRYLOV, (2 * nv + 2) * vN, 4.0 * N * nv,
+                   launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 1, h->partial, h->h2, h->ticket, nullptr,
+                                   s));
+                PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
+                   launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, h->wsq, h->ticket, &ga, s));
+            } else {
+                // classical Gram-Schmidt, projected a second time only where the
+                // first projection removed more than half of ||w||^2 (DGKS):
+                // w -= V h1 and ||w||^2 with the test; then, only if set,
+                // h2 = V^T w and w -= V h2, ||w||^2 (the Givens update with h1 + h2)
+                unsigned* reorth = h->ticket + 2;
+                PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
+                   launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 3, h->partial, h->wsq, h->ticket, &ga, s,
+                                   nullptr, reorth));
+                PL(BAMG_K_KRYLOV, 0.0, 0.0,
+                   launch_multi_dot(N, h->w, h->V, N, j + 1, 0, h->partial, h->h2, h->ticket, s, reorth));
+                PL(BAMG_K_KRYLOV, 0.0, 0.0,
+                   launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, h->wsq, h->ticket, &ga, s,
+                                   reorth));
+            }
             PL(BAMG_K_KRYLOV, 2.0 * vN, N, launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
             total++;
             k = j + 1;
             BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            if (h->tail_grid)  // a grid-barrier timeout of the cycle's cooperative launch
-                BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            // a bounded wait of the cycle (grid barrier, sweep tile) that ran out
+            BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
             BAMG_CUDA_TRY(cudaStreamSynchronize(s));
-            if (h->tail_grid && h->h_pin[0] != 0) return map_dev_error(h->h_pin[0]);
+            if (h->h_pin[0] != 0) return map_dev_error(h->h_pin[0]);
             if (!isfinite(hs[1])) return BAMG_ENAN;
             if (hs[1] / bnorm <= tol || hs[2] != 0.0 || total >= max_iter) break;
         }
@@ -1892,6 +2225,10 @@ extern "C" int fgmres_solve_batched(bamg_t h, const double* b, double* x, double
     }
     BAMG_CUDA_TRY(cudaStreamSynchronize(s));
     h->release(partial);
+    if (st == BAMG_OK) {  // a bounded wait of the cycle (sweep tile) that ran out
+        const int dev_st = check_dev(h, s);
+        if (dev_st != BAMG_OK) return dev_st;
+    }
     int all = 1;
     for (int q = 0; q < S; ++q) {
         if (iters) iters[q] = tot[q];
@@ -2002,11 +2339,20 @@ extern "C" int amg_level_copy(bamg_t h, int level, int* row_ptr, int* col_idx, d
     return BAMG_OK;
 }
 
+extern "C" int amg_level_ilu(bamg_t h, int level, double* lu) {
+    if (!h || level < 0 || level >= h->nlev || !lu) return BAMG_EINVAL;
+    const Level& L = h->lev[level];
+    if (!L.ilu64) return BAMG_EINVAL;
+    BAMG_CUDA_TRY(cudaMemcpy(lu, L.ilu64, sizeof(double) * (size_t)h->F * L.nnzb * h->fb * h->fb,
+                             cudaMemcpyDefault));
+    return BAMG_OK;
+}
+
 extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
-                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_unknowns\":" +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};
@@ -2025,11 +2371,15 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colours\":" + std::to_string(L.n_colours) + ",\"aggregates\":" + std::to_string(L.n_agg) +
              ",\"aggregation_rounds\":" + std::to_string(L.agg_rounds) +
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
-             ",\"smoother_mapping\":\"" + (L.bgs_tpr == 3   ? "thread-split"
+             ",\"smoother_mapping\":\"" + (L.sweep == 2     ? "sweep-split"
+                                          : L.sweep        ? "sweep"
+                                          : L.bgs_tpr == 3 ? "thread-split"
                                           : L.bgs_tpr == 2 ? "thread-half"
                                           : L.bgs_tpr      ? "thread"
                                                            : "warp") +
-             "\",\"residual_mapping\":\"" +
+             "\",\"sweep_tiles\":" + std::to_string(L.sw_tiles) + ",\"tune_step_us\":[" +
+             std::to_string(L.tune_step_us[0]) + "," + std::to_string(L.tune_step_us[1]) + "," +
+             std::to_string(L.tune_step_us[2]) + "]" + ",\"residual_mapping\":\"" +
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "bamg.h"
 
 namespace bamg {
@@ -279,6 +281,77 @@ template <typename T>
 // small colour spread over more SMs); 2: four lanes per scalar row, each
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
+
+// ---- persistent multicolour sweep (k_sweep.cu) ----
+// Every colour c_lo..c_hi-1 of one field step in one launch: the colour-
+// ordered node list (BgsArgs.nodes = the level's whole list) is cut into
+// tiles of sweep_tile_nodes(fb) entries, numbered colour by colour
+// (tile_ptr[c] = first tile of colour c); a tile waits for the tiles of its
+// lower-colour neighbours (dep_lo / dep_hi [tile][colour], from sweep_plan)
+// through per-tile flags.  ctrl: 4 zeroed words kept with the flags; err: the
+// device error flag (kDevTimeout when a bounded wait ran out).
+constexpr int kSweepMaxColours = 32;
+struct SweepArgs {
+    int c_lo = 0, c_hi = 0;           // colours of this field step
+    int C = 0;                        // colours of the level (row length of dep_lo / dep_hi)
+    const int* colour_ptr = nullptr;  // [C + 1] first position of every colour in the node list
+    const int* tile_ptr = nullptr;    // [C + 1]
+    const int* dep_lo = nullptr;      // [tiles][C]
+    const int* dep_hi = nullptr;
+    unsigned* flags = nullptr;        // [tiles]
+    unsigned* ctrl = nullptr;         // ticket, exit count, epoch, spare
+    int* err = nullptr;
+};
+int sweep_tile_nodes(int fb);  // 0: no sweep kernel for this sub-block size
+// tiles = tiles of colours c_lo..c_hi-1; g4: four lanes per scalar row
+template <typename T>
+int launch_bgs_sweep(int b, int fb, const BgsArgs& a, const SweepArgs& sw, int tiles, int g4, cudaStream_t s);
+// ---- ILU(0) sub-solve in colour order (k_ilu.cu) ----
+// factors of every field's A_ff: lu[F][nnzb][fb][fb] (FP64), pos[n] receives
+// each node's position in the colour-ordered list; node_field (optional)
+// restricts every row to its node's field
+int ilu_factor(int n, int b, int fb, int F, long nnzb, int n_colours, const std::vector<int>& colour_ptr,
+               const int* nodes, const int* rp, const int* ci, const int* diag, const int* node_field,
+               const double* vals, int* pos, double* lu, int* err, cudaStream_t s);
+// upk[k] = 1 where block k's column has a higher colour (same node field)
+int launch_upper_flags(int n, const int* rp, const int* ci, const int* colour, const int* node_field,
+                       unsigned char* upk, cudaStream_t s);
+// one colour of the forward (y = L^{-1} r_f, r_f formed on the fly from
+// x_in, y to xt) or backward (x~ = U^{-1} y in xt, then x_out) solve of a
+// field step; lu = the field's plane of factors in the cycle type
+template <typename T>
+int launch_ilu_colour(int b, int fb, const BgsArgs& a, const T* lu, const int* diag, const unsigned char* upk,
+                      bool backward, cudaStream_t s);
+// ---- restricted Schwarz sub-solve on aggregates (k_schwarz.cu) ----
+struct SchwarzArgs {
+    int agg_lo = 0, agg_hi = 0;  // aggregates (subdomains) of this field step
+    int nfs = 1;                 // subdomains per aggregate: F (co-located fields) or 1 (node fields)
+    int b = 0, fb = 0;
+    const int* sd_ptr = nullptr;    // [n_agg + 1] node lists of the subdomains
+    const int* sd_nodes = nullptr;
+    const int* agg_ptr = nullptr;   // own nodes: the aggregate's members
+    const int* members = nullptr;
+    const long* x_off = nullptr;    // [n_agg * nfs + 1] offsets of the restricted inverses
+    const void* X = nullptr;        // own_rows x m per subdomain, column by column (cycle type)
+    const void* rf = nullptr;       // [n][fb] residual of the field
+};
+// node count of every subdomain (-1: more than the kernel takes)
+int schwarz_setup_count(int n_agg, const int* agg_ptr, const int* members, const int* rp, const int* ci,
+                        const int* node_field, int overlap, int* cnt, cudaStream_t s);
+// node lists and the FP64 restricted inverses of every (aggregate, field)
+int schwarz_setup_fill(int n_agg, int F, int b, int fb, int max_m, const int* agg_ptr, const int* members,
+                       const int* rp, const int* ci, const int* node_field, int overlap, const int* sd_ptr,
+                       int* sd_nodes, const double* vals, const long* x_off, double* X, int* err, cudaStream_t s);
+// rf = rhs_f - A_{f,*} (x_in + P uc) over n rows (x_in null: rhs_f)
+template <typename T>
+int launch_field_residual(int b, int fb, int fm, int n, int field, const int* rp, const int* ci, const T* vals,
+                          const T* x_in, const T* uc, const int* agg, const T* rhs, T* rf, cudaStream_t s);
+template <typename T>
+int launch_schwarz_apply(const SchwarzArgs& sa, const BgsArgs& a, cudaStream_t s);
+// dependencies of every tile (tile_of: scratch of n ints)
+int sweep_plan(int n, int C, int ntile, const int* nodes, const int* colour, const int* colour_ptr,
+               const int* tile_ptr, const int* rp, const int* ci, const unsigned char* lowk, int n_tiles,
+               int* tile_of, int* dep_lo, int* dep_hi, cudaStream_t s);
 template <typename T>
 int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
                     const T* rhs, T* y, cudaStream_t s);
@@ -352,10 +425,14 @@ int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int
 // each, no initial contents needed), out[0] = colour count, out[1] = 1 on
 // failure (a colour above 254 or an inconsistent pattern).  Dynamic shared
 // memory: 5 * n + 16 bytes.
+// pre_err (optional, device): a flag that a pattern check launched before
+// this kernel set to nonzero; the kernel then reads no row and reports
+// failure.
 constexpr int kWorklistMaxNodes = 40000;
+constexpr int kWorklistSmemMax = kWorklistMaxNodes * 5 + 16;  // dynamic shared memory limit set on the kernel
 __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                        int* __restrict__ colour, int* __restrict__ qa, int* __restrict__ qb,
-                                       int* __restrict__ out);
+                                       int* __restrict__ out, const int* __restrict__ pre_err);
 // d_queue: 2n device ints of scratch (nullptr: always use the multi-launch rounds)
 int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
                  cudaStream_t s, int* n_colours, int* rounds_out, int* d_queue);
@@ -475,12 +552,15 @@ struct GivensArgs {
     double* scal;      // {h_{j+1,j}, |g_{j+1}|, breakdown, ||w|| before}
 };
 // out[v] = x . Y_v (v < nv) and, if want_xx, out[nv] = x . x; deterministic chunked sums
+// (cond: run only where *cond is nonzero; null = always)
 int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx, double* partial,
-                     double* out, unsigned* ticket, cudaStream_t s);
+                     double* out, unsigned* ticket, cudaStream_t s, const unsigned* cond = nullptr);
 // x -= sign * sum_v h[v] Y_v; then mode 1: out[v] = x . Y_v, mode 2: out[0] = x . x (+ Givens if ga),
-// mode 0: nothing
+// mode 3: as 2, and *reorth = 1 when ||x||^2 < 0.5 * ga.h1[j+1] (a second projection is due; its
+// passes carry cond = reorth), else *reorth = 0, h2 = 0 and the Givens update; mode 0: nothing
 int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign, int mode,
-                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s);
+                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s,
+                    const unsigned* cond = nullptr, unsigned* reorth = nullptr);
 int launch_solve_upper(int k, int m, const double* H, const double* g, double* y, cudaStream_t s);
 int launch_scale(long N, const double* x, const double* scal, double* y, int check_breakdown, cudaStream_t s);
 int launch_init_g(int m, const double* bsq, double* g, double* scal, cudaStream_t s);

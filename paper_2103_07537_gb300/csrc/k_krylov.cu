@@ -17,6 +17,7 @@ namespace bamg {
 
 constexpr int kKThreads = 256;
 constexpr int kDotGroup = 16;  // dot products accumulated together per pass
+constexpr double kReorthRatio = 0.5;  // ||w1||^2 / ||w||^2 below which an Arnoldi step projects again
 
 // fixed chunking of a vector of length N: at least 256 elements per chunk, at
 // most two CTAs per SM of the GB300 (152 SMs).  The basis vectors are mostly
@@ -138,7 +139,9 @@ __device__ void givens_update(const GivensArgs& a, double wsq) {
 __global__ void __launch_bounds__(kKThreads) multi_dot_kernel(long N, const double* __restrict__ x,
                                                               const double* __restrict__ Y, long ld, int nv,
                                                               int want_xx, double* __restrict__ partial,
-                                                              double* __restrict__ out, unsigned* ticket) {
+                                                              double* __restrict__ out, unsigned* ticket,
+                                                              const unsigned* cond) {
+    if (cond && __ldcg(cond) == 0u) return;  // a conditional pass that is not needed (every CTA)
     long e0, e1;
     chunk_range(N, &e0, &e1);
     chunk_dots(e0, e1, x, Y, ld, nv, want_xx, partial);
@@ -147,12 +150,16 @@ __global__ void __launch_bounds__(kKThreads) multi_dot_kernel(long N, const doub
 
 // x -= sign * sum_v h[v] Y_v over the chunk, then (mode 1) the dots of the new
 // x with Y_0..Y_{nv-1} into out, (mode 2) its squared norm into out (and the
-// Givens update when do_givens), (mode 0) nothing
+// Givens update when do_givens), (mode 3) as 2, with the reorthogonalisation
+// test of the Arnoldi step in the last CTA, (mode 0) nothing.  cond: the pass
+// runs only where *cond is nonzero.
 __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __restrict__ x,
                                                              const double* __restrict__ Y, long ld, int nv,
                                                              const double* __restrict__ h, double sign, int mode,
                                                              double* __restrict__ partial, double* __restrict__ out,
-                                                             unsigned* ticket, GivensArgs ga, int do_givens) {
+                                                             unsigned* ticket, GivensArgs ga, int do_givens,
+                                                             const unsigned* cond, unsigned* reorth) {
+    if (cond && __ldcg(cond) == 0u) return;
     __shared__ double sh_h[kMaxRestart + 1];
     for (int v = threadIdx.x; v < nv; v += blockDim.x) sh_h[v] = sign * h[v];
     __syncthreads();
@@ -180,7 +187,22 @@ __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __r
     else chunk_dots(e0, e1, x, Y, ld, 0, 1, partial);
     if (last_cta(ticket)) {
         finish_sums(mode == 1 ? nv : 1, partial, out);
-        if (do_givens) {
+        if (mode == 3) {
+            // one projection is enough when it kept at least half of ||w||^2
+            // (the DGKS test with eta = 1/sqrt(2)); otherwise the step projects
+            // again (the conditional passes) and its Givens update waits for it
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double w1 = __ldcg(out), w0 = __ldcg(ga.h1 + ga.j + 1);
+                const unsigned need = !(w1 >= kReorthRatio * w0);
+                *reorth = need;
+                if (!need) {
+                    double* h2 = const_cast<double*>(ga.h2);
+                    for (int i = 0; i <= ga.j; ++i) h2[i] = 0.0;
+                    givens_update(ga, w1);
+                }
+            }
+        } else if (do_givens) {
             __syncthreads();
             if (threadIdx.x == 0) givens_update(ga, __ldcg(out));
         }
@@ -188,16 +210,17 @@ __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __r
 }
 
 int launch_multi_dot(long N, const double* x, const double* Y, long ld, int nv, int want_xx, double* partial,
-                     double* out, unsigned* ticket, cudaStream_t s) {
-    multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial, out, ticket);
+                     double* out, unsigned* ticket, cudaStream_t s, const unsigned* cond) {
+    multi_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, want_xx, partial, out, ticket, cond);
     return launched(1);
 }
 int launch_axpy_dot(long N, double* x, const double* Y, long ld, int nv, const double* h, double sign, int mode,
-                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s) {
+                    double* partial, double* out, unsigned* ticket, const GivensArgs* ga, cudaStream_t s,
+                    const unsigned* cond, unsigned* reorth) {
     GivensArgs g{};
     if (ga) g = *ga;
     axpy_dot_kernel<<<krylov_chunks(N), kKThreads, 0, s>>>(N, x, Y, ld, nv, h, sign, mode, partial, out, ticket, g,
-                                                           ga ? 1 : 0);
+                                                           ga ? 1 : 0, cond, reorth);
     return launched(1);
 }
 

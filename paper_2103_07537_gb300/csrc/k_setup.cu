@@ -119,13 +119,19 @@ __device__ __forceinline__ int find_col(const int* __restrict__ ci, int k0, int 
     return -1;
 }
 
+// Row i of a BSR pattern: row bounds inside [0, rp[n]], columns in range and
+// strictly ascending, the diagonal block present, and every column j listing
+// i back (structural symmetry).  diag (optional) receives the position of the
+// diagonal block.  Rows of other threads are searched only inside clamped
+// bounds, so a malformed pattern is reported without reading outside it.
 __global__ void check_pattern_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                      int* __restrict__ diag, int* err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int nz = rp[n];
     const int k0 = rp[i], k1 = rp[i + 1];
     int d = -1;
-    if (k1 < k0) {
+    if (k0 < 0 || k1 < k0 || k1 > nz) {
         set_error(err, kDevBadPattern);
         return;
     }
@@ -136,13 +142,13 @@ __global__ void check_pattern_kernel(int n, const int* __restrict__ rp, const in
             return;
         }
         if (j == i) d = k;
-        else if (find_col(ci, rp[j], rp[j + 1], i) < 0) {
+        else if (find_col(ci, min(max(rp[j], 0), nz), min(max(rp[j + 1], 0), nz), i) < 0) {
             set_error(err, kDevBadPattern);
             return;
         }
     }
     if (d < 0) set_error(err, kDevBadPattern);
-    diag[i] = d;
+    if (diag) diag[i] = d;
 }
 
 int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* err, cudaStream_t s) {
@@ -379,10 +385,17 @@ __global__ void max_kernel(int n, const int* __restrict__ v, int* out) {
 // coloured (smallest colour unused by its lower-index neighbours) as soon as
 // its count of uncoloured lower-index neighbours reaches zero; the frontier
 // of such nodes advances one step per iteration.  Same result as the rounds.
+// The count of node j is taken from row j and decremented from the rows of
+// its lower neighbours, so the rule needs a structurally symmetric pattern.
+// A pattern that is not symmetric is reported (out[1] = 1), never coloured
+// silently: a count that goes below zero (a lower row lists j, row j does not
+// list it back), a node coloured while one of its lower neighbours is still
+// uncoloured, or a node left uncoloured at the end (row j lists a lower
+// neighbour whose row does not list j).
 __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int* __restrict__ rp,
                                                                const int* __restrict__ ci, int* __restrict__ colour,
                                                                int* __restrict__ qa, int* __restrict__ qb,
-                                                               int* __restrict__ out) {
+                                                               int* __restrict__ out, const int* __restrict__ pre_err) {
     extern __shared__ int smem_i[];
     int* cnt = smem_i;                                            // n
     unsigned char* col = reinterpret_cast<unsigned char*>(cnt + n);  // n
@@ -392,9 +405,17 @@ __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int*
         qn_cur = 0;
         qn_next = 0;
         cmax = -1;
-        bad = 0;
+        bad = pre_err && *pre_err != 0;  // a pattern check ahead of this launch failed
     }
     __syncthreads();
+    if (bad) {  // the rows are not read: every node uncoloured, failure reported
+        for (int i = tid; i < n; i += blockDim.x) colour[i] = -1;
+        if (tid == 0) {
+            out[0] = 0;
+            out[1] = 1;
+        }
+        return;
+    }
     for (int i = tid; i < n; i += blockDim.x) {
         int c = 0;
         for (int k = rp[i]; k < rp[i + 1]; ++k) c += ci[k] < i;
@@ -420,7 +441,7 @@ __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int*
             }
             int c = 0;
             while (c < 255 && (used[c >> 6] >> (c & 63) & 1ull)) ++c;
-            if (c >= 255) bad = 1;
+            if (c >= 255 || (used[3] >> 63 & 1ull)) bad = 1;  // colour 255 = a lower neighbour not yet coloured
             col[i] = (unsigned char)c;
             atomicMax(&cmax, c);
         }
@@ -429,7 +450,10 @@ __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int*
             const int i = cur[q];
             for (int k = rp[i]; k < rp[i + 1]; ++k) {
                 const int j = ci[k];
-                if (j > i && atomicSub(&cnt[j], 1) == 1) nxt[atomicAdd(&qn_next, 1)] = j;
+                if (j <= i) continue;
+                const int before = atomicSub(&cnt[j], 1);
+                if (before == 1) nxt[atomicAdd(&qn_next, 1)] = j;
+                else if (before < 1) bad = 1;  // row j does not list i
             }
         }
         __syncthreads();
@@ -442,7 +466,13 @@ __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int*
         nxt = t;
         __syncthreads();
     }
-    for (int i = tid; i < n; i += blockDim.x) colour[i] = col[i] == 255 ? -1 : col[i];
+    int left = 0;  // nodes this thread finds uncoloured
+    for (int i = tid; i < n; i += blockDim.x) {
+        left += col[i] == 255;
+        colour[i] = col[i] == 255 ? -1 : col[i];
+    }
+    if (left) bad = 1;
+    __syncthreads();
     if (tid == 0) {
         out[0] = cmax + 1;
         out[1] = bad || qn_cur != 0;
@@ -455,9 +485,13 @@ int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, 
     const int threads = 256, blocks = ceil_div(n, threads);
     if (n <= kWorklistMaxNodes && d_queue) {
         const size_t smem = (size_t)n * 5 + 16;
+        // the limit is always raised to what the largest accepted graph needs,
+        // never to this call's size: amg_colour_noalloc launches the same
+        // kernel after raising it once per device, and a lower limit set here
+        // would make its next launch on a larger graph fail
         BAMG_CUDA_TRY(cudaFuncSetAttribute(colour_worklist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        colour_worklist_kernel<<<1, 1024, smem, s>>>(n, rp, ci, colour, d_queue, d_queue + n, d_flag);
+                                           kWorklistSmemMax));
+        colour_worklist_kernel<<<1, 1024, smem, s>>>(n, rp, ci, colour, d_queue, d_queue + n, d_flag, nullptr);
         note_launch(1);
         BAMG_CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));

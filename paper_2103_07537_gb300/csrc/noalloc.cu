@@ -14,9 +14,9 @@
 namespace bamg {
 namespace {
 
-// Scratch: two queues of kWorklistMaxNodes ints and two result ints
-// (320,016 bytes).  Every GPU that loads the library holds it until the
-// process exits; every call on a device shares it.
+// Scratch: two queues of kWorklistMaxNodes ints, two result ints and the
+// pattern-check flag (320,016 bytes).  Every GPU that loads the library holds
+// it until the process exits; every call on a device shares it.
 constexpr int kNoAllocScratchInts = 2 * kWorklistMaxNodes + 4;
 static __device__ __align__(256) int g_colour_scratch[kNoAllocScratchInts];
 
@@ -26,7 +26,10 @@ int* g_scratch_ptr[kMaxDev] = {};  // device address of g_colour_scratch, per de
 
 // once per device, with that device current: the device address of the
 // scratch array (its host-side name is only a stand-in) and the kernel's
-// shared-memory limit
+// shared-memory limit (the same constant amg_setup sets, so neither lowers it
+// for the other).  The address is kept for the life of the process: after a
+// cudaDeviceReset the library's module is loaded again and the kept address
+// is stale, so the entry point must not be used after a reset.
 int scratch_for_current_device(int** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return BAMG_ECUDA;
@@ -35,7 +38,7 @@ int scratch_for_current_device(int** out) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_colour_scratch) != cudaSuccess || !p) return BAMG_ECUDA;
         if (cudaFuncSetAttribute(colour_worklist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kWorklistMaxNodes * 5 + 16) != cudaSuccess)
+                                 kWorklistSmemMax) != cudaSuccess)
             return BAMG_ECUDA;
         g_scratch_ptr[dev] = static_cast<int*>(p);
     }
@@ -63,9 +66,14 @@ extern "C" int amg_colour_noalloc(const int* row_ptr, const int* col_idx, int n_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* qa = scratch;
     int* qb = scratch + kWorklistMaxNodes;
-    int* res = scratch + 2 * kWorklistMaxNodes;
+    int* res = scratch + 2 * kWorklistMaxNodes;  // [0] colours, [1] failure, [2] pattern check
     const size_t smem = (size_t)n_nodes * 5 + 16;
-    colour_worklist_kernel<<<1, 1024, smem, s>>>(n_nodes, row_ptr, col_idx, colour, qa, qb, res);
+    // the worklist rule needs a valid, structurally symmetric pattern: check
+    // it on the whole GPU first (the flag starts at zero on every call)
+    if (cudaMemsetAsync(res + 2, 0, sizeof(int), s) != cudaSuccess) return BAMG_ECUDA;
+    const int st_chk = launch_check_pattern(n_nodes, row_ptr, col_idx, nullptr, res + 2, s);
+    if (st_chk != BAMG_OK) return st_chk;
+    colour_worklist_kernel<<<1, 1024, smem, s>>>(n_nodes, row_ptr, col_idx, colour, qa, qb, res, res + 2);
     publish_count_kernel<<<1, 32, 0, s>>>(res, n_colours);
     return launched(2);
 }

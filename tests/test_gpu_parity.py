@@ -251,11 +251,12 @@ def test_vcycle_graph_and_direct_launch_agree_bitwise_and_repeat():
 # ---------------------------------------------------------------------------
 # FGMRES
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("ortho", [0, 1])  # second projection where the DGKS test asks / at every step
 @pytest.mark.parametrize("name,restart", [("stokes2d_32", 30), ("mhd2d_16", 30), ("mhd2d_41_ragged", 10),
-                                          ("random_b4_f2", 5)])
-def test_fgmres_iterations_match_oracle(name, restart):
+                                          ("random_b4_f2", 5), ("stokes3d_9", 50)])
+def test_fgmres_iterations_match_oracle(name, restart, ortho):
     s, kw = SYSTEMS[name]()
-    g = make_solver(s, **kw)
+    g = make_solver(s, ortho=ortho, **kw)
     o = make_oracle(s, **kw)
     x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
     st, it, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=restart, max_iter=3000)
@@ -336,6 +337,17 @@ def test_invalid_inputs_are_rejected():
     k0 = s.row_ptr[7]
     ci_bad[k0], ci_bad[k0 + 1] = ci_bad[k0 + 1], ci_bad[k0]
     expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, dev(ci_bad), va, 6, s.field_of_dof, **kw))
+    # a block stored on one side only (row 20 lists node 3 and node 45, and
+    # neither lists 20 back): the pattern is not structurally symmetric
+    for j in (3, 45):
+        row = s.col_idx[s.row_ptr[20]:s.row_ptr[21]]
+        pos = s.row_ptr[20] + int(np.searchsorted(row, j))
+        ci_1 = np.insert(s.col_idx, pos, j).astype(np.int32)
+        va_1 = np.insert(s.vals, pos, 0.0, axis=0)
+        rp_1 = s.row_ptr.copy()
+        rp_1[21:] += 1
+        expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(dev(rp_1), dev(ci_1), dev(va_1.reshape(-1)), 6,
+                                                            s.field_of_dof, **kw))
     # singular node block of one field
     v_bad = s.vals.copy()
     diag = [k for k in range(s.row_ptr[9], s.row_ptr[10]) if s.col_idx[k] == 9][0]
