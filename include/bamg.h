@@ -73,7 +73,12 @@ typedef struct {
                          CTAs) and keep the fastest (default); 0 = warp-per-row everywhere;
                          2 = thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
                          4 = as 2 with four lanes per smoother row (each a quarter of the
-                         row's blocks); 1 also times the variants of 3 and 4                    */
+                         row's blocks); 1 also times the variants of 3 and 4, and the
+                         persistent sweep (see sweep). With 1 the choices are kept for the
+                         life of the process per level shape (device, sizes of the level and
+                         of its colours, block and field shape, precision, layout, launch mode,
+                         sub-solver): a later setup of a level of the same shape reuses them
+                         without timing (amg_stats: tune_cached)                               */
     /* ---- beyond the paper: smoothed transfers, per-node damping, learned weights ---- */
     int smooth_p;     /* 0: tentative P (default); 1: on every coarsened level the smoothed
                          P_f = (I - W_f D_ff^{-1} A_ff) P^_f per field (see amg_setup)        */

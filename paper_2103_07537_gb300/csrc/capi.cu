@@ -137,6 +137,7 @@ struct Level {
     unsigned *sw_flags = nullptr, *sw_ctrl = nullptr;
     // measured field-step times (us): per-colour launches, sweep, sweep with four lanes per row
     float tune_step_us[3] = {0, 0, 0};
+    int tune_cached = 0;  // the mappings came from an earlier tuning of the same level shape
     // ILU(0) sub-solve (sub_solver 1): factors [F][nnzb][fb][fb] in FP64 and in the cycle type,
     // elimination position of every node, higher-colour flag of every block
     double* ilu64 = nullptr;
@@ -715,6 +716,35 @@ static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int rep
     return first >= 40.0f ? first : timed(reps);
 }
 
+// Decisions of the autotuner, kept per process for every level shape they
+// were measured on: a later setup of a level with the same shape (the same
+// pattern again, as in a sequence of Newton or time steps) takes the
+// recorded mappings instead of timing the launches again.  Only the choice
+// of kernels is kept, never a value.  The key holds everything the choice
+// depends on: device, sizes of the level and of every colour, block shape,
+// fields, precision, value layout, launch mode and sub-solver.
+struct TuneRec {
+    int bgs_tpr, spmv_tpr, sweep;
+    float tune_us[6], tune_step_us[3];
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, TuneRec>> g_tune;  // small: one entry per distinct level shape
+std::vector<std::pair<std::string, int>> g_tune_outer;  // outer FP64 SpMV mapping per level-0 shape
+
+static std::string tune_key(const bamg_ctx* h, const Level& L, int l) {
+    int dev = -1;
+    cudaGetDevice(&dev);
+    std::string k = std::to_string(dev) + "/" + std::to_string(l) + "/" + std::to_string(L.n) + "/" +
+                    std::to_string(L.nnzb) + "/" + std::to_string(h->b) + "/" + std::to_string(h->fb) + "/" +
+                    std::to_string(h->nf) + "/" + std::to_string(h->nsys) + "/" + std::to_string(h->p.cycle_prec) +
+                    "/" + std::to_string(L.fm) + "/" + std::to_string(h->p.use_pdl) + "/" +
+                    std::to_string(h->p.sub_solver) + "/" + std::to_string(h->p.sweep) + "/" +
+                    std::to_string(L.sw_tiles) + "/" +
+                    std::to_string(L.omega_s64 != nullptr) + "/";
+    for (int c = 0; c <= L.n_colours; ++c) k += std::to_string(L.colour_ptr[c]) + ",";
+    return k;
+}
+
 // Autotuner: per level, time the row mappings of the smoother (first colour,
 // first field) and of the residual SpMV on the level's own operator, and keep
 // the faster; likewise for the FP64 outer SpMV.  (Timing whole sweeps instead
@@ -727,6 +757,25 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
     const int b = h->b;
     for (int l = 0; l + 1 < h->nlev; ++l) {
         Level& L = h->lev[l];
+        const std::string key = h->p.autotune == 1 ? tune_key(h, L, l) : std::string();
+        if (h->p.autotune == 1) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            bool hit = false;
+            for (const auto& e : g_tune)
+                if (e.first == key) {
+                    L.bgs_tpr = e.second.bgs_tpr;
+                    L.spmv_tpr = e.second.spmv_tpr;
+                    L.sweep = e.second.sweep;
+                    memcpy(L.tune_us, e.second.tune_us, sizeof L.tune_us);
+                    memcpy(L.tune_step_us, e.second.tune_step_us, sizeof L.tune_step_us);
+                    hit = true;
+                    break;
+                }
+            if (hit) {
+                L.tune_cached = 1;
+                continue;
+            }
+        }
         const size_t nb = (size_t)L.n * b;
         BAMG_CUDA_TRY(cudaMemsetAsync(L.xa, 0, nb * sizeof(T), s));
         BAMG_CUDA_TRY(cudaMemsetAsync(L.res, 0, nb * sizeof(T), s));
@@ -814,8 +863,32 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             L.sweep = L.tune_step_us[best] < kTuneMargin * L.tune_step_us[0] ? best : 0;
             TRY(check_dev(h, s));
         }
+        if (h->p.autotune == 1) {
+            TuneRec rec;
+            rec.bgs_tpr = L.bgs_tpr;
+            rec.spmv_tpr = L.spmv_tpr;
+            rec.sweep = L.sweep;
+            memcpy(rec.tune_us, L.tune_us, sizeof rec.tune_us);
+            memcpy(rec.tune_step_us, L.tune_step_us, sizeof rec.tune_step_us);
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_tune.size() < 4096) g_tune.emplace_back(key, rec);
+        }
     }
-    {
+    int outer_cached = -1;
+    std::string okey;
+    if (h->p.autotune == 1) {
+        int dev = -1;
+        cudaGetDevice(&dev);
+        const Level& L0 = h->lev[0];
+        okey = std::to_string(dev) + "/" + std::to_string(L0.n) + "/" + std::to_string(L0.nnzb) + "/" +
+               std::to_string(b) + "/" + std::to_string(h->nsys);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& e : g_tune_outer)
+            if (e.first == okey) outer_cached = e.second;
+    }
+    if (outer_cached >= 0) {
+        h->outer_spmv_tpr = outer_cached;
+    } else {
         const Level& L0 = h->lev[0];
         BAMG_CUDA_TRY(cudaMemsetAsync(h->cyc_in, 0, sizeof(double) * (size_t)L0.n * b, s));
         const float t0 = time_launch(s, e0, e1, 10, [&] {
@@ -826,6 +899,10 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
                                            s);
         });
         h->outer_spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && t1 < kTuneMargin * t0);
+        if (h->p.autotune == 1) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_tune_outer.size() < 4096) g_tune_outer.emplace_back(okey, h->outer_spmv_tpr);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2377,7 +2454,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
                                           : L.bgs_tpr == 2 ? "thread-half"
                                           : L.bgs_tpr      ? "thread"
                                                            : "warp") +
-             "\",\"sweep_tiles\":" + std::to_string(L.sw_tiles) + ",\"tune_step_us\":[" +
+             "\",\"sweep_tiles\":" + std::to_string(L.sw_tiles) + ",\"tune_cached\":" +
+             std::to_string(L.tune_cached) + ",\"tune_step_us\":[" +
              std::to_string(L.tune_step_us[0]) + "," + std::to_string(L.tune_step_us[1]) + "," +
              std::to_string(L.tune_step_us[2]) + "]" + ",\"residual_mapping\":\"" +
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +

@@ -17,7 +17,9 @@ namespace bamg {
 
 constexpr int kKThreads = 256;
 constexpr int kDotGroup = 16;  // dot products accumulated together per pass
-constexpr double kReorthRatio = 0.5;  // ||w1||^2 / ||w||^2 below which an Arnoldi step projects again
+// ||w1||^2 / ||w||^2 below which an Arnoldi step projects a second time
+// (eta = 0.01: the first projection removed more than 99.99% of ||w||^2)
+constexpr double kReorthRatio = 1e-4;
 
 // fixed chunking of a vector of length N: at least 256 elements per chunk, at
 // most two CTAs per SM of the GB300 (152 SMs).  The basis vectors are mostly
@@ -188,8 +190,8 @@ __global__ void __launch_bounds__(kKThreads) axpy_dot_kernel(long N, double* __r
     if (last_cta(ticket)) {
         finish_sums(mode == 1 ? nv : 1, partial, out);
         if (mode == 3) {
-            // one projection is enough when it kept at least half of ||w||^2
-            // (the DGKS test with eta = 1/sqrt(2)); otherwise the step projects
+            // one projection is enough unless it removed nearly all of w
+            // (||w1|| < eta ||w||, eta = 0.01); otherwise the step projects
             // again (the conditional passes) and its Givens update waits for it
             __syncthreads();
             if (threadIdx.x == 0) {

@@ -20,7 +20,8 @@
 // the control words need no clearing between launches or graph replays.  x~
 // written in the launch is read through L2 (ld.global.cg); the producer
 // orders its writes before the flag by a barrier and a fence (as a grid
-// barrier does), the consumer by an acquire load, a fence and a barrier.
+// barrier does), the consumer's polling warp by a fence after the flags, and
+// the CTA by a barrier.
 // The arithmetic per node is that of the thread-per-row kernel of k_solve.cu
 // (same sums in the same order), so the sweep gives the same values.
 #include "bgs_body.cuh"
@@ -28,7 +29,7 @@
 
 namespace bamg {
 
-constexpr long kSweepSpins = 1L << 22;  // polls of one flag (an L2 round trip each): about a second
+constexpr long kSweepSpins = 1L << 22;  // polls of one flag (a 64 ns sleep and an L2 round trip each): seconds
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -103,22 +104,28 @@ __global__ void __launch_bounds__(SweepShape<FB>::kThreads) bgs_sweep_kernel(Bgs
             s_hi[tid] = __ldg(sw.dep_hi + (size_t)tile * sw.C + sw.c_lo + tid);
         }
         __syncthreads();
-        // wait for the tiles of the lower-colour neighbours (each thread a
-        // share of the flags; a timeout anywhere ends every wait)
-        for (int cc = 0; cc < cl; ++cc) {
-            const int lo = s_lo[cc], hi = s_hi[cc];
-            for (int q = lo + tid; q <= hi; q += NT) {
-                long spins = 0;
-                while (ld_acquire_u32(sw.flags + q) != want) {
-                    if (++spins > kSweepSpins) {
-                        set_error(sw.err, kDevTimeout);
-                        break;
+        // wait for the tiles of the lower-colour neighbours: the first warp
+        // polls (relaxed loads, each lane a share of the flags, a short sleep
+        // between polls so that the waiting CTAs do not flood L2), then one
+        // fence orders the flags before the CTA's reads; a timeout anywhere
+        // ends every wait
+        if (tid < 32) {
+            for (int cc = 0; cc < cl; ++cc) {
+                const int lo = s_lo[cc], hi = s_hi[cc];
+                for (int q = lo + tid; q <= hi; q += 32) {
+                    long spins = 0;
+                    while (*reinterpret_cast<volatile const unsigned*>(sw.flags + q) != want) {
+                        if (++spins > kSweepSpins) {
+                            set_error(sw.err, kDevTimeout);
+                            break;
+                        }
+                        if ((spins & 255) == 0 && *reinterpret_cast<volatile int*>(sw.err) != 0) break;
+                        __nanosleep(64);
                     }
-                    if ((spins & 1023) == 0 && *reinterpret_cast<volatile int*>(sw.err) != 0) break;
                 }
             }
+            __threadfence();
         }
-        __threadfence();
         __syncthreads();
         const int pos0 = s_cptr[cl] + (tile - s_tptr[cl]) * NTILE;
         const int pend = s_cptr[cl + 1];

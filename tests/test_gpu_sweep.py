@@ -173,3 +173,24 @@ def test_sweep_parameter_is_validated():
     with pytest.raises(bamg.BamgError) as e:
         make_solver(s, sweep=4, max_levels=2, max_coarse=0)
     assert e.value.status == bamg.BAMG_EINVAL
+
+
+def test_tuning_is_reused_for_the_same_level_shape():
+    s = P.stokes3d(24, 3)
+    kw = dict(max_levels=3, max_coarse=0, cycle_prec=32)
+    g1 = make_solver(s, **kw)
+    g2 = make_solver(s, **kw)
+    l1, l2 = g1.stats()["levels"][:-1], g2.stats()["levels"][:-1]
+    assert all(lv["tune_cached"] == 1 for lv in l2)
+    for a, b in zip(l1, l2):
+        assert a["smoother_mapping"] == b["smoother_mapping"] and a["residual_mapping"] == b["residual_mapping"]
+        assert a["tune_us"] == b["tune_us"]
+    r = dev(np.random.default_rng(4).standard_normal(s.n_unknowns))
+    z1, z2 = torch.empty_like(r), torch.empty_like(r)
+    g1.apply(r, z1)
+    g2.apply(r, z2)
+    torch.cuda.synchronize()
+    assert torch.equal(z1, z2)
+    # a forced launch mode is not overridden by an earlier tuning of the shape
+    g3 = make_solver(s, sweep=2, **kw)
+    assert all(lv["smoother_mapping"] == "sweep" for lv in g3.stats()["levels"][:-1])
