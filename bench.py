@@ -56,7 +56,7 @@ SMS = 152
 WORKLOADS = {
     "mhd2d_128": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d(128, seed),
-        levels=4, max_coarse=0, restart=30, prec=64,
+        levels=4, max_coarse=0, restart=30, prec=64, sub_solver_variants=True,
         desc="2D coupled 4-field Q1 system (u,v,p | Bx,By,psi), 128x128 cells, 6 dofs/node, 99,846 unknowns, "
              "148,225 blocks, nu/eta log-U[1e-3,1], FP64 V(1,1) BGS omega=0.5, 4 levels, FGMRES(30) to 1e-8"),
     "stokes2d_32": dict(
@@ -82,7 +82,7 @@ WORKLOADS = {
              "FP32"),
     "mhd2d_q2q1_128": dict(
         make=lambda seed: __import__("paper_2103_07537_gb300.problems", fromlist=["x"]).mhd2d_q2q1(128, seed),
-        levels=4, max_coarse=0, restart=30, prec=64, omega=0.6, cpu_sample_iters=5,
+        levels=4, max_coarse=0, restart=30, prec=64, omega=0.6, cpu_sample_iters=5, sub_solver_variants=True,
         desc="2D coupled system on mixed elements: (u,v,p) on 66,049 Q2 nodes, (Bx,By,psi) on 16,641 Q1 vertices "
              "(128x128 cells, 248,070 unknowns), 3 dofs/node, separate aggregation per field block, FP64 V(1,1) "
              "BGS omega=0.6 with the node fields as field blocks, 4 levels, FGMRES(30) to 1e-8"),
@@ -539,6 +539,40 @@ def run_ours(args):
             variant["vcycle_rel_diff_vs_fp64"] = None
     if learned and variant:
         variant["cycle"] = f"learned damping, {variant['cycle']}"
+    # --- the paper's sub-solvers of Algorithm 1 against the multicolour sweep -------
+    sub_solvers = None
+    if wl.get("sub_solver_variants") and not args.no_variants:
+        sub_solvers = {"multicolour_sweep": {"value": value, "unit": UNIT, "iterations": iters, "relres": relres,
+                                             "vcycle_ms": statistics.median(vt), "cycle_prec": main_prec}}
+        for key, sub in (("ilu0_colour_order", 1), ("restricted_schwarz_overlap1", 2)):
+            for prec in (main_prec, other_prec):
+                pp = bamg.amg_default_params(max_levels=wl["levels"], max_coarse=wl["max_coarse"], cycle_prec=prec,
+                                             omega=wl.get("omega", 0.5), sub_solver=sub, use_pdl=args.pdl)
+                name = key if prec == main_prec else f"{key}_fp{prec}"
+                try:
+                    step(pp)
+                    ms_v, (st_v, it_v, rr_v, _) = timed(pp, k_o)
+                    hh_ = setup(pp)
+                    try:
+                        zz = torch.empty_like(b)
+                        for _ in range(3):
+                            bamg.amg_apply(hh_, b, zz, stream)
+                        ts_ = []
+                        for _ in range(10):
+                            e0 = torch.cuda.Event(enable_timing=True)
+                            e1 = torch.cuda.Event(enable_timing=True)
+                            e0.record(stream)
+                            bamg.amg_apply(hh_, b, zz, stream)
+                            e1.record(stream)
+                            e1.synchronize()
+                            ts_.append(e0.elapsed_time(e1))
+                    finally:
+                        bamg.amg_destroy(hh_)
+                    sub_solvers[name] = {"value": timed.solved / (ms_v / 1e3), "unit": UNIT, "iterations": it_v,
+                                         "relres": rr_v, "converged": st_v == 0,
+                                         "vcycle_ms": statistics.median(ts_), "cycle_prec": prec}
+                except Exception as exc:  # reported, not fatal
+                    sub_solvers[name] = {"error": str(exc)[:200]}
     # --- FP32 cycle with a smoothed prolongator, P / R values in FP32 or BF16 ------
     pr_variants = None
     if wl.get("pr_variants") and not args.no_variants and main_prec == 32:
@@ -836,7 +870,7 @@ def run_ours(args):
                 "cycle_prec": main_prec, "coarse_prec": coarse_prec,
                 "use_pdl": 0 if stats.get("node_fields", 1) > 1 else args.pdl,
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
-                         "cluster": stats.get("tail_cluster")}, "variant": variant, "pr_variants": pr_variants,
+                         "cluster": stats.get("tail_cluster")}, "variant": variant, "pr_variants": pr_variants, "sub_solvers": sub_solvers,
                 "plain": plain,
                 "kernels": ksum, "roofline": roofline,
                 "clocks": clocks,
