@@ -73,7 +73,10 @@ typedef struct {
                          CTAs) and keep the fastest (default); 0 = warp-per-row everywhere;
                          2 = thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
                          4 = as 2 with four lanes per smoother row (each a quarter of the
-                         row's blocks); 1 also times the variants of 3 and 4, and the
+                         row's blocks); 5 = as 4 with every node's row staged in shared memory
+                         by asynchronous copies ahead of use (levels whose steps read whole blocks:
+                         one field, or the field-major layout; elsewhere 4; the same values
+                         as 4 bit for bit); 1 also times the variants of 3, 4 and 5, and the
                          persistent sweep (see sweep). With 1 the choices are kept for the
                          life of the process per level shape (device, sizes of the level and
                          of its colours, block and field shape, precision, layout, launch mode,

@@ -123,10 +123,13 @@ struct Level {
     void *xa = nullptr, *xb = nullptr, *xt = nullptr, *res = nullptr, *rhs = nullptr, *uc = nullptr;
     int agg_rounds = 0, colour_rounds = 0;
     // row mapping chosen for this level: smoother 0 warp per node, 1 thread per row, 2 thread per
-    // row in half-size CTAs, 3 four lanes per row; residual 0 warp per row, 1 thread per row
+    // row in half-size CTAs, 3 four lanes per row, 4 four lanes per row with the rows staged in
+    // shared memory by asynchronous copies (steps from a zero iterate use 3); residual 0 warp per
+    // row, 1 thread per row
     int bgs_tpr = 0, spmv_tpr = 0;
     // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split
-    float tune_us[6] = {0, 0, 0, 0, 0, 0};
+    float tune_us[7] = {0, 0, 0, 0, 0, 0, 0};
+    int max_row = 0;  // stored blocks in the longest row (the staged smoother's slot size)
     // persistent sweep: 0 = one launch per colour (bgs_tpr), 1 = every colour of a field step
     // in one launch (thread per row), 2 = the same with four lanes per row; the plan exists
     // when sw_tiles > 0
@@ -275,12 +278,14 @@ struct bamg_ctx {
 
     cudaStream_t stream = nullptr;  // the setup stream: allocations and frees are ordered on it
 
+    // every buffer carries 64 bytes beyond its size: the asynchronous copies
+    // of the staged smoother read whole 16-byte units around a row (see k_staged.cu)
     template <typename T>
     int alloc(T** ptr, size_t count) {
         *ptr = nullptr;
         if (count == 0) count = 1;
         void* q = nullptr;
-        if (pool_alloc(&q, count * sizeof(T), stream) != cudaSuccess) return BAMG_ECUDA;
+        if (pool_alloc(&q, count * sizeof(T) + 64, stream) != cudaSuccess) return BAMG_ECUDA;
         allocs.push_back(q);
         bytes += (long)(count * sizeof(T));
         *ptr = static_cast<T*>(q);
@@ -693,6 +698,17 @@ static SweepArgs sweep_args(bamg_ctx* h, const Level& L, int c_lo, int c_hi) {
     return sw;
 }
 
+// one colour of a field step in the level's row mapping (the staged kernel
+// for steps that read whole rows; from a zero iterate its four-lanes twin,
+// which gives the same values)
+template <typename T>
+static int launch_colour_step(bamg_ctx* h, const Level& L, const BgsArgs& a, cudaStream_t s) {
+    if (L.bgs_tpr == 4 && a.x_in) return launch_bgs_colour_staged<T>(h->b, h->fb, a, L.max_row, h->d_err, s);
+    if (L.bgs_tpr == 4) return launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, 2);
+    return L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr - 1)
+                     : launch_bgs_colour<T>(h->b, h->fb, a, s);
+}
+
 // a non-default row mapping must beat warp-per-row by more than 3%
 constexpr float kTuneMargin = 0.97f;
 
@@ -725,7 +741,7 @@ static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int rep
 // fields, precision, value layout, launch mode and sub-solver.
 struct TuneRec {
     int bgs_tpr, spmv_tpr, sweep;
-    float tune_us[6], tune_step_us[3];
+    float tune_us[7], tune_step_us[3];
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, TuneRec>> g_tune;  // small: one entry per distinct level shape
@@ -809,6 +825,8 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         L.tune_us[1] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 0); });
         L.tune_us[4] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 1); });
         L.tune_us[5] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 2); });
+        L.tune_us[6] = time_launch(s, e0, e1, reps,
+                                   [&] { return launch_bgs_colour_staged<T>(b, h->fb, a, L.max_row, h->d_err, s); });
         const T* x = static_cast<const T*>(L.xa);
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
@@ -825,12 +843,13 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         if (h->p.autotune >= 2) L.bgs_tpr = h->p.autotune - 1;
         else if (h->p.autotune == 1) {
             // the fastest thread-per-row variant replaces warp per node only by the margin
-            const float tv[3] = {L.tune_us[1], L.tune_us[4], L.tune_us[5]};
+            const float tv[4] = {L.tune_us[1], L.tune_us[4], L.tune_us[5], L.tune_us[6]};
             int best = 0;
-            for (int v = 1; v < 3; ++v)
+            for (int v = 1; v < 4; ++v)
                 if (tv[v] < tv[best]) best = v;
             L.bgs_tpr = tv[best] < kTuneMargin * L.tune_us[0] ? best + 1 : 0;
         }
+        if (L.bgs_tpr == 4 && L.tune_us[6] >= 1e29f) L.bgs_tpr = 3;  // the staged kernel does not take this level
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
         // one whole field step (every colour of field 0) as per-colour launches
         // in the chosen mapping against the persistent sweep, in the cycle's
@@ -844,8 +863,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
                     ac.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
                     ac.nodes = L.colour_nodes + L.colour_ptr[c];
                     ac.colour = c;
-                    const int st = L.bgs_tpr ? launch_bgs_colour_tpr<T>(b, h->fb, ac, s, L.bgs_tpr - 1)
-                                             : launch_bgs_colour<T>(b, h->fb, ac, s);
+                    const int st = launch_colour_step<T>(h, L, ac, s);
                     if (st != BAMG_OK) return st;
                 }
                 return (int)BAMG_OK;
@@ -1154,6 +1172,15 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         if (h->nf > 1) TRY(field_lower_flags(L.n, L.rp, L.ci, L.colour, L.node_field, L.lowk, s));
         else TRY(launch_lower_flags(L.n, L.rp, L.ci, L.colour, L.lowk, s));
         TRY(build_sweep_plan(h, L, s));
+        {
+            int* mr = nullptr;
+            TRY(h->alloc(&mr, 1));
+            TRY(launch_row_len_max(L.n, L.rp, mr, s));
+            BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, mr, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+            L.max_row = h->h_pin[0];
+            h->release(mr);
+        }
         h->t_phase[3] += ms_since(tp);
         tp = Clock::now();
         if (!L.dinv64) {  // (already there when P was smoothed)
@@ -1344,7 +1371,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 4 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        prm.autotune < 0 || prm.autotune > 5 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
@@ -1677,9 +1704,7 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
             record(h, ph, bytes, flops);
             continue;
         }
-        PL(BAMG_K_SMOOTH, bytes, flops,
-           L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr - 1)
-                     : launch_bgs_colour<T>(h->b, h->fb, a, s));
+        PL(BAMG_K_SMOOTH, bytes, flops, launch_colour_step<T>(h, L, a, s));
     }
     if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
     return BAMG_OK;
@@ -2450,6 +2475,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
              ",\"smoother_mapping\":\"" + (L.sweep == 2     ? "sweep-split"
                                           : L.sweep        ? "sweep"
+                                          : L.bgs_tpr == 4 ? "staged"
                                           : L.bgs_tpr == 3 ? "thread-split"
                                           : L.bgs_tpr == 2 ? "thread-half"
                                           : L.bgs_tpr      ? "thread"
@@ -2461,7 +2487,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
-             std::to_string(L.tune_us[5]) +
+             std::to_string(L.tune_us[5]) + "," + std::to_string(L.tune_us[6]) +
              "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0");
         if (h->nf > 1) {

@@ -282,6 +282,16 @@ template <typename T>
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
 
+// ---- colour step with the rows staged by asynchronous copies (k_staged.cu) ----
+// the four-lanes-per-row colour step with every node's values, columns and
+// lower-colour flags copied to shared memory ahead of use; max_row = the
+// level's longest row (blocks); BAMG_EUNSUPPORTED where the layout stages
+// more than the step reads (several fields, block-major values) or the slots
+// exceed shared memory
+template <typename T>
+int launch_bgs_colour_staged(int b, int fb, const BgsArgs& a, int max_row, int* err, cudaStream_t s);
+int launch_row_len_max(int n, const int* rp, int* out, cudaStream_t s);
+
 // ---- persistent multicolour sweep (k_sweep.cu) ----
 // Every colour c_lo..c_hi-1 of one field step in one launch: the colour-
 // ordered node list (BgsArgs.nodes = the level's whole list) is cut into

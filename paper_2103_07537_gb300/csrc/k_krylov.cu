@@ -38,28 +38,57 @@ __device__ __forceinline__ void chunk_range(long N, long* e0, long* e1) {
     *e1 = min(N, *e0 + per);
 }
 
+// Dots of x with G vectors over the chunk (G fixed at compile time, so every
+// issued FMA is a useful one: the FP64 pipe, 2 FMA per clock per SM on
+// GB300, bounds these passes): vector g is Y_{v0+g}, or x itself for the last
+// one when xx is set.  The block sums go to partial[(v0 + g) * nchunk + chunk].
+template <int G>
+__device__ __forceinline__ void chunk_dots_fixed(long e0, long e1, const double* __restrict__ x,
+                                                 const double* __restrict__ Y, long ld, int v0, bool xx,
+                                                 double* __restrict__ partial, double* sh) {
+    const double* yp[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) yp[g] = (xx && g == G - 1) ? x : Y + (size_t)(v0 + g) * ld;
+    double acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = 0.0;
+    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const double xe = x[e];
+        double yv[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) yv[g] = yp[g][e];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = fma(xe, yv[g], acc[g]);
+    }
+    // the block reduction works on a power-of-two width (its slices must tile
+    // the CTA): the G sums padded with zeros, of which only G are formed
+    constexpr int GP = G <= 1 ? 1 : G <= 2 ? 2 : G <= 4 ? 4 : G <= 8 ? 8 : 16;
+    double accp[GP];
+#pragma unroll
+    for (int g = 0; g < GP; ++g) accp[g] = g < G ? acc[g] : 0.0;
+    const double tot = block_sums<GP, kKThreads>(accp, G, sh);
+    if ((int)threadIdx.x < G) partial[(size_t)(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = tot;
+}
+
 // partial[v * nchunk + chunk] = sum_{e in chunk} x[e] * Y_v[e], v < nv, and
-// if want_xx, partial[nv * nchunk + chunk] = sum x[e]^2
+// if want_xx, partial[nv * nchunk + chunk] = sum x[e]^2: groups of kDotGroup
+// vectors, then one group of the remaining count
 __device__ void chunk_dots(long e0, long e1, const double* __restrict__ x, const double* __restrict__ Y,
                            long ld, int nv, int want_xx, double* __restrict__ partial) {
+    // sized for the widest reduction (kDotGroup): narrower ones need less
     __shared__ double sh[(kKThreads + kKThreads / kDotGroup) * (kDotGroup + 1)];
-    const int nchunk = gridDim.x;
-    for (int v0 = 0; v0 < nv + want_xx; v0 += kDotGroup) {
-        double acc[kDotGroup];
-#pragma unroll
-        for (int g = 0; g < kDotGroup; ++g) acc[g] = 0.0;
-        for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const double xe = x[e];
-#pragma unroll
-            for (int g = 0; g < kDotGroup; ++g) {
-                const int v = v0 + g;
-                if (v < nv) acc[g] = fma(xe, Y[(size_t)v * ld + e], acc[g]);
-                else if (v == nv && want_xx) acc[g] = fma(xe, xe, acc[g]);
-            }
-        }
-        const int gn = min(kDotGroup, nv + want_xx - v0);
-        const double tot = block_sums<kDotGroup, kKThreads>(acc, gn, sh);
-        if ((int)threadIdx.x < gn) partial[(size_t)(v0 + threadIdx.x) * nchunk + blockIdx.x] = tot;
+    const int tot = nv + want_xx;
+    int v0 = 0;
+    for (; v0 + kDotGroup <= tot; v0 += kDotGroup)
+        chunk_dots_fixed<kDotGroup>(e0, e1, x, Y, ld, v0, want_xx && v0 + kDotGroup == tot, partial, sh);
+    const bool xx = want_xx != 0;
+    switch (tot - v0) {
+#define REM(R) \
+    case R: chunk_dots_fixed<R>(e0, e1, x, Y, ld, v0, xx, partial, sh); break;
+        REM(1) REM(2) REM(3) REM(4) REM(5) REM(6) REM(7) REM(8) REM(9) REM(10) REM(11) REM(12) REM(13) REM(14)
+        REM(15)
+#undef REM
+        default: break;
     }
 }
 
