@@ -868,7 +868,7 @@ def run_ours(args):
                              "field_major": [lv.get("field_major") for lv in stats["levels"][:-1]]},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
                 "cycle_prec": main_prec, "coarse_prec": coarse_prec,
-                "use_pdl": 0 if stats.get("node_fields", 1) > 1 else args.pdl,
+                "use_pdl": args.pdl,
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
                          "cluster": stats.get("tail_cluster")}, "variant": variant, "pr_variants": pr_variants, "sub_solvers": sub_solvers,
                 "plain": plain,

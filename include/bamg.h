@@ -14,7 +14,9 @@
  * symmetric; vals[nnzb*b*b] FP64, each b x b block row-major.  The b dofs of a
  * node are interleaved in field order: field_of_dof[b] (HOST array) maps each
  * dof to its field block 0..F-1; it must be non-decreasing with all fields of
- * equal size (F = 1 or 2 with b in {3, 4, 6}, or F = 1 with b in {1, 2}).
+ * equal size fb = b / F, and (b, fb) one of: fb = b for b = 1..8 (one field),
+ * fb = 2 for b = 4, 6, 8, fb = 3 for b = 6, fb = 4 for b = 8
+ * (BAMG_EUNSUPPORTED otherwise).
  * Stored zeros count: the node graph is the stored pattern.
  *
  * Vectors are FP64, n_nodes*b entries, node-major (dof d of node i at

@@ -38,10 +38,12 @@ extern "C" {
  *   A_gg, field g's after those of fields 0..g-1.  Algorithm 1 (Sec. 4.3.2)
  *   takes the node fields as its field blocks: one field step updates the
  *   nodes of one field from the residual of its rows, with one multicolour
- *   node-block Gauss-Seidel sweep on A_gg as the approximate sub-solve.
+ *   node-block Gauss-Seidel sweep on A_gg (or sub_solver's ILU(0) or
+ *   restricted Schwarz) as the approximate sub-solve; the other fields'
+ *   nodes are copied by a kernel of the cycle.
  *   p: as in amg_setup, with smooth_p = 0, no weight arrays and no mlp
- *   (BAMG_EINVAL otherwise); use_pdl, tail_dofs and tail_grid are ignored
- *   (the cycle's field steps end with plain copies).
+ *   (BAMG_EINVAL otherwise); tail_dofs and tail_grid are ignored (the
+ *   single-launch tail records no copies of the other fields' nodes).
  *   n_fields = 1 builds the same hierarchy as amg_setup with one field.
  *   Errors: BAMG_EINVAL for bad ranges or parameters, the other statuses as
  *   for amg_setup; *out is NULL after an error.

@@ -200,8 +200,10 @@ int map_dev_error(int code) {
 
 bool supported_block(int b, int fb) {
     switch (b * 16 + fb) {
-        case 1 * 16 + 1: case 2 * 16 + 2: case 3 * 16 + 3: case 4 * 16 + 4:
-        case 4 * 16 + 2: case 6 * 16 + 6: case 6 * 16 + 3: return true;
+#define CASE(BB, FF) case BB * 16 + FF:
+        BAMG_BLOCK_SHAPES(CASE)
+#undef CASE
+        return true;
         default: return false;
     }
 }
@@ -1410,10 +1412,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
             return BAMG_EINVAL;
         for (int g = 0; g < nf; ++g)
             if (field_node_off[g + 1] <= field_node_off[g]) return BAMG_EINVAL;
-        // a field step ends with plain copies of the other fields' nodes; the
-        // cycle's kernels are then launched without programmatic dependence
-        // and without the single-launch tail
-        prm.use_pdl = 0;
+        // the single-launch tail records no copies of the other fields' nodes
         prm.tail_dofs = 0;
         prm.tail_grid = 0;
     }
@@ -1509,13 +1508,11 @@ static int other_fields(bamg_ctx* h, const Level& L, int f, const T* x_in, T* x_
     for (int g = 0; g < h->nf; ++g) {
         if (g == f) continue;
         const int n_g = L.fo[g + 1] - L.fo[g];
-        const size_t e0 = (size_t)L.fo[g] * b, ne = (size_t)n_g * b;
-        if (!x_in) {
-            BAMG_CUDA_TRY(cudaMemsetAsync(x_out + e0, 0, sizeof(T) * ne, s));
-            continue;
-        }
-        BAMG_CUDA_TRY(cudaMemcpyAsync(x_out + e0, x_in + e0, sizeof(T) * ne, cudaMemcpyDeviceToDevice, s));
-        if (uc) TRY(launch_prolong<T>(b, n_g, L.agg + L.fo[g], uc, x_out + e0, s));
+        const size_t e0 = (size_t)L.fo[g] * b;
+        // one kernel (copy, plus the coarse correction in the first
+        // post-smoothing step): launched like the smoother's kernels, so the
+        // cycle keeps its programmatic dependent launches
+        TRY(launch_copy_prolong<T>(b, n_g, L.agg + L.fo[g], x_in ? x_in + e0 : nullptr, uc, x_out + e0, s));
     }
     return BAMG_OK;
 }

@@ -12,6 +12,19 @@
 namespace bamg {
 
 constexpr int kWarp = 32;
+
+// Every (b, fb) block shape the cycle's kernels are instantiated for: b dofs
+// per node in b / fb field blocks of fb dofs (amg_setup accepts exactly these)
+#define BAMG_BLOCK_SHAPES(M) \
+    M(1, 1) M(2, 2) M(3, 3) M(4, 4) M(5, 5) M(6, 6) M(7, 7) M(8, 8) M(4, 2) M(6, 3) M(6, 2) M(8, 4) M(8, 2)
+
+// threads per CTA of the kernels with FB (or FB x 4) threads per node: a
+// multiple of FB * 4 and of the warp, so that no node is split between CTAs
+template <int FB>
+struct RowThreads {
+    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : FB == 5 ? 160 : FB == 7 ? 224 : 256;
+    static_assert(kThreads % (FB * 4) == 0 && kThreads % 32 == 0, "threads per CTA");
+};
 constexpr int kMaxLevels = 16;
 constexpr int kMaxRestart = 64;
 constexpr int kMaxB = 8;
@@ -244,6 +257,9 @@ int launch_restrict(int b, int nc, const int* agg_ptr, const int* members, const
 // u[i*b+d] += uc[agg[i]*b+d]
 template <typename T>
 int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s);
+// y[i*b+d] = x[i*b+d] (+ uc[agg[i]*b+d] when uc is set), or 0 without x
+template <typename T>
+int launch_copy_prolong(int b, int n, const int* agg, const T* x, const T* uc, T* y, cudaStream_t s);
 // One colour of one field step of the block Gauss-Seidel smoother.
 struct BgsArgs {
     int n_in_colour = 0;

@@ -171,7 +171,7 @@ int launch_upper_flags(int n, const int* rp, const int* ci, const int* colour, c
 // ---------------------------------------------------------------------------
 template <int FB>
 struct IluBlock {
-    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
+    static constexpr int kThreads = RowThreads<FB>::kThreads;
 };
 
 // forward: y_i = L_ii^{-1} (r_f,i - sum_{lower j} L_ij y_j), where the field's
@@ -323,7 +323,7 @@ int launch_ilu_colour(int b, int fb, const BgsArgs& a, const T* lu, const int* d
         if (e != cudaSuccess) return BAMG_ECUDA;                                                              \
         break;                                                                                                \
     }
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

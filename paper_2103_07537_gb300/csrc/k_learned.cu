@@ -117,7 +117,7 @@ int launch_features(int b, int fb, int n, const int* rp, const int* ci, const do
     case BB * 16 + FF:                                                                                   \
         features_kernel<BB, FF><<<grid, 128, 0, s>>>(n, rp, ci, vals, agg, agg_cnt, level, out, err);    \
         break;
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

@@ -337,7 +337,7 @@ int launch_field_residual(int b, int fb, int fm, int n, int field, const int* rp
         if (e != cudaSuccess) return BAMG_ECUDA;                                                             \
         break;                                                                                               \
     }
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

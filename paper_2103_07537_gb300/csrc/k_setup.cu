@@ -767,7 +767,7 @@ int block_inverses(int b, int fb, int n, const int* diag, const double* vals, do
     switch (fb) {
 #define CASE(FF) \
     case FF: block_inverse_kernel<FF><<<blocks, 128, 0, s>>>(b, F, n, diag, vals, dinv64, err); break;
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(6)
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

@@ -257,7 +257,7 @@ int launch_spmv(int b, int fb, int fm, int n, const int* rp, const int* ci, cons
             cudaSuccess)                                                                                    \
             return BAMG_ECUDA;                                                                              \
         break;
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(5, 5) CASE(6, 6) CASE(7, 7) CASE(8, 8) CASE(4, 2) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -302,6 +302,32 @@ __global__ void prolong_kernel(int b, int n, const int* __restrict__ agg, const 
     u[e] += uc[(size_t)agg[i] * b + d];
 }
 
+// the nodes of a range that a field step leaves alone: y = x (+ P uc), or
+// zero without x (the zero initial guess)
+template <typename T>
+__global__ void copy_prolong_kernel(int b, int n, const int* __restrict__ agg, const T* __restrict__ x,
+                                    const T* __restrict__ uc, T* __restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(e / b);
+    if (i >= n) return;
+    const int d = (int)(e - (long)i * b);
+    T v = x ? x[e] : T(0);
+    if (x && uc) v += uc[(size_t)agg[i] * b + d];
+    y[e] = v;
+}
+
+template <typename T>
+int launch_copy_prolong(int b, int n, const int* agg, const T* x, const T* uc, T* y, cudaStream_t s) {
+    if (n <= 0) return BAMG_OK;
+    if (launch_k(copy_prolong_kernel<T>, ceil_div((long)n * b, 256), 256, 0, s, b, n, agg, x, uc, y) != cudaSuccess)
+        return BAMG_ECUDA;
+    return launched(1);
+}
+template int launch_copy_prolong<double>(int, int, const int*, const double*, const double*, double*, cudaStream_t);
+template int launch_copy_prolong<float>(int, int, const int*, const float*, const float*, float*, cudaStream_t);
+
 template <typename T>
 int launch_prolong(int b, int n, const int* agg, const T* uc, T* u, cudaStream_t s) {
     if (n <= 0) return BAMG_OK;
@@ -332,7 +358,7 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
                  : launch_k(bgs_colour_kernel<T, BB, FF, false>, blocks, threads, 0, s, a)) != cudaSuccess) \
             return BAMG_ECUDA;                                                                  \
         break;
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -442,7 +468,7 @@ int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, 
             cudaSuccess)                                                                                    \
             return BAMG_ECUDA;                                                                              \
         break;
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(5, 5) CASE(6, 6) CASE(7, 7) CASE(8, 8) CASE(4, 2) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -457,7 +483,7 @@ template int launch_spmv_tpr<float>(int, int, int, int, const int*, const int*, 
 // half of it: smaller CTAs spread a small colour over more SMs)
 template <int FB>
 struct TprBlock {
-    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
+    static constexpr int kThreads = RowThreads<FB>::kThreads;
 };
 
 // One colour of one field step (same arithmetic as bgs_node up to the order
@@ -557,7 +583,7 @@ int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int v
         if (e != cudaSuccess) return BAMG_ECUDA;                                                              \
         break;                                                                                                \
     }
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -707,7 +733,7 @@ int launch_grid_tail(int b, int fb, const TailPhase* phases, int nphase, int gri
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF: return launch_grid_tail_t<T, BB, FF>(phases, nphase, grid, bar, err, s);
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -720,7 +746,7 @@ int grid_tail_size(int b, int fb) {
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF: return grid_tail_size_t<T, BB, FF>();
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return 0;
     }
@@ -776,7 +802,7 @@ int launch_tail(int b, int fb, const TailPhase* phases, int nphase, int cluster,
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF: return launch_tail_t<T, BB, FF>(phases, nphase, cluster, s);
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }
@@ -789,7 +815,7 @@ int tail_cluster_size(int b, int fb, int want) {
     switch (b * 16 + fb) {
 #define CASE(BB, FF) \
     case BB * 16 + FF: return tail_cluster_size_t<T, BB, FF>(want);
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return 0;
     }

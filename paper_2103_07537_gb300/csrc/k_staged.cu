@@ -39,7 +39,7 @@ constexpr int kStagedStages = 3;
 
 template <int FB>
 struct StagedShape {
-    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
+    static constexpr int kThreads = RowThreads<FB>::kThreads;
     static constexpr int kG = 4;                             // lanes per scalar row
     static constexpr int kNodes = kThreads / (FB * kG);      // nodes per batch
 };
@@ -250,7 +250,7 @@ int launch_bgs_colour_staged(int b, int fb, const BgsArgs& a, int max_row, int* 
         return (a.fm && kFm) ? launch_staged_instance<T, BB, FF, kFm>(a, max_row, err, s)                   \
                              : launch_staged_instance<T, BB, FF, false>(a, max_row, err, s);                \
     }
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

@@ -44,8 +44,9 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 // tile in NTILE / (threads / (FB * G)) passes)
 template <int FB>
 struct SweepShape {
-    static constexpr int kThreads = (FB == 3 || FB == 6) ? 192 : 256;
-    static constexpr int kTile = (kThreads / FB > 64) ? kThreads / FB : 64;
+    static constexpr int kThreads = RowThreads<FB>::kThreads;
+    // at least 64 nodes, a whole number of passes of one thread per row
+    static constexpr int kTile = (kThreads / FB) * ((64 + kThreads / FB - 1) / (kThreads / FB));
 };
 
 int sweep_tile_nodes(int fb) {
@@ -54,7 +55,10 @@ int sweep_tile_nodes(int fb) {
         case 2: return SweepShape<2>::kTile;
         case 3: return SweepShape<3>::kTile;
         case 4: return SweepShape<4>::kTile;
+        case 5: return SweepShape<5>::kTile;
         case 6: return SweepShape<6>::kTile;
+        case 7: return SweepShape<7>::kTile;
+        case 8: return SweepShape<8>::kTile;
         default: return 0;
     }
 }
@@ -231,7 +235,7 @@ int launch_bgs_sweep(int b, int fb, const BgsArgs& a, const SweepArgs& sw, int t
         return (a.fm && kFm) ? launch_sweep_instance<T, BB, FF, 1, kFm>(a, sw, tiles, s)                      \
                              : launch_sweep_instance<T, BB, FF, 1, false>(a, sw, tiles, s);                   \
     }
-        CASE(1, 1) CASE(2, 2) CASE(3, 3) CASE(4, 4) CASE(4, 2) CASE(6, 6) CASE(6, 3)
+        BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
     }

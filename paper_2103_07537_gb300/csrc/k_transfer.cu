@@ -257,7 +257,7 @@ __global__ void rap_general_numeric_kernel(int nc, const int* __restrict__ r_rp,
     }
 }
 
-#define BAMG_FDIAG_CASES(M) M(1, 1) M(2, 2) M(3, 3) M(4, 4) M(4, 2) M(6, 6) M(6, 3)
+#define BAMG_FDIAG_CASES(M) BAMG_BLOCK_SHAPES(M)
 
 int prolongator_numeric(int b, int fb, int n, const int* rp, const int* ci, const double* vals, const double* dinv,
                         const int* agg, const double* omega_p, const int* p_rp, const int* p_ci, double* p_v,

@@ -198,3 +198,23 @@ def test_field_invalid_inputs_are_rejected():
         with pytest.raises(bamg.BamgError) as e:
             bamg.FieldSolver(off, *args, max_levels=2, max_coarse=0, **kw)
         assert e.value.status == bamg.BAMG_EINVAL
+
+
+@pytest.mark.parametrize("sub", [0, 1, 2])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_programmatic_launches_give_identical_node_field_cycles(prec, sub):
+    # the other fields' nodes are copied by a kernel of the cycle, so the
+    # cycle runs with programmatic dependent launches: same bits as without
+    (rp, ci, vals, off), kw = SYSTEMS["q2q1_21_ragged"]()
+    args = (off, dev(rp), dev(ci), dev(vals.reshape(-1)), vals.shape[1])
+    zs = []
+    n, b = len(rp) - 1, vals.shape[1]
+    r = dev(np.random.default_rng(17).standard_normal(n * b))
+    for pdl in (0, 1):
+        g = bamg.FieldSolver(*args, use_pdl=pdl, cycle_prec=prec, sub_solver=sub, **kw)
+        z = torch.empty_like(r)
+        g.apply(r, z)
+        g.apply(r, z)
+        zs.append(z)
+    torch.cuda.synchronize()
+    assert torch.equal(zs[0], zs[1])

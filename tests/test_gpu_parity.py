@@ -329,9 +329,9 @@ def test_invalid_inputs_are_rejected():
     # bad field maps
     expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, ci, va, 6, [0, 0, 1, 1, 1, 1], **kw))
     expect_status(bamg.BAMG_EINVAL, lambda: bamg.Solver(rp, ci, va, 6, [1, 1, 1, 0, 0, 0], **kw))
-    # unsupported block shape for the smoother (b = 5)
-    s5 = P.random_block_system(5, 5, [0] * 5, seed=1)
-    expect_status(bamg.BAMG_EUNSUPPORTED, lambda: make_solver(s5, **kw))
+    # unsupported block shape for the smoother (three fields of one dof)
+    s3 = P.random_block_system(5, 3, [0, 1, 2], seed=1)
+    expect_status(bamg.BAMG_EUNSUPPORTED, lambda: make_solver(s3, **kw))
     # unsorted columns in one row
     ci_bad = s.col_idx.copy()
     k0 = s.row_ptr[7]
