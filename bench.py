@@ -439,8 +439,10 @@ def run_ours(args):
                 st, it, rr = bamg.fgmres_solve(h, b, x, TOL, restart, max_iter, stream)
                 solved[0] = 1 if st == 0 else 0
             prof = None
-            if profile:
-                prof = {k: bamg.amg_profile_read(h, k) for k in bamg.KERNEL_KINDS}
+            if profile:  # per kernel kind and hierarchy level (-1: the outer FGMRES kernels)
+                nl = bamg.amg_num_levels(h)
+                prof = {(k, l): bamg.amg_profile_read_level(h, k, l) for k in bamg.KERNEL_KINDS
+                        for l in range(-1, nl)}
         finally:
             bamg.amg_destroy(h)
         return st, it, rr, prof
@@ -627,16 +629,18 @@ def run_ours(args):
         plain["learned_vs_plain_fp64"] = value / plain["fp64"]["value"] if plain["fp64"]["value"] else None
 
     # --- per-kernel profile pass (events around every launch) --------------------
-    kernels = {}
+    kernels = {}     # per kind
+    kernels_kl = {}  # per (kind, level)
     prof_iters_tot = 0
     for _ in range(max(1, args.profile_steps)):
         flush.zero_()
         _, it_p_, _, prof = step(params64, profile=True)
         prof_iters_tot += it_p_
-        for k, v in prof.items():
-            acc = kernels.setdefault(k, dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
-            for f in acc:
-                acc[f] += v[f]
+        for (k, l), v in prof.items():
+            for key, dst in ((k, kernels), ((k, l), kernels_kl)):
+                acc = dst.setdefault(key, dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
+                for f in acc:
+                    acc[f] += v[f]
     peak_gbs, peak_src = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or 1920.0
     # The dominant kernel of the V-cycle (the metric's "V-cycle ms") and its
@@ -646,10 +650,13 @@ def run_ours(args):
     # its launches per cycle.
     cycle_kinds = {"smooth", "residual", "restrict", "prolong", "tail", "cast", "coarse"}
     prof_iters = max(1, prof_iters_tot // max(1, args.profile_steps))  # V-cycles per profiled solve
-    cyc = {k: v for k, v in kernels.items() if k in cycle_kinds and v["launches"]}
+    # the dominant kernel of the cycle: one kind on one level (one kernel
+    # instance and row mapping, e.g. the finest level's smoother)
+    cyc = {kl: v for kl, v in kernels_kl.items() if kl[0] in cycle_kinds and kl[1] >= 0 and v["launches"]}
     cyc_ms = sum(v["ms"] for v in cyc.values())
-    dom = max(cyc, key=lambda k: cyc[k]["ms"])
-    d = kernels[dom]
+    dom_kl = max(cyc, key=lambda kl: cyc[kl]["ms"])
+    dom = dom_kl[0]
+    d = cyc[dom_kl]
     share = d["ms"] / cyc_ms if cyc_ms > 0 else 0.0
     vcycle_med = statistics.median(vt)
     launches_per_cycle = d["launches"] / (max(1, args.profile_steps) * prof_iters)
@@ -689,13 +696,21 @@ def run_ours(args):
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
                     "traffic": traffic, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alu_tflops": tfl, "alu_frac": tfl / alu_peak_tflops}
-    roofline.update({"kernel": dom, "kernel_prec": f"fp{kernel_prec}",
+    roofline.update({"kernel": dom, "level": dom_kl[1],
+                     "mapping": (stats["levels"][dom_kl[1]].get("smoother_mapping") if dom == "smooth" else
+                                 stats["levels"][dom_kl[1]].get("residual_mapping") if dom == "residual" else None),
+                     "kernel_prec": f"fp{kernel_prec}",
                      "launches_per_cycle": launches_per_cycle, "us_per_launch": us_per_launch,
                      "bytes_per_launch": bytes_per_launch, "flops_per_launch": flops_per_launch,
                      "share_of_cycle": share, "vcycle_ms": vcycle_med,
                      "how": "us_per_launch = vcycle_ms x share_of_cycle / launches_per_cycle (share: the "
-                            "kernel's part of the cycle's kernel time in a profiled solve); achieved = "
-                            "bytes_per_launch (algorithmic) / us_per_launch"})
+                            "kernel's part, on its level, of the cycle's kernel time in a profiled solve); achieved "
+                            "= bytes_per_launch (algorithmic) / us_per_launch"})
+    by_level = {f"{k}@{l}": {"ms_per_solve": v["ms"] / max(1, args.profile_steps),
+                             "launches": v["launches"] // max(1, args.profile_steps),
+                             "share_of_cycle": v["ms"] / cyc_ms if cyc_ms > 0 else None,
+                             "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
+                for (k, l), v in sorted(kernels_kl.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
     ksum = {k: {"ms_per_solve": v["ms"] / max(1, args.profile_steps), "launches": v["launches"] // max(1, args.profile_steps),
                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
                 "TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else 0.0}
@@ -703,13 +718,26 @@ def run_ours(args):
 
     # --- end to end through the host-buffer entry point ---------------------------
     e2e = None
-    if not args.no_e2e and node_fields is not None:
-        # through the public API with host buffers: pinned H2D of A and b,
-        # amg_setup_fields and fgmres_solve, D2H of x
-        hostbufs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                    for a in (s.row_ptr, s.col_idx, s.vals.reshape(-1), s.rhs)]
-        xh = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory()
+    if not args.no_e2e and (node_fields is not None or batched):
+        # through the public API with host buffers: the host entry point copies
+        # A and b to the device, sets up, solves and copies x back
+        hp = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+              for a in (s.row_ptr, s.col_idx, s.vals.reshape(-1), s.rhs)]
+        x_h = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory().numpy()
         k_e = max(1, min(args.steps, 3))
+
+        def host_solve():
+            x_h[:] = 0.0
+            if batched:
+                _, _, rrs = bamg.amg_solve_batched_host(bt.sys_node_off, hp[0], hp[1], hp[2], s.n_nodes, s.nnzb, s.b,
+                                                        s.field_of_dof, hp[3], x_h, TOL, restart, max_iter, params64,
+                                                        stream)
+                return int((rrs <= TOL).sum())
+            st_e, _, _ = bamg.amg_solve_fields_host(node_fields, hp[0], hp[1], hp[2], s.n_nodes, s.nnzb, s.b, hp[3],
+                                                    x_h, TOL, restart, MAX_ITER, params64, stream)
+            return 1 if st_e == 0 else 0
+
+        host_solve()
         tot = 0.0
         nsol = 0
         for _ in range(k_e):
@@ -718,56 +746,16 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            drp, dci, dva, db = [t.to(dev, non_blocking=True) for t in hostbufs]
-            dx = torch.zeros_like(db)
-            hh = bamg.amg_setup_fields(node_fields, drp, dci, dva, s.n_nodes, s.nnzb, s.b, params64, stream)
-            st_e, _, _ = bamg.fgmres_solve(hh, db, dx, TOL, restart, MAX_ITER, stream)
-            bamg.amg_destroy(hh)
-            xh.copy_(dx, non_blocking=True)
+            nsol += host_solve()
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-            nsol += 1 if st_e == 0 else 0
-            del drp, dci, dva, db, dx
-        h2d = sum(t.numel() * t.element_size() for t in hostbufs)
+        h2d = sum(a.nbytes for a in hp) + x_h.nbytes
         if pg:
             tot, nsol = reduce_timing(pg, tot, nsol, dev)
         e2e = {"value": nsol / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(xh.numel() * 8),
-               "api": "amg_setup_fields + fgmres_solve on device copies of pinned host buffers"}
-    elif not args.no_e2e and batched:
-        # through the public API with host buffers: pinned H2D of A and b,
-        # batched setup and solve, D2H of x
-        hostbufs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                    for a in (s.row_ptr, s.col_idx, s.vals.reshape(-1), s.rhs)]
-        xh = torch.zeros(s.n_unknowns, dtype=torch.float64).pin_memory()
-        k_e = max(1, min(args.steps, 3))
-        tot = 0.0
-        nsol = 0
-        for _ in range(k_e):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            drp, dci, dva, db = [t.to(dev, non_blocking=True) for t in hostbufs]
-            dx = torch.zeros_like(db)
-            hh = bamg.amg_setup_batched(bt.sys_node_off, drp, dci, dva, s.n_nodes, s.nnzb, s.b, s.field_of_dof,
-                                        params64, stream)
-            _, _, rrs = bamg.fgmres_solve_batched(hh, db, dx, TOL, restart, max_iter, stream)
-            bamg.amg_destroy(hh)
-            xh.copy_(dx, non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-            nsol += int((rrs <= TOL).sum())
-            del drp, dci, dva, db, dx
-        h2d = sum(t.numel() * t.element_size() for t in hostbufs)
-        if pg:
-            tot, nsol = reduce_timing(pg, tot, nsol, dev)
-        e2e = {"value": nsol / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(xh.numel() * 8),
-               "api": "amg_setup_batched + fgmres_solve_batched on device copies of pinned host buffers"}
+               "d2h_bytes_per_step": int(x_h.nbytes),
+               "api": ("amg_solve_batched_host" if batched else "amg_solve_fields_host") + " (pinned host buffers)"}
     elif not args.no_e2e:
         rp_h = torch.from_numpy(s.row_ptr).pin_memory().numpy()
         ci_h = torch.from_numpy(s.col_idx).pin_memory().numpy()
@@ -872,7 +860,7 @@ def run_ours(args):
                 "tail": {"level": stats.get("tail_level"), "grid_ctas": stats.get("tail_grid"),
                          "cluster": stats.get("tail_cluster")}, "variant": variant, "pr_variants": pr_variants, "sub_solvers": sub_solvers,
                 "plain": plain,
-                "kernels": ksum, "roofline": roofline,
+                "kernels": ksum, "kernels_by_level": by_level, "roofline": roofline,
                 "clocks": clocks,
                 "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

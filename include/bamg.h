@@ -268,6 +268,19 @@ int amg_setup_batched(int nsys, const int* sys_node_off, const int* row_ptr, con
 int fgmres_solve_batched(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
                          int* iters, double* relres, void* stream);
 
+/*
+ * amg_solve_batched_host - end-to-end solve of a batch with HOST buffers:
+ *   copies the block-diagonal A and the right-hand sides to the device, runs
+ *   amg_setup_batched and fgmres_solve_batched on `stream`, copies the
+ *   solutions back to x_host (initial guesses on entry) and frees everything
+ *   it allocated.  Arguments and statuses as those two calls, all arrays on
+ *   the host (pinned memory gives the fastest copies).
+ */
+int amg_solve_batched_host(int nsys, const int* sys_node_off, const int* row_ptr, const int* col_idx,
+                           const double* vals, int n_nodes, int nnzb, int b, const int* field_of_dof,
+                           const amg_params* p, const double* rhs_host, double* x_host, double tol, int restart,
+                           int max_iter, int* iters, double* relres, void* stream);
+
 /* number of systems of the handle (1 for amg_setup) */
 int amg_num_systems(bamg_t h);
 /* node range of every system on level l: sys_node_off[nsys+1] (host) */
@@ -453,6 +466,10 @@ int amg_stats(bamg_t h, char* json, int cap);
 #define BAMG_K_COUNT 9
 int amg_profile(bamg_t h, int enable);
 int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes, double* flops);
+/* The same for the launches of one hierarchy level (level -1: the outer
+ * FGMRES kernels, which belong to no level); clears only those. */
+int amg_profile_read_level(bamg_t h, int kind, int level, double* ms, long long* launches, double* bytes,
+                           double* flops);
 
 /* number of kernels this library has launched in the process so far (kernels
  * replayed from a captured graph count once per replay) */

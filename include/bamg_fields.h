@@ -52,6 +52,19 @@ int amg_setup_fields(const int* row_ptr, const int* col_idx, const double* vals,
                      int n_fields, const int* field_node_off, const amg_params* p, void* stream, bamg_t* out);
 
 /*
+ * amg_solve_fields_host - end-to-end solve of a system with fields on node
+ *   sets, with HOST buffers: copies A and the right-hand side to the device,
+ *   runs amg_setup_fields and fgmres_solve on `stream`, copies the solution
+ *   back to x_host (initial guess on entry) and frees everything it
+ *   allocated.  Arguments and statuses as those two calls, all arrays on the
+ *   host.
+ */
+int amg_solve_fields_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb, int b,
+                          int n_fields, const int* field_node_off, const amg_params* p, const double* rhs_host,
+                          double* x_host, double tol, int restart, int max_iter, int* iters, double* relres,
+                          void* stream);
+
+/*
  * amg_level_fields - field ranges of level `level` of a hierarchy:
  *   node_off[n_fields+1] (nodes of field g) and colour_off[n_fields+1]
  *   (colours of field g; zeros on the coarsest level), host arrays, either

@@ -22,9 +22,10 @@ BAMG_EINVAL, BAMG_ECUDA, BAMG_ESINGULAR_BLOCK, BAMG_ESINGULAR_COARSE = -1, -2, -
 BAMG_ENAN, BAMG_ETIMEOUT, BAMG_EUNSUPPORTED = -5, -6, -7
 
 #: every symbol the C header declares
-EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "bsr_spmv",
+EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_solve_host", "amg_solve_batched_host",
+           "amg_solve_fields_host", "bsr_spmv",
            "amg_num_levels", "amg_level_info", "amg_level_copy", "amg_level_ilu", "amg_stats", "amg_destroy", "amg_strerror",
-           "amg_profile", "amg_profile_read", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
+           "amg_profile", "amg_profile_read", "amg_profile_read_level", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
            "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
            "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
            "amg_level_p", "amg_setup_fields", "amg_level_fields"]
@@ -88,6 +89,12 @@ def load(build_if_missing: bool = True):
         lib.fgmres_solve.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
         lib.amg_solve_host.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip, C.POINTER(AmgParams), _vp,
                                        _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
+        lib.amg_solve_batched_host.argtypes = [C.c_int, _ip, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip,
+                                               C.POINTER(AmgParams), _vp, _vp, C.c_double, C.c_int, C.c_int, _ip,
+                                               _dp, _vp]
+        lib.amg_solve_fields_host.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _ip,
+                                              C.POINTER(AmgParams), _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp,
+                                              _vp]
         lib.bsr_spmv.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
         lib.amg_num_levels.argtypes = [_vp]
         lib.amg_level_info.argtypes = [_vp, C.c_int, _ip, _ip, _ip, _ip]
@@ -99,6 +106,7 @@ def load(build_if_missing: bool = True):
         lib.amg_strerror.restype = C.c_char_p
         lib.amg_profile.argtypes = [_vp, C.c_int]
         lib.amg_profile_read.argtypes = [_vp, C.c_int, _dp, C.POINTER(C.c_longlong), _dp, _dp]
+        lib.amg_profile_read_level.argtypes = [_vp, C.c_int, C.c_int, _dp, C.POINTER(C.c_longlong), _dp, _dp]
         lib.amg_launch_count.argtypes = []
         lib.amg_launch_count.restype = C.c_longlong
         lib.amg_colour_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
@@ -227,6 +235,51 @@ def amg_solve_host(row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, n
     return st, it.value, rr.value
 
 
+def _host_arrays(*arrs):
+    for a, dt in arrs:
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous int32 / float64")
+
+
+def amg_solve_batched_host(sys_node_off, row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, n_nodes: int,
+                           nnzb: int, b: int, field_of_dof, rhs: np.ndarray, x: np.ndarray, tol=1e-8, restart=30,
+                           max_iter=10000, params=None, stream=None):
+    """A batch end to end from host arrays; x (float64) updated in place.
+    Returns (status, iterations[nsys], true relative residuals[nsys])."""
+    off = np.ascontiguousarray(sys_node_off, dtype=np.int32)
+    fm = np.ascontiguousarray(field_of_dof, dtype=np.int32)
+    _host_arrays((row_ptr, np.int32), (col_idx, np.int32), (vals, np.float64), (rhs, np.float64), (x, np.float64))
+    ns = off.size - 1
+    it = np.zeros(ns, np.int32)
+    rr = np.zeros(ns)
+    st = load().amg_solve_batched_host(ns, off.ctypes.data_as(_ip), _hp(row_ptr), _hp(col_idx), _hp(vals),
+                                       int(n_nodes), int(nnzb), int(b), fm.ctypes.data_as(_ip),
+                                       C.byref(params) if params is not None else None, _hp(rhs), _hp(x), float(tol),
+                                       int(restart), int(max_iter), it.ctypes.data_as(_ip),
+                                       rr.ctypes.data_as(_dp), _stream(stream))
+    if st < 0:
+        raise BamgError(st, "amg_solve_batched_host")
+    return st, it, rr
+
+
+def amg_solve_fields_host(field_node_off, row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray,
+                          n_nodes: int, nnzb: int, b: int, rhs: np.ndarray, x: np.ndarray, tol=1e-8, restart=30,
+                          max_iter=10000, params=None, stream=None):
+    """A system with fields on node sets end to end from host arrays; x
+    updated in place.  Returns (status, iterations, true relative residual)."""
+    off = np.ascontiguousarray(field_node_off, dtype=np.int32)
+    _host_arrays((row_ptr, np.int32), (col_idx, np.int32), (vals, np.float64), (rhs, np.float64), (x, np.float64))
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = load().amg_solve_fields_host(_hp(row_ptr), _hp(col_idx), _hp(vals), int(n_nodes), int(nnzb), int(b),
+                                      off.size - 1, off.ctypes.data_as(_ip),
+                                      C.byref(params) if params is not None else None, _hp(rhs), _hp(x), float(tol),
+                                      int(restart), int(max_iter), C.byref(it), C.byref(rr), _stream(stream))
+    if st < 0:
+        raise BamgError(st, "amg_solve_fields_host")
+    return st, it.value, rr.value
+
+
 def bsr_spmv(row_ptr, col_idx, vals, n_nodes: int, b: int, x, y, stream=None) -> None:
     st = load().bsr_spmv(_ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(n_nodes), int(b), _ptr(x), _ptr(y),
                          _stream(stream))
@@ -304,6 +357,16 @@ def amg_profile_read(handle: int, kind) -> dict:
     st = load().amg_profile_read(handle, k, C.byref(ms), C.byref(n), C.byref(by), C.byref(fl))
     if st != BAMG_OK:
         raise BamgError(st, "amg_profile_read")
+    return dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
+
+
+def amg_profile_read_level(handle: int, kind, level: int) -> dict:
+    """As amg_profile_read for the launches of one level (-1: the outer FGMRES kernels)."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ms, n, by, fl = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+    st = load().amg_profile_read_level(handle, k, int(level), C.byref(ms), C.byref(n), C.byref(by), C.byref(fl))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_profile_read_level")
     return dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
 
 

@@ -183,7 +183,9 @@ struct ProfRec {
     cudaEvent_t e0, e1;
     int kind;
     double bytes, flops;
+    int level;  // hierarchy level of the launch (-1: the outer Krylov method)
 };
+constexpr int kProfSlots = kMaxLevels + 1;  // accumulator slot = level + 1
 
 int map_dev_error(int code) {
     switch (code) {
@@ -264,8 +266,11 @@ struct bamg_ctx {
     cudaGraph_t prof_graph = nullptr;
     cudaGraphExec_t prof_exec = nullptr;
     long long prof_graph_kernels = 0;
-    double acc_ms[BAMG_K_COUNT] = {}, acc_bytes[BAMG_K_COUNT] = {}, acc_flops[BAMG_K_COUNT] = {};
-    long long acc_n[BAMG_K_COUNT] = {};
+    // resolved profile records per kernel kind and level slot
+    double acc_ms[BAMG_K_COUNT][kProfSlots] = {}, acc_bytes[BAMG_K_COUNT][kProfSlots] = {},
+           acc_flops[BAMG_K_COUNT][kProfSlots] = {};
+    long long acc_n[BAMG_K_COUNT][kProfSlots] = {};
+    int prof_level = -1;  // level of the launches being issued (profiling)
     // FGMRES workspace
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *h1 = nullptr, *h2 = nullptr,
@@ -351,7 +356,7 @@ static cudaEvent_t take_event(bamg_ctx* h) {
 // the graph (timestamps taken by the GPU between the kernels, no host gaps).
 static int prof_begin(bamg_ctx* h, cudaStream_t s) {
     if (!h->prof) return -1;
-    ProfRec r{take_event(h), take_event(h), -1, 0.0, 0.0};
+    ProfRec r{take_event(h), take_event(h), -1, 0.0, 0.0, h->prof_level};
     std::vector<ProfRec>& v = h->capturing_prof ? h->graph_recs : h->recs;
     if (h->capturing_prof) cudaEventRecordWithFlags(r.e0, s, cudaEventRecordExternal);
     else cudaEventRecord(r.e0, s);
@@ -1745,6 +1750,7 @@ template <typename T>
 static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
     const Level& L = h->lev[l];
     const int b = h->b;
+    h->prof_level = l;  // the launches below belong to level l (until the coarser call returns)
     if (!h->rec && l == h->l_tail && h->tail_d && rhs == h->tail_rhs && out == h->tail_out) {
         // every level from l down runs as one cluster launch of the recorded phases
         if (h->tail_grid)
@@ -1817,6 +1823,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         PL(BAMG_K_RESTRICT, tb + (C.n + 1) * 4.0 + nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
            restrict_explicit<T>(h, L, res, static_cast<T*>(C.rhs), s));
         TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
+        h->prof_level = l;
         PL(BAMG_K_PROLONG, tb + (L.n + 1) * 4.0 + 2.0 * nb * es + ncb * es, 2.0 * L.p_nnz * b * h->fb,
            prolong_explicit<T>(h, L, static_cast<const T*>(C.uc), cur, s));
         const int S_post = h->p.n_post * NS;
@@ -1863,6 +1870,7 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
            launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     }
     TRY(mgv<T>(h, l + 1, static_cast<const T*>(C.rhs), static_cast<T*>(C.uc), s));
+    h->prof_level = l;
     const int S_post = h->p.n_post * NS;
     if (S_post == 0) {
         const double pb = L.n * 4.0 + 2.0 * nb * es + ncb * es;
@@ -1896,6 +1904,11 @@ static int cycle_direct(bamg_ctx* h, const double* r, double* z, cudaStream_t s)
     // for its inputs); profiling keeps plain launches so that the event pairs
     // bracket one kernel each
     PdlScope pdl(h->p.use_pdl != 0 && !h->prof);
+    h->prof_level = 0;
+    struct OuterLevel {  // launches after the cycle belong to the outer method
+        bamg_ctx* h;
+        ~OuterLevel() { h->prof_level = -1; }
+    } outer_level{h};
     if (h->p.cycle_prec == 64) {
         if (h->tail_d && h->l_tail == 0 && (r != h->cyc_in || z != h->cyc_out)) {
             // the recorded single-launch cycle reads and writes the staging vectors
@@ -2029,10 +2042,11 @@ static int apply_profiled(bamg_ctx* h, const double* r, double* z, cudaStream_t 
     for (const ProfRec& rec : h->graph_recs) {
         float e = 0.0f;
         BAMG_CUDA_TRY(cudaEventElapsedTime(&e, rec.e0, rec.e1));
-        h->acc_ms[rec.kind] += e;
-        h->acc_bytes[rec.kind] += rec.bytes;
-        h->acc_flops[rec.kind] += rec.flops;
-        h->acc_n[rec.kind] += 1;
+        const int sl = rec.level + 1;
+        h->acc_ms[rec.kind][sl] += e;
+        h->acc_bytes[rec.kind][sl] += rec.bytes;
+        h->acc_flops[rec.kind][sl] += rec.flops;
+        h->acc_n[rec.kind][sl] += 1;
     }
     return BAMG_OK;
 }
@@ -2350,12 +2364,13 @@ extern "C" int amg_level_systems(bamg_t h, int level, int* sys_node_off) {
 // ---------------------------------------------------------------------------
 // end-to-end with host buffers
 // ---------------------------------------------------------------------------
-extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes,
-                              int nnzb, int b, const int* field_of_dof, const amg_params* p,
-                              const double* rhs_host, double* x_host, double tol, int restart, int max_iter,
-                              int* iters, double* relres, void* stream) {
-    if (!row_ptr || !col_idx || !vals || !rhs_host || !x_host || n_nodes < 1 || nnzb < 1 || b < 1 || b > kMaxB)
-        return BAMG_EINVAL;
+// End to end with host buffers: copies of A, b and x0 on the device (the
+// stream-ordered pool), setup(d_rp, d_ci, d_v, &h) and solve(h, d_b, d_x),
+// x back to the host, everything released.
+template <class Setup, class Solve>
+static int solve_host_common(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
+                             int b, const double* rhs_host, double* x_host, void* stream, Setup&& setup,
+                             Solve&& solve) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t N = (size_t)n_nodes * b;
     int *d_rp = nullptr, *d_ci = nullptr;
@@ -2375,10 +2390,10 @@ extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const doub
          cudaMemcpyAsync(d_b, rhs_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
          cudaMemcpyAsync(d_x, x_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess))
         st = BAMG_ECUDA;
-    if (st == BAMG_OK) st = amg_setup(d_rp, d_ci, d_v, n_nodes, nnzb, b, field_of_dof, p, stream, &h);
+    if (st == BAMG_OK) st = setup(d_rp, d_ci, d_v, &h);
     int solve_st = BAMG_OK;
     if (st == BAMG_OK) {
-        solve_st = fgmres_solve(h, d_b, d_x, tol, restart, max_iter, iters, relres, stream);
+        solve_st = solve(h, d_b, d_x);
         if (solve_st >= 0 &&
             (cudaMemcpyAsync(x_host, d_x, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
              cudaStreamSynchronize(s) != cudaSuccess))
@@ -2390,6 +2405,56 @@ extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const doub
         if (q) cudaFreeAsync(q, s);
     cudaStreamSynchronize(s);
     return st != BAMG_OK ? st : solve_st;
+}
+
+extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes,
+                              int nnzb, int b, const int* field_of_dof, const amg_params* p,
+                              const double* rhs_host, double* x_host, double tol, int restart, int max_iter,
+                              int* iters, double* relres, void* stream) {
+    if (!row_ptr || !col_idx || !vals || !rhs_host || !x_host || n_nodes < 1 || nnzb < 1 || b < 1 || b > kMaxB)
+        return BAMG_EINVAL;
+    return solve_host_common(
+        row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
+        [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
+            return amg_setup(rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h);
+        },
+        [&](bamg_t h, const double* bb, double* x) {
+            return fgmres_solve(h, bb, x, tol, restart, max_iter, iters, relres, stream);
+        });
+}
+
+extern "C" int amg_solve_batched_host(int nsys, const int* sys_node_off, const int* row_ptr, const int* col_idx,
+                                      const double* vals, int n_nodes, int nnzb, int b, const int* field_of_dof,
+                                      const amg_params* p, const double* rhs_host, double* x_host, double tol,
+                                      int restart, int max_iter, int* iters, double* relres, void* stream) {
+    if (nsys < 1 || !sys_node_off || !row_ptr || !col_idx || !vals || !rhs_host || !x_host || n_nodes < 1 ||
+        nnzb < 1 || b < 1 || b > kMaxB)
+        return BAMG_EINVAL;
+    return solve_host_common(
+        row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
+        [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
+            return amg_setup_batched(nsys, sys_node_off, rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h);
+        },
+        [&](bamg_t h, const double* bb, double* x) {
+            return fgmres_solve_batched(h, bb, x, tol, restart, max_iter, iters, relres, stream);
+        });
+}
+
+extern "C" int amg_solve_fields_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes,
+                                     int nnzb, int b, int n_fields, const int* field_node_off, const amg_params* p,
+                                     const double* rhs_host, double* x_host, double tol, int restart, int max_iter,
+                                     int* iters, double* relres, void* stream) {
+    if (!row_ptr || !col_idx || !vals || !rhs_host || !x_host || !field_node_off || n_nodes < 1 || nnzb < 1 ||
+        b < 1 || b > kMaxB || n_fields < 1)
+        return BAMG_EINVAL;
+    return solve_host_common(
+        row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
+        [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
+            return amg_setup_fields(rp, ci, v, n_nodes, nnzb, b, n_fields, field_node_off, p, stream, h);
+        },
+        [&](bamg_t h, const double* bb, double* x) {
+            return fgmres_solve(h, bb, x, tol, restart, max_iter, iters, relres, stream);
+        });
 }
 
 // ---------------------------------------------------------------------------
@@ -2534,39 +2599,57 @@ extern "C" int amg_profile(bamg_t h, int enable) {
     return BAMG_OK;
 }
 
-extern "C" int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes,
-                                double* flops) {
-    if (!h || kind < 0 || kind >= BAMG_K_COUNT) return BAMG_EINVAL;
-    double t = 0.0, by = 0.0, fl = 0.0;
-    long long cnt = 0;
-    std::vector<ProfRec> keep;
+// resolve every direct-launch record into the per-kind, per-level sums
+static int profile_resolve(bamg_ctx* h) {
     for (auto& r : h->recs) {
-        if (r.kind != kind) {
-            keep.push_back(r);
-            continue;
-        }
         BAMG_CUDA_TRY(cudaEventSynchronize(r.e1));
         float e = 0.0f;
         BAMG_CUDA_TRY(cudaEventElapsedTime(&e, r.e0, r.e1));
-        t += e;
-        by += r.bytes;
-        fl += r.flops;
-        cnt++;
+        if (r.kind >= 0) {
+            const int sl = r.level + 1;
+            h->acc_ms[r.kind][sl] += e;
+            h->acc_bytes[r.kind][sl] += r.bytes;
+            h->acc_flops[r.kind][sl] += r.flops;
+            h->acc_n[r.kind][sl] += 1;
+        }
         h->ev_free.push_back(r.e0);
         h->ev_free.push_back(r.e1);
     }
-    h->recs.swap(keep);
-    t += h->acc_ms[kind];
-    by += h->acc_bytes[kind];
-    fl += h->acc_flops[kind];
-    cnt += h->acc_n[kind];
-    h->acc_ms[kind] = h->acc_bytes[kind] = h->acc_flops[kind] = 0.0;
-    h->acc_n[kind] = 0;
+    h->recs.clear();
+    return BAMG_OK;
+}
+
+// the sums of kind over level slots s0..s1-1, then cleared
+static int profile_take(bamg_ctx* h, int kind, int s0, int s1, double* ms, long long* launches, double* bytes,
+                        double* flops) {
+    TRY(profile_resolve(h));
+    double t = 0.0, by = 0.0, fl = 0.0;
+    long long cnt = 0;
+    for (int sl = s0; sl < s1; ++sl) {
+        t += h->acc_ms[kind][sl];
+        by += h->acc_bytes[kind][sl];
+        fl += h->acc_flops[kind][sl];
+        cnt += h->acc_n[kind][sl];
+        h->acc_ms[kind][sl] = h->acc_bytes[kind][sl] = h->acc_flops[kind][sl] = 0.0;
+        h->acc_n[kind][sl] = 0;
+    }
     if (ms) *ms = t;
     if (launches) *launches = cnt;
     if (bytes) *bytes = by;
     if (flops) *flops = fl;
     return BAMG_OK;
+}
+
+extern "C" int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double* bytes,
+                                double* flops) {
+    if (!h || kind < 0 || kind >= BAMG_K_COUNT) return BAMG_EINVAL;
+    return profile_take(h, kind, 0, kProfSlots, ms, launches, bytes, flops);
+}
+
+extern "C" int amg_profile_read_level(bamg_t h, int kind, int level, double* ms, long long* launches,
+                                      double* bytes, double* flops) {
+    if (!h || kind < 0 || kind >= BAMG_K_COUNT || level < -1 || level >= h->nlev) return BAMG_EINVAL;
+    return profile_take(h, kind, level + 1, level + 2, ms, launches, bytes, flops);
 }
 
 // ---------------------------------------------------------------------------

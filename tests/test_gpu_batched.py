@@ -116,3 +116,22 @@ def test_batch_stagnating_member_is_reported_and_others_converge():
     assert st == bamg.BAMG_NOT_CONVERGED
     assert its[5] == 150 and rr[5] > 1e-8
     assert all(its[q] < 150 and rr[q] <= 1e-8 for q in range(5))
+
+
+def test_batch_host_entry_point_matches_device_path(batch):
+    # amg_solve_batched_host: the same setup and solve from host buffers
+    bt, g, _ = batch
+    s = bt.system
+    kw = dict(max_levels=4, max_coarse=0, autotune=0)
+    g0 = bamg.BatchSolver(bt.sys_node_off, dev(s.row_ptr), dev(s.col_idx), dev(s.vals.reshape(-1)), s.b,
+                          s.field_of_dof, **kw)
+    x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+    st, its, rr = g0.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=3000)
+    xh = np.zeros(s.n_unknowns)
+    sth, itsh, rrh = bamg.amg_solve_batched_host(bt.sys_node_off, s.row_ptr, s.col_idx,
+                                                 np.ascontiguousarray(s.vals.reshape(-1)), s.n_nodes, s.nnzb, s.b,
+                                                 s.field_of_dof, s.rhs, xh, 1e-8, 30, 3000,
+                                                 bamg.amg_default_params(**kw))
+    assert st == sth == bamg.BAMG_OK
+    assert np.array_equal(its, itsh) and np.array_equal(rr, rrh)
+    assert np.array_equal(x.cpu().numpy(), xh)

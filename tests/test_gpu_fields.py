@@ -218,3 +218,19 @@ def test_programmatic_launches_give_identical_node_field_cycles(prec, sub):
         zs.append(z)
     torch.cuda.synchronize()
     assert torch.equal(zs[0], zs[1])
+
+
+def test_fields_host_entry_point_matches_device_path():
+    (rp, ci, vals, off), kw = SYSTEMS["q2q1_12"]()
+    kw = dict(kw, autotune=0)
+    n, b = len(rp) - 1, vals.shape[1]
+    rhs = np.random.default_rng(23).standard_normal(n * b)
+    g = bamg.FieldSolver(off, dev(rp), dev(ci), dev(vals.reshape(-1)), b, **kw)
+    x = torch.zeros(n * b, dtype=torch.float64, device="cuda")
+    st, it, rr = g.solve(dev(rhs), x, tol=1e-8, restart=30, max_iter=3000)
+    xh = np.zeros(n * b)
+    sth, ith, rrh = bamg.amg_solve_fields_host(off, np.ascontiguousarray(rp), np.ascontiguousarray(ci),
+                                               np.ascontiguousarray(vals.reshape(-1)), n, len(ci), b, rhs, xh, 1e-8,
+                                               30, 3000, bamg.amg_default_params(**kw))
+    assert st == sth == bamg.BAMG_OK and it == ith and rr == rrh
+    assert np.array_equal(x.cpu().numpy(), xh)
