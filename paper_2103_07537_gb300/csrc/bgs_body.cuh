@@ -84,4 +84,55 @@ __device__ __forceinline__ void bgs_block(const BgsArgs& a, const T* xt, const T
     }
 }
 
+// the blocks kf, kf + S, kf + 2S, ... (< k1) of one matrix row, accumulated
+// in that order into acc (bgs_block per block).  Software-pipelined: the
+// next block's colour flag, column and matrix row are loaded before the
+// current block's gathers, so each step waits for one gather latency rather
+// than the column load followed by its gather.  The first block (column jf,
+// flag lowf, aggregate agf, row arf) is loaded by the caller, before its wait
+// on the previous kernel; vb is the row's first block, VS the stride between
+// blocks.  XIN: x_in is set (every block contributes; without it only blocks
+// of lower colour do, and the others' rows are not loaded) -- a template
+// flag, so that the loads of the next block do not wait on its colour flag.
+template <typename T, int B, int FB, bool CG, int S, bool XIN>
+__device__ __forceinline__ void bgs_walk_x(const BgsArgs& a, const T* xt, const T* x_in, const T* uc,
+                                           const T* __restrict__ vb, int VS, int k0, int kf, int k1, int jf,
+                                           bool lowf, int agf, const T (&arf)[B], T& acc) {
+    int j = jf, ag = agf;
+    bool lw = lowf;
+    T ar[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) ar[c] = arf[c];
+#pragma unroll 2
+    for (int k = kf;; k += S) {
+        const int kn = k + S;
+        const bool more = kn < k1;
+        bool lwn = false;
+        int jn = 0;
+        T an[B];
+        if (more) {
+            lwn = __ldg(a.lowk + kn) != 0;
+            jn = __ldg(a.ci + kn);
+            if (XIN || lwn) load_row<T, B>(vb + (size_t)(kn - k0) * VS, an);
+        }
+        if (XIN || lw) bgs_block<T, B, FB, CG>(a, xt, XIN ? x_in : nullptr, XIN ? uc : nullptr, j, ar, lw, ag, acc);
+        if (!more) break;
+        j = jn;
+        lw = lwn;
+        if (XIN && uc) ag = __ldg(a.agg + jn);
+#pragma unroll
+        for (int c = 0; c < B; ++c) ar[c] = an[c];
+    }
+}
+
+template <typename T, int B, int FB, bool CG, int S>
+__device__ __forceinline__ void bgs_walk(const BgsArgs& a, const T* xt, const T* x_in, const T* uc,
+                                         const T* __restrict__ vb, int VS, int k0, int kf, int k1, int jf,
+                                         bool lowf, int agf, const T (&arf)[B], T& acc) {
+    if (x_in)
+        bgs_walk_x<T, B, FB, CG, S, true>(a, xt, x_in, uc, vb, VS, k0, kf, k1, jf, lowf, agf, arf, acc);
+    else
+        bgs_walk_x<T, B, FB, CG, S, false>(a, xt, x_in, uc, vb, VS, k0, kf, k1, jf, lowf, agf, arf, acc);
+}
+
 }  // namespace bamg

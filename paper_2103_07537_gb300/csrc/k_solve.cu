@@ -154,18 +154,7 @@ __device__ __forceinline__ void bgs_node(const BgsArgs& a, long q, int lane) {
     }
     const T bi = lane < FB ? ld1<T, CG>(static_cast<const T*>(a.rhs) + (size_t)i * B + f0 + lane) : T(0);
     T acc = T(0);
-    if (have) {
-        bgs_block<T, B, FB, CG>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
-#pragma unroll 4
-        for (int k = kf + G; k < k1; k += G) {
-            const bool lower = __ldg(a.lowk + k) != 0;
-            if (!x_in && !lower) continue;
-            const int j = __ldg(a.ci + k);
-            T arow[B];
-            load_row<T, B>(vb + (size_t)(k - k0) * VS, arow);
-            bgs_block<T, B, FB, CG>(a, xt, x_in, uc, j, arow, lower, (x_in && uc) ? __ldg(a.agg + j) : 0, acc);
-        }
-    }
+    if (have) bgs_walk<T, B, FB, CG, G>(a, xt, x_in, uc, vb, VS, k0, kf, k1, jf, lowf, agf, arf, acc);
     acc = reduce_rows<T, FB>(acc, lane);
     // lanes 0..FB-1: the row sums of A_{f,*} x + A_ff x~ for this node
     T t = T(0);
@@ -526,6 +515,9 @@ __global__ void __launch_bounds__(TprBlock<FB>::kThreads) bgs_tpr_kernel(BgsArgs
         pdl_wait();
         pdl_trigger();
         if (have) {
+            // (a plain loop: the software-pipelined walk of bgs_node needs
+            // more registers, and at this mapping's occupancy that measured
+            // slower on levels far larger than L2)
             bgs_block<T, B, FB, false>(a, xt, x_in, uc, jf, arf, lowf, agf, acc);
 #pragma unroll(G > 1 ? 8 : 4)
             for (int k = kf + G; k < k1; k += G) {
