@@ -160,9 +160,18 @@ typedef struct {
     int schwarz_overlap; /* layers of neighbours added to each Schwarz subdomain: 1 (default,
                          the paper's overlap one) or 0 (block Jacobi over the aggregates)     */
     int ortho;        /* Arnoldi orthogonalisation of fgmres_solve: 0 (default) = classical
-                         Gram-Schmidt with a second projection only where the first removed
-                         more than half of ||w||^2 (the DGKS test); 1 = classical Gram-Schmidt
-                         applied twice at every step. Batches use 1.                          */
+                         Gram-Schmidt with a second projection only where the norm of w left
+                         after the first is below 0.01 of the norm before it (the selective
+                         test of Daniel, Gragg, Kaufman and Stewart with eta = 0.01); 1 =
+                         classical Gram-Schmidt applied twice at every step. Batches use 1.   */
+    int coarse_tc;    /* FP32 coarsest solve (coarse_prec 32) of 224 to 2048 unknowns: 1 (default)
+                         = blocked LU with partial pivoting (panels of 16 columns) and the
+                         inverse by blocked triangular solves on the identity, every matrix
+                         product of both on the tensor cores (tcgen05 kind::tf32, each FP32
+                         operand split into two TF32 parts, three products per pair: FP32
+                         accuracy); 0 = the CUDA-core cooperative LU and column-by-column
+                         inverse. Pivots may differ between the two (ties, rounding); both
+                         are backward stable.                                                 */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */
@@ -470,6 +479,24 @@ int amg_profile_read(bamg_t h, int kind, double* ms, long long* launches, double
  * FGMRES kernels, which belong to no level); clears only those. */
 int amg_profile_read_level(bamg_t h, int kind, int level, double* ms, long long* launches, double* bytes,
                            double* flops);
+
+/* Dense kernels of the coarsest direct solve (Sec. 4.1), callable on their own;
+ * both synchronise the stream and allocate (and free) their scratch.
+ *
+ * amg_dense_inverse_f32: inv = a^-1 for a row-major nd x nd FP32 matrix a on
+ * the device (a is not modified: a copy is factored), by LU with partial
+ * pivoting.  method 1: the tensor-core path of coarse_tc (0 < nd <= 2048, else
+ * BAMG_EUNSUPPORTED); 0: the CUDA-core LU and column-by-column inverse.
+ * BAMG_ESINGULAR_COARSE: a pivot below 1e-9 ||a||_inf; BAMG_ETIMEOUT: a
+ * bounded wait of a tensor-core kernel ran out.
+ *
+ * amg_gemm_tc_f32: C += A B, row-major FP32 on the device (A m x k, B k x n,
+ * C m x n; leading dimensions lda >= k, ldb >= n, ldc >= n; C may not overlap
+ * A or B), on the tensor cores: tcgen05 kind::tf32 with each operand split
+ * into two TF32 parts and three products per pair (FP32 accuracy). */
+int amg_dense_inverse_f32(int nd, const float* a, float* inv, int method, void* stream);
+int amg_gemm_tc_f32(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                    void* stream);
 
 /* number of kernels this library has launched in the process so far (kernels
  * replayed from a captured graph count once per replay) */

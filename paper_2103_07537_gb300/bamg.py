@@ -28,7 +28,7 @@ EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_
            "amg_profile", "amg_profile_read", "amg_profile_read_level", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
            "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
            "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
-           "amg_level_p", "amg_setup_fields", "amg_level_fields"]
+           "amg_level_p", "amg_setup_fields", "amg_level_fields", "amg_dense_inverse_f32", "amg_gemm_tc_f32"]
 
 #: network sizes (include/bamg.h)
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -51,7 +51,7 @@ class AmgParams(C.Structure):
                 ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int),
                 ("use_pdl", C.c_int), ("coarse_prec", C.c_int), ("tail_grid", C.c_int),
                 ("value_layout", C.c_int), ("sweep", C.c_int), ("sub_solver", C.c_int),
-                ("schwarz_overlap", C.c_int), ("ortho", C.c_int)]
+                ("schwarz_overlap", C.c_int), ("ortho", C.c_int), ("coarse_tc", C.c_int)]
 
 
 class BamgError(RuntimeError):
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
         lib.amg_launch_count.argtypes = []
         lib.amg_launch_count.restype = C.c_longlong
         lib.amg_colour_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
+        lib.amg_dense_inverse_f32.argtypes = [C.c_int, _vp, _vp, C.c_int, _vp]
+        lib.amg_gemm_tc_f32.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
         lib.amg_setup_batched.argtypes = [C.c_int, _ip, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _ip,
                                           C.POINTER(AmgParams), _vp, C.POINTER(_vp)]
         lib.fgmres_solve_batched.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _ip, _dp, _vp]
@@ -372,6 +374,24 @@ def amg_profile_read_level(handle: int, kind, level: int) -> dict:
 
 def amg_launch_count() -> int:
     return int(load().amg_launch_count())
+
+
+def amg_dense_inverse_f32(a, inv, method: int = 1, stream=None) -> None:
+    """inv = a^-1 for a square contiguous FP32 device tensor a (row-major) by LU
+    with partial pivoting; method 1 = tensor cores, 0 = CUDA cores."""
+    nd = int(a.shape[0])
+    st = load().amg_dense_inverse_f32(nd, _ptr(a), _ptr(inv), int(method), _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_dense_inverse_f32")
+
+
+def amg_gemm_tc_f32(A, B, C_, stream=None) -> None:
+    """C_ += A @ B on the tensor cores (contiguous row-major FP32 device tensors)."""
+    m, k = int(A.shape[0]), int(A.shape[1])
+    n = int(B.shape[1])
+    st = load().amg_gemm_tc_f32(m, n, k, _ptr(A), k, _ptr(B), n, _ptr(C_), n, _stream(stream))
+    if st != BAMG_OK:
+        raise BamgError(st, "amg_gemm_tc_f32")
 
 
 def amg_colour_noalloc(row_ptr, col_idx, n_nodes: int, colour, n_colours, stream=None) -> None:

@@ -236,6 +236,7 @@ struct bamg_ctx {
     double *coarse_a = nullptr, *coarse_inv = nullptr;
     float* coarse_inv32 = nullptr;  // the FP32 inverse (coarse_prec 32), else null
     int* coarse_piv = nullptr;
+    bool coarse_tc_used = false;  // the FP32 coarsest LU and inverse ran on the tensor cores
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -331,6 +332,76 @@ struct bamg_ctx {
         if (_st != BAMG_OK) return _st; \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// dense kernels of the coarsest solve on their own
+// ---------------------------------------------------------------------------
+namespace {
+struct DevBufs {  // device buffers freed on every return path
+    std::vector<void*> p;
+    ~DevBufs() {
+        for (void* q : p) cudaFree(q);
+    }
+    template <typename T>
+    int get(T** out, size_t count) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(T) + 64) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return BAMG_ECUDA;
+        }
+        p.push_back(q);
+        *out = static_cast<T*>(q);
+        return BAMG_OK;
+    }
+};
+int read_flag(const int* d_err, cudaStream_t s) {
+    int e = 0;
+    BAMG_CUDA_TRY(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return map_dev_error(e);
+}
+}  // namespace
+
+extern "C" int amg_dense_inverse_f32(int nd, const float* a, float* inv, int method, void* stream) {
+    if (nd <= 0 || !a || !inv || (method != 0 && method != 1)) return BAMG_EINVAL;
+    if (method == 1 && !tc_lu_supported(nd)) return BAMG_EUNSUPPORTED;
+    if ((long)nd > kMaxCoarseDense) return BAMG_EUNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBufs d;
+    float *f = nullptr, *x = nullptr, *w32 = nullptr;
+    int *piv = nullptr, *err = nullptr;
+    double* w64 = nullptr;
+    const size_t nn = (size_t)nd * nd;
+    TRY(d.get(&f, nn));
+    TRY(d.get(&x, nn));
+    TRY(d.get(&piv, (size_t)nd));
+    TRY(d.get(&err, 1));
+    BAMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    BAMG_CUDA_TRY(cudaMemcpyAsync(f, a, nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (method == 1) {
+        TRY(d.get(&w32, (size_t)tc_lu_scratch_floats(nd)));
+        TRY(dense_lu_inverse_tc(nd, f, piv, inv, x, w32, err, s));
+    } else {
+        TRY(d.get(&w64, (size_t)dense_lu_scratch(nd)));
+        TRY(dense_lu_inverse<float>(nd, f, piv, inv, x, w64, err, s));
+    }
+    return read_flag(err, s);
+}
+
+extern "C" int amg_gemm_tc_f32(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C,
+                               int ldc, void* stream) {
+    if (m < 0 || n < 0 || k < 0 || lda < k || ldb < n || ldc < n || (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B)))))
+        return BAMG_EINVAL;
+    if (m == 0 || n == 0) return BAMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBufs d;
+    int* err = nullptr;
+    TRY(d.get(&err, 1));
+    BAMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    TRY(launch_tc_gemm(m, n, k, A, lda, B, ldb, C, ldc, C, ldc, 1.f, err, s));
+    return read_flag(err, s);
+}
+
+
 // read the device error flags (synchronises s)
 static int check_dev(bamg_ctx* h, cudaStream_t s) {
     BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -411,6 +482,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->sub_solver = 0;
     p->schwarz_overlap = 1;
     p->ortho = 0;
+    p->coarse_tc = 1;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -1284,8 +1356,17 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
             TRY(h->alloc(&lt32, (size_t)(nd * nd)));
             TRY(h->alloc(&h->coarse_inv32, (size_t)(nd * nd)));
             TRY(launch_convert_d2f(nd * nd, h->coarse_a, a32, s));
-            TRY(dense_lu_inverse<float>((int)nd, a32, h->coarse_piv, h->coarse_inv32, lt32, col, h->d_err, s));
-            TRY(check_dev(h, s));
+            h->coarse_tc_used = h->p.coarse_tc == 1 && nd > kCoarseTcMin && tc_lu_supported((int)nd);
+            if (h->coarse_tc_used) {
+                float* work32 = nullptr;
+                TRY(h->alloc(&work32, (size_t)tc_lu_scratch_floats((int)nd)));
+                TRY(dense_lu_inverse_tc((int)nd, a32, h->coarse_piv, h->coarse_inv32, lt32, work32, h->d_err, s));
+                TRY(check_dev(h, s));
+                h->release(work32);
+            } else {
+                TRY(dense_lu_inverse<float>((int)nd, a32, h->coarse_piv, h->coarse_inv32, lt32, col, h->d_err, s));
+                TRY(check_dev(h, s));
+            }
             h->release(lt32);
             h->release(a32);
         } else {
@@ -1386,7 +1467,8 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         (prm.coarse_prec != 64 && prm.coarse_prec != 32) || (prm.coarse_prec == 32 && prm.cycle_prec != 32) ||
         (prm.tail_grid != 0 && prm.tail_grid != 1) || prm.value_layout < 0 || prm.value_layout > 2 ||
         prm.sweep < 0 || prm.sweep > 3 || prm.sub_solver < 0 || prm.sub_solver > 2 ||
-        prm.schwarz_overlap < 0 || prm.schwarz_overlap > 1 || prm.ortho < 0 || prm.ortho > 1)
+        prm.schwarz_overlap < 0 || prm.schwarz_overlap > 1 || prm.ortho < 0 || prm.ortho > 1 ||
+        prm.coarse_tc < 0 || prm.coarse_tc > 1)
         return BAMG_EINVAL;
     if (prm.sub_solver != 0) {
         // the cycle with another sub-solve runs as separate launches: no
@@ -2516,7 +2598,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
-                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};

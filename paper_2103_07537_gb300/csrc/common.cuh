@@ -484,6 +484,21 @@ int coarse_dense(int b, int n, const int* rp, const int* ci, const double* vals,
 long dense_lu_scratch(int nd);
 template <typename T>
 int dense_lu_inverse(int nd, T* a, int* piv, T* inv, T* lt, double* work, int* err, cudaStream_t s);
+
+// FP32 dense LU with partial pivoting and inverse on the tensor cores
+// (k_dense_tc.cu) for 0 < nd <= 2048: a (row-major nd x nd) is factored in
+// place (P a = L U), inv = a^-1 (row-major), pos[r] = position of row r after
+// pivoting; x: nd*nd floats of scratch, work: tc_lu_scratch_floats(nd)
+// floats.  A pivot below 1e-9 ||a||_inf sets kDevSingularCoarse, a bounded
+// wait that ran out kDevTimeout (in *err).
+constexpr int kCoarseTcMin = 223;  // smaller coarsest matrices: the one-CTA shared-memory LU
+bool tc_lu_supported(int nd);
+long tc_lu_scratch_floats(int nd);
+int dense_lu_inverse_tc(int nd, float* a, int* pos, float* inv, float* x, float* work, int* err, cudaStream_t s);
+// C = D + sign * A B, row-major FP32 (m x k, k x n; D may be C or null) on the
+// tensor cores with FP32 accuracy (three TF32 products per operand pair)
+int launch_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, const float* D, int ldd,
+                   float* C, int ldc, float sign, int* err, cudaStream_t s);
 int exclusive_scan(int n, const int* in, int* out, int* d_tmp, long tmp_bytes, cudaStream_t s);
 long scan_tmp_bytes(int n);
 int launch_convert_d2f(long m, const double* x, float* y, cudaStream_t s);

@@ -92,3 +92,25 @@ def test_coarse_prec_validation():
         with pytest.raises(bamg.BamgError) as e:
             make_solver(s, max_levels=2, max_coarse=0, **kw)
         assert e.value.status == bamg.BAMG_EINVAL
+
+
+@pytest.mark.parametrize("coarse_tc", [1, 0])
+def test_fp32_coarse_tensor_core_switch(coarse_tc):
+    """Coarsest matrices above the one-CTA size go to the tensor-core LU by
+    default (coarse_tc 1); coarse_tc 0 keeps the CUDA-core LU.  Both stay within
+    the LU bound."""
+    s = P.mhd2d(12, 5)  # nd 1014
+    a = dense(s)
+    nd = a.shape[0]
+    g = make_solver(s, max_levels=1, cycle_prec=32, coarse_prec=32, coarse_tc=coarse_tc)
+    st = g.stats()
+    assert st["coarse_tc"] == coarse_tc
+    r = P.uniform_pm1(22, 0, nd)
+    z = torch.empty(nd, dtype=torch.float64, device="cuda")
+    g.apply(dev(r), z)
+    torch.cuda.synchronize()
+    zs = np.linalg.solve(a, r)
+    err = np.abs(z.cpu().numpy() - zs).max() / np.abs(zs).max()
+    assert err <= 4.0 * nd * U32 * np.linalg.cond(a, np.inf)
+    small = make_solver(P.random_block_system(6, 6, [0] * 6, seed=3), max_levels=1, cycle_prec=32, coarse_prec=32)
+    assert small.stats()["coarse_tc"] == 0  # 216 unknowns: the one-CTA LU
