@@ -78,8 +78,9 @@ typedef struct {
                          row's blocks); 5 = as 4 with every node's row staged in shared memory
                          by asynchronous copies ahead of use (levels whose steps read whole blocks:
                          one field, or the field-major layout; elsewhere 4; the same values
-                         as 4 bit for bit); 1 also times the variants of 3, 4 and 5, and the
-                         persistent sweep (see sweep). With 1 the choices are kept for the
+                         as 4 bit for bit); 6 = four warps per smoother node, one node per
+                         CTA, thread-per-row SpMV (long rows on small levels); 1 also times the
+                         variants of 3, 4, 5 and 6, and the persistent sweep (see sweep). With 1 the choices are kept for the
                          life of the process per level shape (device, sizes of the level and
                          of its colours, block and field shape, precision, layout, launch mode,
                          sub-solver): a later setup of a level of the same shape reuses them

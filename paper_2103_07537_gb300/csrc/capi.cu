@@ -124,11 +124,11 @@ struct Level {
     int agg_rounds = 0, colour_rounds = 0;
     // row mapping chosen for this level: smoother 0 warp per node, 1 thread per row, 2 thread per
     // row in half-size CTAs, 3 four lanes per row, 4 four lanes per row with the rows staged in
-    // shared memory by asynchronous copies (steps from a zero iterate use 3); residual 0 warp per
-    // row, 1 thread per row
+    // shared memory by asynchronous copies (steps from a zero iterate use 3), 5 four warps per
+    // node; residual 0 warp per row, 1 thread per row
     int bgs_tpr = 0, spmv_tpr = 0;
     // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split
-    float tune_us[7] = {0, 0, 0, 0, 0, 0, 0};
+    float tune_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int max_row = 0;  // stored blocks in the longest row (the staged smoother's slot size)
     // persistent sweep: 0 = one launch per colour (bgs_tpr), 1 = every colour of a field step
     // in one launch (thread per row), 2 = the same with four lanes per row; the plan exists
@@ -782,6 +782,7 @@ static SweepArgs sweep_args(bamg_ctx* h, const Level& L, int c_lo, int c_hi) {
 // which gives the same values)
 template <typename T>
 static int launch_colour_step(bamg_ctx* h, const Level& L, const BgsArgs& a, cudaStream_t s) {
+    if (L.bgs_tpr == 5) return launch_bgs_colour_wide<T>(h->b, h->fb, a, s);
     if (L.bgs_tpr == 4 && a.x_in) return launch_bgs_colour_staged<T>(h->b, h->fb, a, L.max_row, h->d_err, s);
     if (L.bgs_tpr == 4) return launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, 2);
     return L.bgs_tpr ? launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, L.bgs_tpr - 1)
@@ -820,7 +821,7 @@ static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int rep
 // fields, precision, value layout, launch mode and sub-solver.
 struct TuneRec {
     int bgs_tpr, spmv_tpr, sweep;
-    float tune_us[7], tune_step_us[3];
+    float tune_us[8], tune_step_us[3];
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, TuneRec>> g_tune;  // small: one entry per distinct level shape
@@ -906,6 +907,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         L.tune_us[5] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_tpr<T>(b, h->fb, a, s, 2); });
         L.tune_us[6] = time_launch(s, e0, e1, reps,
                                    [&] { return launch_bgs_colour_staged<T>(b, h->fb, a, L.max_row, h->d_err, s); });
+        L.tune_us[7] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_wide<T>(b, h->fb, a, s); });
         const T* x = static_cast<const T*>(L.xa);
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
@@ -922,9 +924,9 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         if (h->p.autotune >= 2) L.bgs_tpr = h->p.autotune - 1;
         else if (h->p.autotune == 1) {
             // the fastest thread-per-row variant replaces warp per node only by the margin
-            const float tv[4] = {L.tune_us[1], L.tune_us[4], L.tune_us[5], L.tune_us[6]};
+            const float tv[5] = {L.tune_us[1], L.tune_us[4], L.tune_us[5], L.tune_us[6], L.tune_us[7]};
             int best = 0;
-            for (int v = 1; v < 4; ++v)
+            for (int v = 1; v < 5; ++v)
                 if (tv[v] < tv[best]) best = v;
             L.bgs_tpr = tv[best] < kTuneMargin * L.tune_us[0] ? best + 1 : 0;
         }
@@ -1099,6 +1101,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&w.state, (size_t)L.n));
         TRY(h->alloc(&w.rootid, (size_t)L.n + 1));
         TRY(h->alloc(&w.agg1, (size_t)L.n));
+        TRY(h->alloc(&w.settled, (size_t)L.n));
         TRY(h->alloc(&w.flag, 4));
         TRY(h->alloc(&d_count, 4));
         TRY(h->alloc(&scan_tmp, (size_t)stb / sizeof(int) + 1));
@@ -1138,6 +1141,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(w.state);
         h->release(w.rootid);
         h->release(w.agg1);
+        h->release(w.settled);
         if (nc == 0 || nc == L.n) break;  // no coarsening possible
         L.n_agg = nc;
         TRY(h->alloc(&L.agg_ptr, (size_t)nc + 1));
@@ -1459,7 +1463,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 5 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        prm.autotune < 0 || prm.autotune > 6 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
@@ -2619,6 +2623,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
              ",\"smoother_mapping\":\"" + (L.sweep == 2     ? "sweep-split"
                                           : L.sweep        ? "sweep"
+                                          : L.bgs_tpr == 5 ? "wide"
                                           : L.bgs_tpr == 4 ? "staged"
                                           : L.bgs_tpr == 3 ? "thread-split"
                                           : L.bgs_tpr == 2 ? "thread-half"
@@ -2631,8 +2636,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              (L.spmv_tpr ? "thread" : "warp") + "\",\"tune_us\":[" + std::to_string(L.tune_us[0]) + "," +
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
-             std::to_string(L.tune_us[5]) + "," + std::to_string(L.tune_us[6]) +
-             "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
+             std::to_string(L.tune_us[5]) + "," + std::to_string(L.tune_us[6]) + "," +
+             std::to_string(L.tune_us[7]) + "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0");
         if (h->nf > 1) {
             o += ",\"field_nodes\":[";

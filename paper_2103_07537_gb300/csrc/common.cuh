@@ -287,6 +287,9 @@ struct BgsArgs {
 };
 template <typename T>
 int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s);
+// the same step with four warps per node, one node per CTA (long rows, small colours)
+template <typename T>
+int launch_bgs_colour_wide(int b, int fb, const BgsArgs& a, cudaStream_t s);
 // FP32 copy of block-major FP64 values in the field-major layout of vrow
 int launch_convert_fieldmajor(int n, int b, int fb, const int* rp, const double* x, float* y, cudaStream_t s);
 // lowk[k] = 1 where block k of row i has a column j != i with colour[j] < colour[i]
@@ -441,6 +444,7 @@ struct AggWork {
     int* agg1;    // [n]
     int* flag;    // [1] device
     int* host_flag;  // pinned host [1]
+    unsigned char* settled = nullptr;  // [n] optional: nodes whose neighbourhood is decided
 };
 // d_count: 2 device ints (aggregate count, error flag); w.host_flag: 2 pinned ints
 int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, int* d_count,

@@ -176,10 +176,15 @@ enum : int { kUndecided = 0, kRoot = 1, kOut = 2 };
 // New roots of one round are pairwise at distance >= 3, and a node becomes a
 // root exactly when every lower node within distance 2 is out: the rounds
 // reach the sequential ascending-order result.
+// A node with no undecided node in {i} + N(i) is settled: its m1 (none) and
+// r1 (a root in N(i): no new root can appear there) never change again, so
+// later rounds skip it (settled: optional, zeroed before the first round).
 __global__ void mis2_pass1_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                  const int* __restrict__ state, int* __restrict__ m1, int* __restrict__ r1) {
+                                  const int* __restrict__ state, int* __restrict__ m1, int* __restrict__ r1,
+                                  unsigned char* __restrict__ settled) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (settled && settled[i]) return;
     int mn = 0x7fffffff, root = 0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {  // the row contains i itself (diagonal block)
         const int j = ci[k];
@@ -189,6 +194,7 @@ __global__ void mis2_pass1_kernel(int n, const int* __restrict__ rp, const int* 
     }
     m1[i] = mn;
     r1[i] = root;
+    if (settled && mn == 0x7fffffff) settled[i] = 1;
 }
 
 __global__ void mis2_pass2_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
@@ -263,6 +269,7 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
                     int* d_scan_tmp, long scan_tmp_b, cudaStream_t s, int* rounds_out) {
     const int threads = 256, blocks = ceil_div(n, threads);
     BAMG_CUDA_TRY(cudaMemsetAsync(w.state, 0, sizeof(int) * (size_t)n, s));
+    if (w.settled) BAMG_CUDA_TRY(cudaMemsetAsync(w.settled, 0, (size_t)n, s));
     const int batch = 16;
     const long max_rounds = 4L * n + 64;
     long rounds = 0;
@@ -270,7 +277,7 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
         for (int r = 0; r < batch; ++r) {
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
             // agg1 and rootid serve as m1 and r1 during the rounds
-            mis2_pass1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.agg1, w.rootid);
+            mis2_pass1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.agg1, w.rootid, w.settled);
             mis2_pass2_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.agg1, w.rootid, w.state, w.flag);
         }
         note_launch(2 * batch);

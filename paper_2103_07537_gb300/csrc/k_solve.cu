@@ -356,6 +356,105 @@ int launch_bgs_colour(int b, int fb, const BgsArgs& a, cudaStream_t s) {
 template int launch_bgs_colour<double>(int, int, const BgsArgs&, cudaStream_t);
 template int launch_bgs_colour<float>(int, int, const BgsArgs&, cudaStream_t);
 
+// One colour of one field step with W warps per node, one node per CTA (the
+// same arithmetic as bgs_node; row sums in another order): warp w takes the
+// row's blocks w G + kk, w G + kk + W G, ... (G blocks per warp pass), the W
+// partial row sums meet in shared memory in warp order, and warp 0 finishes
+// the node.  W times shorter chains of dependent loads per node than one warp
+// per node: for levels whose rows are long and whose colours are small.
+template <typename T, int B, int FB, int W, bool FM>
+__global__ void __launch_bounds__(W * 32) bgs_wide_kernel(BgsArgs a) {
+    __shared__ T part[W][FB];
+    const long q = blockIdx.x;
+    if (q >= a.n_in_colour) return;  // whole CTA
+    constexpr int G = kWarp / FB;  // blocks of the row per warp pass
+    const int lane = threadIdx.x & (kWarp - 1), w = threadIdx.x >> 5;
+    const int kk = lane / FB;
+    const int r = lane - kk * FB;
+    const int f0 = a.field * FB;
+    const T* __restrict__ vals = static_cast<const T*>(a.vals);
+    const T* x_in = static_cast<const T*>(a.x_in);
+    const T* uc = static_cast<const T*>(a.uc);
+    const T* xt = static_cast<const T*>(a.xt);
+    const int i = __ldg(a.nodes + q);
+    const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+    T drow[FB];
+    if (w == 0 && lane < FB) {
+        const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)lane * FB;
+#pragma unroll
+        for (int c = 0; c < FB; ++c) drow[c] = __ldg(D + c);
+    }
+    // the lane's first block before the wait (as in bgs_node)
+    const int kf = k0 + w * G + kk;
+    const bool have = kk < G && kf < k1;
+    const int kq = min(kf, k1 - 1);
+    const int jf = __ldg(a.ci + kq);
+    const bool lowf = __ldg(a.lowk + kq) != 0;
+    const T* vb = vrow<T, B, FB, FM>(vals, k0, k1, k0, f0 + r);
+    constexpr int VS = vstride<T, B, FB, FM>();
+    T arf[B];
+    if (x_in || lowf) load_row<T, B>(vb + (size_t)(kq - k0) * VS, arf);
+    const int agf = (x_in && uc) ? __ldg(a.agg + jf) : 0;
+    pdl_wait();
+    pdl_trigger();
+    const T bi = (w == 0 && lane < FB) ? static_cast<const T*>(a.rhs)[(size_t)i * B + f0 + lane] : T(0);
+    T acc = T(0);
+    if (have) bgs_walk<T, B, FB, false, W * G>(a, xt, x_in, uc, vb, VS, k0, kf, k1, jf, lowf, agf, arf, acc);
+    acc = reduce_rows<T, FB>(acc, lane);
+    if (lane < FB) part[w][lane] = acc;
+    __syncthreads();
+    if (w != 0) return;
+    acc = T(0);
+    if (lane < FB)
+#pragma unroll
+        for (int ww = 0; ww < W; ++ww) acc += part[ww][lane];
+    T t = T(0);
+    if (lane < FB) t = bi - acc;
+    T xn = T(0);
+#pragma unroll
+    for (int c = 0; c < FB; ++c) {
+        const T tc = __shfl_sync(0xffffffffu, t, c);
+        if (lane < FB) xn = fma(drow[c], tc, xn);
+    }
+    if (lane < FB) static_cast<T*>(a.xt)[(size_t)i * FB + lane] = xn;
+    const T xf = __shfl_sync(0xffffffffu, xn, (lane - f0) & (kWarp - 1));
+    if (lane < B) {
+        const size_t e = (size_t)i * B + lane;
+        T v = x_in ? x_in[e] : T(0);
+        if (x_in && uc) v += uc[(size_t)__ldg(a.agg + i) * B + lane];
+        if (lane >= f0 && lane < f0 + FB) {
+            const T om = a.omega_node ? static_cast<const T*>(a.omega_node)[(size_t)i * a.F + a.field] : T(a.omega);
+            v = fma(om, xf, v);
+        }
+        static_cast<T*>(a.x_out)[e] = v;
+    }
+}
+
+constexpr int kWideWarps = 4;
+
+template <typename T>
+int launch_bgs_colour_wide(int b, int fb, const BgsArgs& a, cudaStream_t s) {
+    if (a.n_in_colour <= 0) return BAMG_OK;
+    const int blocks = a.n_in_colour;
+    switch (b * 16 + fb) {
+#define CASE(BB, FF) \
+    case BB * 16 + FF:                                                                                          \
+        if ((a.fm && HasFm<T, BB, FF>::value                                                                    \
+                 ? launch_k(bgs_wide_kernel<T, BB, FF, kWideWarps, HasFm<T, BB, FF>::value>, blocks, kWideWarps * 32, \
+                            0, s, a)                                                                            \
+                 : launch_k(bgs_wide_kernel<T, BB, FF, kWideWarps, false>, blocks, kWideWarps * 32, 0, s, a)) !=   \
+            cudaSuccess)                                                                                        \
+            return BAMG_ECUDA;                                                                                  \
+        break;
+        BAMG_BLOCK_SHAPES(CASE)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return launched(1);
+}
+template int launch_bgs_colour_wide<double>(int, int, const BgsArgs&, cudaStream_t);
+template int launch_bgs_colour_wide<float>(int, int, const BgsArgs&, cudaStream_t);
+
 // lowk[k] for every block of row i: its column j != i has a lower colour
 __global__ void lower_flags_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                    const int* __restrict__ colour, unsigned char* __restrict__ lowk) {

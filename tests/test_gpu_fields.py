@@ -94,7 +94,8 @@ def test_field_hierarchy_matches_oracle(name):
     assert st["levels"][0]["field_nodes"] == np.diff(SYSTEMS[name]()[0][3]).tolist()
 
 
-@pytest.mark.parametrize("mapping", [dict(autotune=0), dict(autotune=2), dict(autotune=3), dict(autotune=4)])
+@pytest.mark.parametrize("mapping", [dict(autotune=0), dict(autotune=2), dict(autotune=3), dict(autotune=4),
+                                     dict(autotune=6)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_field_vcycle_fp64_matches_oracle(name, mapping):
     g, o, (rp, ci, vals, off) = make(SYSTEMS[name](), **mapping)
@@ -200,12 +201,16 @@ def test_field_invalid_inputs_are_rejected():
         assert e.value.status == bamg.BAMG_EINVAL
 
 
+@pytest.mark.parametrize("at", [0, 6])
 @pytest.mark.parametrize("sub", [0, 1, 2])
 @pytest.mark.parametrize("prec", [64, 32])
-def test_programmatic_launches_give_identical_node_field_cycles(prec, sub):
+def test_programmatic_launches_give_identical_node_field_cycles(prec, sub, at):
     # the other fields' nodes are copied by a kernel of the cycle, so the
     # cycle runs with programmatic dependent launches: same bits as without
+    # (the row mapping fixed: warp per node, or four warps per node; the
+    # autotuner could pick mappings with another summation order for the two)
     (rp, ci, vals, off), kw = SYSTEMS["q2q1_21_ragged"]()
+    kw = dict(kw, autotune=at)
     args = (off, dev(rp), dev(ci), dev(vals.reshape(-1)), vals.shape[1])
     zs = []
     n, b = len(rp) - 1, vals.shape[1]

@@ -121,7 +121,7 @@ def test_hierarchy_matches_oracle(name):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mapping", [dict(tail_dofs=0, autotune=0), dict(tail_dofs=65536, autotune=0),
                                      dict(tail_dofs=0, autotune=2), dict(tail_dofs=0, autotune=3),
-                                     dict(tail_dofs=0, autotune=4)])
+                                     dict(tail_dofs=0, autotune=4), dict(tail_dofs=0, autotune=6)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_vcycle_fp64_matches_oracle(name, mapping):
     s, kw = SYSTEMS[name]()
@@ -366,7 +366,8 @@ def test_nonfinite_rhs_reported():
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-def test_programmatic_dependent_launch_gives_identical_cycles(prec):
+@pytest.mark.parametrize("at", [0, 6])
+def test_programmatic_dependent_launch_gives_identical_cycles(prec, at):
     """The V-cycle with programmatic dependent launches (default) and with
     ordinary launches: identical bits, replayed from the graph and direct."""
     s = P.mhd2d(41, 3)
@@ -375,7 +376,7 @@ def test_programmatic_dependent_launch_gives_identical_cycles(prec):
     for pdl in (1, 0):
         for graph in (1, 0):
             sol = make_solver(s, max_levels=4, max_coarse=0, cycle_prec=prec, use_pdl=pdl, use_graph=graph,
-                              autotune=0)
+                              autotune=at)
             z = torch.empty_like(r)
             for _ in range(3):  # repeated cycles reuse every buffer
                 sol.apply(r, z)
@@ -405,3 +406,29 @@ def test_large_coarsest_factorisation(s_fn, levels):
     st, it, rr = sol.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=500)
     _, it_o, _, ok = ref.fgmres(s.rhs, tol=1e-8, restart=30, max_iter=500)
     assert st == 0 and ok and abs(it - it_o) <= 1
+
+
+@pytest.mark.parametrize("n_side,seed", [(220, 1), (300, 2)])
+def test_colouring_frontiers_on_permuted_graph(n_side, seed):
+    """Graphs above the one-CTA worklist size are coloured by frontier rounds;
+    on a randomly renumbered stencil graph (irregular lower/higher neighbour
+    structure) the colours must equal the oracle's sequential first fit."""
+    s = P.random_block_system(n_side, 1, [0], seed)
+    n = s.n_nodes
+    assert n > 40000
+    perm = np.random.default_rng(seed).permutation(n)  # new index of old node i
+    inv = np.argsort(perm)
+    rows = []
+    for new in range(n):
+        old = inv[new]
+        k0, k1 = s.row_ptr[old], s.row_ptr[old + 1]
+        cols = perm[s.col_idx[k0:k1]]
+        order = np.argsort(cols)
+        rows.append((cols[order], s.vals[k0:k1][order]))
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(c) for c, _ in rows])
+    ci = np.concatenate([c for c, _ in rows]).astype(np.int32)
+    va = np.concatenate([v for _, v in rows])
+    g = bamg.Solver(dev(rp), dev(ci), dev(np.ascontiguousarray(va).reshape(-1)), 1, [0], max_levels=3, max_coarse=0)
+    want, _ = oracle.colour(rp, ci)
+    assert np.array_equal(g.level(0)["colour"], want)
