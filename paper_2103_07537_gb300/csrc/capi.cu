@@ -928,7 +928,11 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             int best = 0;
             for (int v = 1; v < 5; ++v)
                 if (tv[v] < tv[best]) best = v;
-            L.bgs_tpr = tv[best] < kTuneMargin * L.tune_us[0] ? best + 1 : 0;
+            // (four warps per node replaces one warp per node on any win: the
+            // same per-node structure, and in the cycle, with programmatic
+            // dependent launches, it gained 7% on the 3D level 1 where the
+            // isolated timing saw 0.6-3%)
+            L.bgs_tpr = tv[best] < (best == 4 ? 1.0f : kTuneMargin) * L.tune_us[0] ? best + 1 : 0;
         }
         if (L.bgs_tpr == 4 && L.tune_us[6] >= 1e29f) L.bgs_tpr = 3;  // the staged kernel does not take this level
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
@@ -1831,6 +1835,16 @@ int prolong_explicit<float>(bamg_ctx* h, const Level& L, const float* uc, float*
                                            true, s);
 }
 
+// the residual after the pre-smoothing can be formed from the higher-colour
+// blocks alone (launch_residual_upper): one field, one sweep from zero of the
+// multicolour Gauss-Seidel sub-solve, one damping value for every node, the
+// thread-per-row residual mapping
+template <typename T>
+static bool upper_residual(const bamg_ctx* h, const Level& L) {
+    return h->F == 1 && h->nf <= 1 && h->p.n_pre == 1 && h->p.sub_solver == 0 && L.spmv_tpr && L.lowk &&
+           level_omega<T>(L) == nullptr;
+}
+
 // MGV(0, rhs, l) of Fig. 1 written to out
 template <typename T>
 static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
@@ -1947,6 +1961,15 @@ static int mgv(bamg_ctx* h, int l, const T* rhs, T* out, cudaStream_t s) {
         pr.x = res;
         pr.y = C.rhs;
         record(h, pr, rst_bytes, nb);
+    } else if (upper_residual<T>(h, L)) {
+        // one sweep from zero on a one-field level: only the higher-colour blocks
+        const double ub = (double)L.nnzb * 5.0 + (L.n + 1) * 4.0 + 0.5 * (L.nnzb - L.n) * (b * b * es + b * es) +
+                          3.0 * nb * es;
+        PL(BAMG_K_RESIDUAL, ub, (double)(L.nnzb - L.n) * b * b,
+           launch_residual_upper<T>(b, level_fm<T>(L), L.n, L.rp, L.ci, L.lowk, level_vals<T>(L),
+                                    static_cast<const T*>(L.xt), rhs, h->p.omega, res, s));
+        PL(BAMG_K_RESTRICT, rst_bytes, nb,
+           launch_restrict<T>(b, L.n_agg, L.agg_ptr, L.members, res, static_cast<T*>(C.rhs), s));
     } else {
         PL(BAMG_K_RESIDUAL, res_bytes, res_flops,
            L.spmv_tpr

@@ -384,6 +384,12 @@ int sweep_plan(int n, int C, int ntile, const int* nodes, const int* colour, con
 template <typename T>
 int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
                     const T* rhs, T* y, cudaStream_t s);
+// y = (1 - omega) rhs - omega (upper-colour part of A) xt: the residual after one
+// pre-smoothing sweep from zero of a one-field level with one damping value
+// (xt: the sweep's x~, lowk: the lower-colour flags)
+template <typename T>
+int launch_residual_upper(int b, int fm, int n, const int* rp, const int* ci, const unsigned char* lowk,
+                          const T* vals, const T* xt, const T* rhs, double omega, T* y, cudaStream_t s);
 
 // One recorded step of the V-cycle below the tail level, executed by the
 // cluster tail kernel (see k_solve.cu).

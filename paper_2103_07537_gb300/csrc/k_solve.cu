@@ -567,6 +567,68 @@ template int launch_spmv_tpr<double>(int, int, int, int, const int*, const int*,
 template int launch_spmv_tpr<float>(int, int, int, int, const int*, const int*, const float*, const float*,
                                     const float*, float*, cudaStream_t);
 
+// Residual after one pre-smoothing sweep from a zero iterate with one field
+// (F = 1) and one damping value: the sweep left x = omega x~ and, for every
+// node i, A_ii x~_i = b_i - sum over lower-colour j of A_ij x~_j (the
+// multicolour Gauss-Seidel step of Algorithm 1), so
+//   (b - A x)_i = (1 - omega) b_i - omega sum over higher-colour j of A_ij x~_j
+// (nodes of one colour do not couple): only the blocks of higher colour are
+// read, about half of the row.  Thread per scalar row.
+template <typename T, int B, bool FM>
+__global__ void __launch_bounds__(256) residual_upper_kernel(int n, const int* __restrict__ rp,
+                                                             const int* __restrict__ ci,
+                                                             const unsigned char* __restrict__ lowk,
+                                                             const T* __restrict__ vals, const T* __restrict__ xt,
+                                                             const T* __restrict__ rhs, T omega, T* __restrict__ y) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / B);
+    if (i >= n) return;
+    const int r = (int)(t - (long)i * B);
+    const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+    pdl_wait();
+    pdl_trigger();
+    T acc = T(0);
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(ci + k);
+        if (j == i || __ldg(lowk + k)) continue;
+        T a[B], xv[B];
+        load_row<T, B>(vrow<T, B, B, FM>(vals, k0, k1, k, r), a);
+        load_row<T, B>(xt + (size_t)j * B, xv);
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+    }
+    const size_t e = (size_t)i * B + r;
+    y[e] = (T(1) - omega) * rhs[e] - omega * acc;
+}
+
+// (one field: the values are block-major, fm is unused)
+template <typename T>
+int launch_residual_upper(int b, int fm, int n, const int* rp, const int* ci, const unsigned char* lowk,
+                          const T* vals, const T* xt, const T* rhs, double omega, T* y, cudaStream_t s) {
+    (void)fm;
+    if (n <= 0) return BAMG_OK;
+    const int blocks = ceil_div((long)n * b, 256);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (b) {
+#define CASE(BB)                                                                                          \
+    case BB:                                                                                              \
+        e = launch_k(residual_upper_kernel<T, BB, false>, blocks, 256, 0, s, n, rp, ci, lowk, vals, xt, rhs, \
+                     (T)omega, y);                                                                        \
+        break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    if (e != cudaSuccess) return BAMG_ECUDA;
+    return launched(1);
+}
+template int launch_residual_upper<double>(int, int, int, const int*, const int*, const unsigned char*,
+                                           const double*, const double*, const double*, double, double*,
+                                           cudaStream_t);
+template int launch_residual_upper<float>(int, int, int, const int*, const int*, const unsigned char*, const float*,
+                                          const float*, const float*, double, float*, cudaStream_t);
+
 // threads per CTA: a multiple of both FB and the warp size (the launch may use
 // half of it: smaller CTAs spread a small colour over more SMs)
 template <int FB>
