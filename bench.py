@@ -162,8 +162,8 @@ def reduce_timing(dist, ms, solved, device):
 # the sources that define the kernels of each kind (the shared header and the
 # public header are part of every kernel)
 KIND_SOURCES = {
-    "smooth": ["k_solve.cu"], "residual": ["k_solve.cu"], "cast": ["k_solve.cu"], "coarse": ["k_solve.cu"],
-    "tail": ["k_solve.cu"], "spmv": ["k_solve.cu"], "restrict": ["k_solve.cu", "k_transfer.cu"],
+    "smooth": ["k_solve.cu", "bgs_body.cuh"], "residual": ["k_solve.cu"], "cast": ["k_solve.cu"], "coarse": ["k_solve.cu"],
+    "tail": ["k_solve.cu", "bgs_body.cuh"], "spmv": ["k_solve.cu"], "restrict": ["k_solve.cu", "k_transfer.cu"],
     "prolong": ["k_solve.cu", "k_transfer.cu"], "krylov": ["k_krylov.cu"],
 }
 
@@ -681,10 +681,15 @@ def run_ours(args):
             tj = json.load(open(os.path.join(pdir, f)))
         except Exception:
             continue
+        # the capture's kernel: the same sources, kind and workload, and (when
+        # it names them) the same level and that level's smoother mapping
         mapping = tj.get("smoother_mapping")
+        lv = tj.get("level")
+        same_mapping = mapping is None or (
+            mapping == [x.get("smoother_mapping") for x in stats["levels"][:-1]] if isinstance(mapping, list)
+            else mapping == stats["levels"][dom_kl[1]].get("smoother_mapping"))
         if tj.get("source_digest") == source_digest(dom) and tj.get("kind") == dom and \
-                tj.get("workload") == args.workload and \
-                (mapping is None or mapping == [lv.get("smoother_mapping") for lv in stats["levels"][:-1]]):
+                tj.get("workload") == args.workload and (lv is None or lv == dom_kl[1]) and same_mapping:
             traffic = tj.get("dram_bytes_per_launch")
     if t_alu > t_mem:
         roofline = {"bound": "alu", "achieved": tfl, "peak": alu_peak_tflops, "unit": "TFLOP/s",
