@@ -935,6 +935,16 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             L.bgs_tpr = tv[best] < (best == 4 ? 1.0f : kTuneMargin) * L.tune_us[0] ? best + 1 : 0;
         }
         if (L.bgs_tpr == 4 && L.tune_us[6] >= 1e29f) L.bgs_tpr = 3;  // the staged kernel does not take this level
+        if (h->p.autotune == 1 && h->p.use_pdl && (L.bgs_tpr == 0 || L.bgs_tpr == 5)) {
+            // warp against four warps per node again in the cycle's launch mode:
+            // with programmatic dependent launches each kernel's loads before
+            // its wait overlap the previous launch, which favours the wider
+            // mapping (3D level 1: 7% faster in the cycle, within 3% alone)
+            PdlScope pdl(true);
+            const float tw = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
+            const float tv = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_wide<T>(b, h->fb, a, s); });
+            L.bgs_tpr = tv < tw ? 5 : 0;
+        }
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
         // one whole field step (every colour of field 0) as per-colour launches
         // in the chosen mapping against the persistent sweep, in the cycle's

@@ -167,6 +167,26 @@ int launch_check_pattern(int n, const int* rp, const int* ci, int* diag, int* er
 // ---------------------------------------------------------------------------
 enum : int { kUndecided = 0, kRoot = 1, kOut = 2 };
 
+// a launch with the programmatic-dependent-launch attribute (the round
+// kernels of aggregation and colouring)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_round(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+// the round kernels' grid: at most four CTAs per SM, a grid-stride loop beyond
+static int round_grid(int n, int threads) { return std::max(1, std::min(ceil_div(n, threads), 152 * 4)); }
+
+
+
 // One round in two one-hop passes over the states at the start of the round.
 // Pass 1: m1[i] = smallest undecided index in {i} + N(i) (INT_MAX if none),
 //         r1[i] = 1 if a root is in {i} + N(i).
@@ -179,39 +199,76 @@ enum : int { kUndecided = 0, kRoot = 1, kOut = 2 };
 // A node with no undecided node in {i} + N(i) is settled: its m1 (none) and
 // r1 (a root in N(i): no new root can appear there) never change again, so
 // later rounds skip it (settled: optional, zeroed before the first round).
-__global__ void mis2_pass1_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                  const int* __restrict__ state, int* __restrict__ m1, int* __restrict__ r1,
-                                  unsigned char* __restrict__ settled) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void mis2_pass1_node(int i, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const int* __restrict__ state, int* __restrict__ m1,
+                                                int* __restrict__ r1, unsigned char* __restrict__ settled) {
     if (settled && settled[i]) return;
     int mn = 0x7fffffff, root = 0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {  // the row contains i itself (diagonal block)
-        const int j = ci[k];
-        const int sj = state[j];
-        if (sj == kUndecided) mn = min(mn, j);
-        if (sj == kRoot) root = 1;
+    constexpr int U = 16;  // loads of a batch in flight together
+    const int k0 = rp[i], k1 = rp[i + 1];
+    for (int kb = k0; kb < k1; kb += U) {  // the row contains i itself (diagonal block)
+        int jj[U], sj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) jj[u] = kb + u < k1 ? ci[kb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) sj[u] = jj[u] >= 0 ? state[jj[u]] : kOut;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (sj[u] == kUndecided) mn = min(mn, jj[u]);
+            if (sj[u] == kRoot) root = 1;
+        }
     }
     m1[i] = mn;
     r1[i] = root;
     if (settled && mn == 0x7fffffff) settled[i] = 1;
 }
 
-__global__ void mis2_pass2_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                  const int* __restrict__ m1, const int* __restrict__ r1, int* __restrict__ state,
-                                  int* __restrict__ any_undecided) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// the rounds run as programmatic dependent launches (each is scheduled while
+// its predecessor drains and waits for it in hardware), a thread per node
+// (a grid-stride loop when launched smaller)
+__global__ void mis2_pass1_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const int* __restrict__ state, int* __restrict__ m1, int* __restrict__ r1,
+                                  unsigned char* __restrict__ settled) {
+    pdl_wait();
+    pdl_trigger();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        mis2_pass1_node(i, rp, ci, state, m1, r1, settled);
+}
+
+__device__ __forceinline__ void mis2_pass2_node(int i, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const int* __restrict__ m1, const int* __restrict__ r1,
+                                                int* __restrict__ state, int* __restrict__ any_undecided) {
     if (state[i] != kUndecided) return;
     int mn = 0x7fffffff, root = 0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const int j = ci[k];
-        mn = min(mn, m1[j]);
-        root |= r1[j];
+    constexpr int U = 16;  // loads of a batch in flight together
+    const int k0 = rp[i], k1 = rp[i + 1];
+    for (int kb = k0; kb < k1; kb += U) {
+        int jj[U], mj[U], rj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) jj[u] = kb + u < k1 ? ci[kb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            mj[u] = jj[u] >= 0 ? m1[jj[u]] : 0x7fffffff;
+            rj[u] = jj[u] >= 0 ? r1[jj[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            mn = min(mn, mj[u]);
+            root |= rj[u];
+        }
     }
     if (root) state[i] = kOut;
     else if (mn == i) state[i] = kRoot;
     else *any_undecided = 1;
+}
+
+__global__ void mis2_pass2_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const int* __restrict__ m1, const int* __restrict__ r1, int* __restrict__ state,
+                                  int* __restrict__ any_undecided) {
+    pdl_wait();
+    pdl_trigger();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        mis2_pass2_node(i, rp, ci, m1, r1, state, any_undecided);
 }
 
 __global__ void is_root_kernel(int n, const int* __restrict__ state, int* __restrict__ flag) {
@@ -277,8 +334,10 @@ int aggregate_nodes(int n, const int* rp, const int* ci, int* agg, AggWork& w, i
         for (int r = 0; r < batch; ++r) {
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
             // agg1 and rootid serve as m1 and r1 during the rounds
-            mis2_pass1_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.state, w.agg1, w.rootid, w.settled);
-            mis2_pass2_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, w.agg1, w.rootid, w.state, w.flag);
+            BAMG_CUDA_TRY(launch_round(mis2_pass1_kernel, blocks, threads, s, n, rp, ci, w.state, w.agg1, w.rootid,
+                                       w.settled));
+            BAMG_CUDA_TRY(launch_round(mis2_pass2_kernel, blocks, threads, s, n, rp, ci, w.agg1, w.rootid, w.state,
+                                       w.flag));
         }
         note_launch(2 * batch);
         rounds += batch;
@@ -354,30 +413,55 @@ int build_members(int n, int nc, const int* agg, int* agg_ptr, int* members, int
 // ---------------------------------------------------------------------------
 constexpr int kMaxColours = 128;
 
-__global__ void colour_round_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                    int* colour, int* flag) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void colour_round_node(int i, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                  int* colour, int* flag) {
     volatile int* col = colour;
     if (col[i] >= 0) return;
-    unsigned long long used[kMaxColours / 64] = {0ull, 0ull};
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const int j = ci[k];
-        if (j >= i) break;  // columns ascending
-        const int cj = col[j];
-        if (cj < 0) {
-            *flag = 1;
-            return;
+    // the row's columns and their colours U at a time: the loads of a batch
+    // are independent (one round trip each instead of one per neighbour)
+    constexpr int U = 16;
+    unsigned long long used0 = 0ull, used1 = 0ull;  // colours 0..63, 64..127
+    const int k0 = rp[i], k1 = rp[i + 1];
+    for (int kb = k0; kb < k1; kb += U) {
+        int jj[U], cj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) jj[u] = kb + u < k1 ? ci[kb + u] : i;
+#pragma unroll
+        for (int u = 0; u < U; ++u) cj[u] = jj[u] < i ? col[jj[u]] : 0;
+        bool lower_left = true;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (jj[u] >= i) {  // columns ascending: no lower neighbour after this one
+                lower_left = false;
+                continue;
+            }
+            if (cj[u] < 0) {  // a lower neighbour not coloured yet: next round
+                *flag = 1;
+                return;
+            }
+            if (cj[u] < 64) used0 |= 1ull << cj[u];
+            else if (cj[u] < kMaxColours) used1 |= 1ull << (cj[u] - 64);
         }
-        if (cj < kMaxColours) used[cj >> 6] |= 1ull << (cj & 63);
+        if (!lower_left) break;
     }
-    int c = 0;
-    while (c < kMaxColours && (used[c >> 6] >> (c & 63) & 1ull)) ++c;
+    // the smallest colour not in use
+    int c = used0 != ~0ull ? __ffsll((long long)~used0) - 1
+                           : (used1 != ~0ull ? 64 + __ffsll((long long)~used1) - 1 : kMaxColours);
     if (c >= kMaxColours) {
         flag[1] = 1;  // too many colours
         c = kMaxColours - 1;
     }
     col[i] = c;
+}
+
+// (programmatic dependent launches as the MIS-2 rounds, over a grid of at
+// most four CTAs per SM: in most rounds most nodes are coloured and return)
+__global__ void colour_round_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci, int* colour,
+                                    int* flag) {
+    pdl_wait();
+    pdl_trigger();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        colour_round_node(i, rp, ci, colour, flag);
 }
 
 __global__ void max_kernel(int n, const int* __restrict__ v, int* out) {
@@ -489,7 +573,7 @@ __global__ void __launch_bounds__(1024) colour_worklist_kernel(int n, const int*
 // d_flag: 3 device ints, h_flag: 3 pinned host ints
 int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, int* h_flag,
                  cudaStream_t s, int* n_colours, int* rounds_out, int* d_queue) {
-    const int threads = 256, blocks = ceil_div(n, threads);
+    const int threads = 256, blocks = ceil_div(n, threads), rgrid = round_grid(n, threads);
     if (n <= kWorklistMaxNodes && d_queue) {
         const size_t smem = (size_t)n * 5 + 16;
         // the limit is always raised to what the largest accepted graph needs,
@@ -509,13 +593,13 @@ int colour_nodes(int n, const int* rp, const int* ci, int* colour, int* d_flag, 
     }
     BAMG_CUDA_TRY(cudaMemsetAsync(colour, 0xff, sizeof(int) * (size_t)n, s));
     BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, 3 * sizeof(int), s));
-    const int batch = 16;
+    const int batch = 32;
     const long max_rounds = 2L * n + 64;
     long rounds = 0;
     for (;;) {
         for (int r = 0; r < batch; ++r) {
             if (r == batch - 1) BAMG_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
-            colour_round_kernel<<<blocks, threads, 0, s>>>(n, rp, ci, colour, d_flag);
+            BAMG_CUDA_TRY(launch_round(colour_round_kernel, rgrid, threads, s, n, rp, ci, colour, d_flag));
         }
         note_launch(batch);
         rounds += batch;

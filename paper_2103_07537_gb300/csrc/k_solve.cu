@@ -187,10 +187,24 @@ template <typename T, typename S, bool CG>
 __device__ __forceinline__ void gemv_row(int row, int lane, int nd, const S* __restrict__ ainv, const T* x,
                                          T* y) {
     const S* a = ainv + (size_t)row * nd;
-    S acc = S(0);
-    for (int c = lane; c < nd; c += kWarp) acc = fma(__ldg(a + c), (S)ld1<T, CG>(x + c), acc);
-    acc = warp_sum(acc);
-    if (lane == 0) y[row] = (T)acc;
+    // four accumulators (columns lane + 32 (4 t + u)): four independent
+    // load pairs in flight per lane, summed in a fixed order
+    S acc[4] = {S(0), S(0), S(0), S(0)};
+    int c = lane;
+    for (; c + 3 * kWarp < nd; c += 4 * kWarp) {
+        S av[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            av[u] = __ldg(a + c + u * kWarp);
+            xv[u] = (S)ld1<T, CG>(x + c + u * kWarp);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(av[u], xv[u], acc[u]);
+    }
+    for (int u = 0; c < nd; c += kWarp, ++u) acc[u] = fma(__ldg(a + c), (S)ld1<T, CG>(x + c), acc[u]);
+    S sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    sum = warp_sum(sum);
+    if (lane == 0) y[row] = (T)sum;
 }
 
 // restriction with R = P^T, P piecewise constant: rc[I,d] = sum_{m in I} res[m,d],
