@@ -237,6 +237,7 @@ struct bamg_ctx {
     float* coarse_inv32 = nullptr;  // the FP32 inverse (coarse_prec 32), else null
     int* coarse_piv = nullptr;
     bool coarse_tc_used = false;  // the FP32 coarsest LU and inverse ran on the tensor cores
+    long arnoldi_steps = 0, second_projections = 0;  // of the last fgmres_solve
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -936,14 +937,29 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         }
         if (L.bgs_tpr == 4 && L.tune_us[6] >= 1e29f) L.bgs_tpr = 3;  // the staged kernel does not take this level
         if (h->p.autotune == 1 && h->p.use_pdl && (L.bgs_tpr == 0 || L.bgs_tpr == 5)) {
-            // warp against four warps per node again in the cycle's launch mode:
-            // with programmatic dependent launches each kernel's loads before
-            // its wait overlap the previous launch, which favours the wider
-            // mapping (3D level 1: 7% faster in the cycle, within 3% alone)
+            // warp against four warps per node again, as a whole field step
+            // (every colour of field 0) in the cycle's launch mode: with
+            // programmatic dependent launches each kernel's loads before its
+            // wait overlap the previous colour, which favours the wider mapping
+            // (3D level 1: 7% faster in the cycle, within 3% one colour alone)
             PdlScope pdl(true);
-            const float tw = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour<T>(b, h->fb, a, s); });
-            const float tv = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_wide<T>(b, h->fb, a, s); });
-            L.bgs_tpr = tv < tw ? 5 : 0;
+            const int c_hi = h->nf > 1 ? L.fcol[1] : L.n_colours;
+            float tstep[2] = {0.f, 0.f};
+            for (int m = 0; m < 2; ++m) {
+                L.bgs_tpr = m == 0 ? 0 : 5;
+                tstep[m] = time_launch(s, e0, e1, reps, [&]() {
+                    for (int c = 0; c < c_hi; ++c) {
+                        BgsArgs ac = a;
+                        ac.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
+                        ac.nodes = L.colour_nodes + L.colour_ptr[c];
+                        ac.colour = c;
+                        const int st = launch_colour_step<T>(h, L, ac, s);
+                        if (st != BAMG_OK) return st;
+                    }
+                    return (int)BAMG_OK;
+                });
+            }
+            L.bgs_tpr = tstep[1] < tstep[0] ? 5 : 0;
         }
         L.spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && L.tune_us[3] < kTuneMargin * L.tune_us[2]);
         // one whole field step (every colour of field 0) as per-colour launches
@@ -2239,6 +2255,8 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int m = restart;
     TRY(ensure_krylov(h, m));
+    h->arnoldi_steps = 0;
+    h->second_projections = 0;
     const Level& L0 = h->lev[0];
     const long N = (long)L0.n * h->b;
     const int bsz = h->b;
@@ -2294,9 +2312,10 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
                    launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h2, 1.0, 2, h->partial, h->wsq, h->ticket, &ga, s));
             } else {
                 // classical Gram-Schmidt, projected a second time only where the
-                // first projection removed more than half of ||w||^2 (DGKS):
-                // w -= V h1 and ||w||^2 with the test; then, only if set,
-                // h2 = V^T w and w -= V h2, ||w||^2 (the Givens update with h1 + h2)
+                // norm of w left after the first projection is below 0.01 of the
+                // norm before it (the selective test of Daniel, Gragg, Kaufman and
+                // Stewart): w -= V h1 and ||w||^2 with the test; then, only if
+                // set, h2 = V^T w and w -= V h2, ||w||^2 (Givens with h1 + h2)
                 unsigned* reorth = h->ticket + 2;
                 PL(BAMG_K_KRYLOV, (nv + 2) * vN, 2.0 * N * (nv + 1),
                    launch_axpy_dot(N, h->w, h->V, N, j + 1, h->h1, 1.0, 3, h->partial, h->wsq, h->ticket, &ga, s,
@@ -2309,12 +2328,16 @@ extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, in
             }
             PL(BAMG_K_KRYLOV, 2.0 * vN, N, launch_scale(N, h->w, h->scal, h->V + (size_t)(j + 1) * N, 1, s));
             total++;
+            h->arnoldi_steps++;
             k = j + 1;
             BAMG_CUDA_TRY(cudaMemcpyAsync(hs, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
             // a bounded wait of the cycle (grid barrier, sweep tile) that ran out
             BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (h->p.ortho != 1)  // whether this step projected twice (statistics)
+                BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 5, h->ticket + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
             BAMG_CUDA_TRY(cudaStreamSynchronize(s));
             if (h->h_pin[0] != 0) return map_dev_error(h->h_pin[0]);
+            h->second_projections += h->p.ortho == 1 ? 1 : (h->h_pin[5] != 0 ? 1 : 0);
             if (!isfinite(hs[1])) return BAMG_ENAN;
             if (hs[1] / bnorm <= tol || hs[2] != 0.0 || total >= max_iter) break;
         }
@@ -2635,7 +2658,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
-                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};
