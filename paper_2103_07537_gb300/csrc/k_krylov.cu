@@ -270,9 +270,12 @@ __global__ void solve_upper_kernel(int k, int m, const double* __restrict__ H, c
 __global__ void scale_kernel(long N, const double* __restrict__ x, const double* __restrict__ scal,
                              double* __restrict__ y, int check_breakdown) {
     if (check_breakdown && scal[2] != 0.0) return;
-    const double den = scal[0];
+    // one division per thread and a product per element: an FP64 division
+    // per element costs about ten FP64 operations, and GB300 issues two per
+    // clock per SM (within an ulp of the quotient)
+    const double rden = 1.0 / scal[0];
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long)gridDim.x * blockDim.x)
-        y[e] = x[e] / den;
+        y[e] = x[e] * rden;
 }
 
 // g = (beta, 0, ..., 0) with beta = sqrt(*bsq); scal[0] = beta
