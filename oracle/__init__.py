@@ -56,7 +56,7 @@ class Params(C.Structure):
                 ("omega_s_arr", _dp), ("omega_s_len", C.c_longlong), ("omega_p_arr", _dp),
                 ("omega_p_len", C.c_longlong), ("mlp", _dp), ("mlp_levels", C.c_int), ("sub_ilu", C.c_int),
                 ("n_node_fields", C.c_int), ("node_field_off", _ip), ("sub_schwarz", C.c_int),
-                ("schwarz_overlap", C.c_int)]
+                ("schwarz_overlap", C.c_int), ("inner_sweeps", C.c_int)]
 
 
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -318,7 +318,8 @@ class Hierarchy:
 
     def __init__(self, row_ptr, col_idx, vals, b, field_of_dof, max_levels=10, max_coarse=2500,
                  n_pre=1, n_post=1, omega=0.5, smooth_p=0, omega_p=0.0, omega_s_arr=None, omega_p_arr=None,
-                 mlp=None, mlp_levels=0, sub_ilu=0, node_field_off=None, sub_schwarz=0, schwarz_overlap=1):
+                 mlp=None, mlp_levels=0, sub_ilu=0, node_field_off=None, sub_schwarz=0, schwarz_overlap=1,
+                 inner_sweeps=1):
         """``node_field_off``: node ranges of fields on disjoint node sets
         (non-co-located fields; every dof of a node in the node's field, so
         ``field_of_dof`` is all zero); None for co-located fields."""
@@ -340,7 +341,7 @@ class Hierarchy:
                              None if self._wp is None else _d(self._wp),
                              0 if self._wp is None else self._wp.size,
                              None if self._mlp is None else _d(self._mlp), int(mlp_levels), int(sub_ilu),
-                             0, None, int(sub_schwarz), int(schwarz_overlap))
+                             0, None, int(sub_schwarz), int(schwarz_overlap), int(inner_sweeps))
         self._foff = None if node_field_off is None else _int32(node_field_off)
         self.NF = 1
         if self._foff is not None:

@@ -1129,7 +1129,8 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
     long long used_s = 0, used_p = 0;
     if ((p->omega_s_arr && p->omega_s_len < 0) || (p->omega_p_arr && p->omega_p_len < 0) || p->mlp_levels < 0 ||
         p->sub_schwarz < 0 || p->sub_schwarz > 2 || p->schwarz_overlap < 0 || p->schwarz_overlap > 1 ||
-        (p->sub_schwarz && p->sub_ilu))
+        (p->sub_schwarz && p->sub_ilu) || p->inner_sweeps < 0 || p->inner_sweeps > 64 ||
+        (p->inner_sweeps > 1 && (p->sub_ilu || p->sub_schwarz || p->n_node_fields > 1)))
         st = ORACLE_EINVAL;
     if (st != ORACLE_OK) {
         oracle_free(h);
@@ -1615,7 +1616,12 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
                 int st = schwarz_apply(h, L, f, 0, fb, rf, xt);
                 if (st) return st;
             }
-            for (int col = 0; col < ((h->p.sub_ilu || h->p.sub_schwarz) ? 0 : L->n_colours); ++col) {
+            /* inner sweeps of the multicolour Gauss-Seidel sub-solve: the formula
+             * below takes every j != i with its current x~, which is zero for the
+             * later colours in the first sweep and the previous sweep's value after */
+            const int inner = h->p.inner_sweeps > 1 ? h->p.inner_sweeps : 1;
+            for (int q = 0; q < ((h->p.sub_ilu || h->p.sub_schwarz) ? 0 : inner); ++q)
+            for (int col = 0; col < L->n_colours; ++col) {
                 for (int i = 0; i < L->n; ++i) {
                     if (L->colour[i] != col) continue;
                     double t[ORACLE_MAX_B];

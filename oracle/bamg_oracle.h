@@ -181,6 +181,12 @@ typedef struct {
      * solved exactly by dense LU with partial pivoting.  Not with sub_ilu. */
     int sub_schwarz;
     int schwarz_overlap;
+    /* inner_sweeps > 1: the multicolour Gauss-Seidel sub-solve of A_ff runs that many
+     * forward sweeps (the first from x~ = 0, each later one from the previous x~, the
+     * higher colours' values taken from the previous sweep); 0 and 1 = one sweep.
+     * Only with the multicolour sub-solve of co-located fields (not with sub_ilu,
+     * sub_schwarz or n_node_fields > 1); at most 64. */
+    int inner_sweeps;
 } oracle_params;
 
 int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,

@@ -66,13 +66,14 @@ def bsr_dense(row_ptr, col_idx, vals):
     return sp.bsr_matrix((vals, col_idx, row_ptr), shape=(n * b, n * b)).toarray()
 
 
-def bgs_matrix_form(A, x, rhs, b, F, colour, omega):
+def bgs_matrix_form(A, x, rhs, b, F, colour, omega, inner=1):
     """One sweep of Algorithm 1 written with dense matrices.
 
     For field f: r_f = rhs_f - A[f rows, :] x; the multicolour node-block
     Gauss-Seidel sweep from zero is a block forward substitution with the
     part of A_ff that is block lower triangular in (colour, index) order;
-    then x_f += omega x~_f.
+    then x_f += omega x~_f.  With inner > 1 the sub-solve iterates
+    x~ <- T^-1 (r_f - (A_ff - T) x~) from x~ = 0, inner times (T: that lower part).
     """
     fb = b // F
     n = len(colour)
@@ -89,7 +90,9 @@ def bgs_matrix_form(A, x, rhs, b, F, colour, omega):
             for j in range(n):
                 if rank[j] <= rank[i]:
                     T[i * fb:(i + 1) * fb, j * fb:(j + 1) * fb] = Aff[i * fb:(i + 1) * fb, j * fb:(j + 1) * fb]
-        xt = np.linalg.solve(T, r_f)
+        xt = np.zeros_like(r_f)
+        for _ in range(inner):
+            xt = np.linalg.solve(T, r_f - (Aff - T) @ xt)
         x[rows] += omega * xt
     return x
 
@@ -399,6 +402,51 @@ def test_bgs_equals_matrix_form(kind, F, omega):
     x2 = h.bgs(0, x0, s.rhs, 2)
     ref2 = bgs_matrix_form(A, ref, s.rhs, s.b, F, L["colour"], omega)
     assert np.allclose(x2, ref2, rtol=1e-10, atol=1e-10 * np.abs(ref2).max())
+
+
+@pytest.mark.parametrize("kind,F", [("random6", 2), ("mhd", 2), ("random4", 1)])
+@pytest.mark.parametrize("inner", [2, 3])
+def test_bgs_inner_sweeps_equal_matrix_form(kind, F, inner):
+    """inner_sweeps > 1: the Gauss-Seidel sub-solve iterates from its first sweep's
+    result, the later colours' values taken from the previous sweep."""
+    if kind == "random6":
+        s = P.random_block_system(6, 6, [0, 0, 0, 1, 1, 1], seed=21)
+    elif kind == "mhd":
+        s = P.mhd2d(6, 2)
+    else:
+        s = P.random_block_system(5, 4, [0, 0, 0, 0], seed=22)
+    h = oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, omega=0.6, inner_sweeps=inner)
+    L = h.level(0)
+    x0 = np.random.default_rng(6).standard_normal(s.n_unknowns)
+    x1 = h.bgs(0, x0, s.rhs, 1)
+    ref = bgs_matrix_form(s.dense(), x0, s.rhs, s.b, F, L["colour"], 0.6, inner)
+    assert np.allclose(x1, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    one = oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, omega=0.6, inner_sweeps=1)
+    assert np.abs(one.bgs(0, x0, s.rhs, 1) - x1).max() > 1e-8  # the extra sweeps change the result
+
+
+def test_bgs_many_inner_sweeps_solve_the_field_block():
+    """Many inner sweeps on a block-diagonally dominant A_ff: the sub-solve
+    converges to A_ff^-1 r_f, so the field step is x_f += omega A_ff^-1 r_f."""
+    s = P.random_block_system(5, 6, [0, 0, 0, 1, 1, 1], seed=25, diag_shift=8.0)
+    h = oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, omega=0.7, inner_sweeps=60)
+    A, b, n = s.dense(), s.b, s.n_nodes
+    x = np.random.default_rng(7).standard_normal(s.n_unknowns)
+    got = h.bgs(0, x, s.rhs, 1)
+    ref = x.copy()
+    for f in range(2):
+        rows = np.array([i * b + f * 3 + r for i in range(n) for r in range(3)])
+        rf = s.rhs[rows] - A[rows, :] @ ref
+        ref[rows] += 0.7 * np.linalg.solve(A[np.ix_(rows, rows)], rf)
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+def test_inner_sweeps_validation():
+    s = P.random_block_system(4, 6, [0, 0, 0, 1, 1, 1], seed=26)
+    for kw in (dict(inner_sweeps=65), dict(inner_sweeps=-1), dict(inner_sweeps=2, sub_ilu=2),
+               dict(inner_sweeps=2, sub_schwarz=2)):
+        with pytest.raises(oracle.OracleError):
+            oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, **kw)
 
 
 def test_bgs_block_diagonal_exact_with_unit_damping():
