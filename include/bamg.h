@@ -173,6 +173,15 @@ typedef struct {
                          accuracy); 0 = the CUDA-core cooperative LU and column-by-column
                          inverse. Pivots may differ between the two (ties, rounding); both
                          are backward stable.                                                 */
+    int inner_sweeps; /* multicolour Gauss-Seidel sweeps of the sub-solve A_ff x~ = r_f in each
+                         field step of Algorithm 1 (sub_solver 0): 1 (default) = one sweep from
+                         zero; k in 2..64 = k sweeps, the first from zero, each later one taking
+                         the previous sweep's x~ for the neighbours of higher colour (x~ tends to
+                         A_ff^{-1} r_f as k grows). k > 1 forms r_f = b_f - A_f* x for all nodes
+                         first, then one launch per colour and sweep; it runs without the tail,
+                         the persistent sweep and the upper-part residual, and needs sub_solver 0
+                         and dof fields (amg_setup, amg_setup_batched; else BAMG_EINVAL).  0 is
+                         taken as 1.                                                          */
 } amg_params;
 
 /* Fills *p with the defaults above (cycle_prec 64, tentative P, no learned weights). */

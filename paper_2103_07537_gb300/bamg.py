@@ -51,7 +51,8 @@ class AmgParams(C.Structure):
                 ("mlp", C.POINTER(C.c_float)), ("pr_storage", C.c_int), ("mlp_levels", C.c_int),
                 ("use_pdl", C.c_int), ("coarse_prec", C.c_int), ("tail_grid", C.c_int),
                 ("value_layout", C.c_int), ("sweep", C.c_int), ("sub_solver", C.c_int),
-                ("schwarz_overlap", C.c_int), ("ortho", C.c_int), ("coarse_tc", C.c_int)]
+                ("schwarz_overlap", C.c_int), ("ortho", C.c_int), ("coarse_tc", C.c_int),
+                ("inner_sweeps", C.c_int)]
 
 
 class BamgError(RuntimeError):

@@ -484,6 +484,7 @@ extern "C" void amg_default_params(amg_params* p) {
     p->schwarz_overlap = 1;
     p->ortho = 0;
     p->coarse_tc = 1;
+    p->inner_sweeps = 1;
 }
 
 extern "C" const char* amg_strerror(int status) {
@@ -1502,9 +1503,11 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         (prm.tail_grid != 0 && prm.tail_grid != 1) || prm.value_layout < 0 || prm.value_layout > 2 ||
         prm.sweep < 0 || prm.sweep > 3 || prm.sub_solver < 0 || prm.sub_solver > 2 ||
         prm.schwarz_overlap < 0 || prm.schwarz_overlap > 1 || prm.ortho < 0 || prm.ortho > 1 ||
-        prm.coarse_tc < 0 || prm.coarse_tc > 1)
+        prm.coarse_tc < 0 || prm.coarse_tc > 1 || prm.inner_sweeps < 0 || prm.inner_sweeps > 64 ||
+        (prm.inner_sweeps > 1 && (prm.sub_solver != 0 || nf > 1)))
         return BAMG_EINVAL;
-    if (prm.sub_solver != 0) {
+    if (prm.inner_sweeps == 0) prm.inner_sweeps = 1;
+    if (prm.sub_solver != 0 || prm.inner_sweeps > 1) {
         // the cycle with another sub-solve runs as separate launches: no
         // recorded single-launch tail, no persistent sweep
         prm.tail_dofs = 0;
@@ -1746,6 +1749,57 @@ static int bgs_step(bamg_ctx* h, int l, int f, const T* rhs, const T* x_in, T* x
         if (nodef) TRY(other_fields<T>(h, L, f, x_in, x_out, uc, s));
         return BAMG_OK;
     }
+    if (h->p.inner_sweeps > 1) {
+        // the sub-solve iterated: r_f = b_f - A_f* x_in for every node first (in
+        // the level's residual buffer, unused while the level smooths), then
+        // inner_sweeps multicolour sweeps on A_ff x~ = r_f, one launch per
+        // colour; the last sweep writes x_out
+        T* rf = static_cast<T*>(L.res);
+        const double es = sizeof(T), B = h->b, FB = h->fb, nn = L.n, nz = L.nnzb;
+        PL(BAMG_K_SMOOTH,
+           nn * (8.0 + 2.0 * FB * es) + (x_in ? nz * (FB * B * es + 4.0 + B * es) : 0.0) +
+               (x_in && uc ? nz * (4.0 + B * es) : 0.0),
+           x_in ? 2.0 * nz * FB * B : 0.0,
+           launch_field_residual<T>(h->b, h->fb, level_fm<T>(L), L.n, f, L.rp, L.ci, level_vals<T>(L), x_in, uc,
+                                    uc ? L.agg : nullptr, rhs, rf, s));
+        const int K = h->p.inner_sweeps;
+        for (int q = 0; q < K; ++q)
+            for (int c = 0; c < L.n_colours; ++c) {
+                BgsArgs a;
+                a.n_in_colour = L.colour_ptr[c + 1] - L.colour_ptr[c];
+                a.nodes = L.colour_nodes + L.colour_ptr[c];
+                a.colour = c;
+                a.colours = L.colour;
+                a.lowk = L.lowk;
+                a.fm = level_fm<T>(L);
+                a.rp = L.rp;
+                a.ci = L.ci;
+                a.vals = level_vals<T>(L);
+                a.dinv = level_dinv<T>(L);
+                a.rhs = rhs;
+                a.x_in = x_in;
+                a.x_out = x_out;
+                a.xt = L.xt;
+                a.uc = uc;
+                a.agg = uc ? L.agg : nullptr;
+                a.field = f;
+                a.F = h->F;
+                a.omega = h->p.omega;
+                a.omega_node = level_omega<T>(L);
+                double bytes = 0.0, flops = 0.0;
+                if (h->prof && have_counts) {
+                    const double nc = a.n_in_colour;
+                    const double used = (q == 0 ? (double)L.colour_nnz_lower[c] : (double)L.colour_nnz[c] - nc);
+                    bytes = (double)L.colour_nnz[c] * (q == 0 ? 1.0 : 4.0) + used * (4.0 + FB * FB * es + FB * es) +
+                            nc * (12.0 + 3.0 * FB * es + FB * FB * es);
+                    if (q == K - 1) bytes += nc * (B * es + (x_in ? B * es : 0.0) + (x_in && uc ? 4.0 + B * es : 0.0));
+                    flops = 2.0 * (used + nc) * FB * FB;
+                }
+                PL(BAMG_K_SMOOTH, bytes, flops,
+                   launch_gs_inner<T>(h->b, h->fb, a, rf, q == 0, q == K - 1, s));
+            }
+        return BAMG_OK;
+    }
     if (L.sweep && L.sw_tiles > 0 && !h->rec) {
         // every colour of the step in one persistent launch
         BgsArgs a;
@@ -1863,12 +1917,12 @@ int prolong_explicit<float>(bamg_ctx* h, const Level& L, const float* uc, float*
 
 // the residual after the pre-smoothing can be formed from the higher-colour
 // blocks alone (launch_residual_upper): one field, one sweep from zero of the
-// multicolour Gauss-Seidel sub-solve, one damping value for every node, the
-// thread-per-row residual mapping
+// multicolour Gauss-Seidel sub-solve (one inner sweep), one damping value for
+// every node, the thread-per-row residual mapping
 template <typename T>
 static bool upper_residual(const bamg_ctx* h, const Level& L) {
-    return h->F == 1 && h->nf <= 1 && h->p.n_pre == 1 && h->p.sub_solver == 0 && L.spmv_tpr && L.lowk &&
-           level_omega<T>(L) == nullptr;
+    return h->F == 1 && h->nf <= 1 && h->p.n_pre == 1 && h->p.sub_solver == 0 && h->p.inner_sweeps <= 1 &&
+           L.spmv_tpr && L.lowk && level_omega<T>(L) == nullptr;
 }
 
 // MGV(0, rhs, l) of Fig. 1 written to out
@@ -2658,7 +2712,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
-                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"coarse_unknowns\":" +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"inner_sweeps\":" + std::to_string(h->p.inner_sweeps) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};

@@ -300,6 +300,10 @@ template <typename T>
 // small colour spread over more SMs); 2: four lanes per scalar row, each
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
+// one colour of sweep q of the iterated sub-solve A_ff x~ = r_f (rf: n x fb;
+// first: higher colours count as zero; last: also writes x_out, see k_solve.cu)
+template <typename T>
+int launch_gs_inner(int b, int fb, const BgsArgs& a, const T* rf, bool first, bool last, cudaStream_t s);
 
 // ---- colour step with the rows staged by asynchronous copies (k_staged.cu) ----
 // the four-lanes-per-row colour step with every node's values, columns and

@@ -759,6 +759,100 @@ int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int v
 template int launch_bgs_colour_tpr<double>(int, int, const BgsArgs&, cudaStream_t, int);
 template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t, int);
 
+// One colour of one of several sweeps of the multicolour Gauss-Seidel
+// sub-solve A_ff x~ = r_f of a field step (Algorithm 1 with the sub-solve
+// iterated), one thread per scalar row of field f:
+//   x~_i = D_i^{-1} (r_f,i - sum_{j != i} A_ff(i,j) x~_j)
+// where, in the first sweep, a neighbour of higher colour contributes nothing
+// (x~ starts from zero; its entry in xt is stale) and, in the later sweeps,
+// its value from the previous sweep.  The nodes of one colour do not couple,
+// so xt is read at other colours' nodes only and written at this colour's.
+// rf (n x FB) holds r_f = b_f - A_f* x_in for every node, formed before the
+// first sweep.  The last sweep also writes node i of x_out: x_in (+ P uc)
+// with field f increased by omega x~_i.
+template <typename T, int B, int FB, bool FM>
+__global__ void __launch_bounds__(TprBlock<FB>::kThreads)
+    gs_inner_kernel(BgsArgs a, const T* __restrict__ rf, int first, int last) {
+    __shared__ T sh_t[TprBlock<FB>::kThreads];
+    const int tloc = threadIdx.x;
+    const int nloc = tloc / FB, r = tloc - nloc * FB;
+    const long q = (long)blockIdx.x * (blockDim.x / FB) + nloc;
+    const bool act = q < a.n_in_colour;
+    const int f0 = a.field * FB;
+    const T* __restrict__ vals = static_cast<const T*>(a.vals);
+    T* xt = static_cast<T*>(a.xt);
+    int i = 0;
+    T t = T(0);
+    if (act) {
+        i = __ldg(a.nodes + q);
+        const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+        // columns f0.. of scalar row f0 + r in each block of the row
+        const T* vb = vrow<T, B, FB, FM>(vals, k0, k1, k0, f0 + r) + f0;
+        constexpr int VS = vstride<T, B, FB, FM>();
+        pdl_wait();
+        pdl_trigger();
+        T acc = T(0);
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            if (first && __ldg(a.lowk + k) == 0) continue;  // also skips the diagonal block
+            const int j = __ldg(a.ci + k);
+            if (j == i) continue;
+            const T* ap = vb + (size_t)(k - k0) * VS;
+            const T* xp = xt + (size_t)j * FB;
+#pragma unroll
+            for (int c = 0; c < FB; ++c) acc = fma(__ldg(ap + c), xp[c], acc);
+        }
+        t = rf[(size_t)i * FB + r] - acc;
+    }
+    sh_t[tloc] = t;
+    __syncthreads();
+    if (!act) return;
+    const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)r * FB;
+    T xn = T(0);
+#pragma unroll
+    for (int c = 0; c < FB; ++c) xn = fma(__ldg(D + c), sh_t[nloc * FB + c], xn);
+    xt[(size_t)i * FB + r] = xn;
+    if (!last) return;
+    const T* __restrict__ x_in = static_cast<const T*>(a.x_in);
+    const T* __restrict__ uc = static_cast<const T*>(a.uc);
+    T* __restrict__ x_out = static_cast<T*>(a.x_out);
+    const T om = a.omega_node ? static_cast<const T*>(a.omega_node)[(size_t)i * a.F + a.field] : T(a.omega);
+    const int ag = (x_in && uc) ? __ldg(a.agg + i) : 0;
+    for (int m = 0; m < a.F; ++m) {
+        const size_t e = (size_t)i * B + m * FB + r;
+        T v = x_in ? x_in[e] : T(0);
+        if (x_in && uc) v += uc[(size_t)ag * B + m * FB + r];
+        if (m == a.field) v = fma(om, xn, v);
+        x_out[e] = v;
+    }
+}
+
+template <typename T>
+int launch_gs_inner(int b, int fb, const BgsArgs& a, const T* rf, bool first, bool last, cudaStream_t s) {
+    if (a.n_in_colour <= 0) return BAMG_OK;
+    switch (b * 16 + fb) {
+#define CASE(BB, FF)                                                                                          \
+    case BB * 16 + FF: {                                                                                      \
+        const int threads = TprBlock<FF>::kThreads;                                                           \
+        constexpr bool kFm = HasFm<T, BB, FF>::value;                                                        \
+        const int grid = ceil_div(a.n_in_colour, threads / FF);                                               \
+        const cudaError_t e =                                                                                 \
+            (a.fm && kFm) ? launch_k(gs_inner_kernel<T, BB, FF, kFm>, grid, threads, 0, s, a, rf, (int)first, \
+                                     (int)last)                                                               \
+                          : launch_k(gs_inner_kernel<T, BB, FF, false>, grid, threads, 0, s, a, rf,          \
+                                     (int)first, (int)last);                                                  \
+        if (e != cudaSuccess) return BAMG_ECUDA;                                                              \
+        break;                                                                                                \
+    }
+        BAMG_BLOCK_SHAPES(CASE)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return launched(1);
+}
+template int launch_gs_inner<double>(int, int, const BgsArgs&, const double*, bool, bool, cudaStream_t);
+template int launch_gs_inner<float>(int, int, const BgsArgs&, const float*, bool, bool, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // Tail kernel: one thread-block cluster executes a recorded list of V-cycle
 // phases (every colour of every field step, residuals, restrictions, the
