@@ -328,7 +328,8 @@ class Hierarchy:
         self.n = self.rp.shape[0] - 1
         fm = _int32(field_of_dof)
         self.F = int(fm.max()) + 1
-        self.fb = self.b // self.F
+        self.fsize = [int((fm == f).sum()) for f in range(self.F)]  # dofs per field (may differ)
+        self.fb = max(self.fsize)
         # keep the weight arrays alive for the duration of the setup call
         self._ws = None if omega_s_arr is None else _f64(omega_s_arr).ravel()
         self._wp = None if omega_p_arr is None else _f64(omega_p_arr).ravel()
@@ -379,7 +380,8 @@ class Hierarchy:
         return n.value, nnz.value, ncol.value, nagg.value
 
     def level(self, l):
-        """dict with row_ptr, col_idx, vals[nnzb,b,b], agg, colour, dinv[n,F,fb,fb]."""
+        """dict with row_ptr, col_idx, vals[nnzb,b,b], agg, colour, dinv[n,F,fb,fb]
+        (fields of unequal size: dinv a list over the fields of [n,fs,fs])."""
         n, nnz, ncol, nagg = self.level_sizes(l)
         rp = np.zeros(n + 1, np.int32)
         ci = np.zeros(nnz, np.int32)
@@ -387,11 +389,20 @@ class Hierarchy:
         coarsest = l == self.num_levels - 1
         agg = None if coarsest else np.zeros(n, np.int32)
         col = None if coarsest else np.zeros(n, np.int32)
-        dinv = None if coarsest else np.zeros((n, self.F, self.fb, self.fb))
+        dinv = None if coarsest else np.zeros((n, sum(fs * fs for fs in self.fsize)))
         lib().oracle_level_get(self._h, l, _i(rp), _i(ci), _d(v),
                                _i(agg) if agg is not None else None,
                                _i(col) if col is not None else None,
                                _d(dinv) if dinv is not None else None)
+        if dinv is not None:
+            if len(set(self.fsize)) == 1:
+                dinv = dinv.reshape(n, self.F, self.fb, self.fb)
+            else:
+                parts, o = [], 0
+                for fs in self.fsize:
+                    parts.append(dinv[:, o:o + fs * fs].reshape(n, fs, fs))
+                    o += fs * fs
+                dinv = parts
         return dict(n=n, nnzb=nnz, n_colours=ncol, n_agg=nagg, row_ptr=rp, col_idx=ci, vals=v,
                     agg=agg, colour=col, dinv=dinv)
 

@@ -802,6 +802,9 @@ struct oracle_hier {
     int NF; /* fields on disjoint node sets (1: co-located fields only) */
     int field_of_dof[ORACLE_MAX_B];
     int fstart[ORACLE_MAX_B]; /* first dof of each field inside a node */
+    int fsize[ORACLE_MAX_B];  /* dofs of each field (fb = the largest) */
+    int doff[ORACLE_MAX_B];   /* offset of field f's inverse block in a node's dinv entries */
+    int dstride;              /* dinv entries per node: sum over the fields of fsize^2 */
     oracle_params p;
     olevel lev[ORACLE_MAX_LEVELS];
     double* lu; /* coarsest level, dense LU */
@@ -966,21 +969,23 @@ static int colour_node_fields(const oracle_hier* h, olevel* L) {
 
 static int level_schwarz(oracle_hier* h, olevel* L);
 
-/* per-field inverses of the node diagonal blocks of level L */
+/* per-field inverses of the node diagonal blocks of level L: node i, field f
+ * at dinv + i*dstride + doff[f] (fsize[f]^2 entries, row-major; with equal
+ * fields this is [n][F][fb*fb]) */
 static int level_dinv(oracle_hier* h, olevel* L) {
-    const int b = h->b, F = h->F, fb = h->fb;
+    const int b = h->b, F = h->F;
     const size_t bb = (size_t)b * b;
-    L->dinv = (double*)malloc(sizeof(double) * (size_t)L->n * F * fb * fb);
+    L->dinv = (double*)malloc(sizeof(double) * (size_t)L->n * h->dstride);
     if (!L->dinv) return ORACLE_ENOMEM;
     for (int i = 0; i < L->n; ++i) {
         int kd = find_pos(L->col_idx, L->row_ptr[i], L->row_ptr[i + 1], i);
         if (kd < 0) return ORACLE_EINVAL;
         for (int f = 0; f < F; ++f) {
             double blk[ORACLE_MAX_B * ORACLE_MAX_B];
-            int s = h->fstart[f];
+            const int s = h->fstart[f], fb = h->fsize[f];
             for (int r = 0; r < fb; ++r)
                 for (int c = 0; c < fb; ++c) blk[r * fb + c] = L->vals[(size_t)kd * bb + (s + r) * b + (s + c)];
-            int st = oracle_block_inverse(fb, blk, L->dinv + ((size_t)i * F + f) * fb * fb);
+            int st = oracle_block_inverse(fb, blk, L->dinv + (size_t)i * h->dstride + h->doff[f]);
             if (st != ORACLE_OK) return st;
         }
     }
@@ -1073,12 +1078,18 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
         }
         if (field_of_dof[d] + 1 > F) F = field_of_dof[d] + 1;
     }
-    if (field_of_dof[0] != 0 || b % F != 0) {
+    if (field_of_dof[0] != 0) {
         free(h);
         return ORACLE_EINVAL;
     }
+    /* field blocks of unequal size (Algorithm 1 needs none equal): each field
+     * its own fsize x fsize diagonal blocks and sub-solve; the options built
+     * on one common field size (smoothed P, learned weights, ILU(0), Schwarz,
+     * fields on node sets) need equal sizes */
     h->F = F;
-    h->fb = b / F;
+    h->fb = 0;
+    h->dstride = 0;
+    int unequal = 0;
     for (int f = 0; f < F; ++f) {
         int cnt = 0, first = -1;
         for (int d = 0; d < b; ++d)
@@ -1086,11 +1097,17 @@ int oracle_setup(int n, int nnzb, int b, const int* row_ptr, const int* col_idx,
                 if (first < 0) first = d;
                 cnt++;
             }
-        if (cnt != h->fb) {
-            free(h);
-            return ORACLE_EINVAL;
-        }
         h->fstart[f] = first;
+        h->fsize[f] = cnt;
+        h->doff[f] = h->dstride;
+        h->dstride += cnt * cnt;
+        if (cnt > h->fb) h->fb = cnt;
+        if (cnt != h->fsize[0]) unequal = 1;
+    }
+    if (unequal && (p->smooth_p || p->omega_p_arr || p->mlp || p->sub_ilu || p->sub_schwarz ||
+                    p->n_node_fields > 1)) {
+        free(h);
+        return ORACLE_EINVAL;
     }
     /* fields on disjoint node sets: contiguous non-empty node ranges, one
      * field per node, and only the plain method (tentative P, constant
@@ -1316,8 +1333,7 @@ int oracle_level_get(const oracle_hier* h, int l, int* row_ptr, int* col_idx, do
     int has_smoother = l < h->nlev - 1;
     if (agg && has_smoother) memcpy(agg, L->agg, sizeof(int) * (size_t)L->n);
     if (colour && has_smoother) memcpy(colour, L->colour, sizeof(int) * (size_t)L->n);
-    if (dinv && has_smoother)
-        memcpy(dinv, L->dinv, sizeof(double) * (size_t)L->n * h->F * h->fb * h->fb);
+    if (dinv && has_smoother) memcpy(dinv, L->dinv, sizeof(double) * (size_t)L->n * h->dstride);
     return ORACLE_OK;
 }
 
@@ -1588,13 +1604,13 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
     if (l < 0 || l >= h->nlev - 1) return ORACLE_EINVAL;
     if (h->NF > 1) return bgs_node_fields(h, l, x, rhs, sweeps, unit_damping);
     olevel* L = &h->lev[l];
-    const int b = h->b, F = h->F, fb = h->fb;
+    const int b = h->b, F = h->F;
     const size_t bb = (size_t)b * b;
     double* rf = h->rf;
     double* xt = h->xt;
     for (int s = 0; s < sweeps; ++s) {
         for (int f = 0; f < F; ++f) {
-            const int f0 = h->fstart[f];
+            const int f0 = h->fstart[f], fb = h->fsize[f]; /* field f: dofs f0 .. f0 + fb - 1 */
             /* residual of the rows of field f, all columns */
             for (int i = 0; i < L->n; ++i)
                 for (int r = 0; r < fb; ++r) {
@@ -1635,7 +1651,7 @@ static int bgs_impl(oracle_hier* h, int l, double* x, const double* rhs, int swe
                         }
                         t[r] = acc;
                     }
-                    const double* Di = L->dinv + ((size_t)i * F + f) * fb * fb;
+                    const double* Di = L->dinv + (size_t)i * h->dstride + h->doff[f];
                     for (int r = 0; r < fb; ++r) {
                         double acc = 0.0;
                         for (int c = 0; c < fb; ++c) acc += Di[r * fb + c] * t[c];

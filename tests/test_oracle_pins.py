@@ -8,6 +8,7 @@ block-diagonal piecewise-constant transfers and cloned aggregates
 (Sec. 4.3.1, eq. blocktransfers); aggregates as a disjoint cover
 (Sec. 4.3.1); damped block Gauss-Seidel (Sec. 4.3.2, Algorithm 1).
 """
+import dataclasses
 import itertools
 
 import numpy as np
@@ -66,7 +67,7 @@ def bsr_dense(row_ptr, col_idx, vals):
     return sp.bsr_matrix((vals, col_idx, row_ptr), shape=(n * b, n * b)).toarray()
 
 
-def bgs_matrix_form(A, x, rhs, b, F, colour, omega, inner=1):
+def bgs_matrix_form(A, x, rhs, b, F, colour, omega, inner=1, fmap=None):
     """One sweep of Algorithm 1 written with dense matrices.
 
     For field f: r_f = rhs_f - A[f rows, :] x; the multicolour node-block
@@ -74,15 +75,20 @@ def bgs_matrix_form(A, x, rhs, b, F, colour, omega, inner=1):
     part of A_ff that is block lower triangular in (colour, index) order;
     then x_f += omega x~_f.  With inner > 1 the sub-solve iterates
     x~ <- T^-1 (r_f - (A_ff - T) x~) from x~ = 0, inner times (T: that lower part).
+    fmap: the field of every dof of a node (fields may differ in size); None:
+    F fields of b / F consecutive dofs.
     """
-    fb = b // F
+    if fmap is None:
+        fmap = [d // (b // F) for d in range(b)]
     n = len(colour)
     order = sorted(range(n), key=lambda i: (colour[i], i))
     rank = np.empty(n, int)
     rank[order] = np.arange(n)
     x = x.copy()
     for f in range(F):
-        rows = np.array([i * b + f * fb + r for i in range(n) for r in range(fb)])
+        dofs = [d for d in range(b) if fmap[d] == f]
+        fb = len(dofs)
+        rows = np.array([i * b + d for i in range(n) for d in dofs])
         r_f = rhs[rows] - A[rows, :] @ x
         Aff = A[np.ix_(rows, rows)]
         T = np.zeros_like(Aff)
@@ -597,3 +603,108 @@ def test_fgmres_zero_rhs_and_initial_guess():
     xs = np.linalg.solve(s.dense(), s.rhs)
     x, it, rr, conv = h.fgmres(s.rhs, x0=xs)
     assert conv and it == 0
+
+
+# ----------------------------------------------------------------------------
+# field blocks of unequal size (Algorithm 1 with fields of different widths)
+# ----------------------------------------------------------------------------
+
+
+def with_fields(s, fmap):
+    return dataclasses.replace(s, field_of_dof=list(fmap))
+
+
+UNEQUAL = {
+    "random_b3_21": lambda: P.random_block_system(6, 3, [0, 0, 1], seed=31),
+    "random_b5_32": lambda: P.random_block_system(5, 5, [0, 0, 0, 1, 1], seed=32),
+    "random_b4_121": lambda: P.random_block_system(5, 4, [0, 1, 1, 2], seed=33),
+    "stokes2d_u_p": lambda: with_fields(P.stokes2d(6, 3), [0, 0, 1]),
+    "mhd2d_u_p_B_r": lambda: with_fields(P.mhd2d(6, 2), [0, 0, 1, 2, 2, 3]),
+}
+
+
+def padded(s):
+    """The system with every field filled up to the widest field's size by
+    dummy dofs: an identity diagonal entry in the node's diagonal block, no
+    coupling, zero right-hand side.  Returns it and the padded index of every
+    original unknown."""
+    fmap = list(s.field_of_dof)
+    F = max(fmap) + 1
+    m = max(fmap.count(f) for f in range(F))
+    bp = F * m
+    pos = np.array([fmap[d] * m + d - fmap.index(fmap[d]) for d in range(s.b)])
+    dummy = np.array([q for q in range(bp) if q not in set(pos.tolist())])
+    V = np.zeros((s.nnzb, bp, bp))
+    V[:, pos[:, None], pos[None, :]] = s.vals
+    for i in range(s.n_nodes):
+        for k in range(s.row_ptr[i], s.row_ptr[i + 1]):
+            if s.col_idx[k] == i:
+                V[k, dummy, dummy] = 1.0
+    rhs = np.zeros((s.n_nodes, bp))
+    rhs[:, pos] = s.rhs.reshape(s.n_nodes, s.b)
+    real = (np.arange(s.n_nodes)[:, None] * bp + pos[None, :]).ravel()
+    return dataclasses.replace(s, b=bp, vals=V, rhs=rhs.ravel(), field_of_dof=[q // m for q in range(bp)]), real
+
+
+@pytest.mark.parametrize("name", list(UNEQUAL))
+@pytest.mark.parametrize("inner", [1, 2])
+def test_bgs_unequal_fields_equal_matrix_form(name, inner):
+    s = UNEQUAL[name]()
+    F = max(s.field_of_dof) + 1
+    h = oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, omega=0.6, inner_sweeps=inner)
+    L = h.level(0)
+    x0 = np.random.default_rng(8).standard_normal(s.n_unknowns)
+    got = h.bgs(0, x0, s.rhs, 1)
+    ref = bgs_matrix_form(s.dense(), x0, s.rhs, s.b, F, L["colour"], 0.6, inner, fmap=s.field_of_dof)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name", ["random_b4_121", "mhd2d_u_p_B_r"])
+def test_unequal_fields_dinv_are_the_field_block_inverses(name):
+    s = UNEQUAL[name]()
+    F = max(s.field_of_dof) + 1
+    h = oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0)
+    dinv = h.level(0)["dinv"]
+    assert isinstance(dinv, list) and len(dinv) == F
+    V = s.vals
+    for i in range(s.n_nodes):
+        k = [k for k in range(s.row_ptr[i], s.row_ptr[i + 1]) if s.col_idx[k] == i][0]
+        for f in range(F):
+            dofs = [d for d in range(s.b) if s.field_of_dof[d] == f]
+            want = np.linalg.inv(V[k][np.ix_(dofs, dofs)])
+            assert np.allclose(dinv[f][i], want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("name", list(UNEQUAL))
+def test_unequal_fields_equal_the_padded_system(name):
+    """Dummy dofs that are decoupled, with a zero right-hand side, stay zero in
+    every step of the method (their residual, sub-solve, restriction and
+    coarse solve are zero), so the V-cycle and FGMRES on the padded system with
+    equal fields give the unpadded method's values."""
+    s = UNEQUAL[name]()
+    sp_, real = padded(s)
+    kw = dict(max_levels=3, max_coarse=0, omega=0.55)
+    h = oracle.Hierarchy.from_system(s, **kw)
+    hp = oracle.Hierarchy.from_system(sp_, **kw)
+    assert hp.num_levels == h.num_levels
+    r = np.random.default_rng(12).standard_normal(s.n_unknowns)
+    rp = np.zeros(sp_.n_unknowns)
+    rp[real] = r
+    z, zp = h.vcycle(r), hp.vcycle(rp)
+    assert np.abs(zp[real] - z).max() <= 1e-13 * np.abs(z).max()
+    mask = np.ones(sp_.n_unknowns, bool)
+    mask[real] = False
+    assert np.all(zp[mask] == 0.0)
+    x, it, rr, _ = h.fgmres(s.rhs, tol=1e-8, restart=20, max_iter=300)
+    xp, itp, rrp, _ = hp.fgmres(sp_.rhs, tol=1e-8, restart=20, max_iter=300)
+    assert it == itp and abs(rr - rrp) <= 1e-12 * rr
+    assert np.abs(xp[real] - x).max() <= 1e-10 * np.abs(x).max()
+
+
+def test_unequal_fields_validation():
+    s = UNEQUAL["random_b3_21"]()
+    for kw in (dict(smooth_p=1), dict(sub_ilu=2), dict(sub_schwarz=2)):
+        with pytest.raises(oracle.OracleError):
+            oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, **kw)
+    with pytest.raises(oracle.OracleError):
+        oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, mlp=np.zeros(oracle.MLP_NPARAMS))
