@@ -13,10 +13,22 @@
  * the diagonal block present in every row; the pattern structurally
  * symmetric; vals[nnzb*b*b] FP64, each b x b block row-major.  The b dofs of a
  * node are interleaved in field order: field_of_dof[b] (HOST array) maps each
- * dof to its field block 0..F-1; it must be non-decreasing with all fields of
- * equal size fb = b / F, and (b, fb) one of: fb = b for b = 1..8 (one field),
- * fb = 2 for b = 4, 6, 8, fb = 3 for b = 6, fb = 4 for b = 8
- * (BAMG_EUNSUPPORTED otherwise).
+ * dof to its field block 0..F-1; it must start at 0 and be non-decreasing in
+ * steps of 0 or 1 (BAMG_EINVAL otherwise).  With fields of equal size fb = b / F,
+ * (b, fb) must be one of: fb = b for b = 1..8 (one field), fb = 2 for
+ * b = 4, 6, 8, fb = 3 for b = 6, fb = 4 for b = 8 (BAMG_EUNSUPPORTED otherwise).
+ * Fields of unequal size (Algorithm 1 takes field blocks of any width, e.g.
+ * velocity | pressure = {2, 1}) run padded: every field is filled up to the
+ * widest field's size fmax with dummy dofs that have one nonzero, on their own
+ * diagonal (the largest magnitude of the node's diagonal block), no coupling,
+ * a zero right-hand side and a zero iterate.  They stay zero in every step, so
+ * the results at the given dofs are the method's on the unpadded system (up to
+ * the order of rounding); the cost is that of the padded block size
+ * b' = F * fmax, which with fb = fmax must be a supported pair above
+ * (BAMG_EUNSUPPORTED otherwise, e.g. {3, 3, 1}).  Vectors passed to the calls
+ * keep the given size n_nodes*b; the introspection calls describe the padded
+ * levels (amg_block_size gives b').  Unequal fields take the tentative P, no
+ * learned weights and sub_solver 0 (BAMG_EUNSUPPORTED otherwise).
  * Stored zeros count: the node graph is the stored pattern.
  *
  * Vectors are FP64, n_nodes*b entries, node-major (dof d of node i at
@@ -439,6 +451,10 @@ int amg_level_p(bamg_t h, int level, int* nnz, int* p_rp, int* p_ci, double* p_v
 
 /* number of levels (>= 1), or a negative status */
 int amg_num_levels(bamg_t h);
+
+/* dofs per node of the hierarchy's levels: b, or the padded b' of fields of
+ * unequal size (see the conventions above); a negative status for a null handle */
+int amg_block_size(bamg_t h);
 
 /* sizes of level l: nodes, stored blocks, colours (0 on the coarsest) and the
  * number of aggregates it is coarsened into (0 on the coarsest). */

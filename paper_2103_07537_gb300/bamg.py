@@ -28,7 +28,8 @@ EXPORTS = ["amg_default_params", "amg_setup", "amg_apply", "fgmres_solve", "amg_
            "amg_profile", "amg_profile_read", "amg_profile_read_level", "amg_launch_count", "amg_colour_noalloc", "amg_setup_batched",
            "fgmres_solve_batched", "amg_num_systems", "amg_level_systems", "amg_features", "mlp_pack",
            "mlp_forward", "mlp_grad", "mlp_adam", "mlp_clip", "amg_set_omega", "amg_select", "amg_level_omega",
-           "amg_level_p", "amg_setup_fields", "amg_level_fields", "amg_dense_inverse_f32", "amg_gemm_tc_f32"]
+           "amg_level_p", "amg_setup_fields", "amg_level_fields", "amg_dense_inverse_f32", "amg_gemm_tc_f32",
+           "amg_block_size"]
 
 #: network sizes (include/bamg.h)
 NFEAT, MLP_H, MLP_OUT = 8, 64, 2
@@ -98,6 +99,7 @@ def load(build_if_missing: bool = True):
                                               _vp]
         lib.bsr_spmv.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]
         lib.amg_num_levels.argtypes = [_vp]
+        lib.amg_block_size.argtypes = [_vp]
         lib.amg_level_info.argtypes = [_vp, C.c_int, _ip, _ip, _ip, _ip]
         lib.amg_level_copy.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.amg_level_ilu.argtypes = [_vp, C.c_int, _vp]
@@ -295,6 +297,14 @@ def amg_num_levels(handle: int) -> int:
     if n < 0:
         raise BamgError(n, "amg_num_levels")
     return n
+
+
+def amg_block_size(handle: int) -> int:
+    """Dofs per node of the hierarchy's levels (the padded size for fields of unequal size)."""
+    b = load().amg_block_size(handle)
+    if b < 0:
+        raise BamgError(b, "amg_block_size")
+    return b
 
 
 def amg_level_info(handle: int, level: int):
@@ -579,7 +589,8 @@ class Solver:
         return amg_num_levels(self.handle)
 
     def level(self, l: int) -> dict:
-        return amg_level_copy(self.handle, l, self.b, self.F)
+        # the levels of a system with fields of unequal size are the padded system's
+        return amg_level_copy(self.handle, l, amg_block_size(self.handle), self.F)
 
     def ilu(self, l: int):
         return amg_level_ilu(self.handle, l, self.b, self.F)

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libbamg.so")
-SOURCES = ["k_solve.cu", "k_sweep.cu", "k_ilu.cu", "k_schwarz.cu", "k_staged.cu", "k_setup.cu", "k_krylov.cu", "k_batched.cu", "k_transfer.cu", "k_learned.cu", "k_fields.cu", "k_dense_tc.cu",
+SOURCES = ["k_solve.cu", "k_sweep.cu", "k_ilu.cu", "k_schwarz.cu", "k_staged.cu", "k_setup.cu", "k_krylov.cu", "k_batched.cu", "k_transfer.cu", "k_learned.cu", "k_fields.cu", "k_dense_tc.cu", "k_pad.cu",
            "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -238,6 +238,11 @@ struct bamg_ctx {
     int* coarse_piv = nullptr;
     bool coarse_tc_used = false;  // the FP32 coarsest LU and inverse ran on the tensor cores
     long arnoldi_steps = 0, second_projections = 0;  // of the last fgmres_solve
+    // fields of unequal size: the hierarchy is the padded system's (b above is
+    // the padded block size); vectors are padded into pad_b / pad_x on entry
+    bool padded = false;
+    PadMap pad{};
+    double *pad_b = nullptr, *pad_x = nullptr;
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -1522,10 +1527,52 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         if (step != 0 && step != 1) return BAMG_EINVAL;
         F = field_of_dof[d] + 1;
     }
-    if (b % F) return BAMG_EINVAL;
+    int fsize[kMaxB] = {}, fmax = 0;
+    for (int d = 0; d < b; ++d) fmax = std::max(fmax, ++fsize[field_of_dof[d]]);
+    bool unequal = false;
+    for (int f = 0; f < F; ++f) unequal |= fsize[f] != fmax;
+    if (unequal) {
+        // fields of unequal size: set up the padded system with equal fields
+        // (k_pad.cu); the options built on one common field size are refused
+        if (nf > 1) return BAMG_EINVAL;
+        if (prm.smooth_p || prm.mlp || prm.omega_p_arr || prm.sub_solver != 0) return BAMG_EUNSUPPORTED;
+        const int bp = F * fmax;
+        if (bp > kMaxB || !supported_block(bp, fmax)) return BAMG_EUNSUPPORTED;
+        PadMap pm;
+        pm.b = b;
+        pm.bp = bp;
+        int first[kMaxB];
+        for (int f = F - 1; f >= 0; --f) first[f] = -1;
+        for (int d = b - 1; d >= 0; --d) first[field_of_dof[d]] = d;
+        for (int q = 0; q < bp; ++q) pm.src[q] = -1;
+        for (int d = 0; d < b; ++d) {
+            const int q = field_of_dof[d] * fmax + (d - first[field_of_dof[d]]);
+            pm.dst[d] = (signed char)q;
+            pm.src[q] = (signed char)d;
+        }
+        int fmap_p[kMaxB];
+        for (int q = 0; q < bp; ++q) fmap_p[q] = q / fmax;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        double* vp = nullptr;
+        if (pool_alloc((void**)&vp, sizeof(double) * (size_t)nnzb * bp * bp, s) != cudaSuccess) return BAMG_ECUDA;
+        int st = launch_pad_values(pm, n_nodes, nnzb, row_ptr, col_idx, vals, vp, s);
+        if (st == BAMG_OK)
+            st = setup_common(row_ptr, col_idx, vp, n_nodes, nnzb, bp, fmap_p, &prm, stream, out, nsys, sys_node_off);
+        cudaFreeAsync(vp, s);
+        if (st != BAMG_OK) return st;
+        bamg_ctx* h = *out;
+        h->padded = true;
+        h->pad = pm;
+        const size_t NP = (size_t)n_nodes * bp;
+        st = h->alloc(&h->pad_b, NP);
+        if (st == BAMG_OK) st = h->alloc(&h->pad_x, NP);
+        if (st != BAMG_OK) {
+            amg_destroy(h);
+            *out = nullptr;
+        }
+        return st;
+    }
     const int fb = b / F;
-    for (int d = 0; d < b; ++d)
-        if (field_of_dof[d] != d / fb) return BAMG_EINVAL;
     if (!supported_block(b, fb)) return BAMG_EUNSUPPORTED;
     // fields on disjoint node sets: contiguous non-empty node ranges, every dof
     // of a node in the node's field, one system, the plain method
@@ -2255,7 +2302,28 @@ static int apply_impl(bamg_ctx* h, const double* r, double* z, cudaStream_t s) {
 
 extern "C" int amg_apply(bamg_t h, const double* r, double* z, void* stream) {
     if (!h || !r || !z || r == z) return BAMG_EINVAL;
-    return apply_impl(h, r, z, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->padded) {  // fields of unequal size: the cycle of the padded system
+        const long n = h->lev[0].n;
+        TRY(launch_pad_vec(h->pad, n, r, h->pad_b, s));
+        TRY(apply_impl(h, h->pad_b, h->pad_x, s));
+        return launch_unpad_vec(h->pad, n, h->pad_x, z, s);
+    }
+    return apply_impl(h, r, z, s);
+}
+
+// the solve of a padded hierarchy (fields of unequal size): b and x padded
+// into the handle's vectors, the solve on them, x unpadded
+template <class Solve>
+static int padded_solve(bamg_ctx* h, const double* b, double* x, cudaStream_t s, Solve&& solve) {
+    const long n = h->lev[0].n;
+    TRY(launch_pad_vec(h->pad, n, b, h->pad_b, s));
+    TRY(launch_pad_vec(h->pad, n, x, h->pad_x, s));
+    const int st = solve(h->pad_b, h->pad_x);
+    if (st < 0) return st;
+    TRY(launch_unpad_vec(h->pad, n, h->pad_x, x, s));
+    BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -2302,10 +2370,22 @@ static int norm_sq(bamg_ctx* h, long N, const double* x, double* dst, cudaStream
     return BAMG_OK;
 }
 
+static int fgmres_impl(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter, int* iters,
+                       double* relres, void* stream);
+
 extern "C" int fgmres_solve(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
                             int* iters, double* relres, void* stream) {
     if (!h || !b || !x || restart < 1 || restart > kMaxRestart || max_iter < 0 || !(tol >= 0.0))
         return BAMG_EINVAL;
+    if (h->padded)
+        return padded_solve(h, b, x, static_cast<cudaStream_t>(stream), [&](const double* bp, double* xp) {
+            return fgmres_impl(h, bp, xp, tol, restart, max_iter, iters, relres, stream);
+        });
+    return fgmres_impl(h, b, x, tol, restart, max_iter, iters, relres, stream);
+}
+
+static int fgmres_impl(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter, int* iters,
+                       double* relres, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int m = restart;
     TRY(ensure_krylov(h, m));
@@ -2435,9 +2515,21 @@ static int ensure_batched_krylov(bamg_ctx* h, int m) {
     return BAMG_OK;
 }
 
+static int fgmres_batched_impl(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
+                               int* iters, double* relres, void* stream);
+
 extern "C" int fgmres_solve_batched(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
                                     int* iters, double* relres, void* stream) {
     if (!h || !b || !x || restart < 1 || restart > kMaxRestart || max_iter < 0 || !(tol >= 0.0)) return BAMG_EINVAL;
+    if (h->padded)
+        return padded_solve(h, b, x, static_cast<cudaStream_t>(stream), [&](const double* bp, double* xp) {
+            return fgmres_batched_impl(h, bp, xp, tol, restart, max_iter, iters, relres, stream);
+        });
+    return fgmres_batched_impl(h, b, x, tol, restart, max_iter, iters, relres, stream);
+}
+
+static int fgmres_batched_impl(bamg_t h, const double* b, double* x, double tol, int restart, int max_iter,
+                               int* iters, double* relres, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int m = restart, S = h->nsys;
     TRY(ensure_krylov(h, m));
@@ -2669,6 +2761,8 @@ extern "C" int bsr_spmv(const int* row_ptr, const int* col_idx, const double* va
 // ---------------------------------------------------------------------------
 extern "C" int amg_num_levels(bamg_t h) { return h ? h->nlev : BAMG_EINVAL; }
 
+extern "C" int amg_block_size(bamg_t h) { return h ? h->b : BAMG_EINVAL; }
+
 extern "C" int amg_level_info(bamg_t h, int level, int* n_nodes, int* nnzb, int* n_colours, int* n_agg) {
     if (!h || level < 0 || level >= h->nlev) return BAMG_EINVAL;
     const Level& L = h->lev[level];
@@ -2710,7 +2804,8 @@ extern "C" int amg_level_ilu(bamg_t h, int level, double* lu) {
 
 extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     if (!h || !json || cap < 1) return BAMG_EINVAL;
-    std::string o = "{\"b\":" + std::to_string(h->b) + ",\"fields\":" + std::to_string(h->F) +
+    std::string o = "{\"b\":" + std::to_string(h->b) + ",\"b_given\":" + std::to_string(h->padded ? h->pad.b : h->b) +
+                    ",\"padded\":" + std::to_string(h->padded ? 1 : 0) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
                     ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"inner_sweeps\":" + std::to_string(h->p.inner_sweeps) + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";

@@ -300,6 +300,17 @@ template <typename T>
 // small colour spread over more SMs); 2: four lanes per scalar row, each
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
+// fields of unequal size run padded (k_pad.cu): padded dof q of a node is
+// place q % fmax of field q / fmax; dummy places have src -1
+struct PadMap {
+    int b = 0, bp = 0;            // dofs per node: given, padded
+    signed char src[kMaxB] = {};  // padded dof -> given dof (-1: dummy)
+    signed char dst[kMaxB] = {};  // given dof -> padded dof
+};
+int launch_pad_values(const PadMap& pm, int n, int nnzb, const int* rp, const int* ci, const double* vals,
+                      double* vp, cudaStream_t s);
+int launch_pad_vec(const PadMap& pm, long n, const double* x, double* xp, cudaStream_t s);
+int launch_unpad_vec(const PadMap& pm, long n, const double* xp, double* x, cudaStream_t s);
 // one colour of sweep q of the iterated sub-solve A_ff x~ = r_f (rf: n x fb;
 // first: higher colours count as zero; last: also writes x_out, see k_solve.cu)
 template <typename T>
