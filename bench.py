@@ -858,7 +858,8 @@ def run_ours(args):
                              "residual": [lv.get("residual_mapping") for lv in stats["levels"][:-1]],
                              "tune_us": [lv.get("tune_us") for lv in stats["levels"][:-1]],
                              "tune_step_us": [lv.get("tune_step_us") for lv in stats["levels"][:-1]],
-                             "field_major": [lv.get("field_major") for lv in stats["levels"][:-1]]},
+                             "field_major": [lv.get("field_major") for lv in stats["levels"][:-1]],
+                             "outer_spmv": stats.get("outer_mapping"), "outer_us": stats.get("outer_us")},
                 "setup_phase_ms": stats.get("setup_phase_ms"),
                 "cycle_prec": main_prec, "coarse_prec": coarse_prec,
                 "use_pdl": args.pdl,

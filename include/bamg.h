@@ -87,12 +87,15 @@ typedef struct {
                          CTAs) and keep the fastest (default); 0 = warp-per-row everywhere;
                          2 = thread-per-row everywhere; 3 = as 2 with half-size smoother CTAs;
                          4 = as 2 with four lanes per smoother row (each a quarter of the
-                         row's blocks); 5 = as 4 with every node's row staged in shared memory
+                         row's blocks) and per row of the FP64 outer SpMV; 5 = as 4 with every node's row staged in shared memory
                          by asynchronous copies ahead of use (levels whose steps read whole blocks:
                          one field, or the field-major layout; elsewhere 4; the same values
                          as 4 bit for bit); 6 = four warps per smoother node, one node per
-                         CTA, thread-per-row SpMV (long rows on small levels); 1 also times the
-                         variants of 3, 4, 5 and 6, and the persistent sweep (see sweep). With 1 the choices are kept for the
+                         CTA, thread-per-row SpMV (long rows on small levels); 7 / 8 = sixteen /
+                         eight lanes per smoother node, each lane taking whole blocks of the
+                         row (several loads in flight per lane; blocks of at most 16 values of
+                         the field rows, fb * b <= 16, elsewhere 4); 1 also times the
+                         variants of 3 to 8, and the persistent sweep (see sweep). With 1 the choices are kept for the
                          life of the process per level shape (device, sizes of the level and
                          of its colours, block and field shape, precision, layout, launch mode,
                          sub-solver): a later setup of a level of the same shape reuses them

@@ -125,10 +125,12 @@ struct Level {
     // row mapping chosen for this level: smoother 0 warp per node, 1 thread per row, 2 thread per
     // row in half-size CTAs, 3 four lanes per row, 4 four lanes per row with the rows staged in
     // shared memory by asynchronous copies (steps from a zero iterate use 3), 5 four warps per
-    // node; residual 0 warp per row, 1 thread per row
+    // node, 6 / 7 sixteen / eight lanes per node taking whole blocks; residual 0 warp per row,
+    // 1 thread per row
     int bgs_tpr = 0, spmv_tpr = 0;
-    // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split
-    float tune_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // measured: smoother warp / thread, residual warp / thread, smoother thread-half / split /
+    // staged / wide / block-split 16 / block-split 8
+    float tune_us[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int max_row = 0;  // stored blocks in the longest row (the staged smoother's slot size)
     // persistent sweep: 0 = one launch per colour (bgs_tpr), 1 = every colour of a field step
     // in one launch (thread per row), 2 = the same with four lanes per row; the plan exists
@@ -214,7 +216,8 @@ bool supported_block(int b, int fb) {
 
 struct bamg_ctx {
     int b = 0, F = 1, fb = 0, nlev = 0;
-    int outer_spmv_tpr = 0;  // row mapping of the FP64 outer SpMV
+    int outer_spmv_tpr = 0;  // row mapping of the FP64 outer SpMV: warp, thread, four lanes per row
+    float outer_us[3] = {0, 0, 0};  // their timed launches (us; kept with the choice in the tuning cache)
     int nsys = 1;  // independent systems solved together (block-diagonal operator)
     int nf = 1;    // fields on disjoint node sets (1: co-located fields only)
     // coarsest level of a batch: one dense inverse per system
@@ -789,6 +792,8 @@ static SweepArgs sweep_args(bamg_ctx* h, const Level& L, int c_lo, int c_hi) {
 // which gives the same values)
 template <typename T>
 static int launch_colour_step(bamg_ctx* h, const Level& L, const BgsArgs& a, cudaStream_t s) {
+    if (L.bgs_tpr == 6 || L.bgs_tpr == 7)
+        return launch_bgs_colour_bsp<T>(h->b, h->fb, a, L.bgs_tpr == 6 ? 16 : 8, s);
     if (L.bgs_tpr == 5) return launch_bgs_colour_wide<T>(h->b, h->fb, a, s);
     if (L.bgs_tpr == 4 && a.x_in) return launch_bgs_colour_staged<T>(h->b, h->fb, a, L.max_row, h->d_err, s);
     if (L.bgs_tpr == 4) return launch_bgs_colour_tpr<T>(h->b, h->fb, a, s, 2);
@@ -828,11 +833,15 @@ static float time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int rep
 // fields, precision, value layout, launch mode and sub-solver.
 struct TuneRec {
     int bgs_tpr, spmv_tpr, sweep;
-    float tune_us[8], tune_step_us[3];
+    float tune_us[10], tune_step_us[3];
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, TuneRec>> g_tune;  // small: one entry per distinct level shape
-std::vector<std::pair<std::string, int>> g_tune_outer;  // outer FP64 SpMV mapping per level-0 shape
+struct OuterRec {
+    int mapping;
+    float us[3];
+};
+std::vector<std::pair<std::string, OuterRec>> g_tune_outer;  // outer FP64 SpMV mapping per level-0 shape
 
 static std::string tune_key(const bamg_ctx* h, const Level& L, int l) {
     int dev = -1;
@@ -915,6 +924,8 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         L.tune_us[6] = time_launch(s, e0, e1, reps,
                                    [&] { return launch_bgs_colour_staged<T>(b, h->fb, a, L.max_row, h->d_err, s); });
         L.tune_us[7] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_wide<T>(b, h->fb, a, s); });
+        L.tune_us[8] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_bsp<T>(b, h->fb, a, 16, s); });
+        L.tune_us[9] = time_launch(s, e0, e1, reps, [&] { return launch_bgs_colour_bsp<T>(b, h->fb, a, 8, s); });
         const T* x = static_cast<const T*>(L.xa);
         const T* r = static_cast<const T*>(L.res);
         T* y = static_cast<T*>(L.xb);
@@ -931,9 +942,10 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
         if (h->p.autotune >= 2) L.bgs_tpr = h->p.autotune - 1;
         else if (h->p.autotune == 1) {
             // the fastest thread-per-row variant replaces warp per node only by the margin
-            const float tv[5] = {L.tune_us[1], L.tune_us[4], L.tune_us[5], L.tune_us[6], L.tune_us[7]};
+            const float tv[7] = {L.tune_us[1], L.tune_us[4], L.tune_us[5], L.tune_us[6],
+                                 L.tune_us[7], L.tune_us[8], L.tune_us[9]};
             int best = 0;
-            for (int v = 1; v < 5; ++v)
+            for (int v = 1; v < 7; ++v)
                 if (tv[v] < tv[best]) best = v;
             // (four warps per node replaces one warp per node on any win: the
             // same per-node structure, and in the cycle, with programmatic
@@ -942,6 +954,7 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             L.bgs_tpr = tv[best] < (best == 4 ? 1.0f : kTuneMargin) * L.tune_us[0] ? best + 1 : 0;
         }
         if (L.bgs_tpr == 4 && L.tune_us[6] >= 1e29f) L.bgs_tpr = 3;  // the staged kernel does not take this level
+        if ((L.bgs_tpr == 6 || L.bgs_tpr == 7) && !bsp_supported(b, h->fb)) L.bgs_tpr = 3;  // block too large
         if (h->p.autotune == 1 && h->p.use_pdl && (L.bgs_tpr == 0 || L.bgs_tpr == 5)) {
             // warp against four warps per node again, as a whole field step
             // (every colour of field 0) in the cycle's launch mode: with
@@ -1019,7 +1032,10 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
                std::to_string(b) + "/" + std::to_string(h->nsys);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (const auto& e : g_tune_outer)
-            if (e.first == okey) outer_cached = e.second;
+            if (e.first == okey) {
+                outer_cached = e.second.mapping;
+                memcpy(h->outer_us, e.second.us, sizeof h->outer_us);
+            }
     }
     if (outer_cached >= 0) {
         h->outer_spmv_tpr = outer_cached;
@@ -1033,10 +1049,26 @@ static int autotune_levels(bamg_ctx* h, cudaStream_t s) {
             return launch_spmv_tpr<double>(b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out,
                                            s);
         });
-        h->outer_spmv_tpr = h->p.autotune >= 2 || (h->p.autotune == 1 && t1 < kTuneMargin * t0);
+        const float t2 = time_launch(s, e0, e1, 10, [&] {
+            return launch_spmv_tpr<double>(b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, h->cyc_in, nullptr, h->cyc_out,
+                                           s, 1);
+        });
+        h->outer_us[0] = t0;
+        h->outer_us[1] = t1;
+        h->outer_us[2] = t2;
+        // 0 warp per row, 1 thread per row, 2 four lanes per row: a thread mapping
+        // replaces warp per row by the margin
+        const float tt[2] = {t1, t2};
+        const int bt = t2 < t1 ? 1 : 0;
+        h->outer_spmv_tpr = h->p.autotune >= 2 ? (h->p.autotune == 4 || h->p.autotune == 5 ? 2 : 1)
+                            : (h->p.autotune == 1 && tt[bt] < kTuneMargin * t0) ? bt + 1
+                                                                                 : 0;
         if (h->p.autotune == 1) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            if (g_tune_outer.size() < 4096) g_tune_outer.emplace_back(okey, h->outer_spmv_tpr);
+            OuterRec rec;
+            rec.mapping = h->outer_spmv_tpr;
+            memcpy(rec.us, h->outer_us, sizeof rec.us);
+            if (g_tune_outer.size() < 4096) g_tune_outer.emplace_back(okey, rec);
         }
     }
     cudaEventDestroy(e0);
@@ -1499,7 +1531,7 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
     else amg_default_params(&prm);
     if (prm.max_levels < 1 || prm.max_levels > kMaxLevels || prm.n_pre < 0 || prm.n_post < 0 ||
         !(prm.omega > 0.0) || (prm.cycle_prec != 32 && prm.cycle_prec != 64) || prm.tail_dofs < 0 ||
-        prm.autotune < 0 || prm.autotune > 6 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
+        prm.autotune < 0 || prm.autotune > 8 || (prm.smooth_p != 0 && prm.smooth_p != 1) ||
         !std::isfinite(prm.omega_p) || (prm.pr_storage != 32 && prm.pr_storage != 16) ||
         (prm.pr_storage == 16 && prm.cycle_prec != 32) || prm.omega_s_len < 0 || prm.omega_p_len < 0 ||
         (prm.omega_s_arr && prm.omega_s_len == 0) || (prm.omega_p_arr && !prm.smooth_p && !prm.mlp) ||
@@ -2360,7 +2392,8 @@ static int ensure_krylov(bamg_ctx* h, int m) {
 // y = A x (or rhs - A x) with the finest FP64 operator, in the tuned row mapping
 static int outer_spmv(bamg_ctx* h, const double* x, const double* rhs, double* y, cudaStream_t s) {
     const Level& L0 = h->lev[0];
-    return h->outer_spmv_tpr ? launch_spmv_tpr<double>(h->b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s)
+    return h->outer_spmv_tpr ? launch_spmv_tpr<double>(h->b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s,
+                                                       h->outer_spmv_tpr - 1)
                              : launch_spmv<double>(h->b, h->fb, 0, L0.n, L0.rp, L0.ci, L0.vals64, x, rhs, y, s);
 }
 
@@ -2807,7 +2840,7 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
     std::string o = "{\"b\":" + std::to_string(h->b) + ",\"b_given\":" + std::to_string(h->padded ? h->pad.b : h->b) +
                     ",\"padded\":" + std::to_string(h->padded ? 1 : 0) + ",\"fields\":" + std::to_string(h->F) +
                     ",\"node_fields\":" + std::to_string(h->nf) + ",\"cycle_prec\":" + std::to_string(h->p.cycle_prec) +
-                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"inner_sweeps\":" + std::to_string(h->p.inner_sweeps) + ",\"coarse_unknowns\":" +
+                    ",\"coarse_prec\":" + std::to_string(h->coarse_inv32 ? 32 : 64) + ",\"coarse_tc\":" + std::to_string(h->coarse_tc_used ? 1 : 0) + ",\"arnoldi_steps\":" + std::to_string(h->arnoldi_steps) + ",\"second_projections\":" + std::to_string(h->second_projections) + ",\"sub_solver\":" + std::to_string(h->p.sub_solver) + ",\"inner_sweeps\":" + std::to_string(h->p.inner_sweeps) + ",\"outer_mapping\":\"" + (h->outer_spmv_tpr == 2 ? "thread-split" : h->outer_spmv_tpr ? "thread" : "warp") + "\",\"outer_us\":[" + std::to_string(h->outer_us[0]) + "," + std::to_string(h->outer_us[1]) + "," + std::to_string(h->outer_us[2]) + "]" + ",\"coarse_unknowns\":" +
                     std::to_string(h->nd) + ",\"device_bytes\":" + std::to_string(h->bytes) + ",\"setup_phase_ms\":{";
     const char* names[8] = {"pattern", "aggregate", "galerkin", "colour", "inverse", "coarse_lu", "vectors",
                             "weights"};
@@ -2828,6 +2861,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              ",\"colouring_rounds\":" + std::to_string(L.colour_rounds) +
              ",\"smoother_mapping\":\"" + (L.sweep == 2     ? "sweep-split"
                                           : L.sweep        ? "sweep"
+                                          : L.bgs_tpr == 7 ? "block-split8"
+                                          : L.bgs_tpr == 6 ? "block-split16"
                                           : L.bgs_tpr == 5 ? "wide"
                                           : L.bgs_tpr == 4 ? "staged"
                                           : L.bgs_tpr == 3 ? "thread-split"
@@ -2842,7 +2877,8 @@ extern "C" int amg_stats(bamg_t h, char* json, int cap) {
              std::to_string(L.tune_us[1]) + "," + std::to_string(L.tune_us[2]) + "," +
              std::to_string(L.tune_us[3]) + "," + std::to_string(L.tune_us[4]) + "," +
              std::to_string(L.tune_us[5]) + "," + std::to_string(L.tune_us[6]) + "," +
-             std::to_string(L.tune_us[7]) + "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
+             std::to_string(L.tune_us[7]) + "," + std::to_string(L.tune_us[8]) + "," +
+             std::to_string(L.tune_us[9]) + "],\"field_major\":" + std::to_string(L.fm) + ",\"smoothed_p\":" + std::to_string(L.smoothed) +
              ",\"p_nnz\":" + std::to_string(L.p_nnz) + ",\"node_damping\":" + (L.omega_s64 ? "1" : "0");
         if (h->nf > 1) {
             o += ",\"field_nodes\":[";

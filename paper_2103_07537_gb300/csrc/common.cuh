@@ -300,6 +300,11 @@ template <typename T>
 // small colour spread over more SMs); 2: four lanes per scalar row, each
 // taking every fourth block (shorter dependent-load chains per thread)
 int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int variant = 0);
+// G = 8 or 16 lanes per node, each taking whole blocks (block-split; shapes
+// with fb * b <= 16, else BAMG_EUNSUPPORTED)
+bool bsp_supported(int b, int fb);
+template <typename T>
+int launch_bgs_colour_bsp(int b, int fb, const BgsArgs& a, int G, cudaStream_t s);
 // fields of unequal size run padded (k_pad.cu): padded dof q of a node is
 // place q % fmax of field q / fmax; dummy places have src -1
 struct PadMap {
@@ -396,9 +401,11 @@ int launch_schwarz_apply(const SchwarzArgs& sa, const BgsArgs& a, cudaStream_t s
 int sweep_plan(int n, int C, int ntile, const int* nodes, const int* colour, const int* colour_ptr,
                const int* tile_ptr, const int* rp, const int* ci, const unsigned char* lowk, int n_tiles,
                int* tile_of, int* dep_lo, int* dep_hi, cudaStream_t s);
+// variant 0: one thread per scalar row; 1: four lanes per scalar row, each
+// taking every fourth block (the partial sums meet by shuffles)
 template <typename T>
 int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
-                    const T* rhs, T* y, cudaStream_t s);
+                    const T* rhs, T* y, cudaStream_t s, int variant = 0);
 // y = (1 - omega) rhs - omega (upper-colour part of A) xt: the residual after one
 // pre-smoothing sweep from zero of a one-field level with one damping value
 // (xt: the sweep's x~, lowk: the lower-colour flags)

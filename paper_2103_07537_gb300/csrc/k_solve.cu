@@ -517,59 +517,83 @@ template int launch_dense_gemv<double, float>(int, const float*, const double*, 
 // levels far larger than L2).  The setup autotuner picks the mapping per
 // level and kernel by timing both.
 // ---------------------------------------------------------------------------
-template <typename T, int B, int FB, bool FM>
+// G lanes per scalar row, lane s taking blocks k0 + s, k0 + s + G, ... (G = 1:
+// the whole row); the lanes' partial sums meet by shuffles (consecutive lanes
+// of one warp).  G > 1 gives each warp fewer, longer contiguous runs of a
+// row's blocks and each lane a shorter chain of dependent loads.
+template <typename T, int B, int FB, bool FM, int G>
 __global__ void __launch_bounds__(256) spmv_tpr_kernel(int n, const int* __restrict__ rp,
                                                        const int* __restrict__ ci, const T* __restrict__ vals,
                                                        const T* __restrict__ x, const T* __restrict__ rhs,
                                                        T* __restrict__ y) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / B);
-    if (i >= n) return;
-    const int r = (int)(t - (long)i * B);
-    const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
-    // the first block before the wait (fixed for the cycle)
-    int jf = 0;
-    T af[B];
-    if (k0 < k1) {
-        jf = __ldg(ci + k0);
-        load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k0, r), af);
-    }
-    pdl_wait();
-    pdl_trigger();
+    const long row = t / G;  // scalar row i * B + r
+    const int sl = (int)(t - row * G);
+    const int i = (int)(row / B);
+    const bool act = i < n;
+    if (G == 1 && !act) return;
+    const int r = (int)(row - (long)i * B);
     T acc = T(0);
-    if (k0 < k1) {
-        T xv[B];
-        load_row<T, B>(x + (size_t)jf * B, xv);
+    if (act) {
+        const int k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+        const int kf = k0 + sl;
+        // the first block before the wait (fixed for the cycle)
+        int jf = 0;
+        T af[B];
+        if (kf < k1) {
+            jf = __ldg(ci + kf);
+            load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, kf, r), af);
+        }
+        pdl_wait();
+        pdl_trigger();
+        if (kf < k1) {
+            T xv[B];
+            load_row<T, B>(x + (size_t)jf * B, xv);
 #pragma unroll
-        for (int c = 0; c < B; ++c) acc = fma(af[c], xv[c], acc);
-    }
+            for (int c = 0; c < B; ++c) acc = fma(af[c], xv[c], acc);
+        }
 #pragma unroll 4
-    for (int k = k0 + 1; k < k1; ++k) {
-        const int j = __ldg(ci + k);
-        T a[B], xv[B];
-        load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k, r), a);
-        load_row<T, B>(x + (size_t)j * B, xv);
+        for (int k = kf + G; k < k1; k += G) {
+            const int j = __ldg(ci + k);
+            T a[B], xv[B];
+            load_row<T, B>(vrow<T, B, FB, FM>(vals, k0, k1, k, r), a);
+            load_row<T, B>(x + (size_t)j * B, xv);
 #pragma unroll
-        for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+            for (int c = 0; c < B; ++c) acc = fma(a[c], xv[c], acc);
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (!act || sl != 0) return;
     }
     y[(size_t)i * B + r] = rhs ? rhs[(size_t)i * B + r] - acc : acc;
 }
 
 template <typename T>
 int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, const T* vals, const T* x,
-                    const T* rhs, T* y, cudaStream_t s) {
+                    const T* rhs, T* y, cudaStream_t s, int variant) {
     if (n <= 0) return BAMG_OK;
-    const int blocks = ceil_div((long)n * b, 256);
+    const int G = variant == 1 ? 4 : 1;
+    const int blocks = ceil_div((long)n * b * G, 256);
     switch (b * 16 + fb) {
-#define CASE(BB, FF) \
-    case BB * 16 + FF:                                                                                      \
-        if ((fm && HasFm<T, BB, FF>::value                                                                  \
-                 ? launch_k(spmv_tpr_kernel<T, BB, FF, HasFm<T, BB, FF>::value>, blocks, 256, 0, s, n, rp, ci,     \
-                            vals, x, rhs, y)                                                                \
-                 : launch_k(spmv_tpr_kernel<T, BB, FF, false>, blocks, 256, 0, s, n, rp, ci, vals, x, rhs, y)) != \
-            cudaSuccess)                                                                                    \
-            return BAMG_ECUDA;                                                                              \
-        break;
+#define CASE(BB, FF)                                                                                         \
+    case BB * 16 + FF: {                                                                                     \
+        constexpr bool kFm = HasFm<T, BB, FF>::value;                                                       \
+        cudaError_t e;                                                                                       \
+        if (G == 4)                                                                                          \
+            e = (fm && kFm) ? launch_k(spmv_tpr_kernel<T, BB, FF, kFm, 4>, blocks, 256, 0, s, n, rp, ci, vals, \
+                                       x, rhs, y)                                                            \
+                            : launch_k(spmv_tpr_kernel<T, BB, FF, false, 4>, blocks, 256, 0, s, n, rp, ci,   \
+                                       vals, x, rhs, y);                                                     \
+        else                                                                                                 \
+            e = (fm && kFm) ? launch_k(spmv_tpr_kernel<T, BB, FF, kFm, 1>, blocks, 256, 0, s, n, rp, ci, vals, \
+                                       x, rhs, y)                                                            \
+                            : launch_k(spmv_tpr_kernel<T, BB, FF, false, 1>, blocks, 256, 0, s, n, rp, ci,   \
+                                       vals, x, rhs, y);                                                     \
+        if (e != cudaSuccess) return BAMG_ECUDA;                                                             \
+        break;                                                                                               \
+    }
         BAMG_BLOCK_SHAPES(CASE)
 #undef CASE
         default: return BAMG_EUNSUPPORTED;
@@ -577,9 +601,9 @@ int launch_spmv_tpr(int b, int fb, int fm, int n, const int* rp, const int* ci, 
     return launched(1);
 }
 template int launch_spmv_tpr<double>(int, int, int, int, const int*, const int*, const double*, const double*,
-                                     const double*, double*, cudaStream_t);
+                                     const double*, double*, cudaStream_t, int);
 template int launch_spmv_tpr<float>(int, int, int, int, const int*, const int*, const float*, const float*,
-                                    const float*, float*, cudaStream_t);
+                                    const float*, float*, cudaStream_t, int);
 
 // Residual after one pre-smoothing sweep from a zero iterate with one field
 // (F = 1) and one damping value: the sweep left x = omega x~ and, for every
@@ -758,6 +782,140 @@ int launch_bgs_colour_tpr(int b, int fb, const BgsArgs& a, cudaStream_t s, int v
 }
 template int launch_bgs_colour_tpr<double>(int, int, const BgsArgs&, cudaStream_t, int);
 template int launch_bgs_colour_tpr<float>(int, int, const BgsArgs&, cudaStream_t, int);
+
+// One colour of one field step (same arithmetic as bgs_node up to the order of
+// the row sums) with G lanes per node, each lane taking whole blocks: lane s
+// takes blocks k0 + s, k0 + s + G, ... and loads the block's FB field rows as
+// independent vector loads, so each lane has several loads in flight (the
+// four-lanes-per-row mapping has one row load per lane at a time, which
+// bounds large colours by latency).  The FB row sums of the G lanes meet by
+// shuffles within the lane group; lane r < FB finishes row r.  Blocks of
+// higher colour contribute x_in only; x~ is loaded for every block when x_in
+// is set (no branch on the colour flag before the gathers) and used where the
+// flag is set.  XIN: x_in is set.  FB x B <= 16 (the block in registers).
+template <typename T, int B, int FB, int G, bool FM, bool XIN>
+__device__ __forceinline__ void bsp_body(const BgsArgs& a, bool act, long q, int s) {
+    static_assert(32 % G == 0, "lane groups inside a warp");
+    const int f0 = a.field * FB;
+    const T* __restrict__ vals = static_cast<const T*>(a.vals);
+    const T* __restrict__ x_in = static_cast<const T*>(a.x_in);
+    const T* __restrict__ uc = static_cast<const T*>(a.uc);
+    const T* xt = static_cast<const T*>(a.xt);
+    T acc[FB];
+#pragma unroll
+    for (int r = 0; r < FB; ++r) acc[r] = T(0);
+    int i = 0;
+    if (act) {
+        i = __ldg(a.nodes + q);
+        const int k0 = __ldg(a.rp + i), k1 = __ldg(a.rp + i + 1);
+        // the FB field rows of block k: FB * B contiguous values at vb + (k - k0) VS
+        const T* vb = vrow<T, B, FB, FM>(vals, k0, k1, k0, f0);
+        constexpr int VS = vstride<T, B, FB, FM>();
+        pdl_wait();
+        pdl_trigger();
+#pragma unroll 2
+        for (int k = k0 + s; k < k1; k += G) {
+            const int j = __ldg(a.ci + k);
+            const bool low = __ldg(a.lowk + k) != 0;  // j precedes i in the colour order
+            if (!XIN && !low) continue;
+            T ar[FB][B];
+#pragma unroll
+            for (int r = 0; r < FB; ++r) load_row<T, B>(vb + (size_t)(k - k0) * VS + r * B, ar[r]);
+            T tv[FB];
+            load_row<T, FB>(xt + (size_t)j * FB, tv);
+            if constexpr (XIN) {
+                T xv[B];
+                load_row<T, B>(x_in + (size_t)j * B, xv);
+                if (uc) {
+                    T pv[B];
+                    load_row<T, B>(uc + (size_t)__ldg(a.agg + j) * B, pv);
+#pragma unroll
+                    for (int c = 0; c < B; ++c) xv[c] += pv[c];
+                }
+#pragma unroll
+                for (int r = 0; r < FB; ++r)
+#pragma unroll
+                    for (int c = 0; c < B; ++c) acc[r] = fma(ar[r][c], xv[c], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < FB; ++r)
+#pragma unroll
+                for (int c = 0; c < FB; ++c) {
+                    // column f0 + c of the row, by selects over register indices
+                    T av = ar[r][c];
+#pragma unroll
+                    for (int ff = 1; ff < B / FB; ++ff) av = (ff == a.field) ? ar[r][ff * FB + c] : av;
+                    const T nv = fma(av, tv[c], acc[r]);
+                    acc[r] = low ? nv : acc[r];
+                }
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < FB; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (!act || s >= FB) return;
+    const T* rhs = static_cast<const T*>(a.rhs) + (size_t)i * B + f0;
+    const T* D = static_cast<const T*>(a.dinv) + ((size_t)i * a.F + a.field) * FB * FB + (size_t)s * FB;
+    T xn = T(0);
+#pragma unroll
+    for (int c = 0; c < FB; ++c) xn = fma(__ldg(D + c), rhs[c] - acc[c], xn);
+    static_cast<T*>(a.xt)[(size_t)i * FB + s] = xn;
+    T* __restrict__ x_out = static_cast<T*>(a.x_out);
+    const T om = a.omega_node ? static_cast<const T*>(a.omega_node)[(size_t)i * a.F + a.field] : T(a.omega);
+    const int ag = (XIN && uc) ? __ldg(a.agg + i) : 0;
+    for (int m = 0; m < a.F; ++m) {
+        const size_t e = (size_t)i * B + m * FB + s;
+        T v = XIN ? x_in[e] : T(0);
+        if (XIN && uc) v += uc[(size_t)ag * B + m * FB + s];
+        if (m == a.field) v = fma(om, xn, v);
+        x_out[e] = v;
+    }
+}
+
+template <typename T, int B, int FB, int G, bool FM>
+__global__ void __launch_bounds__(256) bgs_bsp_kernel(BgsArgs a) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long q = t / G;
+    const int s = (int)(t - q * G);
+    const bool act = q < a.n_in_colour;
+    if (a.x_in) bsp_body<T, B, FB, G, FM, true>(a, act, q, s);
+    else bsp_body<T, B, FB, G, FM, false>(a, act, q, s);
+}
+
+bool bsp_supported(int b, int fb) { return fb * b <= 16; }
+
+template <typename T>
+int launch_bgs_colour_bsp(int b, int fb, const BgsArgs& a, int G, cudaStream_t s) {
+    if (!bsp_supported(b, fb) || (G != 8 && G != 16)) return BAMG_EUNSUPPORTED;
+    if (a.n_in_colour <= 0) return BAMG_OK;
+    const int grid = ceil_div((long)a.n_in_colour * G, 256);
+    switch (b * 16 + fb) {
+#define CASE(BB, FF)                                                                                        \
+    case BB * 16 + FF: {                                                                                    \
+        if constexpr (FF * BB <= 16) {                                                                      \
+            constexpr bool kFm = HasFm<T, BB, FF>::value;                                                  \
+            cudaError_t e;                                                                                  \
+            if (G == 16)                                                                                    \
+                e = (a.fm && kFm) ? launch_k(bgs_bsp_kernel<T, BB, FF, 16, kFm>, grid, 256, 0, s, a)        \
+                                  : launch_k(bgs_bsp_kernel<T, BB, FF, 16, false>, grid, 256, 0, s, a);     \
+            else                                                                                            \
+                e = (a.fm && kFm) ? launch_k(bgs_bsp_kernel<T, BB, FF, 8, kFm>, grid, 256, 0, s, a)         \
+                                  : launch_k(bgs_bsp_kernel<T, BB, FF, 8, false>, grid, 256, 0, s, a);      \
+            if (e != cudaSuccess) return BAMG_ECUDA;                                                        \
+            break;                                                                                          \
+        } else {                                                                                            \
+            return BAMG_EUNSUPPORTED;                                                                       \
+        }                                                                                                   \
+    }
+        BAMG_BLOCK_SHAPES(CASE)
+#undef CASE
+        default: return BAMG_EUNSUPPORTED;
+    }
+    return launched(1);
+}
+template int launch_bgs_colour_bsp<double>(int, int, const BgsArgs&, int, cudaStream_t);
+template int launch_bgs_colour_bsp<float>(int, int, const BgsArgs&, int, cudaStream_t);
 
 // One colour of one of several sweeps of the multicolour Gauss-Seidel
 // sub-solve A_ff x~ = r_f of a field step (Algorithm 1 with the sub-solve

@@ -95,7 +95,7 @@ def test_field_hierarchy_matches_oracle(name):
 
 
 @pytest.mark.parametrize("mapping", [dict(autotune=0), dict(autotune=2), dict(autotune=3), dict(autotune=4),
-                                     dict(autotune=6)])
+                                     dict(autotune=6), dict(autotune=7), dict(autotune=8)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_field_vcycle_fp64_matches_oracle(name, mapping):
     g, o, (rp, ci, vals, off) = make(SYSTEMS[name](), **mapping)

@@ -121,7 +121,8 @@ def test_hierarchy_matches_oracle(name):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mapping", [dict(tail_dofs=0, autotune=0), dict(tail_dofs=65536, autotune=0),
                                      dict(tail_dofs=0, autotune=2), dict(tail_dofs=0, autotune=3),
-                                     dict(tail_dofs=0, autotune=4), dict(tail_dofs=0, autotune=6)])
+                                     dict(tail_dofs=0, autotune=4), dict(tail_dofs=0, autotune=6),
+                                     dict(tail_dofs=0, autotune=7), dict(tail_dofs=0, autotune=8)])
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_vcycle_fp64_matches_oracle(name, mapping):
     s, kw = SYSTEMS[name]()
@@ -189,7 +190,7 @@ def test_field_major_values_bitwise(name):
     # row mapping of the smoother and the residual
     s, kw = SYSTEMS[name]()
     r = dev(np.random.default_rng(11).standard_normal(s.n_unknowns))
-    for at in (0, 2, 3, 4):
+    for at in (0, 2, 3, 4, 7, 8):
         zs = []
         for layout in (1, 2):
             g = make_solver(s, cycle_prec=32, autotune=at, value_layout=layout, **kw)
@@ -230,6 +231,52 @@ def test_row_mappings_agree_and_solve(prec, tuned):
     x = torch.zeros_like(r)
     status, it, rr = gt.solve(r, x, tol=1e-8, restart=10, max_iter=2000)
     assert status == bamg.BAMG_OK and rr <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["stokes2d_32", "stokes3d_9", "random_b4_f2", "poisson_b1", "mhd2d_41_ragged"])
+@pytest.mark.parametrize("at,mapping", [(7, "block-split16"), (8, "block-split8")])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_block_split_mappings_agree_and_solve(name, at, mapping, prec):
+    # lanes taking whole blocks: the warp mapping's cycle up to the order of
+    # the row sums; blocks of more than 16 field-row values (b = 6 with fields
+    # of 3) keep four lanes per row
+    s, kw = SYSTEMS[name]()
+    gw = make_solver(s, autotune=0, cycle_prec=prec, **kw)
+    gb = make_solver(s, autotune=at, cycle_prec=prec, **kw)
+    fb = s.b // (max(s.field_of_dof) + 1)
+    want = mapping if fb * s.b <= 16 else "thread-split"
+    assert all(lv["smoother_mapping"] == want for lv in gb.stats()["levels"][:-1])
+    r = dev(np.random.default_rng(19).standard_normal(s.n_unknowns))
+    zw, zb = torch.empty_like(r), torch.empty_like(r)
+    gw.apply(r, zw)
+    gb.apply(r, zb)
+    zb2 = torch.empty_like(r)
+    gb.apply(r, zb2)
+    torch.cuda.synchronize()
+    assert torch.equal(zb, zb2)  # a fixed order of the row sums: repeatable bit for bit
+    tol = 1e-12 if prec == 64 else 1e-5
+    assert float((zw - zb).abs().max() / zw.abs().max()) <= tol
+    x = torch.zeros_like(r)
+    status, it, rr = gb.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=2000)
+    assert status == bamg.BAMG_OK and rr <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["stokes3d_9", "mhd2d_41_ragged", "random_b6_f1"])
+def test_outer_spmv_mappings_agree(name):
+    # the FP64 outer SpMV of FGMRES as warp per row (autotune 0), thread per
+    # row (2) and four lanes per row (4): the same iterations up to rounding
+    s, kw = SYSTEMS[name]()
+    its = []
+    for at, want in ((0, "warp"), (2, "thread"), (4, "thread-split")):
+        g = make_solver(s, autotune=at, **kw)
+        assert g.stats()["outer_mapping"] == want
+        x = torch.zeros(s.n_unknowns, dtype=torch.float64, device="cuda")
+        status, it, rr = g.solve(dev(s.rhs), x, tol=1e-8, restart=30, max_iter=2000)
+        assert status == bamg.BAMG_OK and rr <= 1e-8
+        res = s.rhs - oracle.spmv(s.row_ptr, s.col_idx, s.vals, x.cpu().numpy())
+        assert np.linalg.norm(res) / np.linalg.norm(s.rhs) <= 1e-8
+        its.append(it)
+    assert max(its) - min(its) <= 1, its
 
 
 def test_vcycle_graph_and_direct_launch_agree_bitwise_and_repeat():
@@ -366,7 +413,7 @@ def test_nonfinite_rhs_reported():
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("at", [0, 6])
+@pytest.mark.parametrize("at", [0, 6, 7])
 def test_programmatic_dependent_launch_gives_identical_cycles(prec, at):
     """The V-cycle with programmatic dependent launches (default) and with
     ordinary launches: identical bits, replayed from the graph and direct."""

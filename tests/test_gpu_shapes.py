@@ -67,6 +67,7 @@ def test_shape_hierarchy_matches_oracle(name):
 
 
 @pytest.mark.parametrize("mapping", [dict(autotune=0), dict(autotune=2), dict(autotune=4), dict(autotune=5),
+                                     dict(autotune=7), dict(autotune=8),
                                      dict(autotune=0, sweep=2), dict(autotune=0, tail_dofs=1 << 30)])
 @pytest.mark.parametrize("name", list(SHAPES))
 def test_shape_vcycle_fp64_matches_oracle(name, mapping):
