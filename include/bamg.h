@@ -264,7 +264,11 @@ int fgmres_solve(bamg_t h, const double* b, double* x, double tol, int restart, 
  *   `stream`, copies the solution back to x_host and frees everything it
  *   allocated.  Arguments as amg_setup / fgmres_solve, all arrays on the host
  *   (pinned memory gives the fastest copies).  x_host holds the initial guess
- *   on entry.
+ *   on entry.  The matrix values are copied on a second stream straight into
+ *   the hierarchy's level-0 array while the setup's pattern phases (pattern
+ *   check, aggregation of level 0, the Galerkin pattern) run on `stream`; the
+ *   first use of the values waits for that copy.  With pageable memory the
+ *   copy is staged by the driver and does not overlap.
  */
 int amg_solve_host(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
                    int b, const int* field_of_dof, const amg_params* p, const double* rhs_host,

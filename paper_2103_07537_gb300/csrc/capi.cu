@@ -246,6 +246,12 @@ struct bamg_ctx {
     bool padded = false;
     PadMap pad{};
     double *pad_b = nullptr, *pad_x = nullptr;
+    // host-buffer entry points: the level-0 values come from host memory; their
+    // copy runs on cap_stream while the setup's pattern phases run on stream,
+    // and the first use of the values waits for vals_ev
+    const double* vals_host = nullptr;
+    cudaEvent_t vals_ev = nullptr;
+    bool vals_pending = false;
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -316,6 +322,8 @@ struct bamg_ctx {
             }
     }
     ~bamg_ctx() {
+        if (cap_stream) cudaStreamSynchronize(cap_stream);  // no copy into memory freed below
+        if (vals_ev) cudaEventDestroy(vals_ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         if (prof_exec) cudaGraphExecDestroy(prof_exec);
@@ -1096,6 +1104,14 @@ static int level_field_graph(bamg_ctx* h, const Level& L, int** rp_f, int** ci_f
     return BAMG_OK;
 }
 
+// the level-0 values on the device before their first use in the setup
+static int vals_ready(bamg_ctx* h, cudaStream_t s) {
+    if (!h->vals_pending) return BAMG_OK;
+    h->vals_pending = false;
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(s, h->vals_ev, 0));
+    return BAMG_OK;
+}
+
 static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const double* vals, int n,
                       int nnzb, cudaStream_t s) {
     auto tp = Clock::now();
@@ -1114,7 +1130,19 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     TRY(h->alloc(&L0.vals64, (size_t)nnzb * bb));
     BAMG_CUDA_TRY(cudaMemcpyAsync(L0.rp, row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s));
     BAMG_CUDA_TRY(cudaMemcpyAsync(L0.ci, col_idx, sizeof(int) * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
-    BAMG_CUDA_TRY(cudaMemcpyAsync(L0.vals64, vals, sizeof(double) * bb * nnzb, cudaMemcpyDeviceToDevice, s));
+    if (h->vals_host) {
+        // host values: copied on the side stream after the stream-ordered
+        // allocation above, overlapping the pattern phases below
+        BAMG_CUDA_TRY(cudaEventCreateWithFlags(&h->vals_ev, cudaEventDisableTiming));
+        BAMG_CUDA_TRY(cudaEventRecord(h->vals_ev, s));
+        BAMG_CUDA_TRY(cudaStreamWaitEvent(h->cap_stream, h->vals_ev, 0));
+        BAMG_CUDA_TRY(cudaMemcpyAsync(L0.vals64, h->vals_host, sizeof(double) * bb * nnzb, cudaMemcpyHostToDevice,
+                                      h->cap_stream));
+        BAMG_CUDA_TRY(cudaEventRecord(h->vals_ev, h->cap_stream));
+        h->vals_pending = true;
+    } else {
+        BAMG_CUDA_TRY(cudaMemcpyAsync(L0.vals64, vals, sizeof(double) * bb * nnzb, cudaMemcpyDeviceToDevice, s));
+    }
     // row_ptr consistency is checked on the host side of the device copy
     BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, L0.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 1, L0.rp, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1220,10 +1248,12 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->t_phase[1] += ms_since(tp);
         tp = Clock::now();
+        if (h->p.mlp) TRY(vals_ready(h, s));  // the features read the values
         TRY(level_weights(h, l, s, &used_s, &used_p));
         h->t_phase[7] += ms_since(tp);
         tp = Clock::now();
         if (L.smoothed) {
+            TRY(vals_ready(h, s));
             TRY(smoothed_galerkin(h, l, s));
             h->release(w.flag);
             h->release(d_count);
@@ -1252,6 +1282,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         TRY(h->alloc(&C.ci, (size_t)C.nnzb));
         TRY(h->alloc(&C.vals64, (size_t)C.nnzb * bb));
         TRY(rap_fill_cols(nc, C.rp, tmp_cols, kRapCap, C.ci, s));
+        TRY(vals_ready(h, s));  // the pattern phases above overlapped the copy of host values
         TRY(rap_numeric(b, nc, L.agg_ptr, L.members, L.rp, L.ci, L.vals64, L.agg, C.rp, C.ci, C.vals64, s));
         BAMG_CUDA_TRY(cudaStreamSynchronize(s));
         h->release(w.flag);
@@ -1265,6 +1296,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->t_phase[2] += ms_since(tp);
         tp = Clock::now();
     }
+    TRY(vals_ready(h, s));  // (a level that was not coarsened)
     if (!h->p.mlp && ((h->p.omega_s_arr && used_s != h->p.omega_s_len) ||
                       (h->p.smooth_p && h->p.omega_p_arr && used_p != h->p.omega_p_len)))
         return BAMG_EINVAL;  // the per-level arrays must match the hierarchy exactly
@@ -1513,9 +1545,12 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     return BAMG_OK;
 }
 
+// vals_on_host: vals is a host array (the host-buffer entry points); its copy
+// to the device overlaps the setup's pattern phases
 static int setup_common(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb, int b,
                         const int* field_of_dof, const amg_params* p, void* stream, bamg_t* out, int nsys,
-                        const int* sys_node_off, int nf = 1, const int* field_node_off = nullptr) {
+                        const int* sys_node_off, int nf = 1, const int* field_node_off = nullptr,
+                        bool vals_on_host = false) {
     if (!out) return BAMG_EINVAL;
     *out = nullptr;
     if (!row_ptr || !col_idx || !vals || !field_of_dof || n_nodes < 1 || nnzb < n_nodes || b < 1 || b > kMaxB)
@@ -1586,8 +1621,18 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         for (int q = 0; q < bp; ++q) fmap_p[q] = q / fmax;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         double* vp = nullptr;
+        double* vd = nullptr;  // host values: a device copy for the padding kernel
         if (pool_alloc((void**)&vp, sizeof(double) * (size_t)nnzb * bp * bp, s) != cudaSuccess) return BAMG_ECUDA;
-        int st = launch_pad_values(pm, n_nodes, nnzb, row_ptr, col_idx, vals, vp, s);
+        if (vals_on_host &&
+            (pool_alloc((void**)&vd, sizeof(double) * (size_t)nnzb * b * b, s) != cudaSuccess ||
+             cudaMemcpyAsync(vd, vals, sizeof(double) * (size_t)nnzb * b * b, cudaMemcpyHostToDevice, s) !=
+                 cudaSuccess)) {
+            if (vd) cudaFreeAsync(vd, s);
+            cudaFreeAsync(vp, s);
+            return BAMG_ECUDA;
+        }
+        int st = launch_pad_values(pm, n_nodes, nnzb, row_ptr, col_idx, vd ? vd : vals, vp, s);
+        if (vd) cudaFreeAsync(vd, s);
         if (st == BAMG_OK)
             st = setup_common(row_ptr, col_idx, vp, n_nodes, nnzb, bp, fmap_p, &prm, stream, out, nsys, sys_node_off);
         cudaFreeAsync(vp, s);
@@ -1636,7 +1681,9 @@ static int setup_common(const int* row_ptr, const int* col_idx, const double* va
         delete h;
         return BAMG_ECUDA;
     }
+    if (vals_on_host) h->vals_host = vals;
     int st = setup_impl(h, row_ptr, col_idx, vals, n_nodes, nnzb, s);
+    h->vals_host = nullptr;  // not kept
     if (st != BAMG_OK) {
         cudaStreamSynchronize(s);
         delete h;
@@ -1657,15 +1704,21 @@ extern "C" int amg_setup_batched(int nsys, const int* sys_node_off, const int* r
     return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, field_of_dof, p, stream, out, nsys, sys_node_off);
 }
 
-extern "C" int amg_setup_fields(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
-                                int b, int n_fields, const int* field_node_off, const amg_params* p, void* stream,
-                                bamg_t* out) {
+static int setup_fields(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb, int b,
+                        int n_fields, const int* field_node_off, const amg_params* p, void* stream, bamg_t* out,
+                        bool vals_on_host) {
     if (!out) return BAMG_EINVAL;
     *out = nullptr;
     if (b < 1 || b > kMaxB || n_fields < 1 || !field_node_off) return BAMG_EINVAL;
     int zeros[kMaxB] = {};
     return setup_common(row_ptr, col_idx, vals, n_nodes, nnzb, b, zeros, p, stream, out, 1, nullptr, n_fields,
-                        field_node_off);
+                        field_node_off, vals_on_host);
+}
+
+extern "C" int amg_setup_fields(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
+                                int b, int n_fields, const int* field_node_off, const amg_params* p, void* stream,
+                                bamg_t* out) {
+    return setup_fields(row_ptr, col_idx, vals, n_nodes, nnzb, b, n_fields, field_node_off, p, stream, out, false);
 }
 
 extern "C" int amg_level_fields(bamg_t h, int level, int* node_off, int* colour_off) {
@@ -2685,9 +2738,11 @@ extern "C" int amg_level_systems(bamg_t h, int level, int* sys_node_off) {
 // ---------------------------------------------------------------------------
 // end-to-end with host buffers
 // ---------------------------------------------------------------------------
-// End to end with host buffers: copies of A, b and x0 on the device (the
-// stream-ordered pool), setup(d_rp, d_ci, d_v, &h) and solve(h, d_b, d_x),
-// x back to the host, everything released.
+// End to end with host buffers: copies of the pattern, b and x0 on the device
+// (the stream-ordered pool), setup(d_rp, d_ci, vals, &h) with the HOST values
+// (the setup copies them into its own level-0 array on a side stream while its
+// pattern phases run) and solve(h, d_b, d_x), x back to the host, everything
+// released.
 template <class Setup, class Solve>
 static int solve_host_common(const int* row_ptr, const int* col_idx, const double* vals, int n_nodes, int nnzb,
                              int b, const double* rhs_host, double* x_host, void* stream, Setup&& setup,
@@ -2695,23 +2750,21 @@ static int solve_host_common(const int* row_ptr, const int* col_idx, const doubl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t N = (size_t)n_nodes * b;
     int *d_rp = nullptr, *d_ci = nullptr;
-    double *d_v = nullptr, *d_b = nullptr, *d_x = nullptr;
+    double *d_b = nullptr, *d_x = nullptr;
     int st = BAMG_OK;
     bamg_t h = nullptr;
     if (pool_alloc((void**)&d_rp, sizeof(int) * (n_nodes + 1), s) != cudaSuccess ||
         pool_alloc((void**)&d_ci, sizeof(int) * (size_t)nnzb, s) != cudaSuccess ||
-        pool_alloc((void**)&d_v, sizeof(double) * (size_t)nnzb * b * b, s) != cudaSuccess ||
         pool_alloc((void**)&d_b, sizeof(double) * N, s) != cudaSuccess ||
         pool_alloc((void**)&d_x, sizeof(double) * N, s) != cudaSuccess)
         st = BAMG_ECUDA;
     if (st == BAMG_OK &&
         (cudaMemcpyAsync(d_rp, row_ptr, sizeof(int) * (n_nodes + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
          cudaMemcpyAsync(d_ci, col_idx, sizeof(int) * (size_t)nnzb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-         cudaMemcpyAsync(d_v, vals, sizeof(double) * (size_t)nnzb * b * b, cudaMemcpyHostToDevice, s) != cudaSuccess ||
          cudaMemcpyAsync(d_b, rhs_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
          cudaMemcpyAsync(d_x, x_host, sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess))
         st = BAMG_ECUDA;
-    if (st == BAMG_OK) st = setup(d_rp, d_ci, d_v, &h);
+    if (st == BAMG_OK) st = setup(d_rp, d_ci, vals, &h);
     int solve_st = BAMG_OK;
     if (st == BAMG_OK) {
         solve_st = solve(h, d_b, d_x);
@@ -2722,7 +2775,7 @@ static int solve_host_common(const int* row_ptr, const int* col_idx, const doubl
     }
     cudaStreamSynchronize(s);
     amg_destroy(h);
-    for (void* q : {(void*)d_rp, (void*)d_ci, (void*)d_v, (void*)d_b, (void*)d_x})
+    for (void* q : {(void*)d_rp, (void*)d_ci, (void*)d_b, (void*)d_x})
         if (q) cudaFreeAsync(q, s);
     cudaStreamSynchronize(s);
     return st != BAMG_OK ? st : solve_st;
@@ -2737,7 +2790,8 @@ extern "C" int amg_solve_host(const int* row_ptr, const int* col_idx, const doub
     return solve_host_common(
         row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
         [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
-            return amg_setup(rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h);
+            return setup_common(rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h, 1, nullptr, 1, nullptr,
+                                true);
         },
         [&](bamg_t h, const double* bb, double* x) {
             return fgmres_solve(h, bb, x, tol, restart, max_iter, iters, relres, stream);
@@ -2754,7 +2808,8 @@ extern "C" int amg_solve_batched_host(int nsys, const int* sys_node_off, const i
     return solve_host_common(
         row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
         [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
-            return amg_setup_batched(nsys, sys_node_off, rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h);
+            return setup_common(rp, ci, v, n_nodes, nnzb, b, field_of_dof, p, stream, h, nsys, sys_node_off, 1,
+                                nullptr, true);
         },
         [&](bamg_t h, const double* bb, double* x) {
             return fgmres_solve_batched(h, bb, x, tol, restart, max_iter, iters, relres, stream);
@@ -2771,7 +2826,7 @@ extern "C" int amg_solve_fields_host(const int* row_ptr, const int* col_idx, con
     return solve_host_common(
         row_ptr, col_idx, vals, n_nodes, nnzb, b, rhs_host, x_host, stream,
         [&](const int* rp, const int* ci, const double* v, bamg_t* h) {
-            return amg_setup_fields(rp, ci, v, n_nodes, nnzb, b, n_fields, field_node_off, p, stream, h);
+            return setup_fields(rp, ci, v, n_nodes, nnzb, b, n_fields, field_node_off, p, stream, h, true);
         },
         [&](bamg_t h, const double* bb, double* x) {
             return fgmres_solve(h, bb, x, tol, restart, max_iter, iters, relres, stream);
