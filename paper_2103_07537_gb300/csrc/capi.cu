@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bamg_fields.h"
@@ -252,6 +253,14 @@ struct bamg_ctx {
     const double* vals_host = nullptr;
     cudaEvent_t vals_ev = nullptr;
     bool vals_pending = false;
+    // the level-0 colouring runs on its own stream, driven by its own host
+    // thread (its rounds poll a host flag), concurrently with the aggregation
+    // and Galerkin products: both need only the pattern
+    std::thread colour_thread;
+    cudaStream_t colour_stream = nullptr;
+    cudaEvent_t colour_ev = nullptr;
+    int colour_status = BAMG_OK, colour_n = 0, colour_rounds = 0;
+    int *colour_flag = nullptr, *colour_queue = nullptr, *colour_pin = nullptr;
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -322,6 +331,13 @@ struct bamg_ctx {
             }
     }
     ~bamg_ctx() {
+        if (colour_thread.joinable()) colour_thread.join();  // no kernel on memory freed below
+        if (colour_stream) {
+            cudaStreamSynchronize(colour_stream);
+            cudaStreamDestroy(colour_stream);
+        }
+        if (colour_ev) cudaEventDestroy(colour_ev);
+        pin_release(colour_pin);
         if (cap_stream) cudaStreamSynchronize(cap_stream);  // no copy into memory freed below
         if (vals_ev) cudaEventDestroy(vals_ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -1104,6 +1120,62 @@ static int level_field_graph(bamg_ctx* h, const Level& L, int** rp_f, int** ci_f
     return BAMG_OK;
 }
 
+// Start the first-fit colouring of level 0 (one field set) on the context's
+// colour stream from a second host thread; the result (the same colouring as
+// on the setup stream) is taken by colour_join.  Without a thread the
+// colouring stays in the setup's own sequence.
+static int colour_start(bamg_ctx* h, Level& L, cudaStream_t s) {
+    TRY(h->alloc(&L.colour, (size_t)L.n));
+    TRY(h->alloc(&h->colour_flag, 4));
+    TRY(h->alloc(&h->colour_queue, 2 * (size_t)L.n));
+    h->colour_pin = reinterpret_cast<int*>(pin_slot());
+    if (!h->colour_pin) return BAMG_ECUDA;
+    BAMG_CUDA_TRY(cudaStreamCreateWithFlags(&h->colour_stream, cudaStreamNonBlocking));
+    BAMG_CUDA_TRY(cudaEventCreateWithFlags(&h->colour_ev, cudaEventDisableTiming));
+    // the pattern and the stream-ordered allocations above come first
+    BAMG_CUDA_TRY(cudaEventRecord(h->colour_ev, s));
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(h->colour_stream, h->colour_ev, 0));
+    int dev = 0;
+    BAMG_CUDA_TRY(cudaGetDevice(&dev));
+    const int n = L.n;
+    const int *rp = L.rp, *ci = L.ci;
+    int* colour = L.colour;
+    try {
+        h->colour_thread = std::thread([h, dev, n, rp, ci, colour]() {
+            int st = cudaSetDevice(dev) == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
+            if (st == BAMG_OK)
+                st = colour_nodes(n, rp, ci, colour, h->colour_flag, h->colour_pin, h->colour_stream, &h->colour_n,
+                                  &h->colour_rounds, h->colour_queue);
+            if (cudaEventRecord(h->colour_ev, h->colour_stream) != cudaSuccess && st == BAMG_OK) st = BAMG_ECUDA;
+            h->colour_status = st;
+        });
+    } catch (...) {
+        // no thread: colour on the setup stream now
+        const int st = colour_nodes(n, rp, ci, colour, h->colour_flag, h->colour_pin, s, &h->colour_n,
+                                    &h->colour_rounds, h->colour_queue);
+        h->colour_status = st;
+        if (st == BAMG_OK) BAMG_CUDA_TRY(cudaEventRecord(h->colour_ev, s));
+    }
+    return BAMG_OK;
+}
+
+// the level-0 colouring of colour_start, ordered before the setup stream's
+// next work; false when none was started
+static int colour_join(bamg_ctx* h, Level& L, cudaStream_t s, bool* done) {
+    *done = false;
+    if (!h->colour_ev) return BAMG_OK;
+    if (h->colour_thread.joinable()) h->colour_thread.join();
+    TRY(h->colour_status);
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(s, h->colour_ev, 0));
+    L.n_colours = h->colour_n;
+    L.colour_rounds = h->colour_rounds;
+    h->release(h->colour_flag);
+    h->release(h->colour_queue);
+    h->colour_flag = h->colour_queue = nullptr;
+    *done = true;
+    return BAMG_OK;
+}
+
 // the level-0 values on the device before their first use in the setup
 static int vals_ready(bamg_ctx* h, cudaStream_t s) {
     if (!h->vals_pending) return BAMG_OK;
@@ -1190,6 +1262,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         }
         const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
         if (!coarsen) break;
+        if (l == 0 && h->nf == 1) TRY(colour_start(h, L, s));  // level 0 gets a smoother
         // aggregation (clone for every field: one aggregate map per level)
         AggWork w{};
         int *d_count = nullptr, *scan_tmp = nullptr;
@@ -1297,6 +1370,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         tp = Clock::now();
     }
     TRY(vals_ready(h, s));  // (a level that was not coarsened)
+    if (h->nlev == 1 && h->colour_thread.joinable()) h->colour_thread.join();  // level 0 kept no smoother
     if (!h->p.mlp && ((h->p.omega_s_arr && used_s != h->p.omega_s_len) ||
                       (h->p.smooth_p && h->p.omega_p_arr && used_p != h->p.omega_p_len)))
         return BAMG_EINVAL;  // the per-level arrays must match the hierarchy exactly
@@ -1307,22 +1381,28 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     // smoother data on every level but the coarsest
     for (int l = 0; l + 1 < h->nlev; ++l) {
         Level& L = h->lev[l];
-        TRY(h->alloc(&L.colour, (size_t)L.n));
-        int *cflag = nullptr, *queue = nullptr;
-        TRY(h->alloc(&cflag, 4));
-        TRY(h->alloc(&queue, 2 * (size_t)L.n));
-        int rounds = 0;
-        int *g_rp = L.rp, *g_ci = L.ci;
-        if (h->nf > 1) TRY(level_field_graph(h, L, &g_rp, &g_ci, s));
-        TRY(colour_nodes(L.n, g_rp, g_ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds, queue));
-        L.colour_rounds = rounds;
-        h->release(cflag);
-        h->release(queue);
+        bool coloured = false;
+        if (l == 0) TRY(colour_join(h, L, s, &coloured));
+        if (!coloured) {
+            TRY(h->alloc(&L.colour, (size_t)L.n));
+            int *cflag = nullptr, *queue = nullptr;
+            TRY(h->alloc(&cflag, 4));
+            TRY(h->alloc(&queue, 2 * (size_t)L.n));
+            int rounds = 0;
+            int *g_rp = L.rp, *g_ci = L.ci;
+            if (h->nf > 1) TRY(level_field_graph(h, L, &g_rp, &g_ci, s));
+            TRY(colour_nodes(L.n, g_rp, g_ci, L.colour, cflag, h->h_pin, s, &L.n_colours, &rounds, queue));
+            L.colour_rounds = rounds;
+            h->release(cflag);
+            h->release(queue);
+            if (h->nf > 1) {
+                h->release(g_rp);
+                h->release(g_ci);
+            }
+        }
         if (h->nf > 1) {
             // first-fit colours per field, shifted so that field g's colours
             // follow those of fields 0..g-1
-            h->release(g_rp);
-            h->release(g_ci);
             int* cm = nullptr;
             TRY(h->alloc(&cm, (size_t)h->nf + 1));
             TRY(field_colour_counts(L.n, h->nf, L.colour, L.node_field, cm, s));
