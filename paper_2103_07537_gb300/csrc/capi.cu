@@ -261,6 +261,13 @@ struct bamg_ctx {
     cudaEvent_t colour_ev = nullptr;
     int colour_status = BAMG_OK, colour_n = 0, colour_rounds = 0;
     int *colour_flag = nullptr, *colour_queue = nullptr, *colour_pin = nullptr;
+    // the tensor-core coarsest LU enqueued on cap_stream ahead of the smoother
+    // data of the finer levels (no host synchronisation inside it); its own
+    // error word, its temporaries released once the setup stream has joined it
+    bool coarse_pending = false;
+    cudaEvent_t coarse_ev = nullptr;
+    int* coarse_err = nullptr;
+    std::vector<void*> coarse_tmp;
     std::vector<void*> allocs;
     long bytes = 0;
     int* d_err = nullptr;   // device error flags [4]
@@ -337,6 +344,7 @@ struct bamg_ctx {
             cudaStreamDestroy(colour_stream);
         }
         if (colour_ev) cudaEventDestroy(colour_ev);
+        if (coarse_ev) cudaEventDestroy(coarse_ev);
         pin_release(colour_pin);
         if (cap_stream) cudaStreamSynchronize(cap_stream);  // no copy into memory freed below
         if (vals_ev) cudaEventDestroy(vals_ev);
@@ -1176,6 +1184,40 @@ static int colour_join(bamg_ctx* h, Level& L, cudaStream_t s, bool* done) {
     return BAMG_OK;
 }
 
+// The tensor-core coarsest LU and inverse of a single system (FP32 coarsest
+// solve of 224 to 2048 unknowns) enqueued on cap_stream, where it runs while
+// the setup stream builds the finer levels' smoother data; the coarse branch
+// of setup_impl joins it.  (The CUDA-core paths keep their place: their
+// cooperative kernels want every CTA resident at once.)
+static int coarse_begin(bamg_ctx* h, cudaStream_t s) {
+    if (h->nsys > 1 || h->p.coarse_prec != 32 || h->p.coarse_tc != 1) return BAMG_OK;
+    const Level& L = h->lev[h->nlev - 1];
+    const long nd = (long)L.n * h->b;
+    if (nd > kMaxCoarseDense || nd <= kCoarseTcMin || !tc_lu_supported((int)nd)) return BAMG_OK;
+    h->nd = (int)nd;
+    h->coarse_tc_used = true;
+    TRY(h->alloc(&h->coarse_a, (size_t)(nd * nd)));
+    TRY(h->alloc(&h->coarse_piv, (size_t)nd));
+    TRY(h->alloc(&h->coarse_inv32, (size_t)(nd * nd)));
+    TRY(h->alloc(&h->coarse_err, 4));
+    float *a32 = nullptr, *lt32 = nullptr, *work32 = nullptr;
+    TRY(h->alloc(&a32, (size_t)(nd * nd)));
+    TRY(h->alloc(&lt32, (size_t)(nd * nd)));
+    TRY(h->alloc(&work32, (size_t)tc_lu_scratch_floats((int)nd)));
+    h->coarse_tmp = {a32, lt32, work32};
+    BAMG_CUDA_TRY(cudaMemsetAsync(h->coarse_err, 0, 4 * sizeof(int), s));
+    BAMG_CUDA_TRY(cudaEventCreateWithFlags(&h->coarse_ev, cudaEventDisableTiming));
+    BAMG_CUDA_TRY(cudaEventRecord(h->coarse_ev, s));  // the coarsest values and the allocations above
+    cudaStream_t cs = h->cap_stream;
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(cs, h->coarse_ev, 0));
+    h->coarse_pending = true;
+    TRY(coarse_dense(h->b, L.n, L.rp, L.ci, L.vals64, h->coarse_a, cs));
+    TRY(launch_convert_d2f(nd * nd, h->coarse_a, a32, cs));
+    TRY(dense_lu_inverse_tc((int)nd, a32, h->coarse_piv, h->coarse_inv32, lt32, work32, h->coarse_err, cs));
+    BAMG_CUDA_TRY(cudaEventRecord(h->coarse_ev, cs));
+    return BAMG_OK;
+}
+
 // the level-0 values on the device before their first use in the setup
 static int vals_ready(bamg_ctx* h, cudaStream_t s) {
     if (!h->vals_pending) return BAMG_OK;
@@ -1377,6 +1419,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     // the caller's host arrays are not kept
     h->p.omega_s_arr = nullptr;
     h->p.omega_p_arr = nullptr;
+    TRY(coarse_begin(h, s));
     h->p.mlp = nullptr;
     // smoother data on every level but the coarsest
     for (int l = 0; l + 1 < h->nlev; ++l) {
@@ -1522,6 +1565,17 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         h->release(col);
         h->release(piv);
         h->nd = 0;
+        h->t_phase[5] += ms_since(tp);
+        tp = Clock::now();
+    } else if (h->coarse_pending) {
+        // the tensor-core LU enqueued by coarse_begin
+        BAMG_CUDA_TRY(cudaStreamWaitEvent(s, h->coarse_ev, 0));
+        h->coarse_pending = false;
+        BAMG_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->coarse_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CUDA_TRY(cudaStreamSynchronize(s));
+        TRY(map_dev_error(h->h_pin[0]));
+        for (void* q : h->coarse_tmp) h->release(q);
+        h->coarse_tmp.clear();
         h->t_phase[5] += ms_since(tp);
         tp = Clock::now();
     } else {
