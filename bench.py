@@ -771,6 +771,7 @@ def run_ours(args):
         bamg.amg_solve_host(rp_h, ci_h, va_h, s.n_nodes, s.nnzb, s.b, s.field_of_dof, b_h, x_h, TOL, restart,
                             MAX_ITER, params64, stream)
         tot = 0.0
+        per_call = []
         for _ in range(k_e):
             x_h[:] = 0.0
             flush.zero_()
@@ -782,13 +783,15 @@ def run_ours(args):
                                 restart, MAX_ITER, params64, stream)
             e1.record(stream)
             e1.synchronize()
-            tot += e0.elapsed_time(e1)
+            per_call.append(e0.elapsed_time(e1))
+            tot += per_call[-1]
         h2d = rp_h.nbytes + ci_h.nbytes + va_h.nbytes + b_h.nbytes + x_h.nbytes
         nsol = k_e
         if pg:
             tot, nsol = reduce_timing(pg, tot, nsol, dev)
         e2e = {"value": nsol / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(x_h.nbytes), "api": "amg_solve_host (pinned host buffers)"}
+               "d2h_bytes_per_step": int(x_h.nbytes), "api": "amg_solve_host (pinned host buffers)",
+               "ms_per_call": [round(t, 3) for t in per_call]}
 
     # --- CPU baseline: the oracle on this host ------------------------------------
     cpu = None
