@@ -86,3 +86,22 @@ def test_no_cpu_fallback():
         bamg.FieldSolver(s.node_field_off, rp, ci, va, 3)
     with pytest.raises(ValueError, match="CUDA"):
         bamg.BatchSolver([0, s.n_nodes], rp, ci, va, 3, [0, 0, 0])
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    # the binding's ctypes amg_params against the C compiler's layout of the
+    # header's struct: every field at the same offset, the same total size
+    fields = [name for name, _ in bamg.AmgParams._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "bamg.h"', 'int main(void) {',
+             '    printf("size %zu\\n", sizeof(amg_params));']
+    lines += ['    printf("%s %%zu\\n", offsetof(amg_params, %s));' % (f, f) for f in fields]
+    lines += ['    return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    assert int(got["size"]) == ctypes.sizeof(bamg.AmgParams)
+    for f in fields:
+        assert int(got[f]) == getattr(bamg.AmgParams, f).offset, f

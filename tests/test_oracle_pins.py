@@ -9,6 +9,7 @@ block-diagonal piecewise-constant transfers and cloned aggregates
 (Sec. 4.3.1); damped block Gauss-Seidel (Sec. 4.3.2, Algorithm 1).
 """
 import dataclasses
+import os
 import itertools
 
 import numpy as np
@@ -708,3 +709,25 @@ def test_unequal_fields_validation():
             oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, **kw)
     with pytest.raises(oracle.OracleError):
         oracle.Hierarchy.from_system(s, max_levels=2, max_coarse=0, mlp=np.zeros(oracle.MLP_NPARAMS))
+
+
+def test_oracle_params_layout_matches_its_header(tmp_path):
+    # the oracle binding's ctypes params against the C compiler's layout of
+    # oracle_params: the same offsets and size
+    import ctypes
+    import subprocess
+    fields = [name for name, _ in oracle.Params._fields_]
+    src = tmp_path / "layout.c"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "bamg_oracle.h"', 'int main(void) {',
+             '    printf("size %zu\\n", sizeof(oracle_params));']
+    lines += ['    printf("%s %%zu\\n", offsetof(oracle_params, %s));' % (f, f) for f in fields]
+    lines += ['    return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "oracle"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    assert int(got["size"]) == ctypes.sizeof(oracle.Params)
+    for f in fields:
+        assert int(got[f]) == getattr(oracle.Params, f).offset, f
