@@ -253,14 +253,17 @@ struct bamg_ctx {
     const double* vals_host = nullptr;
     cudaEvent_t vals_ev = nullptr;
     bool vals_pending = false;
-    // the level-0 colouring runs on its own stream, driven by its own host
-    // thread (its rounds poll a host flag), concurrently with the aggregation
-    // and Galerkin products: both need only the pattern
-    std::thread colour_thread;
-    cudaStream_t colour_stream = nullptr;
-    cudaEvent_t colour_ev = nullptr;
-    int colour_status = BAMG_OK, colour_n = 0, colour_rounds = 0;
-    int *colour_flag = nullptr, *colour_queue = nullptr, *colour_pin = nullptr;
+    // the colouring of every level that gets a smoother runs on its own stream,
+    // driven by its own host thread (its rounds poll a host flag), from the
+    // moment the level's pattern exists, concurrently with the aggregation and
+    // Galerkin products of the levels below (all need only patterns)
+    struct ColourJob {
+        std::thread thread;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev = nullptr;
+        int status = BAMG_OK, n_colours = 0, rounds = 0;
+        int *flag = nullptr, *queue = nullptr, *pin = nullptr;
+    } cjob[kMaxLevels];
     // the tensor-core coarsest LU enqueued on cap_stream ahead of the smoother
     // data of the finer levels (no host synchronisation inside it); its own
     // error word, its temporaries released once the setup stream has joined it
@@ -338,14 +341,16 @@ struct bamg_ctx {
             }
     }
     ~bamg_ctx() {
-        if (colour_thread.joinable()) colour_thread.join();  // no kernel on memory freed below
-        if (colour_stream) {
-            cudaStreamSynchronize(colour_stream);
-            cudaStreamDestroy(colour_stream);
+        for (auto& j : cjob) {
+            if (j.thread.joinable()) j.thread.join();  // no kernel on memory freed below
+            if (j.stream) {
+                cudaStreamSynchronize(j.stream);
+                cudaStreamDestroy(j.stream);
+            }
+            if (j.ev) cudaEventDestroy(j.ev);
+            pin_release(j.pin);
         }
-        if (colour_ev) cudaEventDestroy(colour_ev);
         if (coarse_ev) cudaEventDestroy(coarse_ev);
-        pin_release(colour_pin);
         if (cap_stream) cudaStreamSynchronize(cap_stream);  // no copy into memory freed below
         if (vals_ev) cudaEventDestroy(vals_ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -1128,58 +1133,59 @@ static int level_field_graph(bamg_ctx* h, const Level& L, int** rp_f, int** ci_f
     return BAMG_OK;
 }
 
-// Start the first-fit colouring of level 0 (one field set) on the context's
-// colour stream from a second host thread; the result (the same colouring as
-// on the setup stream) is taken by colour_join.  Without a thread the
-// colouring stays in the setup's own sequence.
-static int colour_start(bamg_ctx* h, Level& L, cudaStream_t s) {
+// Start the first-fit colouring of level l (one field set) on its own stream
+// from a second host thread; the result (the same colouring as on the setup
+// stream) is taken by colour_join.  Without a thread the colouring runs on the
+// setup stream at once.
+static int colour_start(bamg_ctx* h, int l, Level& L, cudaStream_t s) {
+    auto& j = h->cjob[l];
     TRY(h->alloc(&L.colour, (size_t)L.n));
-    TRY(h->alloc(&h->colour_flag, 4));
-    TRY(h->alloc(&h->colour_queue, 2 * (size_t)L.n));
-    h->colour_pin = reinterpret_cast<int*>(pin_slot());
-    if (!h->colour_pin) return BAMG_ECUDA;
-    BAMG_CUDA_TRY(cudaStreamCreateWithFlags(&h->colour_stream, cudaStreamNonBlocking));
-    BAMG_CUDA_TRY(cudaEventCreateWithFlags(&h->colour_ev, cudaEventDisableTiming));
+    TRY(h->alloc(&j.flag, 4));
+    TRY(h->alloc(&j.queue, 2 * (size_t)L.n));
+    j.pin = reinterpret_cast<int*>(pin_slot());
+    if (!j.pin) return BAMG_ECUDA;
+    BAMG_CUDA_TRY(cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking));
+    BAMG_CUDA_TRY(cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming));
     // the pattern and the stream-ordered allocations above come first
-    BAMG_CUDA_TRY(cudaEventRecord(h->colour_ev, s));
-    BAMG_CUDA_TRY(cudaStreamWaitEvent(h->colour_stream, h->colour_ev, 0));
+    BAMG_CUDA_TRY(cudaEventRecord(j.ev, s));
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(j.stream, j.ev, 0));
     int dev = 0;
     BAMG_CUDA_TRY(cudaGetDevice(&dev));
     const int n = L.n;
     const int *rp = L.rp, *ci = L.ci;
     int* colour = L.colour;
+    auto* jp = &j;
     try {
-        h->colour_thread = std::thread([h, dev, n, rp, ci, colour]() {
+        j.thread = std::thread([jp, dev, n, rp, ci, colour]() {
             int st = cudaSetDevice(dev) == cudaSuccess ? BAMG_OK : BAMG_ECUDA;
             if (st == BAMG_OK)
-                st = colour_nodes(n, rp, ci, colour, h->colour_flag, h->colour_pin, h->colour_stream, &h->colour_n,
-                                  &h->colour_rounds, h->colour_queue);
-            if (cudaEventRecord(h->colour_ev, h->colour_stream) != cudaSuccess && st == BAMG_OK) st = BAMG_ECUDA;
-            h->colour_status = st;
+                st = colour_nodes(n, rp, ci, colour, jp->flag, jp->pin, jp->stream, &jp->n_colours, &jp->rounds,
+                                  jp->queue);
+            if (cudaEventRecord(jp->ev, jp->stream) != cudaSuccess && st == BAMG_OK) st = BAMG_ECUDA;
+            jp->status = st;
         });
     } catch (...) {
         // no thread: colour on the setup stream now
-        const int st = colour_nodes(n, rp, ci, colour, h->colour_flag, h->colour_pin, s, &h->colour_n,
-                                    &h->colour_rounds, h->colour_queue);
-        h->colour_status = st;
-        if (st == BAMG_OK) BAMG_CUDA_TRY(cudaEventRecord(h->colour_ev, s));
+        j.status = colour_nodes(n, rp, ci, colour, j.flag, j.pin, s, &j.n_colours, &j.rounds, j.queue);
+        if (j.status == BAMG_OK) BAMG_CUDA_TRY(cudaEventRecord(j.ev, s));
     }
     return BAMG_OK;
 }
 
-// the level-0 colouring of colour_start, ordered before the setup stream's
-// next work; false when none was started
-static int colour_join(bamg_ctx* h, Level& L, cudaStream_t s, bool* done) {
+// the colouring of level l started by colour_start, ordered before the setup
+// stream's next work; *done false when none was started
+static int colour_join(bamg_ctx* h, int l, Level& L, cudaStream_t s, bool* done) {
+    auto& j = h->cjob[l];
     *done = false;
-    if (!h->colour_ev) return BAMG_OK;
-    if (h->colour_thread.joinable()) h->colour_thread.join();
-    TRY(h->colour_status);
-    BAMG_CUDA_TRY(cudaStreamWaitEvent(s, h->colour_ev, 0));
-    L.n_colours = h->colour_n;
-    L.colour_rounds = h->colour_rounds;
-    h->release(h->colour_flag);
-    h->release(h->colour_queue);
-    h->colour_flag = h->colour_queue = nullptr;
+    if (!j.ev) return BAMG_OK;
+    if (j.thread.joinable()) j.thread.join();
+    TRY(j.status);
+    BAMG_CUDA_TRY(cudaStreamWaitEvent(s, j.ev, 0));
+    L.n_colours = j.n_colours;
+    L.colour_rounds = j.rounds;
+    h->release(j.flag);
+    h->release(j.queue);
+    j.flag = j.queue = nullptr;
     *done = true;
     return BAMG_OK;
 }
@@ -1304,7 +1310,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         }
         const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
         if (!coarsen) break;
-        if (l == 0 && h->nf == 1) TRY(colour_start(h, L, s));  // level 0 gets a smoother
+        if (h->nf == 1) TRY(colour_start(h, l, L, s));  // level l gets a smoother
         // aggregation (clone for every field: one aggregate map per level)
         AggWork w{};
         int *d_count = nullptr, *scan_tmp = nullptr;
@@ -1412,7 +1418,8 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         tp = Clock::now();
     }
     TRY(vals_ready(h, s));  // (a level that was not coarsened)
-    if (h->nlev == 1 && h->colour_thread.joinable()) h->colour_thread.join();  // level 0 kept no smoother
+    for (int l = h->nlev - 1; l < kMaxLevels; ++l)  // a level that could not be coarsened keeps no smoother
+        if (h->cjob[l].thread.joinable()) h->cjob[l].thread.join();
     if (!h->p.mlp && ((h->p.omega_s_arr && used_s != h->p.omega_s_len) ||
                       (h->p.smooth_p && h->p.omega_p_arr && used_p != h->p.omega_p_len)))
         return BAMG_EINVAL;  // the per-level arrays must match the hierarchy exactly
@@ -1425,7 +1432,7 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     for (int l = 0; l + 1 < h->nlev; ++l) {
         Level& L = h->lev[l];
         bool coloured = false;
-        if (l == 0) TRY(colour_join(h, L, s, &coloured));
+        TRY(colour_join(h, l, L, s, &coloured));
         if (!coloured) {
             TRY(h->alloc(&L.colour, (size_t)L.n));
             int *cflag = nullptr, *queue = nullptr;
