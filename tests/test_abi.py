@@ -105,3 +105,32 @@ def test_params_struct_layout_matches_the_header(tmp_path):
     assert int(got["size"]) == ctypes.sizeof(bamg.AmgParams)
     for f in fields:
         assert int(got[f]) == getattr(bamg.AmgParams, f).offset, f
+
+
+def test_parameter_and_field_map_refusals_without_gpu():
+    # refusals of amg_setup that return before any CUDA call: inner sweeps out
+    # of range or with another sub-solver, autotune out of range, field maps
+    # that skip a field or start above 0, fields of unequal size with the
+    # options built on one field width, and a padded block wider than 8
+    lib = bamg.load()
+    ip = ctypes.POINTER(ctypes.c_int)
+    dummy = ctypes.c_void_p(16)
+    h = ctypes.c_void_p()
+
+    def setup(fmap, **kw):
+        fm = np.array(fmap, np.int32)
+        prm = bamg.amg_default_params(**kw)
+        st = lib.amg_setup(dummy, dummy, dummy, 10, 10, len(fmap), fm.ctypes.data_as(ip), ctypes.byref(prm), None,
+                           ctypes.byref(h))
+        assert not h.value
+        return st
+
+    for kw in (dict(inner_sweeps=65), dict(inner_sweeps=-1), dict(inner_sweeps=2, sub_solver=1),
+               dict(inner_sweeps=2, sub_solver=2), dict(autotune=9), dict(coarse_tc=2)):
+        assert setup([0, 0, 0, 0], **kw) == bamg.BAMG_EINVAL, kw
+    for fmap in ([0, 0, 2, 2], [1, 1, 0, 0], [0, 1, 0, 1]):
+        assert setup(fmap) == bamg.BAMG_EINVAL, fmap
+    for fmap, kw in (([0, 0, 1], dict(smooth_p=1)), ([0, 0, 1], dict(sub_solver=1)),
+                     ([0, 0, 1], dict(sub_solver=2)), ([0, 0, 0, 1, 1, 1, 2], {})):
+        assert setup(fmap, **kw) == bamg.BAMG_EUNSUPPORTED, (fmap, kw)
+    assert lib.amg_block_size(None) == bamg.BAMG_EINVAL
