@@ -1310,7 +1310,6 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
         }
         const bool coarsen = h->nlev < h->p.max_levels && (long)L.n * b > h->p.max_coarse && l + 1 < kMaxLevels;
         if (!coarsen) break;
-        if (h->nf == 1) TRY(colour_start(h, l, L, s));  // level l gets a smoother
         // aggregation (clone for every field: one aggregate map per level)
         AggWork w{};
         int *d_count = nullptr, *scan_tmp = nullptr;
@@ -1426,6 +1425,10 @@ static int setup_impl(bamg_ctx* h, const int* row_ptr, const int* col_idx, const
     // the caller's host arrays are not kept
     h->p.omega_s_arr = nullptr;
     h->p.omega_p_arr = nullptr;
+    // every smoother level's colouring beside the coarsest LU and the smoother
+    // data (the aggregation and Galerkin products above ran alone)
+    if (h->nf == 1)
+        for (int l = 0; l + 1 < h->nlev; ++l) TRY(colour_start(h, l, h->lev[l], s));
     TRY(coarse_begin(h, s));
     h->p.mlp = nullptr;
     // smoother data on every level but the coarsest
