@@ -254,9 +254,10 @@ struct bamg_ctx {
     cudaEvent_t vals_ev = nullptr;
     bool vals_pending = false;
     // the colouring of every level that gets a smoother runs on its own stream,
-    // driven by its own host thread (its rounds poll a host flag), from the
-    // moment the level's pattern exists, concurrently with the aggregation and
-    // Galerkin products of the levels below (all need only patterns)
+    // driven by its own host thread (its rounds poll a host flag), once the
+    // hierarchy's aggregation and Galerkin products are done, beside the
+    // coarsest LU and the smoother data of the other levels (it needs only the
+    // level's pattern)
     struct ColourJob {
         std::thread thread;
         cudaStream_t stream = nullptr;
